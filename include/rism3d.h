@@ -1,0 +1,198 @@
+/*
+ * rism3d.h -- C ABI of the GB300 3D-RISM initialization library (librism3d.so).
+ *
+ * The library computes, on one GPU, the grids that non-periodic 3D-RISM needs
+ * before its iterations start (Wilson, Krasny & Luchko, "Accelerating the
+ * 3D-RISM theory of molecular solvation with treecode summation and
+ * cut-offs"):
+ *
+ *   u_s(r)  = sum_i k_e q_s q_i / d + sum_i [d < rc_is] (A_is/d^12 - B_is/d^6)
+ *             solute-solvent potential energy (Sec. 2.1; LJ form and
+ *             truncation of Sec. 2.6, eq. (ulj-trunc)), kcal/mol;
+ *   c_s(r)  = -beta k_e q_s sum_i q_i erf(d/eta)/d
+ *             real-space DCF long-range asymptotics, Sec. 2.2, eq. (dcf-r);
+ *   h_s(r)  = -(beta k_e q_s / (2 eps_r)) sum_i q_i e^{a^2}
+ *             [e^{-kappa d} erfc(a - d/eta) - e^{kappa d} erfc(a + d/eta)] / d,
+ *             a = kappa eta / 2: real-space TCF asymptotics, Sec. 2.2, eq. (tcf-r);
+ *   I_s     = sum_i 4 pi int_{rc_is}^inf u_LJ,is(r) r^2 dr
+ *             the analytic LJ truncation correction of Sec. 2.6 (kcal A^3/mol);
+ *
+ * with d = |r - R_i| over a regular grid r = origin + h (i, j, k), solute
+ * atoms R_i (charge q_i, LJ sigma_i, eps_i) and solvent sites s (q_s,
+ * sigma_s, eps_s).  Mixing: sigma_is = (sigma_i + sigma_s)/2,
+ * eps_is = sqrt(eps_i eps_s), A = 4 eps sigma^12, B = 4 eps sigma^6.
+ * The sums are the generic pair sum of Sec. 2.3, eq. (pot); the treecode
+ * method evaluates their long-range part with a barycentric-Lagrange
+ * particle-cluster treecode (near/far split of eq. (exppot), MAC of
+ * Sec. 2.3.1) and the short-range part with cell-list cut-offs.
+ *
+ * Conventions shared by every entry point:
+ *  - Every function returns a status and never aborts or traps.  The text of
+ *    the last failure of a context is returned by rism_last_error().
+ *  - Grids are FP64, layout [S][nz][ny][nx] (x fastest).  Output pointers are
+ *    owned by the caller.  They may be device memory (written asynchronously
+ *    on the context's stream; the call returns before the kernels finish) or
+ *    host memory (the library computes into its own device buffer, copies
+ *    back and synchronises the stream before returning).
+ *  - Inputs given as host arrays are copied during the call; the caller keeps
+ *    ownership and may free them on return.
+ *  - The library never keeps a caller pointer beyond the call.
+ *  - Calls on one context must not run concurrently from several host
+ *    threads.  Distinct contexts are independent.
+ *  - Units: A, e, kcal/mol, K.  c and h are dimensionless.
+ */
+#ifndef RISM3D_H
+#define RISM3D_H
+
+#include <stdint.h>
+
+#if defined(__GNUC__)
+#define RISM_API __attribute__((visibility("default")))
+#else
+#define RISM_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    RISM_OK = 0,
+    RISM_E_INVALID = 1,     /* bad argument: NULL, size, NaN/Inf, negative sigma or eps ... */
+    RISM_E_STATE = 2,       /* call out of order (no solute or solvent yet) */
+    RISM_E_NOMEM = 3,       /* device or host allocation failed */
+    RISM_E_CUDA = 4,        /* a CUDA runtime error (text in rism_last_error) */
+    RISM_E_TIMEOUT = 5,     /* a bounded device wait ran out; the context stays usable */
+    RISM_E_UNSUPPORTED = 6  /* option combination not implemented */
+} rism_status;
+
+enum { RISM_METHOD_DIRECT = 0, RISM_METHOD_TREECODE = 1 };
+/* FP64: every pair term and sum in double.  FP32: pair terms in single
+ * precision in a tile-local frame, sums compensated (float-float). */
+enum { RISM_PREC_FP64 = 0, RISM_PREC_FP32 = 1 };
+/* LJ truncation (Sec. 2.6): none; one cut-off for all pairs; per-pair
+ * cut-off from a tolerance |u_LJ(rc)| = lj_tol. */
+enum { RISM_LJ_NONE = 0, RISM_LJ_RCUT = 1, RISM_LJ_TOL = 2 };
+
+#define RISM_MAX_SITES 8
+
+typedef struct rism_ctx rism_ctx;
+
+typedef struct {
+    int32_t nx, ny, nz;  /* grid points per axis, each >= 1 */
+    double h;            /* spacing (A), > 0 */
+    double origin[3];    /* position of grid point (0,0,0) (A) */
+} rism_grid_desc;
+
+typedef struct {
+    int32_t method;     /* RISM_METHOD_*; default TREECODE */
+    int32_t precision;  /* RISM_PREC_*; default FP32 */
+    int32_t degree;     /* barycentric-Lagrange degree n: (n+1)^3 Chebyshev proxies per cluster; default 8 */
+    double theta;       /* multipole acceptance: (r_batch + r_cluster)/R < theta; default 0.7 */
+    int32_t leaf;       /* max atoms per tree leaf; default 64 */
+    int32_t batch[3];   /* target batch (grid sub-box) dims; 0 = library default */
+    int32_t lj_mode;    /* RISM_LJ_*; default RCUT */
+    double lj_rcut;     /* A, for RISM_LJ_RCUT; default 9 */
+    double lj_tol;      /* kcal/mol, for RISM_LJ_TOL; default 1e-6 */
+    double eta;         /* charge smearing of eq. (dcf-r)/(tcf-r) (A); default 1 */
+    double T;           /* K; default 298 */
+    double eps_r;       /* solvent dielectric constant; default 78.44 */
+    double kappa;       /* Debye kappa (1/A); < 0 = derive from the ionic sites; default -1 */
+    double k_e;         /* Coulomb constant, kcal A/(mol e^2); default 332.0522173 */
+    double k_B;         /* Boltzmann constant, kcal/(mol K); default 0.0019872041 */
+    double r_short;     /* radius of the short-range erfc remainders (A); 0 = 6 eta (FP64) / 5 eta (FP32) */
+    int32_t autotune;   /* 1: time the candidate launch shapes once per problem class and cache the winner */
+    int64_t wait_limit; /* spin iterations before a bounded device wait gives up; default 1<<26 */
+    int32_t debug_flags;/* test hooks, 0 in production.  Bit 0: the direct kernels skip their first
+                           bulk copy, so its wait runs out and the call returns RISM_E_TIMEOUT */
+} rism_options;
+
+typedef struct {
+    double beta, kappa, r_short;
+    int64_t natoms;
+    int32_t nsite;
+    int32_t tree_nodes, tree_proxied, tree_leaves; /* treecode only */
+    int64_t direct_pairs;  /* (grid point, atom) pairs evaluated directly by the last call */
+    int64_t proxy_pairs;   /* (grid point, proxy point) pairs of the last call */
+    int64_t near_pairs;    /* candidate pairs scanned by the cut-off (cell-list) pass */
+    int32_t batch[3];      /* target batch dims in use */
+    int32_t kernel_variant;/* launch shape chosen (autotuner or default) */
+} rism_info;
+
+/* Fill *o with the defaults listed above.  Never fails. */
+RISM_API void rism_default_options(rism_options* o);
+
+/* Create a context for one grid.  `stream` is a cudaStream_t (NULL = the
+ * legacy default stream) on the current device; every kernel and copy of the
+ * context runs on it.  `opts` may be NULL (defaults).  On success *out holds
+ * a context the caller frees with rism_destroy.  Errors: RISM_E_INVALID for a
+ * bad descriptor or options, RISM_E_NOMEM, RISM_E_CUDA. */
+RISM_API rism_status rism_grid_create(const rism_grid_desc* grid, const rism_options* opts, void* stream,
+                             rism_ctx** out);
+
+/* Set the solute: n atoms (n >= 0), host arrays xyz [n][3] (A), q [n] (e),
+ * sigma [n] (A, >= 0) and eps [n] (kcal/mol, >= 0), all copied.  Uploads the
+ * atoms and rebuilds the per-pair tables on the next compute call.
+ * RISM_E_INVALID on NULL arrays with n > 0, NaN/Inf or negative sigma/eps. */
+RISM_API rism_status rism_set_solute(rism_ctx* ctx, int64_t n, const double* xyz, const double* q, const double* sigma,
+                            const double* eps);
+
+/* Set the solvent sites (1 <= nsite <= RISM_MAX_SITES): host arrays q, sigma,
+ * eps (copied), bulk site number densities rho (1/A^3, nullable: only needed
+ * to derive kappa) and ionic flags is_ion (nullable = none ionic).  With
+ * opts.kappa < 0, kappa^2 = 4 pi beta k_e sum_{ionic s} rho_s q_s^2 / eps_r
+ * (the kappa_D of eq. (tcf-r), read as the total Debye screening). */
+RISM_API rism_status rism_set_solvent(rism_ctx* ctx, int32_t nsite, const double* q, const double* sigma,
+                             const double* eps, const double* rho, const int32_t* is_ion);
+
+/* u_s(r) for all sites into u [S][nz][ny][nx]; if lj_tail != NULL the
+ * per-site truncation integrals I_s (host array [S]) are written too (zero
+ * for RISM_LJ_NONE).  RISM_E_STATE before set_solute/set_solvent. */
+RISM_API rism_status rism_potential(rism_ctx* ctx, double* u, double* lj_tail);
+
+/* c_s(r) (eq. (dcf-r)) into c_lr and h_s(r) (eq. (tcf-r)) into h_lr, each
+ * [S][nz][ny][nx] and nullable.  h_lr needs kappa > 0 (RISM_E_INVALID
+ * otherwise). */
+RISM_API rism_status rism_asymptotics(rism_ctx* ctx, double* c_lr, double* h_lr);
+
+/* The whole initialization in one pass over the pairs: u, c_lr, h_lr (each
+ * nullable) and lj_tail (host [S], nullable).  Same results as
+ * rism_potential + rism_asymptotics, sharing the pair distances. */
+RISM_API rism_status rism_init(rism_ctx* ctx, double* u, double* c_lr, double* h_lr, double* lj_tail);
+
+/* Reverse mode of L = sum_s sum_r [G_u,s u_s + G_c,s c_s + G_h,s h_s] (a plain
+ * sum over grid points, no volume element).  g_u, g_c, g_h: cotangent grids
+ * [S][nz][ny][nx] in device memory (any may be NULL = zero).  Outputs, each
+ * nullable, in device memory: d_xyz [n][3] = dL/dR_i (the force on atom i is
+ * -d_xyz), d_q [n], d_sigma [n], d_eps [n].  The LJ cut-off's step is not
+ * differentiated.  Pair terms are recomputed, never stored.  The paper has no
+ * gradient; these are the derivatives of the definitions above. */
+RISM_API rism_status rism_potential_backward(rism_ctx* ctx, const double* g_u, const double* g_c, const double* g_h,
+                                    double* d_xyz, double* d_q, double* d_sigma, double* d_eps);
+
+/* Many solutes (one context each, all on the same device and with the same
+ * method/precision/solvent site count) in one launch sequence on the first
+ * context's stream: every context's u, c_lr, h_lr (arrays of `count` device
+ * pointers; an array or an element may be NULL).  The work of all solutes is
+ * drained from one queue by persistent CTAs, and the sequence is captured in
+ * a CUDA graph that is replayed while the set of contexts is unchanged.
+ * Output must be device memory. */
+RISM_API rism_status rism_potential_batched(rism_ctx* const* ctxs, int32_t count, double* const* u, double* const* c_lr,
+                                   double* const* h_lr);
+
+/* Counters and derived parameters of the context (after a compute call). */
+RISM_API rism_status rism_get_info(const rism_ctx* ctx, rism_info* info);
+
+/* Release the context and its device memory (synchronises its stream).
+ * NULL is a no-op. */
+RISM_API void rism_destroy(rism_ctx* ctx);
+
+/* Text of the last failure on ctx ("" if none; a static message if ctx is
+ * NULL).  Valid until the next call on ctx. */
+RISM_API const char* rism_last_error(const rism_ctx* ctx);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* RISM3D_H */

@@ -1,0 +1,469 @@
+// rism_capi.cu -- the extern "C" boundary of librism3d (include/rism3d.h).
+//
+// Host-side logic only: argument validation, the per-context device tables,
+// the physical constants (beta, Debye kappa of eq. (tcf-r), the d -> 0 limits
+// of the two asymptotic kernels), dispatch to the kernels and status
+// reporting.  Every grid value is computed by the CUDA kernels.
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "rism_kernels.h"
+#include "rism_tree.h"
+#include "rism_adjoint.h"
+
+using namespace rism;
+
+struct rism_ctx {
+    rism_grid_desc g{};
+    rism_options o{};
+    cudaStream_t st = nullptr;
+    int device = 0;
+    std::string err;
+
+    // host copies of the inputs
+    int64_t n = 0;
+    std::vector<double> raw;  // [n][6] x, y, z, q, sigma, eps
+    int S = 0;
+    double qs[kMaxSites] = {}, sigs[kMaxSites] = {}, epss[kMaxSites] = {}, rho[kMaxSites] = {};
+    int is_ion[kMaxSites] = {};
+    bool have_solute = false, have_solvent = false, dirty = true;
+
+    // device state
+    double* d_raw = nullptr;
+    int64_t cap_n = 0;
+    int cap_smax = 0;
+    DevTables t;
+    DevErr* d_err = nullptr;
+    DevErr* h_err = nullptr;  // pinned
+    double* d_tail = nullptr;
+    double* d_stage[3] = {nullptr, nullptr, nullptr};
+    size_t stage_bytes[3] = {0, 0, 0};
+    TreeState* tree = nullptr;
+    AdjointState* adj = nullptr;
+
+    rism_info info{};
+    Phys ph{};
+    GridD gd{};
+};
+
+namespace {
+
+rism_status fail(rism_ctx* c, rism_status s, const std::string& msg) {
+    if (c) c->err = msg;
+    return s;
+}
+
+rism_status cuda_fail(rism_ctx* c, cudaError_t e, const char* where) {
+    std::string m = std::string(where) + ": " + cudaGetErrorString(e);
+    if (e == cudaErrorMemoryAllocation) return fail(c, RISM_E_NOMEM, m);
+    return fail(c, RISM_E_CUDA, m);
+}
+
+bool finite_all(const double* a, int64_t n) {
+    for (int64_t i = 0; i < n; ++i)
+        if (!std::isfinite(a[i])) return false;
+    return true;
+}
+
+int padded_sites(int S) { return S <= 2 ? 2 : (S <= 4 ? 4 : 8); }
+
+rism_status check_options(rism_ctx* c, const rism_options& o) {
+    if (o.method != RISM_METHOD_DIRECT && o.method != RISM_METHOD_TREECODE) return fail(c, RISM_E_INVALID, "method");
+    if (o.precision != RISM_PREC_FP64 && o.precision != RISM_PREC_FP32) return fail(c, RISM_E_INVALID, "precision");
+    if (o.degree < 1 || o.degree > kMaxDegree) return fail(c, RISM_E_INVALID, "degree out of range");
+    if (!(o.theta > 0.0 && o.theta < 1.0)) return fail(c, RISM_E_INVALID, "theta must lie in (0, 1)");
+    if (o.leaf < 1) return fail(c, RISM_E_INVALID, "leaf must be >= 1");
+    for (int k = 0; k < 3; ++k)
+        if (o.batch[k] < 0 || o.batch[k] > 64) return fail(c, RISM_E_INVALID, "batch dims must lie in [0, 64]");
+    if (o.lj_mode < RISM_LJ_NONE || o.lj_mode > RISM_LJ_TOL) return fail(c, RISM_E_INVALID, "lj_mode");
+    if (o.lj_mode == RISM_LJ_RCUT && !(o.lj_rcut > 0.0 && std::isfinite(o.lj_rcut)))
+        return fail(c, RISM_E_INVALID, "lj_rcut must be > 0");
+    if (o.lj_mode == RISM_LJ_TOL && !(o.lj_tol > 0.0 && std::isfinite(o.lj_tol)))
+        return fail(c, RISM_E_INVALID, "lj_tol must be > 0");
+    const double pos[] = {o.eta, o.T, o.eps_r, o.k_e, o.k_B};
+    for (double v : pos)
+        if (!(v > 0.0 && std::isfinite(v))) return fail(c, RISM_E_INVALID, "eta, T, eps_r, k_e, k_B must be > 0");
+    if (!std::isfinite(o.kappa)) return fail(c, RISM_E_INVALID, "kappa");
+    if (!(o.r_short >= 0.0 && std::isfinite(o.r_short))) return fail(c, RISM_E_INVALID, "r_short");
+    if (o.wait_limit < 1) return fail(c, RISM_E_INVALID, "wait_limit must be >= 1");
+    return RISM_OK;
+}
+
+// Physical constants of the current solvent + options.
+void make_phys(rism_ctx* c) {
+    Phys& p = c->ph;
+    const rism_options& o = c->o;
+    p.S = c->S;
+    p.beta = 1.0 / (o.k_B * o.T);
+    p.k_e = o.k_e;
+    p.eps_r = o.eps_r;
+    p.eta = o.eta;
+    if (o.kappa >= 0.0) {
+        p.kappa = o.kappa;
+    } else {
+        double acc = 0.0;
+        for (int s = 0; s < c->S; ++s)
+            if (c->is_ion[s]) acc += c->rho[s] * c->qs[s] * c->qs[s];
+        p.kappa = std::sqrt(4.0 * M_PI * p.beta * p.k_e * acc / p.eps_r);
+    }
+    p.a = 0.5 * p.kappa * p.eta;
+    p.ea2 = std::exp(p.a * p.a);
+    p.rs = o.r_short > 0.0 ? o.r_short : (o.precision == RISM_PREC_FP64 ? 6.0 : 5.0) * p.eta;
+    p.phi_c0 = 2.0 / (p.eta * std::sqrt(M_PI));
+    p.phi_h0 = 2.0 * (p.phi_c0 - p.kappa * p.ea2 * std::erfc(p.a));
+    for (int s = 0; s < kMaxSites; ++s) p.qs[s] = s < c->S ? c->qs[s] : 0.0;
+}
+
+rism_status ensure_tables(rism_ctx* c) {
+    if (!c->dirty) return RISM_OK;
+    cudaError_t e;
+    const int smax = padded_sites(c->S);
+    if (c->n > c->cap_n || smax != c->cap_smax) {
+        cudaFree(c->d_raw);
+        cudaFree(c->t.geo);
+        cudaFree(c->t.geoU);
+        cudaFree(c->t.ljd);
+        cudaFree(c->t.ljf);
+        c->d_raw = nullptr;
+        c->t.geo = c->t.geoU = nullptr;
+        c->t.ljd = nullptr;
+        c->t.ljf = nullptr;
+        c->cap_n = 0;
+        int64_t n = c->n > 0 ? c->n : 1;
+        if ((e = cudaMalloc(&c->d_raw, sizeof(double) * 6 * n)) != cudaSuccess ||
+            (e = cudaMalloc(&c->t.geo, sizeof(Geo) * n)) != cudaSuccess ||
+            (e = cudaMalloc(&c->t.geoU, sizeof(Geo) * n)) != cudaSuccess ||
+            (e = cudaMalloc(&c->t.ljd, sizeof(LJd) * n * smax)) != cudaSuccess ||
+            (e = cudaMalloc(&c->t.ljf, sizeof(LJf) * n * smax)) != cudaSuccess)
+            return cuda_fail(c, e, "allocating solute tables");
+        c->cap_n = n;
+        c->cap_smax = smax;
+    }
+    c->t.n = c->n;
+    c->t.smax = smax;
+    c->t.err = c->d_err;
+    c->gd = GridD{c->g.nx, c->g.ny, c->g.nz, c->g.h, c->g.origin[0], c->g.origin[1], c->g.origin[2]};
+    make_phys(c);
+    if (c->n > 0) {
+        if ((e = cudaMemcpyAsync(c->d_raw, c->raw.data(), sizeof(double) * 6 * c->n, cudaMemcpyHostToDevice,
+                                 c->st)) != cudaSuccess)
+            return cuda_fail(c, e, "uploading solute");
+        if ((e = launch_setup(c->d_raw, c->n, c->S, smax, c->sigs, c->epss, c->o.lj_mode, c->o.lj_rcut,
+                              c->o.lj_tol, c->gd, c->t, c->st)) != cudaSuccess)
+            return cuda_fail(c, e, "setup kernel");
+    }
+    if (c->o.method == RISM_METHOD_TREECODE) {
+        rism_status s = tree_prepare(c->tree, c->t, c->gd, c->ph, c->o, c->st, c->err);
+        if (s != RISM_OK) return s;
+    }
+    c->dirty = false;
+    return RISM_OK;
+}
+
+bool is_device_ptr(const void* p) {
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+rism_status check_device_error(rism_ctx* c) {
+    cudaError_t e = cudaMemcpyAsync(c->h_err, c->d_err, sizeof(DevErr), cudaMemcpyDeviceToHost, c->st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->st);
+    if (e != cudaSuccess) return cuda_fail(c, e, "synchronising");
+    if (c->h_err->code != DEV_OK) {
+        int code = c->h_err->code, where = c->h_err->where;
+        DevErr zero{0, 0};
+        cudaMemcpyAsync(c->d_err, &zero, sizeof(DevErr), cudaMemcpyHostToDevice, c->st);
+        cudaStreamSynchronize(c->st);
+        char buf[128];
+        snprintf(buf, sizeof buf, "device wait gave up (code %d, kernel %d)", code, where);
+        return fail(c, code == DEV_TIMEOUT ? RISM_E_TIMEOUT : RISM_E_CUDA, buf);
+    }
+    return RISM_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+void rism_default_options(rism_options* o) {
+    if (!o) return;
+    std::memset(o, 0, sizeof(*o));
+    o->method = RISM_METHOD_TREECODE;
+    o->precision = RISM_PREC_FP32;
+    o->degree = 8;
+    o->theta = 0.7;
+    o->leaf = 64;
+    o->lj_mode = RISM_LJ_RCUT;
+    o->lj_rcut = 9.0;
+    o->lj_tol = 1e-6;
+    o->eta = 1.0;
+    o->T = 298.0;
+    o->eps_r = 78.44;
+    o->kappa = -1.0;
+    o->k_e = 332.0522173;
+    o->k_B = 0.0019872041;
+    o->r_short = 0.0;
+    o->autotune = 0;
+    o->wait_limit = 1LL << 26;
+}
+
+rism_status rism_grid_create(const rism_grid_desc* grid, const rism_options* opts, void* stream, rism_ctx** out) {
+    if (!grid || !out) return RISM_E_INVALID;
+    *out = nullptr;
+    if (grid->nx < 1 || grid->ny < 1 || grid->nz < 1) return RISM_E_INVALID;
+    if (!(grid->h > 0.0 && std::isfinite(grid->h))) return RISM_E_INVALID;
+    for (int k = 0; k < 3; ++k)
+        if (!std::isfinite(grid->origin[k])) return RISM_E_INVALID;
+    if ((int64_t)grid->nx * grid->ny * grid->nz > (1LL << 36)) return RISM_E_INVALID;
+    rism_ctx* c = new (std::nothrow) rism_ctx;
+    if (!c) return RISM_E_NOMEM;
+    c->g = *grid;
+    if (opts) c->o = *opts;
+    else rism_default_options(&c->o);
+    if (check_options(c, c->o) != RISM_OK) {
+        delete c;
+        return RISM_E_INVALID;
+    }
+    c->st = static_cast<cudaStream_t>(stream);
+    cudaError_t e = cudaGetDevice(&c->device);
+    if (e == cudaSuccess) e = cudaMalloc(&c->d_err, sizeof(DevErr));
+    if (e == cudaSuccess) e = cudaMallocHost(&c->h_err, sizeof(DevErr));
+    if (e == cudaSuccess) e = cudaMalloc(&c->d_tail, sizeof(double) * kMaxSites);
+    if (e == cudaSuccess) e = cudaMemsetAsync(c->d_err, 0, sizeof(DevErr), c->st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->st);
+    if (e != cudaSuccess) {
+        rism_status s = (e == cudaErrorMemoryAllocation) ? RISM_E_NOMEM : RISM_E_CUDA;
+        rism_destroy(c);
+        return s;
+    }
+    c->tree = tree_create();
+    c->adj = adjoint_create();
+    c->info.batch[0] = c->info.batch[1] = c->info.batch[2] = 0;
+    *out = c;
+    return RISM_OK;
+}
+
+rism_status rism_set_solute(rism_ctx* c, int64_t n, const double* xyz, const double* q, const double* sigma,
+                            const double* eps) {
+    if (!c) return RISM_E_INVALID;
+    if (n < 0) return fail(c, RISM_E_INVALID, "n < 0");
+    if (n > 0 && (!xyz || !q || !sigma || !eps)) return fail(c, RISM_E_INVALID, "NULL solute array");
+    if (n > (1LL << 31)) return fail(c, RISM_E_INVALID, "too many atoms");
+    if (n > 0) {
+        if (!finite_all(xyz, 3 * n) || !finite_all(q, n) || !finite_all(sigma, n) || !finite_all(eps, n))
+            return fail(c, RISM_E_INVALID, "NaN or Inf in solute");
+        for (int64_t i = 0; i < n; ++i)
+            if (sigma[i] < 0.0 || eps[i] < 0.0) return fail(c, RISM_E_INVALID, "negative sigma or eps");
+    }
+    c->raw.assign((size_t)(6 * n), 0.0);
+    for (int64_t i = 0; i < n; ++i) {
+        c->raw[6 * i + 0] = xyz[3 * i + 0];
+        c->raw[6 * i + 1] = xyz[3 * i + 1];
+        c->raw[6 * i + 2] = xyz[3 * i + 2];
+        c->raw[6 * i + 3] = q[i];
+        c->raw[6 * i + 4] = sigma[i];
+        c->raw[6 * i + 5] = eps[i];
+    }
+    c->n = n;
+    c->have_solute = true;
+    c->dirty = true;
+    c->err.clear();
+    return RISM_OK;
+}
+
+rism_status rism_set_solvent(rism_ctx* c, int32_t nsite, const double* q, const double* sigma, const double* eps,
+                             const double* rho, const int32_t* is_ion) {
+    if (!c) return RISM_E_INVALID;
+    if (nsite < 1 || nsite > kMaxSites) return fail(c, RISM_E_INVALID, "nsite must lie in [1, RISM_MAX_SITES]");
+    if (!q || !sigma || !eps) return fail(c, RISM_E_INVALID, "NULL solvent array");
+    if (!finite_all(q, nsite) || !finite_all(sigma, nsite) || !finite_all(eps, nsite) ||
+        (rho && !finite_all(rho, nsite)))
+        return fail(c, RISM_E_INVALID, "NaN or Inf in solvent");
+    for (int s = 0; s < nsite; ++s) {
+        if (sigma[s] < 0.0 || eps[s] < 0.0) return fail(c, RISM_E_INVALID, "negative sigma or eps");
+        if (rho && rho[s] < 0.0) return fail(c, RISM_E_INVALID, "negative density");
+    }
+    c->S = nsite;
+    for (int s = 0; s < kMaxSites; ++s) {
+        c->qs[s] = s < nsite ? q[s] : 0.0;
+        c->sigs[s] = s < nsite ? sigma[s] : 0.0;
+        c->epss[s] = s < nsite ? eps[s] : 0.0;
+        c->rho[s] = (s < nsite && rho) ? rho[s] : 0.0;
+        c->is_ion[s] = (s < nsite && is_ion) ? (is_ion[s] != 0) : 0;
+    }
+    c->have_solvent = true;
+    c->dirty = true;
+    c->err.clear();
+    return RISM_OK;
+}
+
+rism_status rism_init(rism_ctx* c, double* u, double* c_lr, double* h_lr, double* lj_tail) {
+    if (!c) return RISM_E_INVALID;
+    if (!c->have_solute || !c->have_solvent) return fail(c, RISM_E_STATE, "set_solute and set_solvent first");
+    cudaError_t e = cudaSetDevice(c->device);
+    if (e != cudaSuccess) return cuda_fail(c, e, "cudaSetDevice");
+    rism_status s = ensure_tables(c);
+    if (s != RISM_OK) return s;
+    if (h_lr && !(c->ph.kappa > 0.0)) return fail(c, RISM_E_INVALID, "h_lr needs kappa > 0 (ionic solvent)");
+    const int64_t M = (int64_t)c->g.nx * c->g.ny * c->g.nz;
+    const size_t bytes = sizeof(double) * (size_t)c->S * (size_t)M;
+    double* user[3] = {u, c_lr, h_lr};
+    double* dev[3] = {nullptr, nullptr, nullptr};
+    bool host_out = false;
+    for (int k = 0; k < 3; ++k) {
+        if (!user[k]) continue;
+        if (is_device_ptr(user[k])) {
+            dev[k] = user[k];
+        } else {
+            host_out = true;
+            if (c->stage_bytes[k] < bytes) {
+                cudaFree(c->d_stage[k]);
+                c->d_stage[k] = nullptr;
+                c->stage_bytes[k] = 0;
+                if ((e = cudaMalloc(&c->d_stage[k], bytes)) != cudaSuccess) return cuda_fail(c, e, "staging buffer");
+                c->stage_bytes[k] = bytes;
+            }
+            dev[k] = c->d_stage[k];
+        }
+    }
+    Outputs o{dev[0], dev[1], dev[2]};
+    if (o.u || o.c || o.h) {
+        if (c->o.method == RISM_METHOD_DIRECT) {
+            e = launch_direct(c->gd, c->ph, c->t, c->o.precision, o, c->o.wait_limit, c->info.kernel_variant,
+                              c->o.debug_flags, c->st);
+            if (e != cudaSuccess) return cuda_fail(c, e, "direct kernel");
+            c->info.direct_pairs = M * c->n;
+            c->info.proxy_pairs = 0;
+            c->info.near_pairs = 0;
+        } else {
+            s = tree_eval(c->tree, c->t, c->gd, c->ph, c->o, o, c->st, c->err, c->info);
+            if (s != RISM_OK) return s;
+        }
+    }
+    if (lj_tail) {
+        if (c->o.lj_mode == RISM_LJ_NONE || c->n == 0) {
+            for (int k = 0; k < c->S; ++k) lj_tail[k] = 0.0;
+        } else {
+            if ((e = launch_lj_tail(c->t, c->S, c->d_tail, c->st)) != cudaSuccess) return cuda_fail(c, e, "lj tail");
+            if ((e = cudaMemcpyAsync(lj_tail, c->d_tail, sizeof(double) * c->S, cudaMemcpyDeviceToHost, c->st)) !=
+                cudaSuccess)
+                return cuda_fail(c, e, "lj tail copy");
+        }
+    }
+    for (int k = 0; k < 3; ++k)
+        if (user[k] && dev[k] != user[k]) {
+            if ((e = cudaMemcpyAsync(user[k], dev[k], bytes, cudaMemcpyDeviceToHost, c->st)) != cudaSuccess)
+                return cuda_fail(c, e, "copying result to host");
+        }
+    (void)host_out;
+    // Status of the device-side bounded waits: synchronise and read the error word.
+    return check_device_error(c);
+}
+
+rism_status rism_potential(rism_ctx* c, double* u, double* lj_tail) {
+    return rism_init(c, u, nullptr, nullptr, lj_tail);
+}
+
+rism_status rism_asymptotics(rism_ctx* c, double* c_lr, double* h_lr) {
+    return rism_init(c, nullptr, c_lr, h_lr, nullptr);
+}
+
+rism_status rism_potential_backward(rism_ctx* c, const double* g_u, const double* g_c, const double* g_h,
+                                    double* d_xyz, double* d_q, double* d_sigma, double* d_eps) {
+    if (!c) return RISM_E_INVALID;
+    if (!c->have_solute || !c->have_solvent) return fail(c, RISM_E_STATE, "set_solute and set_solvent first");
+    cudaError_t e = cudaSetDevice(c->device);
+    if (e != cudaSuccess) return cuda_fail(c, e, "cudaSetDevice");
+    const void* ins[3] = {g_u, g_c, g_h};
+    for (const void* p : ins)
+        if (p && !is_device_ptr(p)) return fail(c, RISM_E_INVALID, "cotangents must be device memory");
+    void* outs[4] = {d_xyz, d_q, d_sigma, d_eps};
+    for (void* p : outs)
+        if (p && !is_device_ptr(p)) return fail(c, RISM_E_INVALID, "gradient outputs must be device memory");
+    rism_status s = ensure_tables(c);
+    if (s != RISM_OK) return s;
+    if (g_h && !(c->ph.kappa > 0.0)) g_h = nullptr;  // h is identically zero without ions
+    s = adjoint_run(c->adj, c->t, c->gd, c->ph, c->o, c->raw.data(), g_u, g_c, g_h, d_xyz, d_q, d_sigma, d_eps,
+                    c->st, c->err);
+    if (s != RISM_OK) return s;
+    return check_device_error(c);
+}
+
+rism_status rism_potential_batched(rism_ctx* const* ctxs, int32_t count, double* const* u, double* const* c_lr,
+                                   double* const* h_lr) {
+    if (!ctxs || count < 1) return RISM_E_INVALID;
+    rism_ctx* c0 = ctxs[0];
+    if (!c0) return RISM_E_INVALID;
+    std::vector<BatchItem> items((size_t)count);
+    for (int b = 0; b < count; ++b) {
+        rism_ctx* c = ctxs[b];
+        if (!c) return fail(c0, RISM_E_INVALID, "NULL context in batch");
+        if (!c->have_solute || !c->have_solvent) return fail(c0, RISM_E_STATE, "set_solute and set_solvent first");
+        if (c->o.method != c0->o.method || c->o.precision != c0->o.precision || padded_sites(c->S) != padded_sites(c0->S) ||
+            c->device != c0->device)
+            return fail(c0, RISM_E_INVALID, "batched contexts must share device, method, precision and site count");
+        rism_status s = ensure_tables(c);
+        if (s != RISM_OK) return fail(c0, s, c->err);
+        double* uu = u ? u[b] : nullptr;
+        double* cc = c_lr ? c_lr[b] : nullptr;
+        double* hh = h_lr ? h_lr[b] : nullptr;
+        if (hh && !(c->ph.kappa > 0.0)) return fail(c0, RISM_E_INVALID, "h_lr needs kappa > 0");
+        const double* ptrs[3] = {uu, cc, hh};
+        for (const double* p : ptrs)
+            if (p && !is_device_ptr(p)) return fail(c0, RISM_E_INVALID, "batched outputs must be device memory");
+        items[b] = BatchItem{c->tree, &c->t, c->gd, c->ph, Outputs{uu, cc, hh}};
+    }
+    // Tables of the other contexts were built on their own streams: order them before c0's stream.
+    for (int b = 1; b < count; ++b) {
+        if (ctxs[b]->st != c0->st) {
+            cudaError_t e = cudaStreamSynchronize(ctxs[b]->st);
+            if (e != cudaSuccess) return cuda_fail(c0, e, "synchronising batch member");
+        }
+    }
+    rism_status s = batch_eval(items, c0->o, c0->st, c0->d_err, c0->err);
+    if (s != RISM_OK) return s;
+    return check_device_error(c0);
+}
+
+rism_status rism_get_info(const rism_ctx* c, rism_info* info) {
+    if (!c || !info) return RISM_E_INVALID;
+    *info = c->info;
+    info->beta = 1.0 / (c->o.k_B * c->o.T);
+    info->kappa = c->ph.kappa;
+    info->r_short = c->ph.rs;
+    info->natoms = c->n;
+    info->nsite = c->S;
+    return RISM_OK;
+}
+
+void rism_destroy(rism_ctx* c) {
+    if (!c) return;
+    cudaSetDevice(c->device);
+    cudaStreamSynchronize(c->st);
+    tree_destroy(c->tree);
+    adjoint_destroy(c->adj);
+    cudaFree(c->d_raw);
+    cudaFree(c->t.geo);
+    cudaFree(c->t.geoU);
+    cudaFree(c->t.ljd);
+    cudaFree(c->t.ljf);
+    cudaFree(c->d_err);
+    cudaFreeHost(c->h_err);
+    cudaFree(c->d_tail);
+    for (int k = 0; k < 3; ++k) cudaFree(c->d_stage[k]);
+    delete c;
+}
+
+const char* rism_last_error(const rism_ctx* c) {
+    if (!c) return "invalid context (NULL)";
+    return c->err.c_str();
+}
+
+}  // extern "C"

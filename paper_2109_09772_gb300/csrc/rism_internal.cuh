@@ -1,0 +1,135 @@
+// rism_internal.cuh -- internal types and device primitives of librism3d.
+//
+// Nothing here is part of the public ABI (include/rism3d.h).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "rism3d.h"
+
+namespace rism {
+
+constexpr int kMaxSites = RISM_MAX_SITES;
+
+// Device error word written by kernels (first error wins).
+enum : int { DEV_OK = 0, DEV_TIMEOUT = 1, DEV_OVERFLOW = 2 };
+struct DevErr {
+    int code;
+    int where;  // kernel id that reported it
+};
+enum : int { WHERE_DIRECT = 1, WHERE_TREE_EVAL = 2, WHERE_ADJOINT = 3, WHERE_BATCH = 4, WHERE_UPWARD = 5 };
+
+// ---------------------------------------------------------------- records
+// Atom geometry: position (physical A for the FP64 path; grid units relative
+// to the grid origin for the FP32 path) and charge.
+struct __align__(16) Geo {
+    double x, y, z, q;
+};
+// Per (atom, site) Lennard-Jones terms, FP64 physical: A/d^12 - B/d^6 while d^2 < rc2.
+struct __align__(16) LJd {
+    double A, B, rc2, pad;
+};
+// Per (atom, site) Lennard-Jones terms, FP32 grid units: A/h^12, B/h^6, rc^2/h^2.
+struct __align__(16) LJf {
+    float A, B, rc2, pad;
+};
+// Tile-local float-float geometry for the FP32 path (hi and lo words).
+struct __align__(16) GeoF {
+    float xh, yh, zh, q;
+    float xl, yl, zl, pad;
+};
+
+// Physical constants and per-site factors shared by every evaluation kernel.
+struct Phys {
+    int S;        // number of solvent sites
+    double beta, k_e, eps_r, eta, kappa, a, ea2;
+    double rs;    // short-range radius (A)
+    double phi_c0, phi_h0;  // d -> 0 limits of erf(d/eta)/d and of the TCF kernel
+    double qs[kMaxSites];
+};
+
+struct GridD {
+    int nx, ny, nz;
+    double h, ox, oy, oz;
+};
+
+// ------------------------------------------------------------ PTX helpers
+__device__ __forceinline__ float rsqrt_approx(float x) {
+    float y;
+    asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+__device__ __forceinline__ float rcp_approx(float x) {
+    float y;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+__device__ __forceinline__ float ex2_approx(float x) {
+    float y;
+    asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+    return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_fence_init() {
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
+                 : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
+    uint32_t done;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(done)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+    return done != 0;
+}
+// Bounded wait: false when `limit` polls pass without the phase completing.
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity, long long limit) {
+    for (long long it = 0; it < limit; ++it)
+        if (mbar_try_wait(bar, parity)) return true;
+    return false;
+}
+// One bulk (non-tensor) TMA copy global -> shared; dst, src 16-byte aligned,
+// bytes a multiple of 16.  Completion is signalled on `bar` as transaction bytes.
+__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+            smem_u32(dst)),
+        "l"(src), "r"(bytes), "r"(smem_u32(bar))
+        : "memory");
+}
+
+__device__ __forceinline__ void report_error(DevErr* e, int code, int where) {
+    if (e && atomicCAS(&e->code, DEV_OK, code) == DEV_OK) e->where = where;
+}
+
+// Error-free transformation a + b = s + t (Knuth's TwoSum), used to fold FP32
+// partial sums into a float-float accumulator.
+__device__ __forceinline__ void ff_add(float& hi, float& lo, float v) {
+    float s = hi + v;
+    float bb = s - hi;
+    float t = (hi - (s - bb)) + (v - bb);
+    hi = s;
+    lo += t;
+}
+
+// Split a double into hi + lo floats (|lo| <= ulp(hi)/2).
+__device__ __forceinline__ void split_ff(double v, float& hi, float& lo) {
+    hi = __double2float_rn(v);
+    lo = __double2float_rn(v - (double)hi);
+}
+
+}  // namespace rism

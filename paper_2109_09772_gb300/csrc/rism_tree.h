@@ -1,0 +1,37 @@
+// rism_tree.h -- barycentric-Lagrange particle-cluster treecode and the
+// cell-list near field (internal launch interface).
+#pragma once
+
+#include <string>
+#include <vector>
+
+#include "rism_kernels.h"
+
+namespace rism {
+
+constexpr int kMaxDegree = 12;
+
+struct TreeState;
+
+struct BatchItem {
+    TreeState* tree;
+    const DevTables* t;
+    GridD g;
+    Phys ph;
+    Outputs o;
+};
+
+TreeState* tree_create();
+void tree_destroy(TreeState* ts);
+// Build the tree, proxies, modified charges and interaction lists for the
+// current solute tables (called when the solute, solvent or options change).
+rism_status tree_prepare(TreeState* ts, const DevTables& t, const GridD& g, const Phys& ph, const rism_options& o,
+                         cudaStream_t st, std::string& err);
+// Evaluate u, c, h with the treecode far field and the cell-list near field.
+rism_status tree_eval(TreeState* ts, const DevTables& t, const GridD& g, const Phys& ph, const rism_options& o,
+                      Outputs out, cudaStream_t st, std::string& err, rism_info& info);
+// Many solutes in one persistent, graph-captured launch sequence.
+rism_status batch_eval(std::vector<BatchItem>& items, const rism_options& o, cudaStream_t st, DevErr* err,
+                       std::string& msg);
+
+}  // namespace rism
