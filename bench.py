@@ -1,0 +1,371 @@
+"""Benchmark of the 3D-RISM initialization path on GB300.
+
+One step = one whole initialization of one solute through the C ABI:
+solute upload, per-pair tables (mixing, cut-offs), tree build, proxy charges,
+interaction lists, evaluation of u, c_lr, h_lr for every grid point and
+solvent site, and the LJ tail integrals.  Workload: the 2,000-atom globule
+(net +8) on a 128^3 grid at 0.5 A with water O/H + 0.1 M Na+/Cl- sites,
+LJ cut-off 9 A, treecode degree 8, theta 0.7 (synthetic, seeded).
+
+value  = grid-point x site evaluations per second (Gpts.site/s), device
+         outputs, CUDA events on the library's stream, L2 flushed between
+         steps (256 MB write outside the timed events).
+e2e    = the same step with HOST output buffers (pinned), the device-to-host
+         copy of u, c, h inside the timed region.
+Under torchrun each rank runs its own seeded solute (independent problems,
+no collective): weak scaling, value = all ranks' points / max rank time.
+
+--impl reference times the FP64 CPU oracle (the reference arm of this
+project) on a bounded sample of the same workload on the host cores.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "grid-pt·site evals/s & init time per solute at stated error vs FP64 direct"
+UNIT = "Gpts·site/s"
+WORKLOAD = "globule2000_128cubed"
+
+
+def _workload(seed=0):
+    from paper_2109_09772_gb300 import inputs as I
+
+    return I.workload(1, seed=seed)
+
+
+def _config(w, method, precision):
+    return {"workload": WORKLOAD, "atoms": w.solute.n, "grid": list(w.grid.n), "spacing_A": w.grid.h,
+            "sites": w.solvent.nsite, "lj_rcut_A": w.opts.get("lj_rcut"), "degree": w.opts.get("degree"),
+            "theta": w.opts.get("theta"), "method": method, "precision": precision,
+            "outputs": "u, c_lr, h_lr (FP64 grids) + LJ tail integrals",
+            "l2": "flushed before every timed step by a 256 MB write (outputs are 201 MB, inputs 96 KB)"}
+
+
+class Clocks:
+    """nvidia-smi sampling during the timed region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+         "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_index):
+        self.idx = device_index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.idx}", f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "100"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx = float(f[2])
+            except ValueError:
+                continue
+            for n, v in zip(names, f[5:9]):
+                if v.lower() == "active":
+                    reasons.add(n)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": mx, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def _peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            return json.load(f), "measured"
+    return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "sm_max_mhz": 2070.0}, "fallback"
+
+
+# FP32-pipe operations of one (grid point, atom) evaluation of the fused
+# FP32 kernels, counted from the loop bodies (FFMA = 2 flops):
+#   far field Phi1 + Phik: dx 2 FADD, d^2 1 FFMA, q/d 1 FMUL, Phi1 1 FADD, d 1 FMUL, -kappa d 1 FMUL,
+#                          Phik 1 FFMA                                     -> 10 flops (+2 MUFU)
+#   LJ, per site within the cut-off test: 2 FFMA + shared 2 FMUL (r^-6)  -> 4 per site + 2
+FLOPS_FAR = 10
+FLOPS_LJ_SITE = 4
+FLOPS_LJ_SHARED = 2
+FP32_LANES_PER_SM = 128
+SMS = 152
+
+
+def _alu_peak_tflops(sm_mhz):
+    return SMS * FP32_LANES_PER_SM * 2 * sm_mhz * 1e6 / 1e12
+
+
+def run_gpu(args):
+    import numpy as np
+    import torch
+
+    from paper_2109_09772_gb300 import build as B
+    from paper_2109_09772_gb300 import rism as R
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    B.build()
+    w = _workload(seed=rank)
+    method = R.METHOD_TREECODE if args.method == "treecode" else R.METHOD_DIRECT
+    prec = R.PREC_FP32 if args.precision == "fp32" else R.PREC_FP64
+    r = R.from_workload(w, method=method, precision=prec, debug_flags=2)
+    S, M = w.solvent.nsite, w.grid.npts
+    xyz, q, sg, ep = w.solute.xyz, w.solute.q, w.solute.sigma, w.solute.eps
+    out = {k: r.empty_grid() for k in ("u", "c", "h")}
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+    st = torch.cuda.current_stream()
+
+    def step():
+        r.set_solute(xyz, q, sg, ep)
+        return r.init(u=True, c=True, h=True, lj_tail=True, out=out)
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    clocks = Clocks(torch.cuda.current_device())
+    clocks.start()
+    times, evals, launches = [], [], 0
+    torch.cuda.synchronize()
+    t_wall0 = time.perf_counter()
+    for _ in range(args.steps):
+        flush.fill_(1.0)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(st)
+        step()
+        e1.record(st)
+        torch.cuda.synchronize()
+        times.append(e0.elapsed_time(e1))
+        inf = r.info()
+        evals.append(inf["eval_ms"])
+        launches += inf["launches"]
+    torch.cuda.synchronize()
+    t_wall = time.perf_counter() - t_wall0
+    ck = clocks.stop()
+    ms = sum(times) / len(times)
+    if dist:
+        t = torch.tensor([ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    value = world * S * M / (ms * 1e-3) / 1e9
+
+    # end to end: host (pinned) output buffers, device-to-host copies inside the timed region
+    hu = torch.empty((S, M), dtype=torch.float64).pin_memory()
+    hc = torch.empty((S, M), dtype=torch.float64).pin_memory()
+    hh = torch.empty((S, M), dtype=torch.float64).pin_memory()
+    tail = np.zeros(S)
+    P = lambda t: t.numpy()
+
+    def step_host():
+        r.set_solute(xyz, q, sg, ep)
+        r.init_host(P(hu), P(hc), P(hh), tail)
+
+    for _ in range(2):
+        step_host()
+    et = []
+    for _ in range(max(3, min(args.steps, 10))):
+        flush.fill_(1.0)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        step_host()
+        et.append(time.perf_counter() - t0)
+    e2e_ms = 1e3 * sum(et) / len(et)
+    if dist:
+        t = torch.tensor([e2e_ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_ms = float(t.item())
+    e2e = {"value": world * S * M / (e2e_ms * 1e-3) / 1e9, "unit": UNIT, "ms_per_step": e2e_ms,
+           "h2d_bytes_per_step": int(xyz.nbytes + q.nbytes + sg.nbytes + ep.nbytes),
+           "d2h_bytes_per_step": int(3 * S * M * 8 + S * 8)}
+
+    # accuracy of this step against the FP64 oracle at sampled points (rank 0 only; not timed)
+    acc = None
+    if rank == 0 and not args.no_check:
+        from oracle import oracle as O
+        from paper_2109_09772_gb300 import inputs as I
+
+        idx = I.sample_indices(M, 2000, seed=7)
+        ref = O.fields(O.Problem.from_workload(w), idx=idx)
+        acc = {}
+        for k in ("u", "c", "h"):
+            g = out[k].reshape(S, -1)[:, torch.as_tensor(idx, device="cuda")].cpu().numpy()
+            acc[k] = float(np.linalg.norm(g - ref[k]) / np.linalg.norm(ref[k]))
+
+    # roofline of the evaluation kernel (ALU bound: FP32 pipe)
+    inf = r.info()
+    peaks, src = _peaks()
+    eval_ms = sum(evals) / len(evals) if evals else 0.0
+    pairs_far = inf["direct_pairs"] + inf["proxy_pairs"]
+    lj_pairs = inf["near_pairs"] if method == R.METHOD_TREECODE else inf["direct_pairs"]
+    flops = pairs_far * FLOPS_FAR + lj_pairs * (FLOPS_LJ_SHARED + FLOPS_LJ_SITE * S)
+    sm_mhz = peaks.get("sm_max_mhz", 2070.0)
+    peak = _alu_peak_tflops(sm_mhz)
+    achieved = flops / (eval_ms * 1e-3) / 1e12 if eval_ms > 0 else None
+    roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+            "frac": (achieved / peak) if achieved else None, "traffic": None,
+            "kernel": "eval (fused far field + near field + epilogue)",
+            "peak_source": f"FP32 FMA pipe: {SMS} SMs x {FP32_LANES_PER_SM} lanes x 2 flops x {sm_mhz:.0f} MHz "
+                           f"(sm_max_mhz from MEASURED_PEAKS.json, {src})",
+            "kernel_ms": eval_ms, "flops_per_launch": flops}
+    res = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+           "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+           "vs_baseline": None, "dtype": "f32 pair terms, f64 accumulate/output" if prec == R.PREC_FP32 else "f64",
+           "data": "synthetic (seeded globule, protein density)",
+           "config": _config(w, args.method, args.precision), "e2e": e2e, "gpu_launches": launches,
+           "clocks": ck, "roofline": roof, "error_vs_fp64_oracle_rel_l2": acc,
+           "counts": {k: inf[k] for k in ("direct_pairs", "proxy_pairs", "near_pairs", "tree_nodes",
+                                            "tree_proxied", "tree_leaves")},
+           "wall_s": t_wall}
+    if rank == 0 and not args.no_fp64:
+        # the plain FP64 direct sum on the same GPU, one timed step (the comparison of the headline)
+        r64 = R.from_workload(w, method=R.METHOD_DIRECT, precision=R.PREC_FP64)
+        r64.init(out=out)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(st)
+        r64.set_solute(xyz, q, sg, ep)
+        r64.init(out=out, lj_tail=True)
+        e1.record(st)
+        torch.cuda.synchronize()
+        t64 = e0.elapsed_time(e1)
+        res["fp64_direct_ms"] = t64
+        res["speedup_vs_fp64_direct"] = t64 / ms
+        r64.close()
+    if rank == 0 and world == 1 and not args.no_cpu:
+        res["cpu_baseline"] = cpu_baseline(args.cpu_seconds)
+    r.close()
+    if dist:
+        dist.barrier()
+        dist.destroy_process_group()
+    if rank == 0:
+        print(json.dumps(res))
+
+
+def cpu_baseline(seconds=15.0, seed=0):
+    """The FP64 oracle as it stands on the host cores, on a bounded sample of grid points of the same
+    workload; value in the bench's unit."""
+    import numpy as np
+
+    from oracle import oracle as O
+    from paper_2109_09772_gb300 import inputs as I
+
+    w = _workload(seed)
+    p = O.Problem.from_workload(w)
+    cores = os.cpu_count() or 1
+    # calibrate on a small sample, then size the sample for about `seconds` of work
+    idx = I.sample_indices(w.grid.npts, 200, seed=11)
+    t0 = time.perf_counter()
+    O.fields(p, idx=idx, nthreads=cores)
+    t = max(time.perf_counter() - t0, 1e-3)
+    n = int(min(w.grid.npts, max(200, 200 * seconds / t)))
+    idx = I.sample_indices(w.grid.npts, n, seed=12)
+    t0 = time.perf_counter()
+    O.fields(p, idx=idx, nthreads=cores)
+    t = time.perf_counter() - t0
+    S = w.solvent.nsite
+    return {"value": S * n / t / 1e9, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": f"{n} random grid points of {WORKLOAD} (all {w.solute.n} atoms, {S} sites, u+c+h), "
+                      f"{t:.1f} s"}
+
+
+def run_reference(args):
+    """Reference arm: the FP64 CPU oracle, bounded sample per step, on the host cores."""
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    import numpy as np
+
+    from oracle import oracle as O
+    from paper_2109_09772_gb300 import inputs as I
+
+    O.build()
+    w = _workload(0)
+    p = O.Problem.from_workload(w)
+    cores = os.cpu_count() or 1
+    S = w.solvent.nsite
+    npts = max(100, int(args.ref_points))
+    for k in range(args.warmup):
+        O.fields(p, idx=I.sample_indices(w.grid.npts, min(npts, 200), seed=100 + k), nthreads=cores)
+    ts = []
+    for k in range(args.steps):
+        idx = I.sample_indices(w.grid.npts, npts, seed=200 + k)
+        t0 = time.perf_counter()
+        O.fields(p, idx=idx, nthreads=cores)
+        ts.append(time.perf_counter() - t0)
+    ms = 1e3 * sum(ts) / len(ts)
+    value = S * npts / (ms * 1e-3) / 1e9
+    sample = f"{npts} random grid points per step of {WORKLOAD} (all {w.solute.n} atoms, {S} sites, u+c+h)"
+    print(json.dumps({"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": 1,
+                      "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
+                      "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+                      "config": _config(w, "oracle (direct FP64, CPU)", "fp64"),
+                      "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+                                       "sample": sample},
+                      "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}))
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--method", default="treecode", choices=["treecode", "direct"])
+    ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64"])
+    ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    ap.add_argument("--ref-points", type=int, default=4000)
+    ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-fp64", action="store_true")
+    ap.add_argument("--no-check", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_gpu(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -104,7 +104,8 @@ typedef struct {
     int32_t autotune;   /* 1: time the candidate launch shapes once per problem class and cache the winner */
     int64_t wait_limit; /* spin iterations before a bounded device wait gives up; default 1<<26 */
     int32_t debug_flags;/* test hooks, 0 in production.  Bit 0: the direct kernels skip their first
-                           bulk copy, so its wait runs out and the call returns RISM_E_TIMEOUT */
+                           bulk copy, so its wait runs out and the call returns RISM_E_TIMEOUT.
+                           Bit 1: time the evaluation kernel with CUDA events (rism_info.eval_ms). */
 } rism_options;
 
 typedef struct {
@@ -117,6 +118,8 @@ typedef struct {
     int64_t near_pairs;    /* candidate pairs scanned by the cut-off (cell-list) pass */
     int32_t batch[3];      /* target batch dims in use */
     int32_t kernel_variant;/* launch shape chosen (autotuner or default) */
+    int32_t launches;      /* kernels launched by the last compute call */
+    float eval_ms;         /* CUDA-event duration of the last evaluation kernel (debug_flags bit 1), else 0 */
 } rism_info;
 
 /* Fill *o with the defaults listed above.  Never fails. */

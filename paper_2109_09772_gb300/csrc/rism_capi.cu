@@ -47,6 +47,8 @@ struct rism_ctx {
     rism_info info{};
     Phys ph{};
     GridD gd{};
+    int setup_launches = 0;  // kernels launched by the last table rebuild
+    cudaEvent_t ev[2] = {nullptr, nullptr};
 };
 
 namespace {
@@ -154,6 +156,7 @@ rism_status ensure_tables(rism_ctx* c) {
         if ((e = launch_setup(c->d_raw, c->n, c->S, smax, c->sigs, c->epss, c->o.lj_mode, c->o.lj_rcut,
                               c->o.lj_tol, c->gd, c->t, c->st)) != cudaSuccess)
             return cuda_fail(c, e, "setup kernel");
+        c->setup_launches += 1;
     }
     if (c->o.method == RISM_METHOD_TREECODE) {
         rism_status s = tree_prepare(c->tree, c->t, c->gd, c->ph, c->o, c->st, c->err);
@@ -334,7 +337,18 @@ rism_status rism_init(rism_ctx* c, double* u, double* c_lr, double* h_lr, double
         }
     }
     Outputs o{dev[0], dev[1], dev[2]};
+    c->info.launches = c->setup_launches;
+    c->setup_launches = 0;
+    c->info.eval_ms = 0.f;
     if (o.u || o.c || o.h) {
+        const bool timed = (c->o.debug_flags & 2) != 0;
+        if (timed) {
+            if (!c->ev[0]) {
+                cudaEventCreate(&c->ev[0]);
+                cudaEventCreate(&c->ev[1]);
+            }
+            cudaEventRecord(c->ev[0], c->st);
+        }
         if (c->o.method == RISM_METHOD_DIRECT) {
             e = launch_direct(c->gd, c->ph, c->t, c->o.precision, o, c->o.wait_limit, c->info.kernel_variant,
                               c->o.debug_flags, c->st);
@@ -342,10 +356,12 @@ rism_status rism_init(rism_ctx* c, double* u, double* c_lr, double* h_lr, double
             c->info.direct_pairs = M * c->n;
             c->info.proxy_pairs = 0;
             c->info.near_pairs = 0;
+            c->info.launches += 1;
         } else {
             s = tree_eval(c->tree, c->t, c->gd, c->ph, c->o, o, c->st, c->err, c->info);
             if (s != RISM_OK) return s;
         }
+        if (timed) cudaEventRecord(c->ev[1], c->st);
     }
     if (lj_tail) {
         if (c->o.lj_mode == RISM_LJ_NONE || c->n == 0) {
@@ -363,8 +379,29 @@ rism_status rism_init(rism_ctx* c, double* u, double* c_lr, double* h_lr, double
                 return cuda_fail(c, e, "copying result to host");
         }
     (void)host_out;
+    if (lj_tail && c->o.lj_mode != RISM_LJ_NONE && c->n > 0) c->info.launches += 1;
     // Status of the device-side bounded waits: synchronise and read the error word.
-    return check_device_error(c);
+    rism_status st = check_device_error(c);
+    if (st == RISM_OK && c->o.method == RISM_METHOD_TREECODE && (o.u || o.c || o.h)) {
+        bool retry = false;
+        st = tree_post(c->tree, c->info, retry, c->err);
+        if (st == RISM_OK && retry) {
+            // the far list outgrew its buffer (now enlarged): rebuild the lists and evaluate again
+            st = tree_prepare(c->tree, c->t, c->gd, c->ph, c->o, c->st, c->err);
+            if (st == RISM_OK) st = tree_eval(c->tree, c->t, c->gd, c->ph, c->o, o, c->st, c->err, c->info);
+            for (int k = 0; k < 3 && st == RISM_OK; ++k)
+                if (user[k] && dev[k] != user[k]) {
+                    if ((e = cudaMemcpyAsync(user[k], dev[k], bytes, cudaMemcpyDeviceToHost, c->st)) != cudaSuccess)
+                        return cuda_fail(c, e, "copying result to host");
+                }
+            if (st == RISM_OK) st = check_device_error(c);
+            if (st == RISM_OK) st = tree_post(c->tree, c->info, retry, c->err);
+            if (st == RISM_OK && retry) st = fail(c, RISM_E_NOMEM, "far list kept growing");
+        }
+    }
+    if (st == RISM_OK && (c->o.debug_flags & 2) && c->ev[0] && (o.u || o.c || o.h))
+        cudaEventElapsedTime(&c->info.eval_ms, c->ev[0], c->ev[1]);
+    return st;
 }
 
 rism_status rism_potential(rism_ctx* c, double* u, double* lj_tail) {
@@ -458,6 +495,8 @@ void rism_destroy(rism_ctx* c) {
     cudaFreeHost(c->h_err);
     cudaFree(c->d_tail);
     for (int k = 0; k < 3; ++k) cudaFree(c->d_stage[k]);
+    if (c->ev[0]) cudaEventDestroy(c->ev[0]);
+    if (c->ev[1]) cudaEventDestroy(c->ev[1]);
     delete c;
 }
 

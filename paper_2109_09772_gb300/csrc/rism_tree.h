@@ -30,6 +30,9 @@ rism_status tree_prepare(TreeState* ts, const DevTables& t, const GridD& g, cons
 // Evaluate u, c, h with the treecode far field and the cell-list near field.
 rism_status tree_eval(TreeState* ts, const DevTables& t, const GridD& g, const Phys& ph, const rism_options& o,
                       Outputs out, cudaStream_t st, std::string& err, rism_info& info);
+// After the stream has been synchronised: copy the counters into info; on a
+// far-list overflow grow the buffer and set retry (run prepare + eval again).
+rism_status tree_post(TreeState* ts, rism_info& info, bool& retry, std::string& err);
 // Many solutes in one persistent, graph-captured launch sequence.
 rism_status batch_eval(std::vector<BatchItem>& items, const rism_options& o, cudaStream_t st, DevErr* err,
                        std::string& msg);

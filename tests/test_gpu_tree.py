@@ -1,0 +1,136 @@
+"""GPU parity of the treecode path (BL particle-cluster far field + cell-list near field) against the
+FP64 oracle, through the C ABI.
+
+The treecode is an approximation: its error at degree 8, theta 0.7 must stay within rel L2 1e-5 per output
+grid; with no accepted cluster (small solutes) it reduces to the FP32 direct sum (1e-6).  Error falls
+geometrically with the degree.
+"""
+import numpy as np
+import pytest
+
+from oracle import oracle as O
+from paper_2109_09772_gb300 import inputs as I
+from tests.helpers import check_fields, nearest_points, rel_l2
+
+pytestmark = pytest.mark.gpu
+
+TREE_TOL = 1e-5
+
+
+@pytest.fixture(scope="module")
+def R():
+    import torch
+
+    from paper_2109_09772_gb300 import build as B
+    from paper_2109_09772_gb300 import rism
+
+    B.build()
+    torch.cuda.set_device(0)
+    return rism
+
+
+def run(R, w, keys=("u", "c", "h"), **opts):
+    r = R.from_workload(w, method=R.METHOD_TREECODE, precision=R.PREC_FP32, **opts)
+    out = r.init(u="u" in keys, c="c" in keys, h="h" in keys, lj_tail=True)
+    res = {k: out[k].cpu().numpy().reshape(r.S, -1) for k in keys}
+    res["info"] = r.info()
+    res["lj_tail"] = out["lj_tail"]
+    r.close()
+    return res
+
+
+def test_small_ragged_no_accepted_cluster(R):
+    """150 atoms: no cluster is large enough for proxies, so every pair is direct (far list) or near
+    (cells): FP32-direct accuracy on a ragged 37x21x13 grid."""
+    w = I.small_workload(n_atoms=150, n=(37, 21, 13), h=0.45, seed=5, ions=True, lj_rcut=4.0, net=2.0)
+    p = O.Problem.from_workload(w)
+    ref = O.fields(p)
+    g = run(R, w)
+    assert g["info"]["proxy_pairs"] == 0
+    check_fields(g, ref, ("u", "c", "h"), 1e-6, w.grid, w.solute.xyz, label="tree small")
+    np.testing.assert_allclose(g["lj_tail"], O.lj_tail(p), rtol=1e-12)
+
+
+def _sampled(w, count=3000, seed=2):
+    return np.union1d(I.sample_indices(w.grid.npts, count, seed=seed), nearest_points(w.grid, w.solute.xyz))
+
+
+def test_globule2000_degree8_theta07(R):
+    """2,000-atom globule, 128^3 grid, 4 sites, LJ cut-off 9 A, degree 8, theta 0.7."""
+    w = I.workload(1)
+    idx = _sampled(w)
+    ref = O.fields(O.Problem.from_workload(w), idx=idx)
+    g = run(R, w)
+    assert g["info"]["proxy_pairs"] > 0 and g["info"]["tree_proxied"] > 0
+    gs = {k: g[k][:, idx] for k in ("u", "c", "h")}
+    check_fields(gs, ref, ("u", "c", "h"), TREE_TOL, w.grid, w.solute.xyz, idx=idx, label="cfg1 tree")
+
+
+def test_error_falls_with_degree(R):
+    """Geometric convergence of the barycentric-Lagrange far field: error(degree) decreases."""
+    w = I.workload(1)
+    idx = I.sample_indices(w.grid.npts, 2000, seed=3)
+    ref = O.fields(O.Problem.from_workload(w), idx=idx, want=("c",))
+    errs = []
+    for deg in (2, 4, 6, 8):
+        g = run(R, w, keys=("c",), degree=deg, leaf=32)
+        errs.append(rel_l2(g["c"][:, idx], ref["c"]))
+    assert errs[0] > errs[1] > errs[2] > errs[3], errs
+    assert errs[0] / errs[2] > 20.0, errs
+
+
+def test_no_lj_cutoff_means_all_atoms_near(R):
+    """Without an LJ cut-off every atom is in the near field of every batch (LJ exact), the far field still
+    uses the tree."""
+    w = I.small_workload(n_atoms=120, n=(20, 18, 14), h=0.5, seed=8, ions=True, lj_rcut=0.0)
+    ref = O.fields(O.Problem.from_workload(w))
+    g = run(R, w)
+    check_fields(g, ref, ("u", "c", "h"), 1e-6, w.grid, w.solute.xyz, label="tree no-cutoff")
+
+
+def test_grid_point_on_an_atom(R):
+    w = I.small_workload(n_atoms=20, n=(16, 12, 10), h=0.5, seed=4, ions=True, lj_rcut=5.0)
+    w.solute.xyz[3] = np.array(w.grid.origin) + 0.5 * np.array([7, 5, 4])
+    ref = O.fields(O.Problem.from_workload(w))
+    g = run(R, w)
+    f = (4 * 12 + 5) * 16 + 7
+    assert np.all(np.isposinf(g["u"][:, f]))
+    keep = np.ones(g["u"].shape[1], dtype=bool)
+    keep[f] = False
+    assert rel_l2(g["u"][:, keep], ref["u"][:, keep]) <= 1e-6
+    for k in ("c", "h"):
+        assert np.all(np.isfinite(g[k]))
+        assert rel_l2(g[k], ref[k]) <= 1e-6
+
+
+def test_zero_atoms(R):
+    w = I.small_workload(n_atoms=5, n=(9, 8, 8), ions=True)
+    r = R.from_workload(w, method=R.METHOD_TREECODE)
+    r.set_solute(np.zeros((0, 3)), [], [], [])
+    out = r.init()
+    for k in ("u", "c", "h"):
+        assert float(out[k].abs().max()) == 0.0
+    r.close()
+
+
+def test_small_leaves_many_nodes_and_repeatable(R):
+    """leaf = 8 gives a deep tree and long lists; results repeat bit for bit."""
+    w = I.workload(1)
+    idx = I.sample_indices(w.grid.npts, 1500, seed=4)
+    ref = O.fields(O.Problem.from_workload(w), idx=idx)
+    a = run(R, w, leaf=8)
+    b = run(R, w, leaf=8)
+    assert a["info"]["tree_nodes"] > 300
+    for k in ("u", "c", "h"):
+        assert np.array_equal(a[k], b[k])
+    check_fields({k: a[k][:, idx] for k in ("u", "c", "h")}, ref, ("u", "c", "h"), TREE_TOL, label="leaf8")
+
+
+def test_ellipsoid13600_224x192x160_sampled(R):
+    """13,600-atom prolate ellipsoid (net -24) on the 224x192x160 grid, degree 8, theta 0.7."""
+    w = I.workload(2)
+    idx = _sampled(w, count=2500, seed=5)
+    ref = O.fields(O.Problem.from_workload(w), idx=idx)
+    g = run(R, w)
+    gs = {k: g[k][:, idx] for k in ("u", "c", "h")}
+    check_fields(gs, ref, ("u", "c", "h"), TREE_TOL, w.grid, w.solute.xyz, idx=idx, label="cfg2 tree")
