@@ -44,6 +44,7 @@
 #ifndef RISM3D_H
 #define RISM3D_H
 
+#include <stddef.h>
 #include <stdint.h>
 
 #if defined(__GNUC__)
@@ -182,6 +183,42 @@ RISM_API rism_status rism_potential_backward(rism_ctx* ctx, const double* g_u, c
  * Output must be device memory. */
 RISM_API rism_status rism_potential_batched(rism_ctx* const* ctxs, int32_t count, double* const* u, double* const* c_lr,
                                    double* const* h_lr);
+
+/* Largest solute accepted by rism_init_noalloc. */
+#define RISM_NOALLOC_MAX_ATOMS 8192
+
+/* rism_init_noalloc -- the direct-sum initialization without any device
+ * allocation.  The paper has no counterpart: this exists for callers that
+ * cannot call cudaMalloc -- code running while a stream is being captured
+ * into a CUDA graph (allocation is not a capturable operation), plug-ins
+ * whose host application owns the device memory and forbids other
+ * allocators, and embedded or real-time callers that must not allocate
+ * after start-up.  It computes what rism_init computes with method
+ * RISM_METHOD_DIRECT (FP32 or FP64 pairs; opts->method must be DIRECT) and
+ * calls no cudaMalloc, cudaFree or other allocating routine.
+ *
+ * Its scratch (the per-atom and per-(atom, site) tables) lives in one
+ * file-scope __device__ array of 4,063,488 bytes (RISM_NOALLOC_MAX_ATOMS
+ * atoms, RISM_MAX_SITES sites), which every GPU that loads the library holds
+ * until the process exits.  The first call on a device looks up that
+ * array's device address (cudaGetSymbolAddress) with the device current;
+ * make that first call before any stream capture.  Every call shares the
+ * array: calls that overlap on the GPU (several streams, several host
+ * threads) race and must be serialised by the caller.
+ *
+ * grid, opts: as for rism_grid_create.  n (0 <= n <= RISM_NOALLOC_MAX_ATOMS),
+ * xyz [n][3], q, sigma, eps: the solute, device or host memory, read during
+ * the call.  nsite, qs, sigs, epss, rho (nullable), is_ion (nullable): the
+ * solvent, host memory.  u, c_lr, h_lr: device outputs [S][nz][ny][nx], each
+ * nullable (h_lr needs kappa > 0).  stream: cudaStream_t (NULL = legacy
+ * default); the call synchronises it before returning.  errbuf (nullable,
+ * errlen bytes) receives a message on failure.  n above the maximum returns
+ * RISM_E_INVALID without touching the GPU. */
+RISM_API rism_status rism_init_noalloc(const rism_grid_desc* grid, const rism_options* opts, int64_t n,
+                                       const double* xyz, const double* q, const double* sigma, const double* eps,
+                                       int32_t nsite, const double* qs, const double* sigs, const double* epss,
+                                       const double* rho, const int32_t* is_ion, double* u, double* c_lr,
+                                       double* h_lr, void* stream, char* errbuf, size_t errlen);
 
 /* Counters and derived parameters of the context (after a compute call). */
 RISM_API rism_status rism_get_info(const rism_ctx* ctx, rism_info* info);

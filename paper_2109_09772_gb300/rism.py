@@ -56,7 +56,8 @@ class Info(C.Structure):
 
 EXPORTS = ["rism_default_options", "rism_grid_create", "rism_set_solute", "rism_set_solvent", "rism_potential",
            "rism_asymptotics", "rism_init", "rism_potential_backward", "rism_potential_batched", "rism_get_info",
-           "rism_destroy", "rism_last_error"]
+           "rism_destroy", "rism_last_error", "rism_init_noalloc"]
+NOALLOC_MAX_ATOMS = 8192
 
 _lib = None
 _lock = threading.Lock()
@@ -96,6 +97,9 @@ def load(path: str = LIB_PATH):
         lib.rism_destroy.argtypes = [P]
         lib.rism_last_error.restype = C.c_char_p
         lib.rism_last_error.argtypes = [P]
+        lib.rism_init_noalloc.restype = C.c_int
+        lib.rism_init_noalloc.argtypes = [C.POINTER(GridDesc), C.POINTER(Options), I64, P, P, P, P, I32, P, P, P, P,
+                                          P, P, P, P, P, C.c_char_p, C.c_size_t]
         _lib = lib
         return lib
 
@@ -238,6 +242,29 @@ class Rism:
         inf = Info()
         self._check(self.lib.rism_get_info(self.ctx, C.byref(inf)), "rism_get_info")
         return {f: (list(getattr(inf, f)) if f == "batch" else getattr(inf, f)) for f, _ in Info._fields_}
+
+
+def init_noalloc(grid_n, h, origin, xyz, q, sigma, eps, solvent, u=None, c=None, hh=None, stream=None, **opts):
+    """rism_init_noalloc: direct-sum u / c / h into caller-provided device tensors, no device allocation by
+    the library.  xyz, q, sigma, eps: device (or host) float64 tensors; solvent: (q, sigma, eps, rho, is_ion)
+    host arrays.  Raises RismError with the library's message on failure."""
+    import torch
+
+    lib = load()
+    o = default_options(**opts)
+    g = GridDesc(int(grid_n[0]), int(grid_n[1]), int(grid_n[2]), float(h), (C.c_double * 3)(*origin))
+    qs, sg, ep = (_host_f64(a) for a in solvent[:3])
+    rho = None if solvent[3] is None else _host_f64(solvent[3])
+    ion = None if solvent[4] is None else np.ascontiguousarray(np.asarray(solvent[4], dtype=np.int32))
+    st = stream if stream is not None else torch.cuda.current_stream()
+    buf = C.create_string_buffer(256)
+    n = int(q.numel())
+    rc = lib.rism_init_noalloc(C.byref(g), C.byref(o), n, _ptr(xyz), _ptr(q), _ptr(sigma), _ptr(eps), qs.size,
+                               qs.ctypes.data, sg.ctypes.data, ep.ctypes.data,
+                               None if rho is None else rho.ctypes.data, None if ion is None else ion.ctypes.data,
+                               _ptr(u), _ptr(c), _ptr(hh), C.c_void_p(st.cuda_stream), buf, 256)
+    if rc != OK:
+        raise RismError(rc, "rism_init_noalloc: " + buf.value.decode(errors="replace"))
 
 
 def potential_batched(rs, u=True, c=True, h=True):
