@@ -11,8 +11,8 @@ struct AdjointState;
 AdjointState* adjoint_create();
 void adjoint_destroy(AdjointState* a);
 rism_status adjoint_run(AdjointState* a, const DevTables& t, const GridD& g, const Phys& ph, const rism_options& o,
-                        const double* raw_host, const double* g_u, const double* g_c, const double* g_h,
-                        double* d_xyz, double* d_q, double* d_sigma, double* d_eps, cudaStream_t st,
-                        std::string& err);
+                        const double* raw_dev, const double* sig_s, const double* eps_s, const double* g_u,
+                        const double* g_c, const double* g_h, double* d_xyz, double* d_q, double* d_sigma,
+                        double* d_eps, cudaStream_t st, std::string& err);
 
 }  // namespace rism

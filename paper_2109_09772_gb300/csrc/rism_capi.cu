@@ -119,25 +119,27 @@ void make_phys(rism_ctx* c) {
     for (int s = 0; s < kMaxSites; ++s) p.qs[s] = s < c->S ? c->qs[s] : 0.0;
 }
 
-rism_status ensure_tables(rism_ctx* c) {
-    if (!c->dirty) return RISM_OK;
+// Allocations of the per-solute tables and the physical constants; no kernel
+// is launched (also used before a graph capture).
+rism_status reserve_tables(rism_ctx* c) {
     cudaError_t e;
     const int smax = padded_sites(c->S);
     if (c->n > c->cap_n || smax != c->cap_smax) {
         cudaFree(c->d_raw);
         cudaFree(c->t.geo);
-        cudaFree(c->t.geoU);
+        cudaFree(c->t.srcf);
         cudaFree(c->t.ljd);
         cudaFree(c->t.ljf);
         c->d_raw = nullptr;
-        c->t.geo = c->t.geoU = nullptr;
+        c->t.geo = nullptr;
+        c->t.srcf = nullptr;
         c->t.ljd = nullptr;
         c->t.ljf = nullptr;
         c->cap_n = 0;
         int64_t n = c->n > 0 ? c->n : 1;
         if ((e = cudaMalloc(&c->d_raw, sizeof(double) * 6 * n)) != cudaSuccess ||
             (e = cudaMalloc(&c->t.geo, sizeof(Geo) * n)) != cudaSuccess ||
-            (e = cudaMalloc(&c->t.geoU, sizeof(Geo) * n)) != cudaSuccess ||
+            (e = cudaMalloc(&c->t.srcf, sizeof(SrcF) * n)) != cudaSuccess ||
             (e = cudaMalloc(&c->t.ljd, sizeof(LJd) * n * smax)) != cudaSuccess ||
             (e = cudaMalloc(&c->t.ljf, sizeof(LJf) * n * smax)) != cudaSuccess)
             return cuda_fail(c, e, "allocating solute tables");
@@ -149,6 +151,15 @@ rism_status ensure_tables(rism_ctx* c) {
     c->t.err = c->d_err;
     c->gd = GridD{c->g.nx, c->g.ny, c->g.nz, c->g.h, c->g.origin[0], c->g.origin[1], c->g.origin[2]};
     make_phys(c);
+    return RISM_OK;
+}
+
+rism_status ensure_tables(rism_ctx* c) {
+    if (!c->dirty) return RISM_OK;
+    cudaError_t e;
+    rism_status rs = reserve_tables(c);
+    if (rs != RISM_OK) return rs;
+    const int smax = c->t.smax;
     if (c->n > 0) {
         if ((e = cudaMemcpyAsync(c->d_raw, c->raw.data(), sizeof(double) * 6 * c->n, cudaMemcpyHostToDevice,
                                  c->st)) != cudaSuccess)
@@ -304,6 +315,7 @@ rism_status rism_set_solvent(rism_ctx* c, int32_t nsite, const double* q, const 
     c->have_solvent = true;
     c->dirty = true;
     c->err.clear();
+    make_phys(c);  // beta, kappa, r_short are reported by rism_get_info from here on
     return RISM_OK;
 }
 
@@ -427,8 +439,8 @@ rism_status rism_potential_backward(rism_ctx* c, const double* g_u, const double
     rism_status s = ensure_tables(c);
     if (s != RISM_OK) return s;
     if (g_h && !(c->ph.kappa > 0.0)) g_h = nullptr;  // h is identically zero without ions
-    s = adjoint_run(c->adj, c->t, c->gd, c->ph, c->o, c->raw.data(), g_u, g_c, g_h, d_xyz, d_q, d_sigma, d_eps,
-                    c->st, c->err);
+    s = adjoint_run(c->adj, c->t, c->gd, c->ph, c->o, c->d_raw, c->sigs, c->epss, g_u, g_c, g_h, d_xyz, d_q,
+                    d_sigma, d_eps, c->st, c->err);
     if (s != RISM_OK) return s;
     return check_device_error(c);
 }
@@ -438,35 +450,74 @@ rism_status rism_potential_batched(rism_ctx* const* ctxs, int32_t count, double*
     if (!ctxs || count < 1) return RISM_E_INVALID;
     rism_ctx* c0 = ctxs[0];
     if (!c0) return RISM_E_INVALID;
+    if (c0->o.method != RISM_METHOD_TREECODE || c0->o.precision != RISM_PREC_FP32)
+        return fail(c0, RISM_E_UNSUPPORTED, "the batched launch runs the FP32 treecode");
+    cudaError_t e = cudaSetDevice(c0->device);
+    if (e != cudaSuccess) return cuda_fail(c0, e, "cudaSetDevice");
     std::vector<BatchItem> items((size_t)count);
     for (int b = 0; b < count; ++b) {
         rism_ctx* c = ctxs[b];
         if (!c) return fail(c0, RISM_E_INVALID, "NULL context in batch");
+        for (int k = 0; k < b; ++k)
+            if (ctxs[k] == c) return fail(c0, RISM_E_INVALID, "a context appears twice in the batch");
         if (!c->have_solute || !c->have_solvent) return fail(c0, RISM_E_STATE, "set_solute and set_solvent first");
-        if (c->o.method != c0->o.method || c->o.precision != c0->o.precision || padded_sites(c->S) != padded_sites(c0->S) ||
-            c->device != c0->device)
-            return fail(c0, RISM_E_INVALID, "batched contexts must share device, method, precision and site count");
-        rism_status s = ensure_tables(c);
-        if (s != RISM_OK) return fail(c0, s, c->err);
+        if (c->o.method != c0->o.method || c->o.precision != c0->o.precision ||
+            padded_sites(c->S) != padded_sites(c0->S) || c->device != c0->device || c->o.degree != c0->o.degree)
+            return fail(c0, RISM_E_INVALID, "batched contexts must share device, method, precision, degree and sites");
         double* uu = u ? u[b] : nullptr;
         double* cc = c_lr ? c_lr[b] : nullptr;
         double* hh = h_lr ? h_lr[b] : nullptr;
+        if ((uu != nullptr) != (u && u[0]) || (cc != nullptr) != (c_lr && c_lr[0]) ||
+            (hh != nullptr) != (h_lr && h_lr[0]))
+            return fail(c0, RISM_E_INVALID, "every solute of a batch must request the same outputs");
+        if (!uu && !cc && !hh) return fail(c0, RISM_E_INVALID, "no output requested");
         if (hh && !(c->ph.kappa > 0.0)) return fail(c0, RISM_E_INVALID, "h_lr needs kappa > 0");
         const double* ptrs[3] = {uu, cc, hh};
         for (const double* p : ptrs)
             if (p && !is_device_ptr(p)) return fail(c0, RISM_E_INVALID, "batched outputs must be device memory");
-        items[b] = BatchItem{c->tree, &c->t, c->gd, c->ph, Outputs{uu, cc, hh}};
+        // allocations and the solute upload happen here, outside the captured graph
+        rism_status s = reserve_tables(c);
+        if (s != RISM_OK) return fail(c0, s, c->err);
+        if (c->n > 0 && (e = cudaMemcpyAsync(c->d_raw, c->raw.data(), sizeof(double) * 6 * c->n,
+                                             cudaMemcpyHostToDevice, c0->st)) != cudaSuccess)
+            return cuda_fail(c0, e, "uploading solute");
+        BatchItem it;
+        it.tree = c->tree;
+        it.t = &c->t;
+        it.g = c->gd;
+        it.ph = c->ph;
+        it.o = Outputs{uu, cc, hh};
+        it.raw = c->d_raw;
+        for (int k = 0; k < kMaxSites; ++k) {
+            it.sig_s[k] = c->sigs[k];
+            it.eps_s[k] = c->epss[k];
+        }
+        it.lj_mode = c->o.lj_mode;
+        it.lj_rcut = c->o.lj_rcut;
+        it.lj_tol = c->o.lj_tol;
+        items[b] = it;
     }
-    // Tables of the other contexts were built on their own streams: order them before c0's stream.
-    for (int b = 1; b < count; ++b) {
-        if (ctxs[b]->st != c0->st) {
-            cudaError_t e = cudaStreamSynchronize(ctxs[b]->st);
-            if (e != cudaSuccess) return cuda_fail(c0, e, "synchronising batch member");
+    rism_status s = RISM_OK;
+    for (int attempt = 0; attempt < 3; ++attempt) {
+        bool retry = false;
+        s = batch_eval(items, c0->o, c0->st, c0->d_err, c0->err, retry);
+        if (s != RISM_OK) return s;
+        s = check_device_error(c0);
+        if (s != RISM_OK) return s;
+        bool again = false;
+        for (int b = 0; b < count; ++b) {
+            s = tree_post(ctxs[b]->tree, ctxs[b]->info, retry, c0->err);
+            if (s != RISM_OK) return s;
+            again = again || retry;
+        }
+        if (!again) {
+            // the tables now match the uploaded solutes; the tree state is not reusable by rism_init
+            // without a rebuild (its batch shape is the batch's), so mark every context dirty
+            for (int b = 0; b < count; ++b) ctxs[b]->dirty = true;
+            return RISM_OK;
         }
     }
-    rism_status s = batch_eval(items, c0->o, c0->st, c0->d_err, c0->err);
-    if (s != RISM_OK) return s;
-    return check_device_error(c0);
+    return fail(c0, RISM_E_NOMEM, "list buffers kept growing");
 }
 
 rism_status rism_get_info(const rism_ctx* c, rism_info* info) {
@@ -488,7 +539,7 @@ void rism_destroy(rism_ctx* c) {
     adjoint_destroy(c->adj);
     cudaFree(c->d_raw);
     cudaFree(c->t.geo);
-    cudaFree(c->t.geoU);
+    cudaFree(c->t.srcf);
     cudaFree(c->t.ljd);
     cudaFree(c->t.ljf);
     cudaFree(c->d_err);

@@ -71,14 +71,14 @@ struct SetupArgs {
     GridD g;
 };
 
-__global__ void k_setup(SetupArgs a, Geo* geo, Geo* geoU, LJd* ljd, LJf* ljf) {
+__global__ void k_setup(SetupArgs a, Geo* geo, SrcF* srcf, LJd* ljd, LJf* ljf) {
     int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (i >= a.n) return;
     const double* r = a.raw + 6 * i;
     double x = r[0], y = r[1], z = r[2], q = r[3], sg = r[4], ep = r[5];
     geo[i] = Geo{x, y, z, q};
     double ih = 1.0 / a.g.h;
-    geoU[i] = Geo{(x - a.g.ox) * ih, (y - a.g.oy) * ih, (z - a.g.oz) * ih, q};
+    srcf[i] = make_srcf((x - a.g.ox) * ih, (y - a.g.oy) * ih, (z - a.g.oz) * ih, q);
     double h2 = a.g.h * a.g.h, h6 = h2 * h2 * h2;
     for (int s = 0; s < a.smax; ++s) {
         LJd d{0.0, 0.0, 0.0, 0.0};
@@ -118,7 +118,7 @@ cudaError_t launch_setup(const double* raw, int64_t n, int S, int smax, const do
     a.lj_tol = lj_tol;
     a.g = g;
     int nb = (int)((n + 127) / 128);
-    k_setup<<<nb, 128, 0, st>>>(a, t.geo, t.geoU, t.ljd, t.ljf);
+    k_setup<<<nb, 128, 0, st>>>(a, t.geo, t.srcf, t.ljd, t.ljf);
     return cudaGetLastError();
 }
 
@@ -294,30 +294,26 @@ __global__ void __launch_bounds__(BX* BY* BZ) k_direct64(GridD g, Phys ph, const
 }
 
 // ------------------------------------------------------------ FP32 direct
-// Pair terms in FP32 in a tile-local frame in grid units: grid coordinates are
-// exact small integers, atom coordinates are float-float (hi + lo) relative to
-// the tile origin, so dx = (i - xh) - xl is exact to half an ulp of dx for
-// every nearby atom.  Per-tile FP32 partial sums are folded into float-float
-// totals (TwoSum), which carry ~48 bits.
+// Pair terms in FP32 from float-float grid-unit source positions (SrcF): the
+// grid coordinates are exact integers, so dx = (i - xh) - xl is exact to half
+// an ulp of dx for every nearby atom.  Per-tile FP32 partial sums are folded
+// into float-float totals (TwoSum), which carry ~48 bits.
 template <int SM, int P, int BX, int BY, int BZ, int T, bool DU, bool DH>
-__global__ void __launch_bounds__(BX* BY* BZ) k_direct32(GridD g, Phys ph, const Geo* __restrict__ geoU,
+__global__ void __launch_bounds__(BX* BY* BZ) k_direct32(GridD g, Phys ph, const SrcF* __restrict__ srcf,
                                                           const LJf* __restrict__ lj, int64_t n, Outputs o,
                                                           DevErr* err, long long wlim, int dbg) {
-    constexpr int NT = BX * BY * BZ;
-    static_assert(NT >= T, "one thread converts one atom");
     extern __shared__ __align__(16) unsigned char smem[];
-    Geo* sgeo = reinterpret_cast<Geo*>(smem);
-    LJf* slj = reinterpret_cast<LJf*>(smem + 2 * T * sizeof(Geo));
-    GeoF* conv = reinterpret_cast<GeoF*>(smem + 2 * T * sizeof(Geo) + 2 * T * SM * sizeof(LJf));
-    uint64_t* bar = reinterpret_cast<uint64_t*>(smem + 2 * T * sizeof(Geo) + 2 * T * SM * sizeof(LJf) +
-                                                T * sizeof(GeoF));
+    SrcF* ssrc = reinterpret_cast<SrcF*>(smem);
+    LJf* slj = reinterpret_cast<LJf*>(smem + 2 * T * sizeof(SrcF));
+    uint64_t* bar = reinterpret_cast<uint64_t*>(smem + 2 * T * sizeof(SrcF) + 2 * T * SM * sizeof(LJf));
 
     const int tid = threadIdx.x;
     const int tx = tid % BX, ty = (tid / BX) % BY, tz = tid / (BX * BY);
-    const int ti0 = blockIdx.x * BX * P, tj0 = blockIdx.y * BY, tk0 = blockIdx.z * BZ;  // tile origin (grid index)
-    const int i0 = ti0 + tx * P, j = tj0 + ty, k = tk0 + tz;
-    const float fx0 = (float)(tx * P), fy = (float)ty, fz = (float)tz;  // tile-local, exact
-    const float h = (float)g.h;
+    const int i0 = (blockIdx.x * BX + tx) * P, j = blockIdx.y * BY + ty, k = blockIdx.z * BZ + tz;
+    float gx[P];
+#pragma unroll
+    for (int p = 0; p < P; ++p) gx[p] = (float)(i0 + p);
+    const float fy = (float)j, fz = (float)k;
     const float rs2 = (float)((ph.rs / g.h) * (ph.rs / g.h));
     const float xs = (float)(g.h / ph.eta);                            // x = d_grid * xs
     const float kap2 = (float)(-ph.kappa * g.h * 1.4426950408889634);  // e^{-kappa d} = 2^(kap2 d_grid)
@@ -344,9 +340,9 @@ __global__ void __launch_bounds__(BX* BY* BZ) k_direct32(GridD g, Phys ph, const
     auto issue = [&](int t) {
         int st = t & 1;
         int cnt = (int)min((int64_t)T, n - (int64_t)t * T);
-        uint32_t b1 = cnt * sizeof(Geo), b2 = cnt * SM * sizeof(LJf);
+        uint32_t b1 = cnt * sizeof(SrcF), b2 = cnt * SM * sizeof(LJf);
         mbar_expect_tx(&bar[st], b1 + b2);
-        bulk_g2s(sgeo + st * T, geoU + (int64_t)t * T, b1, &bar[st]);
+        bulk_g2s(ssrc + st * T, srcf + (int64_t)t * T, b1, &bar[st]);
         bulk_g2s(slj + st * T * SM, lj + (int64_t)t * T * SM, b2, &bar[st]);
     };
     if (tid == 0) {
@@ -365,17 +361,7 @@ __global__ void __launch_bounds__(BX* BY* BZ) k_direct32(GridD g, Phys ph, const
             return;
         }
         const int cnt = (int)min((int64_t)T, n - (int64_t)t * T);
-        if (tid < cnt) {
-            const Geo A = sgeo[st * T + tid];
-            GeoF c;
-            split_ff(A.x - (double)ti0, c.xh, c.xl);
-            split_ff(A.y - (double)tj0, c.yh, c.yl);
-            split_ff(A.z - (double)tk0, c.zh, c.zl);
-            c.q = (float)A.q;
-            c.pad = 0.f;
-            conv[tid] = c;
-        }
-        __syncthreads();
+        const SrcF* Sx = ssrc + st * T;
         const LJf* L = slj + st * T * SM;
         float p1[P], pk[P], psc[P], psh[P], plj[P][SM];
 #pragma unroll
@@ -385,15 +371,14 @@ __global__ void __launch_bounds__(BX* BY* BZ) k_direct32(GridD g, Phys ph, const
             for (int s = 0; s < SM; ++s) plj[p][s] = 0.f;
         }
         for (int aa = 0; aa < cnt; ++aa) {
-            const float4 g0 = *reinterpret_cast<const float4*>(&conv[aa].xh);
-            const float4 g1 = *reinterpret_cast<const float4*>(&conv[aa].xl);
+            const float4 g0 = *reinterpret_cast<const float4*>(&Sx[aa].xh);
+            const float4 g1 = *reinterpret_cast<const float4*>(&Sx[aa].xl);
             const float dy = (fy - g0.y) - g1.y;
             const float dz = (fz - g0.z) - g1.z;
             const float dyz2 = fmaf(dy, dy, dz * dz);
-            const float bx = fx0 - g0.x;
 #pragma unroll
             for (int p = 0; p < P; ++p) {
-                const float dx = (bx + (float)p) - g1.x;
+                const float dx = (gx[p] - g0.x) - g1.x;
                 const float d2 = fmaf(dx, dx, dyz2);
                 const float rr = rsqrt_approx(d2);
                 const float ri = d2 > 0.f ? rr : 0.f;
@@ -436,7 +421,6 @@ __global__ void __launch_bounds__(BX* BY* BZ) k_direct32(GridD g, Phys ph, const
         __syncthreads();
         if (tid == 0 && t + 2 < ntiles) issue(t + 2);
     }
-    (void)h;
     if (j >= g.ny || k >= g.nz || i0 >= g.nx) return;
     const int64_t plane = (int64_t)g.nx * g.ny * g.nz;
     const int64_t row = ((int64_t)k * g.ny + j) * g.nx;
@@ -490,10 +474,10 @@ cudaError_t run_direct(const GridD& g, const Phys& ph, const DevTables& t, int p
         cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
         kern<<<grid, block, sm, st>>>(g, ph, t.geo, t.ljd, t.n, o, t.err, wl, dbg);
     } else {
-        size_t sm = 2 * kT * sizeof(Geo) + 2 * kT * SM * sizeof(LJf) + kT * sizeof(GeoF) + 2 * sizeof(uint64_t);
+        size_t sm = 2 * kT * sizeof(SrcF) + 2 * kT * SM * sizeof(LJf) + 2 * sizeof(uint64_t);
         auto kern = k_direct32<SM, kP, kBX, kBY, kBZ, kT, DU, DH>;
         cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-        kern<<<grid, block, sm, st>>>(g, ph, t.geoU, t.ljf, t.n, o, t.err, wl, dbg);
+        kern<<<grid, block, sm, st>>>(g, ph, t.srcf, t.ljf, t.n, o, t.err, wl, dbg);
     }
     return cudaGetLastError();
 }

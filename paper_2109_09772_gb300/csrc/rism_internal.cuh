@@ -34,8 +34,12 @@ struct __align__(16) LJd {
 struct __align__(16) LJf {
     float A, B, rc2, pad;
 };
-// Tile-local float-float geometry for the FP32 path (hi and lo words).
-struct __align__(16) GeoF {
+// Source point for the FP32 kernels: position in grid units relative to the
+// grid origin as float-float (hi + lo, |lo| <= ulp(hi)/2) and charge.  Grid
+// point indices are exact small integers in FP32, so for a nearby source
+// dx = (i - xh) - xl loses nothing in the first subtraction (Sterbenz) and
+// carries one rounding of dx itself.
+struct __align__(16) SrcF {
     float xh, yh, zh, q;
     float xl, yl, zl, pad;
 };
@@ -130,6 +134,16 @@ __device__ __forceinline__ void ff_add(float& hi, float& lo, float v) {
 __device__ __forceinline__ void split_ff(double v, float& hi, float& lo) {
     hi = __double2float_rn(v);
     lo = __double2float_rn(v - (double)hi);
+}
+
+__device__ __forceinline__ SrcF make_srcf(double x, double y, double z, double q) {
+    SrcF s;
+    split_ff(x, s.xh, s.xl);
+    split_ff(y, s.yh, s.yl);
+    split_ff(z, s.zh, s.zl);
+    s.q = (float)q;
+    s.pad = 0.f;
+    return s;
 }
 
 }  // namespace rism

@@ -14,7 +14,7 @@ struct DevTables {
     int64_t n = 0;    // atoms
     int smax = 2;     // padded site count (2, 4 or 8)
     Geo* geo = nullptr;   // [n] physical positions + charge
-    Geo* geoU = nullptr;  // [n] grid-unit positions (relative to the grid origin) + charge
+    SrcF* srcf = nullptr; // [n] grid-unit positions (relative to the grid origin, float-float) + charge
     LJd* ljd = nullptr;   // [n][smax]
     LJf* ljf = nullptr;   // [n][smax]
     DevErr* err = nullptr;

@@ -29,7 +29,7 @@ constexpr size_t kOffErr = 0;
 constexpr size_t kOffRaw = round_up(sizeof(DevErr));
 constexpr size_t kOffGeo = kOffRaw + round_up(sizeof(double) * 6 * kNoAllocMaxAtoms);
 constexpr size_t kOffGeoU = kOffGeo + round_up(sizeof(Geo) * kNoAllocMaxAtoms);
-constexpr size_t kOffLJd = kOffGeoU + round_up(sizeof(Geo) * kNoAllocMaxAtoms);
+constexpr size_t kOffLJd = kOffGeoU + round_up(sizeof(SrcF) * kNoAllocMaxAtoms);
 constexpr size_t kOffLJf = kOffLJd + round_up(sizeof(LJd) * kNoAllocMaxAtoms * kMaxSites);
 constexpr size_t kScratchBytes = kOffLJf + round_up(sizeof(LJf) * kNoAllocMaxAtoms * kMaxSites);
 static_assert(kScratchBytes == 4063488, "the size stated in rism3d.h");
@@ -140,7 +140,7 @@ extern "C" RISM_API rism_status rism_init_noalloc(const rism_grid_desc* grid, co
     t.smax = smax;
     t.err = reinterpret_cast<DevErr*>(p + kOffErr);
     t.geo = reinterpret_cast<Geo*>(p + kOffGeo);
-    t.geoU = reinterpret_cast<Geo*>(p + kOffGeoU);
+    t.srcf = reinterpret_cast<SrcF*>(p + kOffGeoU);
     t.ljd = reinterpret_cast<LJd*>(p + kOffLJd);
     t.ljf = reinterpret_cast<LJf*>(p + kOffLJf);
     double* raw = reinterpret_cast<double*>(p + kOffRaw);

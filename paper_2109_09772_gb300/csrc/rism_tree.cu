@@ -21,15 +21,23 @@
 // cut-off.  The cells are Morton-code prefixes of the same sorted order the
 // tree is built from, so one device radix sort serves both.
 //
-// Pipeline (all on the context's stream, no host synchronisation):
+// Pipeline (all on the context's stream, no host synchronisation, so that it
+// can be captured in a CUDA graph):
 //   k_bbox_codes -> k_sort_build (one CTA: radix sort, octree, proxy plan)
 //   -> k_node_boxes -> k_gather -> k_cells -> k_upward -> k_proxy_reduce
-//   -> k_lists(count) -> k_scan -> k_lists(fill) -> k_eval32.
-// List and node capacities are checked on the device; an overflow is
-// reported through the state's flag and the host grows the buffers and
-// re-runs the pipeline once.
+//   -> k_far_lists / k_near_lists (count, scan, fill; one warp per batch)
+//   -> k_far32 (far field) -> k_near32 (near field + epilogue).
+// Many solutes: the same per-solute preparation, then one persistent far
+// and one persistent near kernel draining all (solute, batch) work items.
+// List capacities are checked on the device; an overflow is reported through
+// the meta block and the host grows the buffers and runs again.
 #include <cmath>
+#include <cstdio>
+#include <cstdlib>
 #include <cstring>
+#include <map>
+#include <mutex>
+#include <string>
 #include <vector>
 
 #include "rism_tree.h"
@@ -42,7 +50,6 @@ constexpr int kSortThreads = 1024;
 constexpr int kMortonBits = 10;          // per axis
 constexpr int kMaxLevel = kMortonBits;   // octree depth limit
 constexpr int kChunk = 64;               // atoms per upward-pass work item
-constexpr int kBX = 2, kBY = 8, kBZ = 8, kP = 4;  // eval CTA: 128 threads x 4 points = 8x8x8 batch
 constexpr int kT = 64;                   // sources per shared-memory tile
 constexpr int kStack = 8 * kMaxLevel + 8;
 
@@ -59,9 +66,9 @@ struct Node {
 struct TreeMeta {
     int nnodes, nprox, nitems, nleaves;
     int overflow;          // capacity exceeded (nodes / items / far list)
-    int far_total;         // entries the list fill needs
+    int far_total;         // entries the far-list fill needs
+    int near_total;        // entries the near-list fill needs
     int lc;                // cell level of the near field
-    int pad;
     double cube_lo[3];     // Morton cube (grid units)
     double cube_side;
     double cell_side;      // cube_side / 2^lc
@@ -85,13 +92,19 @@ __device__ __forceinline__ uint32_t morton3(uint32_t x, uint32_t y, uint32_t z) 
 // One CTA: min/max of the atoms (grid units), the Morton cube, the codes,
 // and the near-field plan (radius = max(largest LJ cut-off, r_short); cells
 // at least half that radius wide, at most 8^7 of them).
-__global__ void k_bbox_codes(const Geo* __restrict__ geoU, const LJd* __restrict__ ljd, int n, int S, int smax,
-                             double rs, double h, TreeMeta* meta, uint32_t* code, uint32_t* idx) {
+__device__ __forceinline__ Geo to_grid(const Geo& p, const GridD& g) {
+    const double ih = 1.0 / g.h;
+    return Geo{(p.x - g.ox) * ih, (p.y - g.oy) * ih, (p.z - g.oz) * ih, p.q};
+}
+
+__global__ void k_bbox_codes(const Geo* __restrict__ geo, const LJd* __restrict__ ljd, int n, int S, int smax,
+                             double rs, GridD gd, TreeMeta* meta, uint32_t* code, uint32_t* idx) {
+    const double h = gd.h;
     __shared__ double red[7][kSortThreads / 32];
     double lo[3] = {INFINITY, INFINITY, INFINITY}, hi[3] = {-INFINITY, -INFINITY, -INFINITY};
     double rc2 = 0.0;
     for (int i = threadIdx.x; i < n; i += blockDim.x) {
-        Geo g = geoU[i];
+        Geo g = to_grid(geo[i], gd);
         double v[3] = {g.x, g.y, g.z};
         for (int d = 0; d < 3; ++d) {
             lo[d] = fmin(lo[d], v[d]);
@@ -146,7 +159,7 @@ __global__ void k_bbox_codes(const Geo* __restrict__ geoU, const LJd* __restrict
     __syncthreads();
     const double sc = (double)(1 << kMortonBits) / cube[3];
     for (int i = threadIdx.x; i < n; i += blockDim.x) {
-        Geo g = geoU[i];
+        Geo g = to_grid(geo[i], gd);
         uint32_t c[3];
         double v[3] = {g.x, g.y, g.z};
         for (int d = 0; d < 3; ++d) {
@@ -368,7 +381,8 @@ __global__ void __launch_bounds__(kSortThreads) k_sort_build(BuildArgs a, uint32
 }
 
 // --------------------------------- node boxes, gathered sources, cells
-__global__ void k_node_boxes(Node* nodes, const TreeMeta* meta, const uint32_t* idx, const Geo* __restrict__ geoU) {
+__global__ void k_node_boxes(Node* nodes, const TreeMeta* meta, const uint32_t* idx, const Geo* __restrict__ geo,
+                             GridD gd) {
     if (meta->overflow) return;  // the tree is incomplete; the host reports it
     const int nn = meta->nnodes;
     const int lane = threadIdx.x & 31;
@@ -376,7 +390,7 @@ __global__ void k_node_boxes(Node* nodes, const TreeMeta* meta, const uint32_t* 
         Node nd = nodes[nid];
         double lo[3] = {INFINITY, INFINITY, INFINITY}, hi[3] = {-INFINITY, -INFINITY, -INFINITY};
         for (int i = nd.begin + lane; i < nd.end; i += 32) {
-            Geo g = geoU[idx[i]];
+            Geo g = to_grid(geo[idx[i]], gd);
             double v[3] = {g.x, g.y, g.z};
             for (int d = 0; d < 3; ++d) {
                 lo[d] = fmin(lo[d], v[d]);
@@ -396,12 +410,15 @@ __global__ void k_node_boxes(Node* nodes, const TreeMeta* meta, const uint32_t* 
     }
 }
 
-// Sorted copies of the atom geometry and LJ tables (sources of the eval kernel).
-__global__ void k_gather(int n, int smax, const uint32_t* idx, const Geo* __restrict__ geoU,
-                         const LJf* __restrict__ ljf, Geo* src, LJf* ljs) {
+// Sorted copies of the atom geometry (FP64 grid units for the upward pass,
+// float-float for the evaluation kernels) and of the LJ tables.
+__global__ void k_gather(int n, int smax, const uint32_t* idx, const Geo* __restrict__ geo, GridD gd,
+                         const LJf* __restrict__ ljf, Geo* src, SrcF* srcf, LJf* ljs) {
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
         const int j = (int)idx[i];
-        src[i] = geoU[j];
+        const Geo gg = to_grid(geo[j], gd);
+        src[i] = gg;
+        srcf[i] = make_srcf(gg.x, gg.y, gg.z, gg.q);
         for (int s = 0; s < smax; ++s) ljs[(int64_t)i * smax + s] = ljf[(int64_t)j * smax + s];
     }
 }
@@ -492,7 +509,7 @@ __global__ void k_upward(int deg, const TreeMeta* meta, const Node* nodes, const
 // Sum the partials of each proxy set in item order (deterministic) and write
 // the proxy points (grid units) with their modified charges after the atoms.
 __global__ void k_proxy_reduce(int deg, int n, const TreeMeta* meta, const Node* nodes, const int* prox_nodes,
-                               const int* items, const double* part, Geo* src) {
+                               const int* items, const double* part, Geo* src, SrcF* srcf) {
     const int np = deg + 1, P3 = np * np * np;
     if (meta->overflow) return;
     const int nprox = meta->nprox, nitems = meta->nitems;
@@ -509,94 +526,234 @@ __global__ void k_proxy_reduce(int deg, int n, const TreeMeta* meta, const Node*
             const int m1 = p % np, m2 = (p / np) % np, m3 = p / (np * np);
             double q = 0.0;
             for (int it = i0; it < i1; ++it) q += part[(int64_t)it * P3 + p];
-            src[n + (int64_t)k * P3 + p] = Geo{c[0] + r[0] * cospi((double)m1 / deg), c[1] + r[1] * cospi((double)m2 / deg),
-                                               c[2] + r[2] * cospi((double)m3 / deg), q};
+            const Geo pp{c[0] + r[0] * cospi((double)m1 / deg), c[1] + r[1] * cospi((double)m2 / deg),
+                         c[2] + r[2] * cospi((double)m3 / deg), q};
+            src[n + (int64_t)k * P3 + p] = pp;
+            srcf[n + (int64_t)k * P3 + p] = make_srcf(pp.x, pp.y, pp.z, pp.q);
         }
     }
 }
 
-// -------------------------------------------------------------- lists
+// ------------------------------------------------------- target batches
+// A target batch is NXB x NYB x NZB grid points.  The far kernel gives each
+// thread PF consecutive x points, the near kernel 4; both run one CTA per
+// batch (or per work item of the persistent batched kernels).  The variants
+// are the launch shapes the autotuner chooses from.
+struct ShapeDesc {
+    int nx, ny, nz, pf;
+};
+constexpr int kNumShapes = 3;
+__host__ __device__ constexpr ShapeDesc shape_of(int v) {
+    return v == 1 ? ShapeDesc{16, 8, 8, 8} : (v == 2 ? ShapeDesc{8, 8, 4, 4} : ShapeDesc{8, 8, 8, 4});
+}
+
+constexpr int kQCap = 1024;        // frontier capacity of the warp-cooperative traversal
+constexpr int kListWarps = 4;      // warps (batches) per list-building CTA
+
 struct ListArgs {
     int nbx, nby, nbz;        // batches per axis
     int bx, by, bz;           // batch dims (points)
     double theta;
     int n, P3;
-    int cap;                  // capacity of the far-list entry buffer
+    int cap;                  // capacity of the entry buffer
 };
 
-// One thread per target batch: depth-first traversal.  Far list entries are
-// (start, count) ranges of the source array: sorted atoms (direct) or a proxy
-// set (n + k P3, P3).  Adjacent direct ranges are merged.
+__device__ __forceinline__ void batch_geom(const ListArgs& a, int b, double cb[3], double& rb, int lo[3], int hi[3]) {
+    const int ib = b % a.nbx, jb = (b / a.nbx) % a.nby, kb = b / (a.nbx * a.nby);
+    lo[0] = ib * a.bx;
+    lo[1] = jb * a.by;
+    lo[2] = kb * a.bz;
+    hi[0] = lo[0] + a.bx - 1;
+    hi[1] = lo[1] + a.by - 1;
+    hi[2] = lo[2] + a.bz - 1;
+    for (int d = 0; d < 3; ++d) cb[d] = 0.5 * (lo[d] + hi[d]);
+    rb = 0.5 * sqrt((double)((a.bx - 1) * (a.bx - 1) + (a.by - 1) * (a.by - 1) + (a.bz - 1) * (a.bz - 1)));
+}
+
+// Far lists: one warp per target batch, level-synchronous traversal of the
+// octree with the frontier in shared memory.  Entries are (start, count)
+// ranges of the source array: atoms of a node evaluated directly, or a proxy
+// set (n + k P3, P3) of an accepted node.  Order: by level, then by lane --
+// deterministic.
 template <bool FILL>
-__global__ void k_lists(ListArgs a, const Node* __restrict__ nodes, const int* off, int2* ent, int* cnt,
-                        TreeMeta* meta) {
+__global__ void __launch_bounds__(32 * kListWarps) k_far_lists(ListArgs a, const Node* __restrict__ nodes,
+                                                              const int* off, int2* ent, int* cnt, TreeMeta* meta) {
+    __shared__ int qa[kListWarps][kQCap], qb[kListWarps][kQCap];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     const int nb = a.nbx * a.nby * a.nbz;
-    const int b = blockIdx.x * blockDim.x + threadIdx.x;
-    if (b >= nb) return;
-    if (meta->overflow && !FILL) {
-        cnt[b] = 0;  // tree incomplete: empty lists, the host reports the overflow
+    if (meta->overflow) {
+        for (int b = blockIdx.x * kListWarps + w; b < nb; b += gridDim.x * kListWarps)
+            if (!FILL && lane == 0) cnt[b] = 0;
         return;
     }
-    if (meta->overflow) return;
-    const int ib = b % a.nbx, jb = (b / a.nbx) % a.nby, kb = b / (a.nbx * a.nby);
-    const double cb[3] = {ib * a.bx + 0.5 * (a.bx - 1), jb * a.by + 0.5 * (a.by - 1), kb * a.bz + 0.5 * (a.bz - 1)};
-    const double rb = 0.5 * sqrt((double)((a.bx - 1) * (a.bx - 1) + (a.by - 1) * (a.by - 1) + (a.bz - 1) * (a.bz - 1)));
-    int stack[kStack];
-    int sp = 0;
-    if (a.n > 0) stack[sp++] = 0;
-    int m = 0;
-    int base = FILL ? off[b] : 0;
-    int last_s = -1, last_e = -1;
-    long long dpairs = 0, ppairs = 0;
-    const int cap = a.cap;
-    while (sp > 0) {
-        const Node nd = nodes[stack[--sp]];
-        double R2 = 0.0, rn2 = 0.0;
-        for (int d = 0; d < 3; ++d) {
-            const double cn = 0.5 * (nd.lo[d] + nd.hi[d]);
-            R2 += (cb[d] - cn) * (cb[d] - cn);
-            rn2 += 0.25 * (nd.hi[d] - nd.lo[d]) * (nd.hi[d] - nd.lo[d]);
+    const long long pts = (long long)a.bx * a.by * a.bz;
+    for (int b = blockIdx.x * kListWarps + w; b < nb; b += gridDim.x * kListWarps) {
+        double cb[3], rb;
+        int lo[3], hi[3];
+        batch_geom(a, b, cb, rb, lo, hi);
+        int* cur = qa[w];
+        int* nxt = qb[w];
+        int ncur = a.n > 0 ? 1 : 0;
+        if (lane == 0) cur[0] = 0;
+        __syncwarp();
+        int m = 0;
+        const int base = FILL ? off[b] : 0;
+        long long dp = 0, pp = 0;
+        bool ovf = false;
+        while (ncur > 0) {
+            int nnext = 0;
+            for (int c0 = 0; c0 < ncur; c0 += 32) {
+                const int k = c0 + lane;
+                int kind = 0;  // 0 none, 1 entry, 2 open
+                int2 e = make_int2(0, 0);
+                int nch = 0, fch = 0;
+                if (k < ncur) {
+                    const Node nd = nodes[cur[k]];
+                    double R2 = 0.0, rn2 = 0.0;
+                    for (int d = 0; d < 3; ++d) {
+                        const double cn = 0.5 * (nd.lo[d] + nd.hi[d]);
+                        R2 += (cb[d] - cn) * (cb[d] - cn);
+                        rn2 += 0.25 * (nd.hi[d] - nd.lo[d]) * (nd.hi[d] - nd.lo[d]);
+                    }
+                    const double rs = rb + sqrt(rn2);
+                    const bool sep = rs * rs < a.theta * a.theta * R2;
+                    const int cntn = nd.end - nd.begin;
+                    if (sep && nd.prox >= 0) {
+                        kind = 1;
+                        e = make_int2(a.n + nd.prox * a.P3, a.P3);
+                        pp += a.P3;
+                    } else if (nd.first_child < 0 || (sep && cntn <= a.P3)) {
+                        kind = 1;
+                        e = make_int2(nd.begin, cntn);
+                        dp += cntn;
+                    } else {
+                        kind = 2;
+                        nch = nd.nchild;
+                        fch = nd.first_child;
+                    }
+                }
+                const unsigned em = __ballot_sync(0xffffffffu, kind == 1);
+                if (kind == 1) {
+                    const int pos = m + __popc(em & ((1u << lane) - 1u));
+                    if (FILL && base + pos < a.cap) ent[base + pos] = e;
+                }
+                m += __popc(em);
+                // children of opened nodes: exclusive prefix of nch over lanes
+                int x = nch;
+                for (int o = 1; o < 32; o <<= 1) {
+                    const int y = __shfl_up_sync(0xffffffffu, x, o);
+                    if (lane >= o) x += y;
+                }
+                const int tot = __shfl_sync(0xffffffffu, x, 31);
+                const int at = nnext + x - nch;
+                if (kind == 2) {
+                    for (int ch = 0; ch < nch; ++ch) {
+                        if (at + ch < kQCap) nxt[at + ch] = fch + ch;
+                        else ovf = true;
+                    }
+                }
+                nnext += tot;
+            }
+            __syncwarp();
+            if (__any_sync(0xffffffffu, ovf) || nnext > kQCap) {
+                if (lane == 0) meta->overflow = 1;
+                break;
+            }
+            int* t = cur;
+            cur = nxt;
+            nxt = t;
+            ncur = nnext;
+            __syncwarp();
         }
-        const double rs = rb + sqrt(rn2);
-        const bool sep = rs * rs < a.theta * a.theta * R2;
-        const int cntn = nd.end - nd.begin;
-        int s = -1, e = -1;
-        if (sep && nd.prox >= 0) {
-            // proxy set: never merged with atom ranges
-            if (FILL && m < cap - base) ent[base + m] = make_int2(a.n + nd.prox * a.P3, a.P3);
-            ++m;
-            ppairs += a.P3;
-            last_s = last_e = -1;
-            continue;
+        if (!FILL) {
+            for (int o = 16; o > 0; o >>= 1) {
+                dp += __shfl_xor_sync(0xffffffffu, dp, o);
+                pp += __shfl_xor_sync(0xffffffffu, pp, o);
+            }
+            if (lane == 0) {
+                cnt[b] = m;
+                atomicAdd(&meta->direct_pairs, (unsigned long long)(dp * pts));
+                atomicAdd(&meta->proxy_pairs, (unsigned long long)(pp * pts));
+            }
         }
-        if (nd.first_child < 0 || (sep && cntn <= a.P3)) {
-            s = nd.begin;
-            e = nd.end;
-        } else {
-            for (int ch = nd.nchild - 1; ch >= 0; --ch)
-                if (sp < kStack) stack[sp++] = nd.first_child + ch;
-            continue;
-        }
-        dpairs += e - s;
-        if (s == last_e) {
-            last_e = e;
-            if (FILL && m - 1 < cap - base) ent[base + m - 1].y = last_e - last_s;
-        } else {
-            if (FILL && m < cap - base) ent[base + m] = make_int2(s, e - s);
-            ++m;
-            last_s = s;
-            last_e = e;
-        }
-    }
-    if (!FILL) {
-        cnt[b] = m;
-        const long long pts = (long long)a.bx * a.by * a.bz;
-        atomicAdd(&meta->direct_pairs, (unsigned long long)(dpairs * pts));
-        atomicAdd(&meta->proxy_pairs, (unsigned long long)(ppairs * pts));
     }
 }
 
-__global__ void k_scan(int nb, const int* cnt, int* off, int cap, TreeMeta* meta) {
+// Near lists: one warp per target batch; lanes test the cells of the box
+// grown by rnear (x fastest), keep those whose box lies within rnear of the
+// batch box, and emit their atom ranges in cell order.
+template <bool FILL>
+__global__ void __launch_bounds__(32 * kListWarps) k_near_lists(ListArgs a, const TreeMeta* __restrict__ meta_c,
+                                                               const int* __restrict__ cell_start, const int* off,
+                                                               int2* ent, int* cnt, TreeMeta* meta) {
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const int nb = a.nbx * a.nby * a.nbz;
+    if (meta->overflow) {
+        for (int b = blockIdx.x * kListWarps + w; b < nb; b += gridDim.x * kListWarps)
+            if (!FILL && lane == 0) cnt[b] = 0;
+        return;
+    }
+    const int lc = meta_c->lc, ncell = 1 << lc;
+    const double side = meta_c->cell_side, rnear = meta_c->rnear;
+    const double rn = isfinite(rnear) ? rnear : 1e30;
+    const double rn2 = rn * rn;
+    const long long pts = (long long)a.bx * a.by * a.bz;
+    for (int b = blockIdx.x * kListWarps + w; b < nb; b += gridDim.x * kListWarps) {
+        double cb[3], rb;
+        int lo[3], hi[3];
+        batch_geom(a, b, cb, rb, lo, hi);
+        int c0[3], c1[3];
+        bool ok = a.n > 0;
+        for (int d = 0; d < 3; ++d) {
+            c0[d] = (int)fmax(floor((lo[d] - rn - meta_c->cube_lo[d]) / side), 0.0);
+            c1[d] = (int)fmin(floor((hi[d] + rn - meta_c->cube_lo[d]) / side), (double)(ncell - 1));
+            ok = ok && c0[d] <= c1[d];
+        }
+        const int ex = ok ? c1[0] - c0[0] + 1 : 0, ey = ok ? c1[1] - c0[1] + 1 : 0, ez = ok ? c1[2] - c0[2] + 1 : 0;
+        const int total = ex * ey * ez;
+        int m = 0;
+        long long cand = 0;
+        const int base = FILL ? off[b] : 0;
+        for (int k0 = 0; k0 < total; k0 += 32) {
+            const int k = k0 + lane;
+            int2 e = make_int2(0, 0);
+            bool take = false;
+            if (k < total) {
+                const int cc[3] = {c0[0] + k % ex, c0[1] + (k / ex) % ey, c0[2] + k / (ex * ey)};
+                double d2 = 0.0;
+                for (int d = 0; d < 3; ++d) {
+                    const double clo = meta_c->cube_lo[d] + cc[d] * side, chi = clo + side;
+                    const double gap = fmax(0.0, fmax(clo - hi[d], lo[d] - chi));
+                    d2 += gap * gap;
+                }
+                if (d2 < rn2) {
+                    const uint32_t mc = morton3((uint32_t)cc[0], (uint32_t)cc[1], (uint32_t)cc[2]);
+                    const int s0 = cell_start[mc], s1 = cell_start[mc + 1];
+                    if (s1 > s0) {
+                        take = true;
+                        e = make_int2(s0, s1 - s0);
+                        cand += s1 - s0;
+                    }
+                }
+            }
+            const unsigned em = __ballot_sync(0xffffffffu, take);
+            if (take) {
+                const int pos = m + __popc(em & ((1u << lane) - 1u));
+                if (FILL && base + pos < a.cap) ent[base + pos] = e;
+            }
+            m += __popc(em);
+        }
+        if (!FILL) {
+            for (int o = 16; o > 0; o >>= 1) cand += __shfl_xor_sync(0xffffffffu, cand, o);
+            if (lane == 0) {
+                cnt[b] = m;
+                atomicAdd(&meta->near_pairs, (unsigned long long)(cand * pts));
+            }
+        }
+    }
+}
+
+__global__ void k_scan(int nb, const int* cnt, int* off, int cap, TreeMeta* meta, int which) {
     __shared__ int tmp[64];
     __shared__ int carry;
     if (threadIdx.x == 0) carry = 0;
@@ -613,14 +770,15 @@ __global__ void k_scan(int nb, const int* cnt, int* off, int cap, TreeMeta* meta
     }
     if (threadIdx.x == 0) {
         off[nb] = carry;
-        meta->far_total = carry;
+        if (which == 0) meta->far_total = carry;
+        else meta->near_total = carry;
         if (carry > cap) meta->overflow = 1;
     }
 }
 
 __global__ void k_reset_meta(TreeMeta* meta) {
     meta->direct_pairs = meta->proxy_pairs = meta->near_pairs = 0ull;
-    meta->far_total = 0;
+    meta->far_total = meta->near_total = 0;
     meta->overflow = 0;
     meta->nnodes = meta->nprox = meta->nitems = meta->nleaves = 0;
     meta->lc = 0;
@@ -630,34 +788,27 @@ __global__ void k_reset_meta(TreeMeta* meta) {
 }
 
 // ---------------------------------------------------------------- eval
+// Sources reach shared memory through bulk TMA copies issued by thread 0
+// into a kStages-deep ring of tiles guarded by full (copy landed) and empty
+// (all warps done) mbarriers; every wait is bounded.
+constexpr int kStages = 3;
+
 struct EvalArgs {
     GridD g;
     Phys ph;
     int nbx, nby, nbz;
     int n;
-    const Geo* src;        // [sorted atoms | proxies], grid units
+    const SrcF* srcf;      // [sorted atoms | proxies], grid units, float-float
     const LJf* ljs;        // sorted LJ tables
-    const int* off;        // far-list offsets [nb+1]
-    const int2* ent;       // far-list entries
-    const int* cell_start; // [8^lc + 1]
+    const int* far_off;    // far-list offsets [nb+1]
+    const int2* far_ent;
+    const int* near_off;   // near-list offsets [nb+1]
+    const int2* near_ent;
+    float4* far;           // per grid point: Phi1 (hi, lo), Phik (hi, lo), grid units
     Outputs o;
     DevErr* err;
     TreeMeta* meta;
     long long wlim;
-};
-
-// Producer state (thread 0 only): walks the far list, then the cells.
-struct Producer {
-    int phase;            // 0 far, 1 near, 2 done
-    int near_ok;          // the near phase has at least one candidate cell
-    int lc;
-    double cell_lo[3], cell_side, rnear, rnear2;
-    int e, e_end, e_off;  // far entry cursor
-    int cx, cy, cz;       // cell cursor
-    int c0[3], c1[3];     // cell range
-    int cell_pos, cell_end;
-    double box_lo[3], box_hi[3];
-    unsigned long long near_cand;
 };
 
 __device__ __forceinline__ void mbar_expect_tx_only(uint64_t* bar, uint32_t bytes) {
@@ -666,280 +817,288 @@ __device__ __forceinline__ void mbar_expect_tx_only(uint64_t* bar, uint32_t byte
 __device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
     asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
 }
+__device__ __forceinline__ void mbar_inval(uint64_t* bar) {
+    asm volatile("mbarrier.inval.shared::cta.b64 [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
 
-template <int SM>
-__device__ int produce_tile(Producer& P, const EvalArgs& a, Geo* sgeo, LJf* slj, uint64_t* bar, int& kind) {
+template <int SM, bool WITH_LJ>
+struct Ring {
+    SrcF src[kStages][kT];
+    LJf lj[WITH_LJ ? kStages : 1][WITH_LJ ? kT * SM : 1];
+    uint64_t full[kStages], empty[kStages];
+    int cnt[kStages];
+    int abort;
+    int inited;
+};
+
+// Range-list producer state (thread 0).
+struct Cursor {
+    int e, e_end, off;
+    int produced;
+    bool done;
+    int last_phase[kStages];
+};
+
+template <int SM, bool LJ>
+__device__ int fill_ranges(Cursor& c, const int2* __restrict__ ent, const SrcF* __restrict__ src,
+                           const LJf* __restrict__ ljs, SrcF* dst, LJf* ldst, uint64_t* bar) {
     int filled = 0;
-    kind = P.phase;
-    while (P.phase == 0 && filled < kT) {
-        if (P.e >= P.e_end) {
-            P.phase = P.near_ok ? 1 : 2;
-            break;
-        }
-        const int2 en = a.ent[P.e];
-        const int take = min(kT - filled, en.y - P.e_off);
-        const uint32_t bytes = take * sizeof(Geo);
-        mbar_expect_tx_only(bar, bytes);
-        bulk_g2s(sgeo + filled, a.src + en.x + P.e_off, bytes, bar);
-        filled += take;
-        P.e_off += take;
-        if (P.e_off >= en.y) {
-            ++P.e;
-            P.e_off = 0;
-        }
-    }
-    if (filled > 0) {
-        mbar_arrive(bar);
-        return filled;
-    }
-    kind = 1;
-    while (P.phase == 1 && filled < kT) {
-        if (P.cell_pos >= P.cell_end) {
-            // advance to the next non-empty cell that can hold a pair within rnear
-            bool found = false;
-            while (!found) {
-                if (++P.cx > P.c1[0]) {
-                    P.cx = P.c0[0];
-                    if (++P.cy > P.c1[1]) {
-                        P.cy = P.c0[1];
-                        if (++P.cz > P.c1[2]) {
-                            P.phase = 2;
-                            break;
-                        }
-                    }
-                }
-                // distance between the cell box and the batch box
-                const int cc[3] = {P.cx, P.cy, P.cz};
-                double d2 = 0.0;
-                for (int d = 0; d < 3; ++d) {
-                    const double lo = P.cell_lo[d] + cc[d] * P.cell_side, hi = lo + P.cell_side;
-                    const double gap = fmax(0.0, fmax(lo - P.box_hi[d], P.box_lo[d] - hi));
-                    d2 += gap * gap;
-                }
-                if (d2 >= P.rnear2) continue;
-                const uint32_t m = morton3((uint32_t)P.cx, (uint32_t)P.cy, (uint32_t)P.cz);
-                P.cell_pos = a.cell_start[m];
-                P.cell_end = a.cell_start[m + 1];
-                found = P.cell_pos < P.cell_end;
-            }
-            if (P.phase == 2) break;
-        }
-        const int take = min(kT - filled, P.cell_end - P.cell_pos);
-        const uint32_t b1 = take * sizeof(Geo), b2 = take * SM * sizeof(LJf);
+    while (filled < kT && c.e < c.e_end) {
+        const int2 en = ent[c.e];
+        const int take = min(kT - filled, en.y - c.off);
+        const uint32_t b1 = take * sizeof(SrcF), b2 = LJ ? take * SM * sizeof(LJf) : 0;
         mbar_expect_tx_only(bar, b1 + b2);
-        bulk_g2s(sgeo + filled, a.src + P.cell_pos, b1, bar);
-        bulk_g2s(slj + filled * SM, a.ljs + (int64_t)P.cell_pos * SM, b2, bar);
+        bulk_g2s(dst + filled, src + en.x + c.off, b1, bar);
+        if (LJ) bulk_g2s(ldst + filled * SM, ljs + (int64_t)(en.x + c.off) * SM, b2, bar);
         filled += take;
-        P.cell_pos += take;
-    }
-    if (filled > 0) {
-        mbar_arrive(bar);
-        P.near_cand += filled;
+        c.off += take;
+        if (c.off >= en.y) {
+            ++c.e;
+            c.off = 0;
+        }
     }
     return filled;
 }
 
-template <int SM, bool DU, bool DH>
-__global__ void __launch_bounds__(kBX* kBY* kBZ) k_eval32(EvalArgs a) {
-    constexpr int NT = kBX * kBY * kBZ, P = kP;
-    extern __shared__ __align__(16) unsigned char smem[];
-    Geo* sgeo = reinterpret_cast<Geo*>(smem);                                        // [2][kT]
-    LJf* slj = reinterpret_cast<LJf*>(smem + 2 * kT * sizeof(Geo));                  // [2][kT*SM]
-    GeoF* conv = reinterpret_cast<GeoF*>(smem + 2 * kT * sizeof(Geo) + 2 * kT * SM * sizeof(LJf));
-    uint64_t* bar = reinterpret_cast<uint64_t*>(smem + 2 * kT * sizeof(Geo) + 2 * kT * SM * sizeof(LJf) +
-                                                kT * sizeof(GeoF));
-    __shared__ int s_cnt[2], s_kind[2];
-    // lists that overflowed their buffer are incomplete: the host grows them and runs again
-    if (a.meta->overflow) return;
+template <int SM, bool LJ, typename R>
+__device__ __forceinline__ void produce(Cursor& c, R& r, int slot, const int2* ent, const SrcF* src, const LJf* ljs) {
+    const int n = c.done ? 0 : fill_ranges<SM, LJ>(c, ent, src, ljs, r.src[slot], r.lj[LJ ? slot : 0], &r.full[slot]);
+    if (n == 0) c.done = true;
+    r.cnt[slot] = n;
+    c.last_phase[slot] = c.produced / kStages;
+    ++c.produced;
+    mbar_arrive(&r.full[slot]);
+}
 
+// Ring setup for one work item (thread 0), with the barriers of a previous
+// item invalidated first.  Callers put a __syncthreads() on both sides.
+template <typename R>
+__device__ void ring_init(R& r, int nwarps) {
+    for (int s = 0; s < kStages; ++s) {
+        if (r.inited) {
+            mbar_inval(&r.full[s]);
+            mbar_inval(&r.empty[s]);
+        }
+        mbar_init(&r.full[s], 1);
+        mbar_init(&r.empty[s], nwarps);
+    }
+    r.inited = 1;
+    r.abort = 0;
+    mbar_fence_init();
+}
+
+template <typename R>
+__device__ void drain(R& r, const Cursor& c, long long wlim) {
+    for (int s = 0; s < kStages; ++s)
+        if (c.last_phase[s] >= 0) mbar_wait_bounded(&r.full[s], (uint32_t)(c.last_phase[s] & 1), wlim);
+}
+
+// Consumer loop skeleton shared by the far and near bodies.  Returns false
+// after an abort (bounded wait ran out).
+template <int SM, bool LJ, int NWARPS, typename R, typename F>
+__device__ bool run_ring(R& r, Cursor& cur, const int2* ent, const SrcF* src, const LJf* ljs, const EvalArgs& a,
+                         F&& consume) {
+    const int tid = threadIdx.x, lane = tid & 31;
+    if (tid == 0)
+        for (int s = 0; s < kStages; ++s) produce<SM, LJ>(cur, r, s, ent, src, ljs);
+    for (int t = 0;; ++t) {
+        const int slot = t % kStages;
+        const uint32_t ph = (t / kStages) & 1;
+        if (!mbar_wait_bounded(&r.full[slot], ph, a.wlim) || r.abort) {
+            r.abort = 1;
+            report_error(a.err, DEV_TIMEOUT, WHERE_TREE_EVAL);
+            if (tid == 0) drain(r, cur, a.wlim);
+            return false;
+        }
+        const int cnt = r.cnt[slot];
+        if (cnt == 0) return true;
+        consume(slot, cnt);
+        __syncwarp();
+        if (lane == 0) mbar_arrive(&r.empty[slot]);
+        if (tid == 0 && !cur.done) {
+            if (!mbar_wait_bounded(&r.empty[slot], ph, a.wlim)) {
+                r.abort = 1;
+                report_error(a.err, DEV_TIMEOUT, WHERE_TREE_EVAL);
+            } else {
+                produce<SM, LJ>(cur, r, slot, ent, src, ljs);
+            }
+        }
+    }
+}
+
+// ---- far field: Phi1 = sum q/d and Phik = sum q e^{-kappa d}/d over the batch's far list
+template <int NXB, int NYB, int NZB, int PF>
+struct FarShape {
+    static constexpr int TX = NXB / PF, NT = TX * NYB * NZB, NW = NT / 32;
+};
+
+template <int NXB, int NYB, int NZB, int PF, bool DH>
+__device__ void far_body(const EvalArgs& a, int b, Ring<1, false>& r) {
+    using Sh = FarShape<NXB, NYB, NZB, PF>;
+    constexpr int P = PF;
     const int tid = threadIdx.x;
-    const int tx = tid % kBX, ty = (tid / kBX) % kBY, tz = tid / (kBX * kBY);
-    const int b = blockIdx.x;
+    const int tx = tid % Sh::TX, ty = (tid / Sh::TX) % NYB, tz = tid / (Sh::TX * NYB);
     const int ib = b % a.nbx, jb = (b / a.nbx) % a.nby, kb = b / (a.nbx * a.nby);
-    const int ti0 = ib * (kBX * P), tj0 = jb * kBY, tk0 = kb * kBZ;
-    const int i0 = ti0 + tx * P, j = tj0 + ty, k = tk0 + tz;
-    const float fx0 = (float)(tx * P), fy = (float)ty, fz = (float)tz;
+    const int i0 = ib * NXB + tx * P, j = jb * NYB + ty, k = kb * NZB + tz;
+    float gx[P];
+#pragma unroll
+    for (int p = 0; p < P; ++p) gx[p] = (float)(i0 + p);
+    const float fy = (float)j, fz = (float)k;
+    const float kap2 = (float)(-a.ph.kappa * a.g.h * 1.4426950408889634);  // e^{-kappa d} = 2^(kap2 d_grid)
+    float f1h[P], f1l[P], fkh[P], fkl[P];
+#pragma unroll
+    for (int p = 0; p < P; ++p) f1h[p] = f1l[p] = fkh[p] = fkl[p] = 0.f;
+    Cursor cur;
+    __syncthreads();
+    if (tid == 0) {
+        cur.e = a.far_off[b];
+        cur.e_end = a.far_off[b + 1];
+        cur.off = 0;
+        cur.produced = 0;
+        cur.done = false;
+        for (int s = 0; s < kStages; ++s) cur.last_phase[s] = -1;
+        ring_init(r, Sh::NW);
+    }
+    __syncthreads();
+    const bool ok = run_ring<1, false, Sh::NW>(r, cur, a.far_ent, a.srcf, nullptr, a, [&](int slot, int cnt) {
+        const SrcF* Sx = r.src[slot];
+        float p1[P], pk[P];
+#pragma unroll
+        for (int p = 0; p < P; ++p) p1[p] = pk[p] = 0.f;
+        for (int s0 = 0; s0 < cnt; ++s0) {
+            const float4 g0 = *reinterpret_cast<const float4*>(&Sx[s0].xh);
+            const float4 g1 = *reinterpret_cast<const float4*>(&Sx[s0].xl);
+            const float dy = (fy - g0.y) - g1.y;
+            const float dz = (fz - g0.z) - g1.z;
+            const float dyz2 = fmaf(dy, dy, dz * dz);
+#pragma unroll
+            for (int p = 0; p < P; ++p) {
+                const float dx = (gx[p] - g0.x) - g1.x;
+                const float d2 = fmaf(dx, dx, dyz2);
+                const float rr = rsqrt_approx(d2);
+                const float ri = d2 > 0.f ? rr : 0.f;
+                const float qr = g0.w * ri;
+                p1[p] += qr;
+                if (DH) pk[p] = fmaf(qr, ex2_approx(kap2 * (d2 * ri)), pk[p]);
+            }
+        }
+#pragma unroll
+        for (int p = 0; p < P; ++p) {
+            ff_add(f1h[p], f1l[p], p1[p]);
+            if (DH) ff_add(fkh[p], fkl[p], pk[p]);
+        }
+    });
+    if (!ok) return;
+    const GridD& g = a.g;
+    if (j >= g.ny || k >= g.nz || i0 >= g.nx) return;
+    float4* dst = a.far + ((int64_t)k * g.ny + j) * g.nx;
+#pragma unroll
+    for (int p = 0; p < P; ++p)
+        if (i0 + p < g.nx) dst[i0 + p] = make_float4(f1h[p], f1l[p], fkh[p], fkl[p]);
+}
+
+// ---- near field (LJ within cut-offs, erfc remainders within r_short) + epilogue
+template <int NXB, int NYB, int NZB>
+struct NearShape {
+    static constexpr int P = 4, TX = NXB / P, NT = TX * NYB * NZB, NW = NT / 32;
+};
+
+template <int NXB, int NYB, int NZB, int SM, bool DU, bool DH>
+__device__ void near_body(const EvalArgs& a, int b, Ring<SM, true>& r) {
+    using Sh = NearShape<NXB, NYB, NZB>;
+    constexpr int P = Sh::P;
+    const int tid = threadIdx.x;
+    const int tx = tid % Sh::TX, ty = (tid / Sh::TX) % NYB, tz = tid / (Sh::TX * NYB);
+    const int ib = b % a.nbx, jb = (b / a.nbx) % a.nby, kb = b / (a.nbx * a.nby);
+    const int i0 = ib * NXB + tx * P, j = jb * NYB + ty, k = kb * NZB + tz;
+    float gx[P];
+#pragma unroll
+    for (int p = 0; p < P; ++p) gx[p] = (float)(i0 + p);
+    const float fy = (float)j, fz = (float)k;
     const float rs2 = (float)((a.ph.rs / a.g.h) * (a.ph.rs / a.g.h));
     const float xs = (float)(a.g.h / a.ph.eta);
-    const float kap2 = (float)(-a.ph.kappa * a.g.h * 1.4426950408889634);
     const float aa_ = (float)a.ph.a;
     const float c0h = (float)(a.ph.phi_c0 * a.g.h), h0h = (float)(a.ph.phi_h0 * a.g.h);
     const bool DC = a.o.c != nullptr;
+    const double rnear = a.meta->rnear;
+    const float rn2 = isfinite(rnear) ? (float)(rnear * rnear) : INFINITY;
 
-    float f1h[P], f1l[P], fkh[P], fkl[P], sch[P], scl[P], shh[P], shl[P], ljh[P][SM], ljl[P][SM];
+    float sch[P], scl[P], shh[P], shl[P], ljh[P][SM], ljl[P][SM];
 #pragma unroll
     for (int p = 0; p < P; ++p) {
-        f1h[p] = f1l[p] = fkh[p] = fkl[p] = sch[p] = scl[p] = shh[p] = shl[p] = 0.f;
+        sch[p] = scl[p] = shh[p] = shl[p] = 0.f;
 #pragma unroll
         for (int s = 0; s < SM; ++s) ljh[p][s] = ljl[p][s] = 0.f;
     }
     unsigned hit = 0u;
-    __shared__ float s_rn2;
-    if (tid == 0) s_rn2 = isfinite(a.meta->rnear) ? (float)(a.meta->rnear * a.meta->rnear) : INFINITY;
-
-    Producer pr;
-    if (tid == 0) {
-        const TreeMeta* m = a.meta;
-        pr.phase = 0;
-        pr.e = a.off[b];
-        pr.e_end = a.off[b + 1];
-        pr.e_off = 0;
-        pr.near_cand = 0;
-        pr.lc = m->lc;
-        pr.cell_side = m->cell_side;
-        pr.rnear = m->rnear;
-        pr.rnear2 = isfinite(m->rnear) ? m->rnear * m->rnear : INFINITY;
-        for (int d = 0; d < 3; ++d) pr.cell_lo[d] = m->cube_lo[d];
-        const double blo[3] = {(double)ti0, (double)tj0, (double)tk0};
-        const double bhi[3] = {(double)(ti0 + kBX * P - 1), (double)(tj0 + kBY - 1), (double)(tk0 + kBZ - 1)};
-        const int ncell = 1 << pr.lc;
-        bool ok = a.n > 0;
-        for (int d = 0; d < 3; ++d) {
-            pr.box_lo[d] = blo[d];
-            pr.box_hi[d] = bhi[d];
-            double lo = floor((blo[d] - pr.rnear - pr.cell_lo[d]) / pr.cell_side);
-            double hi = floor((bhi[d] + pr.rnear - pr.cell_lo[d]) / pr.cell_side);
-            pr.c0[d] = (int)fmax(lo, 0.0);
-            pr.c1[d] = (int)fmin(hi, (double)(ncell - 1));
-            ok = ok && pr.c0[d] <= pr.c1[d];
-        }
-        pr.near_ok = ok;
-        pr.cx = pr.c0[0] - 1;
-        pr.cy = pr.c0[1];
-        pr.cz = pr.c0[2];
-        pr.cell_pos = pr.cell_end = 0;
-        mbar_init(&bar[0], 1);
-        mbar_init(&bar[1], 1);
-        mbar_fence_init();
-    }
+    Cursor cur;
     __syncthreads();
     if (tid == 0) {
-        for (int st = 0; st < 2; ++st) {
-            int kind;
-            int c = (pr.phase < 2) ? produce_tile<SM>(pr, a, sgeo + st * kT, slj + st * kT * SM, &bar[st], kind) : 0;
-            s_cnt[st] = c;
-            s_kind[st] = kind;
-        }
+        cur.e = a.near_off[b];
+        cur.e_end = a.near_off[b + 1];
+        cur.off = 0;
+        cur.produced = 0;
+        cur.done = false;
+        for (int s = 0; s < kStages; ++s) cur.last_phase[s] = -1;
+        ring_init(r, Sh::NW);
     }
     __syncthreads();
-    for (int t = 0;; ++t) {
-        const int st = t & 1;
-        const int cnt = s_cnt[st];
-        if (cnt == 0) break;
-        const bool near = s_kind[st] == 1;
-        bool ok = mbar_wait_bounded(&bar[st], (t >> 1) & 1, a.wlim);
-        if (__syncthreads_or(!ok)) {
-            if (tid == 0) {
-                report_error(a.err, DEV_TIMEOUT, WHERE_TREE_EVAL);
-                for (int u2 = t; u2 < t + 2; ++u2)
-                    if (s_cnt[u2 & 1] > 0) mbar_wait_bounded(&bar[u2 & 1], (u2 >> 1) & 1, a.wlim);
-            }
-            return;
-        }
-        if (tid < cnt) {
-            const Geo A = sgeo[st * kT + tid];
-            GeoF c;
-            split_ff(A.x - (double)ti0, c.xh, c.xl);
-            split_ff(A.y - (double)tj0, c.yh, c.yl);
-            split_ff(A.z - (double)tk0, c.zh, c.zl);
-            c.q = (float)A.q;
-            c.pad = 0.f;
-            conv[tid] = c;
-        }
-        __syncthreads();
-        if (!near) {
-            float p1[P], pk[P];
+    const bool ok = run_ring<SM, true, Sh::NW>(r, cur, a.near_ent, a.srcf, a.ljs, a, [&](int slot, int cnt) {
+        const SrcF* Sx = r.src[slot];
+        const LJf* L = r.lj[slot];
+        float psc[P], psh[P], plj[P][SM];
 #pragma unroll
-            for (int p = 0; p < P; ++p) p1[p] = pk[p] = 0.f;
-            for (int s0 = 0; s0 < cnt; ++s0) {
-                const float4 g0 = *reinterpret_cast<const float4*>(&conv[s0].xh);
-                const float4 g1 = *reinterpret_cast<const float4*>(&conv[s0].xl);
-                const float dy = (fy - g0.y) - g1.y;
-                const float dz = (fz - g0.z) - g1.z;
-                const float dyz2 = fmaf(dy, dy, dz * dz);
-                const float bx = fx0 - g0.x;
+        for (int p = 0; p < P; ++p) {
+            psc[p] = psh[p] = 0.f;
 #pragma unroll
-                for (int p = 0; p < P; ++p) {
-                    const float dx = (bx + (float)p) - g1.x;
-                    const float d2 = fmaf(dx, dx, dyz2);
-                    const float rr = rsqrt_approx(d2);
-                    const float ri = d2 > 0.f ? rr : 0.f;
-                    const float qr = g0.w * ri;
-                    p1[p] += qr;
-                    if (DH) pk[p] = fmaf(qr, ex2_approx(kap2 * (d2 * ri)), pk[p]);
-                }
-            }
+            for (int s = 0; s < SM; ++s) plj[p][s] = 0.f;
+        }
+        for (int s0 = 0; s0 < cnt; ++s0) {
+            const float4 g0 = *reinterpret_cast<const float4*>(&Sx[s0].xh);
+            const float4 g1 = *reinterpret_cast<const float4*>(&Sx[s0].xl);
+            const float dy = (fy - g0.y) - g1.y;
+            const float dz = (fz - g0.z) - g1.z;
+            const float dyz2 = fmaf(dy, dy, dz * dz);
 #pragma unroll
             for (int p = 0; p < P; ++p) {
-                ff_add(f1h[p], f1l[p], p1[p]);
-                if (DH) ff_add(fkh[p], fkl[p], pk[p]);
-            }
-        } else {
-            const LJf* L = slj + st * kT * SM;
-            const float rn2 = s_rn2;
-            float psc[P], psh[P], plj[P][SM];
-#pragma unroll
-            for (int p = 0; p < P; ++p) {
-                psc[p] = psh[p] = 0.f;
-#pragma unroll
-                for (int s = 0; s < SM; ++s) plj[p][s] = 0.f;
-            }
-            for (int s0 = 0; s0 < cnt; ++s0) {
-                const float4 g0 = *reinterpret_cast<const float4*>(&conv[s0].xh);
-                const float4 g1 = *reinterpret_cast<const float4*>(&conv[s0].xl);
-                const float dy = (fy - g0.y) - g1.y;
-                const float dz = (fz - g0.z) - g1.z;
-                const float dyz2 = fmaf(dy, dy, dz * dz);
-                const float bx = fx0 - g0.x;
-#pragma unroll
-                for (int p = 0; p < P; ++p) {
-                    const float dx = (bx + (float)p) - g1.x;
-                    const float d2 = fmaf(dx, dx, dyz2);
-                    if (d2 >= rn2) continue;
-                    if (d2 < rs2) {
-                        if (d2 > 0.f) {
-                            const float ri = rsqrt_approx(d2);
-                            const float qr = g0.w * ri;
-                            const float x = d2 * ri * xs;
-                            if (DC) psc[p] = fmaf(qr, erfcf(x), psc[p]);
-                            if (DH) psh[p] = fmaf(qr, __expf(-x * x) * (erfcxf(x - aa_) + erfcxf(x + aa_)), psh[p]);
-                        } else {
-                            hit |= 1u << p;
-                            if (DC) psc[p] -= g0.w * c0h;
-                            if (DH) psh[p] -= g0.w * h0h;
-                        }
-                    }
-                    if (DU) {
-                        const float r2i = rcp_approx(d2);
-                        const float r6 = r2i * r2i * r2i;
-#pragma unroll
-                        for (int s = 0; s < SM; ++s) {
-                            const float4 l = *reinterpret_cast<const float4*>(&L[s0 * SM + s]);
-                            if (d2 < l.z) plj[p][s] = fmaf(r6, fmaf(l.x, r6, -l.y), plj[p][s]);
-                        }
+                const float dx = (gx[p] - g0.x) - g1.x;
+                const float d2 = fmaf(dx, dx, dyz2);
+                if (d2 >= rn2) continue;
+                if (d2 < rs2) {
+                    if (d2 > 0.f) {
+                        const float ri = rsqrt_approx(d2);
+                        const float qr = g0.w * ri;
+                        const float x = d2 * ri * xs;
+                        if (DC) psc[p] = fmaf(qr, erfcf(x), psc[p]);
+                        if (DH) psh[p] = fmaf(qr, __expf(-x * x) * (erfcxf(x - aa_) + erfcxf(x + aa_)), psh[p]);
+                    } else {
+                        hit |= 1u << p;
+                        if (DC) psc[p] -= g0.w * c0h;
+                        if (DH) psh[p] -= g0.w * h0h;
                     }
                 }
-            }
-#pragma unroll
-            for (int p = 0; p < P; ++p) {
-                if (DC) ff_add(sch[p], scl[p], psc[p]);
-                if (DH) ff_add(shh[p], shl[p], psh[p]);
                 if (DU) {
+                    const float r2i = rcp_approx(d2);
+                    const float r6 = r2i * r2i * r2i;
 #pragma unroll
-                    for (int s = 0; s < SM; ++s) ff_add(ljh[p][s], ljl[p][s], plj[p][s]);
+                    for (int s = 0; s < SM; ++s) {
+                        const float4 l = *reinterpret_cast<const float4*>(&L[s0 * SM + s]);
+                        if (d2 < l.z) plj[p][s] = fmaf(r6, fmaf(l.x, r6, -l.y), plj[p][s]);
+                    }
                 }
             }
         }
-        __syncthreads();
-        if (tid == 0) {
-            int kind = 2;
-            int c = (pr.phase < 2) ? produce_tile<SM>(pr, a, sgeo + st * kT, slj + st * kT * SM, &bar[st], kind) : 0;
-            s_cnt[st] = c;
-            s_kind[st] = kind;
+#pragma unroll
+        for (int p = 0; p < P; ++p) {
+            if (DC) ff_add(sch[p], scl[p], psc[p]);
+            if (DH) ff_add(shh[p], shl[p], psh[p]);
+            if (DU) {
+#pragma unroll
+                for (int s = 0; s < SM; ++s) ff_add(ljh[p][s], ljl[p][s], plj[p][s]);
+            }
         }
-        __syncthreads();
-    }
-    if (tid == 0) atomicAdd(&a.meta->near_pairs, pr.near_cand * (unsigned long long)(NT * P));
+    });
+    if (!ok) return;
 
     const GridD& g = a.g;
     if (j >= g.ny || k >= g.nz || i0 >= g.nx) return;
@@ -950,10 +1109,12 @@ __global__ void __launch_bounds__(kBX* kBY* kBZ) k_eval32(EvalArgs a) {
     const Phys& ph = a.ph;
     const double cu0 = ph.k_e * ih, cc0 = -ph.beta * ph.k_e * ih, ch0 = -ph.beta * ph.k_e / (2.0 * ph.eps_r) * ih;
     double F1[P], FK[P], SC[P], SH[P];
+    const float4* fr = a.far + row;
 #pragma unroll
     for (int p = 0; p < P; ++p) {
-        F1[p] = (double)f1h[p] + (double)f1l[p];
-        FK[p] = (double)fkh[p] + (double)fkl[p];
+        const float4 f = (i0 + p < g.nx) ? fr[i0 + p] : make_float4(0.f, 0.f, 0.f, 0.f);
+        F1[p] = (double)f.x + (double)f.y;
+        FK[p] = (double)f.z + (double)f.w;
         SC[p] = (double)sch[p] + (double)scl[p];
         SH[p] = (double)shh[p] + (double)shl[p];
     }
@@ -992,67 +1153,196 @@ __global__ void __launch_bounds__(kBX* kBY* kBZ) k_eval32(EvalArgs a) {
     }
 }
 
-template <int SM>
-cudaError_t launch_eval(const EvalArgs& a, int nb, cudaStream_t st) {
-    const size_t sm = 2 * kT * sizeof(Geo) + 2 * kT * SM * sizeof(LJf) + kT * sizeof(GeoF) + 2 * sizeof(uint64_t);
-    const bool du = a.o.u != nullptr, dh = a.o.h != nullptr;
-    auto go = [&](auto kern) {
-        cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-        kern<<<nb, kBX * kBY * kBZ, sm, st>>>(a);
+// ---- per-solute kernels: one CTA per target batch
+template <int NXB, int NYB, int NZB, int PF, bool DH>
+__global__ void __launch_bounds__(FarShape<NXB, NYB, NZB, PF>::NT) k_far32(EvalArgs a) {
+    __shared__ Ring<1, false> r;
+    if (threadIdx.x == 0) r.inited = 0;
+    if (a.meta->overflow) return;  // incomplete lists: the host grows them and runs again
+    far_body<NXB, NYB, NZB, PF, DH>(a, blockIdx.x, r);
+}
+
+template <int NXB, int NYB, int NZB, int SM, bool DU, bool DH>
+__global__ void __launch_bounds__(NearShape<NXB, NYB, NZB>::NT) k_near32(EvalArgs a) {
+    __shared__ Ring<SM, true> r;
+    if (threadIdx.x == 0) r.inited = 0;
+    if (a.meta->overflow) return;
+    near_body<NXB, NYB, NZB, SM, DU, DH>(a, blockIdx.x, r);
+}
+
+// ---- persistent kernels over the (solute, batch) items of many solutes
+struct BatchEval {
+    const EvalArgs* args;   // [count]
+    const int* item_off;    // [count + 1] prefix of batch counts
+    int count, total;
+    int* queue;             // work counter, zeroed before the launch
+};
+
+__device__ __forceinline__ int find_solute(const BatchEval& be, int it) {
+    int lo = 0, hi = be.count - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (be.item_off[mid] <= it) lo = mid; else hi = mid - 1;
+    }
+    return lo;
+}
+
+template <int NXB, int NYB, int NZB, int PF, bool DH>
+__global__ void __launch_bounds__(FarShape<NXB, NYB, NZB, PF>::NT) k_far32_batched(BatchEval be) {
+    __shared__ Ring<1, false> r;
+    __shared__ int s_item;
+    __shared__ EvalArgs sa;
+    if (threadIdx.x == 0) r.inited = 0;
+    for (;;) {
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            s_item = atomicAdd(be.queue, 1);
+            if (s_item < be.total) sa = be.args[find_solute(be, s_item)];
+        }
+        __syncthreads();
+        const int it = s_item;
+        if (it >= be.total) break;
+        if (sa.meta->overflow) continue;
+        const int sid = find_solute(be, it);
+        far_body<NXB, NYB, NZB, PF, DH>(sa, it - be.item_off[sid], r);
+    }
+}
+
+template <int NXB, int NYB, int NZB, int SM, bool DU, bool DH>
+__global__ void __launch_bounds__(NearShape<NXB, NYB, NZB>::NT) k_near32_batched(BatchEval be) {
+    __shared__ Ring<SM, true> r;
+    __shared__ int s_item;
+    __shared__ EvalArgs sa;
+    if (threadIdx.x == 0) r.inited = 0;
+    for (;;) {
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            s_item = atomicAdd(be.queue, 1);
+            if (s_item < be.total) sa = be.args[find_solute(be, s_item)];
+        }
+        __syncthreads();
+        const int it = s_item;
+        if (it >= be.total) break;
+        if (sa.meta->overflow) continue;
+        const int sid = find_solute(be, it);
+        near_body<NXB, NYB, NZB, SM, DU, DH>(sa, it - be.item_off[sid], r);
+    }
+}
+
+// ---- dispatch over (shape, sites, outputs)
+template <int V>
+struct VShape {
+    static constexpr ShapeDesc d = shape_of(V);
+    static constexpr int NX = d.nx, NY = d.ny, NZ = d.nz, PF = d.pf;
+    static constexpr int FT = FarShape<NX, NY, NZ, PF>::NT, NTN = NearShape<NX, NY, NZ>::NT;
+};
+
+template <int V, int SM, bool DU, bool DH>
+struct Kern {
+    using S = VShape<V>;
+    static void far(const EvalArgs& a, int nb, cudaStream_t st) {
+        k_far32<S::NX, S::NY, S::NZ, S::PF, DH><<<nb, S::FT, 0, st>>>(a);
+    }
+    static void near(const EvalArgs& a, int nb, cudaStream_t st) {
+        k_near32<S::NX, S::NY, S::NZ, SM, DU, DH><<<nb, S::NTN, 0, st>>>(a);
+    }
+    static void far_b(const BatchEval& be, int grid, cudaStream_t st) {
+        k_far32_batched<S::NX, S::NY, S::NZ, S::PF, DH><<<grid, S::FT, 0, st>>>(be);
+    }
+    static void near_b(const BatchEval& be, int grid, cudaStream_t st) {
+        k_near32_batched<S::NX, S::NY, S::NZ, SM, DU, DH><<<grid, S::NTN, 0, st>>>(be);
+    }
+    static int occ_far() {
+        int b = 0;
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_far32_batched<S::NX, S::NY, S::NZ, S::PF, DH>, S::FT, 0);
+        return b;
+    }
+    static int occ_near() {
+        int b = 0;
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_near32_batched<S::NX, S::NY, S::NZ, SM, DU, DH>, S::NTN,
+                                                      0);
+        return b;
+    }
+};
+
+// op: 0 per-solute far+near, 1 batched far+near (grid from occupancy)
+template <int V, int SM>
+cudaError_t dispatch_v(int op, bool du, bool dh, const EvalArgs* a, int nb, const BatchEval* be, int sms,
+                       cudaStream_t st) {
+    auto go = [&](auto k) {
+        using K = decltype(k);
+        if (op == 0) {
+            K::far(*a, nb, st);
+            K::near(*a, nb, st);
+        } else {
+            K::far_b(*be, sms * std::max(1, K::occ_far()), st);
+            BatchEval b2 = *be;
+            b2.queue = be->queue + 1;
+            K::near_b(b2, sms * std::max(1, K::occ_near()), st);
+        }
     };
-    if (du && dh) go(k_eval32<SM, true, true>);
-    else if (du) go(k_eval32<SM, true, false>);
-    else if (dh) go(k_eval32<SM, false, true>);
-    else go(k_eval32<SM, false, false>);
+    if (du && dh) go(Kern<V, SM, true, true>{});
+    else if (du) go(Kern<V, SM, true, false>{});
+    else if (dh) go(Kern<V, SM, false, true>{});
+    else go(Kern<V, SM, false, false>{});
     return cudaGetLastError();
+}
+
+template <int SM>
+cudaError_t dispatch_sm(int v, int op, bool du, bool dh, const EvalArgs* a, int nb, const BatchEval* be, int sms,
+                        cudaStream_t st) {
+    switch (v) {
+        case 1: return dispatch_v<1, SM>(op, du, dh, a, nb, be, sms, st);
+        case 2: return dispatch_v<2, SM>(op, du, dh, a, nb, be, sms, st);
+        default: return dispatch_v<0, SM>(op, du, dh, a, nb, be, sms, st);
+    }
+}
+
+cudaError_t dispatch(int smax, int v, int op, bool du, bool dh, const EvalArgs* a, int nb, const BatchEval* be,
+                     int sms, cudaStream_t st) {
+    switch (smax) {
+        case 2: return dispatch_sm<2>(v, op, du, dh, a, nb, be, sms, st);
+        case 4: return dispatch_sm<4>(v, op, du, dh, a, nb, be, sms, st);
+        default: return dispatch_sm<8>(v, op, du, dh, a, nb, be, sms, st);
+    }
 }
 
 }  // namespace
 
 // ------------------------------------------------------------- state
+struct BatchCache;
+
 struct TreeState {
     int64_t cap_n = 0;
-    int cap_nodes = 0, cap_prox = 0, cap_items = 0, cap_far = 0, cap_nb = 0;
+    int cap_nodes = 0, cap_prox = 0, cap_items = 0, cap_nb = 0;
+    int cap_far = 0, cap_near = 0;
     int deg = 0, smax = 0;
     uint32_t *code = nullptr, *idx = nullptr, *code2 = nullptr, *idx2 = nullptr;
     Node* nodes = nullptr;
     int* items = nullptr;
     int* prox_nodes = nullptr;
     double* part = nullptr;
-    Geo* src = nullptr;
+    Geo* src = nullptr;    // sorted atoms + proxies, FP64 grid units (upward pass)
+    SrcF* srcf = nullptr;  // the same as float-float (evaluation kernels)
     LJf* ljs = nullptr;
-    int* cnt = nullptr;
-    int* off = nullptr;
-    int2* ent = nullptr;
+    float4* far = nullptr; // far-field sums per grid point
+    int64_t cap_far_pts = 0;
+    int *far_cnt = nullptr, *far_off = nullptr, *near_cnt = nullptr, *near_off = nullptr;
+    int2 *far_ent = nullptr, *near_ent = nullptr;
     int* cell_start = nullptr;
     TreeMeta* meta = nullptr;
     TreeMeta* h_meta = nullptr;  // pinned copy, filled at the end of tree_eval
     int nb = 0, nbx = 0, nby = 0, nbz = 0;
+    int variant = 0, leaf = 64;  // launch shape and leaf size in use
+    int max_nodes = 0, max_prox = 0, max_items = 0;
     int launches = 0;
     bool prepared = false;
+    std::string tuned_key;       // problem class the current (variant, leaf) was tuned for
+    BatchCache* bc = nullptr;
 };
 
 namespace {
 constexpr int kMaxCells = (1 << 21) + 1;  // 8^7 + 1
-
-void free_state(TreeState* s) {
-    cudaFree(s->code);
-    cudaFree(s->idx);
-    cudaFree(s->code2);
-    cudaFree(s->idx2);
-    cudaFree(s->nodes);
-    cudaFree(s->items);
-    cudaFree(s->prox_nodes);
-    cudaFree(s->part);
-    cudaFree(s->src);
-    cudaFree(s->ljs);
-    cudaFree(s->cnt);
-    cudaFree(s->off);
-    cudaFree(s->ent);
-    cudaFree(s->cell_start);
-    cudaFree(s->meta);
-    cudaFreeHost(s->h_meta);
-}
 
 rism_status cuda_err(std::string& err, cudaError_t e, const char* what) {
     err = std::string(what) + ": " + cudaGetErrorString(e);
@@ -1065,101 +1355,126 @@ cudaError_t regrow(T*& p, size_t count) {
     p = nullptr;
     return cudaMalloc(&p, (count > 0 ? count : 1) * sizeof(T));
 }
-}  // namespace
 
-TreeState* tree_create() { return new TreeState(); }
-
-void tree_destroy(TreeState* ts) {
-    if (!ts) return;
-    free_state(ts);
-    delete ts;
+int sm_count() {
+    static int n = 0;
+    if (n == 0) {
+        int dev = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
+        if (n <= 0) n = 1;
+    }
+    return n;
 }
 
-// Enqueue a7..a9: codes, sort, octree, boxes, sorted sources, cells, upward
-// pass and interaction lists.  Sizes that depend on the atoms are read by the
-// kernels from the device meta block; nothing here waits for the GPU.
-rism_status tree_prepare(TreeState* s, const DevTables& t, const GridD& g, const Phys& ph, const rism_options& o,
-                         cudaStream_t st, std::string& err) {
+// Host allocations for one solute (never inside a stream capture).
+rism_status tree_reserve(TreeState* s, const DevTables& t, const GridD& g, const rism_options& o, std::string& err) {
     cudaError_t e = cudaSuccess;
     const int n = (int)t.n;
     const int deg = o.degree, np = deg + 1, P3 = np * np * np;
-    s->nbx = (g.nx + kBX * kP - 1) / (kBX * kP);
-    s->nby = (g.ny + kBY - 1) / kBY;
-    s->nbz = (g.nz + kBZ - 1) / kBZ;
+    const ShapeDesc sd = shape_of(s->variant);
+    s->nbx = (g.nx + sd.nx - 1) / sd.nx;
+    s->nby = (g.ny + sd.ny - 1) / sd.ny;
+    s->nbz = (g.nz + sd.nz - 1) / sd.nz;
     s->nb = s->nbx * s->nby * s->nbz;
     // Capacity bounds.  Internal nodes hold > leaf atoms and are disjoint per level, so there are at most
-    // n/(leaf+1) per level and 10 levels; each has at most 8 children.  Proxy sets hold > P3 atoms, so at most
-    // n/(P3+1) per level.  Upward items are chunks of kChunk atoms of proxied nodes.
-    const int max_nodes = (int)(90LL * n / (o.leaf + 1)) + 16;
-    const int max_prox = 10 * n / (P3 + 1) + 2;
-    const int max_items = 10 * (n / kChunk + 1) + 2;
+    // n/(leaf+1) per level over 10 levels, each with at most 8 children.  Proxy sets hold > P3 atoms, so at
+    // most n/(P3+1) per level.  Upward items are chunks of kChunk atoms of proxied nodes.
+    s->max_nodes = (int)(90LL * n / (s->leaf + 1)) + 16;
+    s->max_prox = 10 * n / (P3 + 1) + 2;
+    s->max_items = 10 * (n / kChunk + 1) + 2;
     if (!s->meta) {
         if ((e = cudaMalloc(&s->meta, sizeof(TreeMeta))) != cudaSuccess) return cuda_err(err, e, "tree meta");
         if ((e = cudaMallocHost(&s->h_meta, sizeof(TreeMeta))) != cudaSuccess) return cuda_err(err, e, "tree meta");
         if ((e = regrow(s->cell_start, (size_t)kMaxCells)) != cudaSuccess) return cuda_err(err, e, "cell table");
+        std::memset(s->h_meta, 0, sizeof(TreeMeta));
     }
-    if (n > s->cap_n || t.smax != s->smax || max_nodes > s->cap_nodes || deg != s->deg) {
+    if (n > s->cap_n || t.smax != s->smax || s->max_nodes > s->cap_nodes || deg != s->deg) {
         const size_t nn = n > 0 ? (size_t)n : 1;
         if ((e = regrow(s->code, nn)) || (e = regrow(s->idx, nn)) || (e = regrow(s->code2, nn)) ||
-            (e = regrow(s->idx2, nn)) || (e = regrow(s->nodes, (size_t)max_nodes)) ||
-            (e = regrow(s->items, 2 * (size_t)max_items)) || (e = regrow(s->prox_nodes, (size_t)max_prox)) ||
-            (e = regrow(s->part, (size_t)max_items * P3)) || (e = regrow(s->src, nn + (size_t)max_prox * P3)) ||
-            (e = regrow(s->ljs, nn * t.smax)))
+            (e = regrow(s->idx2, nn)) || (e = regrow(s->nodes, (size_t)s->max_nodes)) ||
+            (e = regrow(s->items, 2 * (size_t)s->max_items)) || (e = regrow(s->prox_nodes, (size_t)s->max_prox)) ||
+            (e = regrow(s->part, (size_t)s->max_items * P3)) || (e = regrow(s->src, nn + (size_t)s->max_prox * P3)) ||
+            (e = regrow(s->srcf, nn + (size_t)s->max_prox * P3)) || (e = regrow(s->ljs, nn * t.smax)))
             return cuda_err(err, e, "tree buffers");
         s->cap_n = (int64_t)nn;
-        s->cap_nodes = max_nodes;
-        s->cap_prox = max_prox;
-        s->cap_items = max_items;
+        s->cap_nodes = s->max_nodes;
+        s->cap_prox = s->max_prox;
+        s->cap_items = s->max_items;
         s->smax = t.smax;
         s->deg = deg;
     }
+    const int64_t M = (int64_t)g.nx * g.ny * g.nz;
+    if (M > s->cap_far_pts) {
+        if ((e = regrow(s->far, (size_t)M))) return cuda_err(err, e, "far-field buffer");
+        s->cap_far_pts = M;
+    }
     if (s->nb + 1 > s->cap_nb) {
-        if ((e = regrow(s->cnt, (size_t)s->nb + 1)) || (e = regrow(s->off, (size_t)s->nb + 1)))
+        if ((e = regrow(s->far_cnt, (size_t)s->nb + 1)) || (e = regrow(s->far_off, (size_t)s->nb + 1)) ||
+            (e = regrow(s->near_cnt, (size_t)s->nb + 1)) || (e = regrow(s->near_off, (size_t)s->nb + 1)))
             return cuda_err(err, e, "list offsets");
         s->cap_nb = s->nb + 1;
     }
-    if (s->cap_far < s->nb * 16 + 1024) {
-        const int want = s->nb * 16 + 1024;
-        if ((e = regrow(s->ent, (size_t)want))) return cuda_err(err, e, "far list");
+    const int want = s->nb * 64 + 1024;
+    if (s->cap_far < want) {
+        if ((e = regrow(s->far_ent, (size_t)want))) return cuda_err(err, e, "far list");
         s->cap_far = want;
     }
+    if (s->cap_near < want) {
+        if ((e = regrow(s->near_ent, (size_t)want))) return cuda_err(err, e, "near list");
+        s->cap_near = want;
+    }
+    return RISM_OK;
+}
+
+// Kernel launches of a7..a9 for one solute (no allocation, no host wait:
+// safe inside a stream capture).
+rism_status tree_enqueue(TreeState* s, const DevTables& t, const GridD& g, const Phys& ph, const rism_options& o,
+                         cudaStream_t st, std::string& err) {
+    const int n = (int)t.n;
+    const int deg = o.degree, np = deg + 1, P3 = np * np * np;
+    const ShapeDesc sd = shape_of(s->variant);
     s->launches = 0;
     k_reset_meta<<<1, 1, 0, st>>>(s->meta);
     ++s->launches;
     if (n > 0) {
-        k_bbox_codes<<<1, kSortThreads, 0, st>>>(t.geoU, t.ljd, n, ph.S, t.smax, ph.rs, g.h, s->meta, s->code, s->idx);
-        BuildArgs ba{n, o.leaf, P3, max_nodes, max_prox, max_items};
+        k_bbox_codes<<<1, kSortThreads, 0, st>>>(t.geo, t.ljd, n, ph.S, t.smax, ph.rs, g, s->meta, s->code, s->idx);
+        BuildArgs ba{n, s->leaf, P3, s->max_nodes, s->max_prox, s->max_items};
         const size_t shb = (256 * 32 + 64) * sizeof(int);
         cudaFuncSetAttribute(k_sort_build, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shb);
         k_sort_build<<<1, kSortThreads, shb, st>>>(ba, s->code, s->idx, s->code2, s->idx2, s->nodes, s->items,
                                                    s->prox_nodes, s->meta);
-        k_node_boxes<<<152, 256, 0, st>>>(s->nodes, s->meta, s->idx, t.geoU);
-        k_gather<<<(n + 255) / 256, 256, 0, st>>>(n, t.smax, s->idx, t.geoU, t.ljf, s->src, s->ljs);
+        k_node_boxes<<<sm_count(), 256, 0, st>>>(s->nodes, s->meta, s->idx, t.geo, g);
+        k_gather<<<(n + 255) / 256, 256, 0, st>>>(n, t.smax, s->idx, t.geo, g, t.ljf, s->src, s->srcf, s->ljs);
         k_cells<<<1024, 256, 0, st>>>(n, s->meta, s->code, s->cell_start);
         const size_t shu = (kChunk * 3 * np + kChunk) * sizeof(double);
         cudaFuncSetAttribute(k_upward, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shu);
-        k_upward<<<4 * 152, 256, shu, st>>>(deg, s->meta, s->nodes, s->prox_nodes, s->items, s->src, s->part);
-        k_proxy_reduce<<<152, 256, 0, st>>>(deg, n, s->meta, s->nodes, s->prox_nodes, s->items, s->part, s->src);
+        k_upward<<<4 * sm_count(), 256, shu, st>>>(deg, s->meta, s->nodes, s->prox_nodes, s->items, s->src, s->part);
+        k_proxy_reduce<<<sm_count(), 256, 0, st>>>(deg, n, s->meta, s->nodes, s->prox_nodes, s->items, s->part,
+                                                   s->src, s->srcf);
         s->launches += 7;
     }
-    ListArgs la{s->nbx, s->nby, s->nbz, kBX * kP, kBY, kBZ, o.theta, n, P3, s->cap_far};
-    k_lists<false><<<(s->nb + 127) / 128, 128, 0, st>>>(la, s->nodes, s->off, s->ent, s->cnt, s->meta);
-    k_scan<<<1, 1024, 0, st>>>(s->nb, s->cnt, s->off, s->cap_far, s->meta);
-    k_lists<true><<<(s->nb + 127) / 128, 128, 0, st>>>(la, s->nodes, s->off, s->ent, s->cnt, s->meta);
-    s->launches += 3;
-    if ((e = cudaGetLastError()) != cudaSuccess) return cuda_err(err, e, "tree build");
+    ListArgs fa{s->nbx, s->nby, s->nbz, sd.nx, sd.ny, sd.nz, o.theta, n, P3, s->cap_far};
+    ListArgs na = fa;
+    na.cap = s->cap_near;
+    const int lgrid = (s->nb + kListWarps - 1) / kListWarps;
+    k_far_lists<false><<<lgrid, 32 * kListWarps, 0, st>>>(fa, s->nodes, s->far_off, s->far_ent, s->far_cnt, s->meta);
+    k_scan<<<1, 1024, 0, st>>>(s->nb, s->far_cnt, s->far_off, s->cap_far, s->meta, 0);
+    k_far_lists<true><<<lgrid, 32 * kListWarps, 0, st>>>(fa, s->nodes, s->far_off, s->far_ent, s->far_cnt, s->meta);
+    k_near_lists<false><<<lgrid, 32 * kListWarps, 0, st>>>(na, s->meta, s->cell_start, s->near_off, s->near_ent,
+                                                           s->near_cnt, s->meta);
+    k_scan<<<1, 1024, 0, st>>>(s->nb, s->near_cnt, s->near_off, s->cap_near, s->meta, 1);
+    k_near_lists<true><<<lgrid, 32 * kListWarps, 0, st>>>(na, s->meta, s->cell_start, s->near_off, s->near_ent,
+                                                          s->near_cnt, s->meta);
+    s->launches += 6;
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_err(err, e, "tree build");
     s->prepared = true;
     return RISM_OK;
 }
 
-// Enqueue a10 + a11: the fused far/near evaluation and epilogue, then a copy
-// of the meta block (counts, overflow flag) to pinned memory for tree_post.
-rism_status tree_eval(TreeState* s, const DevTables& t, const GridD& g, const Phys& ph, const rism_options& o,
-                      Outputs out, cudaStream_t st, std::string& err, rism_info& info) {
-    if (!s->prepared) {
-        err = "tree not prepared";
-        return RISM_E_STATE;
-    }
+EvalArgs make_args(TreeState* s, const DevTables& t, const GridD& g, const Phys& ph, const rism_options& o,
+                   Outputs out) {
     EvalArgs a;
     a.g = g;
     a.ph = ph;
@@ -1167,46 +1482,240 @@ rism_status tree_eval(TreeState* s, const DevTables& t, const GridD& g, const Ph
     a.nby = s->nby;
     a.nbz = s->nbz;
     a.n = (int)t.n;
-    a.src = s->src;
+    a.srcf = s->srcf;
     a.ljs = s->ljs;
-    a.off = s->off;
-    a.ent = s->ent;
-    a.cell_start = s->cell_start;
+    a.far_off = s->far_off;
+    a.far_ent = s->far_ent;
+    a.near_off = s->near_off;
+    a.near_ent = s->near_ent;
+    a.far = s->far;
     a.o = out;
     a.err = t.err;
     a.meta = s->meta;
     a.wlim = o.wait_limit;
-    cudaError_t e;
-    switch (t.smax) {
-        case 2: e = launch_eval<2>(a, s->nb, st); break;
-        case 4: e = launch_eval<4>(a, s->nb, st); break;
-        default: e = launch_eval<8>(a, s->nb, st); break;
+    return a;
+}
+
+// ---- autotuner: problem class -> (shape variant, leaf size)
+std::mutex g_tune_mu;
+std::map<std::string, std::pair<int, int>> g_tune;
+bool g_tune_loaded = false;
+
+std::string tune_path() {
+    const char* p = std::getenv("RISM_AUTOTUNE_CACHE");
+    return p ? std::string(p) : std::string();
+}
+
+void tune_load() {
+    if (g_tune_loaded) return;
+    g_tune_loaded = true;
+    const std::string path = tune_path();
+    if (path.empty()) return;
+    FILE* f = std::fopen(path.c_str(), "r");
+    if (!f) return;
+    char key[512];
+    int v, l;
+    // one entry per line: "<key>" variant leaf
+    while (std::fscanf(f, " \"%511[^\"]\" %d %d", key, &v, &l) == 3) g_tune[key] = {v, l};
+    std::fclose(f);
+}
+
+void tune_save() {
+    const std::string path = tune_path();
+    if (path.empty()) return;
+    FILE* f = std::fopen(path.c_str(), "w");
+    if (!f) return;
+    for (auto& kv : g_tune) std::fprintf(f, "\"%s\" %d %d\n", kv.first.c_str(), kv.second.first, kv.second.second);
+    std::fclose(f);
+}
+
+std::string problem_class(const DevTables& t, const GridD& g, const Phys& ph, const rism_options& o) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceProp p;
+    cudaGetDeviceProperties(&p, dev);
+    auto lg = [](double v) { return (int)std::lround(std::log2(v > 1 ? v : 1)); };
+    char buf[400];
+    std::snprintf(buf, sizeof buf, "%s|sm%d|S%d|n2^%d|m2^%d|p%d|th%d|lj%d|k%d", p.name, p.multiProcessorCount,
+                  t.smax, lg((double)t.n), lg((double)g.nx * g.ny * g.nz), o.degree, (int)std::lround(o.theta * 100),
+                  o.lj_mode, ph.kappa > 0.0);
+    for (char* c = buf; *c; ++c)
+        if (*c == '"') *c = '\'';
+    return buf;
+}
+
+}  // namespace
+
+TreeState* tree_create() { return new TreeState(); }
+
+struct BatchCache {
+    std::vector<unsigned char> sig;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    cudaStream_t cs = nullptr;  // private stream the sequence is captured on (the caller's may be the legacy one)
+    EvalArgs* d_args = nullptr;
+    int* d_off = nullptr;
+    int* d_queue = nullptr;
+    int cap = 0;
+    ~BatchCache() {
+        if (exec) cudaGraphExecDestroy(exec);
+        if (graph) cudaGraphDestroy(graph);
+        if (cs) cudaStreamDestroy(cs);
+        cudaFree(d_args);
+        cudaFree(d_off);
+        cudaFree(d_queue);
     }
+};
+
+void tree_destroy(TreeState* s) {
+    if (!s) return;
+    delete s->bc;
+    cudaFree(s->code);
+    cudaFree(s->idx);
+    cudaFree(s->code2);
+    cudaFree(s->idx2);
+    cudaFree(s->nodes);
+    cudaFree(s->items);
+    cudaFree(s->prox_nodes);
+    cudaFree(s->part);
+    cudaFree(s->src);
+    cudaFree(s->srcf);
+    cudaFree(s->far);
+    cudaFree(s->ljs);
+    cudaFree(s->far_cnt);
+    cudaFree(s->far_off);
+    cudaFree(s->near_cnt);
+    cudaFree(s->near_off);
+    cudaFree(s->far_ent);
+    cudaFree(s->near_ent);
+    cudaFree(s->cell_start);
+    cudaFree(s->meta);
+    cudaFreeHost(s->h_meta);
+    delete s;
+}
+
+rism_status tree_prepare(TreeState* s, const DevTables& t, const GridD& g, const Phys& ph, const rism_options& o,
+                         cudaStream_t st, std::string& err) {
+    if (!o.autotune) s->leaf = o.leaf;
+    rism_status r = tree_reserve(s, t, g, o, err);
+    if (r != RISM_OK) return r;
+    return tree_enqueue(s, t, g, ph, o, st, err);
+}
+
+// Time each (shape, leaf) candidate once (prepare + evaluation, CUDA events)
+// and keep the fastest for this problem class.
+static rism_status tree_autotune(TreeState* s, const DevTables& t, const GridD& g, const Phys& ph,
+                                 const rism_options& o, Outputs out, cudaStream_t st, std::string& err) {
+    const std::string key = problem_class(t, g, ph, o);
+    {
+        std::lock_guard<std::mutex> lock(g_tune_mu);
+        tune_load();
+        auto it = g_tune.find(key);
+        if (it != g_tune.end()) {
+            s->variant = it->second.first;
+            s->leaf = it->second.second;
+            s->tuned_key = key;
+            rism_status r = tree_reserve(s, t, g, o, err);
+            return r != RISM_OK ? r : tree_enqueue(s, t, g, ph, o, st, err);
+        }
+    }
+    cudaEvent_t e0, e1;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    float best = 1e30f;
+    int bv = 0, bl = o.leaf;
+    const int leaves[2] = {o.leaf, o.leaf >= 64 ? o.leaf / 2 : o.leaf * 2};
+    for (int v = 0; v < kNumShapes; ++v)
+        for (int li = 0; li < 2; ++li) {
+            s->variant = v;
+            s->leaf = leaves[li];
+            rism_status r = tree_reserve(s, t, g, o, err);
+            if (r != RISM_OK) return r;
+            cudaEventRecord(e0, st);
+            r = tree_enqueue(s, t, g, ph, o, st, err);
+            if (r != RISM_OK) return r;
+            EvalArgs a = make_args(s, t, g, ph, o, out);
+            dispatch(t.smax, v, 0, out.u != nullptr, out.h != nullptr, &a, s->nb, nullptr, 0, st);
+            cudaEventRecord(e1, st);
+            cudaMemcpyAsync(s->h_meta, s->meta, sizeof(TreeMeta), cudaMemcpyDeviceToHost, st);
+            cudaError_t ce = cudaStreamSynchronize(st);
+            if (ce != cudaSuccess) return cuda_err(err, ce, "autotune");
+            float ms = 0.f;
+            cudaEventElapsedTime(&ms, e0, e1);
+            if (!s->h_meta->overflow && ms < best) {
+                best = ms;
+                bv = v;
+                bl = leaves[li];
+            }
+        }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    s->variant = bv;
+    s->leaf = bl;
+    s->tuned_key = key;
+    {
+        std::lock_guard<std::mutex> lock(g_tune_mu);
+        g_tune[key] = {bv, bl};
+        tune_save();
+    }
+    rism_status r = tree_reserve(s, t, g, o, err);
+    return r != RISM_OK ? r : tree_enqueue(s, t, g, ph, o, st, err);
+}
+
+// Enqueue a10 + a11: far kernel, near kernel + epilogue, then a copy of the
+// meta block (counts, overflow flag) to pinned memory for tree_post.
+rism_status tree_eval(TreeState* s, const DevTables& t, const GridD& g, const Phys& ph, const rism_options& o,
+                      Outputs out, cudaStream_t st, std::string& err, rism_info& info) {
+    if (!s->prepared) {
+        err = "tree not prepared";
+        return RISM_E_STATE;
+    }
+    if (o.autotune && s->tuned_key != problem_class(t, g, ph, o)) {
+        rism_status r = tree_autotune(s, t, g, ph, o, out, st, err);
+        if (r != RISM_OK) return r;
+    }
+    EvalArgs a = make_args(s, t, g, ph, o, out);
+    cudaError_t e = dispatch(t.smax, s->variant, 0, out.u != nullptr, out.h != nullptr, &a, s->nb, nullptr, 0, st);
     if (e != cudaSuccess) return cuda_err(err, e, "tree eval");
     if ((e = cudaMemcpyAsync(s->h_meta, s->meta, sizeof(TreeMeta), cudaMemcpyDeviceToHost, st)) != cudaSuccess)
         return cuda_err(err, e, "tree meta copy");
-    info.launches += s->launches + 1;
-    info.batch[0] = kBX * kP;
-    info.batch[1] = kBY;
-    info.batch[2] = kBZ;
+    info.launches += s->launches + 2;
+    const ShapeDesc sd = shape_of(s->variant);
+    info.batch[0] = sd.nx;
+    info.batch[1] = sd.ny;
+    info.batch[2] = sd.nz;
+    info.kernel_variant = s->variant;
     return RISM_OK;
 }
 
-// After the stream has been synchronised: counters into info; a far-list
+// After the stream has been synchronised: counters into info; a list
 // overflow grows the buffer and asks the caller to run prepare + eval again.
 rism_status tree_post(TreeState* s, rism_info& info, bool& retry, std::string& err) {
     const TreeMeta& m = *s->h_meta;
     retry = false;
     if (m.overflow) {
+        bool grew = false;
         if (m.far_total + 1024 > s->cap_far) {
             const int want = m.far_total + m.far_total / 4 + 1024;
-            cudaError_t e = regrow(s->ent, (size_t)want);
+            cudaError_t e = regrow(s->far_ent, (size_t)want);
             if (e != cudaSuccess) return cuda_err(err, e, "far list");
             s->cap_far = want;
+            grew = true;
+        }
+        if (m.near_total + 1024 > s->cap_near) {
+            const int want = m.near_total + m.near_total / 4 + 1024;
+            cudaError_t e = regrow(s->near_ent, (size_t)want);
+            if (e != cudaSuccess) return cuda_err(err, e, "near list");
+            s->cap_near = want;
+            grew = true;
+        }
+        if (grew) {
+            delete s->bc;  // buffers moved: the captured graph is stale
+            s->bc = nullptr;
             retry = true;
             return RISM_OK;
         }
-        err = "tree node or proxy capacity exceeded";
+        err = "tree node, proxy or traversal capacity exceeded";
         return RISM_E_NOMEM;
     }
     info.tree_nodes = m.nnodes;
@@ -1218,9 +1727,113 @@ rism_status tree_post(TreeState* s, rism_info& info, bool& retry, std::string& e
     return RISM_OK;
 }
 
-rism_status batch_eval(std::vector<BatchItem>&, const rism_options&, cudaStream_t, DevErr*, std::string& msg) {
-    msg = "batched launch not built";
-    return RISM_E_UNSUPPORTED;
+// Many solutes: tables, trees, lists and one persistent far + one persistent
+// near kernel draining all (solute, batch) items, captured in a CUDA graph
+// on the first context's stream and replayed while nothing that the captured
+// launches depend on (pointers, sizes, constants) has changed.
+rism_status batch_eval(std::vector<BatchItem>& items, const rism_options& o, cudaStream_t st, DevErr* err,
+                       std::string& msg, bool& retry) {
+    retry = false;
+    const int count = (int)items.size();
+    TreeState* s0 = items[0].tree;
+    const int variant = s0->variant;
+    std::vector<EvalArgs> args((size_t)count);
+    std::vector<int> off((size_t)count + 1, 0);
+    for (int b = 0; b < count; ++b) {
+        BatchItem& it = items[b];
+        it.tree->variant = variant;
+        if (!o.autotune) it.tree->leaf = o.leaf;
+        else it.tree->leaf = s0->leaf;
+        rism_status r = tree_reserve(it.tree, *it.t, it.g, o, msg);
+        if (r != RISM_OK) return r;
+        args[b] = make_args(it.tree, *it.t, it.g, it.ph, o, it.o);
+        off[b + 1] = off[b] + it.tree->nb;
+    }
+    // signature of everything the captured launches depend on
+    std::vector<unsigned char> sig;
+    auto put = [&](const void* p, size_t n) {
+        const unsigned char* c = static_cast<const unsigned char*>(p);
+        sig.insert(sig.end(), c, c + n);
+    };
+    put(args.data(), sizeof(EvalArgs) * args.size());
+    for (int b = 0; b < count; ++b) {
+        const BatchItem& it = items[b];
+        TreeState* s = it.tree;
+        const void* ptrs[] = {it.t->geo, it.t->srcf, it.t->ljd, it.t->ljf, it.raw, s->code, s->nodes, s->part,
+                              s->cell_start, s->far_ent, s->near_ent};
+        put(ptrs, sizeof ptrs);
+        const int ints[] = {(int)it.t->n, it.t->smax, s->leaf, s->max_nodes, s->max_prox, s->max_items, s->cap_far,
+                            s->cap_near, it.lj_mode};
+        put(ints, sizeof ints);
+        const double dbl[] = {it.lj_rcut, it.lj_tol};
+        put(dbl, sizeof dbl);
+        put(it.sig_s, sizeof(double) * kMaxSites);
+        put(it.eps_s, sizeof(double) * kMaxSites);
+    }
+    put(&o, sizeof o);
+    BatchCache*& bc = s0->bc;
+    cudaError_t e = cudaSuccess;
+    if (!bc || bc->sig != sig) {
+        delete bc;
+        bc = new BatchCache();
+        if ((e = cudaMalloc(&bc->d_args, sizeof(EvalArgs) * count)) != cudaSuccess ||
+            (e = cudaMalloc(&bc->d_off, sizeof(int) * (count + 1))) != cudaSuccess ||
+            (e = cudaMalloc(&bc->d_queue, sizeof(int) * 2)) != cudaSuccess)
+            return cuda_err(msg, e, "batch buffers");
+        if ((e = cudaMemcpy(bc->d_args, args.data(), sizeof(EvalArgs) * count, cudaMemcpyHostToDevice)) !=
+                cudaSuccess ||
+            (e = cudaMemcpy(bc->d_off, off.data(), sizeof(int) * (count + 1), cudaMemcpyHostToDevice)) != cudaSuccess)
+            return cuda_err(msg, e, "batch upload");
+        if ((e = cudaStreamCreateWithFlags(&bc->cs, cudaStreamNonBlocking)) != cudaSuccess)
+            return cuda_err(msg, e, "capture stream");
+        cudaStream_t cs = bc->cs;
+        if ((e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal)) != cudaSuccess)
+            return cuda_err(msg, e, "graph capture");
+        rism_status r = RISM_OK;
+        for (int b = 0; b < count && r == RISM_OK; ++b) {
+            BatchItem& it = items[b];
+            DevTables tt = *it.t;
+            if (tt.n > 0) {
+                e = launch_setup(it.raw, tt.n, it.ph.S, tt.smax, it.sig_s, it.eps_s, it.lj_mode, it.lj_rcut, it.lj_tol,
+                                 it.g, tt, cs);
+                if (e != cudaSuccess) r = cuda_err(msg, e, "setup");
+            }
+            if (r == RISM_OK) r = tree_enqueue(it.tree, tt, it.g, it.ph, o, cs, msg);
+        }
+        if (r == RISM_OK) {
+            cudaMemsetAsync(bc->d_queue, 0, sizeof(int) * 2, cs);
+            BatchEval be{bc->d_args, bc->d_off, count, off[count], bc->d_queue};
+            const bool du = items[0].o.u != nullptr, dh = items[0].o.h != nullptr;
+            e = dispatch(s0->smax ? s0->smax : items[0].t->smax, variant, 1, du, dh, nullptr, 0, &be, sm_count(), cs);
+            if (e != cudaSuccess) r = cuda_err(msg, e, "batched eval");
+            for (int b = 0; b < count; ++b)
+                cudaMemcpyAsync(items[b].tree->h_meta, items[b].tree->meta, sizeof(TreeMeta), cudaMemcpyDeviceToHost, cs);
+        }
+        cudaGraph_t graph = nullptr;
+        cudaError_t ce = cudaStreamEndCapture(cs, &graph);
+        if (r != RISM_OK) {
+            if (graph) cudaGraphDestroy(graph);
+            delete bc;
+            bc = nullptr;
+            return r;
+        }
+        if (ce != cudaSuccess) {
+            delete bc;
+            bc = nullptr;
+            return cuda_err(msg, ce, "graph capture");
+        }
+        bc->graph = graph;
+        if ((e = cudaGraphInstantiate(&bc->exec, graph, 0)) != cudaSuccess) {
+            delete bc;
+            bc = nullptr;
+            return cuda_err(msg, e, "graph instantiate");
+        }
+        bc->sig = sig;
+        bc->cap = count;
+    }
+    if ((e = cudaGraphLaunch(bc->exec, st)) != cudaSuccess) return cuda_err(msg, e, "graph launch");
+    (void)err;
+    return RISM_OK;
 }
 
 }  // namespace rism

@@ -19,6 +19,10 @@ struct BatchItem {
     GridD g;
     Phys ph;
     Outputs o;
+    const double* raw;  // [n][6] solute on the device (uploaded before the launch)
+    double sig_s[kMaxSites], eps_s[kMaxSites];
+    int lj_mode;
+    double lj_rcut, lj_tol;
 };
 
 TreeState* tree_create();
@@ -34,7 +38,11 @@ rism_status tree_eval(TreeState* ts, const DevTables& t, const GridD& g, const P
 // far-list overflow grow the buffer and set retry (run prepare + eval again).
 rism_status tree_post(TreeState* ts, rism_info& info, bool& retry, std::string& err);
 // Many solutes in one persistent, graph-captured launch sequence.
+// The whole sequence (per-solute setup and tree kernels, persistent far and
+// near kernels) is captured in a CUDA graph and replayed while unchanged.
+// After the caller synchronises, tree_post on each item reports overflows
+// (retry: run again).
 rism_status batch_eval(std::vector<BatchItem>& items, const rism_options& o, cudaStream_t st, DevErr* err,
-                       std::string& msg);
+                       std::string& msg, bool& retry);
 
 }  // namespace rism
