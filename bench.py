@@ -47,7 +47,7 @@ def _workload(seed=0):
 def _config(w, method, precision):
     return {"workload": WORKLOAD, "atoms": w.solute.n, "grid": list(w.grid.n), "spacing_A": w.grid.h,
             "sites": w.solvent.nsite, "lj_rcut_A": w.opts.get("lj_rcut"), "degree": w.opts.get("degree"),
-            "theta": w.opts.get("theta"), "method": method, "precision": precision,
+            "theta": w.opts.get("theta"), "method": method, "precision": precision, "autotune": True,
             "outputs": "u, c_lr, h_lr (FP64 grids) + LJ tail integrals",
             "l2": "flushed before every timed step by a 256 MB write (outputs are 201 MB, inputs 96 KB)"}
 
@@ -148,7 +148,8 @@ def run_gpu(args):
     w = _workload(seed=rank)
     method = R.METHOD_TREECODE if args.method == "treecode" else R.METHOD_DIRECT
     prec = R.PREC_FP32 if args.precision == "fp32" else R.PREC_FP64
-    r = R.from_workload(w, method=method, precision=prec, debug_flags=2)
+    # the autotuner picks the target-batch shape and leaf size during the (untimed) warm-up
+    r = R.from_workload(w, method=method, precision=prec, debug_flags=2, autotune=1)
     S, M = w.solvent.nsite, w.grid.npts
     xyz, q, sg, ep = w.solute.xyz, w.solute.q, w.solute.sigma, w.solute.eps
     out = {k: r.empty_grid() for k in ("u", "c", "h")}

@@ -38,10 +38,11 @@ struct __align__(16) LJf {
 // grid origin as float-float (hi + lo, |lo| <= ulp(hi)/2) and charge.  Grid
 // point indices are exact small integers in FP32, so for a nearby source
 // dx = (i - xh) - xl loses nothing in the first subtraction (Sterbenz) and
-// carries one rounding of dx itself.
+// carries one rounding of dx itself.  on_grid = 1 when the source sits
+// exactly on a lattice point (only then can d = 0 occur).
 struct __align__(16) SrcF {
     float xh, yh, zh, q;
-    float xl, yl, zl, pad;
+    float xl, yl, zl, on_grid;
 };
 
 // Physical constants and per-site factors shared by every evaluation kernel.
@@ -142,7 +143,7 @@ __device__ __forceinline__ SrcF make_srcf(double x, double y, double z, double q
     split_ff(y, s.yh, s.yl);
     split_ff(z, s.zh, s.zl);
     s.q = (float)q;
-    s.pad = 0.f;
+    s.on_grid = (x == floor(x) && y == floor(y) && z == floor(z)) ? 1.f : 0.f;
     return s;
 }
 

@@ -23,14 +23,17 @@
 //
 // Pipeline (all on the context's stream, no host synchronisation, so that it
 // can be captured in a CUDA graph):
-//   k_bbox_codes -> k_sort_build (one CTA: radix sort, octree, proxy plan)
-//   -> k_node_boxes -> k_gather -> k_cells -> k_upward -> k_proxy_reduce
-//   -> k_far_lists / k_near_lists (count, scan, fill; one warp per batch)
+//   k_bounds -> k_codes (Morton cube, codes, near-field plan) -> k_sort_build
+//   (one CTA: radix sort, sorted sources, octree, proxy plan, node boxes)
+//   -> k_cells -> k_upward -> k_proxy_reduce
+//   -> k_far_lists / k_near_lists (one warp per batch, per-batch slots)
 //   -> k_far32 (far field) -> k_near32 (near field + epilogue).
 // Many solutes: the same per-solute preparation, then one persistent far
 // and one persistent near kernel draining all (solute, batch) work items.
 // List capacities are checked on the device; an overflow is reported through
 // the meta block and the host grows the buffers and runs again.
+#include <algorithm>
+#include <climits>
 #include <cmath>
 #include <cstdio>
 #include <cstdlib>
@@ -49,7 +52,7 @@ namespace {
 constexpr int kSortThreads = 1024;
 constexpr int kMortonBits = 10;          // per axis
 constexpr int kMaxLevel = kMortonBits;   // octree depth limit
-constexpr int kChunk = 64;               // atoms per upward-pass work item
+constexpr int kChunk = 16;               // atoms per upward-pass work item
 constexpr int kT = 64;                   // sources per shared-memory tile
 constexpr int kStack = 8 * kMaxLevel + 8;
 
@@ -66,9 +69,12 @@ struct Node {
 struct TreeMeta {
     int nnodes, nprox, nitems, nleaves;
     int overflow;          // capacity exceeded (nodes / items / far list)
-    int far_total;         // entries the far-list fill needs
-    int near_total;        // entries the near-list fill needs
+    int far_need;          // largest far list of a batch (entries)
+    int near_need;         // largest near list of a batch (entries)
     int lc;                // cell level of the near field
+    int bmin[3], bmax[3];  // atom bounds, order-preserving int encoding of the FP32 grid-unit positions
+    int rc2max;            // largest per-pair LJ cut-off squared (grid units, FP32 bits; +inf without cut-off)
+    int pad;
     double cube_lo[3];     // Morton cube (grid units)
     double cube_side;
     double cell_side;      // cube_side / 2^lc
@@ -89,82 +95,81 @@ __device__ __forceinline__ uint32_t morton3(uint32_t x, uint32_t y, uint32_t z) 
 }
 
 // ------------------------------------------------- bounding cube + codes
-// One CTA: min/max of the atoms (grid units), the Morton cube, the codes,
-// and the near-field plan (radius = max(largest LJ cut-off, r_short); cells
-// at least half that radius wide, at most 8^7 of them).
 __device__ __forceinline__ Geo to_grid(const Geo& p, const GridD& g) {
     const double ih = 1.0 / g.h;
     return Geo{(p.x - g.ox) * ih, (p.y - g.oy) * ih, (p.z - g.oz) * ih, p.q};
 }
 
-__global__ void k_bbox_codes(const Geo* __restrict__ geo, const LJd* __restrict__ ljd, int n, int S, int smax,
-                             double rs, GridD gd, TreeMeta* meta, uint32_t* code, uint32_t* idx) {
-    const double h = gd.h;
-    __shared__ double red[7][kSortThreads / 32];
-    double lo[3] = {INFINITY, INFINITY, INFINITY}, hi[3] = {-INFINITY, -INFINITY, -INFINITY};
-    double rc2 = 0.0;
-    for (int i = threadIdx.x; i < n; i += blockDim.x) {
-        Geo g = to_grid(geo[i], gd);
-        double v[3] = {g.x, g.y, g.z};
+// Order-preserving int encoding of a float (for atomicMin / atomicMax).
+__device__ __forceinline__ int f2ord(float f) {
+    const int i = __float_as_int(f);
+    return i >= 0 ? i : i ^ 0x7fffffff;
+}
+__device__ __forceinline__ float ord2f(int i) { return __int_as_float(i >= 0 ? i : i ^ 0x7fffffff); }
+
+// Atom bounds (grid units, from the float-float source table) and the
+// largest LJ cut-off, reduced with atomics into the meta block.
+__global__ void k_bounds(const SrcF* __restrict__ srcf, const LJf* __restrict__ ljf, int n, int S, int smax,
+                         TreeMeta* meta) {
+    int lo[3] = {INT_MAX, INT_MAX, INT_MAX}, hi[3] = {INT_MIN, INT_MIN, INT_MIN};
+    int rc = 0;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        const SrcF s = srcf[i];
+        const int v[3] = {f2ord(s.xh), f2ord(s.yh), f2ord(s.zh)};
         for (int d = 0; d < 3; ++d) {
-            lo[d] = fmin(lo[d], v[d]);
-            hi[d] = fmax(hi[d], v[d]);
+            lo[d] = min(lo[d], v[d]);
+            hi[d] = max(hi[d], v[d]);
         }
-        for (int s = 0; s < S; ++s) rc2 = fmax(rc2, ljd[(int64_t)i * smax + s].rc2);
+        for (int k = 0; k < S; ++k) rc = max(rc, __float_as_int(ljf[(int64_t)i * smax + k].rc2));
     }
-    for (int d = 0; d < 3; ++d)
-        for (int o = 16; o > 0; o >>= 1) {
-            lo[d] = fmin(lo[d], __shfl_xor_sync(0xffffffffu, lo[d], o));
-            hi[d] = fmax(hi[d], __shfl_xor_sync(0xffffffffu, hi[d], o));
+    for (int o = 16; o > 0; o >>= 1) {
+        for (int d = 0; d < 3; ++d) {
+            lo[d] = min(lo[d], __shfl_xor_sync(0xffffffffu, lo[d], o));
+            hi[d] = max(hi[d], __shfl_xor_sync(0xffffffffu, hi[d], o));
         }
-    for (int o = 16; o > 0; o >>= 1) rc2 = fmax(rc2, __shfl_xor_sync(0xffffffffu, rc2, o));
-    const int w = threadIdx.x >> 5, nw = blockDim.x >> 5;
+        rc = max(rc, __shfl_xor_sync(0xffffffffu, rc, o));
+    }
     if ((threadIdx.x & 31) == 0) {
         for (int d = 0; d < 3; ++d) {
-            red[d][w] = lo[d];
-            red[3 + d][w] = hi[d];
+            atomicMin(&meta->bmin[d], lo[d]);
+            atomicMax(&meta->bmax[d], hi[d]);
         }
-        red[6][w] = rc2;
+        atomicMax(&meta->rc2max, rc);  // non-negative floats order as ints
     }
-    __syncthreads();
-    __shared__ double cube[4];
-    if (threadIdx.x == 0) {
-        double L = 0.0, l0[3], r2 = 0.0;
-        for (int d = 0; d < 3; ++d) {
-            double a = INFINITY, b = -INFINITY;
-            for (int k = 0; k < nw; ++k) {
-                a = fmin(a, red[d][k]);
-                b = fmax(b, red[3 + d][k]);
-            }
-            if (n == 0) a = b = 0.0;
-            l0[d] = a;
-            L = fmax(L, b - a);
-        }
-        for (int k = 0; k < nw; ++k) r2 = fmax(r2, red[6][k]);
-        L = L * (1.0 + 1e-9) + 1e-6;
-        for (int d = 0; d < 3; ++d) {
-            meta->cube_lo[d] = l0[d];
-            cube[d] = l0[d];
-        }
+}
+
+// Morton cube (a cube containing the atom bounds with a one-grid-unit
+// margin), Morton codes of the atoms, and the near-field plan: radius =
+// max(largest LJ cut-off, r_short); cells at least half that radius wide,
+// at most 8^7 of them.  Every thread derives the same cube from the bounds.
+__global__ void k_codes(const SrcF* __restrict__ srcf, int n, double rs_grid, TreeMeta* meta, uint32_t* code,
+                        uint32_t* idx) {
+    float lo[3];
+    float L = 0.f;
+    for (int d = 0; d < 3; ++d) {
+        lo[d] = ord2f(meta->bmin[d]) - 1.0f;
+        L = fmaxf(L, ord2f(meta->bmax[d]) + 1.0f - lo[d]);
+    }
+    const float sc = (float)(1 << kMortonBits) / L;
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        for (int d = 0; d < 3; ++d) meta->cube_lo[d] = lo[d];
         meta->cube_side = L;
-        cube[3] = L;
-        const double rnear = fmax(sqrt(r2), rs) / h;  // infinite without an LJ cut-off
+        const float rc2 = __int_as_float(meta->rc2max);
+        const double rnear = fmax(sqrt((double)rc2), rs_grid);  // infinite without an LJ cut-off
         int lc = 0;
         if (isfinite(rnear))
-            while (lc < 7 && L / (double)(1 << (lc + 1)) >= 0.5 * rnear) ++lc;
+            while (lc < 7 && (double)L / (double)(1 << (lc + 1)) >= 0.5 * rnear) ++lc;
         meta->lc = lc;
-        meta->cell_side = L / (double)(1 << lc);
+        meta->cell_side = (double)L / (double)(1 << lc);
         meta->rnear = rnear;
     }
-    __syncthreads();
-    const double sc = (double)(1 << kMortonBits) / cube[3];
-    for (int i = threadIdx.x; i < n; i += blockDim.x) {
-        Geo g = to_grid(geo[i], gd);
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        const SrcF s = srcf[i];
+        const float v[3] = {s.xh, s.yh, s.zh};
         uint32_t c[3];
-        double v[3] = {g.x, g.y, g.z};
         for (int d = 0; d < 3; ++d) {
-            double t = floor((v[d] - cube[d]) * sc);
-            c[d] = (uint32_t)fmin(fmax(t, 0.0), (double)((1 << kMortonBits) - 1));
+            const float tt = floorf((v[d] - lo[d]) * sc);
+            c[d] = (uint32_t)fminf(fmaxf(tt, 0.f), (float)((1 << kMortonBits) - 1));
         }
         code[i] = morton3(c[0], c[1], c[2]);
         idx[i] = (uint32_t)i;
@@ -178,6 +183,14 @@ __global__ void k_bbox_codes(const Geo* __restrict__ geo, const LJd* __restrict_
 // proxy work plan (items of kChunk atoms per proxied node) is laid out.
 struct BuildArgs {
     int n, leaf, P3, max_nodes, max_prox, max_items;
+    const Geo* geo;        // physical positions (unsorted)
+    const SrcF* srcf;      // float-float grid-unit positions (unsorted)
+    const LJf* ljf;        // LJ tables (unsorted)
+    int smax;
+    GridD gd;
+    Geo* src;              // out: sorted FP64 grid units
+    SrcF* ssrcf;           // out: sorted float-float
+    LJf* ljs;              // out: sorted LJ tables
 };
 
 __device__ int block_exclusive_scan(int v, int* tmp /* >= 32 ints */, int& total) {
@@ -206,7 +219,8 @@ __device__ int block_exclusive_scan(int v, int* tmp /* >= 32 ints */, int& total
 
 __global__ void __launch_bounds__(kSortThreads) k_sort_build(BuildArgs a, uint32_t* code, uint32_t* idx,
                                                              uint32_t* code2, uint32_t* idx2, Node* nodes,
-                                                             int* items, int* prox_nodes, TreeMeta* meta) {
+                                                             int* items, int* prox_nodes, int* prox_items,
+                                                             TreeMeta* meta) {
     extern __shared__ int sh[];
     int* hist = sh;                     // [256][32]
     int* tmp = sh + 256 * 32;           // [64]
@@ -261,15 +275,25 @@ __global__ void __launch_bounds__(kSortThreads) k_sort_build(BuildArgs a, uint32
         uint32_t* t2 = vin; vin = vout; vout = t2;
     }
     // after 4 passes the sorted data is back in code/idx
+    // ---- sorted copies of the sources (FP64 grid units, float-float) and LJ tables
+    for (int i = threadIdx.x; i < n; i += blockDim.x) {
+        const int j = (int)idx[i];
+        a.src[i] = to_grid(a.geo[j], a.gd);
+        a.ssrcf[i] = a.srcf[j];
+        for (int s = 0; s < a.smax; ++s) a.ljs[(int64_t)i * a.smax + s] = a.ljf[(int64_t)j * a.smax + s];
+    }
 
     // ---- octree, level by level: nodes [lvl_begin, lvl_end) at the current level
-    __shared__ int s_nnodes, s_lvl_begin, s_lvl_end, s_overflow;
+    __shared__ int s_nnodes, s_lvl_begin, s_lvl_end, s_overflow, s_lvl[kMaxLevel + 2], s_nlvl;
     if (threadIdx.x == 0) {
         nodes[0] = Node{0, n, -1, 0, 0, -1, 0, 0, {0, 0, 0}, {0, 0, 0}};
         s_nnodes = 1;
         s_lvl_begin = 0;
         s_lvl_end = 1;
         s_overflow = 0;
+        s_lvl[0] = 0;
+        s_lvl[1] = 1;
+        s_nlvl = 1;
     }
     __syncthreads();
     for (int lvl = 0; lvl < kMaxLevel; ++lvl) {
@@ -321,6 +345,10 @@ __global__ void __launch_bounds__(kSortThreads) k_sort_build(BuildArgs a, uint32
         if (threadIdx.x == 0) {
             s_lvl_begin = le;
             s_lvl_end = s_nnodes;
+            if (s_nnodes > le) {
+                s_lvl[s_nlvl + 1] = s_nnodes;
+                ++s_nlvl;
+            }
         }
         __syncthreads();
     }
@@ -356,6 +384,7 @@ __global__ void __launch_bounds__(kSortThreads) k_sort_build(BuildArgs a, uint32
             } else {
                 nodes[nid].prox = k;
                 prox_nodes[k] = nid;
+                prox_items[k] = i0 + oi;
                 // item = (proxy set k, atom chunk start)
                 for (int c = 0; c < nit; ++c) {
                     items[2 * (i0 + oi + c) + 0] = k;
@@ -377,49 +406,44 @@ __global__ void __launch_bounds__(kSortThreads) k_sort_build(BuildArgs a, uint32
         meta->nitems = s_items;
         meta->nleaves = s_leaves;
         meta->overflow = s_overflow;
+        prox_items[s_prox] = s_items;
     }
-}
-
-// --------------------------------- node boxes, gathered sources, cells
-__global__ void k_node_boxes(Node* nodes, const TreeMeta* meta, const uint32_t* idx, const Geo* __restrict__ geo,
-                             GridD gd) {
-    if (meta->overflow) return;  // the tree is incomplete; the host reports it
-    const int nn = meta->nnodes;
-    const int lane = threadIdx.x & 31;
-    for (int nid = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; nid < nn; nid += (gridDim.x * blockDim.x) >> 5) {
-        Node nd = nodes[nid];
-        double lo[3] = {INFINITY, INFINITY, INFINITY}, hi[3] = {-INFINITY, -INFINITY, -INFINITY};
-        for (int i = nd.begin + lane; i < nd.end; i += 32) {
-            Geo g = to_grid(geo[idx[i]], gd);
-            double v[3] = {g.x, g.y, g.z};
-            for (int d = 0; d < 3; ++d) {
-                lo[d] = fmin(lo[d], v[d]);
-                hi[d] = fmax(hi[d], v[d]);
+    __syncthreads();
+    if (s_overflow) return;
+    // ---- tight bounding boxes (grid units), bottom-up: a leaf from its atoms, an
+    // internal node as the union of its children; one warp per node, level by level.
+    for (int lv = s_nlvl - 1; lv >= 0; --lv) {
+        for (int nid = s_lvl[lv] + w; nid < s_lvl[lv + 1]; nid += NW) {
+            const Node nd = nodes[nid];
+            double lo[3] = {INFINITY, INFINITY, INFINITY}, hi[3] = {-INFINITY, -INFINITY, -INFINITY};
+            if (nd.first_child < 0) {
+                for (int i = nd.begin + lane; i < nd.end; i += 32) {
+                    const Geo g = a.src[i];
+                    const double v[3] = {g.x, g.y, g.z};
+                    for (int d = 0; d < 3; ++d) {
+                        lo[d] = fmin(lo[d], v[d]);
+                        hi[d] = fmax(hi[d], v[d]);
+                    }
+                }
+            } else if (lane < nd.nchild) {
+                const Node ch = nodes[nd.first_child + lane];
+                for (int d = 0; d < 3; ++d) {
+                    lo[d] = ch.lo[d];
+                    hi[d] = ch.hi[d];
+                }
             }
+            for (int d = 0; d < 3; ++d)
+                for (int o = 16; o > 0; o >>= 1) {
+                    lo[d] = fmin(lo[d], __shfl_xor_sync(0xffffffffu, lo[d], o));
+                    hi[d] = fmax(hi[d], __shfl_xor_sync(0xffffffffu, hi[d], o));
+                }
+            if (lane == 0)
+                for (int d = 0; d < 3; ++d) {
+                    nodes[nid].lo[d] = lo[d];
+                    nodes[nid].hi[d] = hi[d];
+                }
         }
-        for (int d = 0; d < 3; ++d)
-            for (int o = 16; o > 0; o >>= 1) {
-                lo[d] = fmin(lo[d], __shfl_xor_sync(0xffffffffu, lo[d], o));
-                hi[d] = fmax(hi[d], __shfl_xor_sync(0xffffffffu, hi[d], o));
-            }
-        if (lane == 0)
-            for (int d = 0; d < 3; ++d) {
-                nodes[nid].lo[d] = lo[d];
-                nodes[nid].hi[d] = hi[d];
-            }
-    }
-}
-
-// Sorted copies of the atom geometry (FP64 grid units for the upward pass,
-// float-float for the evaluation kernels) and of the LJ tables.
-__global__ void k_gather(int n, int smax, const uint32_t* idx, const Geo* __restrict__ geo, GridD gd,
-                         const LJf* __restrict__ ljf, Geo* src, SrcF* srcf, LJf* ljs) {
-    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
-        const int j = (int)idx[i];
-        const Geo gg = to_grid(geo[j], gd);
-        src[i] = gg;
-        srcf[i] = make_srcf(gg.x, gg.y, gg.z, gg.q);
-        for (int s = 0; s < smax; ++s) ljs[(int64_t)i * smax + s] = ljf[(int64_t)j * smax + s];
+        __syncthreads();
     }
 }
 
@@ -448,18 +472,36 @@ __device__ __forceinline__ void cheb_box(const Node& nd, int d, double& c, doubl
     r = fmax(0.5 * (nd.hi[d] - nd.lo[d]), fmax(0.05 * w, 0.25));
 }
 
-// Work item = (proxy set, chunk of kChunk atoms): partial modified charges.
+// Chebyshev points of the second kind on node nd's box, all three axes, into
+// tn[3][np] (threads of the CTA cooperate; caller synchronises).
+__device__ __forceinline__ void cheb_table(const Node& nd, int deg, double* tn) {
+    const int np = deg + 1;
+    for (int k = threadIdx.x; k < 3 * np; k += blockDim.x) {
+        const int d = k / np, m = k % np;
+        double c, r;
+        cheb_box(nd, d, c, r);
+        tn[k] = c + r * cospi((double)m / deg);
+    }
+}
+
+// Work item = (proxy set, chunk of kChunk atoms): partial modified charges
+//   Qhat_k = sum_j q_j L_k1(y_j1) L_k2(y_j2) L_k3(y_j3)  (FP64)
+// with the barycentric Lagrange basis at Chebyshev-2 points, weights (-1)^m
+// halved at both ends (exact-node case handled).
 __global__ void k_upward(int deg, const TreeMeta* meta, const Node* nodes, const int* prox_nodes, const int* items,
                          const Geo* __restrict__ src, double* part) {
-    extern __shared__ double Ls[];  // [kChunk][3][deg+1], then q[kChunk]
+    extern __shared__ double Ls[];  // [kChunk][3][deg+1], q[kChunk], tn[3][deg+1]
     const int np = deg + 1, P3 = np * np * np;
     double* qs = Ls + kChunk * 3 * np;
+    double* tn = qs + kChunk;
     if (meta->overflow) return;
     const int nitems = meta->nitems;
     for (int it = blockIdx.x; it < nitems; it += gridDim.x) {
         const int k = items[2 * it], b = items[2 * it + 1];
         const Node nd = nodes[prox_nodes[k]];
         const int cnt = min(kChunk, nd.end - b);
+        __syncthreads();
+        cheb_table(nd, deg, tn);
         __syncthreads();
         for (int t = threadIdx.x; t < kChunk * 3; t += blockDim.x) {
             const int j = t / 3, d = t % 3;
@@ -472,15 +514,10 @@ __global__ void k_upward(int deg, const TreeMeta* meta, const Node* nodes, const
             const Geo g = src[b + j];
             if (d == 0) qs[j] = g.q;
             const double y = d == 0 ? g.x : (d == 1 ? g.y : g.z);
-            double c, r;
-            cheb_box(nd, d, c, r);
-            // barycentric Lagrange basis at Chebyshev-2 points t_m = c + r cos(m pi / deg),
-            // weights (-1)^m, halved at both ends
             int exact = -1;
             double den = 0.0;
             for (int m = 0; m < np; ++m) {
-                const double tm = c + r * cospi((double)m / deg);
-                const double diff = y - tm;
+                const double diff = y - tn[d * np + m];
                 if (diff == 0.0) exact = m;
                 double wm = (m & 1) ? -1.0 : 1.0;
                 if (m == 0 || m == deg) wm *= 0.5;
@@ -508,29 +545,29 @@ __global__ void k_upward(int deg, const TreeMeta* meta, const Node* nodes, const
 
 // Sum the partials of each proxy set in item order (deterministic) and write
 // the proxy points (grid units) with their modified charges after the atoms.
+// Work = (proxy set, block of blockDim proxies), grid-stride.
 __global__ void k_proxy_reduce(int deg, int n, const TreeMeta* meta, const Node* nodes, const int* prox_nodes,
-                               const int* items, const double* part, Geo* src, SrcF* srcf) {
+                               const int* prox_items, const double* part, Geo* src, SrcF* srcf) {
+    __shared__ double tn[3 * (kMaxDegree + 1)];
     const int np = deg + 1, P3 = np * np * np;
     if (meta->overflow) return;
-    const int nprox = meta->nprox, nitems = meta->nitems;
-    for (int k = blockIdx.x; k < nprox; k += gridDim.x) {
-        // items of set k are contiguous: find them by scanning (few sets, few items)
-        int i0 = 0;
-        while (i0 < nitems && items[2 * i0] != k) ++i0;
-        int i1 = i0;
-        while (i1 < nitems && items[2 * i1] == k) ++i1;
+    const int nprox = meta->nprox;
+    const int nblk = (P3 + blockDim.x - 1) / blockDim.x;
+    for (int wi = blockIdx.x; wi < nprox * nblk; wi += gridDim.x) {
+        const int k = wi / nblk, pb = wi % nblk;
         const Node nd = nodes[prox_nodes[k]];
-        double c[3], r[3];
-        for (int d = 0; d < 3; ++d) cheb_box(nd, d, c[d], r[d]);
-        for (int p = threadIdx.x; p < P3; p += blockDim.x) {
-            const int m1 = p % np, m2 = (p / np) % np, m3 = p / (np * np);
-            double q = 0.0;
-            for (int it = i0; it < i1; ++it) q += part[(int64_t)it * P3 + p];
-            const Geo pp{c[0] + r[0] * cospi((double)m1 / deg), c[1] + r[1] * cospi((double)m2 / deg),
-                         c[2] + r[2] * cospi((double)m3 / deg), q};
-            src[n + (int64_t)k * P3 + p] = pp;
-            srcf[n + (int64_t)k * P3 + p] = make_srcf(pp.x, pp.y, pp.z, pp.q);
-        }
+        __syncthreads();
+        cheb_table(nd, deg, tn);
+        __syncthreads();
+        const int p = pb * blockDim.x + threadIdx.x;
+        if (p >= P3) continue;
+        const int i0 = prox_items[k], i1 = prox_items[k + 1];
+        const int m1 = p % np, m2 = (p / np) % np, m3 = p / (np * np);
+        double q = 0.0;
+        for (int it = i0; it < i1; ++it) q += part[(int64_t)it * P3 + p];
+        const Geo pp{tn[m1], tn[np + m2], tn[2 * np + m3], q};
+        src[n + (int64_t)k * P3 + p] = pp;
+        srcf[n + (int64_t)k * P3 + p] = make_srcf(pp.x, pp.y, pp.z, pp.q);
     }
 }
 
@@ -544,7 +581,7 @@ struct ShapeDesc {
 };
 constexpr int kNumShapes = 3;
 __host__ __device__ constexpr ShapeDesc shape_of(int v) {
-    return v == 1 ? ShapeDesc{16, 8, 8, 8} : (v == 2 ? ShapeDesc{8, 8, 4, 4} : ShapeDesc{8, 8, 8, 4});
+    return v == 1 ? ShapeDesc{16, 8, 8, 8} : (v == 2 ? ShapeDesc{8, 8, 8, 8} : ShapeDesc{8, 8, 8, 4});
 }
 
 constexpr int kQCap = 1024;        // frontier capacity of the warp-cooperative traversal
@@ -574,18 +611,14 @@ __device__ __forceinline__ void batch_geom(const ListArgs& a, int b, double cb[3
 // octree with the frontier in shared memory.  Entries are (start, count)
 // ranges of the source array: atoms of a node evaluated directly, or a proxy
 // set (n + k P3, P3) of an accepted node.  Order: by level, then by lane --
-// deterministic.
-template <bool FILL>
-__global__ void __launch_bounds__(32 * kListWarps) k_far_lists(ListArgs a, const Node* __restrict__ nodes,
-                                                              const int* off, int2* ent, int* cnt, TreeMeta* meta) {
+// deterministic.  Batch b owns entries [b cap, (b+1) cap); a longer list sets
+// the overflow flag and records its length for the host to grow cap.
+__global__ void __launch_bounds__(32 * kListWarps) k_far_lists(ListArgs a, const Node* __restrict__ nodes, int2* ent,
+                                                              int* cnt, TreeMeta* meta) {
     __shared__ int qa[kListWarps][kQCap], qb[kListWarps][kQCap];
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     const int nb = a.nbx * a.nby * a.nbz;
-    if (meta->overflow) {
-        for (int b = blockIdx.x * kListWarps + w; b < nb; b += gridDim.x * kListWarps)
-            if (!FILL && lane == 0) cnt[b] = 0;
-        return;
-    }
+    const bool tree_ok = !meta->overflow;
     const long long pts = (long long)a.bx * a.by * a.bz;
     for (int b = blockIdx.x * kListWarps + w; b < nb; b += gridDim.x * kListWarps) {
         double cb[3], rb;
@@ -593,11 +626,11 @@ __global__ void __launch_bounds__(32 * kListWarps) k_far_lists(ListArgs a, const
         batch_geom(a, b, cb, rb, lo, hi);
         int* cur = qa[w];
         int* nxt = qb[w];
-        int ncur = a.n > 0 ? 1 : 0;
+        int ncur = (a.n > 0 && tree_ok) ? 1 : 0;
         if (lane == 0) cur[0] = 0;
         __syncwarp();
         int m = 0;
-        const int base = FILL ? off[b] : 0;
+        int2* out = ent + (int64_t)b * a.cap;
         long long dp = 0, pp = 0;
         bool ovf = false;
         while (ncur > 0) {
@@ -635,10 +668,9 @@ __global__ void __launch_bounds__(32 * kListWarps) k_far_lists(ListArgs a, const
                 const unsigned em = __ballot_sync(0xffffffffu, kind == 1);
                 if (kind == 1) {
                     const int pos = m + __popc(em & ((1u << lane) - 1u));
-                    if (FILL && base + pos < a.cap) ent[base + pos] = e;
+                    if (pos < a.cap) out[pos] = e;
                 }
                 m += __popc(em);
-                // children of opened nodes: exclusive prefix of nch over lanes
                 int x = nch;
                 for (int o = 1; o < 32; o <<= 1) {
                     const int y = __shfl_up_sync(0xffffffffu, x, o);
@@ -656,25 +688,31 @@ __global__ void __launch_bounds__(32 * kListWarps) k_far_lists(ListArgs a, const
             }
             __syncwarp();
             if (__any_sync(0xffffffffu, ovf) || nnext > kQCap) {
-                if (lane == 0) meta->overflow = 1;
+                // the frontier of this batch does not fit: a node or leaf-size setting beyond this build
+                if (lane == 0) {
+                    meta->overflow = 1;
+                    atomicMax(&meta->far_need, 1 << 30);
+                }
                 break;
             }
-            int* t = cur;
+            int* tq = cur;
             cur = nxt;
-            nxt = t;
+            nxt = tq;
             ncur = nnext;
             __syncwarp();
         }
-        if (!FILL) {
-            for (int o = 16; o > 0; o >>= 1) {
-                dp += __shfl_xor_sync(0xffffffffu, dp, o);
-                pp += __shfl_xor_sync(0xffffffffu, pp, o);
+        for (int o = 16; o > 0; o >>= 1) {
+            dp += __shfl_xor_sync(0xffffffffu, dp, o);
+            pp += __shfl_xor_sync(0xffffffffu, pp, o);
+        }
+        if (lane == 0) {
+            cnt[b] = min(m, a.cap);
+            if (m > a.cap) {
+                meta->overflow = 1;
+                atomicMax(&meta->far_need, m);
             }
-            if (lane == 0) {
-                cnt[b] = m;
-                atomicAdd(&meta->direct_pairs, (unsigned long long)(dp * pts));
-                atomicAdd(&meta->proxy_pairs, (unsigned long long)(pp * pts));
-            }
+            atomicAdd(&meta->direct_pairs, (unsigned long long)(dp * pts));
+            atomicAdd(&meta->proxy_pairs, (unsigned long long)(pp * pts));
         }
     }
 }
@@ -682,38 +720,33 @@ __global__ void __launch_bounds__(32 * kListWarps) k_far_lists(ListArgs a, const
 // Near lists: one warp per target batch; lanes test the cells of the box
 // grown by rnear (x fastest), keep those whose box lies within rnear of the
 // batch box, and emit their atom ranges in cell order.
-template <bool FILL>
-__global__ void __launch_bounds__(32 * kListWarps) k_near_lists(ListArgs a, const TreeMeta* __restrict__ meta_c,
-                                                               const int* __restrict__ cell_start, const int* off,
+__global__ void __launch_bounds__(32 * kListWarps) k_near_lists(ListArgs a, const int* __restrict__ cell_start,
                                                                int2* ent, int* cnt, TreeMeta* meta) {
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     const int nb = a.nbx * a.nby * a.nbz;
-    if (meta->overflow) {
-        for (int b = blockIdx.x * kListWarps + w; b < nb; b += gridDim.x * kListWarps)
-            if (!FILL && lane == 0) cnt[b] = 0;
-        return;
-    }
-    const int lc = meta_c->lc, ncell = 1 << lc;
-    const double side = meta_c->cell_side, rnear = meta_c->rnear;
-    const double rn = isfinite(rnear) ? rnear : 1e30;
+    const int lc = meta->lc, ncell = 1 << lc;
+    const double side = meta->cell_side, rnear = meta->rnear;
+    // 0.01 grid units of slack: Morton codes are computed in FP32, so an atom may sit ~1e-5 outside its cell box
+    const double rn = isfinite(rnear) ? rnear + 0.01 : 1e30;
     const double rn2 = rn * rn;
+    const bool tree_ok = !meta->overflow;
     const long long pts = (long long)a.bx * a.by * a.bz;
     for (int b = blockIdx.x * kListWarps + w; b < nb; b += gridDim.x * kListWarps) {
         double cb[3], rb;
         int lo[3], hi[3];
         batch_geom(a, b, cb, rb, lo, hi);
         int c0[3], c1[3];
-        bool ok = a.n > 0;
+        bool ok = a.n > 0 && tree_ok;
         for (int d = 0; d < 3; ++d) {
-            c0[d] = (int)fmax(floor((lo[d] - rn - meta_c->cube_lo[d]) / side), 0.0);
-            c1[d] = (int)fmin(floor((hi[d] + rn - meta_c->cube_lo[d]) / side), (double)(ncell - 1));
+            c0[d] = (int)fmax(floor((lo[d] - rn - meta->cube_lo[d]) / side), 0.0);
+            c1[d] = (int)fmin(floor((hi[d] + rn - meta->cube_lo[d]) / side), (double)(ncell - 1));
             ok = ok && c0[d] <= c1[d];
         }
         const int ex = ok ? c1[0] - c0[0] + 1 : 0, ey = ok ? c1[1] - c0[1] + 1 : 0, ez = ok ? c1[2] - c0[2] + 1 : 0;
         const int total = ex * ey * ez;
         int m = 0;
         long long cand = 0;
-        const int base = FILL ? off[b] : 0;
+        int2* out = ent + (int64_t)b * a.cap;
         for (int k0 = 0; k0 < total; k0 += 32) {
             const int k = k0 + lane;
             int2 e = make_int2(0, 0);
@@ -722,7 +755,7 @@ __global__ void __launch_bounds__(32 * kListWarps) k_near_lists(ListArgs a, cons
                 const int cc[3] = {c0[0] + k % ex, c0[1] + (k / ex) % ey, c0[2] + k / (ex * ey)};
                 double d2 = 0.0;
                 for (int d = 0; d < 3; ++d) {
-                    const double clo = meta_c->cube_lo[d] + cc[d] * side, chi = clo + side;
+                    const double clo = meta->cube_lo[d] + cc[d] * side, chi = clo + side;
                     const double gap = fmax(0.0, fmax(clo - hi[d], lo[d] - chi));
                     d2 += gap * gap;
                 }
@@ -739,49 +772,33 @@ __global__ void __launch_bounds__(32 * kListWarps) k_near_lists(ListArgs a, cons
             const unsigned em = __ballot_sync(0xffffffffu, take);
             if (take) {
                 const int pos = m + __popc(em & ((1u << lane) - 1u));
-                if (FILL && base + pos < a.cap) ent[base + pos] = e;
+                if (pos < a.cap) out[pos] = e;
             }
             m += __popc(em);
         }
-        if (!FILL) {
-            for (int o = 16; o > 0; o >>= 1) cand += __shfl_xor_sync(0xffffffffu, cand, o);
-            if (lane == 0) {
-                cnt[b] = m;
-                atomicAdd(&meta->near_pairs, (unsigned long long)(cand * pts));
+        for (int o = 16; o > 0; o >>= 1) cand += __shfl_xor_sync(0xffffffffu, cand, o);
+        if (lane == 0) {
+            cnt[b] = min(m, a.cap);
+            if (m > a.cap) {
+                meta->overflow = 1;
+                atomicMax(&meta->near_need, m);
             }
+            atomicAdd(&meta->near_pairs, (unsigned long long)(cand * pts));
         }
-    }
-}
-
-__global__ void k_scan(int nb, const int* cnt, int* off, int cap, TreeMeta* meta, int which) {
-    __shared__ int tmp[64];
-    __shared__ int carry;
-    if (threadIdx.x == 0) carry = 0;
-    __syncthreads();
-    for (int base = 0; base < nb; base += blockDim.x) {
-        const int i = base + threadIdx.x;
-        const int v = i < nb ? cnt[i] : 0;
-        int total;
-        const int ex = block_exclusive_scan(v, tmp, total);
-        if (i < nb) off[i] = carry + ex;
-        __syncthreads();
-        if (threadIdx.x == 0) carry += total;
-        __syncthreads();
-    }
-    if (threadIdx.x == 0) {
-        off[nb] = carry;
-        if (which == 0) meta->far_total = carry;
-        else meta->near_total = carry;
-        if (carry > cap) meta->overflow = 1;
     }
 }
 
 __global__ void k_reset_meta(TreeMeta* meta) {
     meta->direct_pairs = meta->proxy_pairs = meta->near_pairs = 0ull;
-    meta->far_total = meta->near_total = 0;
+    meta->far_need = meta->near_need = 0;
     meta->overflow = 0;
     meta->nnodes = meta->nprox = meta->nitems = meta->nleaves = 0;
     meta->lc = 0;
+    for (int d = 0; d < 3; ++d) {
+        meta->bmin[d] = INT_MAX;
+        meta->bmax[d] = INT_MIN;
+    }
+    meta->rc2max = 0;
     meta->cube_lo[0] = meta->cube_lo[1] = meta->cube_lo[2] = 0.0;
     meta->cube_side = meta->cell_side = 1.0;
     meta->rnear = 0.0;
@@ -800,10 +817,11 @@ struct EvalArgs {
     int n;
     const SrcF* srcf;      // [sorted atoms | proxies], grid units, float-float
     const LJf* ljs;        // sorted LJ tables
-    const int* far_off;    // far-list offsets [nb+1]
-    const int2* far_ent;
-    const int* near_off;   // near-list offsets [nb+1]
-    const int2* near_ent;
+    const int* far_cnt;    // far-list length per batch
+    const int2* far_ent;   // [nb][far_cap]
+    const int* near_cnt;
+    const int2* near_ent;  // [nb][near_cap]
+    int far_cap, near_cap;
     float4* far;           // per grid point: Phi1 (hi, lo), Phik (hi, lo), grid units
     Outputs o;
     DevErr* err;
@@ -951,8 +969,8 @@ __device__ void far_body(const EvalArgs& a, int b, Ring<1, false>& r) {
     Cursor cur;
     __syncthreads();
     if (tid == 0) {
-        cur.e = a.far_off[b];
-        cur.e_end = a.far_off[b + 1];
+        cur.e = b * a.far_cap;
+        cur.e_end = cur.e + a.far_cnt[b];
         cur.off = 0;
         cur.produced = 0;
         cur.done = false;
@@ -971,15 +989,29 @@ __device__ void far_body(const EvalArgs& a, int b, Ring<1, false>& r) {
             const float dy = (fy - g0.y) - g1.y;
             const float dz = (fz - g0.z) - g1.z;
             const float dyz2 = fmaf(dy, dy, dz * dz);
+            if (g1.w == 0.f) {
+                // the source is off the lattice: d > 0 for every grid point
 #pragma unroll
-            for (int p = 0; p < P; ++p) {
-                const float dx = (gx[p] - g0.x) - g1.x;
-                const float d2 = fmaf(dx, dx, dyz2);
-                const float rr = rsqrt_approx(d2);
-                const float ri = d2 > 0.f ? rr : 0.f;
-                const float qr = g0.w * ri;
-                p1[p] += qr;
-                if (DH) pk[p] = fmaf(qr, ex2_approx(kap2 * (d2 * ri)), pk[p]);
+                for (int p = 0; p < P; ++p) {
+                    const float dx = (gx[p] - g0.x) - g1.x;
+                    const float d2 = fmaf(dx, dx, dyz2);
+                    const float ri = rsqrt_approx(d2);
+                    const float qr = g0.w * ri;
+                    p1[p] += qr;
+                    if (DH) pk[p] = fmaf(qr, ex2_approx(kap2 * (d2 * ri)), pk[p]);
+                }
+            } else {
+                // on a lattice point: the coincident point's pair is left to the near field (d = 0 limit)
+#pragma unroll
+                for (int p = 0; p < P; ++p) {
+                    const float dx = (gx[p] - g0.x) - g1.x;
+                    const float d2 = fmaf(dx, dx, dyz2);
+                    const float rr = rsqrt_approx(d2);
+                    const float ri = d2 > 0.f ? rr : 0.f;
+                    const float qr = g0.w * ri;
+                    p1[p] += qr;
+                    if (DH) pk[p] = fmaf(qr, ex2_approx(kap2 * (d2 * ri)), pk[p]);
+                }
             }
         }
 #pragma unroll
@@ -1034,8 +1066,8 @@ __device__ void near_body(const EvalArgs& a, int b, Ring<SM, true>& r) {
     Cursor cur;
     __syncthreads();
     if (tid == 0) {
-        cur.e = a.near_off[b];
-        cur.e_end = a.near_off[b + 1];
+        cur.e = b * a.near_cap;
+        cur.e_end = cur.e + a.near_cnt[b];
         cur.off = 0;
         cur.produced = 0;
         cur.done = false;
@@ -1315,7 +1347,8 @@ struct BatchCache;
 struct TreeState {
     int64_t cap_n = 0;
     int cap_nodes = 0, cap_prox = 0, cap_items = 0, cap_nb = 0;
-    int cap_far = 0, cap_near = 0;
+    int cap_far = 0, cap_near = 0;          // entries per batch
+    int64_t cap_far_ent = 0, cap_near_ent = 0;  // entries allocated
     int deg = 0, smax = 0;
     uint32_t *code = nullptr, *idx = nullptr, *code2 = nullptr, *idx2 = nullptr;
     Node* nodes = nullptr;
@@ -1327,7 +1360,7 @@ struct TreeState {
     LJf* ljs = nullptr;
     float4* far = nullptr; // far-field sums per grid point
     int64_t cap_far_pts = 0;
-    int *far_cnt = nullptr, *far_off = nullptr, *near_cnt = nullptr, *near_off = nullptr;
+    int *far_cnt = nullptr, *near_cnt = nullptr, *prox_items = nullptr;
     int2 *far_ent = nullptr, *near_ent = nullptr;
     int* cell_start = nullptr;
     TreeMeta* meta = nullptr;
@@ -1394,6 +1427,7 @@ rism_status tree_reserve(TreeState* s, const DevTables& t, const GridD& g, const
         if ((e = regrow(s->code, nn)) || (e = regrow(s->idx, nn)) || (e = regrow(s->code2, nn)) ||
             (e = regrow(s->idx2, nn)) || (e = regrow(s->nodes, (size_t)s->max_nodes)) ||
             (e = regrow(s->items, 2 * (size_t)s->max_items)) || (e = regrow(s->prox_nodes, (size_t)s->max_prox)) ||
+            (e = regrow(s->prox_items, (size_t)s->max_prox + 1)) ||
             (e = regrow(s->part, (size_t)s->max_items * P3)) || (e = regrow(s->src, nn + (size_t)s->max_prox * P3)) ||
             (e = regrow(s->srcf, nn + (size_t)s->max_prox * P3)) || (e = regrow(s->ljs, nn * t.smax)))
             return cuda_err(err, e, "tree buffers");
@@ -1410,19 +1444,19 @@ rism_status tree_reserve(TreeState* s, const DevTables& t, const GridD& g, const
         s->cap_far_pts = M;
     }
     if (s->nb + 1 > s->cap_nb) {
-        if ((e = regrow(s->far_cnt, (size_t)s->nb + 1)) || (e = regrow(s->far_off, (size_t)s->nb + 1)) ||
-            (e = regrow(s->near_cnt, (size_t)s->nb + 1)) || (e = regrow(s->near_off, (size_t)s->nb + 1)))
-            return cuda_err(err, e, "list offsets");
+        if ((e = regrow(s->far_cnt, (size_t)s->nb + 1)) || (e = regrow(s->near_cnt, (size_t)s->nb + 1)))
+            return cuda_err(err, e, "list counts");
         s->cap_nb = s->nb + 1;
     }
-    const int want = s->nb * 64 + 1024;
-    if (s->cap_far < want) {
-        if ((e = regrow(s->far_ent, (size_t)want))) return cuda_err(err, e, "far list");
-        s->cap_far = want;
+    if (s->cap_far == 0) s->cap_far = 128;
+    if (s->cap_near == 0) s->cap_near = 512;
+    if ((int64_t)s->nb * s->cap_far > s->cap_far_ent) {
+        if ((e = regrow(s->far_ent, (size_t)s->nb * s->cap_far))) return cuda_err(err, e, "far list");
+        s->cap_far_ent = (int64_t)s->nb * s->cap_far;
     }
-    if (s->cap_near < want) {
-        if ((e = regrow(s->near_ent, (size_t)want))) return cuda_err(err, e, "near list");
-        s->cap_near = want;
+    if ((int64_t)s->nb * s->cap_near > s->cap_near_ent) {
+        if ((e = regrow(s->near_ent, (size_t)s->nb * s->cap_near))) return cuda_err(err, e, "near list");
+        s->cap_near_ent = (int64_t)s->nb * s->cap_near;
     }
     return RISM_OK;
 }
@@ -1438,35 +1472,30 @@ rism_status tree_enqueue(TreeState* s, const DevTables& t, const GridD& g, const
     k_reset_meta<<<1, 1, 0, st>>>(s->meta);
     ++s->launches;
     if (n > 0) {
-        k_bbox_codes<<<1, kSortThreads, 0, st>>>(t.geo, t.ljd, n, ph.S, t.smax, ph.rs, g, s->meta, s->code, s->idx);
-        BuildArgs ba{n, s->leaf, P3, s->max_nodes, s->max_prox, s->max_items};
+        const int gb = std::min((n + 255) / 256, 4 * sm_count());
+        k_bounds<<<gb, 256, 0, st>>>(t.srcf, t.ljf, n, ph.S, t.smax, s->meta);
+        k_codes<<<gb, 256, 0, st>>>(t.srcf, n, ph.rs / g.h, s->meta, s->code, s->idx);
+        BuildArgs ba{n, s->leaf, P3, s->max_nodes, s->max_prox, s->max_items, t.geo, t.srcf, t.ljf, t.smax, g,
+                     s->src, s->srcf, s->ljs};
         const size_t shb = (256 * 32 + 64) * sizeof(int);
         cudaFuncSetAttribute(k_sort_build, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shb);
         k_sort_build<<<1, kSortThreads, shb, st>>>(ba, s->code, s->idx, s->code2, s->idx2, s->nodes, s->items,
-                                                   s->prox_nodes, s->meta);
-        k_node_boxes<<<sm_count(), 256, 0, st>>>(s->nodes, s->meta, s->idx, t.geo, g);
-        k_gather<<<(n + 255) / 256, 256, 0, st>>>(n, t.smax, s->idx, t.geo, g, t.ljf, s->src, s->srcf, s->ljs);
+                                                   s->prox_nodes, s->prox_items, s->meta);
         k_cells<<<1024, 256, 0, st>>>(n, s->meta, s->code, s->cell_start);
-        const size_t shu = (kChunk * 3 * np + kChunk) * sizeof(double);
+        const size_t shu = (kChunk * 3 * np + kChunk + 3 * np) * sizeof(double);
         cudaFuncSetAttribute(k_upward, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shu);
         k_upward<<<4 * sm_count(), 256, shu, st>>>(deg, s->meta, s->nodes, s->prox_nodes, s->items, s->src, s->part);
-        k_proxy_reduce<<<sm_count(), 256, 0, st>>>(deg, n, s->meta, s->nodes, s->prox_nodes, s->items, s->part,
-                                                   s->src, s->srcf);
-        s->launches += 7;
+        k_proxy_reduce<<<2 * sm_count(), 256, 0, st>>>(deg, n, s->meta, s->nodes, s->prox_nodes, s->prox_items,
+                                                       s->part, s->src, s->srcf);
+        s->launches += 6;
     }
     ListArgs fa{s->nbx, s->nby, s->nbz, sd.nx, sd.ny, sd.nz, o.theta, n, P3, s->cap_far};
     ListArgs na = fa;
     na.cap = s->cap_near;
     const int lgrid = (s->nb + kListWarps - 1) / kListWarps;
-    k_far_lists<false><<<lgrid, 32 * kListWarps, 0, st>>>(fa, s->nodes, s->far_off, s->far_ent, s->far_cnt, s->meta);
-    k_scan<<<1, 1024, 0, st>>>(s->nb, s->far_cnt, s->far_off, s->cap_far, s->meta, 0);
-    k_far_lists<true><<<lgrid, 32 * kListWarps, 0, st>>>(fa, s->nodes, s->far_off, s->far_ent, s->far_cnt, s->meta);
-    k_near_lists<false><<<lgrid, 32 * kListWarps, 0, st>>>(na, s->meta, s->cell_start, s->near_off, s->near_ent,
-                                                           s->near_cnt, s->meta);
-    k_scan<<<1, 1024, 0, st>>>(s->nb, s->near_cnt, s->near_off, s->cap_near, s->meta, 1);
-    k_near_lists<true><<<lgrid, 32 * kListWarps, 0, st>>>(na, s->meta, s->cell_start, s->near_off, s->near_ent,
-                                                          s->near_cnt, s->meta);
-    s->launches += 6;
+    k_far_lists<<<lgrid, 32 * kListWarps, 0, st>>>(fa, s->nodes, s->far_ent, s->far_cnt, s->meta);
+    k_near_lists<<<lgrid, 32 * kListWarps, 0, st>>>(na, s->cell_start, s->near_ent, s->near_cnt, s->meta);
+    s->launches += 2;
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_err(err, e, "tree build");
     s->prepared = true;
@@ -1484,10 +1513,12 @@ EvalArgs make_args(TreeState* s, const DevTables& t, const GridD& g, const Phys&
     a.n = (int)t.n;
     a.srcf = s->srcf;
     a.ljs = s->ljs;
-    a.far_off = s->far_off;
+    a.far_cnt = s->far_cnt;
     a.far_ent = s->far_ent;
-    a.near_off = s->near_off;
+    a.near_cnt = s->near_cnt;
     a.near_ent = s->near_ent;
+    a.far_cap = s->cap_far;
+    a.near_cap = s->cap_near;
     a.far = s->far;
     a.o = out;
     a.err = t.err;
@@ -1583,9 +1614,8 @@ void tree_destroy(TreeState* s) {
     cudaFree(s->far);
     cudaFree(s->ljs);
     cudaFree(s->far_cnt);
-    cudaFree(s->far_off);
     cudaFree(s->near_cnt);
-    cudaFree(s->near_off);
+    cudaFree(s->prox_items);
     cudaFree(s->far_ent);
     cudaFree(s->near_ent);
     cudaFree(s->cell_start);
@@ -1695,18 +1725,17 @@ rism_status tree_post(TreeState* s, rism_info& info, bool& retry, std::string& e
     retry = false;
     if (m.overflow) {
         bool grew = false;
-        if (m.far_total + 1024 > s->cap_far) {
-            const int want = m.far_total + m.far_total / 4 + 1024;
-            cudaError_t e = regrow(s->far_ent, (size_t)want);
-            if (e != cudaSuccess) return cuda_err(err, e, "far list");
-            s->cap_far = want;
+        auto pow2 = [](int v) {
+            int p = 1;
+            while (p < v) p <<= 1;
+            return p;
+        };
+        if (m.far_need > s->cap_far && m.far_need < (1 << 20)) {
+            s->cap_far = pow2(m.far_need);
             grew = true;
         }
-        if (m.near_total + 1024 > s->cap_near) {
-            const int want = m.near_total + m.near_total / 4 + 1024;
-            cudaError_t e = regrow(s->near_ent, (size_t)want);
-            if (e != cudaSuccess) return cuda_err(err, e, "near list");
-            s->cap_near = want;
+        if (m.near_need > s->cap_near && m.near_need < (1 << 20)) {
+            s->cap_near = pow2(m.near_need);
             grew = true;
         }
         if (grew) {
@@ -1715,7 +1744,7 @@ rism_status tree_post(TreeState* s, rism_info& info, bool& retry, std::string& e
             retry = true;
             return RISM_OK;
         }
-        err = "tree node, proxy or traversal capacity exceeded";
+        err = "tree node, proxy or traversal capacity exceeded (a leaf size this small needs a larger frontier)";
         return RISM_E_NOMEM;
     }
     info.tree_nodes = m.nnodes;
