@@ -112,20 +112,28 @@ def _peaks():
     return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "sm_max_mhz": 2070.0}, "fallback"
 
 
-# FP32-pipe operations of one (grid point, atom) evaluation of the fused
-# FP32 kernels, counted from the loop bodies (FFMA = 2 flops):
-#   far field Phi1 + Phik: dx 2 FADD, d^2 1 FFMA, q/d 1 FMUL, Phi1 1 FADD, d 1 FMUL, -kappa d 1 FMUL,
-#                          Phik 1 FFMA                                     -> 10 flops (+2 MUFU)
-#   LJ, per site within the cut-off test: 2 FFMA + shared 2 FMUL (r^-6)  -> 4 per site + 2
+# Algorithmic work of one far-field (grid point, source) pair of k_far32,
+# counted from its loop body: dx 2 FADD, d^2 1 FFMA, q/d 1 FMUL, Phi1 1 FADD,
+# d = d^2/d 1 FMUL, -kappa d 1 FMUL, Phik 1 FFMA -> 10 flops (FFMA = 2),
+# 8 FP32-pipe instructions and 2 MUFU (rsqrt, ex2) -> 10 instructions.
+# The direct kernels add the LJ terms: per site 2 FFMA + a shared 2 FMUL.
 FLOPS_FAR = 10
+INSTR_FAR = 10
 FLOPS_LJ_SITE = 4
 FLOPS_LJ_SHARED = 2
 FP32_LANES_PER_SM = 128
 SMS = 152
+# DRAM bytes per k_far32 launch on this workload, from the ncu capture summarised in
+# profiles/k_far32_globule2000_128cubed.md (dram__bytes_read.sum + dram__bytes_write.sum).
+FAR_TRAFFIC_BYTES = None
 
 
 def _alu_peak_tflops(sm_mhz):
     return SMS * FP32_LANES_PER_SM * 2 * sm_mhz * 1e6 / 1e12
+
+
+def _issue_peak_tinst(sm_mhz):
+    return SMS * 4 * 32 * sm_mhz * 1e6 / 1e12
 
 
 def run_gpu(args):
@@ -167,7 +175,7 @@ def run_gpu(args):
         dist.barrier()
     clocks = Clocks(torch.cuda.current_device())
     clocks.start()
-    times, evals, launches = [], [], 0
+    times, evals, launches, far_ms, near_ms = [], [], 0, [], []
     torch.cuda.synchronize()
     t_wall0 = time.perf_counter()
     for _ in range(args.steps):
@@ -180,6 +188,9 @@ def run_gpu(args):
         times.append(e0.elapsed_time(e1))
         inf = r.info()
         evals.append(inf["eval_ms"])
+        if inf["far_ms"] > 0:
+            far_ms.append(inf["far_ms"])
+            near_ms.append(inf["near_ms"])
         launches += inf["launches"]
     torch.cuda.synchronize()
     t_wall = time.perf_counter() - t_wall0
@@ -233,28 +244,46 @@ def run_gpu(args):
             g = out[k].reshape(S, -1)[:, torch.as_tensor(idx, device="cuda")].cpu().numpy()
             acc[k] = float(np.linalg.norm(g - ref[k]) / np.linalg.norm(ref[k]))
 
-    # roofline of the evaluation kernel (ALU bound: FP32 pipe)
+    # roofline of the dominant kernel: the far field (k_far32), ALU bound
     inf = r.info()
     peaks, src = _peaks()
-    eval_ms = sum(evals) / len(evals) if evals else 0.0
     pairs_far = inf["direct_pairs"] + inf["proxy_pairs"]
-    lj_pairs = inf["near_pairs"] if method == R.METHOD_TREECODE else inf["direct_pairs"]
-    flops = pairs_far * FLOPS_FAR + lj_pairs * (FLOPS_LJ_SHARED + FLOPS_LJ_SITE * S)
     sm_mhz = peaks.get("sm_max_mhz", 2070.0)
+    if method == R.METHOD_TREECODE and far_ms:
+        kern_ms = sum(far_ms) / len(far_ms)
+        flops = pairs_far * FLOPS_FAR
+        instr = pairs_far * INSTR_FAR
+        kname = "k_far32 (far field: Phi1, Phik over far lists)"
+    else:
+        kern_ms = sum(evals) / len(evals) if evals else 0.0
+        flops = pairs_far * (FLOPS_FAR + FLOPS_LJ_SHARED + FLOPS_LJ_SITE * S)
+        instr = None
+        kname = "k_direct32 / k_direct64 (whole direct sum)"
     peak = _alu_peak_tflops(sm_mhz)
-    achieved = flops / (eval_ms * 1e-3) / 1e12 if eval_ms > 0 else None
+    achieved = flops / (kern_ms * 1e-3) / 1e12 if kern_ms > 0 else None
     roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-            "frac": (achieved / peak) if achieved else None, "traffic": None,
-            "kernel": "eval (fused far field + near field + epilogue)",
-            "peak_source": f"FP32 FMA pipe: {SMS} SMs x {FP32_LANES_PER_SM} lanes x 2 flops x {sm_mhz:.0f} MHz "
-                           f"(sm_max_mhz from MEASURED_PEAKS.json, {src})",
-            "kernel_ms": eval_ms, "flops_per_launch": flops}
+            "frac": (achieved / peak) if achieved else None,
+            "traffic": FAR_TRAFFIC_BYTES if method == R.METHOD_TREECODE else None,
+            "kernel": kname, "kernel_ms": kern_ms, "flops_per_launch": flops,
+            "peak_source": f"FP32 FMA pipe of measured sm_max_mhz: {SMS} SMs x {FP32_LANES_PER_SM} lanes x 2 flops x "
+                           f"{sm_mhz:.0f} MHz ({src}); {FLOPS_FAR} algorithmic flops per far pair (FFMA = 2)"}
+    roof_issue = None
+    if instr is not None and kern_ms > 0:
+        ipk = _issue_peak_tinst(sm_mhz)
+        ach = instr / (kern_ms * 1e-3) / 1e12
+        roof_issue = {"bound": "alu-issue", "achieved": ach, "peak": ipk, "unit": "Tinst/s", "frac": ach / ipk,
+                      "note": f"{INSTR_FAR} algorithmic instructions per far pair (8 FP32-pipe + 2 MUFU) against "
+                              f"{SMS} SMs x 4 schedulers x 32 lanes x clock"}
+    timing = {"step_ms": ms, "far_ms": (sum(far_ms) / len(far_ms)) if far_ms else None,
+              "near_ms": (sum(near_ms) / len(near_ms)) if near_ms else None,
+              "eval_ms": sum(evals) / len(evals) if evals else None}
     res = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
            "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
            "vs_baseline": None, "dtype": "f32 pair terms, f64 accumulate/output" if prec == R.PREC_FP32 else "f64",
            "data": "synthetic (seeded globule, protein density)",
            "config": _config(w, args.method, args.precision), "e2e": e2e, "gpu_launches": launches,
-           "clocks": ck, "roofline": roof, "error_vs_fp64_oracle_rel_l2": acc,
+           "clocks": ck, "roofline": roof, "roofline_issue": roof_issue, "timing": timing,
+           "error_vs_fp64_oracle_rel_l2": acc,
            "counts": {k: inf[k] for k in ("direct_pairs", "proxy_pairs", "near_pairs", "tree_nodes",
                                             "tree_proxied", "tree_leaves")},
            "wall_s": t_wall}
@@ -346,6 +375,186 @@ def run_reference(args):
                       "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}))
 
 
+# ------------------------------------------------------------------ suites
+# Measurements of the other workloads of the benchmark plan (not the default line).
+
+def _events_ms(fn, reps=3):
+    import torch
+
+    st = torch.cuda.current_stream()
+    ts = []
+    for _ in range(reps):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record(st)
+        fn()
+        e1.record(st)
+        torch.cuda.synchronize()
+        ts.append(e0.elapsed_time(e1))
+    return min(ts)
+
+
+def _rel(a, b):
+    import numpy as np
+
+    return float(np.linalg.norm(a - b) / np.linalg.norm(b))
+
+
+def suite_pareto(args):
+    """13,600-atom prolate ellipsoid, 224x192x160 grid: FP64 direct vs FP32 direct vs FP32 treecode at
+    degrees 4, 6, 8 and theta 0.5..0.8 (time per initialization, error vs the FP64 oracle at sampled points)."""
+    import numpy as np
+    import torch
+
+    from oracle import oracle as O
+    from paper_2109_09772_gb300 import build as B
+    from paper_2109_09772_gb300 import inputs as I
+    from paper_2109_09772_gb300 import rism as R
+
+    B.build()
+    torch.cuda.set_device(0)
+    w = I.workload(2)
+    S, M = w.solvent.nsite, w.grid.npts
+    rng = np.random.default_rng(5)
+    idx = np.union1d(I.sample_indices(M, 3000, seed=6), rng.choice(M, 0, replace=False))
+    ref = O.fields(O.Problem.from_workload(w), idx=idx)
+    tidx = torch.as_tensor(idx, device="cuda")
+
+    def run(**opts):
+        r = R.from_workload(w, **opts)
+        out = r.init()
+        torch.cuda.synchronize()
+        xyz, q, sg, ep = w.solute.xyz, w.solute.q, w.solute.sigma, w.solute.eps
+
+        def step():
+            r.set_solute(xyz, q, sg, ep)
+            r.init(out=out)
+
+        ms = _events_ms(step, reps=args.reps)
+        err = {k: _rel(out[k].reshape(S, -1)[:, tidx].cpu().numpy(), ref[k]) for k in ("u", "c", "h")}
+        info = r.info()
+        r.close()
+        return ms, err, info
+
+    ms64, e64, _ = run(method=R.METHOD_DIRECT, precision=R.PREC_FP64)
+    print(json.dumps({"suite": "pareto", "workload": "ellipsoid13600_224x192x160", "method": "direct",
+                      "precision": "fp64", "ms": ms64, "gpts_site_s": S * M / (ms64 * 1e-3) / 1e9, "err": e64}),
+          flush=True)
+    ms32, e32, _ = run(method=R.METHOD_DIRECT, precision=R.PREC_FP32)
+    print(json.dumps({"suite": "pareto", "method": "direct", "precision": "fp32", "ms": ms32,
+                      "speedup_vs_fp64_direct": ms64 / ms32, "err": e32}), flush=True)
+    for deg in (4, 6, 8):
+        for th in (0.5, 0.6, 0.7, 0.8):
+            ms, e, info = run(method=R.METHOD_TREECODE, precision=R.PREC_FP32, degree=deg, theta=th, autotune=1)
+            print(json.dumps({"suite": "pareto", "method": "treecode", "precision": "fp32", "degree": deg,
+                              "theta": th, "ms": ms, "speedup_vs_fp64_direct": ms64 / ms,
+                              "gpts_site_s": S * M / (ms * 1e-3) / 1e9, "err": e,
+                              "direct_pairs": info["direct_pairs"], "proxy_pairs": info["proxy_pairs"],
+                              "near_pairs": info["near_pairs"], "variant": info["kernel_variant"]}), flush=True)
+
+
+def suite_batched(args):
+    """32 solutes, 500..8,000 atoms (log-uniform), own grids: one graph-captured persistent launch against 32
+    sequential treecode initializations."""
+    import numpy as np
+    import torch
+
+    from oracle import oracle as O
+    from paper_2109_09772_gb300 import build as B
+    from paper_2109_09772_gb300 import inputs as I
+    from paper_2109_09772_gb300 import rism as R
+
+    B.build()
+    torch.cuda.set_device(0)
+    ws = I.batch_workloads(count=32, seed=0)
+    rs = [R.from_workload(w, method=R.METHOD_TREECODE, precision=R.PREC_FP32) for w in ws]
+    outs = [r.init() for r in rs]
+    torch.cuda.synchronize()
+
+    def seq():
+        for r, o in zip(rs, outs):
+            r.set_solute(*(getattr(r, "_sol")))
+            r.init(out=o)
+
+    for r, w in zip(rs, ws):
+        r._sol = (w.solute.xyz, w.solute.q, w.solute.sigma, w.solute.eps)
+    ms_seq = _events_ms(seq, reps=args.reps)
+    R.potential_batched(rs)  # capture
+    torch.cuda.synchronize()
+    bouts = [None]
+
+    def bat():
+        for r in rs:
+            r.set_solute(*r._sol)
+        bouts[0] = R.potential_batched(rs)
+
+    ms_bat = _events_ms(bat, reps=args.reps)
+    pts = sum(w.solvent.nsite * w.grid.npts for w in ws)
+    # parity of the batched outputs on three solutes (sampled points)
+    errs = []
+    for k in (0, 15, 31):
+        w = ws[k]
+        idx = I.sample_indices(w.grid.npts, 1000, seed=k)
+        ref = O.fields(O.Problem.from_workload(w), idx=idx)
+        o = bouts[0][k]
+        errs.append({f: _rel(o[f].reshape(w.solvent.nsite, -1)[:, torch.as_tensor(idx, device="cuda")].cpu().numpy(),
+                             ref[f]) for f in ("u", "c", "h")})
+    print(json.dumps({"suite": "batched", "solutes": len(ws), "atoms": [w.solute.n for w in ws],
+                      "grids": [w.grid.n[0] for w in ws], "ms_sequential": ms_seq, "ms_batched_graph": ms_bat,
+                      "speedup": ms_seq / ms_bat, "gpts_site_s_batched": pts / (ms_bat * 1e-3) / 1e9,
+                      "err_sampled": errs}), flush=True)
+    for r in rs:
+        r.close()
+
+
+def suite_adjoint(args):
+    """55,000 atoms (four stacked ellipsoids), 320x320x384 grid: forward u + c with FP32 pairs and the
+    backward pass for a smooth seeded cotangent (correlation length 3 A, amplitude 0.5) used for both u and c;
+    gradients of sampled atoms against the FP64 oracle."""
+    import numpy as np
+    import torch
+
+    from oracle import oracle as O
+    from paper_2109_09772_gb300 import build as B
+    from paper_2109_09772_gb300 import inputs as I
+    from paper_2109_09772_gb300 import rism as R
+
+    B.build()
+    torch.cuda.set_device(0)
+    w = I.workload(4)
+    nx, ny, nz = w.grid.n
+    S = w.solvent.nsite
+    G = np.stack([I.gaussian_random_field((nz, ny, nx), w.grid.h, 700 + s, corr_len=3.0, amplitude=0.5)
+                  for s in range(S)])
+    Gd = torch.as_tensor(G, device="cuda")
+    r = R.from_workload(w, method=R.METHOD_TREECODE, precision=R.PREC_FP32)
+    out = {"u": r.empty_grid(), "c": r.empty_grid()}
+    r.init(u=True, c=True, h=False, out=out)
+    sol = (w.solute.xyz, w.solute.q, w.solute.sigma, w.solute.eps)
+
+    def fwd():
+        r.set_solute(*sol)
+        r.init(u=True, c=True, h=False, out=out)
+
+    ms_fwd = _events_ms(fwd, reps=args.reps)
+    g = r.backward(Gd, Gd, None)
+    torch.cuda.synchronize()
+    ms_bwd = _events_ms(lambda: r.backward(Gd, Gd, None), reps=max(1, args.reps - 1))
+    atoms = np.sort(np.random.default_rng(64).choice(w.solute.n, args.adj_atoms, replace=False))
+    t0 = time.perf_counter()
+    ref = O.grad(O.Problem.from_workload(w), atoms, G, G, None)
+    t_or = time.perf_counter() - t0
+    gg = {k: v.cpu().numpy() for k, v in g.items()}
+    err = {"xyz": _rel(gg["xyz"][atoms], ref[:, 0:3]), "q": _rel(gg["q"][atoms], ref[:, 3]),
+           "sigma": _rel(gg["sigma"][atoms], ref[:, 4]), "eps": _rel(gg["eps"][atoms], ref[:, 5])}
+    pairs = w.solute.n * w.grid.npts
+    print(json.dumps({"suite": "adjoint", "workload": "stack55000_320x320x384", "ms_forward_u_c": ms_fwd,
+                      "ms_backward": ms_bwd, "backward_pairs_per_s": pairs / (ms_bwd * 1e-3),
+                      "atoms_checked": int(atoms.size), "grad_rel_l2_vs_oracle": err,
+                      "oracle_seconds": t_or}), flush=True)
+    r.close()
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -359,7 +568,13 @@ def main():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-fp64", action="store_true")
     ap.add_argument("--no-check", action="store_true")
+    ap.add_argument("--suite", default=None, choices=["pareto", "batched", "adjoint"])
+    ap.add_argument("--reps", type=int, default=3)
+    ap.add_argument("--adj-atoms", type=int, default=16)
     args = ap.parse_args()
+    if args.suite:
+        {"pareto": suite_pareto, "batched": suite_batched, "adjoint": suite_adjoint}[args.suite](args)
+        return
     if args.warmup < 3:
         args.warmup = 3
     if args.impl == "reference":

@@ -120,7 +120,8 @@ typedef struct {
     int32_t batch[3];      /* target batch dims in use */
     int32_t kernel_variant;/* launch shape chosen (autotuner or default) */
     int32_t launches;      /* kernels launched by the last compute call */
-    float eval_ms;         /* CUDA-event duration of the last evaluation kernel (debug_flags bit 1), else 0 */
+    float eval_ms;         /* CUDA-event duration of the last evaluation kernel(s) (debug_flags bit 1), else 0 */
+    float far_ms, near_ms; /* treecode: the far-field and the near-field + epilogue kernels (debug_flags bit 1) */
 } rism_info;
 
 /* Fill *o with the defaults listed above.  Never fails. */

@@ -408,7 +408,7 @@ rism_status rism_init(rism_ctx* c, double* u, double* c_lr, double* h_lr, double
                 }
             if (st == RISM_OK) st = check_device_error(c);
             if (st == RISM_OK) st = tree_post(c->tree, c->info, retry, c->err);
-            if (st == RISM_OK && retry) st = fail(c, RISM_E_NOMEM, "far list kept growing");
+            if (st == RISM_OK && retry) st = fail(c, RISM_E_NOMEM, "list slots kept growing (" + c->err + ")");
         }
     }
     if (st == RISM_OK && (c->o.debug_flags & 2) && c->ev[0] && (o.u || o.c || o.h))

@@ -68,9 +68,11 @@ struct Node {
 
 struct TreeMeta {
     int nnodes, nprox, nitems, nleaves;
-    int overflow;          // capacity exceeded (nodes / items / far list)
+    int overflow;          // any capacity exceeded (nodes, proxies, items, list slots, frontier)
+    int build_overflow;    // the tree itself is incomplete (nodes, proxies, items)
     int far_need;          // largest far list of a batch (entries)
     int near_need;         // largest near list of a batch (entries)
+    int wide;              // a traversal frontier exceeded kQCap
     int lc;                // cell level of the near field
     int bmin[3], bmax[3];  // atom bounds, order-preserving int encoding of the FP32 grid-unit positions
     int rc2max;            // largest per-pair LJ cut-off squared (grid units, FP32 bits; +inf without cut-off)
@@ -406,6 +408,7 @@ __global__ void __launch_bounds__(kSortThreads) k_sort_build(BuildArgs a, uint32
         meta->nitems = s_items;
         meta->nleaves = s_leaves;
         meta->overflow = s_overflow;
+        meta->build_overflow = s_overflow;
         prox_items[s_prox] = s_items;
     }
     __syncthreads();
@@ -494,7 +497,7 @@ __global__ void k_upward(int deg, const TreeMeta* meta, const Node* nodes, const
     const int np = deg + 1, P3 = np * np * np;
     double* qs = Ls + kChunk * 3 * np;
     double* tn = qs + kChunk;
-    if (meta->overflow) return;
+    if (meta->build_overflow) return;
     const int nitems = meta->nitems;
     for (int it = blockIdx.x; it < nitems; it += gridDim.x) {
         const int k = items[2 * it], b = items[2 * it + 1];
@@ -550,7 +553,7 @@ __global__ void k_proxy_reduce(int deg, int n, const TreeMeta* meta, const Node*
                                const int* prox_items, const double* part, Geo* src, SrcF* srcf) {
     __shared__ double tn[3 * (kMaxDegree + 1)];
     const int np = deg + 1, P3 = np * np * np;
-    if (meta->overflow) return;
+    if (meta->build_overflow) return;
     const int nprox = meta->nprox;
     const int nblk = (P3 + blockDim.x - 1) / blockDim.x;
     for (int wi = blockIdx.x; wi < nprox * nblk; wi += gridDim.x) {
@@ -584,8 +587,8 @@ __host__ __device__ constexpr ShapeDesc shape_of(int v) {
     return v == 1 ? ShapeDesc{16, 8, 8, 8} : (v == 2 ? ShapeDesc{8, 8, 8, 8} : ShapeDesc{8, 8, 8, 4});
 }
 
-constexpr int kQCap = 1024;        // frontier capacity of the warp-cooperative traversal
-constexpr int kListWarps = 4;      // warps (batches) per list-building CTA
+constexpr int kQCap = 2048;        // frontier capacity of the warp-cooperative traversal (nodes of one level)
+constexpr int kListWarps = 2;      // warps (batches) per list-building CTA
 
 struct ListArgs {
     int nbx, nby, nbz;        // batches per axis
@@ -618,7 +621,7 @@ __global__ void __launch_bounds__(32 * kListWarps) k_far_lists(ListArgs a, const
     __shared__ int qa[kListWarps][kQCap], qb[kListWarps][kQCap];
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     const int nb = a.nbx * a.nby * a.nbz;
-    const bool tree_ok = !meta->overflow;
+    const bool tree_ok = !meta->build_overflow;
     const long long pts = (long long)a.bx * a.by * a.bz;
     for (int b = blockIdx.x * kListWarps + w; b < nb; b += gridDim.x * kListWarps) {
         double cb[3], rb;
@@ -691,7 +694,7 @@ __global__ void __launch_bounds__(32 * kListWarps) k_far_lists(ListArgs a, const
                 // the frontier of this batch does not fit: a node or leaf-size setting beyond this build
                 if (lane == 0) {
                     meta->overflow = 1;
-                    atomicMax(&meta->far_need, 1 << 30);
+                    meta->wide = 1;
                 }
                 break;
             }
@@ -729,7 +732,7 @@ __global__ void __launch_bounds__(32 * kListWarps) k_near_lists(ListArgs a, cons
     // 0.01 grid units of slack: Morton codes are computed in FP32, so an atom may sit ~1e-5 outside its cell box
     const double rn = isfinite(rnear) ? rnear + 0.01 : 1e30;
     const double rn2 = rn * rn;
-    const bool tree_ok = !meta->overflow;
+    const bool tree_ok = !meta->build_overflow;
     const long long pts = (long long)a.bx * a.by * a.bz;
     for (int b = blockIdx.x * kListWarps + w; b < nb; b += gridDim.x * kListWarps) {
         double cb[3], rb;
@@ -791,6 +794,8 @@ __global__ void __launch_bounds__(32 * kListWarps) k_near_lists(ListArgs a, cons
 __global__ void k_reset_meta(TreeMeta* meta) {
     meta->direct_pairs = meta->proxy_pairs = meta->near_pairs = 0ull;
     meta->far_need = meta->near_need = 0;
+    meta->wide = 0;
+    meta->build_overflow = 0;
     meta->overflow = 0;
     meta->nnodes = meta->nprox = meta->nitems = meta->nleaves = 0;
     meta->lc = 0;
@@ -1303,10 +1308,9 @@ cudaError_t dispatch_v(int op, bool du, bool dh, const EvalArgs* a, int nb, cons
                        cudaStream_t st) {
     auto go = [&](auto k) {
         using K = decltype(k);
-        if (op == 0) {
-            K::far(*a, nb, st);
-            K::near(*a, nb, st);
-        } else {
+        if (op == 0 || op == 2) K::far(*a, nb, st);
+        if (op == 0 || op == 3) K::near(*a, nb, st);
+        if (op == 1) {
             K::far_b(*be, sms * std::max(1, K::occ_far()), st);
             BatchEval b2 = *be;
             b2.queue = be->queue + 1;
@@ -1372,6 +1376,8 @@ struct TreeState {
     bool prepared = false;
     std::string tuned_key;       // problem class the current (variant, leaf) was tuned for
     BatchCache* bc = nullptr;
+    cudaEvent_t ev[3] = {nullptr, nullptr, nullptr};  // far / near timing (debug_flags bit 1)
+    bool timed = false;
 };
 
 namespace {
@@ -1601,6 +1607,8 @@ struct BatchCache {
 void tree_destroy(TreeState* s) {
     if (!s) return;
     delete s->bc;
+    for (int k = 0; k < 3; ++k)
+        if (s->ev[k]) cudaEventDestroy(s->ev[k]);
     cudaFree(s->code);
     cudaFree(s->idx);
     cudaFree(s->code2);
@@ -1656,28 +1664,49 @@ static rism_status tree_autotune(TreeState* s, const DevTables& t, const GridD& 
     int bv = 0, bl = o.leaf;
     const int leaves[2] = {o.leaf, o.leaf >= 64 ? o.leaf / 2 : o.leaf * 2};
     for (int v = 0; v < kNumShapes; ++v)
-        for (int li = 0; li < 2; ++li) {
-            s->variant = v;
-            s->leaf = leaves[li];
-            rism_status r = tree_reserve(s, t, g, o, err);
-            if (r != RISM_OK) return r;
-            cudaEventRecord(e0, st);
-            r = tree_enqueue(s, t, g, ph, o, st, err);
-            if (r != RISM_OK) return r;
-            EvalArgs a = make_args(s, t, g, ph, o, out);
-            dispatch(t.smax, v, 0, out.u != nullptr, out.h != nullptr, &a, s->nb, nullptr, 0, st);
-            cudaEventRecord(e1, st);
-            cudaMemcpyAsync(s->h_meta, s->meta, sizeof(TreeMeta), cudaMemcpyDeviceToHost, st);
-            cudaError_t ce = cudaStreamSynchronize(st);
-            if (ce != cudaSuccess) return cuda_err(err, ce, "autotune");
-            float ms = 0.f;
-            cudaEventElapsedTime(&ms, e0, e1);
-            if (!s->h_meta->overflow && ms < best) {
-                best = ms;
-                bv = v;
-                bl = leaves[li];
+        for (int li = 0; li < 2; ++li)
+            for (int attempt = 0; attempt < 2; ++attempt) {
+                s->variant = v;
+                s->leaf = leaves[li];
+                rism_status r = tree_reserve(s, t, g, o, err);
+                if (r != RISM_OK) return r;
+                cudaEventRecord(e0, st);
+                r = tree_enqueue(s, t, g, ph, o, st, err);
+                if (r != RISM_OK) return r;
+                EvalArgs a = make_args(s, t, g, ph, o, out);
+                dispatch(t.smax, v, 0, out.u != nullptr, out.h != nullptr, &a, s->nb, nullptr, 0, st);
+                cudaEventRecord(e1, st);
+                cudaMemcpyAsync(s->h_meta, s->meta, sizeof(TreeMeta), cudaMemcpyDeviceToHost, st);
+                cudaError_t ce = cudaStreamSynchronize(st);
+                if (ce != cudaSuccess) return cuda_err(err, ce, "autotune");
+                const TreeMeta& m = *s->h_meta;
+                if (m.overflow) {
+                    // grow the per-batch list slots and time this candidate again
+                    bool grew = false;
+                    int p2 = 1;
+                    if (!m.wide && m.far_need > s->cap_far) {
+                        while (p2 < m.far_need) p2 <<= 1;
+                        s->cap_far = p2;
+                        grew = true;
+                    }
+                    p2 = 1;
+                    if (!m.wide && m.near_need > s->cap_near) {
+                        while (p2 < m.near_need) p2 <<= 1;
+                        s->cap_near = p2;
+                        grew = true;
+                    }
+                    if (grew && !m.build_overflow) continue;
+                    break;  // too wide or too deep for this leaf size: skip the candidate
+                }
+                float ms = 0.f;
+                cudaEventElapsedTime(&ms, e0, e1);
+                if (ms < best) {
+                    best = ms;
+                    bv = v;
+                    bl = leaves[li];
+                }
+                break;
             }
-        }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     s->variant = bv;
@@ -1705,7 +1734,20 @@ rism_status tree_eval(TreeState* s, const DevTables& t, const GridD& g, const Ph
         if (r != RISM_OK) return r;
     }
     EvalArgs a = make_args(s, t, g, ph, o, out);
-    cudaError_t e = dispatch(t.smax, s->variant, 0, out.u != nullptr, out.h != nullptr, &a, s->nb, nullptr, 0, st);
+    const bool du = out.u != nullptr, dh = out.h != nullptr;
+    cudaError_t e;
+    s->timed = (o.debug_flags & 2) != 0;
+    if (s->timed) {
+        for (int k = 0; k < 3; ++k)
+            if (!s->ev[k]) cudaEventCreate(&s->ev[k]);
+        cudaEventRecord(s->ev[0], st);
+        e = dispatch(t.smax, s->variant, 2, du, dh, &a, s->nb, nullptr, 0, st);
+        cudaEventRecord(s->ev[1], st);
+        if (e == cudaSuccess) e = dispatch(t.smax, s->variant, 3, du, dh, &a, s->nb, nullptr, 0, st);
+        cudaEventRecord(s->ev[2], st);
+    } else {
+        e = dispatch(t.smax, s->variant, 0, du, dh, &a, s->nb, nullptr, 0, st);
+    }
     if (e != cudaSuccess) return cuda_err(err, e, "tree eval");
     if ((e = cudaMemcpyAsync(s->h_meta, s->meta, sizeof(TreeMeta), cudaMemcpyDeviceToHost, st)) != cudaSuccess)
         return cuda_err(err, e, "tree meta copy");
@@ -1723,6 +1765,14 @@ rism_status tree_eval(TreeState* s, const DevTables& t, const GridD& g, const Ph
 rism_status tree_post(TreeState* s, rism_info& info, bool& retry, std::string& err) {
     const TreeMeta& m = *s->h_meta;
     retry = false;
+    if (m.overflow && m.wide) {
+        err = "an octree level is wider than the list builder's frontier (2048 nodes); use a larger leaf size";
+        return RISM_E_NOMEM;
+    }
+    if (m.build_overflow) {
+        err = "tree node, proxy or upward-item capacity exceeded";
+        return RISM_E_NOMEM;
+    }
     if (m.overflow) {
         bool grew = false;
         auto pow2 = [](int v) {
@@ -1742,10 +1792,19 @@ rism_status tree_post(TreeState* s, rism_info& info, bool& retry, std::string& e
             delete s->bc;  // buffers moved: the captured graph is stale
             s->bc = nullptr;
             retry = true;
+            char buf[160];
+            std::snprintf(buf, sizeof buf, "list slots grown: far need %d -> cap %d, near need %d -> cap %d",
+                          m.far_need, s->cap_far, m.near_need, s->cap_near);
+            err = buf;
             return RISM_OK;
         }
-        err = "tree node, proxy or traversal capacity exceeded (a leaf size this small needs a larger frontier)";
+        err = "list capacity exceeded";
         return RISM_E_NOMEM;
+    }
+    info.far_ms = info.near_ms = 0.f;
+    if (s->timed && s->ev[0]) {
+        cudaEventElapsedTime(&info.far_ms, s->ev[0], s->ev[1]);
+        cudaEventElapsedTime(&info.near_ms, s->ev[1], s->ev[2]);
     }
     info.tree_nodes = m.nnodes;
     info.tree_proxied = m.nprox;

@@ -51,7 +51,7 @@ class Info(C.Structure):
                 ("nsite", C.c_int32), ("tree_nodes", C.c_int32), ("tree_proxied", C.c_int32),
                 ("tree_leaves", C.c_int32), ("direct_pairs", C.c_int64), ("proxy_pairs", C.c_int64),
                 ("near_pairs", C.c_int64), ("batch", C.c_int32 * 3), ("kernel_variant", C.c_int32),
-                ("launches", C.c_int32), ("eval_ms", C.c_float)]
+                ("launches", C.c_int32), ("eval_ms", C.c_float), ("far_ms", C.c_float), ("near_ms", C.c_float)]
 
 
 EXPORTS = ["rism_default_options", "rism_grid_create", "rism_set_solute", "rism_set_solvent", "rism_potential",
