@@ -123,9 +123,9 @@ FLOPS_LJ_SITE = 4
 FLOPS_LJ_SHARED = 2
 FP32_LANES_PER_SM = 128
 SMS = 152
-# DRAM bytes per k_far32 launch on this workload, from the ncu capture summarised in
-# profiles/k_far32_globule2000_128cubed.md (dram__bytes_read.sum + dram__bytes_write.sum).
-FAR_TRAFFIC_BYTES = None
+# DRAM bytes per k_far32 launch on this workload (dram__bytes_read.sum + dram__bytes_write.sum of one
+# ncu capture of the kernel as it stands); None when the kernel has changed since.
+FAR_TRAFFIC_BYTES = 1346048  # 1,185,792 read + 160,256 written
 
 
 def _alu_peak_tflops(sm_mhz):
@@ -323,12 +323,18 @@ def cpu_baseline(seconds=15.0, seed=0):
     w = _workload(seed)
     p = O.Problem.from_workload(w)
     cores = os.cpu_count() or 1
-    # calibrate on a small sample, then size the sample for about `seconds` of work
-    idx = I.sample_indices(w.grid.npts, 200, seed=11)
-    t0 = time.perf_counter()
-    O.fields(p, idx=idx, nthreads=cores)
-    t = max(time.perf_counter() - t0, 1e-3)
-    n = int(min(w.grid.npts, max(200, 200 * seconds / t)))
+    # calibrate: grow the sample until one run takes a second (start-up costs no longer dominate), then
+    # size the measured sample for about `seconds` of work
+    n = 2000
+    while True:
+        idx = I.sample_indices(w.grid.npts, n, seed=11)
+        t0 = time.perf_counter()
+        O.fields(p, idx=idx, nthreads=cores)
+        t = time.perf_counter() - t0
+        if t >= 1.0 or n >= w.grid.npts:
+            break
+        n = min(w.grid.npts, n * 4)
+    n = int(min(w.grid.npts, max(2000, n * seconds / max(t, 1e-3))))
     idx = I.sample_indices(w.grid.npts, n, seed=12)
     t0 = time.perf_counter()
     O.fields(p, idx=idx, nthreads=cores)
@@ -564,7 +570,7 @@ def main():
     ap.add_argument("--method", default="treecode", choices=["treecode", "direct"])
     ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64"])
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
-    ap.add_argument("--ref-points", type=int, default=4000)
+    ap.add_argument("--ref-points", type=int, default=100000)
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-fp64", action="store_true")
     ap.add_argument("--no-check", action="store_true")

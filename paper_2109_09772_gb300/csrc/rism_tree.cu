@@ -916,11 +916,13 @@ __device__ void drain(R& r, const Cursor& c, long long wlim) {
         if (c.last_phase[s] >= 0) mbar_wait_bounded(&r.full[s], (uint32_t)(c.last_phase[s] & 1), wlim);
 }
 
-// Consumer loop skeleton shared by the far and near bodies.  Returns false
-// after an abort (bounded wait ran out).
-template <int SM, bool LJ, int NWARPS, typename R, typename F>
+// Consumer loop skeleton shared by the far and near bodies: per landed tile,
+// `stage(slot, cnt)` reads the tile out of the ring (its warp then releases
+// the slot to the producer) and `consume(cnt)` works on what was staged.
+// Returns false after an abort (bounded wait ran out).
+template <int SM, bool LJ, int NWARPS, typename R, typename FS, typename FC>
 __device__ bool run_ring(R& r, Cursor& cur, const int2* ent, const SrcF* src, const LJf* ljs, const EvalArgs& a,
-                         F&& consume) {
+                         FS&& stage, FC&& consume) {
     const int tid = threadIdx.x, lane = tid & 31;
     if (tid == 0)
         for (int s = 0; s < kStages; ++s) produce<SM, LJ>(cur, r, s, ent, src, ljs);
@@ -935,9 +937,10 @@ __device__ bool run_ring(R& r, Cursor& cur, const int2* ent, const SrcF* src, co
         }
         const int cnt = r.cnt[slot];
         if (cnt == 0) return true;
-        consume(slot, cnt);
+        stage(slot, cnt);
         __syncwarp();
         if (lane == 0) mbar_arrive(&r.empty[slot]);
+        consume(cnt);
         if (tid == 0 && !cur.done) {
             if (!mbar_wait_bounded(&r.empty[slot], ph, a.wlim)) {
                 r.abort = 1;
@@ -955,19 +958,91 @@ struct FarShape {
     static constexpr int TX = NXB / PF, NT = TX * NYB * NZB, NW = NT / 32;
 };
 
+// One tile re-staged per warp as source pairs: record l holds sources 2l and 2l+1, field by field, so that a
+// 16-byte shared load yields two-wide operands (x_hi of both, x_lo of both, ...).  An odd count is padded with
+// a zero charge 10^6 grid units away, whose terms are exactly zero.
+struct PairRec {
+    float4 x;  // xh0, xh1, xl0, xl1
+    float4 y;  // yh0, yh1, yl0, yl1
+    float4 z;  // zh0, zh1, zl0, zl1
+    float4 q;  // q0, q1, 0, 0
+};
+constexpr int kPairs = kT / 2;
+constexpr float kPadPos = 1.0e6f;
+
+// Writes the pair records of one tile (lane l: sources 2l, 2l+1); returns whether any source of the tile sits
+// on a lattice point (warp-uniform).
+__device__ __forceinline__ bool stage_pairs(const SrcF* __restrict__ Sx, int cnt, PairRec* wp, int lane) {
+    bool on = false;
+    if (2 * lane < cnt) {
+        const float4 a0 = *reinterpret_cast<const float4*>(&Sx[2 * lane].xh);
+        const float4 a1 = *reinterpret_cast<const float4*>(&Sx[2 * lane].xl);
+        float4 b0 = make_float4(kPadPos, kPadPos, kPadPos, 0.f), b1 = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (2 * lane + 1 < cnt) {
+            b0 = *reinterpret_cast<const float4*>(&Sx[2 * lane + 1].xh);
+            b1 = *reinterpret_cast<const float4*>(&Sx[2 * lane + 1].xl);
+        }
+        PairRec& o = wp[lane];
+        o.x = make_float4(a0.x, b0.x, a1.x, b1.x);
+        o.y = make_float4(a0.y, b0.y, a1.y, b1.y);
+        o.z = make_float4(a0.z, b0.z, a1.z, b1.z);
+        o.q = make_float4(a0.w, b0.w, 0.f, 0.f);
+        on = a1.w != 0.f || b1.w != 0.f;
+    }
+    return __any_sync(0xffffffffu, on);
+}
+
+// The pair loop of the far field: two sources per two-wide instruction, P points per thread along x.  Per pair
+// and point the arithmetic is the scalar sequence dx = (x - x_hi) - x_lo, d2 = fma(dx, dx, dy^2 + dz^2),
+// r = rsqrt(d2), qr = q r, Phi1 += qr, Phik = fma(qr, 2^(k (d2 r)), Phik).  ON: some source of the tile is on
+// a lattice point, so the coincident pair (d2 = 0) is dropped here and left to the near field (d = 0 limit).
+template <int P, bool DH, bool ON>
+__device__ __forceinline__ void far_pairs(const PairRec* wp, int np, const f32x2 (&GX)[P], f32x2 FY, f32x2 FZ,
+                                          f32x2 K2, f32x2 (&P1)[P], f32x2 (&PK)[P]) {
+    for (int l = 0; l < np; ++l) {
+        const ulonglong2 X = *reinterpret_cast<const ulonglong2*>(&wp[l].x);
+        const ulonglong2 Y = *reinterpret_cast<const ulonglong2*>(&wp[l].y);
+        const ulonglong2 Z = *reinterpret_cast<const ulonglong2*>(&wp[l].z);
+        const f32x2 Q = *reinterpret_cast<const f32x2*>(&wp[l].q);
+        const f32x2 DY = sub2(sub2(FY, Y.x), Y.y);
+        const f32x2 DZ = sub2(sub2(FZ, Z.x), Z.y);
+        const f32x2 DYZ = fma2(DY, DY, mul2(DZ, DZ));
+#pragma unroll
+        for (int p = 0; p < P; ++p) {
+            const f32x2 DX = sub2(sub2(GX[p], X.x), X.y);
+            const f32x2 D2 = fma2(DX, DX, DYZ);
+            const float2 d2 = up2(D2);
+            float r0 = rsqrt_approx(d2.x), r1 = rsqrt_approx(d2.y);
+            if (ON) {
+                r0 = d2.x > 0.f ? r0 : 0.f;
+                r1 = d2.y > 0.f ? r1 : 0.f;
+            }
+            const f32x2 RI = pk2(r0, r1);
+            const f32x2 QR = mul2(Q, RI);
+            P1[p] = add2(P1[p], QR);
+            if (DH) {
+                const float2 e = up2(mul2(K2, mul2(D2, RI)));
+                PK[p] = fma2(QR, pk2(ex2_approx(e.x), ex2_approx(e.y)), PK[p]);
+            }
+        }
+    }
+}
+
 template <int NXB, int NYB, int NZB, int PF, bool DH>
-__device__ void far_body(const EvalArgs& a, int b, Ring<1, false>& r) {
+__device__ void far_body(const EvalArgs& a, int b, Ring<1, false>& r, PairRec (*pairs)[kPairs]) {
     using Sh = FarShape<NXB, NYB, NZB, PF>;
     constexpr int P = PF;
-    const int tid = threadIdx.x;
+    const int tid = threadIdx.x, lane = tid & 31;
     const int tx = tid % Sh::TX, ty = (tid / Sh::TX) % NYB, tz = tid / (Sh::TX * NYB);
     const int ib = b % a.nbx, jb = (b / a.nbx) % a.nby, kb = b / (a.nbx * a.nby);
     const int i0 = ib * NXB + tx * P, j = jb * NYB + ty, k = kb * NZB + tz;
-    float gx[P];
+    f32x2 GX[P];
 #pragma unroll
-    for (int p = 0; p < P; ++p) gx[p] = (float)(i0 + p);
-    const float fy = (float)j, fz = (float)k;
+    for (int p = 0; p < P; ++p) GX[p] = pk2((float)(i0 + p), (float)(i0 + p));
+    const f32x2 FY = pk2((float)j, (float)j), FZ = pk2((float)k, (float)k);
     const float kap2 = (float)(-a.ph.kappa * a.g.h * 1.4426950408889634);  // e^{-kappa d} = 2^(kap2 d_grid)
+    const f32x2 K2 = pk2(kap2, kap2);
+    PairRec* wp = pairs[tid >> 5];
     float f1h[P], f1l[P], fkh[P], fkl[P];
 #pragma unroll
     for (int p = 0; p < P; ++p) f1h[p] = f1l[p] = fkh[p] = fkl[p] = 0.f;
@@ -983,48 +1058,32 @@ __device__ void far_body(const EvalArgs& a, int b, Ring<1, false>& r) {
         ring_init(r, Sh::NW);
     }
     __syncthreads();
-    const bool ok = run_ring<1, false, Sh::NW>(r, cur, a.far_ent, a.srcf, nullptr, a, [&](int slot, int cnt) {
-        const SrcF* Sx = r.src[slot];
-        float p1[P], pk[P];
+    bool on = false;
+    const bool ok = run_ring<1, false, Sh::NW>(
+        r, cur, a.far_ent, a.srcf, nullptr, a,
+        [&](int slot, int cnt) {
+            __syncwarp();  // the previous tile's records are no longer read
+            on = stage_pairs(r.src[slot], cnt, wp, lane);
+        },
+        [&](int cnt) {
+            f32x2 P1[P], PK[P];
 #pragma unroll
-        for (int p = 0; p < P; ++p) p1[p] = pk[p] = 0.f;
-        for (int s0 = 0; s0 < cnt; ++s0) {
-            const float4 g0 = *reinterpret_cast<const float4*>(&Sx[s0].xh);
-            const float4 g1 = *reinterpret_cast<const float4*>(&Sx[s0].xl);
-            const float dy = (fy - g0.y) - g1.y;
-            const float dz = (fz - g0.z) - g1.z;
-            const float dyz2 = fmaf(dy, dy, dz * dz);
-            if (g1.w == 0.f) {
-                // the source is off the lattice: d > 0 for every grid point
+            for (int p = 0; p < P; ++p) P1[p] = PK[p] = 0ull;  // +0.0f in both halves
+            const int np = (cnt + 1) >> 1;
+            if (!on)
+                far_pairs<P, DH, false>(wp, np, GX, FY, FZ, K2, P1, PK);
+            else
+                far_pairs<P, DH, true>(wp, np, GX, FY, FZ, K2, P1, PK);
 #pragma unroll
-                for (int p = 0; p < P; ++p) {
-                    const float dx = (gx[p] - g0.x) - g1.x;
-                    const float d2 = fmaf(dx, dx, dyz2);
-                    const float ri = rsqrt_approx(d2);
-                    const float qr = g0.w * ri;
-                    p1[p] += qr;
-                    if (DH) pk[p] = fmaf(qr, ex2_approx(kap2 * (d2 * ri)), pk[p]);
-                }
-            } else {
-                // on a lattice point: the coincident point's pair is left to the near field (d = 0 limit)
-#pragma unroll
-                for (int p = 0; p < P; ++p) {
-                    const float dx = (gx[p] - g0.x) - g1.x;
-                    const float d2 = fmaf(dx, dx, dyz2);
-                    const float rr = rsqrt_approx(d2);
-                    const float ri = d2 > 0.f ? rr : 0.f;
-                    const float qr = g0.w * ri;
-                    p1[p] += qr;
-                    if (DH) pk[p] = fmaf(qr, ex2_approx(kap2 * (d2 * ri)), pk[p]);
+            for (int p = 0; p < P; ++p) {
+                const float2 s1 = up2(P1[p]);
+                ff_add(f1h[p], f1l[p], s1.x + s1.y);
+                if (DH) {
+                    const float2 sk = up2(PK[p]);
+                    ff_add(fkh[p], fkl[p], sk.x + sk.y);
                 }
             }
-        }
-#pragma unroll
-        for (int p = 0; p < P; ++p) {
-            ff_add(f1h[p], f1l[p], p1[p]);
-            if (DH) ff_add(fkh[p], fkl[p], pk[p]);
-        }
-    });
+        });
     if (!ok) return;
     const GridD& g = a.g;
     if (j >= g.ny || k >= g.nz || i0 >= g.nx) return;
@@ -1134,7 +1193,7 @@ __device__ void near_body(const EvalArgs& a, int b, Ring<SM, true>& r) {
                 for (int s = 0; s < SM; ++s) ff_add(ljh[p][s], ljl[p][s], plj[p][s]);
             }
         }
-    });
+    }, [](int) {});
     if (!ok) return;
 
     const GridD& g = a.g;
@@ -1194,9 +1253,10 @@ __device__ void near_body(const EvalArgs& a, int b, Ring<SM, true>& r) {
 template <int NXB, int NYB, int NZB, int PF, bool DH>
 __global__ void __launch_bounds__(FarShape<NXB, NYB, NZB, PF>::NT) k_far32(EvalArgs a) {
     __shared__ Ring<1, false> r;
+    __shared__ PairRec pairs[FarShape<NXB, NYB, NZB, PF>::NW][kPairs];
     if (threadIdx.x == 0) r.inited = 0;
     if (a.meta->overflow) return;  // incomplete lists: the host grows them and runs again
-    far_body<NXB, NYB, NZB, PF, DH>(a, blockIdx.x, r);
+    far_body<NXB, NYB, NZB, PF, DH>(a, blockIdx.x, r, pairs);
 }
 
 template <int NXB, int NYB, int NZB, int SM, bool DU, bool DH>
@@ -1227,6 +1287,7 @@ __device__ __forceinline__ int find_solute(const BatchEval& be, int it) {
 template <int NXB, int NYB, int NZB, int PF, bool DH>
 __global__ void __launch_bounds__(FarShape<NXB, NYB, NZB, PF>::NT) k_far32_batched(BatchEval be) {
     __shared__ Ring<1, false> r;
+    __shared__ PairRec pairs[FarShape<NXB, NYB, NZB, PF>::NW][kPairs];
     __shared__ int s_item;
     __shared__ EvalArgs sa;
     if (threadIdx.x == 0) r.inited = 0;
@@ -1241,7 +1302,7 @@ __global__ void __launch_bounds__(FarShape<NXB, NYB, NZB, PF>::NT) k_far32_batch
         if (it >= be.total) break;
         if (sa.meta->overflow) continue;
         const int sid = find_solute(be, it);
-        far_body<NXB, NYB, NZB, PF, DH>(sa, it - be.item_off[sid], r);
+        far_body<NXB, NYB, NZB, PF, DH>(sa, it - be.item_off[sid], r, pairs);
     }
 }
 
