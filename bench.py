@@ -175,7 +175,7 @@ def run_gpu(args):
         dist.barrier()
     clocks = Clocks(torch.cuda.current_device())
     clocks.start()
-    times, evals, launches, far_ms, near_ms = [], [], 0, [], []
+    times, evals, launches, far_ms, near_ms, box_ms = [], [], 0, [], [], []
     torch.cuda.synchronize()
     t_wall0 = time.perf_counter()
     for _ in range(args.steps):
@@ -191,6 +191,7 @@ def run_gpu(args):
         if inf["far_ms"] > 0:
             far_ms.append(inf["far_ms"])
             near_ms.append(inf["near_ms"])
+            box_ms.append(inf["box_ms"])
         launches += inf["launches"]
     torch.cuda.synchronize()
     t_wall = time.perf_counter() - t_wall0
@@ -276,6 +277,7 @@ def run_gpu(args):
                               f"{SMS} SMs x 4 schedulers x 32 lanes x clock"}
     timing = {"step_ms": ms, "far_ms": (sum(far_ms) / len(far_ms)) if far_ms else None,
               "near_ms": (sum(near_ms) / len(near_ms)) if near_ms else None,
+              "box_ms": (sum(box_ms) / len(box_ms)) if box_ms else None,
               "eval_ms": sum(evals) / len(evals) if evals else None}
     res = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
            "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
@@ -284,8 +286,8 @@ def run_gpu(args):
            "config": _config(w, args.method, args.precision), "e2e": e2e, "gpu_launches": launches,
            "clocks": ck, "roofline": roof, "roofline_issue": roof_issue, "timing": timing,
            "error_vs_fp64_oracle_rel_l2": acc,
-           "counts": {k: inf[k] for k in ("direct_pairs", "proxy_pairs", "near_pairs", "tree_nodes",
-                                            "tree_proxied", "tree_leaves")},
+           "counts": {k: inf[k] for k in ("direct_pairs", "proxy_pairs", "cp_pairs", "near_pairs", "tree_nodes",
+                                            "tree_proxied", "tree_leaves", "tree_boxes", "kernel_variant")},
            "wall_s": t_wall}
     if rank == 0 and not args.no_fp64:
         # the plain FP64 direct sum on the same GPU, one timed step (the comparison of the headline)

@@ -107,6 +107,11 @@ typedef struct {
     int32_t debug_flags;/* test hooks, 0 in production.  Bit 0: the direct kernels skip their first
                            bulk copy, so its wait runs out and the call returns RISM_E_TIMEOUT.
                            Bit 1: time the evaluation kernel with CUDA events (rism_info.eval_ms). */
+    int32_t target_proxies; /* treecode: 1 (default) = grid boxes of 16^3 points and up also take (n+1)^3
+                               Chebyshev proxy targets: a cluster that meets the acceptance criterion for a
+                               box is summed at the box's proxies and reaches its grid points by
+                               interpolation (cluster-particle form, the paper's orientation of Sec. 2.3.1);
+                               0 = only the atom clusters take proxies (particle-cluster form). */
 } rism_options;
 
 typedef struct {
@@ -122,6 +127,9 @@ typedef struct {
     int32_t launches;      /* kernels launched by the last compute call */
     float eval_ms;         /* CUDA-event duration of the last evaluation kernel(s) (debug_flags bit 1), else 0 */
     float far_ms, near_ms; /* treecode: the far-field and the near-field + epilogue kernels (debug_flags bit 1) */
+    float box_ms;          /* treecode: box-level far field (proxy targets, downward pass, interpolation) */
+    int32_t tree_boxes;    /* target boxes whose proxies received at least one cluster */
+    int64_t cp_pairs;      /* (proxy target, atom) pairs of the box-level far field */
 } rism_info;
 
 /* Fill *o with the defaults listed above.  Never fails. */

@@ -226,6 +226,7 @@ void rism_default_options(rism_options* o) {
     o->r_short = 0.0;
     o->autotune = 0;
     o->wait_limit = 1LL << 26;
+    o->target_proxies = 1;
 }
 
 rism_status rism_grid_create(const rism_grid_desc* grid, const rism_options* opts, void* stream, rism_ctx** out) {
@@ -368,6 +369,9 @@ rism_status rism_init(rism_ctx* c, double* u, double* c_lr, double* h_lr, double
             c->info.direct_pairs = M * c->n;
             c->info.proxy_pairs = 0;
             c->info.near_pairs = 0;
+            c->info.cp_pairs = 0;
+            c->info.tree_boxes = 0;
+            c->info.box_ms = 0.f;
             c->info.launches += 1;
         } else {
             s = tree_eval(c->tree, c->t, c->gd, c->ph, c->o, o, c->st, c->err, c->info);
@@ -397,8 +401,9 @@ rism_status rism_init(rism_ctx* c, double* u, double* c_lr, double* h_lr, double
     if (st == RISM_OK && c->o.method == RISM_METHOD_TREECODE && (o.u || o.c || o.h)) {
         bool retry = false;
         st = tree_post(c->tree, c->info, retry, c->err);
-        if (st == RISM_OK && retry) {
-            // the far list outgrew its buffer (now enlarged): rebuild the lists and evaluate again
+        // a list outgrew its slots (now enlarged): rebuild the lists and evaluate again.  A truncated pass-down
+        // list hides the length of the lists below it, so growth can take more than one round.
+        for (int attempt = 0; attempt < 4 && st == RISM_OK && retry; ++attempt) {
             st = tree_prepare(c->tree, c->t, c->gd, c->ph, c->o, c->st, c->err);
             if (st == RISM_OK) st = tree_eval(c->tree, c->t, c->gd, c->ph, c->o, o, c->st, c->err, c->info);
             for (int k = 0; k < 3 && st == RISM_OK; ++k)
@@ -408,8 +413,8 @@ rism_status rism_init(rism_ctx* c, double* u, double* c_lr, double* h_lr, double
                 }
             if (st == RISM_OK) st = check_device_error(c);
             if (st == RISM_OK) st = tree_post(c->tree, c->info, retry, c->err);
-            if (st == RISM_OK && retry) st = fail(c, RISM_E_NOMEM, "list slots kept growing (" + c->err + ")");
         }
+        if (st == RISM_OK && retry) st = fail(c, RISM_E_NOMEM, "list slots kept growing (" + c->err + ")");
     }
     if (st == RISM_OK && (c->o.debug_flags & 2) && c->ev[0] && (o.u || o.c || o.h))
         cudaEventElapsedTime(&c->info.eval_ms, c->ev[0], c->ev[1]);

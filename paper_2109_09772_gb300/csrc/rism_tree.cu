@@ -82,7 +82,91 @@ struct TreeMeta {
     double cell_side;      // cube_side / 2^lc
     double rnear;          // near-field radius (grid units): max(largest LJ cut-off, r_short)
     unsigned long long direct_pairs, proxy_pairs, near_pairs;
+    unsigned long long cp_pairs;  // (target proxy, atom) pairs of the box-level far field
+    int cp_need, dn_need;  // largest accepted-range list / pass-down list of a target box
+    int tboxes;            // target boxes that took proxies and have a non-empty list
+    int pad2;
 };
+
+// ------------------------------------------------ target boxes (cluster-particle far field)
+// Aligned cubes of the grid with edge 16 << l points (level l = 0 .. L-1), clipped to the grid.  A box with at
+// least n+1 points along each axis and more than (n+1)^3 points takes (n+1)^3 Chebyshev proxy targets; its
+// accepted source clusters are summed at the proxies and reach the grid points by interpolation.
+constexpr int kMaxTL = 16;
+constexpr int kTB0 = 16;   // edge of a level-0 box (points)
+
+struct TBoxes {
+    int L, nbox;
+    int nbx[kMaxTL], nby[kMaxTL], nbz[kMaxTL], off[kMaxTL];
+    int nx, ny, nz;
+    int deg, P3;
+    int enabled;
+    float ck[kMaxDegree + 1];  // cos(k pi / n), exact 1, 0, -1 where they occur
+};
+
+struct TBox {
+    int l, ib, jb, kb;
+    int lo[3], ext[3];
+    double c[3], r;
+    bool proxied;
+};
+
+__host__ __device__ inline TBox tbox_at(const TBoxes& tb, int l, int ib, int jb, int kb) {
+    TBox b;
+    b.l = l;
+    b.ib = ib;
+    b.jb = jb;
+    b.kb = kb;
+    const int E = kTB0 << l;
+    const int n[3] = {tb.nx, tb.ny, tb.nz}, ix[3] = {ib, jb, kb};
+    double r2 = 0.0;
+    long long pts = 1;
+    bool big = true;
+    for (int d = 0; d < 3; ++d) {
+        b.lo[d] = ix[d] * E;
+        b.ext[d] = n[d] - b.lo[d] < E ? n[d] - b.lo[d] : E;
+        b.c[d] = b.lo[d] + 0.5 * (b.ext[d] - 1);
+        r2 += 0.25 * (double)(b.ext[d] - 1) * (b.ext[d] - 1);
+        pts *= b.ext[d];
+        big = big && b.ext[d] >= tb.deg + 1;
+    }
+    b.r = sqrt(r2);
+    b.proxied = tb.enabled && big && pts > tb.P3;
+    return b;
+}
+
+__host__ __device__ inline int tbox_index(const TBoxes& tb, int l, int ib, int jb, int kb) {
+    return tb.off[l] + (kb * tb.nby[l] + jb) * tb.nbx[l] + ib;
+}
+
+__host__ __device__ inline TBox tbox_flat(const TBoxes& tb, int box) {
+    int l = 0;
+    while (l + 1 < tb.L && tb.off[l + 1] <= box) ++l;
+    const int bi = box - tb.off[l];
+    return tbox_at(tb, l, bi % tb.nbx[l], (bi / tb.nbx[l]) % tb.nby[l], bi / (tb.nbx[l] * tb.nby[l]));
+}
+
+// Lagrange basis of the (n+1) Chebyshev points of the second kind of an interval with half-width hw, in
+// barycentric form with weights (-1)^k (halved at both ends), evaluated at offset t from the interval's
+// centre.  Node k sits at hw ck[k] -- the same FP32 product the proxy kernel places its targets at.
+__device__ inline void cheb_basis(int n, const float* ck, float hw, float t, float* L) {
+    float den = 0.f;
+    int hit = -1;
+    for (int k = 0; k <= n; ++k) {
+        const float dx = t - hw * ck[k];
+        if (dx == 0.f) hit = k;
+        float w = (k & 1) ? -1.f : 1.f;
+        if (k == 0 || k == n) w *= 0.5f;
+        L[k] = dx != 0.f ? w / dx : 0.f;
+        den += L[k];
+    }
+    if (hit >= 0) {
+        for (int k = 0; k <= n; ++k) L[k] = k == hit ? 1.f : 0.f;
+        return;
+    }
+    const float inv = 1.f / den;
+    for (int k = 0; k <= n; ++k) L[k] *= inv;
+}
 
 __device__ __forceinline__ uint32_t spread3(uint32_t v) {
     v &= 0x3ffu;
@@ -596,7 +680,43 @@ struct ListArgs {
     double theta;
     int n, P3;
     int cap;                  // capacity of the entry buffer
+    // with target boxes: the traversal of a batch starts from the pass-down list of its level-0 box
+    const int* dn_cnt;        // null: start from the root
+    const int* dn_ent;
+    int dn_cap;
+    TBoxes tb;
 };
+
+// Node index -> (is a node opened for this target?) helpers shared by the traversals.
+__device__ __forceinline__ void node_sphere(const Node& nd, const double c[3], double& R2, double& rn) {
+    double rn2 = 0.0;
+    R2 = 0.0;
+    for (int d = 0; d < 3; ++d) {
+        const double cn = 0.5 * (nd.lo[d] + nd.hi[d]);
+        R2 += (c[d] - cn) * (c[d] - cn);
+        rn2 += 0.25 * (nd.hi[d] - nd.lo[d]) * (nd.hi[d] - nd.lo[d]);
+    }
+    rn = sqrt(rn2);
+}
+
+// Loads a traversal's initial frontier: the root, or the pass-down list of the target's enclosing box.
+// Returns its length (0 when the tree is unusable); sets ovf when it exceeds the frontier.
+__device__ __forceinline__ int load_frontier(int* cur, const int* lst, int cnt, bool use_root, bool ok, int lane,
+                                             bool& ovf) {
+    if (!ok) return 0;
+    if (use_root) {
+        if (lane == 0) cur[0] = 0;
+        __syncwarp();
+        return 1;
+    }
+    if (cnt > kQCap) {
+        ovf = true;
+        cnt = kQCap;
+    }
+    for (int k = lane; k < cnt; k += 32) cur[k] = lst[k];
+    __syncwarp();
+    return cnt;
+}
 
 __device__ __forceinline__ void batch_geom(const ListArgs& a, int b, double cb[3], double& rb, int lo[3], int hi[3]) {
     const int ib = b % a.nbx, jb = (b / a.nbx) % a.nby, kb = b / (a.nbx * a.nby);
@@ -629,13 +749,19 @@ __global__ void __launch_bounds__(32 * kListWarps) k_far_lists(ListArgs a, const
         batch_geom(a, b, cb, rb, lo, hi);
         int* cur = qa[w];
         int* nxt = qb[w];
-        int ncur = (a.n > 0 && tree_ok) ? 1 : 0;
-        if (lane == 0) cur[0] = 0;
-        __syncwarp();
+        bool ovf = false;
+        const int* dl = nullptr;
+        int dc = 0;
+        if (a.dn_cnt) {
+            const int bx0 = lo[0] / kTB0, by0 = lo[1] / kTB0, bz0 = lo[2] / kTB0;
+            const int box = tbox_index(a.tb, 0, bx0, by0, bz0);
+            dl = a.dn_ent + (int64_t)box * a.dn_cap;
+            dc = a.dn_cnt[box];
+        }
+        int ncur = load_frontier(cur, dl, dc, a.dn_cnt == nullptr, a.n > 0 && tree_ok, lane, ovf);
         int m = 0;
         int2* out = ent + (int64_t)b * a.cap;
         long long dp = 0, pp = 0;
-        bool ovf = false;
         while (ncur > 0) {
             int nnext = 0;
             for (int c0 = 0; c0 < ncur; c0 += 32) {
@@ -645,13 +771,9 @@ __global__ void __launch_bounds__(32 * kListWarps) k_far_lists(ListArgs a, const
                 int nch = 0, fch = 0;
                 if (k < ncur) {
                     const Node nd = nodes[cur[k]];
-                    double R2 = 0.0, rn2 = 0.0;
-                    for (int d = 0; d < 3; ++d) {
-                        const double cn = 0.5 * (nd.lo[d] + nd.hi[d]);
-                        R2 += (cb[d] - cn) * (cb[d] - cn);
-                        rn2 += 0.25 * (nd.hi[d] - nd.lo[d]) * (nd.hi[d] - nd.lo[d]);
-                    }
-                    const double rs = rb + sqrt(rn2);
+                    double R2, rn;
+                    node_sphere(nd, cb, R2, rn);
+                    const double rs = rb + rn;
                     const bool sep = rs * rs < a.theta * a.theta * R2;
                     const int cntn = nd.end - nd.begin;
                     if (sep && nd.prox >= 0) {
@@ -704,6 +826,10 @@ __global__ void __launch_bounds__(32 * kListWarps) k_far_lists(ListArgs a, const
             ncur = nnext;
             __syncwarp();
         }
+        if (__any_sync(0xffffffffu, ovf) && lane == 0) {
+            meta->overflow = 1;
+            meta->wide = 1;
+        }
         for (int o = 16; o > 0; o >>= 1) {
             dp += __shfl_xor_sync(0xffffffffu, dp, o);
             pp += __shfl_xor_sync(0xffffffffu, pp, o);
@@ -716,6 +842,137 @@ __global__ void __launch_bounds__(32 * kListWarps) k_far_lists(ListArgs a, const
             }
             atomicAdd(&meta->direct_pairs, (unsigned long long)(dp * pts));
             atomicAdd(&meta->proxy_pairs, (unsigned long long)(pp * pts));
+        }
+    }
+}
+
+// Target-box lists of level l: one warp per box, traversal from the parent's pass-down list (the root at the
+// top level).  A node that meets the acceptance criterion (r_box + r_node)/R < theta of a box with proxies is
+// summed at the box's proxies (its atom range goes to the box's accepted list); a node larger than the box
+// is opened; anything else is passed down to the box's children (the pass-down list).  Entry order: by
+// frontier round, then lane -- deterministic.  Lists longer than their slots set the overflow flag and
+// record their length for the host to grow the slots.
+struct TListArgs {
+    TBoxes tb;
+    int l;
+    int n, P3;
+    double theta;
+    int cp_cap, dn_cap;
+    int* cp_cnt;
+    int2* cp_ent;   // [nbox][cp_cap] atom ranges (start, count)
+    int* dn_cnt;
+    int* dn_ent;    // [nbox][dn_cap] node indices
+};
+
+__global__ void __launch_bounds__(32 * kListWarps) k_tbox_lists(TListArgs a, const Node* __restrict__ nodes,
+                                                               TreeMeta* meta) {
+    __shared__ int qa[kListWarps][kQCap], qb[kListWarps][kQCap];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const TBoxes& tb = a.tb;
+    const int l = a.l;
+    const int nbl = tb.nbx[l] * tb.nby[l] * tb.nbz[l];
+    const bool tree_ok = !meta->build_overflow;
+    for (int bi = blockIdx.x * kListWarps + w; bi < nbl; bi += gridDim.x * kListWarps) {
+        const int ib = bi % tb.nbx[l], jb = (bi / tb.nbx[l]) % tb.nby[l], kb = bi / (tb.nbx[l] * tb.nby[l]);
+        const TBox T = tbox_at(tb, l, ib, jb, kb);
+        const int box = tb.off[l] + bi;
+        int* cur = qa[w];
+        int* nxt = qb[w];
+        bool ovf = false;
+        const bool top = l == tb.L - 1;
+        int pc = 0;
+        const int* pl = nullptr;
+        if (!top) {
+            const int pbox = tbox_index(tb, l + 1, ib >> 1, jb >> 1, kb >> 1);
+            pl = a.dn_ent + (int64_t)pbox * a.dn_cap;
+            pc = a.dn_cnt[pbox];
+        }
+        int ncur = load_frontier(cur, pl, pc, top, a.n > 0 && tree_ok, lane, ovf);
+        int mc = 0, md = 0;
+        int2* cpo = a.cp_ent + (int64_t)box * a.cp_cap;
+        int* dno = a.dn_ent + (int64_t)box * a.dn_cap;
+        long long cpp = 0;
+        while (ncur > 0 && !__any_sync(0xffffffffu, ovf)) {
+            int nnext = 0;
+            for (int c0 = 0; c0 < ncur; c0 += 32) {
+                const int k = c0 + lane;
+                int kind = 0;  // 0 none, 1 accepted, 2 open, 3 pass down
+                int nch = 0, fch = 0, node = 0;
+                int2 e = make_int2(0, 0);
+                if (k < ncur) {
+                    node = cur[k];
+                    const Node nd = nodes[node];
+                    double R2, rn;
+                    node_sphere(nd, T.c, R2, rn);
+                    const double rs = T.r + rn;
+                    if (T.proxied && rs * rs < a.theta * a.theta * R2) {
+                        kind = 1;
+                        e = make_int2(nd.begin, nd.end - nd.begin);
+                        cpp += (long long)a.P3 * (nd.end - nd.begin);
+                    } else if (nd.first_child >= 0 && rn > T.r) {
+                        kind = 2;
+                        nch = nd.nchild;
+                        fch = nd.first_child;
+                    } else {
+                        kind = 3;
+                    }
+                }
+                const unsigned ea = __ballot_sync(0xffffffffu, kind == 1);
+                const unsigned ed = __ballot_sync(0xffffffffu, kind == 3);
+                const unsigned below = (1u << lane) - 1u;
+                if (kind == 1) {
+                    const int pos = mc + __popc(ea & below);
+                    if (pos < a.cp_cap) cpo[pos] = e;
+                }
+                if (kind == 3) {
+                    const int pos = md + __popc(ed & below);
+                    if (pos < a.dn_cap) dno[pos] = node;
+                }
+                mc += __popc(ea);
+                md += __popc(ed);
+                int x = nch;
+                for (int o = 1; o < 32; o <<= 1) {
+                    const int y = __shfl_up_sync(0xffffffffu, x, o);
+                    if (lane >= o) x += y;
+                }
+                const int tot = __shfl_sync(0xffffffffu, x, 31);
+                const int at = nnext + x - nch;
+                if (kind == 2) {
+                    for (int ch = 0; ch < nch; ++ch) {
+                        if (at + ch < kQCap) nxt[at + ch] = fch + ch;
+                        else ovf = true;
+                    }
+                }
+                nnext += tot;
+            }
+            __syncwarp();
+            int* tq = cur;
+            cur = nxt;
+            nxt = tq;
+            ncur = nnext;
+            __syncwarp();
+        }
+        for (int o = 16; o > 0; o >>= 1) cpp += __shfl_xor_sync(0xffffffffu, cpp, o);
+        const bool wide = __any_sync(0xffffffffu, ovf);
+        if (lane == 0) {
+            a.cp_cnt[box] = min(mc, a.cp_cap);
+            a.dn_cnt[box] = min(md, a.dn_cap);
+            if (wide) {
+                meta->overflow = 1;
+                meta->wide = 1;
+            }
+            if (mc > a.cp_cap) {
+                meta->overflow = 1;
+                atomicMax(&meta->cp_need, mc);
+            }
+            if (md > a.dn_cap) {
+                meta->overflow = 1;
+                atomicMax(&meta->dn_need, md);
+            }
+            if (mc > 0) {
+                atomicAdd(&meta->cp_pairs, (unsigned long long)cpp);
+                atomicAdd(&meta->tboxes, 1);
+            }
         }
     }
 }
@@ -792,8 +1049,9 @@ __global__ void __launch_bounds__(32 * kListWarps) k_near_lists(ListArgs a, cons
 }
 
 __global__ void k_reset_meta(TreeMeta* meta) {
-    meta->direct_pairs = meta->proxy_pairs = meta->near_pairs = 0ull;
-    meta->far_need = meta->near_need = 0;
+    meta->direct_pairs = meta->proxy_pairs = meta->near_pairs = meta->cp_pairs = 0ull;
+    meta->far_need = meta->near_need = meta->cp_need = meta->dn_need = 0;
+    meta->tboxes = 0;
     meta->wide = 0;
     meta->build_overflow = 0;
     meta->overflow = 0;
@@ -814,6 +1072,7 @@ __global__ void k_reset_meta(TreeMeta* meta) {
 // into a kStages-deep ring of tiles guarded by full (copy landed) and empty
 // (all warps done) mbarriers; every wait is bounded.
 constexpr int kStages = 3;
+constexpr int kNTab = 128;  // segments of the short-range kernel tables over [0, r_short]
 
 struct EvalArgs {
     GridD g;
@@ -828,6 +1087,9 @@ struct EvalArgs {
     const int2* near_ent;  // [nb][near_cap]
     int far_cap, near_cap;
     float4* far;           // per grid point: Phi1 (hi, lo), Phik (hi, lo), grid units
+    int far_init;          // the far kernel starts from the box-level (interpolated) field already in `far`
+    const float4* ntab;    // [2 kNTab] cubic pieces of erfc(x) and e^{-x^2}[erfcx(x-a) + erfcx(x+a)] in d
+    float ntab_inv;        // kNTab / r_short (grid units)
     Outputs o;
     DevErr* err;
     TreeMeta* meta;
@@ -857,6 +1119,7 @@ struct Ring {
 // Range-list producer state (thread 0).
 struct Cursor {
     int e, e_end, off;
+    int left;              // sources still to deliver (a chunk of the list), INT_MAX: the whole list
     int produced;
     bool done;
     int last_phase[kStages];
@@ -866,9 +1129,10 @@ template <int SM, bool LJ>
 __device__ int fill_ranges(Cursor& c, const int2* __restrict__ ent, const SrcF* __restrict__ src,
                            const LJf* __restrict__ ljs, SrcF* dst, LJf* ldst, uint64_t* bar) {
     int filled = 0;
-    while (filled < kT && c.e < c.e_end) {
+    while (filled < kT && c.e < c.e_end && c.left > 0) {
         const int2 en = ent[c.e];
-        const int take = min(kT - filled, en.y - c.off);
+        const int take = min(min(kT - filled, en.y - c.off), c.left);
+        c.left -= take;
         const uint32_t b1 = take * sizeof(SrcF), b2 = LJ ? take * SM * sizeof(LJf) : 0;
         mbar_expect_tx_only(bar, b1 + b2);
         bulk_g2s(dst + filled, src + en.x + c.off, b1, bar);
@@ -1046,12 +1310,25 @@ __device__ void far_body(const EvalArgs& a, int b, Ring<1, false>& r, PairRec (*
     float f1h[P], f1l[P], fkh[P], fkl[P];
 #pragma unroll
     for (int p = 0; p < P; ++p) f1h[p] = f1l[p] = fkh[p] = fkl[p] = 0.f;
+    if (a.far_init && j < a.g.ny && k < a.g.nz) {
+        const float4* src0 = a.far + ((int64_t)k * a.g.ny + j) * a.g.nx;
+#pragma unroll
+        for (int p = 0; p < P; ++p)
+            if (i0 + p < a.g.nx) {
+                const float4 v = src0[i0 + p];
+                f1h[p] = v.x;
+                f1l[p] = v.y;
+                fkh[p] = v.z;
+                fkl[p] = v.w;
+            }
+    }
     Cursor cur;
     __syncthreads();
     if (tid == 0) {
         cur.e = b * a.far_cap;
         cur.e_end = cur.e + a.far_cnt[b];
         cur.off = 0;
+        cur.left = INT_MAX;
         cur.produced = 0;
         cur.done = false;
         for (int s = 0; s < kStages; ++s) cur.last_phase[s] = -1;
@@ -1093,6 +1370,366 @@ __device__ void far_body(const EvalArgs& a, int b, Ring<1, false>& r, PairRec (*
         if (i0 + p < g.nx) dst[i0 + p] = make_float4(f1h[p], f1l[p], fkh[p], fkl[p]);
 }
 
+// ---- box-level far field: accepted clusters summed at the Chebyshev proxy targets of each target box,
+// pushed down the box hierarchy and interpolated onto the grid points (cluster-particle form).
+struct CPArgs {
+    TBoxes tb;
+    const int* cp_cnt;
+    const int2* cp_ent;  // [nbox][cp_cap] accepted atom ranges
+    int cp_cap;
+    float2* tpot;        // [nbox][P3] (Phi1, Phik) at the proxies, index (kz (n+1) + ky)(n+1) + kx
+    float2* tpart;       // [nbox][kCPChunks - 1][P3] sums of the list chunks after the first
+    int* tnch;           // [nbox] chunks the box's list was split into
+    int* tflag;          // [nbox] nonzero: the box's proxies hold a field (own or inherited)
+};
+
+// Source pairs relative to the box centre: x_s - c = (x_hi - c) + x_lo, one rounding; the proxies are
+// well separated from every accepted source, so no exact-difference form is needed here.
+struct RelRec {
+    float4 xy;  // x0, x1, y0, y1
+    float4 zq;  // z0, z1, q0, q1
+};
+
+__device__ __forceinline__ void stage_rel(const SrcF* __restrict__ Sx, int cnt, RelRec* wp, int lane, float cx,
+                                          float cy, float cz) {
+    if (2 * lane < cnt) {
+        const float4 a0 = *reinterpret_cast<const float4*>(&Sx[2 * lane].xh);
+        const float4 a1 = *reinterpret_cast<const float4*>(&Sx[2 * lane].xl);
+        float4 b0 = make_float4(0.f, 0.f, 0.f, 0.f), b1 = make_float4(0.f, 0.f, 0.f, 0.f);
+        float bx = kPadPos, by = kPadPos, bz = kPadPos;
+        if (2 * lane + 1 < cnt) {
+            b0 = *reinterpret_cast<const float4*>(&Sx[2 * lane + 1].xh);
+            b1 = *reinterpret_cast<const float4*>(&Sx[2 * lane + 1].xl);
+            bx = (b0.x - cx) + b1.x;
+            by = (b0.y - cy) + b1.y;
+            bz = (b0.z - cz) + b1.z;
+        }
+        RelRec& o = wp[lane];
+        o.xy = make_float4((a0.x - cx) + a1.x, bx, (a0.y - cy) + a1.y, by);
+        o.zq = make_float4((a0.z - cz) + a1.z, bz, a0.w, b0.w);
+    }
+}
+
+template <int P, bool DH>
+__device__ __forceinline__ void cp_pairs(const RelRec* wp, int np, const f32x2 (&GX)[P], f32x2 FY, f32x2 FZ,
+                                         f32x2 K2, f32x2 (&P1)[P], f32x2 (&PK)[P]) {
+    for (int l = 0; l < np; ++l) {
+        const ulonglong2 A = *reinterpret_cast<const ulonglong2*>(&wp[l].xy);
+        const ulonglong2 B = *reinterpret_cast<const ulonglong2*>(&wp[l].zq);
+        const f32x2 DY = sub2(FY, A.y);
+        const f32x2 DZ = sub2(FZ, B.x);
+        const f32x2 DYZ = fma2(DY, DY, mul2(DZ, DZ));
+#pragma unroll
+        for (int p = 0; p < P; ++p) {
+            const f32x2 DX = sub2(GX[p], A.x);
+            const f32x2 D2 = fma2(DX, DX, DYZ);
+            const float2 d2 = up2(D2);
+            const f32x2 RI = pk2(rsqrt_approx(d2.x), rsqrt_approx(d2.y));
+            const f32x2 QR = mul2(B.y, RI);
+            P1[p] = add2(P1[p], QR);
+            if (DH) {
+                const float2 e = up2(mul2(K2, mul2(D2, RI)));
+                PK[p] = fma2(QR, pk2(ex2_approx(e.x), ex2_approx(e.y)), PK[p]);
+            }
+        }
+    }
+}
+
+constexpr int kCPThreads = 256;
+constexpr int kCPP = 3;          // proxies per thread (along x)
+constexpr int kCPChunks = 4;     // CTAs a box's accepted list is split over at most
+constexpr int kCPChunkMin = 256; // atoms per chunk at least
+
+// One CTA per (target box, list chunk, pass): the box's accepted atoms split into up to kCPChunks chunks of
+// at least kCPChunkMin atoms; the (n+1)^2 proxy lines of the box split into chunks of kCPP nodes along x,
+// kCPThreads chunks per pass.  Sources stream through the TMA ring.  Chunk 0 writes the box's proxy values,
+// later chunks their partial sums (added in chunk order by k_cp_reduce).
+template <bool DH>
+__global__ void __launch_bounds__(kCPThreads) k_cp_eval(EvalArgs a, CPArgs c) {
+    __shared__ Ring<1, false> r;
+    __shared__ RelRec pairs[kCPThreads / 32][kPairs];
+    __shared__ int s_e, s_off, s_len, s_nch;
+    constexpr int NW = kCPThreads / 32;
+    const int tid = threadIdx.x, lane = tid & 31;
+    if (tid == 0) r.inited = 0;
+    if (a.meta->overflow) return;
+    const int box = blockIdx.x, chunk = blockIdx.y, pass = blockIdx.z;
+    const TBox T = tbox_flat(c.tb, box);
+    if (!T.proxied) return;
+    const int deg = c.tb.deg, n1 = deg + 1, P3 = c.tb.P3;
+    const int nxc = (n1 + kCPP - 1) / kCPP;
+    const int ntask = n1 * n1 * nxc;
+    const int cnt = c.cp_cnt[box];
+    if (cnt == 0) {
+        if (chunk == 0 && pass == 0) {
+            float2* out = c.tpot + (int64_t)box * P3;
+            for (int k = tid; k < P3; k += kCPThreads) out[k] = make_float2(0.f, 0.f);
+            if (tid == 0) {
+                c.tflag[box] = 0;
+                c.tnch[box] = 1;
+            }
+        }
+        return;
+    }
+    const int2* ent = c.cp_ent + (int64_t)box * c.cp_cap;
+    if (tid == 0) {
+        int tot = 0;
+        for (int e = 0; e < cnt; ++e) tot += ent[e].y;
+        const int nch = min(kCPChunks, max(1, tot / kCPChunkMin));
+        s_nch = nch;
+        if (chunk < nch) {
+            const int a0 = (int)((long long)tot * chunk / nch), a1 = (int)((long long)tot * (chunk + 1) / nch);
+            int e = 0, acc = 0;
+            while (e < cnt && acc + ent[e].y <= a0) acc += ent[e++].y;
+            s_e = e;
+            s_off = a0 - acc;
+            s_len = a1 - a0;
+        }
+    }
+    __syncthreads();
+    const int nch = s_nch;
+    if (chunk >= nch || pass * kCPThreads >= ntask) return;
+    if (chunk == 0 && pass == 0 && tid == 0) {
+        c.tflag[box] = 1;
+        c.tnch[box] = nch;
+    }
+    float2* out = chunk == 0 ? c.tpot + (int64_t)box * P3
+                             : c.tpart + ((int64_t)box * (kCPChunks - 1) + chunk - 1) * P3;
+    const int task = pass * kCPThreads + tid;
+    const bool act = task < ntask;
+    const int tk = act ? task : 0;
+    const int line = tk / nxc, xc = tk % nxc, ky = line % n1, kz = line / n1;
+    const float hx = 0.5f * (T.ext[0] - 1), hy = 0.5f * (T.ext[1] - 1), hz = 0.5f * (T.ext[2] - 1);
+    f32x2 GX[kCPP];
+#pragma unroll
+    for (int p = 0; p < kCPP; ++p) {
+        const int kx = min(xc * kCPP + p, deg);
+        const float u = hx * c.tb.ck[kx];
+        GX[p] = pk2(u, u);
+    }
+    const float uy = hy * c.tb.ck[ky], uz = hz * c.tb.ck[kz];
+    const f32x2 FY = pk2(uy, uy), FZ = pk2(uz, uz);
+    const float kap2 = (float)(-a.ph.kappa * a.g.h * 1.4426950408889634);
+    const f32x2 K2 = pk2(kap2, kap2);
+    const float cx = (float)T.c[0], cy = (float)T.c[1], cz = (float)T.c[2];
+    RelRec* wp = pairs[tid >> 5];
+    float f1h[kCPP], f1l[kCPP], fkh[kCPP], fkl[kCPP];
+#pragma unroll
+    for (int p = 0; p < kCPP; ++p) f1h[p] = f1l[p] = fkh[p] = fkl[p] = 0.f;
+    Cursor cur;
+    __syncthreads();
+    if (tid == 0) {
+        cur.e = box * c.cp_cap + s_e;
+        cur.e_end = box * c.cp_cap + cnt;
+        cur.off = s_off;
+        cur.left = s_len;
+        cur.produced = 0;
+        cur.done = false;
+        for (int st = 0; st < kStages; ++st) cur.last_phase[st] = -1;
+        ring_init(r, NW);
+    }
+    __syncthreads();
+    const bool ok = run_ring<1, false, NW>(
+        r, cur, c.cp_ent, a.srcf, nullptr, a,
+        [&](int slot, int n) {
+            __syncwarp();
+            stage_rel(r.src[slot], n, wp, lane, cx, cy, cz);
+            __syncwarp();
+        },
+        [&](int n) {
+            f32x2 P1[kCPP], PK[kCPP];
+#pragma unroll
+            for (int p = 0; p < kCPP; ++p) P1[p] = PK[p] = 0ull;
+            cp_pairs<kCPP, DH>(wp, (n + 1) >> 1, GX, FY, FZ, K2, P1, PK);
+#pragma unroll
+            for (int p = 0; p < kCPP; ++p) {
+                const float2 s1 = up2(P1[p]);
+                ff_add(f1h[p], f1l[p], s1.x + s1.y);
+                if (DH) {
+                    const float2 sk = up2(PK[p]);
+                    ff_add(fkh[p], fkl[p], sk.x + sk.y);
+                }
+            }
+        });
+    if (!ok || !act) return;
+#pragma unroll
+    for (int p = 0; p < kCPP; ++p) {
+        const int kx = xc * kCPP + p;
+        if (kx < n1) out[(kz * n1 + ky) * n1 + kx] = make_float2(f1h[p] + f1l[p], fkh[p] + fkl[p]);
+    }
+}
+
+// Chunk partials added to the box's proxy values in chunk order (deterministic).
+__global__ void __launch_bounds__(256) k_cp_reduce(CPArgs c, const TreeMeta* meta) {
+    if (meta->overflow) return;
+    const int box = blockIdx.x;
+    const TBox T = tbox_flat(c.tb, box);
+    if (!T.proxied || c.cp_cnt[box] == 0) return;
+    const int nch = c.tnch[box], P3 = c.tb.P3;
+    if (nch <= 1) return;
+    float2* dst = c.tpot + (int64_t)box * P3;
+    const float2* part = c.tpart + (int64_t)box * (kCPChunks - 1) * P3;
+    for (int k = threadIdx.x; k < P3; k += blockDim.x) {
+        float2 v = dst[k];
+        for (int ch = 1; ch < nch; ++ch) {
+            const float2 w = part[(int64_t)(ch - 1) * P3 + k];
+            v.x += w.x;
+            v.y += w.y;
+        }
+        dst[k] = v;
+    }
+}
+
+// Separable tensor-product interpolation in shared memory: V holds (n+1)^3 values on the source box's
+// Chebyshev points (x fastest); W[d] the 1D Lagrange weights [m_d][n+1] of the m_d target coordinates of
+// axis d.  Produces O[m2][m1][m0] (x fastest).  S1 and S2 are scratch of (n+1)^2 m0 and (n+1) m1 m0 values.
+__device__ void interp3(int n1, const float2* V, const float* W0, const float* W1, const float* W2, int m0, int m1,
+                        int m2, float2* S1, float2* S2, float2* O) {
+    const int tid = threadIdx.x, nt = blockDim.x;
+    for (int t = tid; t < n1 * n1 * m0; t += nt) {
+        const int ix = t % m0, line = t / m0;  // line = kz (n+1) + ky
+        float ax = 0.f, ay = 0.f;
+        for (int k = 0; k < n1; ++k) {
+            const float wv = W0[ix * n1 + k];
+            const float2 v = V[line * n1 + k];
+            ax = fmaf(wv, v.x, ax);
+            ay = fmaf(wv, v.y, ay);
+        }
+        S1[line * m0 + ix] = make_float2(ax, ay);
+    }
+    __syncthreads();
+    for (int t = tid; t < n1 * m1 * m0; t += nt) {
+        const int ix = t % m0, iy = (t / m0) % m1, kz = t / (m0 * m1);
+        float ax = 0.f, ay = 0.f;
+        for (int k = 0; k < n1; ++k) {
+            const float wv = W1[iy * n1 + k];
+            const float2 v = S1[(kz * n1 + k) * m0 + ix];
+            ax = fmaf(wv, v.x, ax);
+            ay = fmaf(wv, v.y, ay);
+        }
+        S2[(kz * m1 + iy) * m0 + ix] = make_float2(ax, ay);
+    }
+    __syncthreads();
+    for (int t = tid; t < m2 * m1 * m0; t += nt) {
+        const int ix = t % m0, iy = (t / m0) % m1, iz = t / (m0 * m1);
+        float ax = 0.f, ay = 0.f;
+        for (int k = 0; k < n1; ++k) {
+            const float wv = W2[iz * n1 + k];
+            const float2 v = S2[(k * m1 + iy) * m0 + ix];
+            ax = fmaf(wv, v.x, ax);
+            ay = fmaf(wv, v.y, ay);
+        }
+        O[t] = make_float2(ax, ay);
+    }
+    __syncthreads();
+}
+
+// Weight rows for axis d: row i is the Lagrange basis of box B's Chebyshev points along d evaluated at the
+// offset t(i) from B's centre (grid units).
+template <typename X>
+__device__ void basis_rows(const TBoxes& tb, const TBox& B, int d, int m, X t, float* W) {
+    const int deg = tb.deg;
+    const float hw = 0.5f * (B.ext[d] - 1);
+    for (int i = threadIdx.x; i < m; i += blockDim.x) {
+        float L[kMaxDegree + 1];
+        cheb_basis(deg, tb.ck, hw, t(i), L);
+        for (int k = 0; k <= deg; ++k) W[i * (deg + 1) + k] = L[k];
+    }
+}
+
+// Dynamic shared memory of k_l2l / k_tdown for degree n: V, S1, S2, O and the weights.
+__host__ __device__ constexpr size_t interp_smem(int n1, int m) {
+    return sizeof(float2) * ((size_t)n1 * n1 * n1 + (size_t)n1 * n1 * m + (size_t)n1 * m * m + (size_t)m * m * m) +
+           sizeof(float) * 3 * (size_t)m * n1;
+}
+
+// Downward pass, level l + 1 -> l: a box with proxies adds its parent's field interpolated at its own proxies.
+__global__ void __launch_bounds__(256) k_l2l(CPArgs c, int l, const TreeMeta* meta) {
+    extern __shared__ __align__(16) unsigned char sm_raw[];
+    if (meta->overflow) return;
+    const TBoxes& tb = c.tb;
+    const int bi = blockIdx.x;
+    const int ib = bi % tb.nbx[l], jb = (bi / tb.nbx[l]) % tb.nby[l], kb = bi / (tb.nbx[l] * tb.nby[l]);
+    const TBox T = tbox_at(tb, l, ib, jb, kb);
+    if (!T.proxied) return;
+    const TBox Pb = tbox_at(tb, l + 1, ib >> 1, jb >> 1, kb >> 1);
+    const int box = tb.off[l] + bi, pbox = tbox_index(tb, l + 1, ib >> 1, jb >> 1, kb >> 1);
+    if (!Pb.proxied || !c.tflag[pbox]) return;
+    const int deg = tb.deg, n1 = deg + 1, P3 = tb.P3;
+    float2* V = reinterpret_cast<float2*>(sm_raw);
+    float2* S1 = V + P3;
+    float2* S2 = S1 + n1 * n1 * n1;
+    float2* O = S2 + n1 * n1 * n1;
+    float* W = reinterpret_cast<float*>(O + P3);
+    const float2* src = c.tpot + (int64_t)pbox * P3;
+    for (int k = threadIdx.x; k < P3; k += blockDim.x) V[k] = src[k];
+    for (int d = 0; d < 3; ++d) {
+        // child node i relative to the parent's centre: (c_child - c_parent) (exact: half-integers) + hw ck[i]
+        const float off = (float)(T.c[d] - Pb.c[d]), hd = 0.5f * (T.ext[d] - 1);
+        basis_rows(tb, Pb, d, n1, [&](int i) { return off + hd * tb.ck[i]; }, W + d * n1 * n1);
+    }
+    __syncthreads();
+    interp3(n1, V, W, W + n1 * n1, W + 2 * n1 * n1, n1, n1, n1, S1, S2, O);
+    float2* dst = c.tpot + (int64_t)box * P3;
+    for (int k = threadIdx.x; k < P3; k += blockDim.x) {
+        const float2 v = dst[k];
+        dst[k] = make_float2(v.x + O[k].x, v.y + O[k].y);
+    }
+    if (threadIdx.x == 0) c.tflag[box] = 1;
+}
+
+// Box field onto the grid: one CTA per level-0 box region; the lowest box with proxies that contains it
+// (its field includes every ancestor's) is interpolated at the region's points and written to the far-field
+// buffer as the starting value of the far kernel (zero where no box holds a field).
+__global__ void __launch_bounds__(256) k_tdown(CPArgs c, float4* far, const TreeMeta* meta) {
+    extern __shared__ __align__(16) unsigned char sm_raw[];
+    if (meta->overflow) return;
+    const TBoxes& tb = c.tb;
+    const int bi = blockIdx.x;
+    const int ib = bi % tb.nbx[0], jb = (bi / tb.nbx[0]) % tb.nby[0], kb = bi / (tb.nbx[0] * tb.nby[0]);
+    const TBox R = tbox_at(tb, 0, ib, jb, kb);
+    int la = -1;
+    TBox A = R;
+    for (int l = 0; l < tb.L; ++l) {
+        A = tbox_at(tb, l, ib >> l, jb >> l, kb >> l);
+        if (A.proxied) {
+            la = l;
+            break;
+        }
+    }
+    const int m0 = R.ext[0], m1 = R.ext[1], m2 = R.ext[2];
+    const int64_t plane = (int64_t)tb.ny * tb.nx;
+    const bool field = la >= 0 && c.tflag[tbox_index(tb, la, A.ib, A.jb, A.kb)];
+    if (!field) {
+        for (int t = threadIdx.x; t < m0 * m1 * m2; t += blockDim.x) {
+            const int ix = t % m0, iy = (t / m0) % m1, iz = t / (m0 * m1);
+            far[(R.lo[2] + iz) * plane + (int64_t)(R.lo[1] + iy) * tb.nx + R.lo[0] + ix] =
+                make_float4(0.f, 0.f, 0.f, 0.f);
+        }
+        return;
+    }
+    const int deg = tb.deg, n1 = deg + 1, P3 = tb.P3;
+    float2* V = reinterpret_cast<float2*>(sm_raw);
+    float2* S1 = V + P3;
+    float2* S2 = S1 + n1 * n1 * kTB0;
+    float2* O = S2 + n1 * kTB0 * kTB0;
+    float* W = reinterpret_cast<float*>(O + kTB0 * kTB0 * kTB0);
+    const float2* src = c.tpot + (int64_t)tbox_index(tb, la, A.ib, A.jb, A.kb) * P3;
+    for (int k = threadIdx.x; k < P3; k += blockDim.x) V[k] = src[k];
+    const int ms[3] = {m0, m1, m2};
+    for (int d = 0; d < 3; ++d) {
+        const float off = (float)(R.lo[d] - A.c[d]);  // grid point i of the region relative to A's centre (exact)
+        basis_rows(tb, A, d, ms[d], [&](int i) { return off + (float)i; }, W + d * kTB0 * n1);
+    }
+    __syncthreads();
+    interp3(n1, V, W, W + kTB0 * n1, W + 2 * kTB0 * n1, m0, m1, m2, S1, S2, O);
+    for (int t = threadIdx.x; t < m0 * m1 * m2; t += blockDim.x) {
+        const int ix = t % m0, iy = (t / m0) % m1, iz = t / (m0 * m1);
+        far[(R.lo[2] + iz) * plane + (int64_t)(R.lo[1] + iy) * tb.nx + R.lo[0] + ix] =
+            make_float4(O[t].x, 0.f, O[t].y, 0.f);
+    }
+}
+
 // ---- near field (LJ within cut-offs, erfc remainders within r_short) + epilogue
 template <int NXB, int NYB, int NZB>
 struct NearShape {
@@ -1100,7 +1737,7 @@ struct NearShape {
 };
 
 template <int NXB, int NYB, int NZB, int SM, bool DU, bool DH>
-__device__ void near_body(const EvalArgs& a, int b, Ring<SM, true>& r) {
+__device__ void near_body(const EvalArgs& a, int b, Ring<SM, true>& r, float4* tab) {
     using Sh = NearShape<NXB, NYB, NZB>;
     constexpr int P = Sh::P;
     const int tid = threadIdx.x;
@@ -1112,8 +1749,6 @@ __device__ void near_body(const EvalArgs& a, int b, Ring<SM, true>& r) {
     for (int p = 0; p < P; ++p) gx[p] = (float)(i0 + p);
     const float fy = (float)j, fz = (float)k;
     const float rs2 = (float)((a.ph.rs / a.g.h) * (a.ph.rs / a.g.h));
-    const float xs = (float)(a.g.h / a.ph.eta);
-    const float aa_ = (float)a.ph.a;
     const float c0h = (float)(a.ph.phi_c0 * a.g.h), h0h = (float)(a.ph.phi_h0 * a.g.h);
     const bool DC = a.o.c != nullptr;
     const double rnear = a.meta->rnear;
@@ -1127,12 +1762,15 @@ __device__ void near_body(const EvalArgs& a, int b, Ring<SM, true>& r) {
         for (int s = 0; s < SM; ++s) ljh[p][s] = ljl[p][s] = 0.f;
     }
     unsigned hit = 0u;
+    const float tinv = a.ntab_inv;
     Cursor cur;
     __syncthreads();
+    for (int k = tid; k < 2 * kNTab; k += Sh::NT) tab[k] = a.ntab[k];
     if (tid == 0) {
         cur.e = b * a.near_cap;
         cur.e_end = cur.e + a.near_cnt[b];
         cur.off = 0;
+        cur.left = INT_MAX;
         cur.produced = 0;
         cur.done = false;
         for (int s = 0; s < kStages; ++s) cur.last_phase[s] = -1;
@@ -1162,11 +1800,20 @@ __device__ void near_body(const EvalArgs& a, int b, Ring<SM, true>& r) {
                 if (d2 >= rn2) continue;
                 if (d2 < rs2) {
                     if (d2 > 0.f) {
+                        // erfc(x)/d and e^{-x^2}[erfcx(x-a) + erfcx(x+a)]/d from the cubic pieces in d
                         const float ri = rsqrt_approx(d2);
                         const float qr = g0.w * ri;
-                        const float x = d2 * ri * xs;
-                        if (DC) psc[p] = fmaf(qr, erfcf(x), psc[p]);
-                        if (DH) psh[p] = fmaf(qr, __expf(-x * x) * (erfcxf(x - aa_) + erfcxf(x + aa_)), psh[p]);
+                        const float uu = d2 * ri * tinv;
+                        const int it = min((int)uu, kNTab - 1);
+                        const float tt = uu - (float)it;
+                        if (DC) {
+                            const float4 cc = tab[2 * it];
+                            psc[p] = fmaf(qr, fmaf(fmaf(fmaf(cc.w, tt, cc.z), tt, cc.y), tt, cc.x), psc[p]);
+                        }
+                        if (DH) {
+                            const float4 ch = tab[2 * it + 1];
+                            psh[p] = fmaf(qr, fmaf(fmaf(fmaf(ch.w, tt, ch.z), tt, ch.y), tt, ch.x), psh[p]);
+                        }
                     } else {
                         hit |= 1u << p;
                         if (DC) psc[p] -= g0.w * c0h;
@@ -1262,9 +1909,10 @@ __global__ void __launch_bounds__(FarShape<NXB, NYB, NZB, PF>::NT) k_far32(EvalA
 template <int NXB, int NYB, int NZB, int SM, bool DU, bool DH>
 __global__ void __launch_bounds__(NearShape<NXB, NYB, NZB>::NT) k_near32(EvalArgs a) {
     __shared__ Ring<SM, true> r;
+    __shared__ float4 tab[2 * kNTab];
     if (threadIdx.x == 0) r.inited = 0;
     if (a.meta->overflow) return;
-    near_body<NXB, NYB, NZB, SM, DU, DH>(a, blockIdx.x, r);
+    near_body<NXB, NYB, NZB, SM, DU, DH>(a, blockIdx.x, r, tab);
 }
 
 // ---- persistent kernels over the (solute, batch) items of many solutes
@@ -1309,6 +1957,7 @@ __global__ void __launch_bounds__(FarShape<NXB, NYB, NZB, PF>::NT) k_far32_batch
 template <int NXB, int NYB, int NZB, int SM, bool DU, bool DH>
 __global__ void __launch_bounds__(NearShape<NXB, NYB, NZB>::NT) k_near32_batched(BatchEval be) {
     __shared__ Ring<SM, true> r;
+    __shared__ float4 tab[2 * kNTab];
     __shared__ int s_item;
     __shared__ EvalArgs sa;
     if (threadIdx.x == 0) r.inited = 0;
@@ -1323,7 +1972,7 @@ __global__ void __launch_bounds__(NearShape<NXB, NYB, NZB>::NT) k_near32_batched
         if (it >= be.total) break;
         if (sa.meta->overflow) continue;
         const int sid = find_solute(be, it);
-        near_body<NXB, NYB, NZB, SM, DU, DH>(sa, it - be.item_off[sid], r);
+        near_body<NXB, NYB, NZB, SM, DU, DH>(sa, it - be.item_off[sid], r, tab);
     }
 }
 
@@ -1437,8 +2086,19 @@ struct TreeState {
     bool prepared = false;
     std::string tuned_key;       // problem class the current (variant, leaf) was tuned for
     BatchCache* bc = nullptr;
-    cudaEvent_t ev[3] = {nullptr, nullptr, nullptr};  // far / near timing (debug_flags bit 1)
+    cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};  // box / far / near timing (debug_flags bit 1)
     bool timed = false;
+    // target boxes (cluster-particle far field)
+    TBoxes tb{};
+    int cap_cp = 0, cap_dn = 0, cap_tbox = 0;
+    int64_t cap_cp_ent = 0, cap_dn_ent = 0, cap_tpot = 0;
+    int *cp_cnt = nullptr, *dn_cnt = nullptr, *dn_ent = nullptr, *tflag = nullptr, *tnch = nullptr;
+    int2* cp_ent = nullptr;
+    float2 *tpot = nullptr, *tpart = nullptr;
+    // short-range kernel tables
+    float4* ntab = nullptr;
+    double ntab_key[4] = {0.0, 0.0, 0.0, -1.0};
+    float ntab_inv = 0.f;
 };
 
 namespace {
@@ -1468,7 +2128,8 @@ int sm_count() {
 }
 
 // Host allocations for one solute (never inside a stream capture).
-rism_status tree_reserve(TreeState* s, const DevTables& t, const GridD& g, const rism_options& o, std::string& err) {
+rism_status tree_reserve(TreeState* s, const DevTables& t, const GridD& g, const Phys& ph, const rism_options& o,
+                         std::string& err) {
     cudaError_t e = cudaSuccess;
     const int n = (int)t.n;
     const int deg = o.degree, np = deg + 1, P3 = np * np * np;
@@ -1525,7 +2186,147 @@ rism_status tree_reserve(TreeState* s, const DevTables& t, const GridD& g, const
         if ((e = regrow(s->near_ent, (size_t)s->nb * s->cap_near))) return cuda_err(err, e, "near list");
         s->cap_near_ent = (int64_t)s->nb * s->cap_near;
     }
+    // target boxes: levels of aligned 16 << l cubes up to one that covers the grid
+    TBoxes& tb = s->tb;
+    tb = TBoxes{};
+    tb.nx = g.nx;
+    tb.ny = g.ny;
+    tb.nz = g.nz;
+    tb.deg = deg;
+    tb.P3 = P3;
+    tb.enabled = o.target_proxies != 0 && n > 0;
+    for (int k = 0; k <= kMaxDegree; ++k)  // cos(k pi / n) as sin(pi (n - 2k) / (2n)): exact 0 at k = n/2
+        tb.ck[k] = k <= deg ? (float)std::sin(3.14159265358979323846 * (deg - 2 * k) / (2.0 * deg)) : 0.f;
+    const int nmax = std::max(g.nx, std::max(g.ny, g.nz));
+    tb.L = 1;
+    while ((kTB0 << (tb.L - 1)) < nmax && tb.L < kMaxTL) ++tb.L;
+    tb.nbox = 0;
+    for (int l = 0; l < tb.L; ++l) {
+        const int E = kTB0 << l;
+        tb.nbx[l] = (g.nx + E - 1) / E;
+        tb.nby[l] = (g.ny + E - 1) / E;
+        tb.nbz[l] = (g.nz + E - 1) / E;
+        tb.off[l] = tb.nbox;
+        tb.nbox += tb.nbx[l] * tb.nby[l] * tb.nbz[l];
+    }
+    if (tb.enabled) {
+        if (s->cap_cp == 0) s->cap_cp = 64;
+        if (s->cap_dn == 0) s->cap_dn = 128;
+        if (tb.nbox + 1 > s->cap_tbox) {
+            if ((e = regrow(s->cp_cnt, (size_t)tb.nbox + 1)) || (e = regrow(s->dn_cnt, (size_t)tb.nbox + 1)) ||
+                (e = regrow(s->tflag, (size_t)tb.nbox + 1)) || (e = regrow(s->tnch, (size_t)tb.nbox + 1)))
+                return cuda_err(err, e, "target boxes");
+            s->cap_tbox = tb.nbox + 1;
+        }
+        if ((int64_t)tb.nbox * s->cap_cp > s->cap_cp_ent) {
+            if ((e = regrow(s->cp_ent, (size_t)tb.nbox * s->cap_cp))) return cuda_err(err, e, "box lists");
+            s->cap_cp_ent = (int64_t)tb.nbox * s->cap_cp;
+        }
+        if ((int64_t)tb.nbox * s->cap_dn > s->cap_dn_ent) {
+            if ((e = regrow(s->dn_ent, (size_t)tb.nbox * s->cap_dn))) return cuda_err(err, e, "pass-down lists");
+            s->cap_dn_ent = (int64_t)tb.nbox * s->cap_dn;
+        }
+        if ((int64_t)tb.nbox * P3 > s->cap_tpot) {
+            if ((e = regrow(s->tpot, (size_t)tb.nbox * P3)) ||
+                (e = regrow(s->tpart, (size_t)tb.nbox * (kCPChunks - 1) * P3)))
+                return cuda_err(err, e, "proxy targets");
+            s->cap_tpot = (int64_t)tb.nbox * P3;
+        }
+    }
+    // Short-range kernels of the near field as cubic Hermite pieces in d (grid units) over [0, r_short]:
+    // F_c(d) = erfc(x) and F_h(d) = e^{-x^2}[erfcx(x-a) + erfcx(x+a)] = e^{a^2-2ax} erfc(x-a) + e^{a^2+2ax} erfc(x+a),
+    // x = d h / eta, a = kappa eta / 2, with their derivatives dF_c/dx = -2/sqrt(pi) e^{-x^2} and
+    // dF_h/dx = -2a e^{a^2-2ax} erfc(x-a) + 2a e^{a^2+2ax} erfc(x+a) - 4/sqrt(pi) e^{-x^2}; built in FP64.
+    const double key[4] = {ph.eta, g.h, ph.a, ph.rs};
+    if (!s->ntab || std::memcmp(key, s->ntab_key, sizeof key) != 0) {
+        if (!s->ntab && (e = cudaMalloc(&s->ntab, sizeof(float4) * 2 * kNTab)) != cudaSuccess)
+            return cuda_err(err, e, "kernel table");
+        const double sx = g.h / ph.eta, a = ph.a, rsg = ph.rs / g.h, D = rsg / kNTab;
+        const double tsp = 2.0 / std::sqrt(3.14159265358979323846);
+        std::vector<double> fc(kNTab + 1), gc(kNTab + 1), fh(kNTab + 1), gh(kNTab + 1);
+        for (int k = 0; k <= kNTab; ++k) {
+            const double x = k * D * sx, ex = std::exp(-x * x);
+            const double em = std::exp(a * a - 2.0 * a * x), ep = std::exp(a * a + 2.0 * a * x);
+            const double cm = std::erfc(x - a), cp = std::erfc(x + a);
+            fc[k] = std::erfc(x);
+            gc[k] = -tsp * ex * sx * D;  // derivative per segment length
+            fh[k] = em * cm + ep * cp;
+            gh[k] = (-2.0 * a * em * cm + 2.0 * a * ep * cp - 2.0 * tsp * ex) * sx * D;
+        }
+        std::vector<float4> tab(2 * kNTab);
+        auto herm = [](double f0, double f1, double g0, double g1) {
+            return make_float4((float)f0, (float)g0, (float)(3.0 * (f1 - f0) - 2.0 * g0 - g1),
+                               (float)(2.0 * (f0 - f1) + g0 + g1));
+        };
+        for (int k = 0; k < kNTab; ++k) {
+            tab[2 * k] = herm(fc[k], fc[k + 1], gc[k], gc[k + 1]);
+            tab[2 * k + 1] = herm(fh[k], fh[k + 1], gh[k], gh[k + 1]);
+        }
+        if ((e = cudaMemcpy(s->ntab, tab.data(), sizeof(float4) * 2 * kNTab, cudaMemcpyHostToDevice)) != cudaSuccess)
+            return cuda_err(err, e, "kernel table");
+        std::memcpy(s->ntab_key, key, sizeof key);
+        s->ntab_inv = (float)(kNTab / rsg);
+    }
     return RISM_OK;
+}
+
+// Grow list slots after an overflow (powers of two); false when nothing can grow.
+bool grow_lists(TreeState* s, const TreeMeta& m) {
+    if (m.wide || m.build_overflow) return false;
+    auto pow2 = [](int v) {
+        int p = 1;
+        while (p < v) p <<= 1;
+        return p;
+    };
+    bool grew = false;
+    auto grow = [&](int need, int& cap) {
+        if (need > cap && need < (1 << 20)) {
+            cap = pow2(need);
+            grew = true;
+        }
+    };
+    grow(m.far_need, s->cap_far);
+    grow(m.near_need, s->cap_near);
+    grow(m.cp_need, s->cap_cp);
+    grow(m.dn_need, s->cap_dn);
+    return grew;
+}
+
+CPArgs make_cp(TreeState* s) {
+    CPArgs c;
+    c.tb = s->tb;
+    c.cp_cnt = s->cp_cnt;
+    c.cp_ent = s->cp_ent;
+    c.cp_cap = s->cap_cp;
+    c.tpot = s->tpot;
+    c.tpart = s->tpart;
+    c.tnch = s->tnch;
+    c.tflag = s->tflag;
+    return c;
+}
+
+// Box-level far field (no allocation, no host wait): proxies of every target box, the downward pass and the
+// interpolation onto the far-field buffer.  Returns the number of launches.
+int cp_enqueue(TreeState* s, const EvalArgs& a, bool dh, cudaStream_t st) {
+    const TBoxes& tb = s->tb;
+    if (!tb.enabled) return 0;
+    const CPArgs c = make_cp(s);
+    const int n1 = tb.deg + 1;
+    const int npass = (n1 * n1 * ((n1 + kCPP - 1) / kCPP) + kCPThreads - 1) / kCPThreads;
+    const dim3 grid(tb.nbox, kCPChunks, npass);
+    if (dh) k_cp_eval<true><<<grid, kCPThreads, 0, st>>>(a, c);
+    else k_cp_eval<false><<<grid, kCPThreads, 0, st>>>(a, c);
+    k_cp_reduce<<<tb.nbox, 256, 0, st>>>(c, s->meta);
+    int launches = 2;
+    const size_t sl = interp_smem(n1, n1), sd = interp_smem(n1, kTB0);
+    cudaFuncSetAttribute(k_l2l, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sl);
+    cudaFuncSetAttribute(k_tdown, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sd);
+    for (int l = tb.L - 2; l >= 0; --l) {
+        k_l2l<<<tb.nbx[l] * tb.nby[l] * tb.nbz[l], 256, sl, st>>>(c, l, s->meta);
+        ++launches;
+    }
+    k_tdown<<<tb.nbx[0] * tb.nby[0] * tb.nbz[0], 256, sd, st>>>(c, s->far, s->meta);
+    return launches + 1;
 }
 
 // Kernel launches of a7..a9 for one solute (no allocation, no host wait:
@@ -1556,7 +2357,18 @@ rism_status tree_enqueue(TreeState* s, const DevTables& t, const GridD& g, const
                                                        s->part, s->src, s->srcf);
         s->launches += 6;
     }
-    ListArgs fa{s->nbx, s->nby, s->nbz, sd.nx, sd.ny, sd.nz, o.theta, n, P3, s->cap_far};
+    const TBoxes& tb = s->tb;
+    if (tb.enabled) {
+        TListArgs ta{tb, 0, n, P3, o.theta, s->cap_cp, s->cap_dn, s->cp_cnt, s->cp_ent, s->dn_cnt, s->dn_ent};
+        for (int l = tb.L - 1; l >= 0; --l) {
+            ta.l = l;
+            const int nbl = tb.nbx[l] * tb.nby[l] * tb.nbz[l];
+            k_tbox_lists<<<(nbl + kListWarps - 1) / kListWarps, 32 * kListWarps, 0, st>>>(ta, s->nodes, s->meta);
+            ++s->launches;
+        }
+    }
+    ListArgs fa{s->nbx, s->nby, s->nbz, sd.nx, sd.ny, sd.nz, o.theta, n, P3, s->cap_far,
+                tb.enabled ? s->dn_cnt : nullptr, s->dn_ent, s->cap_dn, tb};
     ListArgs na = fa;
     na.cap = s->cap_near;
     const int lgrid = (s->nb + kListWarps - 1) / kListWarps;
@@ -1587,6 +2399,9 @@ EvalArgs make_args(TreeState* s, const DevTables& t, const GridD& g, const Phys&
     a.far_cap = s->cap_far;
     a.near_cap = s->cap_near;
     a.far = s->far;
+    a.far_init = s->tb.enabled ? 1 : 0;
+    a.ntab = s->ntab;
+    a.ntab_inv = s->ntab_inv;
     a.o = out;
     a.err = t.err;
     a.meta = s->meta;
@@ -1668,8 +2483,17 @@ struct BatchCache {
 void tree_destroy(TreeState* s) {
     if (!s) return;
     delete s->bc;
-    for (int k = 0; k < 3; ++k)
+    for (int k = 0; k < 4; ++k)
         if (s->ev[k]) cudaEventDestroy(s->ev[k]);
+    cudaFree(s->cp_cnt);
+    cudaFree(s->dn_cnt);
+    cudaFree(s->dn_ent);
+    cudaFree(s->tflag);
+    cudaFree(s->cp_ent);
+    cudaFree(s->tpot);
+    cudaFree(s->tpart);
+    cudaFree(s->tnch);
+    cudaFree(s->ntab);
     cudaFree(s->code);
     cudaFree(s->idx);
     cudaFree(s->code2);
@@ -1696,7 +2520,7 @@ void tree_destroy(TreeState* s) {
 rism_status tree_prepare(TreeState* s, const DevTables& t, const GridD& g, const Phys& ph, const rism_options& o,
                          cudaStream_t st, std::string& err) {
     if (!o.autotune) s->leaf = o.leaf;
-    rism_status r = tree_reserve(s, t, g, o, err);
+    rism_status r = tree_reserve(s, t, g, ph, o, err);
     if (r != RISM_OK) return r;
     return tree_enqueue(s, t, g, ph, o, st, err);
 }
@@ -1714,7 +2538,7 @@ static rism_status tree_autotune(TreeState* s, const DevTables& t, const GridD& 
             s->variant = it->second.first;
             s->leaf = it->second.second;
             s->tuned_key = key;
-            rism_status r = tree_reserve(s, t, g, o, err);
+            rism_status r = tree_reserve(s, t, g, ph, o, err);
             return r != RISM_OK ? r : tree_enqueue(s, t, g, ph, o, st, err);
         }
     }
@@ -1729,12 +2553,13 @@ static rism_status tree_autotune(TreeState* s, const DevTables& t, const GridD& 
             for (int attempt = 0; attempt < 2; ++attempt) {
                 s->variant = v;
                 s->leaf = leaves[li];
-                rism_status r = tree_reserve(s, t, g, o, err);
+                rism_status r = tree_reserve(s, t, g, ph, o, err);
                 if (r != RISM_OK) return r;
                 cudaEventRecord(e0, st);
                 r = tree_enqueue(s, t, g, ph, o, st, err);
                 if (r != RISM_OK) return r;
                 EvalArgs a = make_args(s, t, g, ph, o, out);
+                cp_enqueue(s, a, out.h != nullptr, st);
                 dispatch(t.smax, v, 0, out.u != nullptr, out.h != nullptr, &a, s->nb, nullptr, 0, st);
                 cudaEventRecord(e1, st);
                 cudaMemcpyAsync(s->h_meta, s->meta, sizeof(TreeMeta), cudaMemcpyDeviceToHost, st);
@@ -1742,21 +2567,8 @@ static rism_status tree_autotune(TreeState* s, const DevTables& t, const GridD& 
                 if (ce != cudaSuccess) return cuda_err(err, ce, "autotune");
                 const TreeMeta& m = *s->h_meta;
                 if (m.overflow) {
-                    // grow the per-batch list slots and time this candidate again
-                    bool grew = false;
-                    int p2 = 1;
-                    if (!m.wide && m.far_need > s->cap_far) {
-                        while (p2 < m.far_need) p2 <<= 1;
-                        s->cap_far = p2;
-                        grew = true;
-                    }
-                    p2 = 1;
-                    if (!m.wide && m.near_need > s->cap_near) {
-                        while (p2 < m.near_need) p2 <<= 1;
-                        s->cap_near = p2;
-                        grew = true;
-                    }
-                    if (grew && !m.build_overflow) continue;
+                    // grow the list slots and time this candidate again
+                    if (grow_lists(s, m)) continue;
                     break;  // too wide or too deep for this leaf size: skip the candidate
                 }
                 float ms = 0.f;
@@ -1778,7 +2590,7 @@ static rism_status tree_autotune(TreeState* s, const DevTables& t, const GridD& 
         g_tune[key] = {bv, bl};
         tune_save();
     }
-    rism_status r = tree_reserve(s, t, g, o, err);
+    rism_status r = tree_reserve(s, t, g, ph, o, err);
     return r != RISM_OK ? r : tree_enqueue(s, t, g, ph, o, st, err);
 }
 
@@ -1798,21 +2610,25 @@ rism_status tree_eval(TreeState* s, const DevTables& t, const GridD& g, const Ph
     const bool du = out.u != nullptr, dh = out.h != nullptr;
     cudaError_t e;
     s->timed = (o.debug_flags & 2) != 0;
+    int cpl = 0;
     if (s->timed) {
-        for (int k = 0; k < 3; ++k)
+        for (int k = 0; k < 4; ++k)
             if (!s->ev[k]) cudaEventCreate(&s->ev[k]);
         cudaEventRecord(s->ev[0], st);
-        e = dispatch(t.smax, s->variant, 2, du, dh, &a, s->nb, nullptr, 0, st);
+        cpl = cp_enqueue(s, a, dh, st);
         cudaEventRecord(s->ev[1], st);
-        if (e == cudaSuccess) e = dispatch(t.smax, s->variant, 3, du, dh, &a, s->nb, nullptr, 0, st);
+        e = dispatch(t.smax, s->variant, 2, du, dh, &a, s->nb, nullptr, 0, st);
         cudaEventRecord(s->ev[2], st);
+        if (e == cudaSuccess) e = dispatch(t.smax, s->variant, 3, du, dh, &a, s->nb, nullptr, 0, st);
+        cudaEventRecord(s->ev[3], st);
     } else {
+        cpl = cp_enqueue(s, a, dh, st);
         e = dispatch(t.smax, s->variant, 0, du, dh, &a, s->nb, nullptr, 0, st);
     }
     if (e != cudaSuccess) return cuda_err(err, e, "tree eval");
     if ((e = cudaMemcpyAsync(s->h_meta, s->meta, sizeof(TreeMeta), cudaMemcpyDeviceToHost, st)) != cudaSuccess)
         return cuda_err(err, e, "tree meta copy");
-    info.launches += s->launches + 2;
+    info.launches += s->launches + 2 + cpl;
     const ShapeDesc sd = shape_of(s->variant);
     info.batch[0] = sd.nx;
     info.batch[1] = sd.ny;
@@ -1835,38 +2651,30 @@ rism_status tree_post(TreeState* s, rism_info& info, bool& retry, std::string& e
         return RISM_E_NOMEM;
     }
     if (m.overflow) {
-        bool grew = false;
-        auto pow2 = [](int v) {
-            int p = 1;
-            while (p < v) p <<= 1;
-            return p;
-        };
-        if (m.far_need > s->cap_far && m.far_need < (1 << 20)) {
-            s->cap_far = pow2(m.far_need);
-            grew = true;
-        }
-        if (m.near_need > s->cap_near && m.near_need < (1 << 20)) {
-            s->cap_near = pow2(m.near_need);
-            grew = true;
-        }
-        if (grew) {
+        if (grow_lists(s, m)) {
             delete s->bc;  // buffers moved: the captured graph is stale
             s->bc = nullptr;
             retry = true;
-            char buf[160];
-            std::snprintf(buf, sizeof buf, "list slots grown: far need %d -> cap %d, near need %d -> cap %d",
-                          m.far_need, s->cap_far, m.near_need, s->cap_near);
+            char buf[256];
+            std::snprintf(buf, sizeof buf,
+                          "list slots grown: far need %d -> cap %d, near need %d -> cap %d, box need %d -> cap %d, "
+                          "pass-down need %d -> cap %d",
+                          m.far_need, s->cap_far, m.near_need, s->cap_near, m.cp_need, s->cap_cp, m.dn_need,
+                          s->cap_dn);
             err = buf;
             return RISM_OK;
         }
         err = "list capacity exceeded";
         return RISM_E_NOMEM;
     }
-    info.far_ms = info.near_ms = 0.f;
+    info.far_ms = info.near_ms = info.box_ms = 0.f;
     if (s->timed && s->ev[0]) {
-        cudaEventElapsedTime(&info.far_ms, s->ev[0], s->ev[1]);
-        cudaEventElapsedTime(&info.near_ms, s->ev[1], s->ev[2]);
+        cudaEventElapsedTime(&info.box_ms, s->ev[0], s->ev[1]);
+        cudaEventElapsedTime(&info.far_ms, s->ev[1], s->ev[2]);
+        cudaEventElapsedTime(&info.near_ms, s->ev[2], s->ev[3]);
     }
+    info.cp_pairs = (int64_t)m.cp_pairs;
+    info.tree_boxes = m.tboxes;
     info.tree_nodes = m.nnodes;
     info.tree_proxied = m.nprox;
     info.tree_leaves = m.nleaves;
@@ -1893,7 +2701,7 @@ rism_status batch_eval(std::vector<BatchItem>& items, const rism_options& o, cud
         it.tree->variant = variant;
         if (!o.autotune) it.tree->leaf = o.leaf;
         else it.tree->leaf = s0->leaf;
-        rism_status r = tree_reserve(it.tree, *it.t, it.g, o, msg);
+        rism_status r = tree_reserve(it.tree, *it.t, it.g, it.ph, o, msg);
         if (r != RISM_OK) return r;
         args[b] = make_args(it.tree, *it.t, it.g, it.ph, o, it.o);
         off[b + 1] = off[b] + it.tree->nb;
@@ -1909,10 +2717,12 @@ rism_status batch_eval(std::vector<BatchItem>& items, const rism_options& o, cud
         const BatchItem& it = items[b];
         TreeState* s = it.tree;
         const void* ptrs[] = {it.t->geo, it.t->srcf, it.t->ljd, it.t->ljf, it.raw, s->code, s->nodes, s->part,
-                              s->cell_start, s->far_ent, s->near_ent};
+                              s->cell_start, s->far_ent, s->near_ent, s->cp_cnt, s->cp_ent, s->dn_cnt, s->dn_ent,
+                              s->tpot, s->tpart, s->tnch, s->tflag};
         put(ptrs, sizeof ptrs);
+        put(&s->tb, sizeof(TBoxes));
         const int ints[] = {(int)it.t->n, it.t->smax, s->leaf, s->max_nodes, s->max_prox, s->max_items, s->cap_far,
-                            s->cap_near, it.lj_mode};
+                            s->cap_near, it.lj_mode, s->cap_cp, s->cap_dn};
         put(ints, sizeof ints);
         const double dbl[] = {it.lj_rcut, it.lj_tol};
         put(dbl, sizeof dbl);
@@ -1948,6 +2758,7 @@ rism_status batch_eval(std::vector<BatchItem>& items, const rism_options& o, cud
                 if (e != cudaSuccess) r = cuda_err(msg, e, "setup");
             }
             if (r == RISM_OK) r = tree_enqueue(it.tree, tt, it.g, it.ph, o, cs, msg);
+            if (r == RISM_OK) cp_enqueue(it.tree, args[b], it.o.h != nullptr, cs);
         }
         if (r == RISM_OK) {
             cudaMemsetAsync(bc->d_queue, 0, sizeof(int) * 2, cs);

@@ -43,7 +43,7 @@ class Options(C.Structure):
                 ("lj_tol", C.c_double), ("eta", C.c_double), ("T", C.c_double), ("eps_r", C.c_double),
                 ("kappa", C.c_double), ("k_e", C.c_double), ("k_B", C.c_double), ("r_short", C.c_double),
                 ("autotune", C.c_int32), ("wait_limit", C.c_int64),
-                ("debug_flags", C.c_int32)]
+                ("debug_flags", C.c_int32), ("target_proxies", C.c_int32)]
 
 
 class Info(C.Structure):
@@ -51,7 +51,8 @@ class Info(C.Structure):
                 ("nsite", C.c_int32), ("tree_nodes", C.c_int32), ("tree_proxied", C.c_int32),
                 ("tree_leaves", C.c_int32), ("direct_pairs", C.c_int64), ("proxy_pairs", C.c_int64),
                 ("near_pairs", C.c_int64), ("batch", C.c_int32 * 3), ("kernel_variant", C.c_int32),
-                ("launches", C.c_int32), ("eval_ms", C.c_float), ("far_ms", C.c_float), ("near_ms", C.c_float)]
+                ("launches", C.c_int32), ("eval_ms", C.c_float), ("far_ms", C.c_float), ("near_ms", C.c_float),
+                ("box_ms", C.c_float), ("tree_boxes", C.c_int32), ("cp_pairs", C.c_int64)]
 
 
 EXPORTS = ["rism_default_options", "rism_grid_create", "rism_set_solute", "rism_set_solvent", "rism_potential",

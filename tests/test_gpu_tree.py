@@ -61,7 +61,7 @@ def test_globule2000_degree8_theta07(R):
     idx = _sampled(w)
     ref = O.fields(O.Problem.from_workload(w), idx=idx)
     g = run(R, w)
-    assert g["info"]["proxy_pairs"] > 0 and g["info"]["tree_proxied"] > 0
+    assert g["info"]["proxy_pairs"] + g["info"]["cp_pairs"] > 0 and g["info"]["tree_proxied"] > 0
     gs = {k: g[k][:, idx] for k in ("u", "c", "h")}
     check_fields(gs, ref, ("u", "c", "h"), TREE_TOL, w.grid, w.solute.xyz, idx=idx, label="cfg1 tree")
 
@@ -145,3 +145,44 @@ def test_ellipsoid13600_degree4_theta05_long_lists(R):
     g = run(R, w, keys=("c", "h"), degree=4, theta=0.5)
     for k in ("c", "h"):
         assert rel_l2(g[k][:, idx], ref[k]) <= 1e-4, k
+
+
+def test_target_proxies_on_and_off_agree_with_oracle(R):
+    """Cluster-particle far field (proxy targets on grid boxes of 16^3 points and up) against the particle-
+    cluster form and the oracle on the 2,000-atom globule: both within the treecode tolerance, and the box
+    level takes a large share of the work."""
+    w = I.workload(1)
+    idx = _sampled(w, count=2500, seed=11)
+    ref = O.fields(O.Problem.from_workload(w), idx=idx)
+    on = run(R, w, target_proxies=1)
+    off = run(R, w, target_proxies=0)
+    assert on["info"]["cp_pairs"] > 0 and on["info"]["tree_boxes"] > 0
+    assert off["info"]["cp_pairs"] == 0
+    assert on["info"]["direct_pairs"] < 0.5 * off["info"]["direct_pairs"]
+    for g, lab in ((on, "boxes on"), (off, "boxes off")):
+        gs = {k: g[k][:, idx] for k in ("u", "c", "h")}
+        check_fields(gs, ref, ("u", "c", "h"), TREE_TOL, w.grid, w.solute.xyz, idx=idx, label=lab)
+
+
+def test_target_proxies_ragged_clipped_boxes(R):
+    """A grid whose sides are not multiples of 16 (boxes clipped at the edges, some too thin for proxies, so
+    their points take the field of an enclosing box) with a solute off-centre: all points against the oracle."""
+    w = I.small_workload(n_atoms=700, n=(150, 37, 70), h=0.5, seed=21, ions=True, lj_rcut=6.0, net=3.0)
+    w.solute.xyz[:, 0] -= 12.0
+    ref = O.fields(O.Problem.from_workload(w))
+    g = run(R, w, target_proxies=1, leaf=16)
+    assert g["info"]["cp_pairs"] > 0
+    check_fields(g, ref, ("u", "c", "h"), TREE_TOL, w.grid, w.solute.xyz, label="ragged boxes")
+
+
+def test_target_proxies_error_falls_with_degree(R):
+    """Geometric convergence with the box-level interpolation active."""
+    w = I.workload(1)
+    idx = I.sample_indices(w.grid.npts, 2000, seed=13)
+    ref = O.fields(O.Problem.from_workload(w), idx=idx, want=("c",))
+    errs = []
+    for deg in (3, 5, 7, 9):
+        g = run(R, w, keys=("c",), degree=deg, target_proxies=1)
+        assert g["info"]["cp_pairs"] > 0
+        errs.append(rel_l2(g["c"][:, idx], ref["c"]))
+    assert errs[0] > errs[1] > errs[2] > errs[3], errs
