@@ -451,14 +451,16 @@ def suite_pareto(args):
     ms32, e32, _ = run(method=R.METHOD_DIRECT, precision=R.PREC_FP32)
     print(json.dumps({"suite": "pareto", "method": "direct", "precision": "fp32", "ms": ms32,
                       "speedup_vs_fp64_direct": ms64 / ms32, "err": e32}), flush=True)
-    for deg in (4, 6, 8):
-        for th in (0.5, 0.6, 0.7, 0.8):
-            ms, e, info = run(method=R.METHOD_TREECODE, precision=R.PREC_FP32, degree=deg, theta=th, autotune=1)
-            print(json.dumps({"suite": "pareto", "method": "treecode", "precision": "fp32", "degree": deg,
-                              "theta": th, "ms": ms, "speedup_vs_fp64_direct": ms64 / ms,
-                              "gpts_site_s": S * M / (ms * 1e-3) / 1e9, "err": e,
-                              "direct_pairs": info["direct_pairs"], "proxy_pairs": info["proxy_pairs"],
-                              "near_pairs": info["near_pairs"], "variant": info["kernel_variant"]}), flush=True)
+    cases = [(deg, th, 1) for deg in (4, 6, 8) for th in (0.5, 0.6, 0.7, 0.8)] + [(8, 0.7, 0)]
+    for deg, th, tp in cases:
+        ms, e, info = run(method=R.METHOD_TREECODE, precision=R.PREC_FP32, degree=deg, theta=th, autotune=1,
+                          target_proxies=tp)
+        print(json.dumps({"suite": "pareto", "method": "treecode", "precision": "fp32", "degree": deg,
+                          "theta": th, "target_proxies": tp, "ms": ms, "speedup_vs_fp64_direct": ms64 / ms,
+                          "gpts_site_s": S * M / (ms * 1e-3) / 1e9, "err": e,
+                          "direct_pairs": info["direct_pairs"], "proxy_pairs": info["proxy_pairs"],
+                          "cp_pairs": info["cp_pairs"], "near_pairs": info["near_pairs"],
+                          "variant": info["kernel_variant"]}), flush=True)
 
 
 def suite_batched(args):

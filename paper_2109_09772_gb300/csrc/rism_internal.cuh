@@ -165,6 +165,26 @@ __device__ __forceinline__ void ff_add(float& hi, float& lo, float v) {
     lo += t;
 }
 
+// float -> double by assembling the IEEE-754 fields on the integer pipe (the FP64 pipe of this part is slow):
+// sign, exponent rebiased by 1023 - 127 = 896, fraction shifted left by 52 - 23 = 29.  Zero, subnormals,
+// infinities and NaN take the conversion instruction.
+__device__ __forceinline__ double f2d_alu(float f) {
+    const uint32_t b = __float_as_uint(f);
+    const uint32_t e = (b >> 23) & 0xffu;
+    if (e == 0u || e == 0xffu) return (double)f;
+    const unsigned long long r = ((unsigned long long)(b >> 31) << 63) |
+                                 ((unsigned long long)(e + 896u) << 52) |
+                                 ((unsigned long long)(b & 0x7fffffu) << 29);
+    return __longlong_as_double((long long)r);
+}
+
+// Error-free sum of two floats: a + b = s + e exactly.
+__device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
+    s = a + b;
+    const float bb = s - a;
+    e = (a - (s - bb)) + (b - bb);
+}
+
 // Split a double into hi + lo floats (|lo| <= ulp(hi)/2).
 __device__ __forceinline__ void split_ff(double v, float& hi, float& lo) {
     hi = __double2float_rn(v);

@@ -55,6 +55,7 @@ constexpr int kMaxLevel = kMortonBits;   // octree depth limit
 constexpr int kChunk = 16;               // atoms per upward-pass work item
 constexpr int kT = 64;                   // sources per shared-memory tile
 constexpr int kStack = 8 * kMaxLevel + 8;
+constexpr double kCellFrac = 0.25;        // near-field cells are at least this fraction of the near radius wide
 
 struct Node {
     int begin, end;        // range in the sorted atom order
@@ -244,7 +245,7 @@ __global__ void k_codes(const SrcF* __restrict__ srcf, int n, double rs_grid, Tr
         const double rnear = fmax(sqrt((double)rc2), rs_grid);  // infinite without an LJ cut-off
         int lc = 0;
         if (isfinite(rnear))
-            while (lc < 7 && (double)L / (double)(1 << (lc + 1)) >= 0.5 * rnear) ++lc;
+            while (lc < 7 && (double)L / (double)(1 << (lc + 1)) >= kCellFrac * rnear) ++lc;
         meta->lc = lc;
         meta->cell_side = (double)L / (double)(1 << lc);
         meta->rnear = rnear;
@@ -685,6 +686,7 @@ struct ListArgs {
     const int* dn_ent;
     int dn_cap;
     TBoxes tb;
+    int use_pc;               // accept source proxies (off when the box level does the far field)
 };
 
 // Node index -> (is a node opened for this target?) helpers shared by the traversals.
@@ -737,7 +739,7 @@ __device__ __forceinline__ void batch_geom(const ListArgs& a, int b, double cb[3
 // deterministic.  Batch b owns entries [b cap, (b+1) cap); a longer list sets
 // the overflow flag and records its length for the host to grow cap.
 __global__ void __launch_bounds__(32 * kListWarps) k_far_lists(ListArgs a, const Node* __restrict__ nodes, int2* ent,
-                                                              int* cnt, TreeMeta* meta) {
+                                                              int* cnt, int* work, TreeMeta* meta) {
     __shared__ int qa[kListWarps][kQCap], qb[kListWarps][kQCap];
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     const int nb = a.nbx * a.nby * a.nbz;
@@ -776,7 +778,7 @@ __global__ void __launch_bounds__(32 * kListWarps) k_far_lists(ListArgs a, const
                     const double rs = rb + rn;
                     const bool sep = rs * rs < a.theta * a.theta * R2;
                     const int cntn = nd.end - nd.begin;
-                    if (sep && nd.prox >= 0) {
+                    if (sep && a.use_pc && nd.prox >= 0) {
                         kind = 1;
                         e = make_int2(a.n + nd.prox * a.P3, a.P3);
                         pp += a.P3;
@@ -835,6 +837,7 @@ __global__ void __launch_bounds__(32 * kListWarps) k_far_lists(ListArgs a, const
             pp += __shfl_xor_sync(0xffffffffu, pp, o);
         }
         if (lane == 0) {
+            work[b] = (int)min(dp + pp, (long long)INT_MAX);
             cnt[b] = min(m, a.cap);
             if (m > a.cap) {
                 meta->overflow = 1;
@@ -981,7 +984,7 @@ __global__ void __launch_bounds__(32 * kListWarps) k_tbox_lists(TListArgs a, con
 // grown by rnear (x fastest), keep those whose box lies within rnear of the
 // batch box, and emit their atom ranges in cell order.
 __global__ void __launch_bounds__(32 * kListWarps) k_near_lists(ListArgs a, const int* __restrict__ cell_start,
-                                                               int2* ent, int* cnt, TreeMeta* meta) {
+                                                               int2* ent, int* cnt, int* work, TreeMeta* meta) {
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     const int nb = a.nbx * a.nby * a.nbz;
     const int lc = meta->lc, ncell = 1 << lc;
@@ -1038,6 +1041,7 @@ __global__ void __launch_bounds__(32 * kListWarps) k_near_lists(ListArgs a, cons
         }
         for (int o = 16; o > 0; o >>= 1) cand += __shfl_xor_sync(0xffffffffu, cand, o);
         if (lane == 0) {
+            work[b] = (int)min(cand, (long long)INT_MAX);
             cnt[b] = min(m, a.cap);
             if (m > a.cap) {
                 meta->overflow = 1;
@@ -1046,6 +1050,29 @@ __global__ void __launch_bounds__(32 * kListWarps) k_near_lists(ListArgs a, cons
             atomicAdd(&meta->near_pairs, (unsigned long long)(cand * pts));
         }
     }
+}
+
+// Launch order of the near-field batches, heaviest first: a counting sort of the batches by the binary
+// order of magnitude of their candidate-atom count (one CTA).  The order changes nothing but which CTAs start
+// first (each batch is computed independently), so long batches do not trail at the end of the launch.
+constexpr int kOrderBuckets = 33;
+__global__ void __launch_bounds__(1024) k_order(int nb, const int* __restrict__ work, int* order) {
+    __shared__ int hist[kOrderBuckets], start[kOrderBuckets];
+    const int tid = threadIdx.x;
+    if (tid < kOrderBuckets) hist[tid] = 0;
+    __syncthreads();
+    auto bucket = [](int w) { return w <= 0 ? 0 : 32 - __clz(w); };  // 0 .. 32
+    for (int b = tid; b < nb; b += blockDim.x) atomicAdd(&hist[bucket(work[b])], 1);
+    __syncthreads();
+    if (tid == 0) {
+        int acc = 0;
+        for (int k = kOrderBuckets - 1; k >= 0; --k) {
+            start[k] = acc;
+            acc += hist[k];
+        }
+    }
+    __syncthreads();
+    for (int b = tid; b < nb; b += blockDim.x) order[atomicAdd(&start[bucket(work[b])], 1)] = b;
 }
 
 __global__ void k_reset_meta(TreeMeta* meta) {
@@ -1090,6 +1117,13 @@ struct EvalArgs {
     int far_init;          // the far kernel starts from the box-level (interpolated) field already in `far`
     const float4* ntab;    // [2 kNTab] cubic pieces of erfc(x) and e^{-x^2}[erfcx(x-a) + erfcx(x+a)] in d
     float ntab_inv;        // kNTab / r_short (grid units)
+    int uni_rc;            // every (atom, site) pair has the same LJ cut-off (global cut-off or none)
+    const int* near_order; // CTA -> batch of the per-solute near kernel (heaviest first)
+    const int* far_order;  // the same for the far kernel
+    // epilogue constants per site (grid-unit sums -> physical fields), split into float pairs on the host:
+    // u = cu Phi1 + LJ, c = cc (Phi1 - S_c), h = ch (2 e^{a^2} Phik - S_h)
+    float cu_h[kMaxSites], cu_l[kMaxSites], cc[kMaxSites], ch[kMaxSites];
+    float e2a_h, e2a_l;
     Outputs o;
     DevErr* err;
     TreeMeta* meta;
@@ -1180,46 +1214,64 @@ __device__ void drain(R& r, const Cursor& c, long long wlim) {
         if (c.last_phase[s] >= 0) mbar_wait_bounded(&r.full[s], (uint32_t)(c.last_phase[s] & 1), wlim);
 }
 
-// Consumer loop skeleton shared by the far and near bodies: per landed tile,
-// `stage(slot, cnt)` reads the tile out of the ring (its warp then releases
-// the slot to the producer) and `consume(cnt)` works on what was staged.
-// Returns false after an abort (bounded wait ran out).
+// Ring driver shared by the far, near and proxy-target bodies, warp-specialised: the warp after the NWARPS
+// consumer warps produces (its lane 0 refills each slot as soon as every consumer warp has released it, so
+// it runs up to kStages tiles ahead); each consumer warp, per landed tile, runs `stage(slot, cnt)` (reads the
+// tile out of the ring), releases the slot and runs `consume(cnt)` on what it staged.  Every wait is bounded:
+// a wait that runs out sets the abort flag and the device error word, and the producer waits (bounded) for
+// its copies in flight before it leaves.
+enum : int { kRingAbort = 0, kRingDone = 1, kRingProducer = 2 };
+
 template <int SM, bool LJ, int NWARPS, typename R, typename FS, typename FC>
-__device__ bool run_ring(R& r, Cursor& cur, const int2* ent, const SrcF* src, const LJf* ljs, const EvalArgs& a,
-                         FS&& stage, FC&& consume) {
+__device__ int run_ring(R& r, Cursor& cur, const int2* ent, const SrcF* src, const LJf* ljs, const EvalArgs& a,
+                        FS&& stage, FC&& consume) {
     const int tid = threadIdx.x, lane = tid & 31;
-    if (tid == 0)
-        for (int s = 0; s < kStages; ++s) produce<SM, LJ>(cur, r, s, ent, src, ljs);
+    volatile int* abort_flag = &r.abort;
+    if (tid >= NWARPS * 32) {
+        if (tid == NWARPS * 32) {
+            bool ok = true;
+            for (int t = 0;; ++t) {
+                const int slot = t % kStages;
+                if (t >= kStages && !mbar_wait_bounded(&r.empty[slot], (uint32_t)((t / kStages - 1) & 1), a.wlim)) {
+                    ok = false;
+                    break;
+                }
+                if (*abort_flag) {
+                    ok = false;
+                    break;
+                }
+                produce<SM, LJ>(cur, r, slot, ent, src, ljs);
+                if (cur.done) break;
+            }
+            if (!ok) {
+                *abort_flag = 1;
+                report_error(a.err, DEV_TIMEOUT, WHERE_TREE_EVAL);
+                drain(r, cur, a.wlim);
+            }
+        }
+        return kRingProducer;
+    }
     for (int t = 0;; ++t) {
         const int slot = t % kStages;
         const uint32_t ph = (t / kStages) & 1;
-        if (!mbar_wait_bounded(&r.full[slot], ph, a.wlim) || r.abort) {
-            r.abort = 1;
+        if (!mbar_wait_bounded(&r.full[slot], ph, a.wlim) || *abort_flag) {
+            *abort_flag = 1;
             report_error(a.err, DEV_TIMEOUT, WHERE_TREE_EVAL);
-            if (tid == 0) drain(r, cur, a.wlim);
-            return false;
+            return kRingAbort;
         }
         const int cnt = r.cnt[slot];
-        if (cnt == 0) return true;
+        if (cnt == 0) return kRingDone;
         stage(slot, cnt);
         __syncwarp();
         if (lane == 0) mbar_arrive(&r.empty[slot]);
         consume(cnt);
-        if (tid == 0 && !cur.done) {
-            if (!mbar_wait_bounded(&r.empty[slot], ph, a.wlim)) {
-                r.abort = 1;
-                report_error(a.err, DEV_TIMEOUT, WHERE_TREE_EVAL);
-            } else {
-                produce<SM, LJ>(cur, r, slot, ent, src, ljs);
-            }
-        }
     }
 }
 
 // ---- far field: Phi1 = sum q/d and Phik = sum q e^{-kappa d}/d over the batch's far list
 template <int NXB, int NYB, int NZB, int PF>
 struct FarShape {
-    static constexpr int TX = NXB / PF, NT = TX * NYB * NZB, NW = NT / 32;
+    static constexpr int TX = NXB / PF, NT = TX * NYB * NZB, NW = NT / 32, NTP = NT + 32;  // + producer warp
 };
 
 // One tile re-staged per warp as source pairs: record l holds sources 2l and 2l+1, field by field, so that a
@@ -1310,7 +1362,7 @@ __device__ void far_body(const EvalArgs& a, int b, Ring<1, false>& r, PairRec (*
     float f1h[P], f1l[P], fkh[P], fkl[P];
 #pragma unroll
     for (int p = 0; p < P; ++p) f1h[p] = f1l[p] = fkh[p] = fkl[p] = 0.f;
-    if (a.far_init && j < a.g.ny && k < a.g.nz) {
+    if (a.far_init && tid < Sh::NT && j < a.g.ny && k < a.g.nz) {
         const float4* src0 = a.far + ((int64_t)k * a.g.ny + j) * a.g.nx;
 #pragma unroll
         for (int p = 0; p < P; ++p)
@@ -1324,7 +1376,7 @@ __device__ void far_body(const EvalArgs& a, int b, Ring<1, false>& r, PairRec (*
     }
     Cursor cur;
     __syncthreads();
-    if (tid == 0) {
+    if (tid == Sh::NT) {
         cur.e = b * a.far_cap;
         cur.e_end = cur.e + a.far_cnt[b];
         cur.off = 0;
@@ -1336,7 +1388,7 @@ __device__ void far_body(const EvalArgs& a, int b, Ring<1, false>& r, PairRec (*
     }
     __syncthreads();
     bool on = false;
-    const bool ok = run_ring<1, false, Sh::NW>(
+    const int rr = run_ring<1, false, Sh::NW>(
         r, cur, a.far_ent, a.srcf, nullptr, a,
         [&](int slot, int cnt) {
             __syncwarp();  // the previous tile's records are no longer read
@@ -1361,7 +1413,7 @@ __device__ void far_body(const EvalArgs& a, int b, Ring<1, false>& r, PairRec (*
                 }
             }
         });
-    if (!ok) return;
+    if (rr != kRingDone) return;
     const GridD& g = a.g;
     if (j >= g.ny || k >= g.nz || i0 >= g.nx) return;
     float4* dst = a.far + ((int64_t)k * g.ny + j) * g.nx;
@@ -1445,7 +1497,7 @@ constexpr int kCPChunkMin = 256; // atoms per chunk at least
 // kCPThreads chunks per pass.  Sources stream through the TMA ring.  Chunk 0 writes the box's proxy values,
 // later chunks their partial sums (added in chunk order by k_cp_reduce).
 template <bool DH>
-__global__ void __launch_bounds__(kCPThreads) k_cp_eval(EvalArgs a, CPArgs c) {
+__global__ void __launch_bounds__(kCPThreads + 32) k_cp_eval(EvalArgs a, CPArgs c) {
     __shared__ Ring<1, false> r;
     __shared__ RelRec pairs[kCPThreads / 32][kPairs];
     __shared__ int s_e, s_off, s_len, s_nch;
@@ -1463,7 +1515,7 @@ __global__ void __launch_bounds__(kCPThreads) k_cp_eval(EvalArgs a, CPArgs c) {
     if (cnt == 0) {
         if (chunk == 0 && pass == 0) {
             float2* out = c.tpot + (int64_t)box * P3;
-            for (int k = tid; k < P3; k += kCPThreads) out[k] = make_float2(0.f, 0.f);
+            for (int k = tid; k < P3; k += blockDim.x) out[k] = make_float2(0.f, 0.f);
             if (tid == 0) {
                 c.tflag[box] = 0;
                 c.tnch[box] = 1;
@@ -1496,7 +1548,7 @@ __global__ void __launch_bounds__(kCPThreads) k_cp_eval(EvalArgs a, CPArgs c) {
     float2* out = chunk == 0 ? c.tpot + (int64_t)box * P3
                              : c.tpart + ((int64_t)box * (kCPChunks - 1) + chunk - 1) * P3;
     const int task = pass * kCPThreads + tid;
-    const bool act = task < ntask;
+    const bool act = tid < kCPThreads && task < ntask;
     const int tk = act ? task : 0;
     const int line = tk / nxc, xc = tk % nxc, ky = line % n1, kz = line / n1;
     const float hx = 0.5f * (T.ext[0] - 1), hy = 0.5f * (T.ext[1] - 1), hz = 0.5f * (T.ext[2] - 1);
@@ -1518,7 +1570,7 @@ __global__ void __launch_bounds__(kCPThreads) k_cp_eval(EvalArgs a, CPArgs c) {
     for (int p = 0; p < kCPP; ++p) f1h[p] = f1l[p] = fkh[p] = fkl[p] = 0.f;
     Cursor cur;
     __syncthreads();
-    if (tid == 0) {
+    if (tid == kCPThreads) {
         cur.e = box * c.cp_cap + s_e;
         cur.e_end = box * c.cp_cap + cnt;
         cur.off = s_off;
@@ -1529,7 +1581,7 @@ __global__ void __launch_bounds__(kCPThreads) k_cp_eval(EvalArgs a, CPArgs c) {
         ring_init(r, NW);
     }
     __syncthreads();
-    const bool ok = run_ring<1, false, NW>(
+    const int rr = run_ring<1, false, NW>(
         r, cur, c.cp_ent, a.srcf, nullptr, a,
         [&](int slot, int n) {
             __syncwarp();
@@ -1551,7 +1603,7 @@ __global__ void __launch_bounds__(kCPThreads) k_cp_eval(EvalArgs a, CPArgs c) {
                 }
             }
         });
-    if (!ok || !act) return;
+    if (rr != kRingDone || !act) return;
 #pragma unroll
     for (int p = 0; p < kCPP; ++p) {
         const int kx = xc * kCPP + p;
@@ -1580,42 +1632,48 @@ __global__ void __launch_bounds__(256) k_cp_reduce(CPArgs c, const TreeMeta* met
     }
 }
 
-// Separable tensor-product interpolation in shared memory: V holds (n+1)^3 values on the source box's
-// Chebyshev points (x fastest); W[d] the 1D Lagrange weights [m_d][n+1] of the m_d target coordinates of
-// axis d.  Produces O[m2][m1][m0] (x fastest).  S1 and S2 are scratch of (n+1)^2 m0 and (n+1) m1 m0 values.
-__device__ void interp3(int n1, const float2* V, const float* W0, const float* W1, const float* W2, int m0, int m1,
-                        int m2, float2* S1, float2* S2, float2* O) {
+// Separable tensor-product interpolation in shared memory: V holds N1^3 values on the source box's
+// Chebyshev points (x fastest); W0/W1/W2 the 1D Lagrange weights [M][N1] of the target coordinates of each
+// axis.  Produces O[M][M][M] (x fastest); S1 and S2 are scratch of N1^2 M and N1 M^2 values.  Compile-time
+// sizes keep the index arithmetic to multiplies and shifts; rows beyond a clipped box's extent are computed
+// from zero weights and never stored.
+template <int N1, int M>
+__device__ void interp3(const float2* V, const float* W0, const float* W1, const float* W2, float2* S1, float2* S2,
+                        float2* O) {
     const int tid = threadIdx.x, nt = blockDim.x;
-    for (int t = tid; t < n1 * n1 * m0; t += nt) {
-        const int ix = t % m0, line = t / m0;  // line = kz (n+1) + ky
+    for (int t = tid; t < N1 * N1 * M; t += nt) {
+        const int ix = t % M, line = t / M;  // line = kz N1 + ky
         float ax = 0.f, ay = 0.f;
-        for (int k = 0; k < n1; ++k) {
-            const float wv = W0[ix * n1 + k];
-            const float2 v = V[line * n1 + k];
+#pragma unroll
+        for (int k = 0; k < N1; ++k) {
+            const float wv = W0[ix * N1 + k];
+            const float2 v = V[line * N1 + k];
             ax = fmaf(wv, v.x, ax);
             ay = fmaf(wv, v.y, ay);
         }
-        S1[line * m0 + ix] = make_float2(ax, ay);
+        S1[t] = make_float2(ax, ay);
     }
     __syncthreads();
-    for (int t = tid; t < n1 * m1 * m0; t += nt) {
-        const int ix = t % m0, iy = (t / m0) % m1, kz = t / (m0 * m1);
+    for (int t = tid; t < N1 * M * M; t += nt) {
+        const int ix = t % M, iy = (t / M) % M, kz = t / (M * M);
         float ax = 0.f, ay = 0.f;
-        for (int k = 0; k < n1; ++k) {
-            const float wv = W1[iy * n1 + k];
-            const float2 v = S1[(kz * n1 + k) * m0 + ix];
+#pragma unroll
+        for (int k = 0; k < N1; ++k) {
+            const float wv = W1[iy * N1 + k];
+            const float2 v = S1[(kz * N1 + k) * M + ix];
             ax = fmaf(wv, v.x, ax);
             ay = fmaf(wv, v.y, ay);
         }
-        S2[(kz * m1 + iy) * m0 + ix] = make_float2(ax, ay);
+        S2[t] = make_float2(ax, ay);
     }
     __syncthreads();
-    for (int t = tid; t < m2 * m1 * m0; t += nt) {
-        const int ix = t % m0, iy = (t / m0) % m1, iz = t / (m0 * m1);
+    for (int t = tid; t < M * M * M; t += nt) {
+        const int ix = t % M, iy = (t / M) % M, iz = t / (M * M);
         float ax = 0.f, ay = 0.f;
-        for (int k = 0; k < n1; ++k) {
-            const float wv = W2[iz * n1 + k];
-            const float2 v = S2[(k * m1 + iy) * m0 + ix];
+#pragma unroll
+        for (int k = 0; k < N1; ++k) {
+            const float wv = W2[iz * N1 + k];
+            const float2 v = S2[(k * M + iy) * M + ix];
             ax = fmaf(wv, v.x, ax);
             ay = fmaf(wv, v.y, ay);
         }
@@ -1626,14 +1684,14 @@ __device__ void interp3(int n1, const float2* V, const float* W0, const float* W
 
 // Weight rows for axis d: row i is the Lagrange basis of box B's Chebyshev points along d evaluated at the
 // offset t(i) from B's centre (grid units).
-template <typename X>
-__device__ void basis_rows(const TBoxes& tb, const TBox& B, int d, int m, X t, float* W) {
-    const int deg = tb.deg;
+template <int N1, typename X>
+__device__ void basis_rows(const TBoxes& tb, const TBox& B, int d, int m, int mpad, X t, float* W) {
     const float hw = 0.5f * (B.ext[d] - 1);
-    for (int i = threadIdx.x; i < m; i += blockDim.x) {
-        float L[kMaxDegree + 1];
-        cheb_basis(deg, tb.ck, hw, t(i), L);
-        for (int k = 0; k <= deg; ++k) W[i * (deg + 1) + k] = L[k];
+    for (int i = threadIdx.x; i < mpad; i += blockDim.x) {
+        float L[N1];
+        if (i < m) cheb_basis(N1 - 1, tb.ck, hw, t(i), L);
+#pragma unroll
+        for (int k = 0; k < N1; ++k) W[i * N1 + k] = i < m ? L[k] : 0.f;
     }
 }
 
@@ -1644,8 +1702,10 @@ __host__ __device__ constexpr size_t interp_smem(int n1, int m) {
 }
 
 // Downward pass, level l + 1 -> l: a box with proxies adds its parent's field interpolated at its own proxies.
+template <int N1>
 __global__ void __launch_bounds__(256) k_l2l(CPArgs c, int l, const TreeMeta* meta) {
     extern __shared__ __align__(16) unsigned char sm_raw[];
+    constexpr int P3 = N1 * N1 * N1;
     if (meta->overflow) return;
     const TBoxes& tb = c.tb;
     const int bi = blockIdx.x;
@@ -1655,21 +1715,20 @@ __global__ void __launch_bounds__(256) k_l2l(CPArgs c, int l, const TreeMeta* me
     const TBox Pb = tbox_at(tb, l + 1, ib >> 1, jb >> 1, kb >> 1);
     const int box = tb.off[l] + bi, pbox = tbox_index(tb, l + 1, ib >> 1, jb >> 1, kb >> 1);
     if (!Pb.proxied || !c.tflag[pbox]) return;
-    const int deg = tb.deg, n1 = deg + 1, P3 = tb.P3;
     float2* V = reinterpret_cast<float2*>(sm_raw);
     float2* S1 = V + P3;
-    float2* S2 = S1 + n1 * n1 * n1;
-    float2* O = S2 + n1 * n1 * n1;
+    float2* S2 = S1 + P3;
+    float2* O = S2 + P3;
     float* W = reinterpret_cast<float*>(O + P3);
     const float2* src = c.tpot + (int64_t)pbox * P3;
     for (int k = threadIdx.x; k < P3; k += blockDim.x) V[k] = src[k];
     for (int d = 0; d < 3; ++d) {
         // child node i relative to the parent's centre: (c_child - c_parent) (exact: half-integers) + hw ck[i]
         const float off = (float)(T.c[d] - Pb.c[d]), hd = 0.5f * (T.ext[d] - 1);
-        basis_rows(tb, Pb, d, n1, [&](int i) { return off + hd * tb.ck[i]; }, W + d * n1 * n1);
+        basis_rows<N1>(tb, Pb, d, N1, N1, [&](int i) { return off + hd * tb.ck[i]; }, W + d * N1 * N1);
     }
     __syncthreads();
-    interp3(n1, V, W, W + n1 * n1, W + 2 * n1 * n1, n1, n1, n1, S1, S2, O);
+    interp3<N1, N1>(V, W, W + N1 * N1, W + 2 * N1 * N1, S1, S2, O);
     float2* dst = c.tpot + (int64_t)box * P3;
     for (int k = threadIdx.x; k < P3; k += blockDim.x) {
         const float2 v = dst[k];
@@ -1681,8 +1740,10 @@ __global__ void __launch_bounds__(256) k_l2l(CPArgs c, int l, const TreeMeta* me
 // Box field onto the grid: one CTA per level-0 box region; the lowest box with proxies that contains it
 // (its field includes every ancestor's) is interpolated at the region's points and written to the far-field
 // buffer as the starting value of the far kernel (zero where no box holds a field).
+template <int N1>
 __global__ void __launch_bounds__(256) k_tdown(CPArgs c, float4* far, const TreeMeta* meta) {
     extern __shared__ __align__(16) unsigned char sm_raw[];
+    constexpr int P3 = N1 * N1 * N1, M = kTB0;
     if (meta->overflow) return;
     const TBoxes& tb = c.tb;
     const int bi = blockIdx.x;
@@ -1701,40 +1762,143 @@ __global__ void __launch_bounds__(256) k_tdown(CPArgs c, float4* far, const Tree
     const int64_t plane = (int64_t)tb.ny * tb.nx;
     const bool field = la >= 0 && c.tflag[tbox_index(tb, la, A.ib, A.jb, A.kb)];
     if (!field) {
-        for (int t = threadIdx.x; t < m0 * m1 * m2; t += blockDim.x) {
-            const int ix = t % m0, iy = (t / m0) % m1, iz = t / (m0 * m1);
-            far[(R.lo[2] + iz) * plane + (int64_t)(R.lo[1] + iy) * tb.nx + R.lo[0] + ix] =
-                make_float4(0.f, 0.f, 0.f, 0.f);
+        for (int t = threadIdx.x; t < M * M * M; t += blockDim.x) {
+            const int ix = t % M, iy = (t / M) % M, iz = t / (M * M);
+            if (ix < m0 && iy < m1 && iz < m2)
+                far[(R.lo[2] + iz) * plane + (int64_t)(R.lo[1] + iy) * tb.nx + R.lo[0] + ix] =
+                    make_float4(0.f, 0.f, 0.f, 0.f);
         }
         return;
     }
-    const int deg = tb.deg, n1 = deg + 1, P3 = tb.P3;
     float2* V = reinterpret_cast<float2*>(sm_raw);
     float2* S1 = V + P3;
-    float2* S2 = S1 + n1 * n1 * kTB0;
-    float2* O = S2 + n1 * kTB0 * kTB0;
-    float* W = reinterpret_cast<float*>(O + kTB0 * kTB0 * kTB0);
+    float2* S2 = S1 + N1 * N1 * M;
+    float2* O = S2 + N1 * M * M;
+    float* W = reinterpret_cast<float*>(O + M * M * M);
     const float2* src = c.tpot + (int64_t)tbox_index(tb, la, A.ib, A.jb, A.kb) * P3;
     for (int k = threadIdx.x; k < P3; k += blockDim.x) V[k] = src[k];
     const int ms[3] = {m0, m1, m2};
     for (int d = 0; d < 3; ++d) {
         const float off = (float)(R.lo[d] - A.c[d]);  // grid point i of the region relative to A's centre (exact)
-        basis_rows(tb, A, d, ms[d], [&](int i) { return off + (float)i; }, W + d * kTB0 * n1);
+        basis_rows<N1>(tb, A, d, ms[d], M, [&](int i) { return off + (float)i; }, W + d * M * N1);
     }
     __syncthreads();
-    interp3(n1, V, W, W + kTB0 * n1, W + 2 * kTB0 * n1, m0, m1, m2, S1, S2, O);
-    for (int t = threadIdx.x; t < m0 * m1 * m2; t += blockDim.x) {
-        const int ix = t % m0, iy = (t / m0) % m1, iz = t / (m0 * m1);
-        far[(R.lo[2] + iz) * plane + (int64_t)(R.lo[1] + iy) * tb.nx + R.lo[0] + ix] =
-            make_float4(O[t].x, 0.f, O[t].y, 0.f);
+    interp3<N1, M>(V, W, W + M * N1, W + 2 * M * N1, S1, S2, O);
+    for (int t = threadIdx.x; t < M * M * M; t += blockDim.x) {
+        const int ix = t % M, iy = (t / M) % M, iz = t / (M * M);
+        if (ix < m0 && iy < m1 && iz < m2)
+            far[(R.lo[2] + iz) * plane + (int64_t)(R.lo[1] + iy) * tb.nx + R.lo[0] + ix] =
+                make_float4(O[t].x, 0.f, O[t].y, 0.f);
+    }
+}
+
+template <int N1>
+void launch_down(const TBoxes& tb, const CPArgs& c, float4* far, const TreeMeta* meta, cudaStream_t st) {
+    const size_t sl = interp_smem(N1, N1), sd = interp_smem(N1, kTB0);
+    cudaFuncSetAttribute(k_l2l<N1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sl);
+    cudaFuncSetAttribute(k_tdown<N1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sd);
+    for (int l = tb.L - 2; l >= 0; --l) k_l2l<N1><<<tb.nbx[l] * tb.nby[l] * tb.nbz[l], 256, sl, st>>>(c, l, meta);
+    k_tdown<N1><<<tb.nbx[0] * tb.nby[0] * tb.nbz[0], 256, sd, st>>>(c, far, meta);
+}
+
+void launch_down_deg(const TBoxes& tb, const CPArgs& c, float4* far, const TreeMeta* meta, cudaStream_t st) {
+    switch (tb.deg) {
+        case 1: return launch_down<2>(tb, c, far, meta, st);
+        case 2: return launch_down<3>(tb, c, far, meta, st);
+        case 3: return launch_down<4>(tb, c, far, meta, st);
+        case 4: return launch_down<5>(tb, c, far, meta, st);
+        case 5: return launch_down<6>(tb, c, far, meta, st);
+        case 6: return launch_down<7>(tb, c, far, meta, st);
+        case 7: return launch_down<8>(tb, c, far, meta, st);
+        case 8: return launch_down<9>(tb, c, far, meta, st);
+        case 9: return launch_down<10>(tb, c, far, meta, st);
+        case 10: return launch_down<11>(tb, c, far, meta, st);
+        case 11: return launch_down<12>(tb, c, far, meta, st);
+        default: return launch_down<13>(tb, c, far, meta, st);
     }
 }
 
 // ---- near field (LJ within cut-offs, erfc remainders within r_short) + epilogue
 template <int NXB, int NYB, int NZB>
 struct NearShape {
-    static constexpr int P = 4, TX = NXB / P, NT = TX * NYB * NZB, NW = NT / 32;
+    static constexpr int P = 4, TX = NXB / P, NT = TX * NYB * NZB, NW = NT / 32, NTP = NT + 32;  // + producer
 };
+
+// One tile of near-field sources against the P points of a thread: LJ within the pair cut-offs (UNI: one
+// cut-off for every pair, tested once per pair instead of once per site) and the short-range remainders of
+// eq. (dcf-r) / eq. (tcf-r) within r_short from the cubic pieces in d.
+// wlo/whi: bounding box of the warp's points; a source farther than the near radius from it (plus slack for
+// the rounded source position) is skipped by the whole warp at once.
+template <int P, int SM, bool DU, bool DH, bool UNI>
+__device__ __forceinline__ void near_tile(const SrcF* __restrict__ Sx, const LJf* __restrict__ L, int cnt,
+                                          const float (&gx)[P], float fy, float fz, float rn2, float rs2, float rcu2,
+                                          float tinv, const float4* tab, bool DC, float c0h, float h0h,
+                                          const float (&wlo)[3], const float (&whi)[3], float rcull2,
+                                          float (&psc)[P], float (&psh)[P], float (&plj)[P][SM], unsigned& hit) {
+    for (int s0 = 0; s0 < cnt; ++s0) {
+        const float4 g0 = *reinterpret_cast<const float4*>(&Sx[s0].xh);
+        const float4 g1 = *reinterpret_cast<const float4*>(&Sx[s0].xl);
+        {
+            const float qx = fmaxf(0.f, fmaxf(wlo[0] - g0.x, g0.x - whi[0]));
+            const float qy = fmaxf(0.f, fmaxf(wlo[1] - g0.y, g0.y - whi[1]));
+            const float qz = fmaxf(0.f, fmaxf(wlo[2] - g0.z, g0.z - whi[2]));
+            if (fmaf(qx, qx, fmaf(qy, qy, qz * qz)) >= rcull2) continue;  // same outcome in every lane
+        }
+        const float dy = (fy - g0.y) - g1.y;
+        const float dz = (fz - g0.z) - g1.z;
+        const float dyz2 = fmaf(dy, dy, dz * dz);
+        const LJf* Ls = L + s0 * SM;
+#pragma unroll
+        for (int p = 0; p < P; ++p) {
+            const float dx = (gx[p] - g0.x) - g1.x;
+            const float d2 = fmaf(dx, dx, dyz2);
+            if (d2 >= rn2) continue;
+            if (d2 < rs2) {
+                if (d2 > 0.f) {
+                    // erfc(x)/d and e^{-x^2}[erfcx(x-a) + erfcx(x+a)]/d from the cubic pieces in d
+                    const float ri = rsqrt_approx(d2);
+                    const float qr = g0.w * ri;
+                    const float uu = d2 * ri * tinv;
+                    const int it = min((int)uu, kNTab - 1);
+                    const float tt = uu - (float)it;
+                    if (DC) {
+                        const float4 cc = tab[2 * it];
+                        psc[p] = fmaf(qr, fmaf(fmaf(fmaf(cc.w, tt, cc.z), tt, cc.y), tt, cc.x), psc[p]);
+                    }
+                    if (DH) {
+                        const float4 ch = tab[2 * it + 1];
+                        psh[p] = fmaf(qr, fmaf(fmaf(fmaf(ch.w, tt, ch.z), tt, ch.y), tt, ch.x), psh[p]);
+                    }
+                } else {
+                    hit |= 1u << p;
+                    if (DC) psc[p] -= g0.w * c0h;
+                    if (DH) psh[p] -= g0.w * h0h;
+                }
+            }
+            if (DU) {
+                if (UNI) {
+                    if (d2 < rcu2) {
+                        const float r2i = rcp_approx(d2);
+                        const float r6 = r2i * r2i * r2i;
+#pragma unroll
+                        for (int s = 0; s < SM; ++s) {
+                            const float2 ab = *reinterpret_cast<const float2*>(&Ls[s]);
+                            plj[p][s] = fmaf(r6, fmaf(ab.x, r6, -ab.y), plj[p][s]);
+                        }
+                    }
+                } else {
+                    const float r2i = rcp_approx(d2);
+                    const float r6 = r2i * r2i * r2i;
+#pragma unroll
+                    for (int s = 0; s < SM; ++s) {
+                        const float4 l = *reinterpret_cast<const float4*>(&Ls[s]);
+                        if (d2 < l.z) plj[p][s] = fmaf(r6, fmaf(l.x, r6, -l.y), plj[p][s]);
+                    }
+                }
+            }
+        }
+    }
+}
 
 template <int NXB, int NYB, int NZB, int SM, bool DU, bool DH>
 __device__ void near_body(const EvalArgs& a, int b, Ring<SM, true>& r, float4* tab) {
@@ -1753,6 +1917,20 @@ __device__ void near_body(const EvalArgs& a, int b, Ring<SM, true>& r, float4* t
     const bool DC = a.o.c != nullptr;
     const double rnear = a.meta->rnear;
     const float rn2 = isfinite(rnear) ? (float)(rnear * rnear) : INFINITY;
+    const float rcu2 = __int_as_float(a.meta->rc2max);  // the cut-off of every pair when a.uni_rc
+    // the warp's point box (grid units) and the culling radius: near radius + 0.01 grid units of slack for the
+    // source position rounded to its high part
+    float wlo[3], whi[3];
+    {
+        const int lo3[3] = {i0, j, k}, hi3[3] = {i0 + P - 1, j, k};
+#pragma unroll
+        for (int d = 0; d < 3; ++d) {
+            wlo[d] = (float)__reduce_min_sync(0xffffffffu, lo3[d]);
+            whi[d] = (float)__reduce_max_sync(0xffffffffu, hi3[d]);
+        }
+    }
+    const float rcull = isfinite(rnear) ? (float)rnear + 0.01f : INFINITY;
+    const float rcull2 = rcull * rcull;
 
     float sch[P], scl[P], shh[P], shl[P], ljh[P][SM], ljl[P][SM];
 #pragma unroll
@@ -1765,8 +1943,8 @@ __device__ void near_body(const EvalArgs& a, int b, Ring<SM, true>& r, float4* t
     const float tinv = a.ntab_inv;
     Cursor cur;
     __syncthreads();
-    for (int k = tid; k < 2 * kNTab; k += Sh::NT) tab[k] = a.ntab[k];
-    if (tid == 0) {
+    for (int k = tid; k < 2 * kNTab; k += blockDim.x) tab[k] = a.ntab[k];
+    if (tid == Sh::NT) {
         cur.e = b * a.near_cap;
         cur.e_end = cur.e + a.near_cnt[b];
         cur.off = 0;
@@ -1777,7 +1955,7 @@ __device__ void near_body(const EvalArgs& a, int b, Ring<SM, true>& r, float4* t
         ring_init(r, Sh::NW);
     }
     __syncthreads();
-    const bool ok = run_ring<SM, true, Sh::NW>(r, cur, a.near_ent, a.srcf, a.ljs, a, [&](int slot, int cnt) {
+    const int rr = run_ring<SM, true, Sh::NW>(r, cur, a.near_ent, a.srcf, a.ljs, a, [&](int slot, int cnt) {
         const SrcF* Sx = r.src[slot];
         const LJf* L = r.lj[slot];
         float psc[P], psh[P], plj[P][SM];
@@ -1787,50 +1965,12 @@ __device__ void near_body(const EvalArgs& a, int b, Ring<SM, true>& r, float4* t
 #pragma unroll
             for (int s = 0; s < SM; ++s) plj[p][s] = 0.f;
         }
-        for (int s0 = 0; s0 < cnt; ++s0) {
-            const float4 g0 = *reinterpret_cast<const float4*>(&Sx[s0].xh);
-            const float4 g1 = *reinterpret_cast<const float4*>(&Sx[s0].xl);
-            const float dy = (fy - g0.y) - g1.y;
-            const float dz = (fz - g0.z) - g1.z;
-            const float dyz2 = fmaf(dy, dy, dz * dz);
-#pragma unroll
-            for (int p = 0; p < P; ++p) {
-                const float dx = (gx[p] - g0.x) - g1.x;
-                const float d2 = fmaf(dx, dx, dyz2);
-                if (d2 >= rn2) continue;
-                if (d2 < rs2) {
-                    if (d2 > 0.f) {
-                        // erfc(x)/d and e^{-x^2}[erfcx(x-a) + erfcx(x+a)]/d from the cubic pieces in d
-                        const float ri = rsqrt_approx(d2);
-                        const float qr = g0.w * ri;
-                        const float uu = d2 * ri * tinv;
-                        const int it = min((int)uu, kNTab - 1);
-                        const float tt = uu - (float)it;
-                        if (DC) {
-                            const float4 cc = tab[2 * it];
-                            psc[p] = fmaf(qr, fmaf(fmaf(fmaf(cc.w, tt, cc.z), tt, cc.y), tt, cc.x), psc[p]);
-                        }
-                        if (DH) {
-                            const float4 ch = tab[2 * it + 1];
-                            psh[p] = fmaf(qr, fmaf(fmaf(fmaf(ch.w, tt, ch.z), tt, ch.y), tt, ch.x), psh[p]);
-                        }
-                    } else {
-                        hit |= 1u << p;
-                        if (DC) psc[p] -= g0.w * c0h;
-                        if (DH) psh[p] -= g0.w * h0h;
-                    }
-                }
-                if (DU) {
-                    const float r2i = rcp_approx(d2);
-                    const float r6 = r2i * r2i * r2i;
-#pragma unroll
-                    for (int s = 0; s < SM; ++s) {
-                        const float4 l = *reinterpret_cast<const float4*>(&L[s0 * SM + s]);
-                        if (d2 < l.z) plj[p][s] = fmaf(r6, fmaf(l.x, r6, -l.y), plj[p][s]);
-                    }
-                }
-            }
-        }
+        if (a.uni_rc)
+            near_tile<P, SM, DU, DH, true>(Sx, L, cnt, gx, fy, fz, rn2, rs2, rcu2, tinv, tab, DC, c0h, h0h, wlo, whi,
+                                           rcull2, psc, psh, plj, hit);
+        else
+            near_tile<P, SM, DU, DH, false>(Sx, L, cnt, gx, fy, fz, rn2, rs2, rcu2, tinv, tab, DC, c0h, h0h, wlo,
+                                            whi, rcull2, psc, psh, plj, hit);
 #pragma unroll
         for (int p = 0; p < P; ++p) {
             if (DC) ff_add(sch[p], scl[p], psc[p]);
@@ -1841,56 +1981,65 @@ __device__ void near_body(const EvalArgs& a, int b, Ring<SM, true>& r, float4* t
             }
         }
     }, [](int) {});
-    if (!ok) return;
+    if (rr != kRingDone) return;
 
     const GridD& g = a.g;
     if (j >= g.ny || k >= g.nz || i0 >= g.nx) return;
     const int64_t plane = (int64_t)g.nx * g.ny * g.nz;
     const int64_t row = ((int64_t)k * g.ny + j) * g.nx;
     const bool vec_ok = (g.nx & 1) == 0;
-    const double ih = 1.0 / g.h;
-    const Phys& ph = a.ph;
-    const double cu0 = ph.k_e * ih, cc0 = -ph.beta * ph.k_e * ih, ch0 = -ph.beta * ph.k_e / (2.0 * ph.eps_r) * ih;
-    double F1[P], FK[P], SC[P], SH[P];
+    // Assembly in float pairs (error-free sums and products), one rounding to float per output, then the
+    // float -> double conversion on the integer pipe: no FP64 arithmetic per grid point.
+    float F1h[P], F1l[P], DC_[P], DH_[P];
     const float4* fr = a.far + row;
 #pragma unroll
     for (int p = 0; p < P; ++p) {
         const float4 f = (i0 + p < g.nx) ? fr[i0 + p] : make_float4(0.f, 0.f, 0.f, 0.f);
-        F1[p] = (double)f.x + (double)f.y;
-        FK[p] = (double)f.z + (double)f.w;
-        SC[p] = (double)sch[p] + (double)scl[p];
-        SH[p] = (double)shh[p] + (double)shl[p];
+        F1h[p] = f.x;
+        F1l[p] = f.y;
+        float s, e;
+        two_sum(f.x, -sch[p], s, e);  // Phi1 - S_c
+        DC_[p] = s + (e + (f.y - scl[p]));
+        const float ph_ = a.e2a_h * f.z;  // 2 e^{a^2} Phik - S_h
+        const float pe = fmaf(a.e2a_h, f.z, -ph_) + (a.e2a_h * f.w + a.e2a_l * f.z);
+        two_sum(ph_, -shh[p], s, e);
+        DH_[p] = s + (e + (pe - shl[p]));
     }
-    auto store = [&](double* base, const double (&v)[P]) {
+    auto store = [&](double* base, const float (&v)[P]) {
         if (vec_ok && i0 + P <= g.nx) {
 #pragma unroll
             for (int p = 0; p < P; p += 2)
-                __stcs(reinterpret_cast<double2*>(base + i0 + p), make_double2(v[p], v[p + 1]));
+                __stcs(reinterpret_cast<double2*>(base + i0 + p), make_double2(f2d_alu(v[p]), f2d_alu(v[p + 1])));
         } else {
 #pragma unroll
             for (int p = 0; p < P; ++p)
-                if (i0 + p < g.nx) __stcs(base + i0 + p, v[p]);
+                if (i0 + p < g.nx) __stcs(base + i0 + p, f2d_alu(v[p]));
         }
     };
 #pragma unroll
     for (int s = 0; s < SM; ++s) {
-        if (s >= ph.S) break;
-        const double qs = ph.qs[s];
-        double v[P];
+        if (s >= a.ph.S) break;
+        float v[P];
         if (DU) {
+            const float cuh = a.cu_h[s], cul = a.cu_l[s];
 #pragma unroll
-            for (int p = 0; p < P; ++p)
-                v[p] = (hit >> p & 1u) ? INFINITY : cu0 * qs * F1[p] + ((double)ljh[p][s] + (double)ljl[p][s]);
+            for (int p = 0; p < P; ++p) {
+                const float pc = cuh * F1h[p];
+                const float pce = fmaf(cuh, F1h[p], -pc) + (cuh * F1l[p] + cul * F1h[p]);
+                float t, e;
+                two_sum(pc, ljh[p][s], t, e);
+                v[p] = (hit >> p & 1u) ? INFINITY : t + (e + (pce + ljl[p][s]));
+            }
             store(a.o.u + s * plane + row, v);
         }
         if (DC) {
 #pragma unroll
-            for (int p = 0; p < P; ++p) v[p] = cc0 * qs * (F1[p] - SC[p]);
+            for (int p = 0; p < P; ++p) v[p] = a.cc[s] * DC_[p];
             store(a.o.c + s * plane + row, v);
         }
         if (DH) {
 #pragma unroll
-            for (int p = 0; p < P; ++p) v[p] = ch0 * qs * (2.0 * ph.ea2 * FK[p] - SH[p]);
+            for (int p = 0; p < P; ++p) v[p] = a.ch[s] * DH_[p];
             store(a.o.h + s * plane + row, v);
         }
     }
@@ -1898,21 +2047,28 @@ __device__ void near_body(const EvalArgs& a, int b, Ring<SM, true>& r, float4* t
 
 // ---- per-solute kernels: one CTA per target batch
 template <int NXB, int NYB, int NZB, int PF, bool DH>
-__global__ void __launch_bounds__(FarShape<NXB, NYB, NZB, PF>::NT) k_far32(EvalArgs a) {
+__global__ void __launch_bounds__(FarShape<NXB, NYB, NZB, PF>::NTP) k_far32(EvalArgs a) {
     __shared__ Ring<1, false> r;
     __shared__ PairRec pairs[FarShape<NXB, NYB, NZB, PF>::NW][kPairs];
     if (threadIdx.x == 0) r.inited = 0;
     if (a.meta->overflow) return;  // incomplete lists: the host grows them and runs again
-    far_body<NXB, NYB, NZB, PF, DH>(a, blockIdx.x, r, pairs);
+    far_body<NXB, NYB, NZB, PF, DH>(a, a.far_order[blockIdx.x], r, pairs);
 }
 
+// Register cap: 3 resident CTAs (consumer warps + producer warp) for up to 4 sites.
+template <int NXB, int NYB, int NZB, int SM>
+struct NearOcc {
+    static constexpr int v = SM <= 4 ? 384 / NearShape<NXB, NYB, NZB>::NT : 1;
+};
+
 template <int NXB, int NYB, int NZB, int SM, bool DU, bool DH>
-__global__ void __launch_bounds__(NearShape<NXB, NYB, NZB>::NT) k_near32(EvalArgs a) {
+__global__ void __launch_bounds__(NearShape<NXB, NYB, NZB>::NTP, (NearOcc<NXB, NYB, NZB, SM>::v))
+    k_near32(EvalArgs a) {
     __shared__ Ring<SM, true> r;
     __shared__ float4 tab[2 * kNTab];
     if (threadIdx.x == 0) r.inited = 0;
     if (a.meta->overflow) return;
-    near_body<NXB, NYB, NZB, SM, DU, DH>(a, blockIdx.x, r, tab);
+    near_body<NXB, NYB, NZB, SM, DU, DH>(a, a.near_order[blockIdx.x], r, tab);
 }
 
 // ---- persistent kernels over the (solute, batch) items of many solutes
@@ -1933,7 +2089,7 @@ __device__ __forceinline__ int find_solute(const BatchEval& be, int it) {
 }
 
 template <int NXB, int NYB, int NZB, int PF, bool DH>
-__global__ void __launch_bounds__(FarShape<NXB, NYB, NZB, PF>::NT) k_far32_batched(BatchEval be) {
+__global__ void __launch_bounds__(FarShape<NXB, NYB, NZB, PF>::NTP) k_far32_batched(BatchEval be) {
     __shared__ Ring<1, false> r;
     __shared__ PairRec pairs[FarShape<NXB, NYB, NZB, PF>::NW][kPairs];
     __shared__ int s_item;
@@ -1955,7 +2111,8 @@ __global__ void __launch_bounds__(FarShape<NXB, NYB, NZB, PF>::NT) k_far32_batch
 }
 
 template <int NXB, int NYB, int NZB, int SM, bool DU, bool DH>
-__global__ void __launch_bounds__(NearShape<NXB, NYB, NZB>::NT) k_near32_batched(BatchEval be) {
+__global__ void __launch_bounds__(NearShape<NXB, NYB, NZB>::NTP, (NearOcc<NXB, NYB, NZB, SM>::v))
+    k_near32_batched(BatchEval be) {
     __shared__ Ring<SM, true> r;
     __shared__ float4 tab[2 * kNTab];
     __shared__ int s_item;
@@ -1981,7 +2138,7 @@ template <int V>
 struct VShape {
     static constexpr ShapeDesc d = shape_of(V);
     static constexpr int NX = d.nx, NY = d.ny, NZ = d.nz, PF = d.pf;
-    static constexpr int FT = FarShape<NX, NY, NZ, PF>::NT, NTN = NearShape<NX, NY, NZ>::NT;
+    static constexpr int FT = FarShape<NX, NY, NZ, PF>::NTP, NTN = NearShape<NX, NY, NZ>::NTP;
 };
 
 template <int V, int SM, bool DU, bool DH>
@@ -2074,7 +2231,8 @@ struct TreeState {
     LJf* ljs = nullptr;
     float4* far = nullptr; // far-field sums per grid point
     int64_t cap_far_pts = 0;
-    int *far_cnt = nullptr, *near_cnt = nullptr, *prox_items = nullptr;
+    int *far_cnt = nullptr, *near_cnt = nullptr, *prox_items = nullptr, *near_work = nullptr, *near_order = nullptr;
+    int *far_work = nullptr, *far_order = nullptr;
     int2 *far_ent = nullptr, *near_ent = nullptr;
     int* cell_start = nullptr;
     TreeMeta* meta = nullptr;
@@ -2172,7 +2330,9 @@ rism_status tree_reserve(TreeState* s, const DevTables& t, const GridD& g, const
         s->cap_far_pts = M;
     }
     if (s->nb + 1 > s->cap_nb) {
-        if ((e = regrow(s->far_cnt, (size_t)s->nb + 1)) || (e = regrow(s->near_cnt, (size_t)s->nb + 1)))
+        if ((e = regrow(s->far_cnt, (size_t)s->nb + 1)) || (e = regrow(s->near_cnt, (size_t)s->nb + 1)) ||
+            (e = regrow(s->near_work, (size_t)s->nb + 1)) || (e = regrow(s->near_order, (size_t)s->nb + 1)) ||
+            (e = regrow(s->far_work, (size_t)s->nb + 1)) || (e = regrow(s->far_order, (size_t)s->nb + 1)))
             return cuda_err(err, e, "list counts");
         s->cap_nb = s->nb + 1;
     }
@@ -2314,19 +2474,11 @@ int cp_enqueue(TreeState* s, const EvalArgs& a, bool dh, cudaStream_t st) {
     const int n1 = tb.deg + 1;
     const int npass = (n1 * n1 * ((n1 + kCPP - 1) / kCPP) + kCPThreads - 1) / kCPThreads;
     const dim3 grid(tb.nbox, kCPChunks, npass);
-    if (dh) k_cp_eval<true><<<grid, kCPThreads, 0, st>>>(a, c);
-    else k_cp_eval<false><<<grid, kCPThreads, 0, st>>>(a, c);
+    if (dh) k_cp_eval<true><<<grid, kCPThreads + 32, 0, st>>>(a, c);
+    else k_cp_eval<false><<<grid, kCPThreads + 32, 0, st>>>(a, c);
     k_cp_reduce<<<tb.nbox, 256, 0, st>>>(c, s->meta);
-    int launches = 2;
-    const size_t sl = interp_smem(n1, n1), sd = interp_smem(n1, kTB0);
-    cudaFuncSetAttribute(k_l2l, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sl);
-    cudaFuncSetAttribute(k_tdown, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sd);
-    for (int l = tb.L - 2; l >= 0; --l) {
-        k_l2l<<<tb.nbx[l] * tb.nby[l] * tb.nbz[l], 256, sl, st>>>(c, l, s->meta);
-        ++launches;
-    }
-    k_tdown<<<tb.nbx[0] * tb.nby[0] * tb.nbz[0], 256, sd, st>>>(c, s->far, s->meta);
-    return launches + 1;
+    launch_down_deg(tb, c, s->far, s->meta, st);
+    return 2 + (tb.L - 1) + 1;
 }
 
 // Kernel launches of a7..a9 for one solute (no allocation, no host wait:
@@ -2350,12 +2502,18 @@ rism_status tree_enqueue(TreeState* s, const DevTables& t, const GridD& g, const
         k_sort_build<<<1, kSortThreads, shb, st>>>(ba, s->code, s->idx, s->code2, s->idx2, s->nodes, s->items,
                                                    s->prox_nodes, s->prox_items, s->meta);
         k_cells<<<1024, 256, 0, st>>>(n, s->meta, s->code, s->cell_start);
-        const size_t shu = (kChunk * 3 * np + kChunk + 3 * np) * sizeof(double);
-        cudaFuncSetAttribute(k_upward, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shu);
-        k_upward<<<4 * sm_count(), 256, shu, st>>>(deg, s->meta, s->nodes, s->prox_nodes, s->items, s->src, s->part);
-        k_proxy_reduce<<<2 * sm_count(), 256, 0, st>>>(deg, n, s->meta, s->nodes, s->prox_nodes, s->prox_items,
-                                                       s->part, s->src, s->srcf);
-        s->launches += 6;
+        s->launches += 4;
+        if (!s->tb.enabled) {
+            // source proxies: only the batch-level traversal uses them (with target boxes on, the box level
+            // accepts every cluster a batch would)
+            const size_t shu = (kChunk * 3 * np + kChunk + 3 * np) * sizeof(double);
+            cudaFuncSetAttribute(k_upward, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shu);
+            k_upward<<<4 * sm_count(), 256, shu, st>>>(deg, s->meta, s->nodes, s->prox_nodes, s->items, s->src,
+                                                       s->part);
+            k_proxy_reduce<<<2 * sm_count(), 256, 0, st>>>(deg, n, s->meta, s->nodes, s->prox_nodes,
+                                                           s->prox_items, s->part, s->src, s->srcf);
+            s->launches += 2;
+        }
     }
     const TBoxes& tb = s->tb;
     if (tb.enabled) {
@@ -2368,13 +2526,16 @@ rism_status tree_enqueue(TreeState* s, const DevTables& t, const GridD& g, const
         }
     }
     ListArgs fa{s->nbx, s->nby, s->nbz, sd.nx, sd.ny, sd.nz, o.theta, n, P3, s->cap_far,
-                tb.enabled ? s->dn_cnt : nullptr, s->dn_ent, s->cap_dn, tb};
+                tb.enabled ? s->dn_cnt : nullptr, s->dn_ent, s->cap_dn, tb, tb.enabled ? 0 : 1};
     ListArgs na = fa;
     na.cap = s->cap_near;
     const int lgrid = (s->nb + kListWarps - 1) / kListWarps;
-    k_far_lists<<<lgrid, 32 * kListWarps, 0, st>>>(fa, s->nodes, s->far_ent, s->far_cnt, s->meta);
-    k_near_lists<<<lgrid, 32 * kListWarps, 0, st>>>(na, s->cell_start, s->near_ent, s->near_cnt, s->meta);
-    s->launches += 2;
+    k_far_lists<<<lgrid, 32 * kListWarps, 0, st>>>(fa, s->nodes, s->far_ent, s->far_cnt, s->far_work, s->meta);
+    k_near_lists<<<lgrid, 32 * kListWarps, 0, st>>>(na, s->cell_start, s->near_ent, s->near_cnt, s->near_work,
+                                                     s->meta);
+    k_order<<<1, 1024, 0, st>>>(s->nb, s->near_work, s->near_order);
+    k_order<<<1, 1024, 0, st>>>(s->nb, s->far_work, s->far_order);
+    s->launches += 4;
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_err(err, e, "tree build");
     s->prepared = true;
@@ -2402,6 +2563,23 @@ EvalArgs make_args(TreeState* s, const DevTables& t, const GridD& g, const Phys&
     a.far_init = s->tb.enabled ? 1 : 0;
     a.ntab = s->ntab;
     a.ntab_inv = s->ntab_inv;
+    a.uni_rc = o.lj_mode != RISM_LJ_TOL ? 1 : 0;
+    a.near_order = s->near_order;
+    a.far_order = s->far_order;
+    {
+        const double ih = 1.0 / g.h;
+        for (int k = 0; k < kMaxSites; ++k) {
+            const double qs = k < ph.S ? ph.qs[k] : 0.0;
+            const double cu = ph.k_e * ih * qs;
+            a.cu_h[k] = (float)cu;
+            a.cu_l[k] = (float)(cu - (double)a.cu_h[k]);
+            a.cc[k] = (float)(-ph.beta * ph.k_e * ih * qs);
+            a.ch[k] = (float)(-ph.beta * ph.k_e / (2.0 * ph.eps_r) * ih * qs);
+        }
+        const double e2 = 2.0 * ph.ea2;
+        a.e2a_h = (float)e2;
+        a.e2a_l = (float)(e2 - (double)a.e2a_h);
+    }
     a.o = out;
     a.err = t.err;
     a.meta = s->meta;
@@ -2508,6 +2686,10 @@ void tree_destroy(TreeState* s) {
     cudaFree(s->ljs);
     cudaFree(s->far_cnt);
     cudaFree(s->near_cnt);
+    cudaFree(s->near_work);
+    cudaFree(s->near_order);
+    cudaFree(s->far_work);
+    cudaFree(s->far_order);
     cudaFree(s->prox_items);
     cudaFree(s->far_ent);
     cudaFree(s->near_ent);
