@@ -1821,7 +1821,7 @@ void launch_down_deg(const TBoxes& tb, const CPArgs& c, float4* far, const TreeM
 // ---- near field (LJ within cut-offs, erfc remainders within r_short) + epilogue
 template <int NXB, int NYB, int NZB>
 struct NearShape {
-    static constexpr int P = 4, TX = NXB / P, NT = TX * NYB * NZB, NW = NT / 32, NTP = NT + 32;  // + producer
+    static constexpr int P = 2, TX = NXB / P, NT = TX * NYB * NZB, NW = NT / 32, NTP = NT + 32;  // + producer
 };
 
 // One tile of near-field sources against the P points of a thread: LJ within the pair cut-offs (UNI: one
@@ -2055,14 +2055,15 @@ __global__ void __launch_bounds__(FarShape<NXB, NYB, NZB, PF>::NTP) k_far32(Eval
     far_body<NXB, NYB, NZB, PF, DH>(a, a.far_order[blockIdx.x], r, pairs);
 }
 
-// Register cap: 3 resident CTAs (consumer warps + producer warp) for up to 4 sites.
-template <int NXB, int NYB, int NZB, int SM>
+// Register cap (resident CTAs of consumer warps + producer warp) for up to 4 sites: 3 when only u or only the
+// asymptotics are wanted, 2 for u, c and h together (more accumulators; a tighter cap spills).
+template <int NXB, int NYB, int NZB, int SM, bool DU, bool DH>
 struct NearOcc {
-    static constexpr int v = SM <= 4 ? 384 / NearShape<NXB, NYB, NZB>::NT : 1;
+    static constexpr int v = SM <= 4 ? ((DU && DH) ? 2 : 3) : 1;
 };
 
 template <int NXB, int NYB, int NZB, int SM, bool DU, bool DH>
-__global__ void __launch_bounds__(NearShape<NXB, NYB, NZB>::NTP, (NearOcc<NXB, NYB, NZB, SM>::v))
+__global__ void __launch_bounds__(NearShape<NXB, NYB, NZB>::NTP, (NearOcc<NXB, NYB, NZB, SM, DU, DH>::v))
     k_near32(EvalArgs a) {
     __shared__ Ring<SM, true> r;
     __shared__ float4 tab[2 * kNTab];
@@ -2111,7 +2112,7 @@ __global__ void __launch_bounds__(FarShape<NXB, NYB, NZB, PF>::NTP) k_far32_batc
 }
 
 template <int NXB, int NYB, int NZB, int SM, bool DU, bool DH>
-__global__ void __launch_bounds__(NearShape<NXB, NYB, NZB>::NTP, (NearOcc<NXB, NYB, NZB, SM>::v))
+__global__ void __launch_bounds__(NearShape<NXB, NYB, NZB>::NTP, (NearOcc<NXB, NYB, NZB, SM, DU, DH>::v))
     k_near32_batched(BatchEval be) {
     __shared__ Ring<SM, true> r;
     __shared__ float4 tab[2 * kNTab];
