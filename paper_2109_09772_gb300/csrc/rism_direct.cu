@@ -123,16 +123,18 @@ cudaError_t launch_setup(const double* raw, int64_t n, int S, int smax, const do
 }
 
 // I_s = sum_i 4 pi (A/(9 rc^9) - B/(3 rc^3)); one CTA per site, fixed-order reduction.
-__global__ void k_lj_tail(const LJd* lj, int64_t n, int smax, double* out) {
-    constexpr int NT = 256;
+constexpr int kTailThreads = 1024;
+__global__ void __launch_bounds__(kTailThreads) k_lj_tail(const LJd* lj, int64_t n, int smax, double* out) {
+    constexpr int NT = kTailThreads;
     __shared__ double red[NT];
     int s = blockIdx.x;
     double acc = 0.0;
     for (int64_t i = threadIdx.x; i < n; i += NT) {
         LJd p = lj[i * smax + s];
         if (isfinite(p.rc2) && p.rc2 > 0.0) {
-            double rc = sqrt(p.rc2), rc3 = rc * rc * rc;
-            acc += 4.0 * M_PI * (p.A / (9.0 * rc3 * rc3 * rc3) - p.B / (3.0 * rc3));
+            // 4 pi (A / (9 rc^9) - B / (3 rc^3)) with r3 = rc^-3 from one reciprocal square root
+            const double ri = rsqrt(p.rc2), r3 = ri * ri * ri;
+            acc += 4.0 * M_PI * r3 * (p.A * (1.0 / 9.0) * r3 * r3 - p.B * (1.0 / 3.0));
         }
     }
     red[threadIdx.x] = acc;
@@ -145,7 +147,7 @@ __global__ void k_lj_tail(const LJd* lj, int64_t n, int smax, double* out) {
 }
 
 cudaError_t launch_lj_tail(const DevTables& t, int S, double* dev_out, cudaStream_t st) {
-    k_lj_tail<<<S, 256, 0, st>>>(t.ljd, t.n, t.smax, dev_out);
+    k_lj_tail<<<S, kTailThreads, 0, st>>>(t.ljd, t.n, t.smax, dev_out);
     return cudaGetLastError();
 }
 

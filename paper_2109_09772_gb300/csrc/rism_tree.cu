@@ -64,7 +64,7 @@ struct Node {
     int level;
     int prox;              // proxy set index, -1 if none
     int pad0, pad1;
-    double lo[3], hi[3];   // tight bounding box (grid units)
+    float lo[3], hi[3];    // bounding box of the atoms' positions (grid units, FP32 high parts)
 };
 
 struct TreeMeta {
@@ -182,8 +182,7 @@ __device__ __forceinline__ uint32_t morton3(uint32_t x, uint32_t y, uint32_t z) 
 }
 
 // ------------------------------------------------- bounding cube + codes
-__device__ __forceinline__ Geo to_grid(const Geo& p, const GridD& g) {
-    const double ih = 1.0 / g.h;
+__device__ __forceinline__ Geo to_grid(const Geo& p, const GridD& g, double ih) {
     return Geo{(p.x - g.ox) * ih, (p.y - g.oy) * ih, (p.z - g.oz) * ih, p.q};
 }
 
@@ -275,6 +274,7 @@ struct BuildArgs {
     const LJf* ljf;        // LJ tables (unsorted)
     int smax;
     GridD gd;
+    double ih;             // 1 / h
     Geo* src;              // out: sorted FP64 grid units
     SrcF* ssrcf;           // out: sorted float-float
     LJf* ljs;              // out: sorted LJ tables
@@ -365,7 +365,7 @@ __global__ void __launch_bounds__(kSortThreads) k_sort_build(BuildArgs a, uint32
     // ---- sorted copies of the sources (FP64 grid units, float-float) and LJ tables
     for (int i = threadIdx.x; i < n; i += blockDim.x) {
         const int j = (int)idx[i];
-        a.src[i] = to_grid(a.geo[j], a.gd);
+        a.src[i] = to_grid(a.geo[j], a.gd, a.ih);
         a.ssrcf[i] = a.srcf[j];
         for (int s = 0; s < a.smax; ++s) a.ljs[(int64_t)i * a.smax + s] = a.ljf[(int64_t)j * a.smax + s];
     }
@@ -502,28 +502,30 @@ __global__ void __launch_bounds__(kSortThreads) k_sort_build(BuildArgs a, uint32
     // internal node as the union of its children; one warp per node, level by level.
     for (int lv = s_nlvl - 1; lv >= 0; --lv) {
         for (int nid = s_lvl[lv] + w; nid < s_lvl[lv + 1]; nid += NW) {
+            // reduced in FP32 over the high parts of the float-float positions (within 1e-5 grid units of
+            // the exact box; the box only steers the acceptance test and the proxy placement)
             const Node nd = nodes[nid];
-            double lo[3] = {INFINITY, INFINITY, INFINITY}, hi[3] = {-INFINITY, -INFINITY, -INFINITY};
+            float lo[3] = {INFINITY, INFINITY, INFINITY}, hi[3] = {-INFINITY, -INFINITY, -INFINITY};
             if (nd.first_child < 0) {
                 for (int i = nd.begin + lane; i < nd.end; i += 32) {
-                    const Geo g = a.src[i];
-                    const double v[3] = {g.x, g.y, g.z};
+                    const SrcF g = a.ssrcf[i];
+                    const float v[3] = {g.xh, g.yh, g.zh};
                     for (int d = 0; d < 3; ++d) {
-                        lo[d] = fmin(lo[d], v[d]);
-                        hi[d] = fmax(hi[d], v[d]);
+                        lo[d] = fminf(lo[d], v[d]);
+                        hi[d] = fmaxf(hi[d], v[d]);
                     }
                 }
             } else if (lane < nd.nchild) {
                 const Node ch = nodes[nd.first_child + lane];
                 for (int d = 0; d < 3; ++d) {
-                    lo[d] = ch.lo[d];
-                    hi[d] = ch.hi[d];
+                    lo[d] = (float)ch.lo[d];
+                    hi[d] = (float)ch.hi[d];
                 }
             }
             for (int d = 0; d < 3; ++d)
                 for (int o = 16; o > 0; o >>= 1) {
-                    lo[d] = fmin(lo[d], __shfl_xor_sync(0xffffffffu, lo[d], o));
-                    hi[d] = fmax(hi[d], __shfl_xor_sync(0xffffffffu, hi[d], o));
+                    lo[d] = fminf(lo[d], __shfl_xor_sync(0xffffffffu, lo[d], o));
+                    hi[d] = fmaxf(hi[d], __shfl_xor_sync(0xffffffffu, hi[d], o));
                 }
             if (lane == 0)
                 for (int d = 0; d < 3; ++d) {
@@ -690,15 +692,15 @@ struct ListArgs {
 };
 
 // Node index -> (is a node opened for this target?) helpers shared by the traversals.
-__device__ __forceinline__ void node_sphere(const Node& nd, const double c[3], double& R2, double& rn) {
-    double rn2 = 0.0;
-    R2 = 0.0;
+__device__ __forceinline__ void node_sphere(const Node& nd, const float c[3], float& R2, float& rn) {
+    float rn2 = 0.f;
+    R2 = 0.f;
     for (int d = 0; d < 3; ++d) {
-        const double cn = 0.5 * (nd.lo[d] + nd.hi[d]);
+        const float cn = 0.5f * (nd.lo[d] + nd.hi[d]);
         R2 += (c[d] - cn) * (c[d] - cn);
-        rn2 += 0.25 * (nd.hi[d] - nd.lo[d]) * (nd.hi[d] - nd.lo[d]);
+        rn2 += 0.25f * (nd.hi[d] - nd.lo[d]) * (nd.hi[d] - nd.lo[d]);
     }
-    rn = sqrt(rn2);
+    rn = sqrtf(rn2);
 }
 
 // Loads a traversal's initial frontier: the root, or the pass-down list of the target's enclosing box.
@@ -749,6 +751,8 @@ __global__ void __launch_bounds__(32 * kListWarps) k_far_lists(ListArgs a, const
         double cb[3], rb;
         int lo[3], hi[3];
         batch_geom(a, b, cb, rb, lo, hi);
+        const float cbf[3] = {(float)cb[0], (float)cb[1], (float)cb[2]}, rbf = (float)rb;
+        const float th2 = (float)(a.theta * a.theta);
         int* cur = qa[w];
         int* nxt = qb[w];
         bool ovf = false;
@@ -773,10 +777,10 @@ __global__ void __launch_bounds__(32 * kListWarps) k_far_lists(ListArgs a, const
                 int nch = 0, fch = 0;
                 if (k < ncur) {
                     const Node nd = nodes[cur[k]];
-                    double R2, rn;
-                    node_sphere(nd, cb, R2, rn);
-                    const double rs = rb + rn;
-                    const bool sep = rs * rs < a.theta * a.theta * R2;
+                    float R2, rn;
+                    node_sphere(nd, cbf, R2, rn);
+                    const float rs = rbf + rn;
+                    const bool sep = rs * rs < th2 * R2;
                     const int cntn = nd.end - nd.begin;
                     if (sep && a.use_pc && nd.prox >= 0) {
                         kind = 1;
@@ -878,6 +882,8 @@ __global__ void __launch_bounds__(32 * kListWarps) k_tbox_lists(TListArgs a, con
     for (int bi = blockIdx.x * kListWarps + w; bi < nbl; bi += gridDim.x * kListWarps) {
         const int ib = bi % tb.nbx[l], jb = (bi / tb.nbx[l]) % tb.nby[l], kb = bi / (tb.nbx[l] * tb.nby[l]);
         const TBox T = tbox_at(tb, l, ib, jb, kb);
+        const float tc[3] = {(float)T.c[0], (float)T.c[1], (float)T.c[2]}, tr = (float)T.r;
+        const float th2 = (float)(a.theta * a.theta);
         const int box = tb.off[l] + bi;
         int* cur = qa[w];
         int* nxt = qb[w];
@@ -905,14 +911,14 @@ __global__ void __launch_bounds__(32 * kListWarps) k_tbox_lists(TListArgs a, con
                 if (k < ncur) {
                     node = cur[k];
                     const Node nd = nodes[node];
-                    double R2, rn;
-                    node_sphere(nd, T.c, R2, rn);
-                    const double rs = T.r + rn;
-                    if (T.proxied && rs * rs < a.theta * a.theta * R2) {
+                    float R2, rn;
+                    node_sphere(nd, tc, R2, rn);
+                    const float rs = tr + rn;
+                    if (T.proxied && rs * rs < th2 * R2) {
                         kind = 1;
                         e = make_int2(nd.begin, nd.end - nd.begin);
                         cpp += (long long)a.P3 * (nd.end - nd.begin);
-                    } else if (nd.first_child >= 0 && rn > T.r) {
+                    } else if (nd.first_child >= 0 && rn > tr) {
                         kind = 2;
                         nch = nd.nchild;
                         fch = nd.first_child;
@@ -2497,7 +2503,7 @@ rism_status tree_enqueue(TreeState* s, const DevTables& t, const GridD& g, const
         k_bounds<<<gb, 256, 0, st>>>(t.srcf, t.ljf, n, ph.S, t.smax, s->meta);
         k_codes<<<gb, 256, 0, st>>>(t.srcf, n, ph.rs / g.h, s->meta, s->code, s->idx);
         BuildArgs ba{n, s->leaf, P3, s->max_nodes, s->max_prox, s->max_items, t.geo, t.srcf, t.ljf, t.smax, g,
-                     s->src, s->srcf, s->ljs};
+                     1.0 / g.h, s->src, s->srcf, s->ljs};
         const size_t shb = (256 * 32 + 64) * sizeof(int);
         cudaFuncSetAttribute(k_sort_build, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shb);
         k_sort_build<<<1, kSortThreads, shb, st>>>(ba, s->code, s->idx, s->code2, s->idx2, s->nodes, s->items,
