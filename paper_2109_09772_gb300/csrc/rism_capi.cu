@@ -30,6 +30,7 @@ struct rism_ctx {
     double qs[kMaxSites] = {}, sigs[kMaxSites] = {}, epss[kMaxSites] = {}, rho[kMaxSites] = {};
     int is_ion[kMaxSites] = {};
     bool have_solute = false, have_solvent = false, dirty = true;
+    int64_t tree_calls = 0;  // treecode initializations of this context (the graph path starts at the second)
 
     // device state
     double* d_raw = nullptr;
@@ -39,6 +40,9 @@ struct rism_ctx {
     DevErr* d_err = nullptr;
     DevErr* h_err = nullptr;  // pinned
     double* d_tail = nullptr;
+    double* h_raw = nullptr;  // pinned copy of raw for the graph-replayed step
+    int64_t cap_h_raw = 0;
+    double* h_tail = nullptr;  // pinned [RISM_MAX_SITES]
     double* d_stage[3] = {nullptr, nullptr, nullptr};
     size_t stage_bytes[3] = {0, 0, 0};
     TreeState* tree = nullptr;
@@ -251,6 +255,7 @@ rism_status rism_grid_create(const rism_grid_desc* grid, const rism_options* opt
     if (e == cudaSuccess) e = cudaMalloc(&c->d_err, sizeof(DevErr));
     if (e == cudaSuccess) e = cudaMallocHost(&c->h_err, sizeof(DevErr));
     if (e == cudaSuccess) e = cudaMalloc(&c->d_tail, sizeof(double) * kMaxSites);
+    if (e == cudaSuccess) e = cudaMallocHost(&c->h_tail, sizeof(double) * kMaxSites);
     if (e == cudaSuccess) e = cudaMemsetAsync(c->d_err, 0, sizeof(DevErr), c->st);
     if (e == cudaSuccess) e = cudaStreamSynchronize(c->st);
     if (e != cudaSuccess) {
@@ -325,8 +330,7 @@ rism_status rism_init(rism_ctx* c, double* u, double* c_lr, double* h_lr, double
     if (!c->have_solute || !c->have_solvent) return fail(c, RISM_E_STATE, "set_solute and set_solvent first");
     cudaError_t e = cudaSetDevice(c->device);
     if (e != cudaSuccess) return cuda_fail(c, e, "cudaSetDevice");
-    rism_status s = ensure_tables(c);
-    if (s != RISM_OK) return s;
+    rism_status s = RISM_OK;
     if (h_lr && !(c->ph.kappa > 0.0)) return fail(c, RISM_E_INVALID, "h_lr needs kappa > 0 (ionic solvent)");
     const int64_t M = (int64_t)c->g.nx * c->g.ny * c->g.nz;
     const size_t bytes = sizeof(double) * (size_t)c->S * (size_t)M;
@@ -350,6 +354,46 @@ rism_status rism_init(rism_ctx* c, double* u, double* c_lr, double* h_lr, double
         }
     }
     Outputs o{dev[0], dev[1], dev[2]};
+    // Graph-replayed step (treecode, new solute coordinates, device outputs, from the context's second
+    // treecode call on): solute upload from pinned memory, tables, tree, lists and evaluation in one launch.
+    const bool any_out = o.u || o.c || o.h;
+    if (c->o.method == RISM_METHOD_TREECODE && any_out) ++c->tree_calls;
+    if (c->o.method == RISM_METHOD_TREECODE && c->dirty && c->n > 0 && !host_out && any_out && c->tree_calls > 1) {
+        if ((s = reserve_tables(c)) != RISM_OK) return s;
+        if (c->cap_h_raw < c->n) {
+            cudaFreeHost(c->h_raw);
+            c->h_raw = nullptr;
+            c->cap_h_raw = 0;
+            if ((e = cudaMallocHost(&c->h_raw, sizeof(double) * 6 * c->n)) != cudaSuccess)
+                return cuda_fail(c, e, "pinned solute buffer");
+            c->cap_h_raw = c->n;
+        }
+        std::memcpy(c->h_raw, c->raw.data(), sizeof(double) * 6 * c->n);
+        const bool tail = lj_tail && c->o.lj_mode != RISM_LJ_NONE;
+        SoluteStep step{c->h_raw, c->d_raw, c->n, c->sigs, c->epss, c->o.lj_mode, c->o.lj_rcut, c->o.lj_tol,
+                        tail ? c->d_tail : nullptr, c->h_tail};
+        c->info.eval_ms = 0.f;
+        bool used = false;
+        s = tree_graph_step(c->tree, c->t, c->gd, c->ph, c->o, o, step, c->st, c->err, c->info, used);
+        if (s != RISM_OK) return s;
+        if (used) {
+            rism_status st = check_device_error(c);
+            bool retry = false;
+            if (st == RISM_OK) st = tree_post(c->tree, c->info, retry, c->err);
+            if (st != RISM_OK) return st;
+            if (!retry) {
+                if (lj_tail)
+                    for (int k = 0; k < c->S; ++k) lj_tail[k] = tail ? c->h_tail[k] : 0.0;
+                c->dirty = false;
+                c->setup_launches = 0;
+                if (c->o.debug_flags & 2) c->info.eval_ms = c->info.box_ms + c->info.far_ms + c->info.near_ms;
+                return RISM_OK;
+            }
+            // a list outgrew its slots (now enlarged): rebuild through the regular path below
+        }
+    }
+    s = ensure_tables(c);
+    if (s != RISM_OK) return s;
     c->info.launches = c->setup_launches;
     c->setup_launches = 0;
     c->info.eval_ms = 0.f;
@@ -549,6 +593,8 @@ void rism_destroy(rism_ctx* c) {
     cudaFree(c->t.ljf);
     cudaFree(c->d_err);
     cudaFreeHost(c->h_err);
+    cudaFreeHost(c->h_tail);
+    cudaFreeHost(c->h_raw);
     cudaFree(c->d_tail);
     for (int k = 0; k < 3; ++k) cudaFree(c->d_stage[k]);
     if (c->ev[0]) cudaEventDestroy(c->ev[0]);

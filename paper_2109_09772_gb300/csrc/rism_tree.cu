@@ -2221,6 +2221,7 @@ cudaError_t dispatch(int smax, int v, int op, bool du, bool dh, const EvalArgs* 
 
 // ------------------------------------------------------------- state
 struct BatchCache;
+struct SoluteGraph;
 
 struct TreeState {
     int64_t cap_n = 0;
@@ -2260,6 +2261,7 @@ struct TreeState {
     int *cp_cnt = nullptr, *dn_cnt = nullptr, *dn_ent = nullptr, *tflag = nullptr, *tnch = nullptr;
     int2* cp_ent = nullptr;
     float2 *tpot = nullptr, *tpart = nullptr;
+    SoluteGraph* sg = nullptr;  // captured solute step (tree_graph_step)
     // short-range kernel tables
     float4* ntab = nullptr;
     double ntab_key[4] = {0.0, 0.0, 0.0, -1.0};
@@ -2665,8 +2667,28 @@ struct BatchCache {
     }
 };
 
+struct SoluteGraph {
+    std::vector<unsigned char> sig;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    cudaStream_t cs = nullptr;
+    int launches = 0;
+    ~SoluteGraph() {
+        if (exec) cudaGraphExecDestroy(exec);
+        if (graph) cudaGraphDestroy(graph);
+        if (cs) cudaStreamDestroy(cs);
+    }
+};
+
+void tree_graph_reset(TreeState* s) {
+    if (!s) return;
+    delete s->sg;
+    s->sg = nullptr;
+}
+
 void tree_destroy(TreeState* s) {
     if (!s) return;
+    delete s->sg;
     delete s->bc;
     for (int k = 0; k < 4; ++k)
         if (s->ev[k]) cudaEventDestroy(s->ev[k]);
@@ -2841,8 +2863,9 @@ rism_status tree_post(TreeState* s, rism_info& info, bool& retry, std::string& e
     }
     if (m.overflow) {
         if (grow_lists(s, m)) {
-            delete s->bc;  // buffers moved: the captured graph is stale
+            delete s->bc;  // buffers moved: the captured graphs are stale
             s->bc = nullptr;
+            tree_graph_reset(s);
             retry = true;
             char buf[256];
             std::snprintf(buf, sizeof buf,
@@ -2870,6 +2893,119 @@ rism_status tree_post(TreeState* s, rism_info& info, bool& retry, std::string& e
     info.direct_pairs = (int64_t)m.direct_pairs;
     info.proxy_pairs = (int64_t)m.proxy_pairs;
     info.near_pairs = (int64_t)m.near_pairs;
+    return RISM_OK;
+}
+
+rism_status tree_graph_step(TreeState* s, const DevTables& t, const GridD& g, const Phys& ph, const rism_options& o,
+                            Outputs out, const SoluteStep& step, cudaStream_t st, std::string& err, rism_info& info,
+                            bool& used) {
+    used = false;
+    if (o.autotune && s->tuned_key != problem_class(t, g, ph, o)) return RISM_OK;  // time the candidates first
+    if (!o.autotune) s->leaf = o.leaf;
+    rism_status r = tree_reserve(s, t, g, ph, o, err);
+    if (r != RISM_OK) return r;
+    const EvalArgs a = make_args(s, t, g, ph, o, out);
+    const CPArgs cpa = make_cp(s);
+    std::vector<unsigned char> sig;
+    auto put = [&](const void* p, size_t n) {
+        const unsigned char* c = static_cast<const unsigned char*>(p);
+        sig.insert(sig.end(), c, c + n);
+    };
+    put(&a, sizeof a);
+    put(&cpa, sizeof cpa);
+    put(&t, sizeof t);
+    put(&step, sizeof step);
+    put(step.sig_s, sizeof(double) * kMaxSites);
+    put(step.eps_s, sizeof(double) * kMaxSites);
+    put(&o, sizeof o);
+    const void* ptrs[] = {s->code, s->idx, s->code2, s->idx2, s->nodes, s->items, s->prox_nodes, s->part,
+                          s->src, s->srcf, s->ljs, s->far_cnt, s->near_cnt, s->prox_items, s->near_work,
+                          s->near_order, s->far_work, s->far_order, s->far_ent, s->near_ent, s->cell_start,
+                          s->meta, s->h_meta, s->dn_cnt, s->dn_ent, s->tflag, s->tnch, s->ntab};
+    put(ptrs, sizeof ptrs);
+    const int ints[] = {s->variant, s->leaf, s->max_nodes, s->max_prox, s->max_items, s->cap_far, s->cap_near,
+                        s->cap_cp, s->cap_dn, s->nb};
+    put(ints, sizeof ints);
+    cudaError_t e = cudaSuccess;
+    if (!s->sg || s->sg->sig != sig) {
+        tree_graph_reset(s);
+        if (o.debug_flags & 2)
+            for (int k = 0; k < 4; ++k)
+                if (!s->ev[k] && (e = cudaEventCreate(&s->ev[k])) != cudaSuccess) return cuda_err(err, e, "events");
+        SoluteGraph* G = new SoluteGraph();
+        s->sg = G;
+        if ((e = cudaStreamCreateWithFlags(&G->cs, cudaStreamNonBlocking)) != cudaSuccess) {
+            tree_graph_reset(s);
+            return cuda_err(err, e, "capture stream");
+        }
+        cudaStream_t cs = G->cs;
+        if ((e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal)) != cudaSuccess) {
+            tree_graph_reset(s);
+            return cuda_err(err, e, "graph capture");
+        }
+        const bool dh = out.h != nullptr, du = out.u != nullptr;
+        int launches = 0;
+        cudaMemcpyAsync(step.d_raw, step.h_raw, sizeof(double) * 6 * step.n, cudaMemcpyHostToDevice, cs);
+        DevTables tt = t;
+        e = launch_setup(step.d_raw, step.n, ph.S, t.smax, step.sig_s, step.eps_s, step.lj_mode, step.lj_rcut,
+                         step.lj_tol, g, tt, cs);
+        ++launches;
+        if (e == cudaSuccess) {
+            r = tree_enqueue(s, t, g, ph, o, cs, err);
+            launches += s->launches;
+        }
+        const bool timed = (o.debug_flags & 2) != 0;
+        // timing events become event-record nodes of the graph (external records)
+        auto rec = [&](int k) {
+            if (timed && e == cudaSuccess) e = cudaEventRecordWithFlags(s->ev[k], cs, cudaEventRecordExternal);
+        };
+        if (e == cudaSuccess && r == RISM_OK) {
+            rec(0);
+            launches += cp_enqueue(s, a, dh, cs);
+            rec(1);
+            if (e == cudaSuccess) e = dispatch(t.smax, s->variant, 2, du, dh, &a, s->nb, nullptr, 0, cs);
+            rec(2);
+            if (e == cudaSuccess) e = dispatch(t.smax, s->variant, 3, du, dh, &a, s->nb, nullptr, 0, cs);
+            rec(3);
+            launches += 2;
+        }
+        if (e == cudaSuccess && r == RISM_OK && step.d_tail) {
+            e = launch_lj_tail(t, ph.S, step.d_tail, cs);
+            ++launches;
+            if (e == cudaSuccess)
+                e = cudaMemcpyAsync(step.h_tail, step.d_tail, sizeof(double) * ph.S, cudaMemcpyDeviceToHost, cs);
+        }
+        if (e == cudaSuccess && r == RISM_OK)
+            e = cudaMemcpyAsync(s->h_meta, s->meta, sizeof(TreeMeta), cudaMemcpyDeviceToHost, cs);
+        cudaGraph_t graph = nullptr;
+        const cudaError_t ce = cudaStreamEndCapture(cs, &graph);
+        if (r != RISM_OK || e != cudaSuccess || ce != cudaSuccess) {
+            if (graph) cudaGraphDestroy(graph);
+            tree_graph_reset(s);
+            if (r != RISM_OK) return r;
+            return cuda_err(err, e != cudaSuccess ? e : ce, "solute graph capture");
+        }
+        G->graph = graph;
+        if ((e = cudaGraphInstantiate(&G->exec, graph, 0)) != cudaSuccess) {
+            tree_graph_reset(s);
+            return cuda_err(err, e, "graph instantiate");
+        }
+        G->sig = sig;
+        G->launches = launches;
+    }
+    if ((e = cudaGraphLaunch(s->sg->exec, st)) != cudaSuccess) {
+        tree_graph_reset(s);
+        return cuda_err(err, e, "graph launch");
+    }
+    used = true;
+    s->prepared = true;
+    s->timed = (o.debug_flags & 2) != 0;
+    info.launches = s->sg->launches;
+    const ShapeDesc sd = shape_of(s->variant);
+    info.batch[0] = sd.nx;
+    info.batch[1] = sd.ny;
+    info.batch[2] = sd.nz;
+    info.kernel_variant = s->variant;
     return RISM_OK;
 }
 

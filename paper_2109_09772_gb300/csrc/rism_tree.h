@@ -37,6 +37,28 @@ rism_status tree_eval(TreeState* ts, const DevTables& t, const GridD& g, const P
 // After the stream has been synchronised: copy the counters into info; on a
 // far-list overflow grow the buffer and set retry (run prepare + eval again).
 rism_status tree_post(TreeState* ts, rism_info& info, bool& retry, std::string& err);
+// One solute step as a replayed CUDA graph: upload of the solute from pinned host memory, setup of the
+// per-pair tables, tree, lists, box-level far field, far and near kernels, LJ tail and the copies of the
+// tail and the counters to pinned host memory.  The sequence is captured on a private stream the first time
+// a signature (every pointer, size and constant the launches depend on) is seen and replayed afterwards.
+// used = false (nothing enqueued) while the autotuner still has to time this problem class.
+struct SoluteStep {
+    const double* h_raw;  // pinned [n][6]
+    double* d_raw;        // device [n][6]
+    int64_t n;
+    const double* sig_s;
+    const double* eps_s;
+    int lj_mode;
+    double lj_rcut, lj_tol;
+    double* d_tail;       // device [S] or null (no tail)
+    double* h_tail;       // pinned [S]
+};
+rism_status tree_graph_step(TreeState* ts, const DevTables& t, const GridD& g, const Phys& ph, const rism_options& o,
+                            Outputs out, const SoluteStep& step, cudaStream_t st, std::string& err, rism_info& info,
+                            bool& used);
+// Drop the captured solute graph (buffers moved or the retry path ran).
+void tree_graph_reset(TreeState* ts);
+
 // Many solutes in one persistent, graph-captured launch sequence.
 // The whole sequence (per-solute setup and tree kernels, persistent far and
 // near kernels) is captured in a CUDA graph and replayed while unchanged.

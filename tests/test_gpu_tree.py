@@ -186,3 +186,50 @@ def test_target_proxies_error_falls_with_degree(R):
         assert g["info"]["cp_pairs"] > 0
         errs.append(rel_l2(g["c"][:, idx], ref["c"]))
     assert errs[0] > errs[1] > errs[2] > errs[3], errs
+
+
+def _fresh(R, w, xyz):
+    r = R.from_workload(w, method=R.METHOD_TREECODE, precision=R.PREC_FP32)
+    r.set_solute(xyz, w.solute.q, w.solute.sigma, w.solute.eps)
+    out = r.init(lj_tail=True)
+    res = {k: out[k].cpu().numpy() for k in ("u", "c", "h")}
+    res["lj_tail"] = out["lj_tail"]
+    r.close()
+    return res
+
+
+def test_graph_replay_matches_regular_path(R):
+    """From the second treecode call on, a context replays one captured graph (solute upload from pinned
+    memory, tables, tree, lists, evaluation, LJ tail).  New coordinates each call: every result equals, bit
+    for bit, a fresh context's first (uncaptured) call."""
+    w = I.small_workload(n_atoms=600, n=(48, 40, 36), h=0.5, seed=17, ions=True, lj_rcut=6.0, net=2.0)
+    r = R.from_workload(w, method=R.METHOD_TREECODE, precision=R.PREC_FP32)
+    rng = np.random.default_rng(3)
+    out = None
+    for step in range(4):
+        xyz = w.solute.xyz + rng.normal(0.0, 0.2, size=w.solute.xyz.shape)
+        r.set_solute(xyz, w.solute.q, w.solute.sigma, w.solute.eps)
+        out = r.init(lj_tail=True, out={k: out[k] for k in ("u", "c", "h")} if out else None)
+        ref = _fresh(R, w, xyz)
+        for k in ("u", "c", "h"):
+            assert np.array_equal(out[k].cpu().numpy(), ref[k]), (step, k)
+        np.testing.assert_array_equal(out["lj_tail"], ref["lj_tail"])
+    r.close()
+
+
+def test_graph_replay_larger_solute_grows_lists(R):
+    """The replayed step meets a solute with longer lists than the captured one: the call grows the list
+    slots, runs the regular path, and the result equals a fresh context's."""
+    small = I.small_workload(n_atoms=60, n=(48, 40, 36), h=0.5, seed=19, ions=True, lj_rcut=6.0)
+    big = I.small_workload(n_atoms=900, n=(48, 40, 36), h=0.5, seed=20, ions=True, lj_rcut=6.0)
+    r = R.from_workload(small, method=R.METHOD_TREECODE, precision=R.PREC_FP32, leaf=8)
+    r.init()
+    r.init()
+    r.set_solute(big.solute.xyz, big.solute.q, big.solute.sigma, big.solute.eps)
+    out = r.init(lj_tail=True)
+    r2 = R.from_workload(big, method=R.METHOD_TREECODE, precision=R.PREC_FP32, leaf=8)
+    ref = r2.init(lj_tail=True)
+    for k in ("u", "c", "h"):
+        assert np.array_equal(out[k].cpu().numpy(), ref[k].cpu().numpy()), k
+    r.close()
+    r2.close()
