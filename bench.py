@@ -112,28 +112,30 @@ def _peaks():
     return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "sm_max_mhz": 2070.0}, "fallback"
 
 
-# Algorithmic work of one far-field (grid point, source) pair of k_far32,
-# counted from its loop body: dx 2 FADD, d^2 1 FFMA, q/d 1 FMUL, Phi1 1 FADD,
-# d = d^2/d 1 FMUL, -kappa d 1 FMUL, Phik 1 FFMA -> 10 flops (FFMA = 2),
-# 8 FP32-pipe instructions and 2 MUFU (rsqrt, ex2) -> 10 instructions.
-# The direct kernels add the LJ terms: per site 2 FFMA + a shared 2 FMUL.
+# Algorithmic work per unit, counted from the loop bodies (thread instructions of one lane).
+# Far and box-level pairs (k_far32, k_cp_eval): dx 2 FADD, d^2 1 FFMA, q/d 1 FMUL, Phi1 1 FADD, d 1 FMUL,
+# -kappa d 1 FMUL, Phik 1 FFMA and the MUFU rsqrt and ex2: 10 flops (FFMA = 2).  The special-function pipe
+# bounds them: on this part rsqrt issues at 16 and ex2 at 32 per clock per SM (a microbenchmark of
+# independent MUFU chains, see the k_far32 profile summary), so a pair costs 1/16 + 1/32 SM clocks.
+# Near pairs (k_near32): a tested pair 4 (dx 2, d^2 1, compare 1); a pair inside the LJ cut-off 4 + 2 S
+# (compare, rcp, r^-6 2 FMUL, per site 2 FFMA); a pair inside r_short 10 + 4 F (two compares, rsqrt, q/d,
+# table coordinate 2 FMUL, index 2, fraction 2, per field c / h a cubic piece 3 FFMA + 1 accumulate).
 FLOPS_FAR = 10
-INSTR_FAR = 10
+MUFU_CLK_PER_PAIR = 1.0 / 16.0 + 1.0 / 32.0
+NEAR_TESTED, NEAR_LJ_BASE, NEAR_LJ_SITE, NEAR_SR_BASE, NEAR_SR_FIELD = 4, 4, 2, 10, 4
 FLOPS_LJ_SITE = 4
 FLOPS_LJ_SHARED = 2
 FP32_LANES_PER_SM = 128
 SMS = 152
-# DRAM bytes per k_far32 launch on this workload (dram__bytes_read.sum + dram__bytes_write.sum of one
-# ncu capture of the kernel as it stands); None when the kernel has changed since.
-FAR_TRAFFIC_BYTES = 1346048  # 1,185,792 read + 160,256 written
+# DRAM bytes per launch on this workload (dram__bytes_read.sum + dram__bytes_write.sum of one ncu capture of
+# the kernel as it stands); None when the kernel has changed since the capture.
+FAR_TRAFFIC_BYTES = None
+NEAR_TRAFFIC_BYTES = None
+BOX_TRAFFIC_BYTES = None
 
 
 def _alu_peak_tflops(sm_mhz):
     return SMS * FP32_LANES_PER_SM * 2 * sm_mhz * 1e6 / 1e12
-
-
-def _issue_peak_tinst(sm_mhz):
-    return SMS * 4 * 32 * sm_mhz * 1e6 / 1e12
 
 
 def run_gpu(args):
@@ -245,36 +247,46 @@ def run_gpu(args):
             g = out[k].reshape(S, -1)[:, torch.as_tensor(idx, device="cuda")].cpu().numpy()
             acc[k] = float(np.linalg.norm(g - ref[k]) / np.linalg.norm(ref[k]))
 
-    # roofline of the dominant kernel: the far field (k_far32), ALU bound
+    # rooflines of the evaluation kernels (CUDA events on the library stream); "roofline" is the dominant one
     inf = r.info()
     peaks, src = _peaks()
     pairs_far = inf["direct_pairs"] + inf["proxy_pairs"]
     sm_mhz = peaks.get("sm_max_mhz", 2070.0)
+    clk = sm_mhz * 1e6
+    mean = lambda v: (sum(v) / len(v)) if v else 0.0
+    kern = {}
     if method == R.METHOD_TREECODE and far_ms:
-        kern_ms = sum(far_ms) / len(far_ms)
-        flops = pairs_far * FLOPS_FAR
-        instr = pairs_far * INSTR_FAR
-        kname = "k_far32 (far field: Phi1, Phik over far lists)"
+        xu_peak = SMS * clk / MUFU_CLK_PER_PAIR / 1e9  # Gpairs/s
+        issue_peak = SMS * 4 * 32 * clk / 1e12  # T thread-instructions/s
+        nf = 2  # the step requests c and h
+        near_inst = (inf["near_tested"] * NEAR_TESTED + inf["lj_pairs"] * (NEAR_LJ_BASE + NEAR_LJ_SITE * S) +
+                     inf["sr_pairs"] * (NEAR_SR_BASE + NEAR_SR_FIELD * nf))
+        for name, t_ms, work, peak, unit, bound, traffic, desc in (
+                ("k_far32", mean(far_ms), pairs_far, xu_peak, "Gpairs/s", "alu", FAR_TRAFFIC_BYTES,
+                 "far field of the target batches: direct and source-proxy pairs; MUFU-bound"),
+                ("box level (k_cp_eval + interpolation)", mean(box_ms), inf["cp_pairs"], xu_peak, "Gpairs/s", "alu",
+                 BOX_TRAFFIC_BYTES, "proxy-target pairs, timed with the downward pass and interpolation"),
+                ("k_near32", mean(near_ms), near_inst, issue_peak, "Tinst/s", "alu", NEAR_TRAFFIC_BYTES,
+                 "near field + epilogue: algorithmic instructions of the tested / LJ / short-range pairs against "
+                 "the issue rate (4 schedulers x 32 lanes x clock per SM)")):
+            if t_ms <= 0:
+                continue
+            scale = 1e9 if unit == "Gpairs/s" else 1e12
+            ach = work / (t_ms * 1e-3) / scale
+            kern[name] = {"bound": bound, "achieved": ach, "peak": peak, "unit": unit, "frac": ach / peak,
+                          "traffic": traffic, "kernel_ms": t_ms, "work_per_launch": work, "what": desc,
+                          "peak_source": f"{SMS} SMs at {sm_mhz:.0f} MHz ({src} sm_max_mhz)"}
+        kname = max(kern, key=lambda k: kern[k]["kernel_ms"])
+        roof = dict(kern[kname], kernel=kname)
     else:
-        kern_ms = sum(evals) / len(evals) if evals else 0.0
+        kern_ms = mean(evals)
         flops = pairs_far * (FLOPS_FAR + FLOPS_LJ_SHARED + FLOPS_LJ_SITE * S)
-        instr = None
-        kname = "k_direct32 / k_direct64 (whole direct sum)"
-    peak = _alu_peak_tflops(sm_mhz)
-    achieved = flops / (kern_ms * 1e-3) / 1e12 if kern_ms > 0 else None
-    roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-            "frac": (achieved / peak) if achieved else None,
-            "traffic": FAR_TRAFFIC_BYTES if method == R.METHOD_TREECODE else None,
-            "kernel": kname, "kernel_ms": kern_ms, "flops_per_launch": flops,
-            "peak_source": f"FP32 FMA pipe of measured sm_max_mhz: {SMS} SMs x {FP32_LANES_PER_SM} lanes x 2 flops x "
-                           f"{sm_mhz:.0f} MHz ({src}); {FLOPS_FAR} algorithmic flops per far pair (FFMA = 2)"}
-    roof_issue = None
-    if instr is not None and kern_ms > 0:
-        ipk = _issue_peak_tinst(sm_mhz)
-        ach = instr / (kern_ms * 1e-3) / 1e12
-        roof_issue = {"bound": "alu-issue", "achieved": ach, "peak": ipk, "unit": "Tinst/s", "frac": ach / ipk,
-                      "note": f"{INSTR_FAR} algorithmic instructions per far pair (8 FP32-pipe + 2 MUFU) against "
-                              f"{SMS} SMs x 4 schedulers x 32 lanes x clock"}
+        peak = _alu_peak_tflops(sm_mhz)
+        achieved = flops / (kern_ms * 1e-3) / 1e12 if kern_ms > 0 else None
+        roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                "frac": (achieved / peak) if achieved else None, "traffic": None,
+                "kernel": "k_direct32 / k_direct64 (whole direct sum)", "kernel_ms": kern_ms,
+                "peak_source": f"FP32 FMA pipe: {SMS} SMs x {FP32_LANES_PER_SM} lanes x 2 x {sm_mhz:.0f} MHz ({src})"}
     timing = {"step_ms": ms, "far_ms": (sum(far_ms) / len(far_ms)) if far_ms else None,
               "near_ms": (sum(near_ms) / len(near_ms)) if near_ms else None,
               "box_ms": (sum(box_ms) / len(box_ms)) if box_ms else None,
@@ -284,10 +296,11 @@ def run_gpu(args):
            "vs_baseline": None, "dtype": "f32 pair terms, f64 accumulate/output" if prec == R.PREC_FP32 else "f64",
            "data": "synthetic (seeded globule, protein density)",
            "config": _config(w, args.method, args.precision), "e2e": e2e, "gpu_launches": launches,
-           "clocks": ck, "roofline": roof, "roofline_issue": roof_issue, "timing": timing,
+           "clocks": ck, "roofline": roof, "roofline_kernels": kern, "timing": timing,
            "error_vs_fp64_oracle_rel_l2": acc,
-           "counts": {k: inf[k] for k in ("direct_pairs", "proxy_pairs", "cp_pairs", "near_pairs", "tree_nodes",
-                                            "tree_proxied", "tree_leaves", "tree_boxes", "kernel_variant")},
+           "counts": {k: inf[k] for k in ("direct_pairs", "proxy_pairs", "cp_pairs", "near_pairs", "near_tested",
+                                            "lj_pairs", "sr_pairs", "tree_nodes", "tree_proxied", "tree_leaves",
+                                            "tree_boxes", "kernel_variant")},
            "wall_s": t_wall}
     if rank == 0 and not args.no_fp64:
         # the plain FP64 direct sum on the same GPU, one timed step (the comparison of the headline)

@@ -130,6 +130,9 @@ typedef struct {
     float box_ms;          /* treecode: box-level far field (proxy targets, downward pass, interpolation) */
     int32_t tree_boxes;    /* target boxes whose proxies received at least one cluster */
     int64_t cp_pairs;      /* (proxy target, atom) pairs of the box-level far field */
+    int64_t near_tested;   /* treecode near field: (point, atom) pairs distance-tested */
+    int64_t lj_pairs;      /* ... of them inside the LJ cut-off (LJ evaluated) */
+    int64_t sr_pairs;      /* ... of them inside r_short at d > 0 (short-range remainders evaluated) */
 } rism_info;
 
 /* Fill *o with the defaults listed above.  Never fails. */

@@ -415,6 +415,7 @@ rism_status rism_init(rism_ctx* c, double* u, double* c_lr, double* h_lr, double
             c->info.near_pairs = 0;
             c->info.cp_pairs = 0;
             c->info.tree_boxes = 0;
+            c->info.near_tested = c->info.lj_pairs = c->info.sr_pairs = 0;
             c->info.box_ms = 0.f;
             c->info.launches += 1;
         } else {

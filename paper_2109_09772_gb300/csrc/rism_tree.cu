@@ -53,7 +53,7 @@ constexpr int kSortThreads = 1024;
 constexpr int kMortonBits = 10;          // per axis
 constexpr int kMaxLevel = kMortonBits;   // octree depth limit
 constexpr int kChunk = 16;               // atoms per upward-pass work item
-constexpr int kT = 64;                   // sources per shared-memory tile
+constexpr int kT = 64;                   // sources per shared-memory tile (<= 64: the near culling uses two ballots)
 constexpr int kStack = 8 * kMaxLevel + 8;
 constexpr double kCellFrac = 0.25;        // near-field cells are at least this fraction of the near radius wide
 
@@ -84,6 +84,8 @@ struct TreeMeta {
     double rnear;          // near-field radius (grid units): max(largest LJ cut-off, r_short)
     unsigned long long direct_pairs, proxy_pairs, near_pairs;
     unsigned long long cp_pairs;  // (target proxy, atom) pairs of the box-level far field
+    unsigned long long near_tested, lj_pairs, sr_pairs;  // near kernel: pairs tested, inside the LJ cut-off,
+                                                          // inside r_short (d > 0)
     int cp_need, dn_need;  // largest accepted-range list / pass-down list of a target box
     int tboxes;            // target boxes that took proxies and have a non-empty list
     int pad2;
@@ -1083,6 +1085,7 @@ __global__ void __launch_bounds__(1024) k_order(int nb, const int* __restrict__ 
 
 __global__ void k_reset_meta(TreeMeta* meta) {
     meta->direct_pairs = meta->proxy_pairs = meta->near_pairs = meta->cp_pairs = 0ull;
+    meta->near_tested = meta->lj_pairs = meta->sr_pairs = 0ull;
     meta->far_need = meta->near_need = meta->cp_need = meta->dn_need = 0;
     meta->tboxes = 0;
     meta->wide = 0;
@@ -1840,16 +1843,28 @@ __device__ __forceinline__ void near_tile(const SrcF* __restrict__ Sx, const LJf
                                           const float (&gx)[P], float fy, float fz, float rn2, float rs2, float rcu2,
                                           float tinv, const float4* tab, bool DC, float c0h, float h0h,
                                           const float (&wlo)[3], const float (&whi)[3], float rcull2,
-                                          float (&psc)[P], float (&psh)[P], float (&plj)[P][SM], unsigned& hit) {
-    for (int s0 = 0; s0 < cnt; ++s0) {
+                                          float (&psc)[P], float (&psh)[P], float (&plj)[P][SM], unsigned& hit,
+                                          unsigned (&cnt3)[3]) {
+    // Warp-parallel culling of the tile: lane l tests sources l and l + 32 against the warp's point box; the
+    // ballots list the survivors, which every lane then visits in tile order.  A culled source has no point
+    // of the warp within the near radius, so skipping it changes no sum.
+    const int lane = threadIdx.x & 31;
+    auto keep = [&](int i) {
+        if (i >= cnt) return false;
+        const float4 g = *reinterpret_cast<const float4*>(&Sx[i].xh);
+        const float qx = fmaxf(0.f, fmaxf(wlo[0] - g.x, g.x - whi[0]));
+        const float qy = fmaxf(0.f, fmaxf(wlo[1] - g.y, g.y - whi[1]));
+        const float qz = fmaxf(0.f, fmaxf(wlo[2] - g.z, g.z - whi[2]));
+        return fmaf(qx, qx, fmaf(qy, qy, qz * qz)) < rcull2;
+    };
+    const unsigned long long live =
+        (unsigned long long)__ballot_sync(0xffffffffu, keep(lane)) |
+        ((unsigned long long)__ballot_sync(0xffffffffu, keep(lane + 32)) << 32);
+    for (unsigned long long mk = live; mk != 0ull; mk &= mk - 1ull) {
+        const int s0 = __ffsll((long long)mk) - 1;
         const float4 g0 = *reinterpret_cast<const float4*>(&Sx[s0].xh);
         const float4 g1 = *reinterpret_cast<const float4*>(&Sx[s0].xl);
-        {
-            const float qx = fmaxf(0.f, fmaxf(wlo[0] - g0.x, g0.x - whi[0]));
-            const float qy = fmaxf(0.f, fmaxf(wlo[1] - g0.y, g0.y - whi[1]));
-            const float qz = fmaxf(0.f, fmaxf(wlo[2] - g0.z, g0.z - whi[2]));
-            if (fmaf(qx, qx, fmaf(qy, qy, qz * qz)) >= rcull2) continue;  // same outcome in every lane
-        }
+        cnt3[0] += P;
         const float dy = (fy - g0.y) - g1.y;
         const float dz = (fz - g0.z) - g1.z;
         const float dyz2 = fmaf(dy, dy, dz * dz);
@@ -1862,6 +1877,7 @@ __device__ __forceinline__ void near_tile(const SrcF* __restrict__ Sx, const LJf
             if (d2 < rs2) {
                 if (d2 > 0.f) {
                     // erfc(x)/d and e^{-x^2}[erfcx(x-a) + erfcx(x+a)]/d from the cubic pieces in d
+                    ++cnt3[2];
                     const float ri = rsqrt_approx(d2);
                     const float qr = g0.w * ri;
                     const float uu = d2 * ri * tinv;
@@ -1884,6 +1900,7 @@ __device__ __forceinline__ void near_tile(const SrcF* __restrict__ Sx, const LJf
             if (DU) {
                 if (UNI) {
                     if (d2 < rcu2) {
+                        ++cnt3[1];
                         const float r2i = rcp_approx(d2);
                         const float r6 = r2i * r2i * r2i;
 #pragma unroll
@@ -1893,6 +1910,7 @@ __device__ __forceinline__ void near_tile(const SrcF* __restrict__ Sx, const LJf
                         }
                     }
                 } else {
+                    ++cnt3[1];
                     const float r2i = rcp_approx(d2);
                     const float r6 = r2i * r2i * r2i;
 #pragma unroll
@@ -1946,6 +1964,7 @@ __device__ void near_body(const EvalArgs& a, int b, Ring<SM, true>& r, float4* t
         for (int s = 0; s < SM; ++s) ljh[p][s] = ljl[p][s] = 0.f;
     }
     unsigned hit = 0u;
+    unsigned cnt3[3] = {0u, 0u, 0u};  // pairs tested / inside the LJ cut-off / inside r_short
     const float tinv = a.ntab_inv;
     Cursor cur;
     __syncthreads();
@@ -1973,10 +1992,10 @@ __device__ void near_body(const EvalArgs& a, int b, Ring<SM, true>& r, float4* t
         }
         if (a.uni_rc)
             near_tile<P, SM, DU, DH, true>(Sx, L, cnt, gx, fy, fz, rn2, rs2, rcu2, tinv, tab, DC, c0h, h0h, wlo, whi,
-                                           rcull2, psc, psh, plj, hit);
+                                           rcull2, psc, psh, plj, hit, cnt3);
         else
             near_tile<P, SM, DU, DH, false>(Sx, L, cnt, gx, fy, fz, rn2, rs2, rcu2, tinv, tab, DC, c0h, h0h, wlo,
-                                            whi, rcull2, psc, psh, plj, hit);
+                                            whi, rcull2, psc, psh, plj, hit, cnt3);
 #pragma unroll
         for (int p = 0; p < P; ++p) {
             if (DC) ff_add(sch[p], scl[p], psc[p]);
@@ -1988,6 +2007,19 @@ __device__ void near_body(const EvalArgs& a, int b, Ring<SM, true>& r, float4* t
         }
     }, [](int) {});
     if (rr != kRingDone) return;
+    {
+        unsigned long long c0 = cnt3[0], c1 = cnt3[1], c2 = cnt3[2];
+        for (int o = 16; o > 0; o >>= 1) {
+            c0 += __shfl_xor_sync(0xffffffffu, c0, o);
+            c1 += __shfl_xor_sync(0xffffffffu, c1, o);
+            c2 += __shfl_xor_sync(0xffffffffu, c2, o);
+        }
+        if ((tid & 31) == 0) {
+            atomicAdd(&a.meta->near_tested, c0);
+            atomicAdd(&a.meta->lj_pairs, c1);
+            atomicAdd(&a.meta->sr_pairs, c2);
+        }
+    }
 
     const GridD& g = a.g;
     if (j >= g.ny || k >= g.nz || i0 >= g.nx) return;
@@ -2887,6 +2919,9 @@ rism_status tree_post(TreeState* s, rism_info& info, bool& retry, std::string& e
     }
     info.cp_pairs = (int64_t)m.cp_pairs;
     info.tree_boxes = m.tboxes;
+    info.near_tested = (int64_t)m.near_tested;
+    info.lj_pairs = (int64_t)m.lj_pairs;
+    info.sr_pairs = (int64_t)m.sr_pairs;
     info.tree_nodes = m.nnodes;
     info.tree_proxied = m.nprox;
     info.tree_leaves = m.nleaves;

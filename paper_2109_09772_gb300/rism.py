@@ -52,7 +52,8 @@ class Info(C.Structure):
                 ("tree_leaves", C.c_int32), ("direct_pairs", C.c_int64), ("proxy_pairs", C.c_int64),
                 ("near_pairs", C.c_int64), ("batch", C.c_int32 * 3), ("kernel_variant", C.c_int32),
                 ("launches", C.c_int32), ("eval_ms", C.c_float), ("far_ms", C.c_float), ("near_ms", C.c_float),
-                ("box_ms", C.c_float), ("tree_boxes", C.c_int32), ("cp_pairs", C.c_int64)]
+                ("box_ms", C.c_float), ("tree_boxes", C.c_int32), ("cp_pairs", C.c_int64),
+                ("near_tested", C.c_int64), ("lj_pairs", C.c_int64), ("sr_pairs", C.c_int64)]
 
 
 EXPORTS = ["rism_default_options", "rism_grid_create", "rism_set_solute", "rism_set_solvent", "rism_potential",
