@@ -44,6 +44,23 @@ def _workload(seed=0):
     return I.workload(1, seed=seed)
 
 
+def reduce_max(dist, v, device):
+    """The slowest rank's value (max over ranks); the rank's own value without a process group."""
+    if dist is None:
+        return v
+    import torch
+
+    t = torch.tensor([float(v)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_value(world, S, M, ms):
+    """Whole-job throughput in Gpts*site/s: every rank initializes its own solute of S sites on M points
+    (weak scaling, independent problems), so a step of the slowest rank delivers world * S * M values."""
+    return world * S * M / (ms * 1e-3) / 1e9
+
+
 def _config(w, method, precision):
     return {"workload": WORKLOAD, "atoms": w.solute.n, "grid": list(w.grid.n), "spacing_A": w.grid.h,
             "sites": w.solvent.nsite, "lj_rcut_A": w.opts.get("lj_rcut"), "degree": w.opts.get("degree"),
@@ -198,12 +215,8 @@ def run_gpu(args):
     torch.cuda.synchronize()
     t_wall = time.perf_counter() - t_wall0
     ck = clocks.stop()
-    ms = sum(times) / len(times)
-    if dist:
-        t = torch.tensor([ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
-    value = world * S * M / (ms * 1e-3) / 1e9
+    ms = reduce_max(dist, sum(times) / len(times), "cuda")
+    value = job_value(world, S, M, ms)
 
     # end to end: host (pinned) output buffers, device-to-host copies inside the timed region
     hu = torch.empty((S, M), dtype=torch.float64).pin_memory()
@@ -225,12 +238,8 @@ def run_gpu(args):
         t0 = time.perf_counter()
         step_host()
         et.append(time.perf_counter() - t0)
-    e2e_ms = 1e3 * sum(et) / len(et)
-    if dist:
-        t = torch.tensor([e2e_ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_ms = float(t.item())
-    e2e = {"value": world * S * M / (e2e_ms * 1e-3) / 1e9, "unit": UNIT, "ms_per_step": e2e_ms,
+    e2e_ms = reduce_max(dist, 1e3 * sum(et) / len(et), "cuda")
+    e2e = {"value": job_value(world, S, M, e2e_ms), "unit": UNIT, "ms_per_step": e2e_ms,
            "h2d_bytes_per_step": int(xyz.nbytes + q.nbytes + sg.nbytes + ep.nbytes),
            "d2h_bytes_per_step": int(3 * S * M * 8 + S * 8)}
 
@@ -578,6 +587,19 @@ def suite_adjoint(args):
     r.close()
 
 
+def suite_mufu(args):
+    """Issue rates of rsqrt / ex2 / rcp / FFMA (thread ops per clock per SM): compiles and runs the
+    microbenchmark in paper_2109_09772_gb300/microbench (the denominators of the pair kernels' rooflines)."""
+    import tempfile
+
+    src = os.path.join(ROOT, "paper_2109_09772_gb300", "microbench", "mufu_rates.cu")
+    with tempfile.TemporaryDirectory() as d:
+        exe = os.path.join(d, "mufu_rates")
+        subprocess.run(["nvcc", "-gencode", "arch=compute_103a,code=sm_103a", "-O3", "-o", exe, src], check=True)
+        r = subprocess.run([exe], capture_output=True, text=True, check=True)
+    print(r.stdout.strip(), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -591,12 +613,13 @@ def main():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-fp64", action="store_true")
     ap.add_argument("--no-check", action="store_true")
-    ap.add_argument("--suite", default=None, choices=["pareto", "batched", "adjoint"])
+    ap.add_argument("--suite", default=None, choices=["pareto", "batched", "adjoint", "mufu"])
     ap.add_argument("--reps", type=int, default=3)
     ap.add_argument("--adj-atoms", type=int, default=16)
     args = ap.parse_args()
     if args.suite:
-        {"pareto": suite_pareto, "batched": suite_batched, "adjoint": suite_adjoint}[args.suite](args)
+        {"pareto": suite_pareto, "batched": suite_batched, "adjoint": suite_adjoint,
+         "mufu": suite_mufu}[args.suite](args)
         return
     if args.warmup < 3:
         args.warmup = 3

@@ -68,8 +68,10 @@ typedef enum {
 } rism_status;
 
 enum { RISM_METHOD_DIRECT = 0, RISM_METHOD_TREECODE = 1 };
-/* FP64: every pair term and sum in double.  FP32: pair terms in single
- * precision in a tile-local frame, sums compensated (float-float). */
+/* FP64: every pair term and sum in double (direct method only: the treecode
+ * with FP64 returns RISM_E_UNSUPPORTED, its interpolation error is far above
+ * FP32 pair rounding).  FP32: pair terms in single precision with exact
+ * lattice-relative distances, sums compensated (float-float). */
 enum { RISM_PREC_FP64 = 0, RISM_PREC_FP32 = 1 };
 /* LJ truncation (Sec. 2.6): none; one cut-off for all pairs; per-pair
  * cut-off from a tolerance |u_LJ(rc)| = lj_tol. */
@@ -103,7 +105,8 @@ typedef struct {
     double k_B;         /* Boltzmann constant, kcal/(mol K); default 0.0019872041 */
     double r_short;     /* radius of the short-range erfc remainders (A); 0 = 6 eta (FP64) / 5 eta (FP32) */
     int32_t autotune;   /* 1: time the candidate launch shapes once per problem class and cache the winner */
-    int64_t wait_limit; /* spin iterations before a bounded device wait gives up; default 1<<26 */
+    int64_t wait_limit; /* polls (each may sleep up to 200 ns) before a bounded device wait gives up;
+                           default 1<<24 (a few seconds) */
     int32_t debug_flags;/* test hooks, 0 in production.  Bit 0: the direct kernels skip their first
                            bulk copy, so its wait runs out and the call returns RISM_E_TIMEOUT.
                            Bit 1: time the evaluation kernel with CUDA events (rism_info.eval_ms). */

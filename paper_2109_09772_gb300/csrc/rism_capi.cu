@@ -79,6 +79,8 @@ int padded_sites(int S) { return S <= 2 ? 2 : (S <= 4 ? 4 : 8); }
 rism_status check_options(rism_ctx* c, const rism_options& o) {
     if (o.method != RISM_METHOD_DIRECT && o.method != RISM_METHOD_TREECODE) return fail(c, RISM_E_INVALID, "method");
     if (o.precision != RISM_PREC_FP64 && o.precision != RISM_PREC_FP32) return fail(c, RISM_E_INVALID, "precision");
+    if (o.method == RISM_METHOD_TREECODE && o.precision == RISM_PREC_FP64)
+        return fail(c, RISM_E_UNSUPPORTED, "the treecode computes FP32 pair terms; FP64 needs the direct method");
     if (o.degree < 1 || o.degree > kMaxDegree) return fail(c, RISM_E_INVALID, "degree out of range");
     if (!(o.theta > 0.0 && o.theta < 1.0)) return fail(c, RISM_E_INVALID, "theta must lie in (0, 1)");
     if (o.leaf < 1) return fail(c, RISM_E_INVALID, "leaf must be >= 1");
@@ -229,7 +231,7 @@ void rism_default_options(rism_options* o) {
     o->k_B = 0.0019872041;
     o->r_short = 0.0;
     o->autotune = 0;
-    o->wait_limit = 1LL << 26;
+    o->wait_limit = 1LL << 24;
     o->target_proxies = 1;
 }
 
@@ -246,9 +248,10 @@ rism_status rism_grid_create(const rism_grid_desc* grid, const rism_options* opt
     c->g = *grid;
     if (opts) c->o = *opts;
     else rism_default_options(&c->o);
-    if (check_options(c, c->o) != RISM_OK) {
+    const rism_status cs = check_options(c, c->o);
+    if (cs != RISM_OK) {
         delete c;
-        return RISM_E_INVALID;
+        return cs;
     }
     c->st = static_cast<cudaStream_t>(stream);
     cudaError_t e = cudaGetDevice(&c->device);

@@ -135,10 +135,24 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
         : "memory");
     return done != 0;
 }
+// try_wait with a suspend-time hint: the waiting thread may sleep up to `ns` nanoseconds for the phase
+// instead of returning at once, so a waiting warp issues few instructions.
+__device__ __forceinline__ bool mbar_try_wait_sleep(uint64_t* bar, uint32_t parity, uint32_t ns) {
+    uint32_t done;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(done)
+        : "r"(smem_u32(bar)), "r"(parity), "r"(ns)
+        : "memory");
+    return done != 0;
+}
+constexpr uint32_t kWaitSleepNs = 200;  // suspend hint per poll; limit polls x 200 ns bounds a wait
 // Bounded wait: false when `limit` polls pass without the phase completing.
 __device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity, long long limit) {
     for (long long it = 0; it < limit; ++it)
-        if (mbar_try_wait(bar, parity)) return true;
+        if (mbar_try_wait_sleep(bar, parity, kWaitSleepNs)) return true;
     return false;
 }
 // One bulk (non-tensor) TMA copy global -> shared; dst, src 16-byte aligned,

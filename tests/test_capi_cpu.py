@@ -101,6 +101,9 @@ def test_invalid_arguments_rejected_without_gpu(lib):
     assert lib.rism_grid_create(C.byref(g), C.byref(bad), None, C.byref(ctx)) == rism.E_INVALID
     bad = rism.default_options(degree=0)
     assert lib.rism_grid_create(C.byref(g), C.byref(bad), None, C.byref(ctx)) == rism.E_INVALID
+    # the treecode computes FP32 pair terms: asking it for FP64 is refused, not silently downgraded
+    bad = rism.default_options(method=rism.METHOD_TREECODE, precision=rism.PREC_FP64)
+    assert lib.rism_grid_create(C.byref(g), C.byref(bad), None, C.byref(ctx)) == rism.E_UNSUPPORTED
     # NULL contexts
     assert lib.rism_init(None, None, None, None, None) == rism.E_INVALID
     assert lib.rism_set_solute(None, 0, None, None, None, None) == rism.E_INVALID
