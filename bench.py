@@ -511,14 +511,13 @@ def suite_batched(args):
     for r, w in zip(rs, ws):
         r._sol = (w.solute.xyz, w.solute.q, w.solute.sigma, w.solute.eps)
     ms_seq = _events_ms(seq, reps=args.reps)
-    R.potential_batched(rs)  # capture
+    bouts = [R.potential_batched(rs)]  # capture
     torch.cuda.synchronize()
-    bouts = [None]
 
     def bat():
         for r in rs:
             r.set_solute(*r._sol)
-        bouts[0] = R.potential_batched(rs)
+        bouts[0] = R.potential_batched(rs, out=bouts[0])
 
     ms_bat = _events_ms(bat, reps=args.reps)
     pts = sum(w.solvent.nsite * w.grid.npts for w in ws)

@@ -1129,6 +1129,8 @@ struct EvalArgs {
     int uni_rc;            // every (atom, site) pair has the same LJ cut-off (global cut-off or none)
     const int* near_order; // CTA -> batch of the per-solute near kernel (heaviest first)
     const int* far_order;  // the same for the far kernel
+    const int* near_work;  // per batch: candidate atoms of the near list
+    const int* far_work;   // per batch: atoms and proxies of the far list
     // epilogue constants per site (grid-unit sums -> physical fields), split into float pairs on the host:
     // u = cu Phi1 + LJ, c = cc (Phi1 - S_c), h = ch (2 e^{a^2} Phik - S_h)
     float cu_h[kMaxSites], cu_l[kMaxSites], cc[kMaxSites], ch[kMaxSites];
@@ -2116,7 +2118,17 @@ struct BatchEval {
     const int* item_off;    // [count + 1] prefix of batch counts
     int count, total;
     int* queue;             // work counter, zeroed before the launch
+    const int* order;       // queue position -> global item (heaviest first over all solutes)
 };
+
+// Work of every (solute, batch) item in one array (far: near = 0, near: near = 1), for the global order.
+__global__ void k_gather_work(const EvalArgs* args, const int* item_off, int count, int near, int* work) {
+    const int sid = blockIdx.x;
+    if (sid >= count) return;
+    const int* w = near ? args[sid].near_work : args[sid].far_work;
+    const int b0 = item_off[sid], nb = item_off[sid + 1] - b0;
+    for (int b = threadIdx.x; b < nb; b += blockDim.x) work[b0 + b] = w[b];
+}
 
 __device__ __forceinline__ int find_solute(const BatchEval& be, int it) {
     int lo = 0, hi = be.count - 1;
@@ -2137,7 +2149,8 @@ __global__ void __launch_bounds__(FarShape<NXB, NYB, NZB, PF>::NTP) k_far32_batc
     for (;;) {
         __syncthreads();
         if (threadIdx.x == 0) {
-            s_item = atomicAdd(be.queue, 1);
+            const int q = atomicAdd(be.queue, 1);
+            s_item = q < be.total ? be.order[q] : be.total;
             if (s_item < be.total) sa = be.args[find_solute(be, s_item)];
         }
         __syncthreads();
@@ -2160,7 +2173,8 @@ __global__ void __launch_bounds__(NearShape<NXB, NYB, NZB>::NTP, (NearOcc<NXB, N
     for (;;) {
         __syncthreads();
         if (threadIdx.x == 0) {
-            s_item = atomicAdd(be.queue, 1);
+            const int q = atomicAdd(be.queue, 1);
+            s_item = q < be.total ? be.order[q] : be.total;
             if (s_item < be.total) sa = be.args[find_solute(be, s_item)];
         }
         __syncthreads();
@@ -2220,6 +2234,7 @@ cudaError_t dispatch_v(int op, bool du, bool dh, const EvalArgs* a, int nb, cons
             K::far_b(*be, sms * std::max(1, K::occ_far()), st);
             BatchEval b2 = *be;
             b2.queue = be->queue + 1;
+            b2.order = be->order + be->total;  // the near order follows the far order
             K::near_b(b2, sms * std::max(1, K::occ_near()), st);
         }
     };
@@ -2607,6 +2622,8 @@ EvalArgs make_args(TreeState* s, const DevTables& t, const GridD& g, const Phys&
     a.uni_rc = o.lj_mode != RISM_LJ_TOL ? 1 : 0;
     a.near_order = s->near_order;
     a.far_order = s->far_order;
+    a.near_work = s->near_work;
+    a.far_work = s->far_work;
     {
         const double ih = 1.0 / g.h;
         for (int k = 0; k < kMaxSites; ++k) {
@@ -2688,6 +2705,11 @@ struct BatchCache {
     EvalArgs* d_args = nullptr;
     int* d_off = nullptr;
     int* d_queue = nullptr;
+    int* d_work = nullptr;   // [total] item work (far, then near)
+    int* d_order = nullptr;  // [2 total] global orders: far, then near
+    static constexpr int kBranches = 8;  // per-solute preparations captured on this many forked streams
+    cudaStream_t side[kBranches] = {};
+    cudaEvent_t fork = nullptr, join[kBranches] = {};
     int cap = 0;
     ~BatchCache() {
         if (exec) cudaGraphExecDestroy(exec);
@@ -2696,6 +2718,13 @@ struct BatchCache {
         cudaFree(d_args);
         cudaFree(d_off);
         cudaFree(d_queue);
+        cudaFree(d_work);
+        cudaFree(d_order);
+        for (int k = 0; k < kBranches; ++k) {
+            if (side[k]) cudaStreamDestroy(side[k]);
+            if (join[k]) cudaEventDestroy(join[k]);
+        }
+        if (fork) cudaEventDestroy(fork);
     }
 };
 
@@ -3097,7 +3126,9 @@ rism_status batch_eval(std::vector<BatchItem>& items, const rism_options& o, cud
         bc = new BatchCache();
         if ((e = cudaMalloc(&bc->d_args, sizeof(EvalArgs) * count)) != cudaSuccess ||
             (e = cudaMalloc(&bc->d_off, sizeof(int) * (count + 1))) != cudaSuccess ||
-            (e = cudaMalloc(&bc->d_queue, sizeof(int) * 2)) != cudaSuccess)
+            (e = cudaMalloc(&bc->d_queue, sizeof(int) * 2)) != cudaSuccess ||
+            (e = cudaMalloc(&bc->d_work, sizeof(int) * ((size_t)off[count] + 1))) != cudaSuccess ||
+            (e = cudaMalloc(&bc->d_order, sizeof(int) * (2 * (size_t)off[count] + 1))) != cudaSuccess)
             return cuda_err(msg, e, "batch buffers");
         if ((e = cudaMemcpy(bc->d_args, args.data(), sizeof(EvalArgs) * count, cudaMemcpyHostToDevice)) !=
                 cudaSuccess ||
@@ -3105,24 +3136,43 @@ rism_status batch_eval(std::vector<BatchItem>& items, const rism_options& o, cud
             return cuda_err(msg, e, "batch upload");
         if ((e = cudaStreamCreateWithFlags(&bc->cs, cudaStreamNonBlocking)) != cudaSuccess)
             return cuda_err(msg, e, "capture stream");
+        if ((e = cudaEventCreateWithFlags(&bc->fork, cudaEventDisableTiming)) != cudaSuccess)
+            return cuda_err(msg, e, "capture events");
+        for (int k = 0; k < BatchCache::kBranches; ++k)
+            if ((e = cudaStreamCreateWithFlags(&bc->side[k], cudaStreamNonBlocking)) != cudaSuccess ||
+                (e = cudaEventCreateWithFlags(&bc->join[k], cudaEventDisableTiming)) != cudaSuccess)
+                return cuda_err(msg, e, "capture streams");
         cudaStream_t cs = bc->cs;
         if ((e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal)) != cudaSuccess)
             return cuda_err(msg, e, "graph capture");
         rism_status r = RISM_OK;
+        // the solutes' preparations are independent: fork them over side streams (parallel graph branches)
+        const int nbr = std::min(count, (int)BatchCache::kBranches);
+        cudaEventRecord(bc->fork, cs);
+        for (int k = 0; k < nbr; ++k) cudaStreamWaitEvent(bc->side[k], bc->fork, 0);
         for (int b = 0; b < count && r == RISM_OK; ++b) {
             BatchItem& it = items[b];
+            cudaStream_t bs = bc->side[b % nbr];
             DevTables tt = *it.t;
             if (tt.n > 0) {
                 e = launch_setup(it.raw, tt.n, it.ph.S, tt.smax, it.sig_s, it.eps_s, it.lj_mode, it.lj_rcut, it.lj_tol,
-                                 it.g, tt, cs);
+                                 it.g, tt, bs);
                 if (e != cudaSuccess) r = cuda_err(msg, e, "setup");
             }
-            if (r == RISM_OK) r = tree_enqueue(it.tree, tt, it.g, it.ph, o, cs, msg);
-            if (r == RISM_OK) cp_enqueue(it.tree, args[b], it.o.h != nullptr, cs);
+            if (r == RISM_OK) r = tree_enqueue(it.tree, tt, it.g, it.ph, o, bs, msg);
+            if (r == RISM_OK) cp_enqueue(it.tree, args[b], it.o.h != nullptr, bs);
+        }
+        for (int k = 0; k < nbr; ++k) {
+            cudaEventRecord(bc->join[k], bc->side[k]);
+            cudaStreamWaitEvent(cs, bc->join[k], 0);
         }
         if (r == RISM_OK) {
             cudaMemsetAsync(bc->d_queue, 0, sizeof(int) * 2, cs);
-            BatchEval be{bc->d_args, bc->d_off, count, off[count], bc->d_queue};
+            for (int nr = 0; nr < 2; ++nr) {  // global heaviest-first orders over all (solute, batch) items
+                k_gather_work<<<count, 256, 0, cs>>>(bc->d_args, bc->d_off, count, nr, bc->d_work);
+                k_order<<<1, 1024, 0, cs>>>(off[count], bc->d_work, bc->d_order + (size_t)nr * off[count]);
+            }
+            BatchEval be{bc->d_args, bc->d_off, count, off[count], bc->d_queue, bc->d_order};
             const bool du = items[0].o.u != nullptr, dh = items[0].o.h != nullptr;
             e = dispatch(s0->smax ? s0->smax : items[0].t->smax, variant, 1, du, dh, nullptr, 0, &be, sm_count(), cs);
             if (e != cudaSuccess) r = cuda_err(msg, e, "batched eval");
