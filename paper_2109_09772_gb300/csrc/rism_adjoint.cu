@@ -26,6 +26,7 @@
 #include <cmath>
 
 #include "rism_adjoint.h"
+#include "rism_tree.h"
 
 namespace rism {
 namespace {
@@ -370,10 +371,10 @@ static rism_status aerr(std::string& err, cudaError_t e, const char* what) {
     return e == cudaErrorMemoryAllocation ? RISM_E_NOMEM : RISM_E_CUDA;
 }
 
-rism_status adjoint_run(AdjointState* s, const DevTables& t, const GridD& g, const Phys& ph, const rism_options& o,
-                        const double* raw_dev, const double* sig_s, const double* eps_s, const double* g_u,
-                        const double* g_c, const double* g_h, double* d_xyz, double* d_q, double* d_sigma,
-                        double* d_eps, cudaStream_t st, std::string& err) {
+rism_status adjoint_run(AdjointState* s, TreeState* tree, const DevTables& t, const GridD& g, const Phys& ph,
+                        const rism_options& o, const double* raw_dev, const double* sig_s, const double* eps_s,
+                        const double* g_u, const double* g_c, const double* g_h, double* d_xyz, double* d_q,
+                        double* d_sigma, double* d_eps, cudaStream_t st, std::string& err) {
     if (o.precision != RISM_PREC_FP32) {
         err = "the adjoint is implemented with FP32 pair terms (precision RISM_PREC_FP32)";
         return RISM_E_UNSUPPORTED;
@@ -423,9 +424,19 @@ rism_status adjoint_run(AdjointState* s, const DevTables& t, const GridD& g, con
     fa.part = s->part;
     fa.err = t.err;
     fa.wlim = o.wait_limit;
-    dim3 grid(ablocks, chunks);
-    if (g_h && ph.kappa > 0.0) k_adj_far<true><<<grid, kAT, 0, st>>>(fa);
-    else k_adj_far<false><<<grid, kAT, 0, st>>>(fa);
+    const bool dh = g_h && ph.kappa > 0.0;
+    bool tree_far = false;
+    if (tree && o.method == RISM_METHOD_TREECODE) {
+        rism_status r = tree_adjoint_far(tree, t, g, ph, o, s->w, dh, s->part, st, err, tree_far);
+        if (r != RISM_OK) return r;
+    }
+    if (tree_far) {
+        chunks = 1;  // one partial per atom, written in original atom order
+    } else {
+        dim3 grid(ablocks, chunks);
+        if (dh) k_adj_far<true><<<grid, kAT, 0, st>>>(fa);
+        else k_adj_far<false><<<grid, kAT, 0, st>>>(fa);
+    }
     NearAdjArgs na;
     na.g = g;
     na.ph = ph;

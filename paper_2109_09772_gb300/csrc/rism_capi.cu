@@ -492,8 +492,8 @@ rism_status rism_potential_backward(rism_ctx* c, const double* g_u, const double
     rism_status s = ensure_tables(c);
     if (s != RISM_OK) return s;
     if (g_h && !(c->ph.kappa > 0.0)) g_h = nullptr;  // h is identically zero without ions
-    s = adjoint_run(c->adj, c->t, c->gd, c->ph, c->o, c->d_raw, c->sigs, c->epss, g_u, g_c, g_h, d_xyz, d_q,
-                    d_sigma, d_eps, c->st, c->err);
+    s = adjoint_run(c->adj, c->tree, c->t, c->gd, c->ph, c->o, c->d_raw, c->sigs, c->epss, g_u, g_c, g_h, d_xyz,
+                    d_q, d_sigma, d_eps, c->st, c->err);
     if (s != RISM_OK) return s;
     return check_device_error(c);
 }

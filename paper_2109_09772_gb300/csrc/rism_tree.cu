@@ -2269,6 +2269,7 @@ cudaError_t dispatch(int smax, int v, int op, bool du, bool dh, const EvalArgs* 
 // ------------------------------------------------------------- state
 struct BatchCache;
 struct SoluteGraph;
+struct AdjTree;
 
 struct TreeState {
     int64_t cap_n = 0;
@@ -2309,6 +2310,7 @@ struct TreeState {
     int2* cp_ent = nullptr;
     float2 *tpot = nullptr, *tpart = nullptr;
     SoluteGraph* sg = nullptr;  // captured solute step (tree_graph_step)
+    AdjTree* adj = nullptr;     // reverse-mode far field over grid boxes (tree_adjoint_far)
     // short-range kernel tables
     float4* ntab = nullptr;
     double ntab_key[4] = {0.0, 0.0, 0.0, -1.0};
@@ -2747,8 +2749,11 @@ void tree_graph_reset(TreeState* s) {
     s->sg = nullptr;
 }
 
+void adjtree_delete(AdjTree* a);
+
 void tree_destroy(TreeState* s) {
     if (!s) return;
+    adjtree_delete(s->adj);
     delete s->sg;
     delete s->bc;
     for (int k = 0; k < 4; ++k)
@@ -3204,6 +3209,552 @@ rism_status batch_eval(std::vector<BatchItem>& items, const rism_options& o, cud
     if ((e = cudaGraphLaunch(bc->exec, st)) != cudaSuccess) return cuda_err(msg, e, "graph launch");
     (void)err;
     return RISM_OK;
+}
+
+
+// ---------------------------------------------------------------- reverse mode: far field over grid boxes
+// The far part of dL/dR_i and dL/dq_i is a field of the grid weights W(r) (A1 for 1/d, Ak for e^{-kappa d}/d)
+// evaluated, with its gradient, at the atoms: sum_r W(r) K(|r - R_i|).  Transposed to the forward pass, the grid
+// boxes become source clusters: a box's (n+1)^3 proxies carry the weights aggregated through its Lagrange basis,
+// Q_k = sum_r W(r) L_k(r) (exact level to level, a child's basis reproduces the parent's polynomials), and an
+// atom leaf sums Q_k K(|t_k - R_i|) for each box that meets the acceptance criterion, the grid points
+// themselves for the level-0 regions that do not.
+namespace {
+
+constexpr int kAL = 32;             // atoms per group of an octree leaf in the reverse far field
+constexpr int kADirect = 0x40000000; // entry flag: a level-0 region summed point by point
+
+struct AdjTreeMeta {
+    int overflow, need;
+};
+
+// Level-0 region -> the proxies of its lowest box with proxies: transposed separable interpolation.
+template <int N1>
+__global__ void __launch_bounds__(256) k_adj_qregion(TBoxes tb, const float4* __restrict__ w, float2* qpart,
+                                                     int* rlow) {
+    extern __shared__ __align__(16) unsigned char sm_raw[];
+    constexpr int M = kTB0, P3 = N1 * N1 * N1;
+    const int bi = blockIdx.x;
+    const int ib = bi % tb.nbx[0], jb = (bi / tb.nbx[0]) % tb.nby[0], kb = bi / (tb.nbx[0] * tb.nby[0]);
+    const TBox R = tbox_at(tb, 0, ib, jb, kb);
+    int la = -1;
+    TBox A = R;
+    for (int l = 0; l < tb.L; ++l) {
+        A = tbox_at(tb, l, ib >> l, jb >> l, kb >> l);
+        if (A.proxied) {
+            la = l;
+            break;
+        }
+    }
+    if (threadIdx.x == 0) rlow[bi] = la;
+    if (la < 0) return;
+    float2* V = reinterpret_cast<float2*>(sm_raw);  // [z][y][x]
+    float2* S1 = V + M * M * M;                     // [z][y][kx]
+    float2* S2 = S1 + M * M * N1;                   // [z][ky][kx]
+    float* W = reinterpret_cast<float*>(S2 + M * N1 * N1);
+    const int m0 = R.ext[0], m1 = R.ext[1], m2 = R.ext[2];
+    const int64_t plane = (int64_t)tb.ny * tb.nx;
+    for (int t = threadIdx.x; t < M * M * M; t += blockDim.x) {
+        const int ix = t % M, iy = (t / M) % M, iz = t / (M * M);
+        float2 v = make_float2(0.f, 0.f);
+        if (ix < m0 && iy < m1 && iz < m2) {
+            const float4 q = w[(R.lo[2] + iz) * plane + (int64_t)(R.lo[1] + iy) * tb.nx + R.lo[0] + ix];
+            v = make_float2(q.x, q.y);
+        }
+        V[t] = v;
+    }
+    const int ms[3] = {m0, m1, m2};
+    for (int d = 0; d < 3; ++d) {
+        const float off = (float)(R.lo[d] - A.c[d]);
+        basis_rows<N1>(tb, A, d, ms[d], M, [&](int i) { return off + (float)i; }, W + d * M * N1);
+    }
+    __syncthreads();
+    const float *Wx = W, *Wy = W + M * N1, *Wz = W + 2 * M * N1;
+    for (int t = threadIdx.x; t < M * M * N1; t += blockDim.x) {
+        const int kx = t % N1, yz = t / N1;  // yz = z M + y
+        float ax = 0.f, ay = 0.f;
+#pragma unroll 4
+        for (int x = 0; x < M; ++x) {
+            const float wv = Wx[x * N1 + kx];
+            const float2 v = V[yz * M + x];
+            ax = fmaf(wv, v.x, ax);
+            ay = fmaf(wv, v.y, ay);
+        }
+        S1[t] = make_float2(ax, ay);
+    }
+    __syncthreads();
+    for (int t = threadIdx.x; t < M * N1 * N1; t += blockDim.x) {
+        const int kx = t % N1, ky = (t / N1) % N1, z = t / (N1 * N1);
+        float ax = 0.f, ay = 0.f;
+#pragma unroll 4
+        for (int y = 0; y < M; ++y) {
+            const float wv = Wy[y * N1 + ky];
+            const float2 v = S1[(z * M + y) * N1 + kx];
+            ax = fmaf(wv, v.x, ax);
+            ay = fmaf(wv, v.y, ay);
+        }
+        S2[t] = make_float2(ax, ay);
+    }
+    __syncthreads();
+    float2* out = qpart + (int64_t)bi * P3;
+    for (int t = threadIdx.x; t < P3; t += blockDim.x) {
+        const int kx = t % N1, ky = (t / N1) % N1, kz = t / (N1 * N1);
+        float ax = 0.f, ay = 0.f;
+#pragma unroll 4
+        for (int z = 0; z < M; ++z) {
+            const float wv = Wz[z * N1 + kz];
+            const float2 v = S2[(z * N1 + ky) * N1 + kx];
+            ax = fmaf(wv, v.x, ax);
+            ay = fmaf(wv, v.y, ay);
+        }
+        out[t] = make_float2(ax, ay);
+    }
+}
+
+// Proxies of the boxes of level l: the regions whose lowest box with proxies this is, plus the transposed
+// level-to-level interpolation of every child with proxies (computed by the previous launch).  Fixed order.
+template <int N1>
+__global__ void __launch_bounds__(256) k_adj_qagg(TBoxes tb, int l, const float2* __restrict__ qpart,
+                                                  const int* __restrict__ rlow, float2* qtot) {
+    extern __shared__ __align__(16) unsigned char sm_raw[];
+    constexpr int P3 = N1 * N1 * N1;
+    const int bi = blockIdx.x;
+    const int ib = bi % tb.nbx[l], jb = (bi / tb.nbx[l]) % tb.nby[l], kb = bi / (tb.nbx[l] * tb.nby[l]);
+    const TBox A = tbox_at(tb, l, ib, jb, kb);
+    if (!A.proxied) return;
+    float2* acc = reinterpret_cast<float2*>(sm_raw);  // [P3]
+    float2* V = acc + P3;                             // child proxies
+    float2* S1 = V + P3;
+    float2* S2 = S1 + P3;
+    float* W = reinterpret_cast<float*>(S2 + P3);      // [3][N1][N1]
+    for (int k = threadIdx.x; k < P3; k += blockDim.x) acc[k] = make_float2(0.f, 0.f);
+    const int sp = 1 << l;
+    const int r0x = ib * sp, r0y = jb * sp, r0z = kb * sp;
+    const int r1x = min(r0x + sp, tb.nbx[0]), r1y = min(r0y + sp, tb.nby[0]), r1z = min(r0z + sp, tb.nbz[0]);
+    for (int rz = r0z; rz < r1z; ++rz)
+        for (int ry = r0y; ry < r1y; ++ry)
+            for (int rx = r0x; rx < r1x; ++rx) {
+                const int rb = (rz * tb.nby[0] + ry) * tb.nbx[0] + rx;
+                if (rlow[rb] != l) continue;
+                const float2* src = qpart + (int64_t)rb * P3;
+                for (int k = threadIdx.x; k < P3; k += blockDim.x) {
+                    const float2 v = src[k];
+                    acc[k].x += v.x;
+                    acc[k].y += v.y;
+                }
+            }
+    __syncthreads();
+    if (l > 0) {
+        for (int c = 0; c < 8; ++c) {
+            const int cx = 2 * ib + (c & 1), cy = 2 * jb + ((c >> 1) & 1), cz = 2 * kb + (c >> 2);
+            if (cx >= tb.nbx[l - 1] || cy >= tb.nby[l - 1] || cz >= tb.nbz[l - 1]) continue;
+            const TBox C = tbox_at(tb, l - 1, cx, cy, cz);
+            if (!C.proxied) continue;
+            const float2* src = qtot + (int64_t)tbox_index(tb, l - 1, cx, cy, cz) * P3;
+            for (int k = threadIdx.x; k < P3; k += blockDim.x) V[k] = src[k];
+            for (int d = 0; d < 3; ++d) {
+                const float off = (float)(C.c[d] - A.c[d]), hd = 0.5f * (C.ext[d] - 1);
+                basis_rows<N1>(tb, A, d, N1, N1, [&](int i) { return off + hd * tb.ck[i]; }, W + d * N1 * N1);
+            }
+            __syncthreads();
+            const float *Wx = W, *Wy = W + N1 * N1, *Wz = W + 2 * N1 * N1;
+            for (int t = threadIdx.x; t < P3; t += blockDim.x) {  // contract the child's x index
+                const int kx = t % N1, yz = t / N1;
+                float ax = 0.f, ay = 0.f;
+#pragma unroll
+                for (int j = 0; j < N1; ++j) {
+                    const float wv = Wx[j * N1 + kx];
+                    const float2 v = V[yz * N1 + j];
+                    ax = fmaf(wv, v.x, ax);
+                    ay = fmaf(wv, v.y, ay);
+                }
+                S1[t] = make_float2(ax, ay);
+            }
+            __syncthreads();
+            for (int t = threadIdx.x; t < P3; t += blockDim.x) {  // the child's y index
+                const int kx = t % N1, ky = (t / N1) % N1, z = t / (N1 * N1);
+                float ax = 0.f, ay = 0.f;
+#pragma unroll
+                for (int j = 0; j < N1; ++j) {
+                    const float wv = Wy[j * N1 + ky];
+                    const float2 v = S1[(z * N1 + j) * N1 + kx];
+                    ax = fmaf(wv, v.x, ax);
+                    ay = fmaf(wv, v.y, ay);
+                }
+                S2[t] = make_float2(ax, ay);
+            }
+            __syncthreads();
+            for (int t = threadIdx.x; t < P3; t += blockDim.x) {  // the child's z index
+                const int kx = t % N1, ky = (t / N1) % N1, kz = t / (N1 * N1);
+                float ax = 0.f, ay = 0.f;
+#pragma unroll
+                for (int j = 0; j < N1; ++j) {
+                    const float wv = Wz[j * N1 + kz];
+                    const float2 v = S2[(j * N1 + ky) * N1 + kx];
+                    ax = fmaf(wv, v.x, ax);
+                    ay = fmaf(wv, v.y, ay);
+                }
+                acc[t].x += ax;
+                acc[t].y += ay;
+            }
+            __syncthreads();
+        }
+    }
+    float2* dst = qtot + (int64_t)(tb.off[l] + bi) * P3;
+    for (int k = threadIdx.x; k < P3; k += blockDim.x) dst[k] = acc[k];
+}
+
+// Octree leaves in node order (one CTA): leaf_ids[0 .. count).
+__global__ void __launch_bounds__(1024) k_leaf_list(const TreeMeta* meta, const Node* __restrict__ nodes,
+                                                    int* leaf_ids, int* count) {
+    __shared__ int tmp[64];
+    __shared__ int base;
+    if (threadIdx.x == 0) base = 0;
+    __syncthreads();
+    const int nn = meta->nnodes;
+    for (int b0 = 0; b0 < nn; b0 += blockDim.x) {
+        const int nid = b0 + threadIdx.x;
+        const int f = (nid < nn && nodes[nid].first_child < 0) ? 1 : 0;
+        int tot;
+        const int off = block_exclusive_scan(f, tmp, tot);
+        if (f) leaf_ids[base + off] = nid;
+        __syncthreads();
+        if (threadIdx.x == 0) base += tot;
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) *count = base;
+}
+
+// Interaction lists of the atom leaves (one warp per leaf): the grid-box hierarchy from the top; a box with
+// proxies that meets (r_leaf + r_box)/R < theta is accepted, another box is opened, a level-0 region that is
+// not accepted is summed point by point.  Order: frontier round, then lane -- deterministic.
+__global__ void __launch_bounds__(32 * kListWarps) k_adj_lists(TBoxes tb, const Node* __restrict__ nodes,
+                                                              const int* __restrict__ leaf_ids,
+                                                              const int* __restrict__ nleaf_p, float theta, int cap,
+                                                              int* cnt, int* ent, AdjTreeMeta* meta) {
+    __shared__ int qa[kListWarps][kQCap], qb[kListWarps][kQCap];
+    const int lane = threadIdx.x & 31, wv = threadIdx.x >> 5;
+    const int nleaf = *nleaf_p;
+    const float th2 = theta * theta;
+    for (int leaf = blockIdx.x * kListWarps + wv; leaf < nleaf; leaf += gridDim.x * kListWarps) {
+        const Node nd = nodes[leaf_ids[leaf]];
+        float c[3], r2 = 0.f;
+        for (int d = 0; d < 3; ++d) {
+            c[d] = 0.5f * (nd.lo[d] + nd.hi[d]);
+            r2 += 0.25f * (nd.hi[d] - nd.lo[d]) * (nd.hi[d] - nd.lo[d]);
+        }
+        const float rl = sqrtf(r2) + 0.01f;  // slack for the low parts of the positions
+        int* cur = qa[wv];
+        int* nxt = qb[wv];
+        const int Lt = tb.L - 1;
+        const int ntop = tb.nbx[Lt] * tb.nby[Lt] * tb.nbz[Lt];
+        bool ovf = ntop > kQCap;
+        for (int k = lane; k < min(ntop, kQCap); k += 32) cur[k] = tb.off[Lt] + k;
+        __syncwarp();
+        int ncur = min(ntop, kQCap), m = 0;
+        int* out = ent + (int64_t)leaf * cap;
+        while (ncur > 0 && !__any_sync(0xffffffffu, ovf)) {
+            int nnext = 0;
+            for (int c0 = 0; c0 < ncur; c0 += 32) {
+                const int k = c0 + lane;
+                int kind = 0, e = 0, nch = 0;
+                int chl = 0, cx0 = 0, cy0 = 0, cz0 = 0;
+                if (k < ncur) {
+                    const TBox T = tbox_flat(tb, cur[k]);
+                    float R2 = 0.f;
+                    for (int d = 0; d < 3; ++d) R2 += (c[d] - (float)T.c[d]) * (c[d] - (float)T.c[d]);
+                    const float rs = rl + (float)T.r;
+                    if (T.proxied && rs * rs < th2 * R2) {
+                        kind = 1;
+                        e = cur[k];
+                    } else if (T.l > 0) {
+                        kind = 2;
+                        chl = T.l - 1;
+                        cx0 = 2 * T.ib;
+                        cy0 = 2 * T.jb;
+                        cz0 = 2 * T.kb;
+                        nch = 0;
+                        for (int q = 0; q < 8; ++q)
+                            nch += (cx0 + (q & 1) < tb.nbx[chl] && cy0 + ((q >> 1) & 1) < tb.nby[chl] &&
+                                    cz0 + (q >> 2) < tb.nbz[chl]);
+                    } else {
+                        kind = 1;
+                        e = cur[k] | kADirect;
+                    }
+                }
+                const unsigned em = __ballot_sync(0xffffffffu, kind == 1);
+                if (kind == 1) {
+                    const int pos = m + __popc(em & ((1u << lane) - 1u));
+                    if (pos < cap) out[pos] = e;
+                }
+                m += __popc(em);
+                int x = nch;
+                for (int o = 1; o < 32; o <<= 1) {
+                    const int y = __shfl_up_sync(0xffffffffu, x, o);
+                    if (lane >= o) x += y;
+                }
+                const int tot = __shfl_sync(0xffffffffu, x, 31);
+                int at = nnext + x - nch;
+                if (kind == 2) {
+                    for (int q = 0; q < 8; ++q) {
+                        const int cx = cx0 + (q & 1), cy = cy0 + ((q >> 1) & 1), cz = cz0 + (q >> 2);
+                        if (cx >= tb.nbx[chl] || cy >= tb.nby[chl] || cz >= tb.nbz[chl]) continue;
+                        if (at < kQCap) nxt[at] = tbox_index(tb, chl, cx, cy, cz);
+                        else ovf = true;
+                        ++at;
+                    }
+                }
+                nnext += tot;
+            }
+            __syncwarp();
+            int* tq = cur;
+            cur = nxt;
+            nxt = tq;
+            ncur = min(nnext, kQCap);
+            if (nnext > kQCap) ovf = true;
+            __syncwarp();
+        }
+        const bool wide = __any_sync(0xffffffffu, ovf);
+        if (lane == 0) {
+            cnt[leaf] = min(m, cap);
+            if (wide || m > cap) {
+                meta->overflow = 1;
+                atomicMax(&meta->need, wide ? (1 << 30) : m);
+            }
+        }
+    }
+}
+
+constexpr int kADThreads = 128;  // 4 threads per atom of a leaf
+constexpr int kADSub = kADThreads / kAL;
+
+// One pair of the reverse far field: potential and radial factor of W1/d + Wk e^{-kappa d}/d.
+template <bool DH>
+__device__ __forceinline__ void adj_pair(float dx, float dy, float dz, float w1, float wk, float kap2, float kapg,
+                                         float& pq, float& px, float& py, float& pz) {
+    const float d2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+    const float rr = rsqrt_approx(d2);
+    const float ri = d2 > 0.f ? rr : 0.f;  // a grid point on the atom: no term (d = 0 has no gradient)
+    float t1 = w1 * ri, tg = t1;
+    if (DH) {
+        const float d = d2 * ri;
+        const float tk = wk * ri * ex2_approx(kap2 * d);
+        t1 += tk;
+        tg = fmaf(tk, kapg * d, t1);
+    }
+    pq += t1;
+    const float rad = tg * ri * ri;
+    px = fmaf(dx, rad, px);
+    py = fmaf(dy, rad, py);
+    pz = fmaf(dz, rad, pz);
+}
+
+// One group of up to kAL atoms of a leaf (kADSub threads per atom, consecutive lanes) against the leaf's list.
+template <bool DH>
+__device__ void adj_leaf_group(const TBoxes& tb, const SrcF* __restrict__ ssrcf, const uint32_t* __restrict__ idx,
+                               const float4* __restrict__ w, const float2* __restrict__ qtot,
+                               const int* __restrict__ cnt, const int* __restrict__ ent, int cap, float kap2,
+                               float kapg, double* part, float2* Q, int leaf, int j, bool act, int tid, int sub) {
+    const SrcF sf = act ? ssrcf[j] : SrcF{0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+    const int n1 = tb.deg + 1, P3 = tb.P3;
+    float h[4] = {0.f, 0.f, 0.f, 0.f}, lo4[4] = {0.f, 0.f, 0.f, 0.f};
+    const int ne = cnt[leaf];
+    const int64_t plane = (int64_t)tb.ny * tb.nx;
+    for (int e = 0; e < ne; ++e) {
+        const int code = ent[(int64_t)leaf * cap + e];
+        float pq = 0.f, px = 0.f, py = 0.f, pz = 0.f;
+        if (!(code & kADirect)) {
+            const TBox T = tbox_flat(tb, code);
+            __syncthreads();
+            const float2* src = qtot + (int64_t)code * P3;
+            for (int k = tid; k < P3; k += kADThreads) Q[k] = src[k];
+            __syncthreads();
+            // atom relative to the box centre; proxy k at (hx ck[kx], hy ck[ky], hz ck[kz])
+            const float ax = (sf.xh - (float)T.c[0]) + sf.xl, ay = (sf.yh - (float)T.c[1]) + sf.yl,
+                        az = (sf.zh - (float)T.c[2]) + sf.zl;
+            const float hx = 0.5f * (T.ext[0] - 1), hy = 0.5f * (T.ext[1] - 1), hz = 0.5f * (T.ext[2] - 1);
+            for (int k = sub; k < P3; k += kADSub) {
+                const int kx = k % n1, ky = (k / n1) % n1, kz = k / (n1 * n1);
+                const float2 q = Q[k];
+                adj_pair<DH>(hx * tb.ck[kx] - ax, hy * tb.ck[ky] - ay, hz * tb.ck[kz] - az, q.x, q.y, kap2, kapg,
+                             pq, px, py, pz);
+            }
+        } else {
+            const TBox R = tbox_flat(tb, code & ~kADirect);
+            const int m0 = R.ext[0], m1 = R.ext[1], npt = m0 * m1 * R.ext[2];
+            for (int p = sub; p < npt; p += kADSub) {
+                const int ix = p % m0, iy = (p / m0) % m1, iz = p / (m0 * m1);
+                const int gx = R.lo[0] + ix, gy = R.lo[1] + iy, gz = R.lo[2] + iz;
+                const float4 wv = w[gz * plane + (int64_t)gy * tb.nx + gx];
+                // lattice point minus the atom: exact first subtraction for nearby atoms
+                adj_pair<DH>(((float)gx - sf.xh) - sf.xl, ((float)gy - sf.yh) - sf.yl, ((float)gz - sf.zh) - sf.zl,
+                             wv.x, wv.y, kap2, kapg, pq, px, py, pz);
+            }
+        }
+        ff_add(h[0], lo4[0], pq);
+        ff_add(h[1], lo4[1], px);
+        ff_add(h[2], lo4[2], py);
+        ff_add(h[3], lo4[3], pz);
+    }
+    // the kADSub threads of an atom are consecutive lanes: combine them in a fixed order
+    double v[4];
+    for (int q = 0; q < 4; ++q) {
+        v[q] = (double)h[q] + (double)lo4[q];
+        for (int o = 1; o < kADSub; o <<= 1) v[q] += __shfl_xor_sync(0xffffffffu, v[q], o);
+    }
+    if (act && sub == 0) {
+        double* o = part + (int64_t)idx[j] * 4;
+        for (int q = 0; q < 4; ++q) o[q] = v[q];
+    }
+}
+
+template <bool DH>
+__global__ void __launch_bounds__(kADThreads) k_adj_treefar(TBoxes tb, const SrcF* __restrict__ ssrcf,
+                                                           const uint32_t* __restrict__ idx,
+                                                           const Node* __restrict__ nodes,
+                                                           const int* __restrict__ leaf_ids,
+                                                           const int* __restrict__ nleaf_p,
+                                                           const float4* __restrict__ w,
+                                                           const float2* __restrict__ qtot, const int* __restrict__ cnt,
+                                                           const int* __restrict__ ent, int cap, float kap2,
+                                                           float kapg, const AdjTreeMeta* meta, double* part) {
+    extern __shared__ __align__(16) unsigned char sm_raw[];
+    float2* Q = reinterpret_cast<float2*>(sm_raw);  // one box's proxies
+    if (meta->overflow || blockIdx.x >= *nleaf_p) return;
+    const int leaf = blockIdx.x, tid = threadIdx.x, a = tid / kADSub, sub = tid % kADSub;
+    const Node nd = nodes[leaf_ids[leaf]];
+    for (int g0 = nd.begin; g0 < nd.end; g0 += kAL)  // groups of kAL atoms of the leaf
+        adj_leaf_group<DH>(tb, ssrcf, idx, w, qtot, cnt, ent, cap, kap2, kapg, part, Q, leaf, g0 + a, g0 + a < nd.end,
+                           tid, sub);
+}
+
+template <int N1>
+void launch_adj_q(const TBoxes& tb, const float4* w, float2* qpart, int* rlow, float2* qtot, cudaStream_t st) {
+    constexpr int M = kTB0, P3 = N1 * N1 * N1;
+    const size_t sr = sizeof(float2) * (M * M * M + M * M * N1 + M * N1 * N1) + sizeof(float) * 3 * M * N1;
+    const size_t sa = sizeof(float2) * 4 * P3 + sizeof(float) * 3 * N1 * N1;
+    cudaFuncSetAttribute(k_adj_qregion<N1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sr);
+    cudaFuncSetAttribute(k_adj_qagg<N1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sa);
+    k_adj_qregion<N1><<<tb.nbx[0] * tb.nby[0] * tb.nbz[0], 256, sr, st>>>(tb, w, qpart, rlow);
+    for (int l = 0; l < tb.L; ++l)
+        k_adj_qagg<N1><<<tb.nbx[l] * tb.nby[l] * tb.nbz[l], 256, sa, st>>>(tb, l, qpart, rlow, qtot);
+}
+
+void launch_adj_q_deg(const TBoxes& tb, const float4* w, float2* qpart, int* rlow, float2* qtot, cudaStream_t st) {
+    switch (tb.deg) {
+        case 1: return launch_adj_q<2>(tb, w, qpart, rlow, qtot, st);
+        case 2: return launch_adj_q<3>(tb, w, qpart, rlow, qtot, st);
+        case 3: return launch_adj_q<4>(tb, w, qpart, rlow, qtot, st);
+        case 4: return launch_adj_q<5>(tb, w, qpart, rlow, qtot, st);
+        case 5: return launch_adj_q<6>(tb, w, qpart, rlow, qtot, st);
+        case 6: return launch_adj_q<7>(tb, w, qpart, rlow, qtot, st);
+        case 7: return launch_adj_q<8>(tb, w, qpart, rlow, qtot, st);
+        case 8: return launch_adj_q<9>(tb, w, qpart, rlow, qtot, st);
+        case 9: return launch_adj_q<10>(tb, w, qpart, rlow, qtot, st);
+        case 10: return launch_adj_q<11>(tb, w, qpart, rlow, qtot, st);
+        case 11: return launch_adj_q<12>(tb, w, qpart, rlow, qtot, st);
+        default: return launch_adj_q<13>(tb, w, qpart, rlow, qtot, st);
+    }
+}
+
+}  // namespace
+
+struct AdjTree {
+    float2 *qpart = nullptr, *qtot = nullptr;
+    int* rlow = nullptr;
+    int *leaf_ids = nullptr, *nleaf = nullptr;
+    int64_t cap_leaf_ids = 0;
+    int64_t cap_qpart = 0, cap_qtot = 0, cap_rlow = 0;
+    int *cnt = nullptr, *ent = nullptr;
+    int cap = 256, cap_leaf = 0;
+    int64_t cap_ent = 0;
+    AdjTreeMeta *meta = nullptr, *h_meta = nullptr;
+    ~AdjTree() {
+        cudaFree(qpart);
+        cudaFree(qtot);
+        cudaFree(rlow);
+        cudaFree(leaf_ids);
+        cudaFree(nleaf);
+        cudaFree(cnt);
+        cudaFree(ent);
+        cudaFree(meta);
+        cudaFreeHost(h_meta);
+    }
+};
+
+void adjtree_delete(AdjTree* a) { delete a; }
+
+rism_status tree_adjoint_far(TreeState* s, const DevTables& t, const GridD& g, const Phys& ph, const rism_options& o,
+                             const float4* w, bool dh, double* part, cudaStream_t st, std::string& err, bool& used) {
+    used = false;
+    const TBoxes& tb = s->tb;
+    const int n = (int)t.n;
+    if (!tb.enabled || !s->prepared || n == 0) return RISM_OK;
+    if (!s->adj) s->adj = new AdjTree();
+    AdjTree& A = *s->adj;
+    cudaError_t e;
+    const int nb0 = tb.nbx[0] * tb.nby[0] * tb.nbz[0];
+    const int nleaf = s->max_nodes;  // upper bound of the octree leaves (their count stays on the device)
+    auto grow = [&](auto*& p, int64_t& cap, int64_t need) -> cudaError_t {
+        if (need <= cap) return cudaSuccess;
+        cudaFree(p);
+        p = nullptr;
+        cap = 0;
+        cudaError_t r = cudaMalloc(&p, sizeof(*p) * (size_t)need);
+        if (r == cudaSuccess) cap = need;
+        return r;
+    };
+    if ((e = grow(A.qpart, A.cap_qpart, (int64_t)nb0 * tb.P3)) != cudaSuccess ||
+        (e = grow(A.qtot, A.cap_qtot, (int64_t)tb.nbox * tb.P3)) != cudaSuccess ||
+        (e = grow(A.rlow, A.cap_rlow, (int64_t)nb0)) != cudaSuccess)
+        return cuda_err(err, e, "reverse-mode box buffers");
+    if (!A.meta) {
+        if ((e = cudaMalloc(&A.meta, sizeof(AdjTreeMeta))) != cudaSuccess ||
+            (e = cudaMallocHost(&A.h_meta, sizeof(AdjTreeMeta))) != cudaSuccess ||
+            (e = cudaMalloc(&A.nleaf, sizeof(int))) != cudaSuccess)
+            return cuda_err(err, e, "reverse-mode meta");
+    }
+    if ((e = grow(A.leaf_ids, A.cap_leaf_ids, (int64_t)nleaf + 1)) != cudaSuccess)
+        return cuda_err(err, e, "reverse-mode leaves");
+    k_leaf_list<<<1, 1024, 0, st>>>(s->meta, s->nodes, A.leaf_ids, A.nleaf);
+    launch_adj_q_deg(tb, w, A.qpart, A.rlow, A.qtot, st);
+    const size_t sq = sizeof(float2) * tb.P3;
+    for (int attempt = 0; attempt < 4; ++attempt) {
+        if (nleaf + 1 > A.cap_leaf) {
+            cudaFree(A.cnt);
+            A.cnt = nullptr;
+            if ((e = cudaMalloc(&A.cnt, sizeof(int) * (nleaf + 1))) != cudaSuccess) return cuda_err(err, e, "lists");
+            A.cap_leaf = nleaf + 1;
+        }
+        if ((e = grow(A.ent, A.cap_ent, (int64_t)nleaf * A.cap)) != cudaSuccess) return cuda_err(err, e, "lists");
+        cudaMemsetAsync(A.meta, 0, sizeof(AdjTreeMeta), st);
+        k_adj_lists<<<(nleaf + kListWarps - 1) / kListWarps, 32 * kListWarps, 0, st>>>(
+            tb, s->nodes, A.leaf_ids, A.nleaf, (float)o.theta, A.cap, A.cnt, A.ent, A.meta);
+        const float kap2 = (float)(-ph.kappa * g.h * 1.4426950408889634), kapg = (float)(ph.kappa * g.h);
+        if (dh)
+            k_adj_treefar<true><<<nleaf, kADThreads, sq, st>>>(tb, s->srcf, s->idx, s->nodes, A.leaf_ids, A.nleaf, w,
+                                                               A.qtot, A.cnt, A.ent, A.cap, kap2, kapg, A.meta, part);
+        else
+            k_adj_treefar<false><<<nleaf, kADThreads, sq, st>>>(tb, s->srcf, s->idx, s->nodes, A.leaf_ids, A.nleaf,
+                                                                w, A.qtot, A.cnt, A.ent, A.cap, kap2, kapg, A.meta,
+                                                                part);
+        if ((e = cudaMemcpyAsync(A.h_meta, A.meta, sizeof(AdjTreeMeta), cudaMemcpyDeviceToHost, st)) != cudaSuccess ||
+            (e = cudaStreamSynchronize(st)) != cudaSuccess)
+            return cuda_err(err, e, "reverse-mode lists");
+        if (!A.h_meta->overflow) {
+            used = true;
+            return RISM_OK;
+        }
+        if (A.h_meta->need >= (1 << 30)) {
+            err = "a reverse-mode traversal frontier exceeded 2048 boxes";
+            return RISM_E_NOMEM;
+        }
+        int p2 = 1;
+        while (p2 < A.h_meta->need) p2 <<= 1;
+        A.cap = p2;
+    }
+    err = "reverse-mode list slots kept growing";
+    return RISM_E_NOMEM;
 }
 
 }  // namespace rism

@@ -59,6 +59,13 @@ rism_status tree_graph_step(TreeState* ts, const DevTables& t, const GridD& g, c
 // Drop the captured solute graph (buffers moved or the retry path ran).
 void tree_graph_reset(TreeState* ts);
 
+// Reverse mode, far part, with the grid boxes as source clusters: w holds the per-point weights (A1 of 1/d,
+// Ak of e^{-kappa d}/d in .x, .y); part receives per atom (original order) dq, Gx, Gy, Gz in grid units, as
+// one chunk of the direct far kernel would.  used = false (nothing done) when target boxes are off or the tree
+// is not prepared for the current solute.  Synchronises the stream (list growth).
+rism_status tree_adjoint_far(TreeState* ts, const DevTables& t, const GridD& g, const Phys& ph, const rism_options& o,
+                             const float4* w, bool dh, double* part, cudaStream_t st, std::string& err, bool& used);
+
 // Many solutes in one persistent, graph-captured launch sequence.
 // The whole sequence (per-solute setup and tree kernels, persistent far and
 // near kernels) is captured in a CUDA graph and replayed while unchanged.
