@@ -37,15 +37,24 @@ constexpr int kRowT = 64;    // grid points per shared-memory tile (a row segmen
 constexpr int kNearT = 256;  // threads per near-adjoint CTA
 
 __global__ void k_adj_weights(int64_t M, int S, const double* __restrict__ gu, const double* __restrict__ gc,
-                              const double* __restrict__ gh, Phys ph, float4* w) {
+                              const double* __restrict__ gh, Phys ph, float4* w, float4* gu4) {
     const double c1 = ph.k_e, cc = -ph.beta * ph.k_e, chh = -ph.beta * ph.k_e / (2.0 * ph.eps_r);
     for (int64_t f = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; f < M; f += (int64_t)gridDim.x * blockDim.x) {
         double a = 0.0, b = 0.0, h = 0.0;
+        float g8[kMaxSites] = {};
         for (int s = 0; s < S; ++s) {
             const double qs = ph.qs[s];
-            if (gu) a += qs * gu[s * M + f];
+            if (gu) {
+                const double v = gu[s * M + f];
+                a += qs * v;
+                g8[s] = (float)v;
+            }
             if (gc) b += qs * gc[s * M + f];
             if (gh) h += qs * gh[s * M + f];
+        }
+        if (gu) {
+            gu4[f] = make_float4(g8[0], g8[1], g8[2], g8[3]);
+            if (S > 4) gu4[M + f] = make_float4(g8[4], g8[5], g8[6], g8[7]);
         }
         const double W1 = c1 * a, Wc = cc * b, Wh = chh * h;
         w[f] = make_float4((float)(W1 + Wc), (float)(2.0 * ph.ea2 * Wh), (float)Wc, (float)Wh);
@@ -185,7 +194,8 @@ struct NearAdjArgs {
     const SrcF* srcf;
     const LJf* ljf;          // [n][smax] grid units
     const float4* w;
-    const double* gu;        // [S][M] (nullable)
+    const float4* gu4;       // [ceil(S/4)][M]: G_u of the sites in FP32, four per record (nullable)
+    const uint32_t* order;   // CTA -> atom (Morton order from the tree, for cache reuse); null: identity
     double sig_s[kMaxSites], eps_s[kMaxSites];
     double rnear;            // max cut-off / r_short (A); infinite = whole grid
     double* out;             // [n][6]: dq, Gx, Gy, Gz (grid units as in the far part), dLJ/dR (3), ...
@@ -208,8 +218,8 @@ __device__ __forceinline__ double block_sum(double v, double* red) {
 // factor sum G_u,s dLJ/dd / d (-> dR), dLJ/dsigma_i and dLJ/deps_i.
 __global__ void __launch_bounds__(kNearT) k_adj_near(NearAdjArgs a) {
     __shared__ double red[kNearT / 32];
-    const int i = blockIdx.x;
-    if (i >= a.n) return;
+    if ((int)blockIdx.x >= a.n) return;
+    const int i = a.order ? (int)a.order[blockIdx.x] : (int)blockIdx.x;
     const GridD& g = a.g;
     const int64_t M = (int64_t)g.nx * g.ny * g.nz;
     const SrcF sf = a.srcf[i];
@@ -245,12 +255,14 @@ __global__ void __launch_bounds__(kNearT) k_adj_near(NearAdjArgs a) {
         }
     }
     const int bx = hi[0] - lo[0] + 1, by = hi[1] - lo[1] + 1, bz = hi[2] - lo[2] + 1;
-    const int64_t nbox = (bx > 0 && by > 0 && bz > 0) ? (int64_t)bx * by * bz : 0;
+    const int nplane = (bx > 0 && by > 0 && bz > 0) ? bx * by : 0;
     float acc[9] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};  // dq, Gx, Gy, Gz, LJx, LJy, LJz, dsig, deps
     float hi9[9] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f}, lo9[9] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
     int cntp = 0;
-    for (int64_t b = threadIdx.x; b < nbox; b += blockDim.x) {
-        const int ii = lo[0] + (int)(b % bx), jj = lo[1] + (int)((b / bx) % by), kk = lo[2] + (int)(b / ((int64_t)bx * by));
+    // threads over the (x, y) plane of the box (one 32-bit division each), z innermost
+    for (int b = threadIdx.x; b < nplane; b += blockDim.x)
+    for (int kk = lo[2]; kk <= hi[2]; ++kk) {
+        const int ii = lo[0] + b % bx, jj = lo[1] + b / bx;
         const float dx = ((float)ii - sf.xh) - sf.xl, dy = ((float)jj - sf.yh) - sf.yl, dz = ((float)kk - sf.zh) - sf.zl;
         const float d2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
         if (d2 >= rn2 || d2 == 0.f) continue;
@@ -281,13 +293,16 @@ __global__ void __launch_bounds__(kNearT) k_adj_near(NearAdjArgs a) {
         acc[1] = fmaf(dx, rad, acc[1]);
         acc[2] = fmaf(dy, rad, acc[2]);
         acc[3] = fmaf(dz, rad, acc[3]);
-        if (a.gu) {
+        if (a.gu4) {
             const float r2i = rcp_approx(d2);
             const float r6 = r2i * r2i * r2i, r12 = r6 * r6;
             float lrad = 0.f, ds = 0.f, de = 0.f;
+            float4 g4 = a.gu4[f];
             for (int s = 0; s < a.S; ++s) {
+                if (s == 4) g4 = a.gu4[M + f];
+                const int c4 = s & 3;
+                const float G = c4 == 0 ? g4.x : (c4 == 1 ? g4.y : (c4 == 2 ? g4.z : g4.w));
                 if (!(d2 < Rc[s])) continue;
-                const float G = (float)a.gu[s * M + f];
                 const float A12 = Ls[s] * r12, B6 = Bs[s] * r6;
                 lrad = fmaf(G, (-12.f * A12 + 6.f * B6) * r2i, lrad);  // dLJ/dd / d, grid units
                 ds = fmaf(G * isg[s], 12.f * A12 - 6.f * B6, ds);
@@ -350,6 +365,8 @@ __global__ void k_adj_final(FinalArgs a) {
 struct AdjointState {
     float4* w = nullptr;
     int64_t cap_w = 0;
+    float4* gu4 = nullptr;
+    int64_t cap_gu4 = 0;
     double* part = nullptr;
     int64_t cap_part = 0;
     double* near = nullptr;
@@ -361,6 +378,7 @@ AdjointState* adjoint_create() { return new AdjointState(); }
 void adjoint_destroy(AdjointState* s) {
     if (!s) return;
     cudaFree(s->w);
+    cudaFree(s->gu4);
     cudaFree(s->part);
     cudaFree(s->near);
     delete s;
@@ -408,7 +426,14 @@ rism_status adjoint_run(AdjointState* s, TreeState* tree, const DevTables& t, co
         if ((e = cudaMalloc(&s->near, sizeof(double) * 9 * n)) != cudaSuccess) return aerr(err, e, "adjoint near");
         s->cap_near = (int64_t)n * 9;
     }
-    k_adj_weights<<<4 * 152, 256, 0, st>>>(M, ph.S, g_u, g_c, g_h, ph, s->w);
+    const int64_t need_gu4 = g_u ? M * ((ph.S + 3) / 4) : 0;
+    if (need_gu4 > s->cap_gu4) {
+        cudaFree(s->gu4);
+        s->gu4 = nullptr;
+        if ((e = cudaMalloc(&s->gu4, sizeof(float4) * need_gu4)) != cudaSuccess) return aerr(err, e, "adjoint G_u");
+        s->cap_gu4 = need_gu4;
+    }
+    k_adj_weights<<<4 * 152, 256, 0, st>>>(M, ph.S, g_u, g_c, g_h, ph, s->w, s->gu4);
     FarAdjArgs fa;
     fa.nx = g.nx;
     fa.ny = g.ny;
@@ -447,7 +472,8 @@ rism_status adjoint_run(AdjointState* s, TreeState* tree, const DevTables& t, co
     na.srcf = t.srcf;
     na.ljf = t.ljf;
     na.w = s->w;
-    na.gu = g_u;
+    na.gu4 = g_u ? s->gu4 : nullptr;
+    na.order = (tree && o.method == RISM_METHOD_TREECODE) ? tree_atom_order(tree) : nullptr;
     double rc_max = 0.0;
     if (o.lj_mode == RISM_LJ_RCUT) rc_max = o.lj_rcut;
     else rc_max = INFINITY;  // no cut-off, or per-pair cut-offs: scan the whole grid, the kernel tests each pair

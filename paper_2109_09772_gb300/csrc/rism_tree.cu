@@ -3221,7 +3221,7 @@ rism_status batch_eval(std::vector<BatchItem>& items, const rism_options& o, cud
 // themselves for the level-0 regions that do not.
 namespace {
 
-constexpr int kAL = 32;             // atoms per group of an octree leaf in the reverse far field
+constexpr int kAL = 32;             // atoms per target group (part of one octree leaf) in the reverse far field
 constexpr int kADirect = 0x40000000; // entry flag: a level-0 region summed point by point
 
 struct AdjTreeMeta {
@@ -3404,9 +3404,10 @@ __global__ void __launch_bounds__(256) k_adj_qagg(TBoxes tb, int l, const float2
     for (int k = threadIdx.x; k < P3; k += blockDim.x) dst[k] = acc[k];
 }
 
-// Octree leaves in node order (one CTA): leaf_ids[0 .. count).
-__global__ void __launch_bounds__(1024) k_leaf_list(const TreeMeta* meta, const Node* __restrict__ nodes,
-                                                    int* leaf_ids, int* count) {
+// Reverse-mode targets (one CTA): every octree leaf split into groups of at most kAL consecutive atoms, in node
+// order; grp[g] = (first atom, count), *count = the number of groups.
+__global__ void __launch_bounds__(1024) k_leaf_list(const TreeMeta* meta, const Node* __restrict__ nodes, int2* grp,
+                                                    int* count) {
     __shared__ int tmp[64];
     __shared__ int base;
     if (threadIdx.x == 0) base = 0;
@@ -3414,10 +3415,18 @@ __global__ void __launch_bounds__(1024) k_leaf_list(const TreeMeta* meta, const 
     const int nn = meta->nnodes;
     for (int b0 = 0; b0 < nn; b0 += blockDim.x) {
         const int nid = b0 + threadIdx.x;
-        const int f = (nid < nn && nodes[nid].first_child < 0) ? 1 : 0;
+        int ng = 0, nb = 0, ne = 0;
+        if (nid < nn) {
+            const Node nd = nodes[nid];
+            if (nd.first_child < 0) {
+                nb = nd.begin;
+                ne = nd.end;
+                ng = (ne - nb + kAL - 1) / kAL;
+            }
+        }
         int tot;
-        const int off = block_exclusive_scan(f, tmp, tot);
-        if (f) leaf_ids[base + off] = nid;
+        const int off = block_exclusive_scan(ng, tmp, tot);
+        for (int q = 0; q < ng; ++q) grp[base + off + q] = make_int2(nb + q * kAL, min(kAL, ne - nb - q * kAL));
         __syncthreads();
         if (threadIdx.x == 0) base += tot;
         __syncthreads();
@@ -3428,8 +3437,8 @@ __global__ void __launch_bounds__(1024) k_leaf_list(const TreeMeta* meta, const 
 // Interaction lists of the atom leaves (one warp per leaf): the grid-box hierarchy from the top; a box with
 // proxies that meets (r_leaf + r_box)/R < theta is accepted, another box is opened, a level-0 region that is
 // not accepted is summed point by point.  Order: frontier round, then lane -- deterministic.
-__global__ void __launch_bounds__(32 * kListWarps) k_adj_lists(TBoxes tb, const Node* __restrict__ nodes,
-                                                              const int* __restrict__ leaf_ids,
+__global__ void __launch_bounds__(32 * kListWarps) k_adj_lists(TBoxes tb, const SrcF* __restrict__ ssrcf,
+                                                              const int2* __restrict__ grp,
                                                               const int* __restrict__ nleaf_p, float theta, int cap,
                                                               int* cnt, int* ent, AdjTreeMeta* meta) {
     __shared__ int qa[kListWarps][kQCap], qb[kListWarps][kQCap];
@@ -3437,11 +3446,22 @@ __global__ void __launch_bounds__(32 * kListWarps) k_adj_lists(TBoxes tb, const 
     const int nleaf = *nleaf_p;
     const float th2 = theta * theta;
     for (int leaf = blockIdx.x * kListWarps + wv; leaf < nleaf; leaf += gridDim.x * kListWarps) {
-        const Node nd = nodes[leaf_ids[leaf]];
+        const int2 gr = grp[leaf];  // a group of consecutive atoms of one octree leaf: a compact box
+        float lo[3] = {INFINITY, INFINITY, INFINITY}, hi[3] = {-INFINITY, -INFINITY, -INFINITY};
+        if (lane < gr.y) {
+            const SrcF sf = ssrcf[gr.x + lane];
+            lo[0] = hi[0] = sf.xh;
+            lo[1] = hi[1] = sf.yh;
+            lo[2] = hi[2] = sf.zh;
+        }
         float c[3], r2 = 0.f;
         for (int d = 0; d < 3; ++d) {
-            c[d] = 0.5f * (nd.lo[d] + nd.hi[d]);
-            r2 += 0.25f * (nd.hi[d] - nd.lo[d]) * (nd.hi[d] - nd.lo[d]);
+            for (int o = 16; o > 0; o >>= 1) {
+                lo[d] = fminf(lo[d], __shfl_xor_sync(0xffffffffu, lo[d], o));
+                hi[d] = fmaxf(hi[d], __shfl_xor_sync(0xffffffffu, hi[d], o));
+            }
+            c[d] = 0.5f * (lo[d] + hi[d]);
+            r2 += 0.25f * (hi[d] - lo[d]) * (hi[d] - lo[d]);
         }
         const float rl = sqrtf(r2) + 0.01f;  // slack for the low parts of the positions
         int* cur = qa[wv];
@@ -3560,35 +3580,47 @@ __device__ void adj_leaf_group(const TBoxes& tb, const SrcF* __restrict__ ssrcf,
     float h[4] = {0.f, 0.f, 0.f, 0.f}, lo4[4] = {0.f, 0.f, 0.f, 0.f};
     const int ne = cnt[leaf];
     const int64_t plane = (int64_t)tb.ny * tb.nx;
+    // proxy offsets from the box centre and the A1 weight (16-byte aligned after the even-sized Q array)
+    float4* Pc = reinterpret_cast<float4*>(Q + ((P3 + 1) & ~1));
     for (int e = 0; e < ne; ++e) {
         const int code = ent[(int64_t)leaf * cap + e];
         float pq = 0.f, px = 0.f, py = 0.f, pz = 0.f;
         if (!(code & kADirect)) {
             const TBox T = tbox_flat(tb, code);
+            const float hx = 0.5f * (T.ext[0] - 1), hy = 0.5f * (T.ext[1] - 1), hz = 0.5f * (T.ext[2] - 1);
             __syncthreads();
             const float2* src = qtot + (int64_t)code * P3;
-            for (int k = tid; k < P3; k += kADThreads) Q[k] = src[k];
+            for (int k = tid; k < P3; k += kADThreads) {
+                const int kx = k % n1, ky = (k / n1) % n1, kz = k / (n1 * n1);
+                const float2 q = src[k];
+                Q[k] = q;
+                Pc[k] = make_float4(hx * tb.ck[kx], hy * tb.ck[ky], hz * tb.ck[kz], q.x);
+            }
             __syncthreads();
-            // atom relative to the box centre; proxy k at (hx ck[kx], hy ck[ky], hz ck[kz])
+            // atom relative to the box centre
             const float ax = (sf.xh - (float)T.c[0]) + sf.xl, ay = (sf.yh - (float)T.c[1]) + sf.yl,
                         az = (sf.zh - (float)T.c[2]) + sf.zl;
-            const float hx = 0.5f * (T.ext[0] - 1), hy = 0.5f * (T.ext[1] - 1), hz = 0.5f * (T.ext[2] - 1);
             for (int k = sub; k < P3; k += kADSub) {
-                const int kx = k % n1, ky = (k / n1) % n1, kz = k / (n1 * n1);
-                const float2 q = Q[k];
-                adj_pair<DH>(hx * tb.ck[kx] - ax, hy * tb.ck[ky] - ay, hz * tb.ck[kz] - az, q.x, q.y, kap2, kapg,
-                             pq, px, py, pz);
+                const float4 pc = Pc[k];
+                adj_pair<DH>(pc.x - ax, pc.y - ay, pc.z - az, pc.w, DH ? Q[k].y : 0.f, kap2, kapg, pq, px, py, pz);
             }
         } else {
             const TBox R = tbox_flat(tb, code & ~kADirect);
-            const int m0 = R.ext[0], m1 = R.ext[1], npt = m0 * m1 * R.ext[2];
-            for (int p = sub; p < npt; p += kADSub) {
-                const int ix = p % m0, iy = (p / m0) % m1, iz = p / (m0 * m1);
-                const int gx = R.lo[0] + ix, gy = R.lo[1] + iy, gz = R.lo[2] + iz;
-                const float4 wv = w[gz * plane + (int64_t)gy * tb.nx + gx];
-                // lattice point minus the atom: exact first subtraction for nearby atoms
-                adj_pair<DH>(((float)gx - sf.xh) - sf.xl, ((float)gy - sf.yh) - sf.yl, ((float)gz - sf.zh) - sf.zl,
-                             wv.x, wv.y, kap2, kapg, pq, px, py, pz);
+            const int m0 = R.ext[0], m1 = R.ext[1], m2 = R.ext[2];
+            // lattice point minus the atom: exact first subtraction for nearby atoms
+            for (int iz = 0; iz < m2; ++iz) {
+                const int gz = R.lo[2] + iz;
+                const float dz = ((float)gz - sf.zh) - sf.zl;
+                for (int iy = 0; iy < m1; ++iy) {
+                    const int gy = R.lo[1] + iy;
+                    const float dy = ((float)gy - sf.yh) - sf.yl;
+                    const float4* row = w + gz * plane + (int64_t)gy * tb.nx + R.lo[0];
+                    for (int ix = sub; ix < m0; ix += kADSub) {
+                        const float4 wv = row[ix];
+                        adj_pair<DH>(((float)(R.lo[0] + ix) - sf.xh) - sf.xl, dy, dz, wv.x, wv.y, kap2, kapg, pq,
+                                     px, py, pz);
+                    }
+                }
             }
         }
         ff_add(h[0], lo4[0], pq);
@@ -3611,8 +3643,7 @@ __device__ void adj_leaf_group(const TBoxes& tb, const SrcF* __restrict__ ssrcf,
 template <bool DH>
 __global__ void __launch_bounds__(kADThreads) k_adj_treefar(TBoxes tb, const SrcF* __restrict__ ssrcf,
                                                            const uint32_t* __restrict__ idx,
-                                                           const Node* __restrict__ nodes,
-                                                           const int* __restrict__ leaf_ids,
+                                                           const int2* __restrict__ grp,
                                                            const int* __restrict__ nleaf_p,
                                                            const float4* __restrict__ w,
                                                            const float2* __restrict__ qtot, const int* __restrict__ cnt,
@@ -3622,10 +3653,9 @@ __global__ void __launch_bounds__(kADThreads) k_adj_treefar(TBoxes tb, const Src
     float2* Q = reinterpret_cast<float2*>(sm_raw);  // one box's proxies
     if (meta->overflow || blockIdx.x >= *nleaf_p) return;
     const int leaf = blockIdx.x, tid = threadIdx.x, a = tid / kADSub, sub = tid % kADSub;
-    const Node nd = nodes[leaf_ids[leaf]];
-    for (int g0 = nd.begin; g0 < nd.end; g0 += kAL)  // groups of kAL atoms of the leaf
-        adj_leaf_group<DH>(tb, ssrcf, idx, w, qtot, cnt, ent, cap, kap2, kapg, part, Q, leaf, g0 + a, g0 + a < nd.end,
-                           tid, sub);
+    const int2 gr = grp[leaf];
+    adj_leaf_group<DH>(tb, ssrcf, idx, w, qtot, cnt, ent, cap, kap2, kapg, part, Q, leaf, gr.x + a, a < gr.y, tid,
+                       sub);
 }
 
 template <int N1>
@@ -3662,8 +3692,9 @@ void launch_adj_q_deg(const TBoxes& tb, const float4* w, float2* qpart, int* rlo
 struct AdjTree {
     float2 *qpart = nullptr, *qtot = nullptr;
     int* rlow = nullptr;
-    int *leaf_ids = nullptr, *nleaf = nullptr;
-    int64_t cap_leaf_ids = 0;
+    int2* grp = nullptr;  // reverse-mode targets: (first atom, count) of each group of an octree leaf
+    int* nleaf = nullptr;
+    int64_t cap_grp = 0;
     int64_t cap_qpart = 0, cap_qtot = 0, cap_rlow = 0;
     int *cnt = nullptr, *ent = nullptr;
     int cap = 256, cap_leaf = 0;
@@ -3673,7 +3704,7 @@ struct AdjTree {
         cudaFree(qpart);
         cudaFree(qtot);
         cudaFree(rlow);
-        cudaFree(leaf_ids);
+        cudaFree(grp);
         cudaFree(nleaf);
         cudaFree(cnt);
         cudaFree(ent);
@@ -3683,6 +3714,8 @@ struct AdjTree {
 };
 
 void adjtree_delete(AdjTree* a) { delete a; }
+
+const uint32_t* tree_atom_order(TreeState* s) { return (s && s->prepared) ? s->idx : nullptr; }
 
 rism_status tree_adjoint_far(TreeState* s, const DevTables& t, const GridD& g, const Phys& ph, const rism_options& o,
                              const float4* w, bool dh, double* part, cudaStream_t st, std::string& err, bool& used) {
@@ -3694,7 +3727,8 @@ rism_status tree_adjoint_far(TreeState* s, const DevTables& t, const GridD& g, c
     AdjTree& A = *s->adj;
     cudaError_t e;
     const int nb0 = tb.nbx[0] * tb.nby[0] * tb.nbz[0];
-    const int nleaf = s->max_nodes;  // upper bound of the octree leaves (their count stays on the device)
+    // upper bound of the target groups: every leaf adds at most one partial group (the count stays on the device)
+    const int nleaf = n / kAL + s->max_nodes + 1;
     auto grow = [&](auto*& p, int64_t& cap, int64_t need) -> cudaError_t {
         if (need <= cap) return cudaSuccess;
         cudaFree(p);
@@ -3714,11 +3748,11 @@ rism_status tree_adjoint_far(TreeState* s, const DevTables& t, const GridD& g, c
             (e = cudaMalloc(&A.nleaf, sizeof(int))) != cudaSuccess)
             return cuda_err(err, e, "reverse-mode meta");
     }
-    if ((e = grow(A.leaf_ids, A.cap_leaf_ids, (int64_t)nleaf + 1)) != cudaSuccess)
+    if ((e = grow(A.grp, A.cap_grp, (int64_t)nleaf + 1)) != cudaSuccess)
         return cuda_err(err, e, "reverse-mode leaves");
-    k_leaf_list<<<1, 1024, 0, st>>>(s->meta, s->nodes, A.leaf_ids, A.nleaf);
+    k_leaf_list<<<1, 1024, 0, st>>>(s->meta, s->nodes, A.grp, A.nleaf);
     launch_adj_q_deg(tb, w, A.qpart, A.rlow, A.qtot, st);
-    const size_t sq = sizeof(float2) * tb.P3;
+    const size_t sq = sizeof(float2) * ((tb.P3 + 1) & ~1) + sizeof(float4) * tb.P3;
     for (int attempt = 0; attempt < 4; ++attempt) {
         if (nleaf + 1 > A.cap_leaf) {
             cudaFree(A.cnt);
@@ -3729,15 +3763,14 @@ rism_status tree_adjoint_far(TreeState* s, const DevTables& t, const GridD& g, c
         if ((e = grow(A.ent, A.cap_ent, (int64_t)nleaf * A.cap)) != cudaSuccess) return cuda_err(err, e, "lists");
         cudaMemsetAsync(A.meta, 0, sizeof(AdjTreeMeta), st);
         k_adj_lists<<<(nleaf + kListWarps - 1) / kListWarps, 32 * kListWarps, 0, st>>>(
-            tb, s->nodes, A.leaf_ids, A.nleaf, (float)o.theta, A.cap, A.cnt, A.ent, A.meta);
+            tb, s->srcf, A.grp, A.nleaf, (float)o.theta, A.cap, A.cnt, A.ent, A.meta);
         const float kap2 = (float)(-ph.kappa * g.h * 1.4426950408889634), kapg = (float)(ph.kappa * g.h);
         if (dh)
-            k_adj_treefar<true><<<nleaf, kADThreads, sq, st>>>(tb, s->srcf, s->idx, s->nodes, A.leaf_ids, A.nleaf, w,
-                                                               A.qtot, A.cnt, A.ent, A.cap, kap2, kapg, A.meta, part);
+            k_adj_treefar<true><<<nleaf, kADThreads, sq, st>>>(tb, s->srcf, s->idx, A.grp, A.nleaf, w, A.qtot, A.cnt,
+                                                               A.ent, A.cap, kap2, kapg, A.meta, part);
         else
-            k_adj_treefar<false><<<nleaf, kADThreads, sq, st>>>(tb, s->srcf, s->idx, s->nodes, A.leaf_ids, A.nleaf,
-                                                                w, A.qtot, A.cnt, A.ent, A.cap, kap2, kapg, A.meta,
-                                                                part);
+            k_adj_treefar<false><<<nleaf, kADThreads, sq, st>>>(tb, s->srcf, s->idx, A.grp, A.nleaf, w, A.qtot,
+                                                                A.cnt, A.ent, A.cap, kap2, kapg, A.meta, part);
         if ((e = cudaMemcpyAsync(A.h_meta, A.meta, sizeof(AdjTreeMeta), cudaMemcpyDeviceToHost, st)) != cudaSuccess ||
             (e = cudaStreamSynchronize(st)) != cudaSuccess)
             return cuda_err(err, e, "reverse-mode lists");

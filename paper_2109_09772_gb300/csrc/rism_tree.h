@@ -66,6 +66,9 @@ void tree_graph_reset(TreeState* ts);
 rism_status tree_adjoint_far(TreeState* ts, const DevTables& t, const GridD& g, const Phys& ph, const rism_options& o,
                              const float4* w, bool dh, double* part, cudaStream_t st, std::string& err, bool& used);
 
+// Original atom indices in Morton (sorted) order of the last tree build, or null before any.
+const uint32_t* tree_atom_order(TreeState* ts);
+
 // Many solutes in one persistent, graph-captured launch sequence.
 // The whole sequence (per-solute setup and tree kernels, persistent far and
 // near kernels) is captured in a CUDA graph and replayed while unchanged.
