@@ -259,11 +259,21 @@ __global__ void __launch_bounds__(kNearT) k_adj_near(NearAdjArgs a) {
     float acc[9] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};  // dq, Gx, Gy, Gz, LJx, LJy, LJz, dsig, deps
     float hi9[9] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f}, lo9[9] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
     int cntp = 0;
-    // threads over the (x, y) plane of the box (one 32-bit division each), z innermost
-    for (int b = threadIdx.x; b < nplane; b += blockDim.x)
-    for (int kk = lo[2]; kk <= hi[2]; ++kk) {
-        const int ii = lo[0] + b % bx, jj = lo[1] + b / bx;
-        const float dx = ((float)ii - sf.xh) - sf.xl, dy = ((float)jj - sf.yh) - sf.yl, dz = ((float)kk - sf.zh) - sf.zl;
+    // threads over the (x, y) columns of the box (one 32-bit division each); z runs over the column's chord of
+    // the near sphere (one grid unit of margin; the exact test below decides)
+    for (int b = threadIdx.x; b < nplane; b += blockDim.x) {
+    const int ii = lo[0] + b % bx, jj = lo[1] + b / bx;
+    const float dx = ((float)ii - sf.xh) - sf.xl, dy = ((float)jj - sf.yh) - sf.yl;
+    int k0 = lo[2], k1 = hi[2];
+    if (isfinite(rn2)) {
+        const float rem = rn2 - fmaf(dx, dx, dy * dy);
+        if (rem < 0.f) continue;
+        const float hz = sqrtf(rem) + 1.0f;
+        k0 = max(k0, (int)floorf(sf.zh - hz));
+        k1 = min(k1, (int)ceilf(sf.zh + hz));
+    }
+    for (int kk = k0; kk <= k1; ++kk) {
+        const float dz = ((float)kk - sf.zh) - sf.zl;
         const float d2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
         if (d2 >= rn2 || d2 == 0.f) continue;
         const int64_t f = ((int64_t)kk * g.ny + jj) * g.nx + ii;
@@ -321,6 +331,7 @@ __global__ void __launch_bounds__(kNearT) k_adj_near(NearAdjArgs a) {
             }
             cntp = 0;
         }
+    }
     }
     for (int q = 0; q < 9; ++q) ff_add(hi9[q], lo9[q], acc[q]);
     double tot[9];
