@@ -146,9 +146,9 @@ FP32_LANES_PER_SM = 128
 SMS = 152
 # DRAM bytes per launch on this workload (dram__bytes_read.sum + dram__bytes_write.sum of one ncu capture of
 # the kernel as it stands); None when the kernel has changed since the capture.
-FAR_TRAFFIC_BYTES = None
-NEAR_TRAFFIC_BYTES = None
-BOX_TRAFFIC_BYTES = None
+FAR_TRAFFIC_BYTES = 34071040     # 34,052,096 read (the far-field buffer it starts from) + 18,944 written
+NEAR_TRAFFIC_BYTES = 187320320   # 34,962,944 read + 152,357,376 written (u, c, h)
+BOX_TRAFFIC_BYTES = None         # several kernels
 
 
 def _alu_peak_tflops(sm_mhz):
