@@ -280,6 +280,7 @@ struct BuildArgs {
     Geo* src;              // out: sorted FP64 grid units
     SrcF* ssrcf;           // out: sorted float-float
     LJf* ljs;              // out: sorted LJ tables
+    LJf* ljs2;             // out: the same as {A, A, -B, -B} (two-wide operands of the near field)
 };
 
 __device__ int block_exclusive_scan(int v, int* tmp /* >= 32 ints */, int& total) {
@@ -369,7 +370,11 @@ __global__ void __launch_bounds__(kSortThreads) k_sort_build(BuildArgs a, uint32
         const int j = (int)idx[i];
         a.src[i] = to_grid(a.geo[j], a.gd, a.ih);
         a.ssrcf[i] = a.srcf[j];
-        for (int s = 0; s < a.smax; ++s) a.ljs[(int64_t)i * a.smax + s] = a.ljf[(int64_t)j * a.smax + s];
+        for (int s = 0; s < a.smax; ++s) {
+            const LJf l = a.ljf[(int64_t)j * a.smax + s];
+            a.ljs[(int64_t)i * a.smax + s] = l;
+            a.ljs2[(int64_t)i * a.smax + s] = LJf{l.A, l.A, -l.B, -l.B};
+        }
     }
 
     // ---- octree, level by level: nodes [lvl_begin, lvl_end) at the current level
@@ -1118,6 +1123,7 @@ struct EvalArgs {
     int n;
     const SrcF* srcf;      // [sorted atoms | proxies], grid units, float-float
     const LJf* ljs;        // sorted LJ tables
+    const LJf* ljs2;       // sorted LJ tables as {A, A, -B, -B}
     const int* far_cnt;    // far-list length per batch
     const int2* far_ent;   // [nb][far_cap]
     const int* near_cnt;
@@ -1927,6 +1933,95 @@ __device__ __forceinline__ void near_tile(const SrcF* __restrict__ Sx, const LJf
     }
 }
 
+// The same tile for two points per thread and one cut-off for every pair, with the distances and the LJ terms
+// of both points in two-wide instructions: L2 holds {A, A, -B, -B} per (atom, site), so one shared load gives
+// both operands of a site.  Per pair the arithmetic (and so every result) is that of near_tile.
+template <int SM, bool DU, bool DH>
+__device__ __forceinline__ void near_tile_uni2(const SrcF* __restrict__ Sx, const LJf* __restrict__ L2, int cnt,
+                                               const float (&gx)[2], float fy, float fz, float rn2, float rs2,
+                                               float rcu2, float tinv, const float4* tab, bool DC, float c0h,
+                                               float h0h, const float (&wlo)[3], const float (&whi)[3], float rcull2,
+                                               float (&psc)[2], float (&psh)[2], float (&plj)[2][SM], unsigned& hit,
+                                               unsigned (&cnt3)[3]) {
+    const int lane = threadIdx.x & 31;
+    auto keep = [&](int i) {
+        if (i >= cnt) return false;
+        const float4 g = *reinterpret_cast<const float4*>(&Sx[i].xh);
+        const float qx = fmaxf(0.f, fmaxf(wlo[0] - g.x, g.x - whi[0]));
+        const float qy = fmaxf(0.f, fmaxf(wlo[1] - g.y, g.y - whi[1]));
+        const float qz = fmaxf(0.f, fmaxf(wlo[2] - g.z, g.z - whi[2]));
+        return fmaf(qx, qx, fmaf(qy, qy, qz * qz)) < rcull2;
+    };
+    const unsigned long long live =
+        (unsigned long long)__ballot_sync(0xffffffffu, keep(lane)) |
+        ((unsigned long long)__ballot_sync(0xffffffffu, keep(lane + 32)) << 32);
+    const f32x2 GX2 = pk2(gx[0], gx[1]);
+    f32x2 ACC[SM];
+#pragma unroll
+    for (int s = 0; s < SM; ++s) ACC[s] = 0ull;
+    for (unsigned long long mk = live; mk != 0ull; mk &= mk - 1ull) {
+        const int s0 = __ffsll((long long)mk) - 1;
+        const float4 g0 = *reinterpret_cast<const float4*>(&Sx[s0].xh);
+        const float4 g1 = *reinterpret_cast<const float4*>(&Sx[s0].xl);
+        cnt3[0] += 2;
+        const float dy = (fy - g0.y) - g1.y;
+        const float dz = (fz - g0.z) - g1.z;
+        const float dyz2 = fmaf(dy, dy, dz * dz);
+        const f32x2 DX = sub2(sub2(GX2, pk2(g0.x, g0.x)), pk2(g1.x, g1.x));
+        const float2 d2 = up2(fma2(DX, DX, pk2(dyz2, dyz2)));
+        if (fminf(d2.x, d2.y) >= rn2) continue;
+        if (fminf(d2.x, d2.y) < rs2) {
+#pragma unroll
+            for (int p = 0; p < 2; ++p) {
+                const float dd = p ? d2.y : d2.x;
+                if (dd >= rs2) continue;
+                if (dd > 0.f) {
+                    // erfc(x)/d and e^{-x^2}[erfcx(x-a) + erfcx(x+a)]/d from the cubic pieces in d
+                    ++cnt3[2];
+                    const float ri = rsqrt_approx(dd);
+                    const float qr = g0.w * ri;
+                    const float uu = dd * ri * tinv;
+                    const int it = min((int)uu, kNTab - 1);
+                    const float tt = uu - (float)it;
+                    if (DC) {
+                        const float4 cc = tab[2 * it];
+                        psc[p] = fmaf(qr, fmaf(fmaf(fmaf(cc.w, tt, cc.z), tt, cc.y), tt, cc.x), psc[p]);
+                    }
+                    if (DH) {
+                        const float4 ch = tab[2 * it + 1];
+                        psh[p] = fmaf(qr, fmaf(fmaf(fmaf(ch.w, tt, ch.z), tt, ch.y), tt, ch.x), psh[p]);
+                    }
+                } else {
+                    hit |= 1u << p;
+                    if (DC) psc[p] -= g0.w * c0h;
+                    if (DH) psh[p] -= g0.w * h0h;
+                }
+            }
+        }
+        if (DU) {
+            const bool in0 = d2.x < rcu2, in1 = d2.y < rcu2;
+            if (in0 || in1) {
+                cnt3[1] += (unsigned)in0 + (unsigned)in1;
+                const float r0 = rcp_approx(d2.x), r1 = rcp_approx(d2.y);
+                const f32x2 R2 = pk2(in0 ? r0 : 0.f, in1 ? r1 : 0.f);  // a point outside the cut-off adds +0
+                const f32x2 R6 = mul2(mul2(R2, R2), R2);
+                const LJf* Ls = L2 + s0 * SM;
+#pragma unroll
+                for (int s = 0; s < SM; ++s) {
+                    const ulonglong2 ab = *reinterpret_cast<const ulonglong2*>(&Ls[s]);  // (A, A), (-B, -B)
+                    ACC[s] = fma2(R6, fma2(ab.x, R6, ab.y), ACC[s]);
+                }
+            }
+        }
+    }
+#pragma unroll
+    for (int s = 0; s < SM; ++s) {
+        const float2 v = up2(ACC[s]);
+        plj[0][s] += v.x;
+        plj[1][s] += v.y;
+    }
+}
+
 template <int NXB, int NYB, int NZB, int SM, bool DU, bool DH>
 __device__ void near_body(const EvalArgs& a, int b, Ring<SM, true>& r, float4* tab) {
     using Sh = NearShape<NXB, NYB, NZB>;
@@ -1983,7 +2078,8 @@ __device__ void near_body(const EvalArgs& a, int b, Ring<SM, true>& r, float4* t
         ring_init(r, Sh::NW);
     }
     __syncthreads();
-    const int rr = run_ring<SM, true, Sh::NW>(r, cur, a.near_ent, a.srcf, a.ljs, a, [&](int slot, int cnt) {
+    const LJf* ljt = (a.uni_rc && P == 2) ? a.ljs2 : a.ljs;  // the two-wide tile reads {A, A, -B, -B}
+    const int rr = run_ring<SM, true, Sh::NW>(r, cur, a.near_ent, a.srcf, ljt, a, [&](int slot, int cnt) {
         const SrcF* Sx = r.src[slot];
         const LJf* L = r.lj[slot];
         float psc[P], psh[P], plj[P][SM];
@@ -1993,12 +2089,22 @@ __device__ void near_body(const EvalArgs& a, int b, Ring<SM, true>& r, float4* t
 #pragma unroll
             for (int s = 0; s < SM; ++s) plj[p][s] = 0.f;
         }
-        if (a.uni_rc)
-            near_tile<P, SM, DU, DH, true>(Sx, L, cnt, gx, fy, fz, rn2, rs2, rcu2, tinv, tab, DC, c0h, h0h, wlo, whi,
+        bool done = false;
+        if constexpr (P == 2) {
+            if (a.uni_rc) {
+                near_tile_uni2<SM, DU, DH>(Sx, L, cnt, gx, fy, fz, rn2, rs2, rcu2, tinv, tab, DC, c0h, h0h, wlo, whi,
                                            rcull2, psc, psh, plj, hit, cnt3);
-        else
-            near_tile<P, SM, DU, DH, false>(Sx, L, cnt, gx, fy, fz, rn2, rs2, rcu2, tinv, tab, DC, c0h, h0h, wlo,
-                                            whi, rcull2, psc, psh, plj, hit, cnt3);
+                done = true;
+            }
+        }
+        if (!done) {
+            if (a.uni_rc)
+                near_tile<P, SM, DU, DH, true>(Sx, L, cnt, gx, fy, fz, rn2, rs2, rcu2, tinv, tab, DC, c0h, h0h, wlo,
+                                               whi, rcull2, psc, psh, plj, hit, cnt3);
+            else
+                near_tile<P, SM, DU, DH, false>(Sx, L, cnt, gx, fy, fz, rn2, rs2, rcu2, tinv, tab, DC, c0h, h0h, wlo,
+                                                whi, rcull2, psc, psh, plj, hit, cnt3);
+        }
 #pragma unroll
         for (int p = 0; p < P; ++p) {
             if (DC) ff_add(sch[p], scl[p], psc[p]);
@@ -2286,6 +2392,7 @@ struct TreeState {
     Geo* src = nullptr;    // sorted atoms + proxies, FP64 grid units (upward pass)
     SrcF* srcf = nullptr;  // the same as float-float (evaluation kernels)
     LJf* ljs = nullptr;
+    LJf* ljs2 = nullptr;   // sorted LJ tables as {A, A, -B, -B}
     float4* far = nullptr; // far-field sums per grid point
     int64_t cap_far_pts = 0;
     int *far_cnt = nullptr, *near_cnt = nullptr, *prox_items = nullptr, *near_work = nullptr, *near_order = nullptr;
@@ -2374,7 +2481,8 @@ rism_status tree_reserve(TreeState* s, const DevTables& t, const GridD& g, const
             (e = regrow(s->items, 2 * (size_t)s->max_items)) || (e = regrow(s->prox_nodes, (size_t)s->max_prox)) ||
             (e = regrow(s->prox_items, (size_t)s->max_prox + 1)) ||
             (e = regrow(s->part, (size_t)s->max_items * P3)) || (e = regrow(s->src, nn + (size_t)s->max_prox * P3)) ||
-            (e = regrow(s->srcf, nn + (size_t)s->max_prox * P3)) || (e = regrow(s->ljs, nn * t.smax)))
+            (e = regrow(s->srcf, nn + (size_t)s->max_prox * P3)) || (e = regrow(s->ljs, nn * t.smax)) ||
+            (e = regrow(s->ljs2, nn * t.smax)))
             return cuda_err(err, e, "tree buffers");
         s->cap_n = (int64_t)nn;
         s->cap_nodes = s->max_nodes;
@@ -2555,7 +2663,7 @@ rism_status tree_enqueue(TreeState* s, const DevTables& t, const GridD& g, const
         k_bounds<<<gb, 256, 0, st>>>(t.srcf, t.ljf, n, ph.S, t.smax, s->meta);
         k_codes<<<gb, 256, 0, st>>>(t.srcf, n, ph.rs / g.h, s->meta, s->code, s->idx);
         BuildArgs ba{n, s->leaf, P3, s->max_nodes, s->max_prox, s->max_items, t.geo, t.srcf, t.ljf, t.smax, g,
-                     1.0 / g.h, s->src, s->srcf, s->ljs};
+                     1.0 / g.h, s->src, s->srcf, s->ljs, s->ljs2};
         const size_t shb = (256 * 32 + 64) * sizeof(int);
         cudaFuncSetAttribute(k_sort_build, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shb);
         k_sort_build<<<1, kSortThreads, shb, st>>>(ba, s->code, s->idx, s->code2, s->idx2, s->nodes, s->items,
@@ -2612,6 +2720,7 @@ EvalArgs make_args(TreeState* s, const DevTables& t, const GridD& g, const Phys&
     a.n = (int)t.n;
     a.srcf = s->srcf;
     a.ljs = s->ljs;
+    a.ljs2 = s->ljs2;
     a.far_cnt = s->far_cnt;
     a.far_ent = s->far_ent;
     a.near_cnt = s->near_cnt;
@@ -2784,6 +2893,7 @@ void tree_destroy(TreeState* s) {
     cudaFree(s->srcf);
     cudaFree(s->far);
     cudaFree(s->ljs);
+    cudaFree(s->ljs2);
     cudaFree(s->far_cnt);
     cudaFree(s->near_cnt);
     cudaFree(s->near_work);
