@@ -2026,10 +2026,16 @@ template <int NXB, int NYB, int NZB, int SM, bool DU, bool DH>
 __device__ void near_body(const EvalArgs& a, int b, Ring<SM, true>& r, float4* tab) {
     using Sh = NearShape<NXB, NYB, NZB>;
     constexpr int P = Sh::P;
+    static_assert(P == 2 && NXB % 4 == 0 && NYB % 4 == 0 && NZB % 4 == 0, "near warps tile the batch in 4x4x4");
     const int tid = threadIdx.x;
-    const int tx = tid % Sh::TX, ty = (tid / Sh::TX) % NYB, tz = tid / (Sh::TX * NYB);
+    // each warp owns a 4x4x4 block of the batch (compact: small culling box, coherent distances), a lane two
+    // consecutive points along x of it
+    constexpr int WX = NXB / 4, WY = NYB / 4;
+    const int wq = tid >> 5, ln = tid & 31;
+    const int wx = wq % WX, wy = (wq / WX) % WY, wz = wq / (WX * WY);
     const int ib = b % a.nbx, jb = (b / a.nbx) % a.nby, kb = b / (a.nbx * a.nby);
-    const int i0 = ib * NXB + tx * P, j = jb * NYB + ty, k = kb * NZB + tz;
+    const int i0 = ib * NXB + 4 * wx + 2 * (ln & 1), j = jb * NYB + 4 * wy + ((ln >> 1) & 3),
+              k = kb * NZB + 4 * wz + (ln >> 3);
     float gx[P];
 #pragma unroll
     for (int p = 0; p < P; ++p) gx[p] = (float)(i0 + p);
