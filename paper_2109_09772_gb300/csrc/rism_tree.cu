@@ -54,7 +54,6 @@ constexpr int kMortonBits = 10;          // per axis
 constexpr int kMaxLevel = kMortonBits;   // octree depth limit
 constexpr int kChunk = 16;               // atoms per upward-pass work item
 constexpr int kT = 64;                   // sources per shared-memory tile (<= 64: the near culling uses two ballots)
-constexpr int kStack = 8 * kMaxLevel + 8;
 constexpr double kCellFrac = 0.25;        // near-field cells are at least this fraction of the near radius wide
 
 struct Node {
@@ -1134,7 +1133,8 @@ struct EvalArgs {
     const float4* ntab;    // [2 kNTab] cubic pieces of erfc(x) and e^{-x^2}[erfcx(x-a) + erfcx(x+a)] in d
     float ntab_inv;        // kNTab / r_short (grid units)
     int uni_rc;            // every (atom, site) pair has the same LJ cut-off (global cut-off or none)
-    const int* near_order; // CTA -> batch of the per-solute near kernel (heaviest first)
+    const int* near_order; // work item -> batch of the per-solute near kernel (heaviest first)
+    int* wq;               // [2] work queue of the persistent near kernel: items taken, CTAs done (0 between launches)
     const int* far_order;  // the same for the far kernel
     const int* near_work;  // per batch: candidate atoms of the near list
     const int* far_work;   // per batch: atoms and proxies of the far list
@@ -1166,6 +1166,10 @@ struct Ring {
     int cnt[kStages];
     int abort;
     int inited;
+    unsigned long long stat[3];  // per-CTA diagnostic pair counts (near kernel)
+    int stat_warps;              // consumer warps that have added theirs
+    int item[kStages];           // item stream: the work item of the tile in each slot (-1: end of stream)
+    int last[kStages];           // item stream: nonzero on the last tile of its item
 };
 
 // Range-list producer state (thread 0).
@@ -1283,6 +1287,95 @@ __device__ int run_ring(R& r, Cursor& cur, const int2* ent, const SrcF* src, con
         __syncwarp();
         if (lane == 0) mbar_arrive(&r.empty[slot]);
         consume(cnt);
+    }
+}
+
+// Source list of one work item of an item stream.
+struct ItemSrc {
+    const int2* ent;  // range entries (first source, count)
+    int e, e_end;     // the item's entries
+    const SrcF* src;
+    const LJf* ljs;
+};
+
+// Ring driver of a persistent CTA that works through a sequence of items (target batches): the producer lane
+// fills the ring with the tiles of item after item without a pause (every item takes at least one tile, the
+// last one flagged; an item without sources gets one empty tile), so the next item's sources load while the
+// consumer warps finish the previous one.  next(n, item, src) gives the CTA's n-th item (false: none left);
+// each consumer warp calls begin(item) before the item's first tile, stage(slot, cnt) per tile (before the slot
+// is released), and finish(item) after its last tile.  The ring barriers are initialised once per launch.
+// Waits are bounded as in run_ring.
+template <int SM, bool LJ, int NWARPS, typename R, typename FN, typename FB, typename FS, typename FF>
+__device__ int run_stream(R& r, long long wlim, DevErr* err, FN&& next, FB&& begin, FS&& stage, FF&& finish) {
+    const int tid = threadIdx.x, lane = tid & 31;
+    volatile int* abort_flag = &r.abort;
+    if (tid >= NWARPS * 32) {
+        if (tid == NWARPS * 32) {
+            Cursor c;
+            c.produced = 0;
+            for (int s = 0; s < kStages; ++s) c.last_phase[s] = -1;
+            bool ok = true;
+            for (int n = 0; ok; ++n) {
+                int item = -1;
+                ItemSrc is{nullptr, 0, 0, nullptr, nullptr};
+                const bool have = next(n, item, is);
+                c.e = have ? is.e : 0;
+                c.e_end = have ? is.e_end : 0;
+                c.off = 0;
+                c.left = INT_MAX;
+                for (bool more = true; more;) {
+                    const int t = c.produced, slot = t % kStages;
+                    if (t >= kStages && !mbar_wait_bounded(&r.empty[slot], (uint32_t)((t / kStages - 1) & 1), wlim)) {
+                        ok = false;
+                        break;
+                    }
+                    if (*abort_flag) {
+                        ok = false;
+                        break;
+                    }
+                    const int cnt = have ? fill_ranges<SM, LJ>(c, is.ent, is.src, is.ljs, r.src[slot],
+                                                               r.lj[LJ ? slot : 0], &r.full[slot])
+                                         : 0;
+                    more = have && c.e < c.e_end;
+                    r.cnt[slot] = cnt;
+                    r.item[slot] = have ? item : -1;
+                    r.last[slot] = more ? 0 : 1;
+                    c.last_phase[slot] = t / kStages;
+                    c.produced = t + 1;
+                    mbar_arrive(&r.full[slot]);
+                }
+                if (!have) break;
+            }
+            if (!ok) {
+                *abort_flag = 1;
+                report_error(err, DEV_TIMEOUT, WHERE_TREE_EVAL);
+                drain(r, c, wlim);
+            }
+        }
+        return kRingProducer;
+    }
+    bool open = false;
+    for (int t = 0;; ++t) {
+        const int slot = t % kStages;
+        const uint32_t ph = (t / kStages) & 1;
+        if (!mbar_wait_bounded(&r.full[slot], ph, wlim) || *abort_flag) {
+            *abort_flag = 1;
+            report_error(err, DEV_TIMEOUT, WHERE_TREE_EVAL);
+            return kRingAbort;
+        }
+        const int item = r.item[slot], cnt = r.cnt[slot], last = r.last[slot];
+        if (item < 0) return kRingDone;
+        if (!open) {
+            begin(item);
+            open = true;
+        }
+        if (cnt > 0) stage(slot, cnt);
+        __syncwarp();
+        if (lane == 0) mbar_arrive(&r.empty[slot]);
+        if (last) {
+            finish(item);
+            open = false;
+        }
     }
 }
 
@@ -1837,9 +1930,14 @@ void launch_down_deg(const TBoxes& tb, const CPArgs& c, float4* far, const TreeM
 }
 
 // ---- near field (LJ within cut-offs, erfc remainders within r_short) + epilogue
+// A near CTA covers SX = min(NXB, 8) points along x of its batch (a batch wider than that takes NSUB CTAs, which
+// read the same near list): 256 consumer threads keep the accumulators of a thread in registers at two CTAs
+// per SM.
 template <int NXB, int NYB, int NZB>
 struct NearShape {
-    static constexpr int P = 2, TX = NXB / P, NT = TX * NYB * NZB, NW = NT / 32, NTP = NT + 32;  // + producer
+    static constexpr int P = 2, SX = NXB < 8 ? NXB : 8, NSUB = NXB / SX, TX = SX / P, NT = TX * NYB * NZB,
+                         NW = NT / 32, NTP = NT + 32;  // + producer
+    static_assert(NXB % SX == 0, "near sub-batches tile the batch along x");
 };
 
 // One tile of near-field sources against the P points of a thread: LJ within the pair cut-offs (UNI: one
@@ -2022,124 +2120,109 @@ __device__ __forceinline__ void near_tile_uni2(const SrcF* __restrict__ Sx, cons
     }
 }
 
-template <int NXB, int NYB, int NZB, int SM, bool DU, bool DH>
-__device__ void near_body(const EvalArgs& a, int b, Ring<SM, true>& r, float4* tab) {
+// Constants of the near field of one solute (grid units).
+struct NearConst {
+    float rs2, c0h, h0h, rn2, rcu2, rcull2, tinv;
+    bool DC, uni;
+};
+
+__device__ __forceinline__ NearConst near_const(const EvalArgs& a) {
+    NearConst c;
+    c.rs2 = (float)((a.ph.rs / a.g.h) * (a.ph.rs / a.g.h));
+    c.c0h = (float)(a.ph.phi_c0 * a.g.h);
+    c.h0h = (float)(a.ph.phi_h0 * a.g.h);
+    c.DC = a.o.c != nullptr;
+    const double rnear = a.meta->rnear;
+    c.rn2 = isfinite(rnear) ? (float)(rnear * rnear) : INFINITY;
+    c.rcu2 = __int_as_float(a.meta->rc2max);  // the cut-off of every pair when a.uni_rc
+    // culling radius: near radius + 0.01 grid units of slack for the source position rounded to its high part
+    const float rcull = isfinite(rnear) ? (float)rnear + 0.01f : INFINITY;
+    c.rcull2 = rcull * rcull;
+    c.tinv = a.ntab_inv;
+    c.uni = a.uni_rc != 0;
+    return c;
+}
+
+// The two points of a near-field thread in one target batch, its warp's point box and its accumulators
+// (float pairs: the sums of the tiles are folded in error-free).
+template <int SM>
+struct NearPts {
+    int i0, j, k;
+    float gx[2], fy, fz, wlo[3], whi[3];
+    float sch[2], scl[2], shh[2], shl[2], ljh[2][SM], ljl[2][SM];
+    unsigned hit;
+};
+
+// Points of sub-batch `sub` of batch b: each warp owns a 4x4x4 block of the sub-batch (compact: small culling
+// box, coherent distances), a lane two consecutive points along x of it.  Called by whole warps.
+template <int NXB, int NYB, int NZB, int SM>
+__device__ __forceinline__ void near_begin(NearPts<SM>& q, const EvalArgs& a, int b, int sub) {
     using Sh = NearShape<NXB, NYB, NZB>;
-    constexpr int P = Sh::P;
-    static_assert(P == 2 && NXB % 4 == 0 && NYB % 4 == 0 && NZB % 4 == 0, "near warps tile the batch in 4x4x4");
-    const int tid = threadIdx.x;
-    // each warp owns a 4x4x4 block of the batch (compact: small culling box, coherent distances), a lane two
-    // consecutive points along x of it
-    constexpr int WX = NXB / 4, WY = NYB / 4;
-    const int wq = tid >> 5, ln = tid & 31;
+    static_assert(Sh::P == 2 && Sh::SX % 4 == 0 && NYB % 4 == 0 && NZB % 4 == 0,
+                  "near warps tile the batch in 4x4x4");
+    constexpr int WX = Sh::SX / 4, WY = NYB / 4;
+    const int tid = threadIdx.x, wq = tid >> 5, ln = tid & 31;
     const int wx = wq % WX, wy = (wq / WX) % WY, wz = wq / (WX * WY);
     const int ib = b % a.nbx, jb = (b / a.nbx) % a.nby, kb = b / (a.nbx * a.nby);
-    const int i0 = ib * NXB + 4 * wx + 2 * (ln & 1), j = jb * NYB + 4 * wy + ((ln >> 1) & 3),
-              k = kb * NZB + 4 * wz + (ln >> 3);
-    float gx[P];
+    q.i0 = ib * NXB + sub * Sh::SX + 4 * wx + 2 * (ln & 1);
+    q.j = jb * NYB + 4 * wy + ((ln >> 1) & 3);
+    q.k = kb * NZB + 4 * wz + (ln >> 3);
+    q.gx[0] = (float)q.i0;
+    q.gx[1] = (float)(q.i0 + 1);
+    q.fy = (float)q.j;
+    q.fz = (float)q.k;
+    const int lo3[3] = {q.i0, q.j, q.k}, hi3[3] = {q.i0 + 1, q.j, q.k};
 #pragma unroll
-    for (int p = 0; p < P; ++p) gx[p] = (float)(i0 + p);
-    const float fy = (float)j, fz = (float)k;
-    const float rs2 = (float)((a.ph.rs / a.g.h) * (a.ph.rs / a.g.h));
-    const float c0h = (float)(a.ph.phi_c0 * a.g.h), h0h = (float)(a.ph.phi_h0 * a.g.h);
-    const bool DC = a.o.c != nullptr;
-    const double rnear = a.meta->rnear;
-    const float rn2 = isfinite(rnear) ? (float)(rnear * rnear) : INFINITY;
-    const float rcu2 = __int_as_float(a.meta->rc2max);  // the cut-off of every pair when a.uni_rc
-    // the warp's point box (grid units) and the culling radius: near radius + 0.01 grid units of slack for the
-    // source position rounded to its high part
-    float wlo[3], whi[3];
-    {
-        const int lo3[3] = {i0, j, k}, hi3[3] = {i0 + P - 1, j, k};
-#pragma unroll
-        for (int d = 0; d < 3; ++d) {
-            wlo[d] = (float)__reduce_min_sync(0xffffffffu, lo3[d]);
-            whi[d] = (float)__reduce_max_sync(0xffffffffu, hi3[d]);
-        }
+    for (int d = 0; d < 3; ++d) {
+        q.wlo[d] = (float)__reduce_min_sync(0xffffffffu, lo3[d]);
+        q.whi[d] = (float)__reduce_max_sync(0xffffffffu, hi3[d]);
     }
-    const float rcull = isfinite(rnear) ? (float)rnear + 0.01f : INFINITY;
-    const float rcull2 = rcull * rcull;
+#pragma unroll
+    for (int p = 0; p < 2; ++p) {
+        q.sch[p] = q.scl[p] = q.shh[p] = q.shl[p] = 0.f;
+#pragma unroll
+        for (int s = 0; s < SM; ++s) q.ljh[p][s] = q.ljl[p][s] = 0.f;
+    }
+    q.hit = 0u;
+}
 
-    float sch[P], scl[P], shh[P], shl[P], ljh[P][SM], ljl[P][SM];
+// One tile of the near list against the thread's points, folded into its accumulators.
+template <int SM, bool DU, bool DH>
+__device__ __forceinline__ void near_stage(NearPts<SM>& q, const NearConst& c, const SrcF* Sx, const LJf* L, int cnt,
+                                           const float4* tab, unsigned (&cnt3)[3]) {
+    float psc[2], psh[2], plj[2][SM];
 #pragma unroll
-    for (int p = 0; p < P; ++p) {
-        sch[p] = scl[p] = shh[p] = shl[p] = 0.f;
+    for (int p = 0; p < 2; ++p) {
+        psc[p] = psh[p] = 0.f;
 #pragma unroll
-        for (int s = 0; s < SM; ++s) ljh[p][s] = ljl[p][s] = 0.f;
+        for (int s = 0; s < SM; ++s) plj[p][s] = 0.f;
     }
-    unsigned hit = 0u;
-    unsigned cnt3[3] = {0u, 0u, 0u};  // pairs tested / inside the LJ cut-off / inside r_short
-    const float tinv = a.ntab_inv;
-    Cursor cur;
-    __syncthreads();
-    for (int k = tid; k < 2 * kNTab; k += blockDim.x) tab[k] = a.ntab[k];
-    if (tid == Sh::NT) {
-        cur.e = b * a.near_cap;
-        cur.e_end = cur.e + a.near_cnt[b];
-        cur.off = 0;
-        cur.left = INT_MAX;
-        cur.produced = 0;
-        cur.done = false;
-        for (int s = 0; s < kStages; ++s) cur.last_phase[s] = -1;
-        ring_init(r, Sh::NW);
-    }
-    __syncthreads();
-    const LJf* ljt = (a.uni_rc && P == 2) ? a.ljs2 : a.ljs;  // the two-wide tile reads {A, A, -B, -B}
-    const int rr = run_ring<SM, true, Sh::NW>(r, cur, a.near_ent, a.srcf, ljt, a, [&](int slot, int cnt) {
-        const SrcF* Sx = r.src[slot];
-        const LJf* L = r.lj[slot];
-        float psc[P], psh[P], plj[P][SM];
+    if (c.uni)
+        near_tile_uni2<SM, DU, DH>(Sx, L, cnt, q.gx, q.fy, q.fz, c.rn2, c.rs2, c.rcu2, c.tinv, tab, c.DC, c.c0h,
+                                   c.h0h, q.wlo, q.whi, c.rcull2, psc, psh, plj, q.hit, cnt3);
+    else
+        near_tile<2, SM, DU, DH, false>(Sx, L, cnt, q.gx, q.fy, q.fz, c.rn2, c.rs2, c.rcu2, c.tinv, tab, c.DC, c.c0h,
+                                        c.h0h, q.wlo, q.whi, c.rcull2, psc, psh, plj, q.hit, cnt3);
 #pragma unroll
-        for (int p = 0; p < P; ++p) {
-            psc[p] = psh[p] = 0.f;
+    for (int p = 0; p < 2; ++p) {
+        if (c.DC) ff_add(q.sch[p], q.scl[p], psc[p]);
+        if (DH) ff_add(q.shh[p], q.shl[p], psh[p]);
+        if (DU) {
 #pragma unroll
-            for (int s = 0; s < SM; ++s) plj[p][s] = 0.f;
-        }
-        bool done = false;
-        if constexpr (P == 2) {
-            if (a.uni_rc) {
-                near_tile_uni2<SM, DU, DH>(Sx, L, cnt, gx, fy, fz, rn2, rs2, rcu2, tinv, tab, DC, c0h, h0h, wlo, whi,
-                                           rcull2, psc, psh, plj, hit, cnt3);
-                done = true;
-            }
-        }
-        if (!done) {
-            if (a.uni_rc)
-                near_tile<P, SM, DU, DH, true>(Sx, L, cnt, gx, fy, fz, rn2, rs2, rcu2, tinv, tab, DC, c0h, h0h, wlo,
-                                               whi, rcull2, psc, psh, plj, hit, cnt3);
-            else
-                near_tile<P, SM, DU, DH, false>(Sx, L, cnt, gx, fy, fz, rn2, rs2, rcu2, tinv, tab, DC, c0h, h0h, wlo,
-                                                whi, rcull2, psc, psh, plj, hit, cnt3);
-        }
-#pragma unroll
-        for (int p = 0; p < P; ++p) {
-            if (DC) ff_add(sch[p], scl[p], psc[p]);
-            if (DH) ff_add(shh[p], shl[p], psh[p]);
-            if (DU) {
-#pragma unroll
-                for (int s = 0; s < SM; ++s) ff_add(ljh[p][s], ljl[p][s], plj[p][s]);
-            }
-        }
-    }, [](int) {});
-    if (rr != kRingDone) return;
-    {
-        unsigned long long c0 = cnt3[0], c1 = cnt3[1], c2 = cnt3[2];
-        for (int o = 16; o > 0; o >>= 1) {
-            c0 += __shfl_xor_sync(0xffffffffu, c0, o);
-            c1 += __shfl_xor_sync(0xffffffffu, c1, o);
-            c2 += __shfl_xor_sync(0xffffffffu, c2, o);
-        }
-        if ((tid & 31) == 0) {
-            atomicAdd(&a.meta->near_tested, c0);
-            atomicAdd(&a.meta->lj_pairs, c1);
-            atomicAdd(&a.meta->sr_pairs, c2);
+            for (int s = 0; s < SM; ++s) ff_add(q.ljh[p][s], q.ljl[p][s], plj[p][s]);
         }
     }
+}
 
+// Epilogue of one batch: the far-field sums of the point plus the near sums, assembled into u, c and h.
+template <int SM, bool DU, bool DH>
+__device__ __forceinline__ void near_finish(const NearPts<SM>& q, const NearConst& c, const EvalArgs& a) {
+    constexpr int P = 2;
     const GridD& g = a.g;
-    if (j >= g.ny || k >= g.nz || i0 >= g.nx) return;
+    const int i0 = q.i0;
+    if (q.j >= g.ny || q.k >= g.nz || i0 >= g.nx) return;
     const int64_t plane = (int64_t)g.nx * g.ny * g.nz;
-    const int64_t row = ((int64_t)k * g.ny + j) * g.nx;
+    const int64_t row = ((int64_t)q.k * g.ny + q.j) * g.nx;
     const bool vec_ok = (g.nx & 1) == 0;
     // Assembly in float pairs (error-free sums and products), one rounding to float per output, then the
     // float -> double conversion on the integer pipe: no FP64 arithmetic per grid point.
@@ -2151,18 +2234,16 @@ __device__ void near_body(const EvalArgs& a, int b, Ring<SM, true>& r, float4* t
         F1h[p] = f.x;
         F1l[p] = f.y;
         float s, e;
-        two_sum(f.x, -sch[p], s, e);  // Phi1 - S_c
-        DC_[p] = s + (e + (f.y - scl[p]));
+        two_sum(f.x, -q.sch[p], s, e);  // Phi1 - S_c
+        DC_[p] = s + (e + (f.y - q.scl[p]));
         const float ph_ = a.e2a_h * f.z;  // 2 e^{a^2} Phik - S_h
         const float pe = fmaf(a.e2a_h, f.z, -ph_) + (a.e2a_h * f.w + a.e2a_l * f.z);
-        two_sum(ph_, -shh[p], s, e);
-        DH_[p] = s + (e + (pe - shl[p]));
+        two_sum(ph_, -q.shh[p], s, e);
+        DH_[p] = s + (e + (pe - q.shl[p]));
     }
     auto store = [&](double* base, const float (&v)[P]) {
         if (vec_ok && i0 + P <= g.nx) {
-#pragma unroll
-            for (int p = 0; p < P; p += 2)
-                __stcs(reinterpret_cast<double2*>(base + i0 + p), make_double2(f2d_alu(v[p]), f2d_alu(v[p + 1])));
+            __stcs(reinterpret_cast<double2*>(base + i0), make_double2(f2d_alu(v[0]), f2d_alu(v[1])));
         } else {
 #pragma unroll
             for (int p = 0; p < P; ++p)
@@ -2180,12 +2261,12 @@ __device__ void near_body(const EvalArgs& a, int b, Ring<SM, true>& r, float4* t
                 const float pc = cuh * F1h[p];
                 const float pce = fmaf(cuh, F1h[p], -pc) + (cuh * F1l[p] + cul * F1h[p]);
                 float t, e;
-                two_sum(pc, ljh[p][s], t, e);
-                v[p] = (hit >> p & 1u) ? INFINITY : t + (e + (pce + ljl[p][s]));
+                two_sum(pc, q.ljh[p][s], t, e);
+                v[p] = (q.hit >> p & 1u) ? INFINITY : t + (e + (pce + q.ljl[p][s]));
             }
             store(a.o.u + s * plane + row, v);
         }
-        if (DC) {
+        if (c.DC) {
 #pragma unroll
             for (int p = 0; p < P; ++p) v[p] = a.cc[s] * DC_[p];
             store(a.o.c + s * plane + row, v);
@@ -2196,6 +2277,71 @@ __device__ void near_body(const EvalArgs& a, int b, Ring<SM, true>& r, float4* t
             store(a.o.h + s * plane + row, v);
         }
     }
+}
+
+// Diagnostic pair counts, one global update per CTA: each consumer warp adds its counts in shared memory, the
+// last warp to arrive publishes the CTA's totals (when nonzero).  r.stat / r.stat_warps start at zero.
+template <int NW, typename R>
+__device__ __forceinline__ void near_publish(R& r, TreeMeta* meta, const unsigned (&cnt3)[3]) {
+    unsigned long long c0 = cnt3[0], c1 = cnt3[1], c2 = cnt3[2];
+    for (int o = 16; o > 0; o >>= 1) {
+        c0 += __shfl_xor_sync(0xffffffffu, c0, o);
+        c1 += __shfl_xor_sync(0xffffffffu, c1, o);
+        c2 += __shfl_xor_sync(0xffffffffu, c2, o);
+    }
+    if ((threadIdx.x & 31) == 0) {
+        if (c0) {
+            atomicAdd(&r.stat[0], c0);
+            atomicAdd(&r.stat[1], c1);
+            atomicAdd(&r.stat[2], c2);
+        }
+        __threadfence_block();
+        if (atomicAdd(&r.stat_warps, 1) == NW - 1) {
+            __threadfence_block();
+            const unsigned long long t0 = atomicAdd(&r.stat[0], 0ull), t1 = atomicAdd(&r.stat[1], 0ull),
+                                     t2 = atomicAdd(&r.stat[2], 0ull);
+            if (t0) {
+                atomicAdd(&meta->near_tested, t0);
+                atomicAdd(&meta->lj_pairs, t1);
+                atomicAdd(&meta->sr_pairs, t2);
+            }
+        }
+    }
+}
+
+// One work item (sub-batch `sub` of batch b) with its own ring setup: the body of the persistent batched
+// kernel, whose consecutive items may belong to different solutes.
+template <int NXB, int NYB, int NZB, int SM, bool DU, bool DH>
+__device__ void near_body(const EvalArgs& a, int b, int sub, Ring<SM, true>& r, float4* tab) {
+    using Sh = NearShape<NXB, NYB, NZB>;
+    const int tid = threadIdx.x;
+    const NearConst c = near_const(a);
+    NearPts<SM> q;
+    unsigned cnt3[3] = {0u, 0u, 0u};  // pairs tested / inside the LJ cut-off / inside r_short
+    Cursor cur;
+    __syncthreads();
+    for (int k = tid; k < 2 * kNTab; k += blockDim.x) tab[k] = a.ntab[k];
+    if (tid == Sh::NT) {
+        cur.e = b * a.near_cap;
+        cur.e_end = cur.e + a.near_cnt[b];
+        cur.off = 0;
+        cur.left = INT_MAX;
+        cur.produced = 0;
+        cur.done = false;
+        for (int s = 0; s < kStages; ++s) cur.last_phase[s] = -1;
+        ring_init(r, Sh::NW);
+        r.stat[0] = r.stat[1] = r.stat[2] = 0ull;
+        r.stat_warps = 0;
+    }
+    __syncthreads();
+    if (tid < Sh::NT) near_begin<NXB, NYB, NZB, SM>(q, a, b, sub);
+    const LJf* ljt = c.uni ? a.ljs2 : a.ljs;  // the two-wide tile reads {A, A, -B, -B}
+    const int rr = run_ring<SM, true, Sh::NW>(r, cur, a.near_ent, a.srcf, ljt, a, [&](int slot, int cnt) {
+        near_stage<SM, DU, DH>(q, c, r.src[slot], r.lj[slot], cnt, tab, cnt3);
+    }, [](int) {});
+    if (rr != kRingDone) return;
+    near_publish<Sh::NW>(r, a.meta, cnt3);
+    near_finish<SM, DU, DH>(q, c, a);
 }
 
 // ---- per-solute kernels: one CTA per target batch
@@ -2215,14 +2361,59 @@ struct NearOcc {
     static constexpr int v = SM <= 4 ? ((DU && DH) ? 2 : 3) : 1;
 };
 
+// Work queue of a persistent kernel: wq[0] counts the items taken, wq[1] the CTAs whose producer takes no more.
+// The last CTA to leave resets both, so every launch (and every replay of a captured one) starts from zero.
+__device__ __forceinline__ void queue_leave(int* wq) {
+    __threadfence();
+    if (atomicAdd(&wq[1], 1) == (int)gridDim.x - 1) {
+        atomicExch(&wq[0], 0);
+        atomicExch(&wq[1], 0);
+    }
+}
+
+// Persistent near-field kernel of one solute: the producer of each CTA takes the next item (sub-batch) of the
+// heaviest-first order from the work queue and streams the near lists of its items through one ring
+// (run_stream), so the per-batch setup and epilogue overlap the loading of the next batch's sources.
 template <int NXB, int NYB, int NZB, int SM, bool DU, bool DH>
 __global__ void __launch_bounds__(NearShape<NXB, NYB, NZB>::NTP, (NearOcc<NXB, NYB, NZB, SM, DU, DH>::v))
-    k_near32(EvalArgs a) {
+    k_near32(const __grid_constant__ EvalArgs a) {
+    using Sh = NearShape<NXB, NYB, NZB>;
+    constexpr int NS = Sh::NSUB;
     __shared__ Ring<SM, true> r;
     __shared__ float4 tab[2 * kNTab];
-    if (threadIdx.x == 0) r.inited = 0;
-    if (a.meta->overflow) return;
-    near_body<NXB, NYB, NZB, SM, DU, DH>(a, a.near_order[blockIdx.x], r, tab);
+    const int tid = threadIdx.x;
+    if (a.meta->overflow) {  // incomplete lists: the host grows them and runs again
+        if (tid == Sh::NT) queue_leave(a.wq);
+        return;
+    }
+    for (int k = tid; k < 2 * kNTab; k += blockDim.x) tab[k] = a.ntab[k];
+    if (tid == Sh::NT) {
+        r.inited = 0;
+        ring_init(r, Sh::NW);
+        r.stat[0] = r.stat[1] = r.stat[2] = 0ull;
+        r.stat_warps = 0;
+    }
+    __syncthreads();
+    const int total = a.nbx * a.nby * a.nbz * NS;
+    const NearConst c = near_const(a);
+    const LJf* ljt = c.uni ? a.ljs2 : a.ljs;  // the two-wide tile reads {A, A, -B, -B}
+    NearPts<SM> q;
+    unsigned cnt3[3] = {0u, 0u, 0u};  // pairs tested / inside the LJ cut-off / inside r_short
+    const int rr = run_stream<SM, true, Sh::NW>(
+        r, a.wlim, a.err,
+        [&](int, int& item, ItemSrc& is) {
+            const int qi = atomicAdd(&a.wq[0], 1);  // next position of the heaviest-first order
+            if (qi >= total) return false;
+            const int b = a.near_order[qi / NS];
+            item = b * NS + qi % NS;
+            is = ItemSrc{a.near_ent, b * a.near_cap, b * a.near_cap + a.near_cnt[b], a.srcf, ljt};
+            return true;
+        },
+        [&](int item) { near_begin<NXB, NYB, NZB, SM>(q, a, item / NS, item % NS); },
+        [&](int slot, int cnt) { near_stage<SM, DU, DH>(q, c, r.src[slot], r.lj[slot], cnt, tab, cnt3); },
+        [&](int) { near_finish<SM, DU, DH>(q, c, a); });
+    if (rr == kRingDone) near_publish<Sh::NW>(r, a.meta, cnt3);
+    if (tid == Sh::NT) queue_leave(a.wq);
 }
 
 // ---- persistent kernels over the (solute, batch) items of many solutes
@@ -2278,16 +2469,19 @@ __global__ void __launch_bounds__(FarShape<NXB, NYB, NZB, PF>::NTP) k_far32_batc
 template <int NXB, int NYB, int NZB, int SM, bool DU, bool DH>
 __global__ void __launch_bounds__(NearShape<NXB, NYB, NZB>::NTP, (NearOcc<NXB, NYB, NZB, SM, DU, DH>::v))
     k_near32_batched(BatchEval be) {
+    constexpr int NS = NearShape<NXB, NYB, NZB>::NSUB;
     __shared__ Ring<SM, true> r;
     __shared__ float4 tab[2 * kNTab];
-    __shared__ int s_item;
+    __shared__ int s_item, s_sub;
     __shared__ EvalArgs sa;
     if (threadIdx.x == 0) r.inited = 0;
     for (;;) {
         __syncthreads();
         if (threadIdx.x == 0) {
+            // queue position q: sub-batch q % NS of the item at order position q / NS
             const int q = atomicAdd(be.queue, 1);
-            s_item = q < be.total ? be.order[q] : be.total;
+            s_item = q < be.total * NS ? be.order[q / NS] : be.total;
+            s_sub = q % NS;
             if (s_item < be.total) sa = be.args[find_solute(be, s_item)];
         }
         __syncthreads();
@@ -2295,7 +2489,7 @@ __global__ void __launch_bounds__(NearShape<NXB, NYB, NZB>::NTP, (NearOcc<NXB, N
         if (it >= be.total) break;
         if (sa.meta->overflow) continue;
         const int sid = find_solute(be, it);
-        near_body<NXB, NYB, NZB, SM, DU, DH>(sa, it - be.item_off[sid], r, tab);
+        near_body<NXB, NYB, NZB, SM, DU, DH>(sa, it - be.item_off[sid], s_sub, r, tab);
     }
 }
 
@@ -2307,6 +2501,8 @@ struct VShape {
     static constexpr int FT = FarShape<NX, NY, NZ, PF>::NTP, NTN = NearShape<NX, NY, NZ>::NTP;
 };
 
+int sm_count();
+
 template <int V, int SM, bool DU, bool DH>
 struct Kern {
     using S = VShape<V>;
@@ -2314,7 +2510,14 @@ struct Kern {
         k_far32<S::NX, S::NY, S::NZ, S::PF, DH><<<nb, S::FT, 0, st>>>(a);
     }
     static void near(const EvalArgs& a, int nb, cudaStream_t st) {
-        k_near32<S::NX, S::NY, S::NZ, SM, DU, DH><<<nb, S::NTN, 0, st>>>(a);
+        // persistent: at most the CTAs that are resident at once
+        static const int resident = [] {
+            int b = 0;
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_near32<S::NX, S::NY, S::NZ, SM, DU, DH>, S::NTN, 0);
+            return std::max(1, b) * sm_count();
+        }();
+        const int items = nb * NearShape<S::NX, S::NY, S::NZ>::NSUB;
+        k_near32<S::NX, S::NY, S::NZ, SM, DU, DH><<<std::max(1, std::min(items, resident)), S::NTN, 0, st>>>(a);
     }
     static void far_b(const BatchEval& be, int grid, cudaStream_t st) {
         k_far32_batched<S::NX, S::NY, S::NZ, S::PF, DH><<<grid, S::FT, 0, st>>>(be);
@@ -2403,6 +2606,7 @@ struct TreeState {
     int64_t cap_far_pts = 0;
     int *far_cnt = nullptr, *near_cnt = nullptr, *prox_items = nullptr, *near_work = nullptr, *near_order = nullptr;
     int *far_work = nullptr, *far_order = nullptr;
+    int* wq = nullptr;  // work-queue counters of the persistent near kernel
     int2 *far_ent = nullptr, *near_ent = nullptr;
     int* cell_start = nullptr;
     TreeMeta* meta = nullptr;
@@ -2501,6 +2705,10 @@ rism_status tree_reserve(TreeState* s, const DevTables& t, const GridD& g, const
     if (M > s->cap_far_pts) {
         if ((e = regrow(s->far, (size_t)M))) return cuda_err(err, e, "far-field buffer");
         s->cap_far_pts = M;
+    }
+    if (!s->wq) {
+        if ((e = cudaMalloc(&s->wq, 2 * sizeof(int))) || (e = cudaMemset(s->wq, 0, 2 * sizeof(int))))
+            return cuda_err(err, e, "work queue");
     }
     if (s->nb + 1 > s->cap_nb) {
         if ((e = regrow(s->far_cnt, (size_t)s->nb + 1)) || (e = regrow(s->near_cnt, (size_t)s->nb + 1)) ||
@@ -2739,6 +2947,7 @@ EvalArgs make_args(TreeState* s, const DevTables& t, const GridD& g, const Phys&
     a.ntab_inv = s->ntab_inv;
     a.uni_rc = o.lj_mode != RISM_LJ_TOL ? 1 : 0;
     a.near_order = s->near_order;
+    a.wq = s->wq;
     a.far_order = s->far_order;
     a.near_work = s->near_work;
     a.far_work = s->far_work;
@@ -2904,6 +3113,7 @@ void tree_destroy(TreeState* s) {
     cudaFree(s->near_cnt);
     cudaFree(s->near_work);
     cudaFree(s->near_order);
+    cudaFree(s->wq);
     cudaFree(s->far_work);
     cudaFree(s->far_order);
     cudaFree(s->prox_items);
