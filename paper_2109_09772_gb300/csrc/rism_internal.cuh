@@ -179,15 +179,29 @@ __device__ __forceinline__ void ff_add(float& hi, float& lo, float v) {
     lo += t;
 }
 
-// float -> double by assembling the IEEE-754 fields on the integer pipe (the FP64 pipe of this part is slow):
-// sign, exponent rebiased by 1023 - 127 = 896, fraction shifted left by 52 - 23 = 29.  Zero, subnormals,
-// infinities and NaN take the conversion instruction.
+// float -> double on the integer pipe (the FP64 pipe of this part is slow).  Normal numbers: sign, exponent
+// rebiased by 1023 - 127 = 896, fraction shifted left by 52 - 23 = 29.  The rare rest, out of line so that the
+// common path stays short: all-ones exponent (infinity, NaN) kept all-ones, zero kept zero, a subnormal
+// m 2^-149 renormalised from the position p of its leading bit as 2^(p - 149) (1 + f).
+static __device__ __noinline__ double f2d_special(uint32_t b) {
+    const uint32_t e = (b >> 23) & 0xffu, m = b & 0x7fffffu;
+    const unsigned long long sign = (unsigned long long)(b >> 31) << 63;
+    unsigned long long r;
+    if (e == 0xffu) {
+        r = sign | (0x7ffull << 52) | ((unsigned long long)m << 29);
+    } else if (m == 0u) {
+        r = sign;
+    } else {
+        const int p = 31 - __clz((int)m);
+        r = sign | ((unsigned long long)(p + 874) << 52) | (((unsigned long long)m << (52 - p)) & 0xfffffffffffffull);
+    }
+    return __longlong_as_double((long long)r);
+}
 __device__ __forceinline__ double f2d_alu(float f) {
     const uint32_t b = __float_as_uint(f);
     const uint32_t e = (b >> 23) & 0xffu;
-    if (e == 0u || e == 0xffu) return (double)f;
-    const unsigned long long r = ((unsigned long long)(b >> 31) << 63) |
-                                 ((unsigned long long)(e + 896u) << 52) |
+    if (__builtin_expect(e - 1u >= 254u, 0)) return f2d_special(b);
+    const unsigned long long r = ((unsigned long long)(b >> 31) << 63) | ((unsigned long long)(e + 896u) << 52) |
                                  ((unsigned long long)(b & 0x7fffffu) << 29);
     return __longlong_as_double((long long)r);
 }

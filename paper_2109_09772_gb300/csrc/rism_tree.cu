@@ -50,6 +50,7 @@ namespace rism {
 namespace {
 
 constexpr int kSortThreads = 1024;
+constexpr int kSortSmem = 4096;  // atoms sorted in shared memory (64-bit keys and the sorted codes: 48 KB)
 constexpr int kMortonBits = 10;          // per axis
 constexpr int kMaxLevel = kMortonBits;   // octree depth limit
 constexpr int kChunk = 16;               // atoms per upward-pass work item
@@ -276,7 +277,7 @@ struct BuildArgs {
     int smax;
     GridD gd;
     double ih;             // 1 / h
-    Geo* src;              // out: sorted FP64 grid units
+    Geo* src;              // out: sorted FP64 grid units (null: not needed)
     SrcF* ssrcf;           // out: sorted float-float
     LJf* ljs;              // out: sorted LJ tables
     LJf* ljs2;             // out: the same as {A, A, -B, -B} (two-wide operands of the near field)
@@ -318,56 +319,90 @@ __global__ void __launch_bounds__(kSortThreads) k_sort_build(BuildArgs a, uint32
     constexpr int NW = kSortThreads / 32;
     const int seg = ((n + NW - 1) / NW + 31) / 32 * 32;
     const int s0 = min(n, w * seg), s1 = min(n, s0 + seg);
-    uint32_t *kin = code, *vin = idx, *kout = code2, *vout = idx2;
-    for (int pass = 0; pass < 4; ++pass) {
-        const int shift = 8 * pass;
-        for (int k = threadIdx.x; k < 256 * NW; k += blockDim.x) hist[k] = 0;
+    // up to kSortSmem atoms: a bitonic sort in shared memory of the 64-bit keys (code << 32 | index), unique,
+    // so the order is that of the stable radix sort; the sorted codes stay there for the octree's searches.
+    // Above that: the stable LSD radix sort through global memory.
+    const bool in_smem = n <= kSortSmem;
+    unsigned long long* sk = reinterpret_cast<unsigned long long*>(sh + 256 * 32 + 64);  // [kSortSmem]
+    uint32_t* sc = reinterpret_cast<uint32_t*>(sk + kSortSmem);                          // [kSortSmem]
+    if (in_smem) {
+        int N = 1;
+        while (N < n) N <<= 1;
+        for (int i = threadIdx.x; i < N; i += blockDim.x)
+            sk[i] = i < n ? ((unsigned long long)code[i] << 32) | idx[i] : ~0ull;
         __syncthreads();
-        for (int b = s0; b < s1; b += 32) {
-            int i = b + lane;
-            if (i < s1) atomicAdd(&hist[((kin[i] >> shift) & 255u) * NW + w], 1);
+        for (int k = 2; k <= N; k <<= 1)
+            for (int j = k >> 1; j > 0; j >>= 1) {
+                for (int t = threadIdx.x; t < N / 2; t += blockDim.x) {
+                    const int i = ((t & ~(j - 1)) << 1) | (t & (j - 1)), l = i + j;
+                    const unsigned long long x = sk[i], y = sk[l];
+                    if ((x > y) == ((i & k) == 0)) {
+                        sk[i] = y;
+                        sk[l] = x;
+                    }
+                }
+                __syncthreads();
+            }
+        for (int i = threadIdx.x; i < n; i += blockDim.x) {
+            const unsigned long long v = sk[i];
+            sc[i] = code[i] = (uint32_t)(v >> 32);
+            idx[i] = (uint32_t)v;
         }
         __syncthreads();
-        // exclusive scan of hist in (digit, warp) order: 8192 entries, 8 per thread
-        {
-            int loc[8], sum = 0;
-            for (int k = 0; k < 8; ++k) {
-                loc[k] = hist[threadIdx.x * 8 + k];
-                sum += loc[k];
+    } else {
+        uint32_t *kin = code, *vin = idx, *kout = code2, *vout = idx2;
+        for (int pass = 0; pass < 4; ++pass) {
+            const int shift = 8 * pass;
+            for (int k = threadIdx.x; k < 256 * NW; k += blockDim.x) hist[k] = 0;
+            __syncthreads();
+            for (int b = s0; b < s1; b += 32) {
+                int i = b + lane;
+                if (i < s1) atomicAdd(&hist[((kin[i] >> shift) & 255u) * NW + w], 1);
             }
-            int total;
-            int base = block_exclusive_scan(sum, tmp, total);
-            for (int k = 0; k < 8; ++k) {
-                hist[threadIdx.x * 8 + k] = base;
-                base += loc[k];
+            __syncthreads();
+            // exclusive scan of hist in (digit, warp) order: 8192 entries, 8 per thread
+            {
+                int loc[8], sum = 0;
+                for (int k = 0; k < 8; ++k) {
+                    loc[k] = hist[threadIdx.x * 8 + k];
+                    sum += loc[k];
+                }
+                int total;
+                int base = block_exclusive_scan(sum, tmp, total);
+                for (int k = 0; k < 8; ++k) {
+                    hist[threadIdx.x * 8 + k] = base;
+                    base += loc[k];
+                }
             }
+            __syncthreads();
+            for (int b = s0; b < s1; b += 32) {
+                int i = b + lane;
+                bool act = i < s1;
+                uint32_t key = act ? kin[i] : 0u, val = act ? vin[i] : 0u;
+                uint32_t d = act ? ((key >> shift) & 255u) : 256u + lane;  // inactive lanes never match
+                unsigned peers = __match_any_sync(0xffffffffu, d);
+                int rank = __popc(peers & ((1u << lane) - 1u));
+                int base = act ? hist[d * NW + w] : 0;
+                if (act) {
+                    kout[base + rank] = key;
+                    vout[base + rank] = val;
+                }
+                __syncwarp();
+                if (act && rank == 0) hist[d * NW + w] = base + __popc(peers);
+                __syncwarp();
+            }
+            __syncthreads();
+            uint32_t* t1 = kin; kin = kout; kout = t1;
+            uint32_t* t2 = vin; vin = vout; vout = t2;
         }
-        __syncthreads();
-        for (int b = s0; b < s1; b += 32) {
-            int i = b + lane;
-            bool act = i < s1;
-            uint32_t key = act ? kin[i] : 0u, val = act ? vin[i] : 0u;
-            uint32_t d = act ? ((key >> shift) & 255u) : 256u + lane;  // inactive lanes never match
-            unsigned peers = __match_any_sync(0xffffffffu, d);
-            int rank = __popc(peers & ((1u << lane) - 1u));
-            int base = act ? hist[d * NW + w] : 0;
-            if (act) {
-                kout[base + rank] = key;
-                vout[base + rank] = val;
-            }
-            __syncwarp();
-            if (act && rank == 0) hist[d * NW + w] = base + __popc(peers);
-            __syncwarp();
-        }
-        __syncthreads();
-        uint32_t* t1 = kin; kin = kout; kout = t1;
-        uint32_t* t2 = vin; vin = vout; vout = t2;
+        // after 4 passes the sorted data is back in code/idx
     }
-    // after 4 passes the sorted data is back in code/idx
-    // ---- sorted copies of the sources (FP64 grid units, float-float) and LJ tables
+    const uint32_t* scode = in_smem ? sc : code;  // sorted codes for the searches below
+    // ---- sorted copies of the sources (FP64 grid units when the source proxies need them, float-float) and
+    // LJ tables
     for (int i = threadIdx.x; i < n; i += blockDim.x) {
         const int j = (int)idx[i];
-        a.src[i] = to_grid(a.geo[j], a.gd, a.ih);
+        if (a.src) a.src[i] = to_grid(a.geo[j], a.gd, a.ih);
         a.ssrcf[i] = a.srcf[j];
         for (int s = 0; s < a.smax; ++s) {
             const LJf l = a.ljf[(int64_t)j * a.smax + s];
@@ -408,7 +443,7 @@ __global__ void __launch_bounds__(kSortThreads) k_sort_build(BuildArgs a, uint32
                         int lo = cb[ch - 1], hi = nd.end;
                         while (lo < hi) {
                             int mid = (lo + hi) >> 1;
-                            if ((int)((code[mid] >> sh3) & 7u) < ch) lo = mid + 1; else hi = mid;
+                            if ((int)((scode[mid] >> sh3) & 7u) < ch) lo = mid + 1; else hi = mid;
                         }
                         cb[ch] = lo;
                     }
@@ -1142,6 +1177,9 @@ struct EvalArgs {
     // u = cu Phi1 + LJ, c = cc (Phi1 - S_c), h = ch (2 e^{a^2} Phik - S_h)
     float cu_h[kMaxSites], cu_l[kMaxSites], cc[kMaxSites], ch[kMaxSites];
     float e2a_h, e2a_l;
+    // FP32 constants of the kernels, rounded once on the host (no FP64 instruction in the kernels):
+    float kap2;           // -kappa h log2(e): e^{-kappa d} = 2^(kap2 d_grid)
+    float rs2, c0h, h0h;  // (r_short / h)^2; the d -> 0 limits of the two short-range kernels times h
     Outputs o;
     DevErr* err;
     TreeMeta* meta;
@@ -1303,10 +1341,11 @@ struct ItemSrc {
 // last one flagged; an item without sources gets one empty tile), so the next item's sources load while the
 // consumer warps finish the previous one.  next(n, item, src) gives the CTA's n-th item (false: none left);
 // each consumer warp calls begin(item) before the item's first tile, stage(slot, cnt) per tile (before the slot
-// is released), and finish(item) after its last tile.  The ring barriers are initialised once per launch.
+// is released) and consume(cnt) after the release, and finish(item) after the item's last tile.  The ring barriers are initialised once per launch.
 // Waits are bounded as in run_ring.
-template <int SM, bool LJ, int NWARPS, typename R, typename FN, typename FB, typename FS, typename FF>
-__device__ int run_stream(R& r, long long wlim, DevErr* err, FN&& next, FB&& begin, FS&& stage, FF&& finish) {
+template <int SM, bool LJ, int NWARPS, typename R, typename FN, typename FB, typename FS, typename FC, typename FF>
+__device__ int run_stream(R& r, long long wlim, DevErr* err, FN&& next, FB&& begin, FS&& stage, FC&& consume,
+                          FF&& finish) {
     const int tid = threadIdx.x, lane = tid & 31;
     volatile int* abort_flag = &r.abort;
     if (tid >= NWARPS * 32) {
@@ -1372,6 +1411,7 @@ __device__ int run_stream(R& r, long long wlim, DevErr* err, FN&& next, FB&& beg
         if (cnt > 0) stage(slot, cnt);
         __syncwarp();
         if (lane == 0) mbar_arrive(&r.empty[slot]);
+        if (cnt > 0) consume(cnt);
         if (last) {
             finish(item);
             open = false;
@@ -1455,36 +1495,96 @@ __device__ __forceinline__ void far_pairs(const PairRec* wp, int np, const f32x2
     }
 }
 
+// Points of a far-field thread in one target batch (PF consecutive points along x) and their float-pair sums.
+template <int PF>
+struct FarPts {
+    int i0, j, k;
+    f32x2 GX[PF], FY, FZ;
+    float f1h[PF], f1l[PF], fkh[PF], fkl[PF];
+    bool on;  // some source of the current tile sits on a lattice point
+};
+
+// Points of batch b; the sums start from the box-level field already in `far` when a.far_init.
+template <int NXB, int NYB, int NZB, int PF>
+__device__ __forceinline__ void far_begin(FarPts<PF>& q, const EvalArgs& a, int b) {
+    using Sh = FarShape<NXB, NYB, NZB, PF>;
+    const int tid = threadIdx.x;
+    const int tx = tid % Sh::TX, ty = (tid / Sh::TX) % NYB, tz = tid / (Sh::TX * NYB);
+    const int ib = b % a.nbx, jb = (b / a.nbx) % a.nby, kb = b / (a.nbx * a.nby);
+    q.i0 = ib * NXB + tx * PF;
+    q.j = jb * NYB + ty;
+    q.k = kb * NZB + tz;
+#pragma unroll
+    for (int p = 0; p < PF; ++p)
+        q.GX[p] = pk2((float)(q.i0 + p), (float)(q.i0 + p));
+    q.FY = pk2((float)q.j, (float)q.j);
+    q.FZ = pk2((float)q.k, (float)q.k);
+#pragma unroll
+    for (int p = 0; p < PF; ++p) q.f1h[p] = q.f1l[p] = q.fkh[p] = q.fkl[p] = 0.f;
+    q.on = false;
+    if (a.far_init && q.j < a.g.ny && q.k < a.g.nz) {
+        const float4* src0 = a.far + ((int64_t)q.k * a.g.ny + q.j) * a.g.nx;
+#pragma unroll
+        for (int p = 0; p < PF; ++p)
+            if (q.i0 + p < a.g.nx) {
+                const float4 v = src0[q.i0 + p];
+                q.f1h[p] = v.x;
+                q.f1l[p] = v.y;
+                q.fkh[p] = v.z;
+                q.fkl[p] = v.w;
+            }
+    }
+}
+
+// The pair records of one tile (before the slot is released) ...
+__device__ __forceinline__ void far_stage(bool& on, const SrcF* Sx, int cnt, PairRec* wp) {
+    __syncwarp();  // the previous tile's records are no longer read
+    on = stage_pairs(Sx, cnt, wp, threadIdx.x & 31);
+}
+
+// ... and their pairs with the thread's points, folded into its sums.
+template <int PF, bool DH>
+__device__ __forceinline__ void far_consume(FarPts<PF>& q, const PairRec* wp, int cnt, f32x2 K2) {
+    f32x2 P1[PF], PK[PF];
+#pragma unroll
+    for (int p = 0; p < PF; ++p) P1[p] = PK[p] = 0ull;  // +0.0f in both halves
+    const int np = (cnt + 1) >> 1;
+    if (!q.on)
+        far_pairs<PF, DH, false>(wp, np, q.GX, q.FY, q.FZ, K2, P1, PK);
+    else
+        far_pairs<PF, DH, true>(wp, np, q.GX, q.FY, q.FZ, K2, P1, PK);
+#pragma unroll
+    for (int p = 0; p < PF; ++p) {
+        const float2 s1 = up2(P1[p]);
+        ff_add(q.f1h[p], q.f1l[p], s1.x + s1.y);
+        if (DH) {
+            const float2 sk = up2(PK[p]);
+            ff_add(q.fkh[p], q.fkl[p], sk.x + sk.y);
+        }
+    }
+}
+
+template <int PF>
+__device__ __forceinline__ void far_finish(const FarPts<PF>& q, const EvalArgs& a) {
+    const GridD& g = a.g;
+    if (q.j >= g.ny || q.k >= g.nz || q.i0 >= g.nx) return;
+    float4* dst = a.far + ((int64_t)q.k * g.ny + q.j) * g.nx;
+#pragma unroll
+    for (int p = 0; p < PF; ++p)
+        if (q.i0 + p < g.nx) dst[q.i0 + p] = make_float4(q.f1h[p], q.f1l[p], q.fkh[p], q.fkl[p]);
+}
+
+__device__ __forceinline__ f32x2 far_k2(const EvalArgs& a) { return pk2(a.kap2, a.kap2); }
+
+// One batch with its own ring setup: the body of the persistent batched kernel.
 template <int NXB, int NYB, int NZB, int PF, bool DH>
 __device__ void far_body(const EvalArgs& a, int b, Ring<1, false>& r, PairRec (*pairs)[kPairs]) {
     using Sh = FarShape<NXB, NYB, NZB, PF>;
-    constexpr int P = PF;
-    const int tid = threadIdx.x, lane = tid & 31;
-    const int tx = tid % Sh::TX, ty = (tid / Sh::TX) % NYB, tz = tid / (Sh::TX * NYB);
-    const int ib = b % a.nbx, jb = (b / a.nbx) % a.nby, kb = b / (a.nbx * a.nby);
-    const int i0 = ib * NXB + tx * P, j = jb * NYB + ty, k = kb * NZB + tz;
-    f32x2 GX[P];
-#pragma unroll
-    for (int p = 0; p < P; ++p) GX[p] = pk2((float)(i0 + p), (float)(i0 + p));
-    const f32x2 FY = pk2((float)j, (float)j), FZ = pk2((float)k, (float)k);
-    const float kap2 = (float)(-a.ph.kappa * a.g.h * 1.4426950408889634);  // e^{-kappa d} = 2^(kap2 d_grid)
-    const f32x2 K2 = pk2(kap2, kap2);
+    const int tid = threadIdx.x;
+    const f32x2 K2 = far_k2(a);
     PairRec* wp = pairs[tid >> 5];
-    float f1h[P], f1l[P], fkh[P], fkl[P];
-#pragma unroll
-    for (int p = 0; p < P; ++p) f1h[p] = f1l[p] = fkh[p] = fkl[p] = 0.f;
-    if (a.far_init && tid < Sh::NT && j < a.g.ny && k < a.g.nz) {
-        const float4* src0 = a.far + ((int64_t)k * a.g.ny + j) * a.g.nx;
-#pragma unroll
-        for (int p = 0; p < P; ++p)
-            if (i0 + p < a.g.nx) {
-                const float4 v = src0[i0 + p];
-                f1h[p] = v.x;
-                f1l[p] = v.y;
-                fkh[p] = v.z;
-                fkl[p] = v.w;
-            }
-    }
+    FarPts<PF> q;
+    if (tid < Sh::NT) far_begin<NXB, NYB, NZB, PF>(q, a, b);
     Cursor cur;
     __syncthreads();
     if (tid == Sh::NT) {
@@ -1498,39 +1598,11 @@ __device__ void far_body(const EvalArgs& a, int b, Ring<1, false>& r, PairRec (*
         ring_init(r, Sh::NW);
     }
     __syncthreads();
-    bool on = false;
     const int rr = run_ring<1, false, Sh::NW>(
-        r, cur, a.far_ent, a.srcf, nullptr, a,
-        [&](int slot, int cnt) {
-            __syncwarp();  // the previous tile's records are no longer read
-            on = stage_pairs(r.src[slot], cnt, wp, lane);
-        },
-        [&](int cnt) {
-            f32x2 P1[P], PK[P];
-#pragma unroll
-            for (int p = 0; p < P; ++p) P1[p] = PK[p] = 0ull;  // +0.0f in both halves
-            const int np = (cnt + 1) >> 1;
-            if (!on)
-                far_pairs<P, DH, false>(wp, np, GX, FY, FZ, K2, P1, PK);
-            else
-                far_pairs<P, DH, true>(wp, np, GX, FY, FZ, K2, P1, PK);
-#pragma unroll
-            for (int p = 0; p < P; ++p) {
-                const float2 s1 = up2(P1[p]);
-                ff_add(f1h[p], f1l[p], s1.x + s1.y);
-                if (DH) {
-                    const float2 sk = up2(PK[p]);
-                    ff_add(fkh[p], fkl[p], sk.x + sk.y);
-                }
-            }
-        });
+        r, cur, a.far_ent, a.srcf, nullptr, a, [&](int slot, int cnt) { far_stage(q.on, r.src[slot], cnt, wp); },
+        [&](int cnt) { far_consume<PF, DH>(q, wp, cnt, K2); });
     if (rr != kRingDone) return;
-    const GridD& g = a.g;
-    if (j >= g.ny || k >= g.nz || i0 >= g.nx) return;
-    float4* dst = a.far + ((int64_t)k * g.ny + j) * g.nx;
-#pragma unroll
-    for (int p = 0; p < P; ++p)
-        if (i0 + p < g.nx) dst[i0 + p] = make_float4(f1h[p], f1l[p], fkh[p], fkl[p]);
+    far_finish<PF>(q, a);
 }
 
 // ---- box-level far field: accepted clusters summed at the Chebyshev proxy targets of each target box,
@@ -1672,9 +1744,10 @@ __global__ void __launch_bounds__(kCPThreads + 32) k_cp_eval(EvalArgs a, CPArgs 
     }
     const float uy = hy * c.tb.ck[ky], uz = hz * c.tb.ck[kz];
     const f32x2 FY = pk2(uy, uy), FZ = pk2(uz, uz);
-    const float kap2 = (float)(-a.ph.kappa * a.g.h * 1.4426950408889634);
-    const f32x2 K2 = pk2(kap2, kap2);
-    const float cx = (float)T.c[0], cy = (float)T.c[1], cz = (float)T.c[2];
+    const f32x2 K2 = pk2(a.kap2, a.kap2);
+    // box centre lo + (ext - 1) / 2: exact in FP32 (the same value as the FP64 centre)
+    const float cx = (float)T.lo[0] + 0.5f * (float)(T.ext[0] - 1), cy = (float)T.lo[1] + 0.5f * (float)(T.ext[1] - 1),
+                cz = (float)T.lo[2] + 0.5f * (float)(T.ext[2] - 1);
     RelRec* wp = pairs[tid >> 5];
     float f1h[kCPP], f1l[kCPP], fkh[kCPP], fkl[kCPP];
 #pragma unroll
@@ -1938,7 +2011,17 @@ struct NearShape {
     static constexpr int P = 2, SX = NXB < 8 ? NXB : 8, NSUB = NXB / SX, TX = SX / P, NT = TX * NYB * NZB,
                          NW = NT / 32, NTP = NT + 32;  // + producer
     static_assert(NXB % SX == 0, "near sub-batches tile the batch along x");
+    static_assert(NW <= 16, "the per-warp source lists of the near tile hold 16 warps");
 };
+
+// Segment index and offset of u in [0, kNTab] (up to rounding) for the cubic pieces, without conversion
+// instructions: adding 1.5 2^23 leaves round(u - 1/2) (ties to even) in the low bits of the sum, and the sum
+// minus 1.5 2^23 is that integer as a float.  A tie gives the lower segment at offset 1, its end point.
+__device__ __forceinline__ float seg_split(float u, int& it) {
+    const float sh = (u - 0.5f) + 12582912.0f;
+    it = min(__float_as_int(sh) - 0x4B400000, kNTab - 1);
+    return u - fminf(sh - 12582912.0f, (float)(kNTab - 1));
+}
 
 // One tile of near-field sources against the P points of a thread: LJ within the pair cut-offs (UNI: one
 // cut-off for every pair, tested once per pair instead of once per site) and the short-range remainders of
@@ -1988,8 +2071,8 @@ __device__ __forceinline__ void near_tile(const SrcF* __restrict__ Sx, const LJf
                     const float ri = rsqrt_approx(d2);
                     const float qr = g0.w * ri;
                     const float uu = d2 * ri * tinv;
-                    const int it = min((int)uu, kNTab - 1);
-                    const float tt = uu - (float)it;
+                    int it;
+                    const float tt = seg_split(uu, it);
                     if (DC) {
                         const float4 cc = tab[2 * it];
                         psc[p] = fmaf(qr, fmaf(fmaf(fmaf(cc.w, tt, cc.z), tt, cc.y), tt, cc.x), psc[p]);
@@ -2033,7 +2116,8 @@ __device__ __forceinline__ void near_tile(const SrcF* __restrict__ Sx, const LJf
 
 // The same tile for two points per thread and one cut-off for every pair, with the distances and the LJ terms
 // of both points in two-wide instructions: L2 holds {A, A, -B, -B} per (atom, site), so one shared load gives
-// both operands of a site.  Per pair the arithmetic (and so every result) is that of near_tile.
+// both operands of a site.  Per pair the arithmetic is that of near_tile; a point outside the near radius
+// gets zero terms from both cut-off tests, so no separate radius test is needed.
 template <int SM, bool DU, bool DH>
 __device__ __forceinline__ void near_tile_uni2(const SrcF* __restrict__ Sx, const LJf* __restrict__ L2, int cnt,
                                                const float (&gx)[2], float fy, float fz, float rn2, float rs2,
@@ -2041,7 +2125,10 @@ __device__ __forceinline__ void near_tile_uni2(const SrcF* __restrict__ Sx, cons
                                                float h0h, const float (&wlo)[3], const float (&whi)[3], float rcull2,
                                                float (&psc)[2], float (&psh)[2], float (&plj)[2][SM], unsigned& hit,
                                                unsigned (&cnt3)[3]) {
+    // the tile's sources that survive the culling, listed per warp in tile order (kernels of up to 16 warps)
+    __shared__ int wl_all[16][kT];
     const int lane = threadIdx.x & 31;
+    int* wl = wl_all[threadIdx.x >> 5];
     auto keep = [&](int i) {
         if (i >= cnt) return false;
         const float4 g = *reinterpret_cast<const float4*>(&Sx[i].xh);
@@ -2050,37 +2137,55 @@ __device__ __forceinline__ void near_tile_uni2(const SrcF* __restrict__ Sx, cons
         const float qz = fmaxf(0.f, fmaxf(wlo[2] - g.z, g.z - whi[2]));
         return fmaf(qx, qx, fmaf(qy, qy, qz * qz)) < rcull2;
     };
-    const unsigned long long live =
-        (unsigned long long)__ballot_sync(0xffffffffu, keep(lane)) |
-        ((unsigned long long)__ballot_sync(0xffffffffu, keep(lane + 32)) << 32);
+    const bool k0 = keep(lane), k1 = keep(lane + 32);
+    const unsigned b0 = __ballot_sync(0xffffffffu, k0), b1 = __ballot_sync(0xffffffffu, k1);
+    const unsigned lt = (1u << lane) - 1u;
+    const int n0 = __popc(b0), n = n0 + __popc(b1);
+    __syncwarp();  // the previous tile's list is no longer read
+    if (k0) wl[__popc(b0 & lt)] = lane;
+    if (k1) wl[n0 + __popc(b1 & lt)] = lane + 32;
+    __syncwarp();
+    cnt3[0] += 2u * (unsigned)n;
     const f32x2 GX2 = pk2(gx[0], gx[1]);
     f32x2 ACC[SM];
 #pragma unroll
     for (int s = 0; s < SM; ++s) ACC[s] = 0ull;
-    for (unsigned long long mk = live; mk != 0ull; mk &= mk - 1ull) {
-        const int s0 = __ffsll((long long)mk) - 1;
+    auto dist = [&](int s0, float& q, float2& d2) {
         const float4 g0 = *reinterpret_cast<const float4*>(&Sx[s0].xh);
         const float4 g1 = *reinterpret_cast<const float4*>(&Sx[s0].xl);
-        cnt3[0] += 2;
         const float dy = (fy - g0.y) - g1.y;
         const float dz = (fz - g0.z) - g1.z;
         const float dyz2 = fmaf(dy, dy, dz * dz);
         const f32x2 DX = sub2(sub2(GX2, pk2(g0.x, g0.x)), pk2(g1.x, g1.x));
-        const float2 d2 = up2(fma2(DX, DX, pk2(dyz2, dyz2)));
-        if (fminf(d2.x, d2.y) >= rn2) continue;
+        d2 = up2(fma2(DX, DX, pk2(dyz2, dyz2)));
+        q = g0.w;
+    };
+    auto lj = [&](int s0, float2 d2) {
+        const bool in0 = d2.x < rcu2, in1 = d2.y < rcu2;
+        cnt3[1] += (unsigned)in0 + (unsigned)in1;
+        const float r0 = rcp_approx(d2.x), r1 = rcp_approx(d2.y);
+        const f32x2 R2 = pk2(in0 ? r0 : 0.f, in1 ? r1 : 0.f);  // a point outside the cut-off adds +0
+        const f32x2 R6 = mul2(mul2(R2, R2), R2);
+        const LJf* Ls = L2 + s0 * SM;
+#pragma unroll
+        for (int s = 0; s < SM; ++s) {
+            const ulonglong2 ab = *reinterpret_cast<const ulonglong2*>(&Ls[s]);  // (A, A), (-B, -B)
+            ACC[s] = fma2(R6, fma2(ab.x, R6, ab.y), ACC[s]);
+        }
+    };
+    auto sr = [&](float q, float2 d2) {
         if (fminf(d2.x, d2.y) < rs2) {
 #pragma unroll
             for (int p = 0; p < 2; ++p) {
                 const float dd = p ? d2.y : d2.x;
                 if (dd >= rs2) continue;
                 if (dd > 0.f) {
-                    // erfc(x)/d and e^{-x^2}[erfcx(x-a) + erfcx(x+a)]/d from the cubic pieces in d
                     ++cnt3[2];
                     const float ri = rsqrt_approx(dd);
-                    const float qr = g0.w * ri;
+                    const float qr = q * ri;
                     const float uu = dd * ri * tinv;
-                    const int it = min((int)uu, kNTab - 1);
-                    const float tt = uu - (float)it;
+                    int it;
+                    const float tt = seg_split(uu, it);
                     if (DC) {
                         const float4 cc = tab[2 * it];
                         psc[p] = fmaf(qr, fmaf(fmaf(fmaf(cc.w, tt, cc.z), tt, cc.y), tt, cc.x), psc[p]);
@@ -2091,26 +2196,35 @@ __device__ __forceinline__ void near_tile_uni2(const SrcF* __restrict__ Sx, cons
                     }
                 } else {
                     hit |= 1u << p;
-                    if (DC) psc[p] -= g0.w * c0h;
-                    if (DH) psh[p] -= g0.w * h0h;
+                    if (DC) psc[p] -= q * c0h;
+                    if (DH) psh[p] -= q * h0h;
                 }
             }
         }
+    };
+    // two sources per step: their loads, distances and LJ terms are independent (more in flight per warp);
+    // the sums still take the sources in tile order
+    int i = 0;
+    for (; i + 2 <= n; i += 2) {
+        const int sa = wl[i], sb = wl[i + 1];
+        float qa, qb;
+        float2 da, db;
+        dist(sa, qa, da);
+        dist(sb, qb, db);
         if (DU) {
-            const bool in0 = d2.x < rcu2, in1 = d2.y < rcu2;
-            if (in0 || in1) {
-                cnt3[1] += (unsigned)in0 + (unsigned)in1;
-                const float r0 = rcp_approx(d2.x), r1 = rcp_approx(d2.y);
-                const f32x2 R2 = pk2(in0 ? r0 : 0.f, in1 ? r1 : 0.f);  // a point outside the cut-off adds +0
-                const f32x2 R6 = mul2(mul2(R2, R2), R2);
-                const LJf* Ls = L2 + s0 * SM;
-#pragma unroll
-                for (int s = 0; s < SM; ++s) {
-                    const ulonglong2 ab = *reinterpret_cast<const ulonglong2*>(&Ls[s]);  // (A, A), (-B, -B)
-                    ACC[s] = fma2(R6, fma2(ab.x, R6, ab.y), ACC[s]);
-                }
-            }
+            lj(sa, da);
+            lj(sb, db);
         }
+        sr(qa, da);
+        sr(qb, db);
+    }
+    if (i < n) {
+        const int sa = wl[i];
+        float qa;
+        float2 da;
+        dist(sa, qa, da);
+        if (DU) lj(sa, da);
+        sr(qa, da);
     }
 #pragma unroll
     for (int s = 0; s < SM; ++s) {
@@ -2128,9 +2242,9 @@ struct NearConst {
 
 __device__ __forceinline__ NearConst near_const(const EvalArgs& a) {
     NearConst c;
-    c.rs2 = (float)((a.ph.rs / a.g.h) * (a.ph.rs / a.g.h));
-    c.c0h = (float)(a.ph.phi_c0 * a.g.h);
-    c.h0h = (float)(a.ph.phi_h0 * a.g.h);
+    c.rs2 = a.rs2;
+    c.c0h = a.c0h;
+    c.h0h = a.h0h;
     c.DC = a.o.c != nullptr;
     const double rnear = a.meta->rnear;
     c.rn2 = isfinite(rnear) ? (float)(rnear * rnear) : INFINITY;
@@ -2344,7 +2458,19 @@ __device__ void near_body(const EvalArgs& a, int b, int sub, Ring<SM, true>& r, 
     near_finish<SM, DU, DH>(q, c, a);
 }
 
-// ---- per-solute kernels: one CTA per target batch
+// ---- per-solute kernels
+// Work queue of a persistent kernel: wq[0] counts the items taken, wq[1] the CTAs whose producer takes no more.
+// The last CTA to leave resets both, so every launch (and every replay of a captured one) starts from zero.
+__device__ __forceinline__ void queue_leave(int* wq) {
+    __threadfence();
+    if (atomicAdd(&wq[1], 1) == (int)gridDim.x - 1) {
+        atomicExch(&wq[0], 0);
+        atomicExch(&wq[1], 0);
+    }
+}
+
+// Far field of one solute, one CTA per target batch (heaviest first).  A persistent form like k_near32's measured
+// slower here: the far items carry no epilogue to hide, and the queue adds latency before each batch's first tile.
 template <int NXB, int NYB, int NZB, int PF, bool DH>
 __global__ void __launch_bounds__(FarShape<NXB, NYB, NZB, PF>::NTP) k_far32(EvalArgs a) {
     __shared__ Ring<1, false> r;
@@ -2360,16 +2486,6 @@ template <int NXB, int NYB, int NZB, int SM, bool DU, bool DH>
 struct NearOcc {
     static constexpr int v = SM <= 4 ? ((DU && DH) ? 2 : 3) : 1;
 };
-
-// Work queue of a persistent kernel: wq[0] counts the items taken, wq[1] the CTAs whose producer takes no more.
-// The last CTA to leave resets both, so every launch (and every replay of a captured one) starts from zero.
-__device__ __forceinline__ void queue_leave(int* wq) {
-    __threadfence();
-    if (atomicAdd(&wq[1], 1) == (int)gridDim.x - 1) {
-        atomicExch(&wq[0], 0);
-        atomicExch(&wq[1], 0);
-    }
-}
 
 // Persistent near-field kernel of one solute: the producer of each CTA takes the next item (sub-batch) of the
 // heaviest-first order from the work queue and streams the near lists of its items through one ring
@@ -2411,7 +2527,7 @@ __global__ void __launch_bounds__(NearShape<NXB, NYB, NZB>::NTP, (NearOcc<NXB, N
         },
         [&](int item) { near_begin<NXB, NYB, NZB, SM>(q, a, item / NS, item % NS); },
         [&](int slot, int cnt) { near_stage<SM, DU, DH>(q, c, r.src[slot], r.lj[slot], cnt, tab, cnt3); },
-        [&](int) { near_finish<SM, DU, DH>(q, c, a); });
+        [](int) {}, [&](int) { near_finish<SM, DU, DH>(q, c, a); });
     if (rr == kRingDone) near_publish<Sh::NW>(r, a.meta, cnt3);
     if (tid == Sh::NT) queue_leave(a.wq);
 }
@@ -2876,9 +2992,11 @@ rism_status tree_enqueue(TreeState* s, const DevTables& t, const GridD& g, const
         const int gb = std::min((n + 255) / 256, 4 * sm_count());
         k_bounds<<<gb, 256, 0, st>>>(t.srcf, t.ljf, n, ph.S, t.smax, s->meta);
         k_codes<<<gb, 256, 0, st>>>(t.srcf, n, ph.rs / g.h, s->meta, s->code, s->idx);
+        // the FP64 sorted positions feed only the source proxies' upward pass (off with target boxes)
         BuildArgs ba{n, s->leaf, P3, s->max_nodes, s->max_prox, s->max_items, t.geo, t.srcf, t.ljf, t.smax, g,
-                     1.0 / g.h, s->src, s->srcf, s->ljs, s->ljs2};
-        const size_t shb = (256 * 32 + 64) * sizeof(int);
+                     1.0 / g.h, s->tb.enabled ? nullptr : s->src, s->srcf, s->ljs, s->ljs2};
+        const size_t shb = (256 * 32 + 64) * sizeof(int) +
+                           (t.n <= kSortSmem ? kSortSmem * (sizeof(unsigned long long) + sizeof(uint32_t)) : 0);
         cudaFuncSetAttribute(k_sort_build, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shb);
         k_sort_build<<<1, kSortThreads, shb, st>>>(ba, s->code, s->idx, s->code2, s->idx2, s->nodes, s->items,
                                                    s->prox_nodes, s->prox_items, s->meta);
@@ -2964,6 +3082,10 @@ EvalArgs make_args(TreeState* s, const DevTables& t, const GridD& g, const Phys&
         const double e2 = 2.0 * ph.ea2;
         a.e2a_h = (float)e2;
         a.e2a_l = (float)(e2 - (double)a.e2a_h);
+        a.kap2 = (float)(-ph.kappa * g.h * 1.4426950408889634);
+        a.rs2 = (float)((ph.rs / g.h) * (ph.rs / g.h));
+        a.c0h = (float)(ph.phi_c0 * g.h);
+        a.h0h = (float)(ph.phi_h0 * g.h);
     }
     a.o = out;
     a.err = t.err;
