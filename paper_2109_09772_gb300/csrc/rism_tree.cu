@@ -50,7 +50,8 @@ namespace rism {
 namespace {
 
 constexpr int kSortThreads = 1024;
-constexpr int kSortSmem = 4096;  // atoms sorted in shared memory (64-bit keys and the sorted codes: 48 KB)
+constexpr int kSortSmem = 4096;  // atoms sorted in shared memory (64-bit keys, sorted codes, positions: 96 KB)
+constexpr int kNodeSmem = 1024;  // octree nodes kept in shared memory during the build (56 KB)
 constexpr int kMortonBits = 10;          // per axis
 constexpr int kMaxLevel = kMortonBits;   // octree depth limit
 constexpr int kChunk = 16;               // atoms per upward-pass work item
@@ -331,6 +332,8 @@ __global__ void __launch_bounds__(kSortThreads) k_sort_build(BuildArgs a, uint32
         for (int i = threadIdx.x; i < N; i += blockDim.x)
             sk[i] = i < n ? ((unsigned long long)code[i] << 32) | idx[i] : ~0ull;
         __syncthreads();
+        // a stage with j <= 32 pairs elements within the 64 of one warp (per 32 consecutive t), so between two
+        // such stages the warp synchronises alone
         for (int k = 2; k <= N; k <<= 1)
             for (int j = k >> 1; j > 0; j >>= 1) {
                 for (int t = threadIdx.x; t < N / 2; t += blockDim.x) {
@@ -341,8 +344,13 @@ __global__ void __launch_bounds__(kSortThreads) k_sort_build(BuildArgs a, uint32
                         sk[l] = x;
                     }
                 }
-                __syncthreads();
+                const int jn = j > 1 ? j >> 1 : k;  // j of the next stage
+                if (j >= 64 || jn >= 64)
+                    __syncthreads();
+                else
+                    __syncwarp();
             }
+        __syncthreads();
         for (int i = threadIdx.x; i < n; i += blockDim.x) {
             const unsigned long long v = sk[i];
             sc[i] = code[i] = (uint32_t)(v >> 32);
@@ -398,87 +406,96 @@ __global__ void __launch_bounds__(kSortThreads) k_sort_build(BuildArgs a, uint32
         // after 4 passes the sorted data is back in code/idx
     }
     const uint32_t* scode = in_smem ? sc : code;  // sorted codes for the searches below
-    // ---- sorted copies of the sources (FP64 grid units when the source proxies need them, float-float) and
-    // LJ tables
-    for (int i = threadIdx.x; i < n; i += blockDim.x) {
-        const int j = (int)idx[i];
-        if (a.src) a.src[i] = to_grid(a.geo[j], a.gd, a.ih);
-        a.ssrcf[i] = a.srcf[j];
-        for (int s = 0; s < a.smax; ++s) {
-            const LJf l = a.ljf[(int64_t)j * a.smax + s];
-            a.ljs[(int64_t)i * a.smax + s] = l;
-            a.ljs2[(int64_t)i * a.smax + s] = LJf{l.A, l.A, -l.B, -l.B};
+    // small solutes keep the sorted high-part positions and (while they fit) the nodes in shared memory, so
+    // the level-by-level phases below do not wait on global memory between levels
+    float* spos = reinterpret_cast<float*>(sc + kSortSmem);  // [kSortSmem][3]
+    Node* snodes = reinterpret_cast<Node*>(spos + 3 * kSortSmem);  // [kNodeSmem]
+    // sorted high-part positions for the bounding boxes (the sorted tables themselves: k_gather_sorted)
+    if (in_smem)
+        for (int i = threadIdx.x; i < n; i += blockDim.x) {
+            const float4 f = *reinterpret_cast<const float4*>(&a.srcf[(uint32_t)sk[i]].xh);
+            spos[3 * i] = f.x;
+            spos[3 * i + 1] = f.y;
+            spos[3 * i + 2] = f.z;
         }
-    }
 
-    // ---- octree, level by level: nodes [lvl_begin, lvl_end) at the current level
+    // ---- octree, level by level: nodes [lvl_begin, lvl_end) at the current level, built in shared memory
+    // while they fit in kNodeSmem, else (built again) in global memory
     __shared__ int s_nnodes, s_lvl_begin, s_lvl_end, s_overflow, s_lvl[kMaxLevel + 2], s_nlvl;
-    if (threadIdx.x == 0) {
-        nodes[0] = Node{0, n, -1, 0, 0, -1, 0, 0, {0, 0, 0}, {0, 0, 0}};
-        s_nnodes = 1;
-        s_lvl_begin = 0;
-        s_lvl_end = 1;
-        s_overflow = 0;
-        s_lvl[0] = 0;
-        s_lvl[1] = 1;
-        s_nlvl = 1;
-    }
-    __syncthreads();
-    for (int lvl = 0; lvl < kMaxLevel; ++lvl) {
-        const int lb = s_lvl_begin, le = s_lvl_end;
-        if (lb >= le) break;
-        for (int base = lb; base < le; base += blockDim.x) {
-            const int nid = base + threadIdx.x;
-            int cb[9];
-            int nch = 0;
-            bool split = false;
-            if (nid < le) {
-                Node nd = nodes[nid];
-                split = (nd.end - nd.begin) > a.leaf;
-                if (split) {
-                    const int sh3 = 3 * (kMortonBits - 1 - lvl);
-                    cb[0] = nd.begin;
-                    for (int ch = 1; ch < 8; ++ch) {
-                        // first position in [begin, end) whose child digit >= ch
-                        int lo = cb[ch - 1], hi = nd.end;
-                        while (lo < hi) {
-                            int mid = (lo + hi) >> 1;
-                            if ((int)((scode[mid] >> sh3) & 7u) < ch) lo = mid + 1; else hi = mid;
-                        }
-                        cb[ch] = lo;
-                    }
-                    cb[8] = nd.end;
-                    for (int ch = 0; ch < 8; ++ch) nch += cb[ch + 1] > cb[ch];
-                }
-            }
-            int total;
-            int off = block_exclusive_scan(nch, tmp, total);
-            const int start = s_nnodes;
-            if (nid < le && split) {
-                if (start + off + nch > a.max_nodes) {
-                    s_overflow = 1;
-                } else {
-                    nodes[nid].first_child = start + off;
-                    nodes[nid].nchild = nch;
-                    int k = start + off;
-                    for (int ch = 0; ch < 8; ++ch)
-                        if (cb[ch + 1] > cb[ch])
-                            nodes[k++] = Node{cb[ch], cb[ch + 1], -1, 0, lvl + 1, -1, 0, 0, {0, 0, 0}, {0, 0, 0}};
-                }
-            }
-            __syncthreads();
-            if (threadIdx.x == 0) s_nnodes = min(start + total, a.max_nodes);
-            __syncthreads();
-        }
+    Node* store = in_smem ? snodes : nodes;
+    int cap = in_smem ? min(kNodeSmem, a.max_nodes) : a.max_nodes;
+    for (;;) {
         if (threadIdx.x == 0) {
-            s_lvl_begin = le;
-            s_lvl_end = s_nnodes;
-            if (s_nnodes > le) {
-                s_lvl[s_nlvl + 1] = s_nnodes;
-                ++s_nlvl;
-            }
+            store[0] = Node{0, n, -1, 0, 0, -1, 0, 0, {0, 0, 0}, {0, 0, 0}};
+            s_nnodes = 1;
+            s_lvl_begin = 0;
+            s_lvl_end = 1;
+            s_overflow = 0;
+            s_lvl[0] = 0;
+            s_lvl[1] = 1;
+            s_nlvl = 1;
         }
         __syncthreads();
+        for (int lvl = 0; lvl < kMaxLevel; ++lvl) {
+            const int lb = s_lvl_begin, le = s_lvl_end;
+            if (lb >= le) break;
+            for (int base = lb; base < le; base += blockDim.x) {
+                const int nid = base + threadIdx.x;
+                int cb[9];
+                int nch = 0;
+                bool split = false;
+                if (nid < le) {
+                    const Node nd = store[nid];
+                    split = (nd.end - nd.begin) > a.leaf;
+                    if (split) {
+                        const int sh3 = 3 * (kMortonBits - 1 - lvl);
+                        cb[0] = nd.begin;
+                        for (int ch = 1; ch < 8; ++ch) {
+                            // first position in [begin, end) whose child digit >= ch
+                            int lo = cb[ch - 1], hi = nd.end;
+                            while (lo < hi) {
+                                int mid = (lo + hi) >> 1;
+                                if ((int)((scode[mid] >> sh3) & 7u) < ch) lo = mid + 1; else hi = mid;
+                            }
+                            cb[ch] = lo;
+                        }
+                        cb[8] = nd.end;
+                        for (int ch = 0; ch < 8; ++ch) nch += cb[ch + 1] > cb[ch];
+                    }
+                }
+                int total;
+                int off = block_exclusive_scan(nch, tmp, total);
+                const int start = s_nnodes;
+                if (nid < le && split) {
+                    if (start + off + nch > cap) {
+                        s_overflow = 1;
+                    } else {
+                        store[nid].first_child = start + off;
+                        store[nid].nchild = nch;
+                        int k = start + off;
+                        for (int ch = 0; ch < 8; ++ch)
+                            if (cb[ch + 1] > cb[ch])
+                                store[k++] = Node{cb[ch], cb[ch + 1], -1, 0, lvl + 1, -1, 0, 0, {0, 0, 0}, {0, 0, 0}};
+                    }
+                }
+                __syncthreads();
+                if (threadIdx.x == 0) s_nnodes = min(start + total, cap);
+                __syncthreads();
+            }
+            if (threadIdx.x == 0) {
+                s_lvl_begin = le;
+                s_lvl_end = s_nnodes;
+                if (s_nnodes > le) {
+                    s_lvl[s_nlvl + 1] = s_nnodes;
+                    ++s_nlvl;
+                }
+            }
+            __syncthreads();
+        }
+        if (!(s_overflow && store != nodes)) break;
+        __syncthreads();  // every thread has read s_overflow before it is reset
+        store = nodes;
+        cap = a.max_nodes;
     }
     // ---- proxy plan: nodes with more than P3 atoms get proxies; items of kChunk atoms
     const int nn = s_nnodes;
@@ -493,7 +510,7 @@ __global__ void __launch_bounds__(kSortThreads) k_sort_build(BuildArgs a, uint32
         const int nid = base + threadIdx.x;
         int isp = 0, nit = 0, leaf = 0;
         if (nid < nn) {
-            Node nd = nodes[nid];
+            const Node nd = store[nid];
             int cnt = nd.end - nd.begin;
             isp = cnt > a.P3;
             nit = isp ? (cnt + kChunk - 1) / kChunk : 0;
@@ -508,15 +525,15 @@ __global__ void __launch_bounds__(kSortThreads) k_sort_build(BuildArgs a, uint32
             int k = p0 + op;
             if (k >= a.max_prox || i0 + oi + nit > a.max_items) {
                 s_overflow = 1;
-                nodes[nid].prox = -1;
+                store[nid].prox = -1;
             } else {
-                nodes[nid].prox = k;
+                store[nid].prox = k;
                 prox_nodes[k] = nid;
                 prox_items[k] = i0 + oi;
                 // item = (proxy set k, atom chunk start)
                 for (int c = 0; c < nit; ++c) {
                     items[2 * (i0 + oi + c) + 0] = k;
-                    items[2 * (i0 + oi + c) + 1] = nodes[nid].begin + c * kChunk;
+                    items[2 * (i0 + oi + c) + 1] = store[nid].begin + c * kChunk;
                 }
             }
         }
@@ -545,22 +562,31 @@ __global__ void __launch_bounds__(kSortThreads) k_sort_build(BuildArgs a, uint32
         for (int nid = s_lvl[lv] + w; nid < s_lvl[lv + 1]; nid += NW) {
             // reduced in FP32 over the high parts of the float-float positions (within 1e-5 grid units of
             // the exact box; the box only steers the acceptance test and the proxy placement)
-            const Node nd = nodes[nid];
+            const Node nd = store[nid];
             float lo[3] = {INFINITY, INFINITY, INFINITY}, hi[3] = {-INFINITY, -INFINITY, -INFINITY};
             if (nd.first_child < 0) {
                 for (int i = nd.begin + lane; i < nd.end; i += 32) {
-                    const SrcF g = a.ssrcf[i];
-                    const float v[3] = {g.xh, g.yh, g.zh};
+                    float v[3];
+                    if (in_smem) {
+                        v[0] = spos[3 * i];
+                        v[1] = spos[3 * i + 1];
+                        v[2] = spos[3 * i + 2];
+                    } else {
+                        const SrcF g = a.srcf[idx[i]];
+                        v[0] = g.xh;
+                        v[1] = g.yh;
+                        v[2] = g.zh;
+                    }
                     for (int d = 0; d < 3; ++d) {
                         lo[d] = fminf(lo[d], v[d]);
                         hi[d] = fmaxf(hi[d], v[d]);
                     }
                 }
             } else if (lane < nd.nchild) {
-                const Node ch = nodes[nd.first_child + lane];
+                const Node ch = store[nd.first_child + lane];
                 for (int d = 0; d < 3; ++d) {
-                    lo[d] = (float)ch.lo[d];
-                    hi[d] = (float)ch.hi[d];
+                    lo[d] = ch.lo[d];
+                    hi[d] = ch.hi[d];
                 }
             }
             for (int d = 0; d < 3; ++d)
@@ -570,11 +596,28 @@ __global__ void __launch_bounds__(kSortThreads) k_sort_build(BuildArgs a, uint32
                 }
             if (lane == 0)
                 for (int d = 0; d < 3; ++d) {
-                    nodes[nid].lo[d] = lo[d];
-                    nodes[nid].hi[d] = hi[d];
+                    store[nid].lo[d] = lo[d];
+                    store[nid].hi[d] = hi[d];
                 }
         }
         __syncthreads();
+    }
+    if (store != nodes)
+        for (int k = threadIdx.x; k < nn; k += blockDim.x) nodes[k] = store[k];
+}
+
+// Sorted copies of the sources (FP64 grid units when the source proxies need them, float-float) and of the LJ
+// tables, in the order of the sorted codes; one thread per atom.
+__global__ void k_gather_sorted(BuildArgs a, const uint32_t* __restrict__ idx) {
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < a.n; i += gridDim.x * blockDim.x) {
+        const int j = (int)idx[i];
+        if (a.src) a.src[i] = to_grid(a.geo[j], a.gd, a.ih);
+        a.ssrcf[i] = a.srcf[j];
+        for (int s = 0; s < a.smax; ++s) {
+            const LJf l = a.ljf[(int64_t)j * a.smax + s];
+            a.ljs[(int64_t)i * a.smax + s] = l;
+            a.ljs2[(int64_t)i * a.smax + s] = LJf{l.A, l.A, -l.B, -l.B};
+        }
     }
 }
 
@@ -2996,12 +3039,15 @@ rism_status tree_enqueue(TreeState* s, const DevTables& t, const GridD& g, const
         BuildArgs ba{n, s->leaf, P3, s->max_nodes, s->max_prox, s->max_items, t.geo, t.srcf, t.ljf, t.smax, g,
                      1.0 / g.h, s->tb.enabled ? nullptr : s->src, s->srcf, s->ljs, s->ljs2};
         const size_t shb = (256 * 32 + 64) * sizeof(int) +
-                           (t.n <= kSortSmem ? kSortSmem * (sizeof(unsigned long long) + sizeof(uint32_t)) : 0);
+                           (t.n <= kSortSmem ? kSortSmem * (sizeof(unsigned long long) + 4 * sizeof(uint32_t)) +
+                                                   kNodeSmem * sizeof(Node)
+                                             : 0);
         cudaFuncSetAttribute(k_sort_build, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shb);
         k_sort_build<<<1, kSortThreads, shb, st>>>(ba, s->code, s->idx, s->code2, s->idx2, s->nodes, s->items,
                                                    s->prox_nodes, s->prox_items, s->meta);
+        k_gather_sorted<<<std::min((n + 255) / 256, 4 * sm_count()), 256, 0, st>>>(ba, s->idx);
         k_cells<<<1024, 256, 0, st>>>(n, s->meta, s->code, s->cell_start);
-        s->launches += 4;
+        s->launches += 5;
         if (!s->tb.enabled) {
             // source proxies: only the batch-level traversal uses them (with target boxes on, the box level
             // accepts every cluster a batch would)
