@@ -71,33 +71,38 @@ struct SetupArgs {
     GridD g;
 };
 
+// One thread per (atom, site slot): the pair's Lorentz-Berthelot LJ terms (FP64 and FP32 grid units); the
+// thread of slot 0 also writes the atom's position records.
 __global__ void k_setup(SetupArgs a, Geo* geo, SrcF* srcf, LJd* ljd, LJf* ljf) {
-    int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    if (i >= a.n) return;
+    const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (t >= a.n * a.smax) return;
+    const int64_t i = t / a.smax;
+    const int s = (int)(t - i * a.smax);
     const double* r = a.raw + 6 * i;
-    double x = r[0], y = r[1], z = r[2], q = r[3], sg = r[4], ep = r[5];
-    geo[i] = Geo{x, y, z, q};
-    double ih = 1.0 / a.g.h;
-    srcf[i] = make_srcf((x - a.g.ox) * ih, (y - a.g.oy) * ih, (z - a.g.oz) * ih, q);
-    double h2 = a.g.h * a.g.h, h6 = h2 * h2 * h2;
-    for (int s = 0; s < a.smax; ++s) {
-        LJd d{0.0, 0.0, 0.0, 0.0};
-        LJf f{0.f, 0.f, 0.f, 0.f};
-        if (s < a.S) {
-            double sig = 0.5 * (sg + a.sig_s[s]);      // Lorentz
-            double eps = sqrt(ep * a.eps_s[s]);        // Berthelot
-            double s2 = sig * sig, s6 = s2 * s2 * s2;
-            double A = 4.0 * eps * s6 * s6, B = 4.0 * eps * s6;
-            double rc2;
-            if (a.lj_mode == RISM_LJ_RCUT) rc2 = a.lj_rcut * a.lj_rcut;
-            else if (a.lj_mode == RISM_LJ_TOL) { double rc = rcut_from_tol(A, B, a.lj_tol); rc2 = rc * rc; }
-            else rc2 = INFINITY;
-            d = LJd{A, B, rc2, 0.0};
-            f = LJf{(float)(A / (h6 * h6)), (float)(B / h6), (float)(rc2 / h2), 0.f};
-        }
-        ljd[i * a.smax + s] = d;
-        ljf[i * a.smax + s] = f;
+    if (s == 0) {
+        const double x = r[0], y = r[1], z = r[2], q = r[3];
+        geo[i] = Geo{x, y, z, q};
+        const double ih = 1.0 / a.g.h;
+        srcf[i] = make_srcf((x - a.g.ox) * ih, (y - a.g.oy) * ih, (z - a.g.oz) * ih, q);
     }
+    LJd d{0.0, 0.0, 0.0, 0.0};
+    LJf f{0.f, 0.f, 0.f, 0.f};
+    if (s < a.S) {
+        const double sg = r[4], ep = r[5];
+        const double h2 = a.g.h * a.g.h, h6 = h2 * h2 * h2;
+        double sig = 0.5 * (sg + a.sig_s[s]);      // Lorentz
+        double eps = sqrt(ep * a.eps_s[s]);        // Berthelot
+        double s2 = sig * sig, s6 = s2 * s2 * s2;
+        double A = 4.0 * eps * s6 * s6, B = 4.0 * eps * s6;
+        double rc2;
+        if (a.lj_mode == RISM_LJ_RCUT) rc2 = a.lj_rcut * a.lj_rcut;
+        else if (a.lj_mode == RISM_LJ_TOL) { double rc = rcut_from_tol(A, B, a.lj_tol); rc2 = rc * rc; }
+        else rc2 = INFINITY;
+        d = LJd{A, B, rc2, 0.0};
+        f = LJf{(float)(A / (h6 * h6)), (float)(B / h6), (float)(rc2 / h2), 0.f};
+    }
+    ljd[t] = d;
+    ljf[t] = f;
 }
 
 cudaError_t launch_setup(const double* raw, int64_t n, int S, int smax, const double* sig_s, const double* eps_s,
@@ -117,7 +122,7 @@ cudaError_t launch_setup(const double* raw, int64_t n, int S, int smax, const do
     a.lj_rcut = lj_rcut;
     a.lj_tol = lj_tol;
     a.g = g;
-    int nb = (int)((n + 127) / 128);
+    const int nb = (int)((n * smax + 127) / 128);
     k_setup<<<nb, 128, 0, st>>>(a, t.geo, t.srcf, t.ljd, t.ljf);
     return cudaGetLastError();
 }

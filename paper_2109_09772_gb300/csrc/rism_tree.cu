@@ -108,10 +108,12 @@ struct TBoxes {
     float ck[kMaxDegree + 1];  // cos(k pi / n), exact 1, 0, -1 where they occur
 };
 
+// Centre and radius in FP32: the centre lo + (ext - 1) / 2 is a half-integer and r^2 a quarter-integer, both
+// exact; r is the correctly rounded square root (no FP64 instruction in the kernels that place boxes).
 struct TBox {
     int l, ib, jb, kb;
     int lo[3], ext[3];
-    double c[3], r;
+    float c[3], r;
     bool proxied;
 };
 
@@ -123,18 +125,18 @@ __host__ __device__ inline TBox tbox_at(const TBoxes& tb, int l, int ib, int jb,
     b.kb = kb;
     const int E = kTB0 << l;
     const int n[3] = {tb.nx, tb.ny, tb.nz}, ix[3] = {ib, jb, kb};
-    double r2 = 0.0;
+    float r2 = 0.f;
     long long pts = 1;
     bool big = true;
     for (int d = 0; d < 3; ++d) {
         b.lo[d] = ix[d] * E;
         b.ext[d] = n[d] - b.lo[d] < E ? n[d] - b.lo[d] : E;
-        b.c[d] = b.lo[d] + 0.5 * (b.ext[d] - 1);
-        r2 += 0.25 * (double)(b.ext[d] - 1) * (b.ext[d] - 1);
+        b.c[d] = (float)b.lo[d] + 0.5f * (float)(b.ext[d] - 1);
+        r2 += 0.25f * (float)((b.ext[d] - 1) * (b.ext[d] - 1));
         pts *= b.ext[d];
         big = big && b.ext[d] >= tb.deg + 1;
     }
-    b.r = sqrt(r2);
+    b.r = sqrtf(r2);
     b.proxied = tb.enabled && big && pts > tb.P3;
     return b;
 }
@@ -806,7 +808,9 @@ __device__ __forceinline__ int load_frontier(int* cur, const int* lst, int cnt, 
     return cnt;
 }
 
-__device__ __forceinline__ void batch_geom(const ListArgs& a, int b, double cb[3], double& rb, int lo[3], int hi[3]) {
+// Batch b: its point range, centre (half-integers, exact in FP32) and radius (the correctly rounded root of an
+// exact integer); FP32 only, as in every list kernel.
+__device__ __forceinline__ void batch_geom(const ListArgs& a, int b, float cb[3], float& rb, int lo[3], int hi[3]) {
     const int ib = b % a.nbx, jb = (b / a.nbx) % a.nby, kb = b / (a.nbx * a.nby);
     lo[0] = ib * a.bx;
     lo[1] = jb * a.by;
@@ -814,8 +818,8 @@ __device__ __forceinline__ void batch_geom(const ListArgs& a, int b, double cb[3
     hi[0] = lo[0] + a.bx - 1;
     hi[1] = lo[1] + a.by - 1;
     hi[2] = lo[2] + a.bz - 1;
-    for (int d = 0; d < 3; ++d) cb[d] = 0.5 * (lo[d] + hi[d]);
-    rb = 0.5 * sqrt((double)((a.bx - 1) * (a.bx - 1) + (a.by - 1) * (a.by - 1) + (a.bz - 1) * (a.bz - 1)));
+    for (int d = 0; d < 3; ++d) cb[d] = 0.5f * (float)(lo[d] + hi[d]);
+    rb = 0.5f * sqrtf((float)((a.bx - 1) * (a.bx - 1) + (a.by - 1) * (a.by - 1) + (a.bz - 1) * (a.bz - 1)));
 }
 
 // Far lists: one warp per target batch, level-synchronous traversal of the
@@ -831,12 +835,11 @@ __global__ void __launch_bounds__(32 * kListWarps) k_far_lists(ListArgs a, const
     const int nb = a.nbx * a.nby * a.nbz;
     const bool tree_ok = !meta->build_overflow;
     const long long pts = (long long)a.bx * a.by * a.bz;
+    const float th2 = (float)(a.theta * a.theta);
     for (int b = blockIdx.x * kListWarps + w; b < nb; b += gridDim.x * kListWarps) {
-        double cb[3], rb;
+        float cbf[3], rbf;
         int lo[3], hi[3];
-        batch_geom(a, b, cb, rb, lo, hi);
-        const float cbf[3] = {(float)cb[0], (float)cb[1], (float)cb[2]}, rbf = (float)rb;
-        const float th2 = (float)(a.theta * a.theta);
+        batch_geom(a, b, cbf, rbf, lo, hi);
         int* cur = qa[w];
         int* nxt = qb[w];
         bool ovf = false;
@@ -963,11 +966,11 @@ __global__ void __launch_bounds__(32 * kListWarps) k_tbox_lists(TListArgs a, con
     const int l = a.l;
     const int nbl = tb.nbx[l] * tb.nby[l] * tb.nbz[l];
     const bool tree_ok = !meta->build_overflow;
+    const float th2 = (float)(a.theta * a.theta);
     for (int bi = blockIdx.x * kListWarps + w; bi < nbl; bi += gridDim.x * kListWarps) {
         const int ib = bi % tb.nbx[l], jb = (bi / tb.nbx[l]) % tb.nby[l], kb = bi / (tb.nbx[l] * tb.nby[l]);
         const TBox T = tbox_at(tb, l, ib, jb, kb);
-        const float tc[3] = {(float)T.c[0], (float)T.c[1], (float)T.c[2]}, tr = (float)T.r;
-        const float th2 = (float)(a.theta * a.theta);
+        const float tc[3] = {T.c[0], T.c[1], T.c[2]}, tr = T.r;
         const int box = tb.off[l] + bi;
         int* cur = qa[w];
         int* nxt = qb[w];
@@ -1086,7 +1089,7 @@ __global__ void __launch_bounds__(32 * kListWarps) k_near_lists(ListArgs a, cons
     const bool tree_ok = !meta->build_overflow;
     const long long pts = (long long)a.bx * a.by * a.bz;
     for (int b = blockIdx.x * kListWarps + w; b < nb; b += gridDim.x * kListWarps) {
-        double cb[3], rb;
+        float cb[3], rb;
         int lo[3], hi[3];
         batch_geom(a, b, cb, rb, lo, hi);
         int c0[3], c1[3];
@@ -1859,52 +1862,68 @@ __global__ void __launch_bounds__(256) k_cp_reduce(CPArgs c, const TreeMeta* met
     }
 }
 
-// Separable tensor-product interpolation in shared memory: V holds N1^3 values on the source box's
-// Chebyshev points (x fastest); W0/W1/W2 the 1D Lagrange weights [M][N1] of the target coordinates of each
-// axis.  Produces O[M][M][M] (x fastest); S1 and S2 are scratch of N1^2 M and N1 M^2 values.  Compile-time
-// sizes keep the index arithmetic to multiplies and shifts; rows beyond a clipped box's extent are computed
-// from zero weights and never stored.
-template <int N1, int M>
+// Separable tensor-product interpolation: V holds N1^3 values on the source box's Chebyshev points (x
+// fastest); W0/W1/W2 the 1D Lagrange weights [M][N1] of the target coordinates of each axis.  Each pass
+// contracts one axis with a thread per output line: the thread loads the N1 inputs of its line once into
+// registers and forms all M outputs of the line (the weights are the same for every thread of the pass, so
+// their loads are broadcasts).  S1 = x-contracted [N1][N1][M] and S2 = y-contracted [N1][M][M] live in shared
+// memory; the z pass hands each output value to emit(iz, iy, ix, v).  Every sum runs over k = 0 .. N1-1 in
+// order.  Rows beyond a clipped box's extent are computed from zero weights; the caller skips them.
+template <int N1, int M, typename FE>
 __device__ void interp3(const float2* V, const float* W0, const float* W1, const float* W2, float2* S1, float2* S2,
-                        float2* O) {
+                        FE&& emit) {
     const int tid = threadIdx.x, nt = blockDim.x;
-    for (int t = tid; t < N1 * N1 * M; t += nt) {
-        const int ix = t % M, line = t / M;  // line = kz N1 + ky
-        float ax = 0.f, ay = 0.f;
+    for (int line = tid; line < N1 * N1; line += nt) {  // line = kz N1 + ky
+        float2 v[N1];
 #pragma unroll
-        for (int k = 0; k < N1; ++k) {
-            const float wv = W0[ix * N1 + k];
-            const float2 v = V[line * N1 + k];
-            ax = fmaf(wv, v.x, ax);
-            ay = fmaf(wv, v.y, ay);
+        for (int k = 0; k < N1; ++k) v[k] = V[line * N1 + k];
+#pragma unroll 4
+        for (int ix = 0; ix < M; ++ix) {
+            float ax = 0.f, ay = 0.f;
+#pragma unroll
+            for (int k = 0; k < N1; ++k) {
+                const float wv = W0[ix * N1 + k];
+                ax = fmaf(wv, v[k].x, ax);
+                ay = fmaf(wv, v[k].y, ay);
+            }
+            S1[line * M + ix] = make_float2(ax, ay);
         }
-        S1[t] = make_float2(ax, ay);
     }
     __syncthreads();
-    for (int t = tid; t < N1 * M * M; t += nt) {
-        const int ix = t % M, iy = (t / M) % M, kz = t / (M * M);
-        float ax = 0.f, ay = 0.f;
+    for (int t = tid; t < N1 * M; t += nt) {  // t = kz M + ix
+        const int ix = t % M, kz = t / M;
+        float2 v[N1];
 #pragma unroll
-        for (int k = 0; k < N1; ++k) {
-            const float wv = W1[iy * N1 + k];
-            const float2 v = S1[(kz * N1 + k) * M + ix];
-            ax = fmaf(wv, v.x, ax);
-            ay = fmaf(wv, v.y, ay);
+        for (int k = 0; k < N1; ++k) v[k] = S1[(kz * N1 + k) * M + ix];
+#pragma unroll 4
+        for (int iy = 0; iy < M; ++iy) {
+            float ax = 0.f, ay = 0.f;
+#pragma unroll
+            for (int k = 0; k < N1; ++k) {
+                const float wv = W1[iy * N1 + k];
+                ax = fmaf(wv, v[k].x, ax);
+                ay = fmaf(wv, v[k].y, ay);
+            }
+            S2[(kz * M + iy) * M + ix] = make_float2(ax, ay);
         }
-        S2[t] = make_float2(ax, ay);
     }
     __syncthreads();
-    for (int t = tid; t < M * M * M; t += nt) {
-        const int ix = t % M, iy = (t / M) % M, iz = t / (M * M);
-        float ax = 0.f, ay = 0.f;
+    for (int t = tid; t < M * M; t += nt) {  // t = iy M + ix
+        const int ix = t % M, iy = t / M;
+        float2 v[N1];
 #pragma unroll
-        for (int k = 0; k < N1; ++k) {
-            const float wv = W2[iz * N1 + k];
-            const float2 v = S2[(k * M + iy) * M + ix];
-            ax = fmaf(wv, v.x, ax);
-            ay = fmaf(wv, v.y, ay);
+        for (int k = 0; k < N1; ++k) v[k] = S2[(k * M + iy) * M + ix];
+#pragma unroll 4
+        for (int iz = 0; iz < M; ++iz) {
+            float ax = 0.f, ay = 0.f;
+#pragma unroll
+            for (int k = 0; k < N1; ++k) {
+                const float wv = W2[iz * N1 + k];
+                ax = fmaf(wv, v[k].x, ax);
+                ay = fmaf(wv, v[k].y, ay);
+            }
+            emit(iz, iy, ix, make_float2(ax, ay));
         }
-        O[t] = make_float2(ax, ay);
     }
     __syncthreads();
 }
@@ -1922,9 +1941,9 @@ __device__ void basis_rows(const TBoxes& tb, const TBox& B, int d, int m, int mp
     }
 }
 
-// Dynamic shared memory of k_l2l / k_tdown for degree n: V, S1, S2, O and the weights.
+// Dynamic shared memory of k_l2l / k_tdown for degree n: V, S1, S2 and the weights.
 __host__ __device__ constexpr size_t interp_smem(int n1, int m) {
-    return sizeof(float2) * ((size_t)n1 * n1 * n1 + (size_t)n1 * n1 * m + (size_t)n1 * m * m + (size_t)m * m * m) +
+    return sizeof(float2) * ((size_t)n1 * n1 * n1 + (size_t)n1 * n1 * m + (size_t)n1 * m * m) +
            sizeof(float) * 3 * (size_t)m * n1;
 }
 
@@ -1945,22 +1964,21 @@ __global__ void __launch_bounds__(256) k_l2l(CPArgs c, int l, const TreeMeta* me
     float2* V = reinterpret_cast<float2*>(sm_raw);
     float2* S1 = V + P3;
     float2* S2 = S1 + P3;
-    float2* O = S2 + P3;
-    float* W = reinterpret_cast<float*>(O + P3);
+    float* W = reinterpret_cast<float*>(S2 + P3);
     const float2* src = c.tpot + (int64_t)pbox * P3;
     for (int k = threadIdx.x; k < P3; k += blockDim.x) V[k] = src[k];
     for (int d = 0; d < 3; ++d) {
         // child node i relative to the parent's centre: (c_child - c_parent) (exact: half-integers) + hw ck[i]
-        const float off = (float)(T.c[d] - Pb.c[d]), hd = 0.5f * (T.ext[d] - 1);
+        const float off = T.c[d] - Pb.c[d], hd = 0.5f * (T.ext[d] - 1);
         basis_rows<N1>(tb, Pb, d, N1, N1, [&](int i) { return off + hd * tb.ck[i]; }, W + d * N1 * N1);
     }
     __syncthreads();
-    interp3<N1, N1>(V, W, W + N1 * N1, W + 2 * N1 * N1, S1, S2, O);
     float2* dst = c.tpot + (int64_t)box * P3;
-    for (int k = threadIdx.x; k < P3; k += blockDim.x) {
+    interp3<N1, N1>(V, W, W + N1 * N1, W + 2 * N1 * N1, S1, S2, [&](int iz, int iy, int ix, float2 o) {
+        const int k = (iz * N1 + iy) * N1 + ix;
         const float2 v = dst[k];
-        dst[k] = make_float2(v.x + O[k].x, v.y + O[k].y);
-    }
+        dst[k] = make_float2(v.x + o.x, v.y + o.y);
+    });
     if (threadIdx.x == 0) c.tflag[box] = 1;
 }
 
@@ -2000,23 +2018,19 @@ __global__ void __launch_bounds__(256) k_tdown(CPArgs c, float4* far, const Tree
     float2* V = reinterpret_cast<float2*>(sm_raw);
     float2* S1 = V + P3;
     float2* S2 = S1 + N1 * N1 * M;
-    float2* O = S2 + N1 * M * M;
-    float* W = reinterpret_cast<float*>(O + M * M * M);
+    float* W = reinterpret_cast<float*>(S2 + N1 * M * M);
     const float2* src = c.tpot + (int64_t)tbox_index(tb, la, A.ib, A.jb, A.kb) * P3;
     for (int k = threadIdx.x; k < P3; k += blockDim.x) V[k] = src[k];
     const int ms[3] = {m0, m1, m2};
     for (int d = 0; d < 3; ++d) {
-        const float off = (float)(R.lo[d] - A.c[d]);  // grid point i of the region relative to A's centre (exact)
+        const float off = (float)R.lo[d] - A.c[d];  // grid point i of the region relative to A's centre (exact)
         basis_rows<N1>(tb, A, d, ms[d], M, [&](int i) { return off + (float)i; }, W + d * M * N1);
     }
     __syncthreads();
-    interp3<N1, M>(V, W, W + M * N1, W + 2 * M * N1, S1, S2, O);
-    for (int t = threadIdx.x; t < M * M * M; t += blockDim.x) {
-        const int ix = t % M, iy = (t / M) % M, iz = t / (M * M);
+    interp3<N1, M>(V, W, W + M * N1, W + 2 * M * N1, S1, S2, [&](int iz, int iy, int ix, float2 o) {
         if (ix < m0 && iy < m1 && iz < m2)
-            far[(R.lo[2] + iz) * plane + (int64_t)(R.lo[1] + iy) * tb.nx + R.lo[0] + ix] =
-                make_float4(O[t].x, 0.f, O[t].y, 0.f);
-    }
+            far[(R.lo[2] + iz) * plane + (int64_t)(R.lo[1] + iy) * tb.nx + R.lo[0] + ix] = make_float4(o.x, 0.f, o.y, 0.f);
+    });
 }
 
 template <int N1>
@@ -3785,7 +3799,7 @@ __global__ void __launch_bounds__(256) k_adj_qregion(TBoxes tb, const float4* __
     }
     const int ms[3] = {m0, m1, m2};
     for (int d = 0; d < 3; ++d) {
-        const float off = (float)(R.lo[d] - A.c[d]);
+        const float off = (float)R.lo[d] - A.c[d];
         basis_rows<N1>(tb, A, d, ms[d], M, [&](int i) { return off + (float)i; }, W + d * M * N1);
     }
     __syncthreads();
@@ -3873,7 +3887,7 @@ __global__ void __launch_bounds__(256) k_adj_qagg(TBoxes tb, int l, const float2
             const float2* src = qtot + (int64_t)tbox_index(tb, l - 1, cx, cy, cz) * P3;
             for (int k = threadIdx.x; k < P3; k += blockDim.x) V[k] = src[k];
             for (int d = 0; d < 3; ++d) {
-                const float off = (float)(C.c[d] - A.c[d]), hd = 0.5f * (C.ext[d] - 1);
+                const float off = C.c[d] - A.c[d], hd = 0.5f * (C.ext[d] - 1);
                 basis_rows<N1>(tb, A, d, N1, N1, [&](int i) { return off + hd * tb.ck[i]; }, W + d * N1 * N1);
             }
             __syncthreads();
