@@ -760,6 +760,16 @@ __host__ __device__ constexpr ShapeDesc shape_of(int v) {
     return v == 1 ? ShapeDesc{16, 8, 8, 8} : (v == 2 ? ShapeDesc{8, 8, 8, 8} : ShapeDesc{8, 8, 8, 4});
 }
 
+// Far-field buffer layout: blocks of 8x8x8 grid points (x fastest inside a block, the blocks x-fastest), the
+// grid padded to whole blocks, so the points of an 8x8x8 target (sub-)batch are one contiguous 8 KB run.
+__host__ __device__ inline int64_t far_index(int nx, int ny, int i, int j, int k) {
+    const int bx = (nx + 7) >> 3, by = (ny + 7) >> 3;
+    return ((((int64_t)(k >> 3) * by + (j >> 3)) * bx + (i >> 3)) << 9) + (((k & 7) << 6) | ((j & 7) << 3) | (i & 7));
+}
+__host__ __device__ inline int64_t far_points(int nx, int ny, int nz) {
+    return (int64_t)((nx + 7) >> 3) * ((ny + 7) >> 3) * ((nz + 7) >> 3) * 512;
+}
+
 constexpr int kQCap = 2048;        // frontier capacity of the warp-cooperative traversal (nodes of one level)
 constexpr int kListWarps = 2;      // warps (batches) per list-building CTA
 
@@ -1209,7 +1219,7 @@ struct EvalArgs {
     const int* near_cnt;
     const int2* near_ent;  // [nb][near_cap]
     int far_cap, near_cap;
-    float4* far;           // per grid point: Phi1 (hi, lo), Phik (hi, lo), grid units
+    float4* far;           // per grid point (far_index layout): Phi1 (hi, lo), Phik (hi, lo), grid units
     int far_init;          // the far kernel starts from the box-level (interpolated) field already in `far`
     const float4* ntab;    // [2 kNTab] cubic pieces of erfc(x) and e^{-x^2}[erfcx(x-a) + erfcx(x+a)] in d
     float ntab_inv;        // kNTab / r_short (grid units)
@@ -1386,12 +1396,14 @@ struct ItemSrc {
 // fills the ring with the tiles of item after item without a pause (every item takes at least one tile, the
 // last one flagged; an item without sources gets one empty tile), so the next item's sources load while the
 // consumer warps finish the previous one.  next(n, item, src) gives the CTA's n-th item (false: none left);
+// extra(n, item, bar) may add copies of its own to the barrier of the item's first tile (they land with it);
 // each consumer warp calls begin(item) before the item's first tile, stage(slot, cnt) per tile (before the slot
-// is released) and consume(cnt) after the release, and finish(item) after the item's last tile.  The ring barriers are initialised once per launch.
-// Waits are bounded as in run_ring.
-template <int SM, bool LJ, int NWARPS, typename R, typename FN, typename FB, typename FS, typename FC, typename FF>
-__device__ int run_stream(R& r, long long wlim, DevErr* err, FN&& next, FB&& begin, FS&& stage, FC&& consume,
-                          FF&& finish) {
+// is released) and consume(cnt) after the release, and finish(item) after the item's last tile.  The ring
+// barriers are initialised once per launch.  Waits are bounded as in run_ring.
+template <int SM, bool LJ, int NWARPS, typename R, typename FN, typename FX, typename FB, typename FS, typename FC,
+          typename FF>
+__device__ int run_stream(R& r, long long wlim, DevErr* err, FN&& next, FX&& extra, FB&& begin, FS&& stage,
+                          FC&& consume, FF&& finish) {
     const int tid = threadIdx.x, lane = tid & 31;
     volatile int* abort_flag = &r.abort;
     if (tid >= NWARPS * 32) {
@@ -1408,7 +1420,7 @@ __device__ int run_stream(R& r, long long wlim, DevErr* err, FN&& next, FB&& beg
                 c.e_end = have ? is.e_end : 0;
                 c.off = 0;
                 c.left = INT_MAX;
-                for (bool more = true; more;) {
+                for (bool more = true, first = true; more; first = false) {
                     const int t = c.produced, slot = t % kStages;
                     if (t >= kStages && !mbar_wait_bounded(&r.empty[slot], (uint32_t)((t / kStages - 1) & 1), wlim)) {
                         ok = false;
@@ -1418,6 +1430,7 @@ __device__ int run_stream(R& r, long long wlim, DevErr* err, FN&& next, FB&& beg
                         ok = false;
                         break;
                     }
+                    if (have && first) extra(n, item, &r.full[slot]);
                     const int cnt = have ? fill_ranges<SM, LJ>(c, is.ent, is.src, is.ljs, r.src[slot],
                                                                r.lj[LJ ? slot : 0], &r.full[slot])
                                          : 0;
@@ -1569,7 +1582,7 @@ __device__ __forceinline__ void far_begin(FarPts<PF>& q, const EvalArgs& a, int 
     for (int p = 0; p < PF; ++p) q.f1h[p] = q.f1l[p] = q.fkh[p] = q.fkl[p] = 0.f;
     q.on = false;
     if (a.far_init && q.j < a.g.ny && q.k < a.g.nz) {
-        const float4* src0 = a.far + ((int64_t)q.k * a.g.ny + q.j) * a.g.nx;
+        const float4* src0 = a.far + far_index(a.g.nx, a.g.ny, q.i0, q.j, q.k) - q.i0;  // PF points in a block row
 #pragma unroll
         for (int p = 0; p < PF; ++p)
             if (q.i0 + p < a.g.nx) {
@@ -1614,7 +1627,7 @@ template <int PF>
 __device__ __forceinline__ void far_finish(const FarPts<PF>& q, const EvalArgs& a) {
     const GridD& g = a.g;
     if (q.j >= g.ny || q.k >= g.nz || q.i0 >= g.nx) return;
-    float4* dst = a.far + ((int64_t)q.k * g.ny + q.j) * g.nx;
+    float4* dst = a.far + far_index(g.nx, g.ny, q.i0, q.j, q.k) - q.i0;  // PF points in a block row
 #pragma unroll
     for (int p = 0; p < PF; ++p)
         if (q.i0 + p < g.nx) dst[q.i0 + p] = make_float4(q.f1h[p], q.f1l[p], q.fkh[p], q.fkl[p]);
@@ -2004,13 +2017,12 @@ __global__ void __launch_bounds__(256) k_tdown(CPArgs c, float4* far, const Tree
         }
     }
     const int m0 = R.ext[0], m1 = R.ext[1], m2 = R.ext[2];
-    const int64_t plane = (int64_t)tb.ny * tb.nx;
     const bool field = la >= 0 && c.tflag[tbox_index(tb, la, A.ib, A.jb, A.kb)];
     if (!field) {
         for (int t = threadIdx.x; t < M * M * M; t += blockDim.x) {
             const int ix = t % M, iy = (t / M) % M, iz = t / (M * M);
             if (ix < m0 && iy < m1 && iz < m2)
-                far[(R.lo[2] + iz) * plane + (int64_t)(R.lo[1] + iy) * tb.nx + R.lo[0] + ix] =
+                far[far_index(tb.nx, tb.ny, R.lo[0] + ix, R.lo[1] + iy, R.lo[2] + iz)] =
                     make_float4(0.f, 0.f, 0.f, 0.f);
         }
         return;
@@ -2029,7 +2041,7 @@ __global__ void __launch_bounds__(256) k_tdown(CPArgs c, float4* far, const Tree
     __syncthreads();
     interp3<N1, M>(V, W, W + M * N1, W + 2 * M * N1, S1, S2, [&](int iz, int iy, int ix, float2 o) {
         if (ix < m0 && iy < m1 && iz < m2)
-            far[(R.lo[2] + iz) * plane + (int64_t)(R.lo[1] + iy) * tb.nx + R.lo[0] + ix] = make_float4(o.x, 0.f, o.y, 0.f);
+            far[far_index(tb.nx, tb.ny, R.lo[0] + ix, R.lo[1] + iy, R.lo[2] + iz)] = make_float4(o.x, 0.f, o.y, 0.f);
     });
 }
 
@@ -2386,8 +2398,10 @@ __device__ __forceinline__ void near_stage(NearPts<SM>& q, const NearConst& c, c
 }
 
 // Epilogue of one batch: the far-field sums of the point plus the near sums, assembled into u, c and h.
+// fr: the far-field records of the thread's two points (global memory or a shared-memory copy).
 template <int SM, bool DU, bool DH>
-__device__ __forceinline__ void near_finish(const NearPts<SM>& q, const NearConst& c, const EvalArgs& a) {
+__device__ __forceinline__ void near_finish(const NearPts<SM>& q, const NearConst& c, const EvalArgs& a,
+                                            const float4* fr) {
     constexpr int P = 2;
     const GridD& g = a.g;
     const int i0 = q.i0;
@@ -2398,10 +2412,9 @@ __device__ __forceinline__ void near_finish(const NearPts<SM>& q, const NearCons
     // Assembly in float pairs (error-free sums and products), one rounding to float per output, then the
     // float -> double conversion on the integer pipe: no FP64 arithmetic per grid point.
     float F1h[P], F1l[P], DC_[P], DH_[P];
-    const float4* fr = a.far + row;
 #pragma unroll
     for (int p = 0; p < P; ++p) {
-        const float4 f = (i0 + p < g.nx) ? fr[i0 + p] : make_float4(0.f, 0.f, 0.f, 0.f);
+        const float4 f = (i0 + p < g.nx) ? fr[p] : make_float4(0.f, 0.f, 0.f, 0.f);
         F1h[p] = f.x;
         F1l[p] = f.y;
         float s, e;
@@ -2512,7 +2525,7 @@ __device__ void near_body(const EvalArgs& a, int b, int sub, Ring<SM, true>& r, 
     }, [](int) {});
     if (rr != kRingDone) return;
     near_publish<Sh::NW>(r, a.meta, cnt3);
-    near_finish<SM, DU, DH>(q, c, a);
+    near_finish<SM, DU, DH>(q, c, a, a.far + far_index(a.g.nx, a.g.ny, q.i0, q.j, q.k));  // both in one block row
 }
 
 // ---- per-solute kernels
@@ -2544,6 +2557,8 @@ struct NearOcc {
     static constexpr int v = SM <= 4 ? ((DU && DH) ? 2 : 3) : 1;
 };
 
+constexpr int kFarBuf = 4;  // far-field record buffers of the persistent near kernel (sub-batches in flight)
+
 // Persistent near-field kernel of one solute: the producer of each CTA takes the next item (sub-batch) of the
 // heaviest-first order from the work queue and streams the near lists of its items through one ring
 // (run_stream), so the per-batch setup and epilogue overlap the loading of the next batch's sources.
@@ -2554,6 +2569,13 @@ __global__ void __launch_bounds__(NearShape<NXB, NYB, NZB>::NTP, (NearOcc<NXB, N
     constexpr int NS = Sh::NSUB;
     __shared__ Ring<SM, true> r;
     __shared__ float4 tab[2 * kNTab];
+    // far-field records of the last kFarBuf sub-batches (one 8x8x8 block of the far buffer each), copied by the
+    // producer with each sub-batch's first tile.  It runs at most kStages = 3 tiles, so 3 sub-batches, ahead of
+    // the slowest warp, whose epilogue reads sub-batch n - 4's buffer before it releases the tile that lets the
+    // producer start sub-batch n.
+    static_assert(Sh::SX == 8 && NYB == 8 && NZB == 8, "a sub-batch is one 8x8x8 block of the far buffer");
+    static_assert(kStages <= kFarBuf - 1, "the far-field buffers cover the sub-batches the producer runs ahead");
+    extern __shared__ __align__(16) float4 farbuf[];  // [kFarBuf][512], dynamic
     const int tid = threadIdx.x;
     if (a.meta->overflow) {  // incomplete lists: the host grows them and runs again
         if (tid == Sh::NT) queue_leave(a.wq);
@@ -2572,6 +2594,7 @@ __global__ void __launch_bounds__(NearShape<NXB, NYB, NZB>::NTP, (NearOcc<NXB, N
     const LJf* ljt = c.uni ? a.ljs2 : a.ljs;  // the two-wide tile reads {A, A, -B, -B}
     NearPts<SM> q;
     unsigned cnt3[3] = {0u, 0u, 0u};  // pairs tested / inside the LJ cut-off / inside r_short
+    int seq = 0;                      // sub-batches finished by this warp (the producer counts them alike)
     const int rr = run_stream<SM, true, Sh::NW>(
         r, a.wlim, a.err,
         [&](int, int& item, ItemSrc& is) {
@@ -2582,9 +2605,19 @@ __global__ void __launch_bounds__(NearShape<NXB, NYB, NZB>::NTP, (NearOcc<NXB, N
             is = ItemSrc{a.near_ent, b * a.near_cap, b * a.near_cap + a.near_cnt[b], a.srcf, ljt};
             return true;
         },
+        [&](int n, int item, uint64_t* bar) {
+            const int b = item / NS, ib = b % a.nbx, jb = (b / a.nbx) % a.nby, kb = b / (a.nbx * a.nby);
+            const int64_t blk = far_index(a.g.nx, a.g.ny, ib * NXB + (item % NS) * 8, jb * NYB, kb * NZB);
+            mbar_expect_tx_only(bar, 512 * sizeof(float4));
+            bulk_g2s(farbuf + (n % kFarBuf) * 512, a.far + blk, 512 * sizeof(float4), bar);
+        },
         [&](int item) { near_begin<NXB, NYB, NZB, SM>(q, a, item / NS, item % NS); },
         [&](int slot, int cnt) { near_stage<SM, DU, DH>(q, c, r.src[slot], r.lj[slot], cnt, tab, cnt3); },
-        [](int) {}, [&](int) { near_finish<SM, DU, DH>(q, c, a); });
+        [](int) {},
+        [&](int) {
+            near_finish<SM, DU, DH>(q, c, a, farbuf + (seq % kFarBuf) * 512 + ((q.k & 7) << 6 | (q.j & 7) << 3 | (q.i0 & 7)));
+            ++seq;
+        });
     if (rr == kRingDone) near_publish<Sh::NW>(r, a.meta, cnt3);
     if (tid == Sh::NT) queue_leave(a.wq);
 }
@@ -2684,13 +2717,16 @@ struct Kern {
     }
     static void near(const EvalArgs& a, int nb, cudaStream_t st) {
         // persistent: at most the CTAs that are resident at once
+        constexpr size_t dyn = sizeof(float4) * 512 * kFarBuf;  // far-field record buffers
         static const int resident = [] {
+            cudaFuncSetAttribute(k_near32<S::NX, S::NY, S::NZ, SM, DU, DH>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)dyn);
             int b = 0;
-            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_near32<S::NX, S::NY, S::NZ, SM, DU, DH>, S::NTN, 0);
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_near32<S::NX, S::NY, S::NZ, SM, DU, DH>, S::NTN, dyn);
             return std::max(1, b) * sm_count();
         }();
         const int items = nb * NearShape<S::NX, S::NY, S::NZ>::NSUB;
-        k_near32<S::NX, S::NY, S::NZ, SM, DU, DH><<<std::max(1, std::min(items, resident)), S::NTN, 0, st>>>(a);
+        k_near32<S::NX, S::NY, S::NZ, SM, DU, DH><<<std::max(1, std::min(items, resident)), S::NTN, dyn, st>>>(a);
     }
     static void far_b(const BatchEval& be, int grid, cudaStream_t st) {
         k_far32_batched<S::NX, S::NY, S::NZ, S::PF, DH><<<grid, S::FT, 0, st>>>(be);
@@ -2874,7 +2910,7 @@ rism_status tree_reserve(TreeState* s, const DevTables& t, const GridD& g, const
         s->smax = t.smax;
         s->deg = deg;
     }
-    const int64_t M = (int64_t)g.nx * g.ny * g.nz;
+    const int64_t M = far_points(g.nx, g.ny, g.nz);
     if (M > s->cap_far_pts) {
         if ((e = regrow(s->far, (size_t)M))) return cuda_err(err, e, "far-field buffer");
         s->cap_far_pts = M;
