@@ -329,14 +329,62 @@ __global__ void __launch_bounds__(kSortThreads) k_sort_build(BuildArgs a, uint32
     unsigned long long* sk = reinterpret_cast<unsigned long long*>(sh + 256 * 32 + 64);  // [kSortSmem]
     uint32_t* sc = reinterpret_cast<uint32_t*>(sk + kSortSmem);                          // [kSortSmem]
     if (in_smem) {
+        // Bucket sort on the top 10 bits of the code, one bucket per thread: count, scan, scatter, then each
+        // thread sorts its bucket by insertion on the unique 64-bit keys (the result does not depend on the
+        // order of the scatter).  A bucket of more than kBucketMax keys (clustered atoms) hands over to the
+        // bitonic sort below.
+        static_assert(kSortThreads == 1024 && kSortSmem % kSortThreads == 0, "one bucket per thread");
+        constexpr int KPT = kSortSmem / kSortThreads, kBucketShift = 3 * kMortonBits - 10, kBucketMax = 32;
+        int* bcnt = hist;  // [1024] keys per bucket (the radix histogram is unused on this path)
+        __shared__ int s_bmax;
+        if (threadIdx.x == 0) s_bmax = 0;
+        bcnt[threadIdx.x] = 0;
+        __syncthreads();
+        unsigned long long key[KPT];
+        int slot[KPT];
+#pragma unroll
+        for (int u = 0; u < KPT; ++u) {
+            const int i = threadIdx.x + u * kSortThreads;
+            const uint32_t cd = i < n ? code[i] : 0u;
+            key[u] = ((unsigned long long)cd << 32) | (i < n ? idx[i] : 0u);
+            slot[u] = i < n ? atomicAdd(&bcnt[cd >> kBucketShift], 1) : 0;
+        }
+        __syncthreads();
+        const int mycnt = bcnt[threadIdx.x];
+        atomicMax(&s_bmax, mycnt);
+        int total;
+        const int start = block_exclusive_scan(mycnt, tmp, total);
+        bcnt[kSortThreads + threadIdx.x] = start;  // bucket starts
+        __syncthreads();
+        const bool buckets = s_bmax <= kBucketMax;
+        if (buckets) {
+#pragma unroll
+            for (int u = 0; u < KPT; ++u) {
+                const int i = threadIdx.x + u * kSortThreads;
+                if (i < n) sk[bcnt[kSortThreads + ((uint32_t)(key[u] >> 32) >> kBucketShift)] + slot[u]] = key[u];
+            }
+            __syncthreads();
+            for (int x = start + 1; x < start + mycnt; ++x) {
+                const unsigned long long v = sk[x];
+                int y = x - 1;
+                while (y >= start && sk[y] > v) {
+                    sk[y + 1] = sk[y];
+                    --y;
+                }
+                sk[y + 1] = v;
+            }
+            __syncthreads();
+        }
         int N = 1;
         while (N < n) N <<= 1;
-        for (int i = threadIdx.x; i < N; i += blockDim.x)
-            sk[i] = i < n ? ((unsigned long long)code[i] << 32) | idx[i] : ~0ull;
-        __syncthreads();
+        if (!buckets) {
+            for (int i = threadIdx.x; i < N; i += blockDim.x)
+                sk[i] = i < n ? ((unsigned long long)code[i] << 32) | idx[i] : ~0ull;
+            __syncthreads();
+        }
         // a stage with j <= 32 pairs elements within the 64 of one warp (per 32 consecutive t), so between two
         // such stages the warp synchronises alone
-        for (int k = 2; k <= N; k <<= 1)
+        for (int k = 2; k <= (buckets ? 1 : N); k <<= 1)
             for (int j = k >> 1; j > 0; j >>= 1) {
                 for (int t = threadIdx.x; t < N / 2; t += blockDim.x) {
                     const int i = ((t & ~(j - 1)) << 1) | (t & (j - 1)), l = i + j;
