@@ -489,43 +489,43 @@ __global__ void __launch_bounds__(kSortThreads) k_sort_build(BuildArgs a, uint32
         for (int lvl = 0; lvl < kMaxLevel; ++lvl) {
             const int lb = s_lvl_begin, le = s_lvl_end;
             if (lb >= le) break;
-            for (int base = lb; base < le; base += blockDim.x) {
-                const int nid = base + threadIdx.x;
-                int cb[9];
-                int nch = 0;
+            // eight lanes per node: lane ch finds where child ch starts (a binary search over the node's range,
+            // the eight searches run side by side); children are numbered in digit order as before
+            for (int base = lb; base < le; base += blockDim.x / 8) {
+                const int nid = base + (threadIdx.x >> 3), ch = threadIdx.x & 7, g0 = lane & ~7;
+                Node nd{0, 0, -1, 0, 0, -1, 0, 0, {0, 0, 0}, {0, 0, 0}};
                 bool split = false;
+                int pos = 0;
                 if (nid < le) {
-                    const Node nd = store[nid];
+                    nd = store[nid];
                     split = (nd.end - nd.begin) > a.leaf;
                     if (split) {
                         const int sh3 = 3 * (kMortonBits - 1 - lvl);
-                        cb[0] = nd.begin;
-                        for (int ch = 1; ch < 8; ++ch) {
-                            // first position in [begin, end) whose child digit >= ch
-                            int lo = cb[ch - 1], hi = nd.end;
-                            while (lo < hi) {
-                                int mid = (lo + hi) >> 1;
-                                if ((int)((scode[mid] >> sh3) & 7u) < ch) lo = mid + 1; else hi = mid;
-                            }
-                            cb[ch] = lo;
+                        int lo = nd.begin, hi = nd.end;  // first position whose child digit >= ch
+                        while (lo < hi) {
+                            const int mid = (lo + hi) >> 1;
+                            if ((int)((scode[mid] >> sh3) & 7u) < ch) lo = mid + 1; else hi = mid;
                         }
-                        cb[8] = nd.end;
-                        for (int ch = 0; ch < 8; ++ch) nch += cb[ch + 1] > cb[ch];
+                        pos = lo;
                     }
                 }
+                const int nxt = __shfl_sync(0xffffffffu, pos, (lane & 7) == 7 ? lane : lane + 1);
+                const int cend = ch == 7 ? nd.end : nxt;
+                const bool ne = split && cend > pos;  // child ch is not empty
+                const unsigned grp = (__ballot_sync(0xffffffffu, ne) >> g0) & 0xffu;
+                const int nch = __popc(grp), before = __popc(grp & ((1u << ch) - 1u));
                 int total;
-                int off = block_exclusive_scan(nch, tmp, total);
+                const int off = __shfl_sync(0xffffffffu, block_exclusive_scan(ch == 0 ? nch : 0, tmp, total), g0);
                 const int start = s_nnodes;
-                if (nid < le && split) {
+                if (split) {
                     if (start + off + nch > cap) {
                         s_overflow = 1;
                     } else {
-                        store[nid].first_child = start + off;
-                        store[nid].nchild = nch;
-                        int k = start + off;
-                        for (int ch = 0; ch < 8; ++ch)
-                            if (cb[ch + 1] > cb[ch])
-                                store[k++] = Node{cb[ch], cb[ch + 1], -1, 0, lvl + 1, -1, 0, 0, {0, 0, 0}, {0, 0, 0}};
+                        if (ch == 0) {
+                            store[nid].first_child = start + off;
+                            store[nid].nchild = nch;
+                        }
+                        if (ne) store[start + off + before] = Node{pos, cend, -1, 0, lvl + 1, -1, 0, 0, {0, 0, 0}, {0, 0, 0}};
                     }
                 }
                 __syncthreads();
