@@ -121,7 +121,8 @@ typedef struct {
     double beta, kappa, r_short;
     int64_t natoms;
     int32_t nsite;
-    int32_t tree_nodes, tree_proxied, tree_leaves; /* treecode only */
+    int32_t tree_nodes, tree_proxied, tree_leaves; /* treecode only; tree_proxied: octree nodes given source
+                                                      proxies (0 when target boxes take the far field) */
     int64_t direct_pairs;  /* (grid point, atom) pairs evaluated directly by the last call */
     int64_t proxy_pairs;   /* (grid point, proxy point) pairs of the last call */
     int64_t near_pairs;    /* candidate pairs scanned by the cut-off (cell-list) pass */

@@ -556,19 +556,22 @@ __global__ void __launch_bounds__(kSortThreads) k_sort_build(BuildArgs a, uint32
         s_leaves = 0;
     }
     __syncthreads();
+    const bool plan = a.src != nullptr;  // the source proxies are wanted (no target boxes): lay out their work
     for (int base = 0; base < nn; base += blockDim.x) {
         const int nid = base + threadIdx.x;
         int isp = 0, nit = 0, leaf = 0;
         if (nid < nn) {
             const Node nd = store[nid];
             int cnt = nd.end - nd.begin;
-            isp = cnt > a.P3;
+            isp = plan && cnt > a.P3;
             nit = isp ? (cnt + kChunk - 1) / kChunk : 0;
             leaf = nd.first_child < 0;
         }
-        int tp, ti, tl;
-        int op = block_exclusive_scan(isp, tmp, tp);
-        int oi = block_exclusive_scan(nit, tmp, ti);
+        int tp = 0, ti = 0, tl, op = 0, oi = 0;
+        if (plan) {
+            op = block_exclusive_scan(isp, tmp, tp);
+            oi = block_exclusive_scan(nit, tmp, ti);
+        }
         block_exclusive_scan(leaf, tmp, tl);
         const int p0 = s_prox, i0 = s_items;
         if (nid < nn && isp) {

@@ -61,7 +61,8 @@ def test_globule2000_degree8_theta07(R):
     idx = _sampled(w)
     ref = O.fields(O.Problem.from_workload(w), idx=idx)
     g = run(R, w)
-    assert g["info"]["proxy_pairs"] + g["info"]["cp_pairs"] > 0 and g["info"]["tree_proxied"] > 0
+    # target boxes take the far field here: proxies at the boxes, none at the octree nodes
+    assert g["info"]["cp_pairs"] > 0 and g["info"]["tree_boxes"] > 0 and g["info"]["tree_proxied"] == 0
     gs = {k: g[k][:, idx] for k in ("u", "c", "h")}
     check_fields(gs, ref, ("u", "c", "h"), TREE_TOL, w.grid, w.solute.xyz, idx=idx, label="cfg1 tree")
 
