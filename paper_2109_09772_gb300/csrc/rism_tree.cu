@@ -1207,12 +1207,16 @@ __global__ void __launch_bounds__(32 * kListWarps) k_near_lists(ListArgs a, cons
     }
 }
 
-// Launch order of the near-field batches, heaviest first: a counting sort of the batches by the binary
-// order of magnitude of their candidate-atom count (one CTA).  The order changes nothing but which CTAs start
-// first (each batch is computed independently), so long batches do not trail at the end of the launch.
+// Launch order of the batches, heaviest first: a counting sort of the batches by the binary order of magnitude
+// of their work (one CTA per list: CTA 0 orders work0 into order0, CTA 1 work1 into order1).  The order changes
+// nothing but which CTAs start first (each batch is computed independently), so long batches do not trail at
+// the end of the launch.
 constexpr int kOrderBuckets = 33;
-__global__ void __launch_bounds__(1024) k_order(int nb, const int* __restrict__ work, int* order) {
+__global__ void __launch_bounds__(1024) k_order(int nb, const int* __restrict__ work0, int* order0,
+                                                const int* __restrict__ work1, int* order1) {
     __shared__ int hist[kOrderBuckets], start[kOrderBuckets];
+    const int* __restrict__ work = blockIdx.x == 0 ? work0 : work1;
+    int* order = blockIdx.x == 0 ? order0 : order1;
     const int tid = threadIdx.x;
     if (tid < kOrderBuckets) hist[tid] = 0;
     __syncthreads();
@@ -3179,9 +3183,8 @@ rism_status tree_enqueue(TreeState* s, const DevTables& t, const GridD& g, const
     k_far_lists<<<lgrid, 32 * kListWarps, 0, st>>>(fa, s->nodes, s->far_ent, s->far_cnt, s->far_work, s->meta);
     k_near_lists<<<lgrid, 32 * kListWarps, 0, st>>>(na, s->cell_start, s->near_ent, s->near_cnt, s->near_work,
                                                      s->meta);
-    k_order<<<1, 1024, 0, st>>>(s->nb, s->near_work, s->near_order);
-    k_order<<<1, 1024, 0, st>>>(s->nb, s->far_work, s->far_order);
-    s->launches += 4;
+    k_order<<<2, 1024, 0, st>>>(s->nb, s->near_work, s->near_order, s->far_work, s->far_order);
+    s->launches += 3;
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_err(err, e, "tree build");
     s->prepared = true;
@@ -3796,7 +3799,8 @@ rism_status batch_eval(std::vector<BatchItem>& items, const rism_options& o, cud
             cudaMemsetAsync(bc->d_queue, 0, sizeof(int) * 2, cs);
             for (int nr = 0; nr < 2; ++nr) {  // global heaviest-first orders over all (solute, batch) items
                 k_gather_work<<<count, 256, 0, cs>>>(bc->d_args, bc->d_off, count, nr, bc->d_work);
-                k_order<<<1, 1024, 0, cs>>>(off[count], bc->d_work, bc->d_order + (size_t)nr * off[count]);
+                k_order<<<1, 1024, 0, cs>>>(off[count], bc->d_work, bc->d_order + (size_t)nr * off[count], nullptr,
+                                            nullptr);
             }
             BatchEval be{bc->d_args, bc->d_off, count, off[count], bc->d_queue, bc->d_order};
             const bool du = items[0].o.u != nullptr, dh = items[0].o.h != nullptr;
