@@ -488,7 +488,9 @@ __global__ void __launch_bounds__(kSortThreads) k_sort_build(BuildArgs a, uint32
         __syncthreads();
         for (int lvl = 0; lvl < kMaxLevel; ++lvl) {
             const int lb = s_lvl_begin, le = s_lvl_end;
-            if (lb >= le) break;
+            // after an overflow the slots past the last written node hold no nodes: stop (uniform: shared flag
+            // read after a barrier)
+            if (lb >= le || s_overflow) break;
             // eight lanes per node: lane ch finds where child ch starts (a binary search over the node's range,
             // the eight searches run side by side); children are numbered in digit order as before
             for (int base = lb; base < le; base += blockDim.x / 8) {
@@ -498,7 +500,9 @@ __global__ void __launch_bounds__(kSortThreads) k_sort_build(BuildArgs a, uint32
                 int pos = 0;
                 if (nid < le) {
                     nd = store[nid];
-                    split = (nd.end - nd.begin) > a.leaf;
+                    // a range outside [0, n) would index past the codes: never split it (cannot happen for a node
+                    // this loop wrote; the check keeps the searches in bounds regardless)
+                    split = nd.begin >= 0 && nd.end <= n && (nd.end - nd.begin) > a.leaf;
                     if (split) {
                         const int sh3 = 3 * (kMortonBits - 1 - lvl);
                         int lo = nd.begin, hi = nd.end;  // first position whose child digit >= ch
@@ -531,6 +535,7 @@ __global__ void __launch_bounds__(kSortThreads) k_sort_build(BuildArgs a, uint32
                 __syncthreads();
                 if (threadIdx.x == 0) s_nnodes = min(start + total, cap);
                 __syncthreads();
+                if (s_overflow) break;
             }
             if (threadIdx.x == 0) {
                 s_lvl_begin = le;
@@ -549,6 +554,15 @@ __global__ void __launch_bounds__(kSortThreads) k_sort_build(BuildArgs a, uint32
     }
     // ---- proxy plan: nodes with more than P3 atoms get proxies; items of kChunk atoms
     const int nn = s_nnodes;
+    if (s_overflow) {  // the tree is incomplete: the host grows the node capacity and builds again
+        if (threadIdx.x == 0) {
+            meta->nnodes = nn;
+            meta->nprox = meta->nitems = meta->nleaves = 0;
+            meta->overflow = meta->build_overflow = 1;
+            prox_items[0] = 0;
+        }
+        return;
+    }
     __shared__ int s_prox, s_items, s_leaves;
     if (threadIdx.x == 0) {
         s_prox = 0;

@@ -234,3 +234,28 @@ def test_graph_replay_larger_solute_grows_lists(R):
         assert np.array_equal(out[k].cpu().numpy(), ref[k].cpu().numpy()), k
     r.close()
     r2.close()
+
+
+def test_build_fallbacks_clustered_atoms_and_many_nodes(R):
+    """The tree build's other paths against the oracle: a dense cluster of 1,100 atoms with three atoms 22 A away
+    crowds the sort's buckets (the build then sorts bitonically), and leaf = 1 gives more nodes than the
+    build keeps in shared memory (it builds again in global memory).  Both match the oracle and give the
+    same fields as the roomy build (leaf 32 on the same solute)."""
+    from dataclasses import replace
+
+    core = I.sphere_solute(1100, 7.5, 1.0, seed=11, min_spacing=1.0)
+    far = np.array([[22.0, 0.5, -1.0], [-21.5, 3.0, 2.0], [0.5, -21.0, 22.0]])  # tens of atoms share a bucket
+    sol = I.Solute(np.vstack([core.xyz, far]), np.concatenate([core.q, [0.5, -0.5, 0.0]]),
+                   np.concatenate([core.sigma, [3.0, 3.2, 3.4]]), np.concatenate([core.eps, [0.1, 0.15, 0.2]]))
+    base = I.small_workload(n_atoms=40, n=(100, 96, 104), h=0.5, seed=3, lj_rcut=6.0)
+    w = replace(base, solute=sol)
+    idx = np.union1d(I.sample_indices(w.grid.npts, 2500, seed=8), nearest_points(w.grid, sol.xyz))
+    ref = O.fields(O.Problem.from_workload(w), idx=idx)
+    roomy = run(R, w, leaf=32)
+    many = run(R, w, leaf=1)
+    assert many["info"]["tree_nodes"] > 1024 >= roomy["info"]["tree_nodes"]
+    for g, label in ((roomy, "leaf32"), (many, "leaf1")):
+        check_fields({k: g[k][:, idx] for k in ("u", "c", "h")}, ref, ("u", "c", "h"), TREE_TOL, w.grid, sol.xyz,
+                     idx=idx, label=label)
+    for k in ("u", "c", "h"):
+        assert rel_l2(many[k], roomy[k]) < TREE_TOL
