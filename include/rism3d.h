@@ -33,7 +33,8 @@
  *    owned by the caller.  They may be device memory (written asynchronously
  *    on the context's stream; the call returns before the kernels finish) or
  *    host memory (the library computes into its own device buffer, copies
- *    back and synchronises the stream before returning).
+ *    back -- the output grids concurrently, on separate copy streams -- and
+ *    synchronises the stream before returning).
  *  - Inputs given as host arrays are copied during the call; the caller keeps
  *    ownership and may free them on return.
  *  - The library never keeps a caller pointer beyond the call.

@@ -53,6 +53,9 @@ struct rism_ctx {
     GridD gd{};
     int setup_launches = 0;  // kernels launched by the last table rebuild
     cudaEvent_t ev[2] = {nullptr, nullptr};
+    // host outputs: one copy stream per output grid, so the device-to-host copies run on several copy engines
+    cudaStream_t cp_st[3] = {nullptr, nullptr, nullptr};
+    cudaEvent_t cp_fork = nullptr, cp_join[3] = {nullptr, nullptr, nullptr};
 };
 
 namespace {
@@ -328,6 +331,37 @@ rism_status rism_set_solvent(rism_ctx* c, int32_t nsite, const double* q, const 
     return RISM_OK;
 }
 
+namespace {
+
+// Device staging -> caller's host buffers for the outputs staged in device memory: each grid on its own stream
+// (forked from and joined back to the context's stream), so the copies overlap on several copy engines.
+rism_status copy_outputs(rism_ctx* c, double* const (&user)[3], double* const (&dev)[3], const bool (&staged)[3],
+                         size_t bytes) {
+    cudaError_t e = cudaSuccess;
+    int nhost = 0;
+    for (int k = 0; k < 3; ++k) nhost += staged[k];
+    if (nhost == 0) return RISM_OK;
+    if (!c->cp_fork) {
+        for (int k = 0; k < 3 && e == cudaSuccess; ++k)
+            if ((e = cudaStreamCreateWithFlags(&c->cp_st[k], cudaStreamNonBlocking)) == cudaSuccess)
+                e = cudaEventCreateWithFlags(&c->cp_join[k], cudaEventDisableTiming);
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&c->cp_fork, cudaEventDisableTiming);
+        if (e != cudaSuccess) return cuda_fail(c, e, "copy streams");
+    }
+    if ((e = cudaEventRecord(c->cp_fork, c->st)) != cudaSuccess) return cuda_fail(c, e, "copying result to host");
+    for (int k = 0; k < 3; ++k) {
+        if (!staged[k]) continue;
+        if ((e = cudaStreamWaitEvent(c->cp_st[k], c->cp_fork, 0)) != cudaSuccess ||
+            (e = cudaMemcpyAsync(user[k], dev[k], bytes, cudaMemcpyDeviceToHost, c->cp_st[k])) != cudaSuccess ||
+            (e = cudaEventRecord(c->cp_join[k], c->cp_st[k])) != cudaSuccess ||
+            (e = cudaStreamWaitEvent(c->st, c->cp_join[k], 0)) != cudaSuccess)
+            return cuda_fail(c, e, "copying result to host");
+    }
+    return RISM_OK;
+}
+
+}  // namespace
+
 rism_status rism_init(rism_ctx* c, double* u, double* c_lr, double* h_lr, double* lj_tail) {
     if (!c) return RISM_E_INVALID;
     if (!c->have_solute || !c->have_solvent) return fail(c, RISM_E_STATE, "set_solute and set_solvent first");
@@ -339,13 +373,17 @@ rism_status rism_init(rism_ctx* c, double* u, double* c_lr, double* h_lr, double
     const size_t bytes = sizeof(double) * (size_t)c->S * (size_t)M;
     double* user[3] = {u, c_lr, h_lr};
     double* dev[3] = {nullptr, nullptr, nullptr};
+    bool staged[3] = {false, false, false};  // computed into a device buffer and copied to the host buffer
     bool host_out = false;
     for (int k = 0; k < 3; ++k) {
         if (!user[k]) continue;
         if (is_device_ptr(user[k])) {
             dev[k] = user[k];
         } else {
+            // host memory (page-locked or not): computed into a device buffer, copied back.  Kernel stores
+            // straight into page-locked host memory measured slower here than the copy engines.
             host_out = true;
+            staged[k] = true;
             if (c->stage_bytes[k] < bytes) {
                 cudaFree(c->d_stage[k]);
                 c->d_stage[k] = nullptr;
@@ -357,11 +395,12 @@ rism_status rism_init(rism_ctx* c, double* u, double* c_lr, double* h_lr, double
         }
     }
     Outputs o{dev[0], dev[1], dev[2]};
-    // Graph-replayed step (treecode, new solute coordinates, device outputs, from the context's second
-    // treecode call on): solute upload from pinned memory, tables, tree, lists and evaluation in one launch.
+    // Graph-replayed step (treecode, new solute coordinates, from the context's second treecode call on; host
+    // outputs use the staging buffers): solute upload from pinned memory, tables, tree, lists and evaluation in
+    // one launch.
     const bool any_out = o.u || o.c || o.h;
     if (c->o.method == RISM_METHOD_TREECODE && any_out) ++c->tree_calls;
-    if (c->o.method == RISM_METHOD_TREECODE && c->dirty && c->n > 0 && !host_out && any_out && c->tree_calls > 1) {
+    if (c->o.method == RISM_METHOD_TREECODE && c->dirty && c->n > 0 && any_out && c->tree_calls > 1) {
         if ((s = reserve_tables(c)) != RISM_OK) return s;
         if (c->cap_h_raw < c->n) {
             cudaFreeHost(c->h_raw);
@@ -387,6 +426,10 @@ rism_status rism_init(rism_ctx* c, double* u, double* c_lr, double* h_lr, double
             if (!retry) {
                 if (lj_tail)
                     for (int k = 0; k < c->S; ++k) lj_tail[k] = tail ? c->h_tail[k] : 0.0;
+                if (host_out) {
+                    if ((st = copy_outputs(c, user, dev, staged, bytes)) != RISM_OK) return st;
+                    if ((e = cudaStreamSynchronize(c->st)) != cudaSuccess) return cuda_fail(c, e, "copying result to host");
+                }
                 c->dirty = false;
                 c->setup_launches = 0;
                 if (c->o.debug_flags & 2) c->info.eval_ms = c->info.box_ms + c->info.far_ms + c->info.near_ms;
@@ -437,11 +480,7 @@ rism_status rism_init(rism_ctx* c, double* u, double* c_lr, double* h_lr, double
                 return cuda_fail(c, e, "lj tail copy");
         }
     }
-    for (int k = 0; k < 3; ++k)
-        if (user[k] && dev[k] != user[k]) {
-            if ((e = cudaMemcpyAsync(user[k], dev[k], bytes, cudaMemcpyDeviceToHost, c->st)) != cudaSuccess)
-                return cuda_fail(c, e, "copying result to host");
-        }
+    if ((s = copy_outputs(c, user, dev, staged, bytes)) != RISM_OK) return s;
     (void)host_out;
     if (lj_tail && c->o.lj_mode != RISM_LJ_NONE && c->n > 0) c->info.launches += 1;
     // Status of the device-side bounded waits: synchronise and read the error word.
@@ -454,11 +493,7 @@ rism_status rism_init(rism_ctx* c, double* u, double* c_lr, double* h_lr, double
         for (int attempt = 0; attempt < 4 && st == RISM_OK && retry; ++attempt) {
             st = tree_prepare(c->tree, c->t, c->gd, c->ph, c->o, c->st, c->err);
             if (st == RISM_OK) st = tree_eval(c->tree, c->t, c->gd, c->ph, c->o, o, c->st, c->err, c->info);
-            for (int k = 0; k < 3 && st == RISM_OK; ++k)
-                if (user[k] && dev[k] != user[k]) {
-                    if ((e = cudaMemcpyAsync(user[k], dev[k], bytes, cudaMemcpyDeviceToHost, c->st)) != cudaSuccess)
-                        return cuda_fail(c, e, "copying result to host");
-                }
+            if (st == RISM_OK) st = copy_outputs(c, user, dev, staged, bytes);
             if (st == RISM_OK) st = check_device_error(c);
             if (st == RISM_OK) st = tree_post(c->tree, c->info, retry, c->err);
         }
@@ -603,6 +638,11 @@ void rism_destroy(rism_ctx* c) {
     for (int k = 0; k < 3; ++k) cudaFree(c->d_stage[k]);
     if (c->ev[0]) cudaEventDestroy(c->ev[0]);
     if (c->ev[1]) cudaEventDestroy(c->ev[1]);
+    for (int k = 0; k < 3; ++k) {
+        if (c->cp_st[k]) cudaStreamDestroy(c->cp_st[k]);
+        if (c->cp_join[k]) cudaEventDestroy(c->cp_join[k]);
+    }
+    if (c->cp_fork) cudaEventDestroy(c->cp_fork);
     delete c;
 }
 

@@ -259,3 +259,36 @@ def test_build_fallbacks_clustered_atoms_and_many_nodes(R):
                      idx=idx, label=label)
     for k in ("u", "c", "h"):
         assert rel_l2(many[k], roomy[k]) < TREE_TOL
+
+
+def test_host_outputs_through_replayed_step(R):
+    """Host output buffers, page-locked or pageable, take the replayed step too (from a context's second call
+    on) and arrive by concurrent copies from device buffers: equal to the device outputs bit for bit, also
+    after the atoms move."""
+    import torch
+
+    w = I.workload(1)
+    S, M = w.solvent.nsite, w.grid.npts
+    sol = w.solute
+    rd = R.from_workload(w, method=R.METHOD_TREECODE, precision=R.PREC_FP32)
+    rp = R.from_workload(w, method=R.METHOD_TREECODE, precision=R.PREC_FP32)
+    rq = R.from_workload(w, method=R.METHOD_TREECODE, precision=R.PREC_FP32)
+    pinned = [torch.empty((S, M), dtype=torch.float64).pin_memory().numpy() for _ in range(3)]
+    pageable = [np.empty((S, M)) for _ in range(3)]
+    tp, tq = np.zeros(S), np.zeros(S)
+    for step in range(3):
+        xyz = sol.xyz + (0.37 if step == 2 else 0.0)
+        rd.set_solute(xyz, sol.q, sol.sigma, sol.eps)
+        out = rd.init(lj_tail=True)
+        rp.set_solute(xyz, sol.q, sol.sigma, sol.eps)
+        rp.init_host(*pinned, tp)
+        rq.set_solute(xyz, sol.q, sol.sigma, sol.eps)
+        rq.init_host(*pageable, tq)
+        for i, k in enumerate(("u", "c", "h")):
+            ref = out[k].cpu().numpy().reshape(S, M)
+            assert np.array_equal(ref, pinned[i]), (step, k, "page-locked")
+            assert np.array_equal(ref, pageable[i]), (step, k, "pageable")
+        np.testing.assert_array_equal(np.asarray(out["lj_tail"]), tp)
+        np.testing.assert_array_equal(np.asarray(out["lj_tail"]), tq)
+    for r in (rd, rp, rq):
+        r.close()
