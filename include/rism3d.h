@@ -110,7 +110,9 @@ typedef struct {
                            default 1<<24 (a few seconds) */
     int32_t debug_flags;/* test hooks, 0 in production.  Bit 0: the direct kernels skip their first
                            bulk copy, so its wait runs out and the call returns RISM_E_TIMEOUT.
-                           Bit 1: time the evaluation kernel with CUDA events (rism_info.eval_ms). */
+                           Bit 1: time the evaluation kernel with CUDA events (rism_info.eval_ms).
+                           Bits 4-5 (treecode, autotune off): v + 1 runs launch shape v (0-2; see
+                           rism_info.kernel_variant) instead of shape 0. */
     int32_t target_proxies; /* treecode: 1 (default) = grid boxes of 16^3 points and up also take (n+1)^3
                                Chebyshev proxy targets: a cluster that meets the acceptance criterion for a
                                box is summed at the box's proxies and reaches its grid points by

@@ -3411,9 +3411,17 @@ void tree_destroy(TreeState* s) {
     delete s;
 }
 
+// Without the autotuner: the leaf size of the options and launch shape 0, or the shape that debug_flags bits 4-5
+// name (value v + 1 forces shape v; a test hook).
+static void fixed_shape(TreeState* s, const rism_options& o) {
+    s->leaf = o.leaf;
+    const int v = (o.debug_flags >> 4) & 3;
+    s->variant = v >= 1 && v <= kNumShapes ? v - 1 : 0;
+}
+
 rism_status tree_prepare(TreeState* s, const DevTables& t, const GridD& g, const Phys& ph, const rism_options& o,
                          cudaStream_t st, std::string& err) {
-    if (!o.autotune) s->leaf = o.leaf;
+    if (!o.autotune) fixed_shape(s, o);
     rism_status r = tree_reserve(s, t, g, ph, o, err);
     if (r != RISM_OK) return r;
     return tree_enqueue(s, t, g, ph, o, st, err);
@@ -3599,7 +3607,7 @@ rism_status tree_graph_step(TreeState* s, const DevTables& t, const GridD& g, co
                             bool& used) {
     used = false;
     if (o.autotune && s->tuned_key != problem_class(t, g, ph, o)) return RISM_OK;  // time the candidates first
-    if (!o.autotune) s->leaf = o.leaf;
+    if (!o.autotune) fixed_shape(s, o);
     rism_status r = tree_reserve(s, t, g, ph, o, err);
     if (r != RISM_OK) return r;
     const EvalArgs a = make_args(s, t, g, ph, o, out);

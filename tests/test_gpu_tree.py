@@ -292,3 +292,15 @@ def test_host_outputs_through_replayed_step(R):
         np.testing.assert_array_equal(np.asarray(out["lj_tail"]), tq)
     for r in (rd, rp, rq):
         r.close()
+
+
+@pytest.mark.parametrize("shape", [0, 1, 2])
+def test_each_launch_shape(R, shape):
+    """Each launch shape (8x8x8 with 4 far points per thread, 16x8x8 with two near sub-batches per batch, 8x8x8
+    with 8 far points per thread), forced through the debug hook, against the oracle on the 2,000-atom globule."""
+    w = I.workload(1)
+    idx = I.sample_indices(w.grid.npts, 1500, seed=21)
+    ref = O.fields(O.Problem.from_workload(w), idx=idx)
+    g = run(R, w, debug_flags=(shape + 1) << 4)
+    assert g["info"]["kernel_variant"] == shape
+    check_fields({k: g[k][:, idx] for k in ("u", "c", "h")}, ref, ("u", "c", "h"), TREE_TOL, label=f"shape{shape}")
