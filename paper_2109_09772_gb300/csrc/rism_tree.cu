@@ -19,14 +19,16 @@
 // erfc remainders of eq. (dcf-r)/(tcf-r) within r_short -- are summed over
 // the atoms of the cells that intersect the batch box grown by the largest
 // cut-off.  The cells are Morton-code prefixes of the same sorted order the
-// tree is built from, so one device radix sort serves both.
+// tree is built from, so one device sort serves both.
 //
 // Pipeline (all on the context's stream, no host synchronisation, so that it
 // can be captured in a CUDA graph):
 //   k_bounds -> k_codes (Morton cube, codes, near-field plan) -> k_sort_build
-//   (one CTA: radix sort, sorted sources, octree, proxy plan, node boxes)
-//   -> k_cells -> k_upward -> k_proxy_reduce
-//   -> k_far_lists / k_near_lists (one warp per batch, per-batch slots)
+//   (one CTA: sort, octree, proxy plan, node boxes) -> k_gather_cells (sorted
+//   tables, cell table) -> k_upward -> k_proxy_reduce (source proxies only)
+//   -> k_tbox_lists per level (target boxes) -> k_far_lists / k_near_lists
+//   (one warp per batch, per-batch slots) -> k_order -> k_cp_eval ->
+//   k_cp_reduce -> k_l2l per level -> k_tdown (box-level far field)
 //   -> k_far32 (far field) -> k_near32 (near field + epilogue).
 // Many solutes: the same per-solute preparation, then one persistent far
 // and one persistent near kernel draining all (solute, batch) work items.
@@ -460,7 +462,7 @@ __global__ void __launch_bounds__(kSortThreads) k_sort_build(BuildArgs a, uint32
     // the level-by-level phases below do not wait on global memory between levels
     float* spos = reinterpret_cast<float*>(sc + kSortSmem);  // [kSortSmem][3]
     Node* snodes = reinterpret_cast<Node*>(spos + 3 * kSortSmem);  // [kNodeSmem]
-    // sorted high-part positions for the bounding boxes (the sorted tables themselves: k_gather_sorted)
+    // sorted high-part positions for the bounding boxes (the sorted tables themselves: k_gather_cells)
     if (in_smem)
         for (int i = threadIdx.x; i < n; i += blockDim.x) {
             const float4 f = *reinterpret_cast<const float4*>(&a.srcf[(uint32_t)sk[i]].xh);
@@ -673,10 +675,13 @@ __global__ void __launch_bounds__(kSortThreads) k_sort_build(BuildArgs a, uint32
         for (int k = threadIdx.x; k < nn; k += blockDim.x) nodes[k] = store[k];
 }
 
-// Sorted copies of the sources (FP64 grid units when the source proxies need them, float-float) and of the LJ
-// tables, in the order of the sorted codes; one thread per atom.
-__global__ void k_gather_sorted(BuildArgs a, const uint32_t* __restrict__ idx) {
-    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < a.n; i += gridDim.x * blockDim.x) {
+// After the sort, in one launch: the sorted copies of the sources (FP64 grid units when the source proxies need
+// them, float-float) and of the LJ tables, one thread per atom; and the near-field cell table, cell_start[m] =
+// first sorted position whose level-lc Morton prefix is >= m, one thread per cell.
+__global__ void k_gather_cells(BuildArgs a, const uint32_t* __restrict__ idx, const TreeMeta* meta,
+                               const uint32_t* __restrict__ code, int* cell_start) {
+    const int t0 = blockIdx.x * blockDim.x + threadIdx.x, stride = gridDim.x * blockDim.x;
+    for (int i = t0; i < a.n; i += stride) {
         const int j = (int)idx[i];
         if (a.src) a.src[i] = to_grid(a.geo[j], a.gd, a.ih);
         a.ssrcf[i] = a.srcf[j];
@@ -686,15 +691,11 @@ __global__ void k_gather_sorted(BuildArgs a, const uint32_t* __restrict__ idx) {
             a.ljs2[(int64_t)i * a.smax + s] = LJf{l.A, l.A, -l.B, -l.B};
         }
     }
-}
-
-// cell_start[m] = first sorted position whose level-lc Morton prefix is >= m.
-__global__ void k_cells(int n, const TreeMeta* meta, const uint32_t* code, int* cell_start) {
     const int lc = meta->lc;
     const int ncell = 1 << (3 * lc);
     const int sh = 3 * (kMortonBits - lc);
-    for (int m = blockIdx.x * blockDim.x + threadIdx.x; m <= ncell; m += gridDim.x * blockDim.x) {
-        int lo = 0, hi = n;
+    for (int m = t0; m <= ncell; m += stride) {
+        int lo = 0, hi = a.n;
         while (lo < hi) {
             int mid = (lo + hi) >> 1;
             if ((int)(code[mid] >> sh) < m) lo = mid + 1; else hi = mid;
@@ -3164,9 +3165,8 @@ rism_status tree_enqueue(TreeState* s, const DevTables& t, const GridD& g, const
         cudaFuncSetAttribute(k_sort_build, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shb);
         k_sort_build<<<1, kSortThreads, shb, st>>>(ba, s->code, s->idx, s->code2, s->idx2, s->nodes, s->items,
                                                    s->prox_nodes, s->prox_items, s->meta);
-        k_gather_sorted<<<std::min((n + 255) / 256, 4 * sm_count()), 256, 0, st>>>(ba, s->idx);
-        k_cells<<<1024, 256, 0, st>>>(n, s->meta, s->code, s->cell_start);
-        s->launches += 5;
+        k_gather_cells<<<1024, 256, 0, st>>>(ba, s->idx, s->meta, s->code, s->cell_start);
+        s->launches += 4;
         if (!s->tb.enabled) {
             // source proxies: only the batch-level traversal uses them (with target boxes on, the box level
             // accepts every cluster a batch would)
