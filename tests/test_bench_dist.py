@@ -51,3 +51,28 @@ def test_single_rank_without_process_group():
     assert bench.job_value(1, 4, 1000, 2.0) == pytest.approx(4 * 1000 / 2e-3 / 1e9)
     a, b = bench._workload(seed=0), bench._workload(seed=1)
     assert a.solute.n == b.solute.n and not np.allclose(a.solute.xyz, b.solute.xyz)
+
+
+def test_reference_arm_json_line_on_cpu():
+    """`bench.py --impl reference` (the oracle on the host cores) prints one JSON line with the bench's metric and
+    unit and no transfers; a rank other than 0 prints nothing and exits 0."""
+    import json
+    import subprocess
+    import sys
+
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    cmd = [sys.executable, os.path.join(root, "bench.py"), "--impl", "reference", "--steps", "1", "--warmup", "3",
+           "--ref-points", "200"]
+    r = subprocess.run(cmd, cwd=root, capture_output=True, text=True, timeout=300)
+    assert r.returncode == 0, r.stderr[-2000:]
+    lines = [ln for ln in r.stdout.splitlines() if ln.strip()]
+    assert len(lines) == 1
+    d = json.loads(lines[0])
+    import bench
+
+    assert d["impl"] == "reference" and d["metric"] == bench.METRIC and d["unit"] == bench.UNIT
+    assert d["value"] > 0 and d["higher_is_better"] is True and d["steps"] == 1
+    assert d["cpu_baseline"]["kind"] == "oracle" and d["cpu_baseline"]["value"] == d["value"]
+    assert d["e2e"]["h2d_bytes_per_step"] == 0 and d["e2e"]["d2h_bytes_per_step"] == 0
+    r1 = subprocess.run(cmd, cwd=root, capture_output=True, text=True, timeout=300, env=dict(os.environ, RANK="1"))
+    assert r1.returncode == 0 and r1.stdout.strip() == ""
