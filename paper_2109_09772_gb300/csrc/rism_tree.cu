@@ -815,9 +815,10 @@ __global__ void k_proxy_reduce(int deg, int n, const TreeMeta* meta, const Node*
 
 // ------------------------------------------------------- target batches
 // A target batch is NXB x NYB x NZB grid points.  The far kernel gives each
-// thread PF consecutive x points, the near kernel 4; both run one CTA per
-// batch (or per work item of the persistent batched kernels).  The variants
-// are the launch shapes the autotuner chooses from.
+// thread PF consecutive x points and runs one CTA per batch; the near kernel
+// works on sub-batches 8 points wide, a 4x4x4 block per warp and two points
+// per lane, in persistent CTAs (the batched kernels: per work item).  The
+// variants are the launch shapes the autotuner chooses from.
 struct ShapeDesc {
     int nx, ny, nz, pf;
 };
@@ -1270,8 +1271,8 @@ __global__ void k_reset_meta(TreeMeta* meta) {
 }
 
 // ---------------------------------------------------------------- eval
-// Sources reach shared memory through bulk TMA copies issued by thread 0
-// into a kStages-deep ring of tiles guarded by full (copy landed) and empty
+// Sources reach shared memory through bulk TMA copies issued by one producer
+// lane into a kStages-deep ring of tiles guarded by full (copy landed) and empty
 // (all warps done) mbarriers; every wait is bounded.
 constexpr int kStages = 3;
 constexpr int kNTab = 128;  // segments of the short-range kernel tables over [0, r_short]
@@ -1336,7 +1337,7 @@ struct Ring {
     int last[kStages];           // item stream: nonzero on the last tile of its item
 };
 
-// Range-list producer state (thread 0).
+// Range-list producer state (the producer lane).
 struct Cursor {
     int e, e_end, off;
     int left;              // sources still to deliver (a chunk of the list), INT_MAX: the whole list
@@ -1377,7 +1378,7 @@ __device__ __forceinline__ void produce(Cursor& c, R& r, int slot, const int2* e
     mbar_arrive(&r.full[slot]);
 }
 
-// Ring setup for one work item (thread 0), with the barriers of a previous
+// Ring setup for one work item (one thread), with the barriers of a previous
 // item invalidated first.  Callers put a __syncthreads() on both sides.
 template <typename R>
 __device__ void ring_init(R& r, int nwarps) {
