@@ -3,9 +3,11 @@
 One step = one whole initialization of one solute through the C ABI:
 solute upload, per-pair tables (mixing, cut-offs), tree build, proxy charges,
 interaction lists, evaluation of u, c_lr, h_lr for every grid point and
-solvent site, and the LJ tail integrals.  Workload: the 2,000-atom globule
-(net +8) on a 128^3 grid at 0.5 A with water O/H + 0.1 M Na+/Cl- sites,
-LJ cut-off 9 A, treecode degree 8, theta 0.7 (synthetic, seeded).
+solvent site, and the LJ tail integrals.  Default workload: the
+tubulin-dimer-sized solute -- 13,600 atoms in a prolate 80x65x45 A ellipsoid
+(net -24) on a 224x192x160 grid at 0.5 A with water O/H + 0.1 M Na+/Cl-
+sites, LJ cut-off 9 A, treecode degree 8, theta 0.7 (synthetic, seeded).
+``--workload globule2000`` runs the 2,000-atom globule on 128^3 instead.
 
 value  = grid-point x site evaluations per second (Gpts.site/s), device
          outputs, CUDA events on the library's stream, L2 flushed between
@@ -35,13 +37,25 @@ if ROOT not in sys.path:
 
 METRIC = "grid-pt·site evals/s & init time per solute at stated error vs FP64 direct"
 UNIT = "Gpts·site/s"
-WORKLOAD = "globule2000_128cubed"
+# name -> (index of the seeded workload definition, name of the workload with its sizes)
+WORKLOADS = {"ellipsoid13600": (2, "ellipsoid13600_224x192x160"), "globule2000": (1, "globule2000_128cubed")}
+DEFAULT_WORKLOAD = "ellipsoid13600"
+WORKLOAD = WORKLOADS[DEFAULT_WORKLOAD][1]
+
+
+def _select(name):
+    global WORKLOAD
+    WORKLOAD = WORKLOADS[name][1]
+    return WORKLOADS[name][0]
+
+
+_WIDX = [WORKLOADS[DEFAULT_WORKLOAD][0]]
 
 
 def _workload(seed=0):
     from paper_2109_09772_gb300 import inputs as I
 
-    return I.workload(1, seed=seed)
+    return I.workload(_WIDX[0], seed=seed)
 
 
 def reduce_max(dist, v, device):
@@ -66,7 +80,8 @@ def _config(w, method, precision):
             "sites": w.solvent.nsite, "lj_rcut_A": w.opts.get("lj_rcut"), "degree": w.opts.get("degree"),
             "theta": w.opts.get("theta"), "method": method, "precision": precision, "autotune": True,
             "outputs": "u, c_lr, h_lr (FP64 grids) + LJ tail integrals",
-            "l2": "flushed before every timed step by a 256 MB write (outputs are 201 MB, inputs 96 KB)"}
+            "l2": f"flushed before every timed step by a 256 MB write (outputs {3 * w.solvent.nsite * w.grid.npts * 8 / 1e6:.0f} MB, "
+                  f"inputs {w.solute.n * 48 / 1e3:.0f} KB)"}
 
 
 class Clocks:
@@ -144,11 +159,12 @@ FLOPS_LJ_SITE = 4
 FLOPS_LJ_SHARED = 2
 FP32_LANES_PER_SM = 128
 SMS = 152
-# DRAM bytes per launch on this workload (dram__bytes_read.sum + dram__bytes_write.sum of one ncu capture of
-# the kernel as it stands); None when the kernel has changed since the capture.
-FAR_TRAFFIC_BYTES = 34063104     # 34,052,352 read (the far-field buffer it starts from) + 10,752 written
-NEAR_TRAFFIC_BYTES = 187017216   # 34,521,600 read (far field) + 152,495,616 written (u, c, h)
-BOX_TRAFFIC_BYTES = None         # several kernels
+# DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum of one ncu capture of the kernel as it
+# stands), per workload; None when the kernel has changed since the capture or no capture was taken.
+TRAFFIC_BYTES = {
+    "ellipsoid13600_224x192x160": {"k_far32": None, "k_near32": None, "box": None},
+    "globule2000_128cubed": {"k_far32": None, "k_near32": None, "box": None},
+}
 
 
 def _alu_peak_tflops(sm_mhz):
@@ -218,30 +234,32 @@ def run_gpu(args):
     ms = reduce_max(dist, sum(times) / len(times), "cuda")
     value = job_value(world, S, M, ms)
 
-    # end to end: host (pinned) output buffers, device-to-host copies inside the timed region
-    hu = torch.empty((S, M), dtype=torch.float64).pin_memory()
-    hc = torch.empty((S, M), dtype=torch.float64).pin_memory()
-    hh = torch.empty((S, M), dtype=torch.float64).pin_memory()
-    tail = np.zeros(S)
-    P = lambda t: t.numpy()
+    e2e = None
+    if not args.no_e2e:
+        # end to end: host (pinned) output buffers, device-to-host copies inside the timed region
+        hu = torch.empty((S, M), dtype=torch.float64).pin_memory()
+        hc = torch.empty((S, M), dtype=torch.float64).pin_memory()
+        hh = torch.empty((S, M), dtype=torch.float64).pin_memory()
+        tail = np.zeros(S)
+        P = lambda t: t.numpy()
 
-    def step_host():
-        r.set_solute(xyz, q, sg, ep)
-        r.init_host(P(hu), P(hc), P(hh), tail)
+        def step_host():
+            r.set_solute(xyz, q, sg, ep)
+            r.init_host(P(hu), P(hc), P(hh), tail)
 
-    for _ in range(2):
-        step_host()
-    et = []
-    for _ in range(max(3, min(args.steps, 10))):
-        flush.fill_(1.0)
-        torch.cuda.synchronize()
-        t0 = time.perf_counter()
-        step_host()
-        et.append(time.perf_counter() - t0)
-    e2e_ms = reduce_max(dist, 1e3 * sum(et) / len(et), "cuda")
-    e2e = {"value": job_value(world, S, M, e2e_ms), "unit": UNIT, "ms_per_step": e2e_ms,
-           "h2d_bytes_per_step": int(xyz.nbytes + q.nbytes + sg.nbytes + ep.nbytes),
-           "d2h_bytes_per_step": int(3 * S * M * 8 + S * 8)}
+        for _ in range(2):
+            step_host()
+        et = []
+        for _ in range(max(3, min(args.steps, 10))):
+            flush.fill_(1.0)
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            step_host()
+            et.append(time.perf_counter() - t0)
+        e2e_ms = reduce_max(dist, 1e3 * sum(et) / len(et), "cuda")
+        e2e = {"value": job_value(world, S, M, e2e_ms), "unit": UNIT, "ms_per_step": e2e_ms,
+               "h2d_bytes_per_step": int(xyz.nbytes + q.nbytes + sg.nbytes + ep.nbytes),
+               "d2h_bytes_per_step": int(3 * S * M * 8 + S * 8)}
 
     # accuracy of this step against the FP64 oracle at sampled points (rank 0 only; not timed)
     acc = None
@@ -249,12 +267,17 @@ def run_gpu(args):
         from oracle import oracle as O
         from paper_2109_09772_gb300 import inputs as I
 
-        idx = I.sample_indices(M, 2000, seed=7)
+        # random points plus the grid point nearest each atom (where |u| peaks)
+        nx, ny, nz = w.grid.n
+        ijk = np.rint((w.solute.xyz - np.asarray(w.grid.origin)) / w.grid.h).astype(np.int64)
+        ijk = np.clip(ijk, 0, np.array([nx - 1, ny - 1, nz - 1]))
+        idx = np.union1d(I.sample_indices(M, args.check_points, seed=7), (ijk[:, 2] * ny + ijk[:, 1]) * nx + ijk[:, 0])
         ref = O.fields(O.Problem.from_workload(w), idx=idx)
-        acc = {}
+        acc = {"points": int(idx.size)}
         for k in ("u", "c", "h"):
             g = out[k].reshape(S, -1)[:, torch.as_tensor(idx, device="cuda")].cpu().numpy()
             acc[k] = float(np.linalg.norm(g - ref[k]) / np.linalg.norm(ref[k]))
+            acc[k + "_max_abs_over_max"] = float(np.abs(g - ref[k]).max() / np.abs(ref[k]).max())
 
     # rooflines of the evaluation kernels (CUDA events on the library stream); "roofline" is the dominant one
     inf = r.info()
@@ -271,11 +294,11 @@ def run_gpu(args):
         near_inst = (inf["near_tested"] * NEAR_TESTED + inf["lj_pairs"] * (NEAR_LJ_BASE + NEAR_LJ_SITE * S) +
                      inf["sr_pairs"] * (NEAR_SR_BASE + NEAR_SR_FIELD * nf))
         for name, t_ms, work, peak, unit, bound, traffic, desc in (
-                ("k_far32", mean(far_ms), pairs_far, xu_peak, "Gpairs/s", "alu", FAR_TRAFFIC_BYTES,
+                ("k_far32", mean(far_ms), pairs_far, xu_peak, "Gpairs/s", "alu", TRAFFIC_BYTES[WORKLOAD]["k_far32"],
                  "far field of the target batches: direct and source-proxy pairs; MUFU-bound"),
                 ("box level (k_cp_eval + interpolation)", mean(box_ms), inf["cp_pairs"], xu_peak, "Gpairs/s", "alu",
-                 BOX_TRAFFIC_BYTES, "proxy-target pairs, timed with the downward pass and interpolation"),
-                ("k_near32", mean(near_ms), near_inst, issue_peak, "Tinst/s", "alu", NEAR_TRAFFIC_BYTES,
+                 TRAFFIC_BYTES[WORKLOAD]["box"], "proxy-target pairs, timed with the downward pass and interpolation"),
+                ("k_near32", mean(near_ms), near_inst, issue_peak, "Tinst/s", "alu", TRAFFIC_BYTES[WORKLOAD]["k_near32"],
                  "near field + epilogue: algorithmic instructions of the tested / LJ / short-range pairs against "
                  "the issue rate (4 schedulers x 32 lanes x clock per SM)")):
             if t_ms <= 0:
@@ -302,7 +325,8 @@ def run_gpu(args):
               "eval_ms": sum(evals) / len(evals) if evals else None}
     res = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
            "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
-           "vs_baseline": None, "dtype": "f32 pair terms, f64 accumulate/output" if prec == R.PREC_FP32 else "f64",
+           "vs_baseline": None, "dtype": ("f32 (FP32 pair terms, float-float sums, each output rounded to FP32 and stored as FP64)"
+                     if prec == R.PREC_FP32 else "f64"),
            "data": "synthetic (seeded globule, protein density)",
            "config": _config(w, args.method, args.precision), "e2e": e2e, "gpu_launches": launches,
            "clocks": ck, "roofline": roof, "roofline_kernels": kern, "timing": timing,
@@ -587,11 +611,11 @@ def suite_adjoint(args):
 
 
 def suite_mufu(args):
-    """Issue rates of rsqrt / ex2 / rcp / FFMA (thread ops per clock per SM): compiles and runs the
-    microbenchmark in paper_2109_09772_gb300/microbench (the denominators of the pair kernels' rooflines)."""
+    """Issue rates of rsqrt / ex2 / rcp / FFMA / DFMA (thread ops per clock per SM): compiles and runs the
+    microbenchmark in microbench/ (the denominators of the pair kernels' rooflines)."""
     import tempfile
 
-    src = os.path.join(ROOT, "paper_2109_09772_gb300", "microbench", "mufu_rates.cu")
+    src = os.path.join(ROOT, "microbench", "mufu_rates.cu")
     with tempfile.TemporaryDirectory() as d:
         exe = os.path.join(d, "mufu_rates")
         subprocess.run(["nvcc", "-gencode", "arch=compute_103a,code=sm_103a", "-O3", "-o", exe, src], check=True)
@@ -608,14 +632,18 @@ def main():
     ap.add_argument("--method", default="treecode", choices=["treecode", "direct"])
     ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64"])
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
-    ap.add_argument("--ref-points", type=int, default=100000)
+    ap.add_argument("--ref-points", type=int, default=30000)
+    ap.add_argument("--workload", default=DEFAULT_WORKLOAD, choices=sorted(WORKLOADS))
+    ap.add_argument("--check-points", type=int, default=20000)
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-fp64", action="store_true")
     ap.add_argument("--no-check", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--suite", default=None, choices=["pareto", "batched", "adjoint", "mufu"])
     ap.add_argument("--reps", type=int, default=3)
     ap.add_argument("--adj-atoms", type=int, default=16)
     args = ap.parse_args()
+    _WIDX[0] = _select(args.workload)
     if args.suite:
         {"pareto": suite_pareto, "batched": suite_batched, "adjoint": suite_adjoint,
          "mufu": suite_mufu}[args.suite](args)

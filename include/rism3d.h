@@ -83,7 +83,7 @@ enum { RISM_LJ_NONE = 0, RISM_LJ_RCUT = 1, RISM_LJ_TOL = 2 };
 typedef struct rism_ctx rism_ctx;
 
 typedef struct {
-    int32_t nx, ny, nz;  /* grid points per axis, each >= 1 */
+    int32_t nx, ny, nz;  /* grid points per axis, 1 <= n <= 65535, at most 2^36 points in all */
     double h;            /* spacing (A), > 0 */
     double origin[3];    /* position of grid point (0,0,0) (A) */
 } rism_grid_desc;
@@ -208,31 +208,36 @@ RISM_API rism_status rism_potential_batched(rism_ctx* const* ctxs, int32_t count
 
 /* rism_init_noalloc -- the direct-sum initialization without any device
  * allocation.  The paper has no counterpart: this exists for callers that
- * cannot call cudaMalloc -- code running while a stream is being captured
- * into a CUDA graph (allocation is not a capturable operation), plug-ins
- * whose host application owns the device memory and forbids other
- * allocators, and embedded or real-time callers that must not allocate
- * after start-up.  It computes what rism_init computes with method
- * RISM_METHOD_DIRECT (FP32 or FP64 pairs; opts->method must be DIRECT) and
- * calls no cudaMalloc, cudaFree or other allocating routine.
+ * cannot call cudaMalloc -- plug-ins whose host application owns the device
+ * memory and forbids other allocators, and embedded or real-time callers
+ * that must not allocate after start-up.  It computes what rism_init
+ * computes with method RISM_METHOD_DIRECT (FP32 or FP64 pairs;
+ * opts->method must be DIRECT) and calls no cudaMalloc, cudaFree or other
+ * allocating routine.
  *
  * Its scratch (the per-atom and per-(atom, site) tables) lives in one
  * file-scope __device__ array of 4,063,488 bytes (RISM_NOALLOC_MAX_ATOMS
  * atoms, RISM_MAX_SITES sites), which every GPU that loads the library holds
  * until the process exits.  The first call on a device looks up that
- * array's device address (cudaGetSymbolAddress) with the device current;
- * make that first call before any stream capture.  Every call shares the
- * array: calls that overlap on the GPU (several streams, several host
- * threads) race and must be serialised by the caller.
+ * array's device address (cudaGetSymbolAddress) with the device current.
+ * Every call shares the array and leaves its contents behind: calls that
+ * overlap on the GPU (several streams, several host threads) race and must
+ * be serialised by the caller.
  *
- * grid, opts: as for rism_grid_create.  n (0 <= n <= RISM_NOALLOC_MAX_ATOMS),
- * xyz [n][3], q, sigma, eps: the solute, device or host memory, read during
- * the call.  nsite, qs, sigs, epss, rho (nullable), is_ion (nullable): the
- * solvent, host memory.  u, c_lr, h_lr: device outputs [S][nz][ny][nx], each
- * nullable (h_lr needs kappa > 0).  stream: cudaStream_t (NULL = legacy
- * default); the call synchronises it before returning.  errbuf (nullable,
- * errlen bytes) receives a message on failure.  n above the maximum returns
- * RISM_E_INVALID without touching the GPU. */
+ * grid, opts: as for rism_grid_create (same checks).  n (0 <= n <=
+ * RISM_NOALLOC_MAX_ATOMS), xyz [n][3], q, sigma, eps: the solute, device or
+ * host memory, copied during the call; host arrays get the checks of
+ * rism_set_solute before the GPU is touched, device arrays the same checks
+ * on the GPU (RISM_E_INVALID after the call, outputs then unspecified).
+ * nsite, qs, sigs, epss, rho (nullable), is_ion (nullable): the solvent,
+ * host memory, checked as by rism_set_solvent.  u, c_lr, h_lr: outputs
+ * [S][nz][ny][nx], each nullable (h_lr needs kappa > 0); they must be device
+ * (or managed) memory -- a host pointer returns RISM_E_INVALID and nothing
+ * is launched.  stream: cudaStream_t (NULL = legacy default); the call reads
+ * the device error word back into host memory and synchronises the stream
+ * before returning.  errbuf (nullable, errlen bytes) receives a message on
+ * failure.  n above the maximum returns RISM_E_INVALID without touching the
+ * GPU. */
 RISM_API rism_status rism_init_noalloc(const rism_grid_desc* grid, const rism_options* opts, int64_t n,
                                        const double* xyz, const double* q, const double* sigma, const double* eps,
                                        int32_t nsite, const double* qs, const double* sigs, const double* epss,

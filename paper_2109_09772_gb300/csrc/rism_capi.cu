@@ -13,6 +13,7 @@
 #include "rism_kernels.h"
 #include "rism_tree.h"
 #include "rism_adjoint.h"
+#include "rism_validate.h"
 
 using namespace rism;
 
@@ -71,35 +72,12 @@ rism_status cuda_fail(rism_ctx* c, cudaError_t e, const char* where) {
     return fail(c, RISM_E_CUDA, m);
 }
 
-bool finite_all(const double* a, int64_t n) {
-    for (int64_t i = 0; i < n; ++i)
-        if (!std::isfinite(a[i])) return false;
-    return true;
-}
-
 int padded_sites(int S) { return S <= 2 ? 2 : (S <= 4 ? 4 : 8); }
 
 rism_status check_options(rism_ctx* c, const rism_options& o) {
-    if (o.method != RISM_METHOD_DIRECT && o.method != RISM_METHOD_TREECODE) return fail(c, RISM_E_INVALID, "method");
-    if (o.precision != RISM_PREC_FP64 && o.precision != RISM_PREC_FP32) return fail(c, RISM_E_INVALID, "precision");
-    if (o.method == RISM_METHOD_TREECODE && o.precision == RISM_PREC_FP64)
-        return fail(c, RISM_E_UNSUPPORTED, "the treecode computes FP32 pair terms; FP64 needs the direct method");
-    if (o.degree < 1 || o.degree > kMaxDegree) return fail(c, RISM_E_INVALID, "degree out of range");
-    if (!(o.theta > 0.0 && o.theta < 1.0)) return fail(c, RISM_E_INVALID, "theta must lie in (0, 1)");
-    if (o.leaf < 1) return fail(c, RISM_E_INVALID, "leaf must be >= 1");
-    for (int k = 0; k < 3; ++k)
-        if (o.batch[k] < 0 || o.batch[k] > 64) return fail(c, RISM_E_INVALID, "batch dims must lie in [0, 64]");
-    if (o.lj_mode < RISM_LJ_NONE || o.lj_mode > RISM_LJ_TOL) return fail(c, RISM_E_INVALID, "lj_mode");
-    if (o.lj_mode == RISM_LJ_RCUT && !(o.lj_rcut > 0.0 && std::isfinite(o.lj_rcut)))
-        return fail(c, RISM_E_INVALID, "lj_rcut must be > 0");
-    if (o.lj_mode == RISM_LJ_TOL && !(o.lj_tol > 0.0 && std::isfinite(o.lj_tol)))
-        return fail(c, RISM_E_INVALID, "lj_tol must be > 0");
-    const double pos[] = {o.eta, o.T, o.eps_r, o.k_e, o.k_B};
-    for (double v : pos)
-        if (!(v > 0.0 && std::isfinite(v))) return fail(c, RISM_E_INVALID, "eta, T, eps_r, k_e, k_B must be > 0");
-    if (!std::isfinite(o.kappa)) return fail(c, RISM_E_INVALID, "kappa");
-    if (!(o.r_short >= 0.0 && std::isfinite(o.r_short))) return fail(c, RISM_E_INVALID, "r_short");
-    if (o.wait_limit < 1) return fail(c, RISM_E_INVALID, "wait_limit must be >= 1");
+    bool unsupported = false;
+    const char* m = rism::check_options(o, &unsupported);
+    if (m) return fail(c, unsupported ? RISM_E_UNSUPPORTED : RISM_E_INVALID, m);
     return RISM_OK;
 }
 
@@ -186,15 +164,6 @@ rism_status ensure_tables(rism_ctx* c) {
     return RISM_OK;
 }
 
-bool is_device_ptr(const void* p) {
-    cudaPointerAttributes a;
-    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
-        cudaGetLastError();
-        return false;
-    }
-    return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
-}
-
 rism_status check_device_error(rism_ctx* c) {
     cudaError_t e = cudaMemcpyAsync(c->h_err, c->d_err, sizeof(DevErr), cudaMemcpyDeviceToHost, c->st);
     if (e == cudaSuccess) e = cudaStreamSynchronize(c->st);
@@ -241,11 +210,7 @@ void rism_default_options(rism_options* o) {
 rism_status rism_grid_create(const rism_grid_desc* grid, const rism_options* opts, void* stream, rism_ctx** out) {
     if (!grid || !out) return RISM_E_INVALID;
     *out = nullptr;
-    if (grid->nx < 1 || grid->ny < 1 || grid->nz < 1) return RISM_E_INVALID;
-    if (!(grid->h > 0.0 && std::isfinite(grid->h))) return RISM_E_INVALID;
-    for (int k = 0; k < 3; ++k)
-        if (!std::isfinite(grid->origin[k])) return RISM_E_INVALID;
-    if ((int64_t)grid->nx * grid->ny * grid->nz > (1LL << 36)) return RISM_E_INVALID;
+    if (check_grid_desc(*grid)) return RISM_E_INVALID;
     rism_ctx* c = new (std::nothrow) rism_ctx;
     if (!c) return RISM_E_NOMEM;
     c->g = *grid;
@@ -279,15 +244,7 @@ rism_status rism_grid_create(const rism_grid_desc* grid, const rism_options* opt
 rism_status rism_set_solute(rism_ctx* c, int64_t n, const double* xyz, const double* q, const double* sigma,
                             const double* eps) {
     if (!c) return RISM_E_INVALID;
-    if (n < 0) return fail(c, RISM_E_INVALID, "n < 0");
-    if (n > 0 && (!xyz || !q || !sigma || !eps)) return fail(c, RISM_E_INVALID, "NULL solute array");
-    if (n > (1LL << 31)) return fail(c, RISM_E_INVALID, "too many atoms");
-    if (n > 0) {
-        if (!finite_all(xyz, 3 * n) || !finite_all(q, n) || !finite_all(sigma, n) || !finite_all(eps, n))
-            return fail(c, RISM_E_INVALID, "NaN or Inf in solute");
-        for (int64_t i = 0; i < n; ++i)
-            if (sigma[i] < 0.0 || eps[i] < 0.0) return fail(c, RISM_E_INVALID, "negative sigma or eps");
-    }
+    if (const char* m = check_host_solute(n, xyz, q, sigma, eps)) return fail(c, RISM_E_INVALID, m);
     c->raw.assign((size_t)(6 * n), 0.0);
     for (int64_t i = 0; i < n; ++i) {
         c->raw[6 * i + 0] = xyz[3 * i + 0];
@@ -307,15 +264,7 @@ rism_status rism_set_solute(rism_ctx* c, int64_t n, const double* xyz, const dou
 rism_status rism_set_solvent(rism_ctx* c, int32_t nsite, const double* q, const double* sigma, const double* eps,
                              const double* rho, const int32_t* is_ion) {
     if (!c) return RISM_E_INVALID;
-    if (nsite < 1 || nsite > kMaxSites) return fail(c, RISM_E_INVALID, "nsite must lie in [1, RISM_MAX_SITES]");
-    if (!q || !sigma || !eps) return fail(c, RISM_E_INVALID, "NULL solvent array");
-    if (!finite_all(q, nsite) || !finite_all(sigma, nsite) || !finite_all(eps, nsite) ||
-        (rho && !finite_all(rho, nsite)))
-        return fail(c, RISM_E_INVALID, "NaN or Inf in solvent");
-    for (int s = 0; s < nsite; ++s) {
-        if (sigma[s] < 0.0 || eps[s] < 0.0) return fail(c, RISM_E_INVALID, "negative sigma or eps");
-        if (rho && rho[s] < 0.0) return fail(c, RISM_E_INVALID, "negative density");
-    }
+    if (const char* m = check_solvent(nsite, q, sigma, eps, rho)) return fail(c, RISM_E_INVALID, m);
     c->S = nsite;
     for (int s = 0; s < kMaxSites; ++s) {
         c->qs[s] = s < nsite ? q[s] : 0.0;

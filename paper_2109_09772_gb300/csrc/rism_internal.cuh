@@ -13,12 +13,13 @@ namespace rism {
 constexpr int kMaxSites = RISM_MAX_SITES;
 
 // Device error word written by kernels (first error wins).
-enum : int { DEV_OK = 0, DEV_TIMEOUT = 1, DEV_OVERFLOW = 2 };
+enum : int { DEV_OK = 0, DEV_TIMEOUT = 1, DEV_OVERFLOW = 2, DEV_BAD_INPUT = 3 };
 struct DevErr {
     int code;
     int where;  // kernel id that reported it
 };
-enum : int { WHERE_DIRECT = 1, WHERE_TREE_EVAL = 2, WHERE_ADJOINT = 3, WHERE_BATCH = 4, WHERE_UPWARD = 5 };
+enum : int { WHERE_DIRECT = 1, WHERE_TREE_EVAL = 2, WHERE_ADJOINT = 3, WHERE_BATCH = 4, WHERE_UPWARD = 5,
+             WHERE_INPUT_CHECK = 6 };
 
 // ---------------------------------------------------------------- records
 // Atom geometry: position (physical A for the FP64 path; grid units relative

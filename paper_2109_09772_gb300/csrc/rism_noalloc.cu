@@ -1,20 +1,21 @@
 // rism_noalloc.cu -- rism_init_noalloc: the direct-sum initialization without
 // any device allocation.
 //
-// Some callers cannot call cudaMalloc: code that runs while a CUDA stream is
-// being captured into a graph (allocation is not a capturable operation),
-// plug-ins whose host application owns the device memory pool and forbids
-// other allocators, and embedded or real-time callers that must not allocate
-// after start-up.  For them this entry point keeps its scratch -- the
-// per-atom and per-(atom, site) tables that the context-based API allocates
-// with cudaMalloc -- in one file-scope __device__ array of fixed size.  Every
-// GPU that loads the library holds that array until the process exits.
+// Some callers cannot call cudaMalloc: plug-ins whose host application owns
+// the device memory pool and forbids other allocators, and embedded or
+// real-time callers that must not allocate after start-up (an allocation can
+// block, fail late or fragment a pool sized up front).  For them this entry
+// point keeps its scratch -- the per-atom and per-(atom, site) tables that the
+// context-based API allocates with cudaMalloc -- in one file-scope __device__
+// array of fixed size.  Every GPU that loads the library holds that array
+// until the process exits.
 #include <cmath>
 #include <cstdio>
 #include <cstring>
 #include <mutex>
 
 #include "rism_kernels.h"
+#include "rism_validate.h"
 
 namespace rism {
 namespace {
@@ -66,10 +67,17 @@ rism_status say(char* buf, size_t len, rism_status s, const char* msg) {
     return s;
 }
 
-bool finite_all(const double* a, int64_t n) {
-    for (int64_t i = 0; i < n; ++i)
-        if (!std::isfinite(a[i])) return false;
-    return true;
+// The solute gathered into scratch ([n][6]: x, y, z, q, sigma, eps) must be finite with sigma, eps >= 0, the
+// checks rism_set_solute makes on the host; used when the caller's arrays are device memory.  A bad row sets
+// the error word (the kernels that follow read no index from these values, so they run to completion).
+__global__ void k_check_solute(const double* raw, int64_t n, DevErr* err) {
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const double* r = raw + 6 * i;
+    bool ok = true;
+    for (int k = 0; k < 6; ++k) ok = ok && isfinite(r[k]);
+    ok = ok && r[4] >= 0.0 && r[5] >= 0.0;
+    if (!ok) report_error(err, DEV_BAD_INPUT, WHERE_INPUT_CHECK);
 }
 
 }  // namespace
@@ -83,27 +91,38 @@ extern "C" RISM_API rism_status rism_init_noalloc(const rism_grid_desc* grid, co
                                                   const double* sigs, const double* epss, const double* rho,
                                                   const int32_t* is_ion, double* u, double* c_lr, double* h_lr,
                                                   void* stream, char* errbuf, size_t errlen) {
+    // ---- everything below is checked before the GPU is touched
     if (!grid || !opts) return say(errbuf, errlen, RISM_E_INVALID, "grid and opts are required");
     if (n < 0 || n > kNoAllocMaxAtoms)
         return say(errbuf, errlen, RISM_E_INVALID,
                    "rism_init_noalloc: atom count outside [0, RISM_NOALLOC_MAX_ATOMS]; use the context API");
     if (n > 0 && (!xyz || !q || !sigma || !eps)) return say(errbuf, errlen, RISM_E_INVALID, "NULL solute array");
-    if (nsite < 1 || nsite > kMaxSites || !qs || !sigs || !epss)
-        return say(errbuf, errlen, RISM_E_INVALID, "nsite must lie in [1, RISM_MAX_SITES] with q, sigma, eps");
-    if (grid->nx < 1 || grid->ny < 1 || grid->nz < 1 || !(grid->h > 0.0) || !std::isfinite(grid->h))
-        return say(errbuf, errlen, RISM_E_INVALID, "bad grid descriptor");
+    if (const char* m = check_grid_desc(*grid)) return say(errbuf, errlen, RISM_E_INVALID, m);
     const rism_options& o = *opts;
     if (o.method != RISM_METHOD_DIRECT) return say(errbuf, errlen, RISM_E_UNSUPPORTED, "direct method only");
-    if (o.precision != RISM_PREC_FP32 && o.precision != RISM_PREC_FP64)
-        return say(errbuf, errlen, RISM_E_INVALID, "precision");
-    if (!(o.eta > 0 && o.T > 0 && o.eps_r > 0 && o.k_e > 0 && o.k_B > 0) || o.wait_limit < 1)
-        return say(errbuf, errlen, RISM_E_INVALID, "eta, T, eps_r, k_e, k_B must be > 0");
-    if (o.lj_mode < RISM_LJ_NONE || o.lj_mode > RISM_LJ_TOL ||
-        (o.lj_mode == RISM_LJ_RCUT && !(o.lj_rcut > 0)) || (o.lj_mode == RISM_LJ_TOL && !(o.lj_tol > 0)))
-        return say(errbuf, errlen, RISM_E_INVALID, "LJ cut-off options");
-    if (!finite_all(qs, nsite) || !finite_all(sigs, nsite) || !finite_all(epss, nsite) ||
-        (rho && !finite_all(rho, nsite)))
-        return say(errbuf, errlen, RISM_E_INVALID, "NaN or Inf in solvent");
+    bool unsupported = false;
+    if (const char* m = check_options(o, &unsupported))
+        return say(errbuf, errlen, unsupported ? RISM_E_UNSUPPORTED : RISM_E_INVALID, m);
+    if (const char* m = check_solvent(nsite, qs, sigs, epss, rho)) return say(errbuf, errlen, RISM_E_INVALID, m);
+    // outputs are written by the kernels: they must be device (or managed) memory
+    const double* outs[3] = {u, c_lr, h_lr};
+    for (const double* p : outs)
+        if (p && !is_device_ptr(p))
+            return say(errbuf, errlen, RISM_E_INVALID, "rism_init_noalloc: outputs must be device memory");
+    // solute arrays in host memory get the host checks of rism_set_solute; device arrays are checked on the GPU
+    const double* sol[4] = {xyz, q, sigma, eps};
+    const int64_t len[4] = {3 * n, n, n, n};
+    bool device_solute = false;
+    for (int k = 0; k < 4 && n > 0; ++k) {
+        if (is_device_ptr(sol[k])) {
+            device_solute = true;
+            continue;
+        }
+        if (!finite_all(sol[k], len[k])) return say(errbuf, errlen, RISM_E_INVALID, "NaN or Inf in solute");
+        if (k >= 2)
+            for (int64_t i = 0; i < n; ++i)
+                if (sol[k][i] < 0.0) return say(errbuf, errlen, RISM_E_INVALID, "negative sigma or eps");
+    }
 
     // physical constants (beta, Debye kappa of eq. (tcf-r), d -> 0 limits)
     Phys ph{};
@@ -130,6 +149,7 @@ extern "C" RISM_API rism_status rism_init_noalloc(const rism_grid_desc* grid, co
     const GridD g{grid->nx, grid->ny, grid->nz, grid->h, grid->origin[0], grid->origin[1], grid->origin[2]};
     const int smax = nsite <= 2 ? 2 : (nsite <= 4 ? 4 : 8);
 
+    // ---- the GPU part
     void* base = nullptr;
     cudaError_t e = scratch_address(&base);
     if (e != cudaSuccess) return say(errbuf, errlen, RISM_E_CUDA, cudaGetErrorString(e));
@@ -161,6 +181,10 @@ extern "C" RISM_API rism_status rism_init_noalloc(const rism_grid_desc* grid, co
             (e = cudaMemcpy2DAsync(raw + 5, row, eps, sizeof(double), sizeof(double), n, cudaMemcpyDefault, st)) !=
                 cudaSuccess)
             return say(errbuf, errlen, RISM_E_CUDA, cudaGetErrorString(e));
+        if (device_solute) {
+            k_check_solute<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(raw, n, t.err);
+            if ((e = cudaGetLastError()) != cudaSuccess) return say(errbuf, errlen, RISM_E_CUDA, cudaGetErrorString(e));
+        }
         if ((e = launch_setup(raw, n, nsite, smax, sigs, epss, o.lj_mode, o.lj_rcut, o.lj_tol, g, t, st)) !=
             cudaSuccess)
             return say(errbuf, errlen, RISM_E_CUDA, cudaGetErrorString(e));
@@ -174,6 +198,8 @@ extern "C" RISM_API rism_status rism_init_noalloc(const rism_grid_desc* grid, co
     if ((e = cudaMemcpyAsync(&he, t.err, sizeof(DevErr), cudaMemcpyDeviceToHost, st)) != cudaSuccess ||
         (e = cudaStreamSynchronize(st)) != cudaSuccess)
         return say(errbuf, errlen, RISM_E_CUDA, cudaGetErrorString(e));
+    if (he.code == DEV_BAD_INPUT)
+        return say(errbuf, errlen, RISM_E_INVALID, "NaN, Inf or negative sigma/eps in the device solute arrays");
     if (he.code == DEV_TIMEOUT) return say(errbuf, errlen, RISM_E_TIMEOUT, "a bounded device wait ran out");
     if (he.code != DEV_OK) return say(errbuf, errlen, RISM_E_CUDA, "device error");
     return say(errbuf, errlen, RISM_OK, "");

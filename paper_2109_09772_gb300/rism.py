@@ -248,8 +248,9 @@ class Rism:
 
 def init_noalloc(grid_n, h, origin, xyz, q, sigma, eps, solvent, u=None, c=None, hh=None, stream=None, **opts):
     """rism_init_noalloc: direct-sum u / c / h into caller-provided device tensors, no device allocation by
-    the library.  xyz, q, sigma, eps: device (or host) float64 tensors; solvent: (q, sigma, eps, rho, is_ion)
-    host arrays.  Raises RismError with the library's message on failure."""
+    the library (for callers that cannot allocate device memory themselves).  xyz, q, sigma, eps: device (or
+    host) float64 tensors; solvent: (q, sigma, eps, rho, is_ion) host arrays; u, c, hh: device tensors.
+    Raises RismError with the library's message on failure."""
     import torch
 
     lib = load()

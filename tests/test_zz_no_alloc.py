@@ -1,5 +1,5 @@
 """rism_init_noalloc: the allocation-free direct-sum entry point, for callers that cannot call cudaMalloc
-(stream capture, host-owned memory pools, no allocation after start-up).
+(plug-ins whose host application owns the device memory, callers that must not allocate after start-up).
 
 Its output must match the context API (rism_init, direct method) within the tolerance the parity tests use
 (rel L2 1e-6 for FP32 pairs, 1e-12 for FP64 pairs) on two calls in a row: the shared scratch array keeps the
@@ -75,3 +75,39 @@ def test_noalloc_rejects_too_many_atoms(R):
         R.init_noalloc(w.grid.n, w.grid.h, w.grid.origin, xyz, z, z, z, solvent, u=u, method=R.METHOD_DIRECT)
     assert e.value.status == R.E_INVALID
     assert "RISM_NOALLOC_MAX_ATOMS" in str(e.value)
+
+
+def test_noalloc_refuses_host_outputs_and_bad_device_inputs(R):
+    """A host output pointer is refused before any launch; NaN / negative sigma in device-resident solute
+    arrays are found by the library's device-side check and refused; the next good call still works."""
+    import torch
+
+    w = I.small_workload(n_atoms=40, n=(16, 12, 10), h=0.5, seed=3, ions=True, lj_rcut=4.0)
+    S = w.solvent.nsite
+    nx, ny, nz = w.grid.n
+    solvent = (w.solvent.q, w.solvent.sigma, w.solvent.eps, w.solvent.rho, w.solvent.is_ion)
+    args = lambda xyz, sg: (w.grid.n, w.grid.h, w.grid.origin, _dev(xyz), _dev(w.solute.q), _dev(sg),
+                            _dev(w.solute.eps), solvent)
+    host_u = torch.zeros((S, nz, ny, nx), dtype=torch.float64)
+    with pytest.raises(R.RismError) as e:
+        R.init_noalloc(*args(w.solute.xyz, w.solute.sigma), u=host_u, method=R.METHOD_DIRECT)
+    assert e.value.status == R.E_INVALID and "device memory" in str(e.value)
+    u = torch.zeros((S, nz, ny, nx), dtype=torch.float64, device="cuda")
+    bad_xyz = w.solute.xyz.copy()
+    bad_xyz[7, 1] = float("nan")
+    with pytest.raises(R.RismError) as e:
+        R.init_noalloc(*args(bad_xyz, w.solute.sigma), u=u, method=R.METHOD_DIRECT)
+    assert e.value.status == R.E_INVALID
+    bad_sig = w.solute.sigma.copy()
+    bad_sig[3] = -1.0
+    with pytest.raises(R.RismError) as e:
+        R.init_noalloc(*args(w.solute.xyz, bad_sig), u=u, method=R.METHOD_DIRECT)
+    assert e.value.status == R.E_INVALID
+    # the error word left in the shared scratch by the refused calls does not leak into the next call
+    R.init_noalloc(*args(w.solute.xyz, w.solute.sigma), u=u, method=R.METHOD_DIRECT, lj_mode=R.LJ_RCUT,
+                   lj_rcut=4.0)
+    torch.cuda.synchronize()
+    r = R.from_workload(w, method=R.METHOD_DIRECT, precision=R.PREC_FP32)
+    ref = r.init(u=True, c=False, h=False)["u"].cpu().numpy()
+    r.close()
+    assert rel_l2(u.cpu().numpy(), ref) <= 1e-6
