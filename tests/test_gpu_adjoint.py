@@ -203,3 +203,74 @@ def test_treecode_reverse_ragged_and_repeatable(R):
     atoms = np.arange(w.solute.n)
     ref = O.grad(O.Problem.from_workload(w), atoms, G["u"], G["c"], G["h"])
     _check(a, ref, atoms, label="tree reverse ragged")
+
+
+def _fd_safe_atoms(w, count, delta, rc, seed):
+    """Seeded atoms none of whose +-delta probes along x, y, z moves a grid point across the LJ cut-off (such a
+    crossing makes L jump by G u_LJ(r_c), which the derivative does not contain)."""
+    from tests.helpers import lj_boundary_pairs
+
+    rel = 4.0 * delta / rc
+    _, ats = lj_boundary_pairs(w.grid, w.solute.xyz, rc, rel=rel)
+    bad = set(ats.tolist())
+    order = np.random.default_rng(seed).permutation(w.solute.n)
+    return np.sort(np.array([a for a in order if a not in bad][:count]))
+
+
+def test_stack55000_backward_64_atoms_vs_oracle_and_central_differences(R):
+    """The differentiation workload: 55,000 atoms (four stacked ellipsoids) on 320x320x384, forward u + c with
+    FP32 pairs (treecode), backward with a smooth seeded cotangent (correlation length 3 A, amplitude 0.5) used
+    for both u and c.  64 seeded atoms: the gradient against the FP64 oracle's analytic gradient, and against
+    central differences (delta 1e-5 A, 1e-6 relative for q, sigma, eps) of L restricted to the atom's own terms
+    (L is a sum over atoms), each term evaluated by the FP64 direct sum on a one-atom solute."""
+    import torch
+
+    w = I.workload(4)
+    nx, ny, nz = w.grid.n
+    S = w.solvent.nsite
+    G = np.stack([I.gaussian_random_field((nz, ny, nx), w.grid.h, 700 + s, corr_len=3.0, amplitude=0.5)
+                  for s in range(S)])
+    Gd = torch.as_tensor(G, device="cuda")
+    r = R.from_workload(w, method=R.METHOD_TREECODE, precision=R.PREC_FP32)
+    r.init(u=True, c=True, h=False)
+    g = {k: v.cpu().numpy() for k, v in r.backward(Gd, Gd, None).items()}
+    r.close()
+    rc = float(w.opts["lj_rcut"])
+    delta = 1e-5
+    atoms = _fd_safe_atoms(w, 64, delta, rc, seed=64)
+    assert atoms.size == 64
+    # the FP64 oracle's analytic gradient of the same L
+    ref = O.grad(O.Problem.from_workload(w), atoms, G, G, None)
+    _check(g, ref, atoms, label="55k vs oracle")
+
+    # central differences of L_i = sum_s sum_r G_s (u_i,s + c_i,s), atom i alone, FP64 direct sums
+    one = R.Rism(w.grid.n, w.grid.h, w.grid.origin, method=R.METHOD_DIRECT, precision=R.PREC_FP64,
+                 lj_mode=R.LJ_RCUT, lj_rcut=rc)
+    one.set_solvent(w.solvent.q, w.solvent.sigma, w.solvent.eps, w.solvent.rho, w.solvent.is_ion)
+    out = {"u": one.empty_grid(), "c": one.empty_grid()}
+
+    def loss(x, q, s, e):
+        one.set_solute(x.reshape(1, 3), [q], [s], [e])
+        one.init(u=True, c=True, h=False, out=out)
+        return float((Gd * out["u"]).sum() + (Gd * out["c"]).sum())
+
+    fd = np.zeros((atoms.size, 6))
+    for n, a in enumerate(atoms):
+        base = [w.solute.xyz[a].copy(), float(w.solute.q[a]), float(w.solute.sigma[a]), float(w.solute.eps[a])]
+        for comp in range(6):
+            step = delta if comp < 3 else 1e-6 * max(abs(base[comp - 2]), 1e-3)
+            vals = []
+            for sgn in (1.0, -1.0):
+                x, q, s, e = base[0].copy(), base[1], base[2], base[3]
+                if comp < 3:
+                    x[comp] += sgn * step
+                elif comp == 3:
+                    q += sgn * step
+                elif comp == 4:
+                    s += sgn * step
+                else:
+                    e += sgn * step
+                vals.append(loss(x, q, s, e))
+            fd[n, comp] = (vals[0] - vals[1]) / (2.0 * step)
+    one.close()
+    _check(g, fd, atoms, label="55k vs central differences")

@@ -103,3 +103,25 @@ def test_autotune_picks_a_shape_and_caches_it(R, tmp_path):
     assert os.path.exists(path) and os.path.getsize(path) > 0
     line = open(path).read().strip().splitlines()[0]
     assert "S4" in line and line.split()[-2] == str(info["kernel_variant"])
+
+
+def test_batched_32_solutes_500_to_8000_atoms_against_oracle(R):
+    """The 32-solute batch of the benchmark plan (500..8,000 atoms, log-uniform, own grids) in one persistent
+    graph-captured launch; solutes above 4,096 atoms take the radix-sort tree build inside the batched graph.
+    Every solute against the FP64 oracle at sampled points and at the point nearest each atom."""
+    import torch
+
+    ws = I.batch_workloads(count=32, seed=0)
+    assert sum(w.solute.n > 4096 for w in ws) >= 2
+    rs = [R.from_workload(w, method=R.METHOD_TREECODE, precision=R.PREC_FP32) for w in ws]
+    outs = R.potential_batched(rs)
+    outs = R.potential_batched(rs, out=outs)  # the replayed graph
+    torch.cuda.synchronize()
+    for w, o in zip(ws, outs):
+        idx = np.union1d(I.sample_indices(w.grid.npts, 600, seed=w.solute.n), nearest_points(w.grid, w.solute.xyz))
+        ref = O.fields(O.Problem.from_workload(w), idx=idx)
+        t = torch.as_tensor(idx, device="cuda")
+        g = {k: o[k].reshape(w.solvent.nsite, -1)[:, t].cpu().numpy() for k in ("u", "c", "h")}
+        check_fields(g, ref, ("u", "c", "h"), 1e-5, w.grid, w.solute.xyz, idx=idx, label=w.name)
+    for r in rs:
+        r.close()
