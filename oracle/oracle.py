@@ -60,6 +60,12 @@ def _load():
             lib.orc_grad.restype = C.c_int
             lib.orc_grad.argtypes = [I64, P, P, P, P, I32, P, P, P, P, D, D, D, D, D,
                                      I32, I32, I32, D, P, P, P, P, I64, P, P, I32]
+            lib.orc_lra_pair.restype = None
+            lib.orc_lra_pair.argtypes = [D, D, I64, P, P, P]
+            lib.orc_lra_atom_sums.restype = C.c_int
+            lib.orc_lra_atom_sums.argtypes = [I64, P, P, D, D, I64, P, P, P, I32]
+            lib.orc_lra_integral.restype = C.c_int
+            lib.orc_lra_integral.argtypes = [I64, P, P, I32, P, D, D, D, D, D, P, P, I32]
             _lib = lib
     return _lib
 
@@ -210,3 +216,36 @@ def grad(p: Problem, atoms, gu=None, gc=None, gh=None, nthreads: int = 0):
     if rc_ != 0:
         raise MemoryError("oracle allocation failed")
     return out[:, :6]
+
+
+def lra_pair(eta, kappa_, R):
+    """I_hc(R), I_hh(R): the all-space overlap integrals of the TCF kernel with the DCF kernel and with itself,
+    for two unit charges R apart (1D quadrature over the wave number)."""
+    lib = _load()
+    R = _f64(np.atleast_1d(R))
+    a, b = np.empty_like(R), np.empty_like(R)
+    lib.orc_lra_pair(float(eta), float(kappa_), R.size, _p(R), _p(a), _p(b))
+    return a, b
+
+
+def lra_atom_sums(p: Problem, atoms, nthreads: int = 0):
+    """[len(atoms), 2]: P_hc[a] = sum_b Q_b I_hc(R_ab), P_hh[a] = sum_b Q_b I_hh(R_ab) (b over every atom)."""
+    lib = _load()
+    atoms = np.ascontiguousarray(atoms, dtype=np.int64)
+    phc, phh = np.empty(atoms.size), np.empty(atoms.size)
+    lib.orc_lra_atom_sums(p.natoms, _p(_f64(p.xyz)), _p(_f64(p.q)), p.eta, kappa(p), atoms.size, _p(atoms),
+                          _p(phc), _p(phh), int(nthreads))
+    return np.stack([phc, phh], 1)
+
+
+def lra_integral(p: Problem, nthreads: int = 0):
+    """(T [S], (S_hh, S_hc)): the all-space integral of eq. (excess-chemical-potential-LRA) per site (A^3) and
+    the two atom-pair sums it is assembled from."""
+    lib = _load()
+    T = np.empty(p.nsite)
+    S2 = np.empty(2)
+    rc = lib.orc_lra_integral(p.natoms, _p(_f64(p.xyz)), _p(_f64(p.q)), p.nsite, _p(_f64(p.qs)), beta(p), p.k_e,
+                              p.eps_r, p.eta, kappa(p), _p(T), _p(S2), int(nthreads))
+    if rc != 0:
+        raise MemoryError("oracle allocation failed")
+    return T, (float(S2[0]), float(S2[1]))

@@ -17,7 +17,9 @@
  *   - I_s: the analytic LJ truncation correction integral, Sec. 2.6;
  *   - dL/dR_i, dL/dq_i, dL/dsigma_i, dL/deps_i of L = sum_s sum_r
  *     [G_u u + G_c c + G_h h] (the paper has no gradient; these are the
- *     plain derivatives of the three definitions above).
+ *     plain derivatives of the three definitions above);
+ *   - T_s: the all-space integral of eq. (excess-chemical-potential-LRA)
+ *     (Sec. 2.2), as a double sum over atom pairs of 1D integrals.
  *
  * Readings of the paper taken here (the paper is silent or ambiguous):
  *   - Gaussian-unit formulas are multiplied by the Coulomb constant k_e
@@ -428,5 +430,139 @@ int orc_grad(int64_t n, const double* xyz, const double* q, const double* sigma,
         out[a * 8 + 7] = 0.0;
     }
     free(part);
+    return 0;
+}
+
+/* ------------------------------------------- all-space LRA integral */
+
+/*
+ * The last integral of eq. (excess-chemical-potential-LRA) (Sec. 2.2), per solvent site gamma:
+ *   T_gamma = int over all space of [ 1/2 (h_gamma^lr)^2 Theta(Q^U q_gamma) - 1/2 h_gamma^lr c_gamma^lr ] dr,
+ * with h^lr of eq. (tcf-r), c^lr of eq. (dcf-r) and Q^U the total solute charge.  The paper computes it "via
+ * 1D integrals" and notes its O(N_atom^2) cost (Sec. 4.7).  Both asymptotic functions are sums over atoms of
+ * one radial kernel each (phi_h, phi_c above), so the integral is a double sum over atom pairs of
+ *   I_hh(R) = int phi_h(|r|) phi_h(|r - R|) dr,    I_hc(R) = int phi_h(|r|) phi_c(|r - R|) dr,
+ * R = |R_a - R_b|, and each of these is one 1D integral over the wave number k of the product of the kernels'
+ * 3D Fourier transforms (eq. (tcf-k) and eq. (dcf-k) without their prefactors: 8 pi e^{-k^2 eta^2/4}/(k^2 +
+ * kappa^2) for phi_h with its e^{kappa^2 eta^2/4} prefactor, 4 pi e^{-k^2 eta^2/4}/k^2 for phi_c):
+ *   I(R) = 1/(2 pi^2) int_0^inf k^2 F(k) G(k) sin(kR)/(kR) dk
+ *   I_hc(R) = 16 int_0^inf e^{-k^2 eta^2/2} j0(kR) / (k^2 + kappa^2) dk
+ *   I_hh(R) = 32 int_0^inf k^2 e^{-k^2 eta^2/2} j0(kR) / (k^2 + kappa^2)^2 dk.
+ * The 1D integrals are taken by composite 10-point Gauss-Legendre quadrature up to the wave number where the
+ * Gaussian factor falls below 1e-20, on panels no wider than pi/R (half a period of sin(kR)), 0.5/eta, and
+ * max(kappa, k)/8 (the Lorentzian factors peak at k = 0 with width kappa).
+ */
+
+static const double GL10_X[5] = {0.1488743389816312108848260, 0.4333953941292471907992659,
+                                 0.6794095682990244062343274, 0.8650633666889845107320967,
+                                 0.9739065285171717200779640};
+static const double GL10_W[5] = {0.2955242247147528701738930, 0.2692667193099963550912269,
+                                 0.2190863625159820439955349, 0.1494513491505805931457763,
+                                 0.0666713443086881375935688};
+
+static double j0s(double x)
+{
+    if (fabs(x) < 1e-4) { double x2 = x * x; return 1.0 - x2 / 6.0 + x2 * x2 / 120.0; }
+    return sin(x) / x;
+}
+
+/* I_hc(R), I_hh(R) for m distances (kappa > 0). */
+void orc_lra_pair(double eta, double kappa, int64_t m, const double* R, double* Ihc, double* Ihh)
+{
+    double kmax = sqrt(2.0 * 46.06) / eta; /* e^{-k^2 eta^2 / 2} = 1e-20 */
+    double k2 = kappa * kappa;
+    for (int64_t i = 0; i < m; ++i) {
+        double r = R[i];
+        double wmax = 0.5 / eta;
+        if (r > 0.0 && ORC_PI / r < wmax) wmax = ORC_PI / r;
+        nsum_t shc, shh;
+        ns_init(&shc);
+        ns_init(&shh);
+        double k0 = 0.0;
+        while (k0 < kmax) {
+            double width = (k0 > kappa ? k0 : kappa) / 8.0;
+            if (width > wmax) width = wmax;
+            if (k0 + width > kmax) width = kmax - k0;
+            double mid = k0 + 0.5 * width, half = 0.5 * width;
+            k0 += width;
+            for (int g = 0; g < 10; ++g) {
+                double k = mid + (g < 5 ? -1.0 : 1.0) * half * GL10_X[g % 5];
+                double w = half * GL10_W[g % 5];
+                double gau = exp(-0.5 * k * k * eta * eta);
+                double den = k * k + k2;
+                double j = j0s(k * r);
+                ns_add(&shc, w * gau * j / den);
+                ns_add(&shh, w * k * k * gau * j / (den * den));
+            }
+        }
+        if (Ihc) Ihc[i] = 16.0 * ns_get(&shc);
+        if (Ihh) Ihh[i] = 32.0 * ns_get(&shh);
+    }
+}
+
+/* Per listed atom a: P_hc[a] = sum_b Q_b I_hc(|R_a - R_b|), P_hh[a] = sum_b Q_b I_hh(...), b over all atoms
+ * (b = a included, R = 0). */
+int orc_lra_atom_sums(int64_t n, const double* xyz, const double* q, double eta, double kappa, int64_t nlist,
+                      const int64_t* atoms, double* Phc, double* Phh, int32_t nthreads)
+{
+#ifdef _OPENMP
+    if (nthreads > 0) omp_set_num_threads(nthreads);
+#pragma omp parallel for schedule(dynamic, 1)
+#endif
+    for (int64_t t = 0; t < nlist; ++t) {
+        int64_t a = atoms[t];
+        nsum_t shc, shh;
+        ns_init(&shc);
+        ns_init(&shh);
+        for (int64_t b = 0; b < n; ++b) {
+            double dx = xyz[3 * a + 0] - xyz[3 * b + 0], dy = xyz[3 * a + 1] - xyz[3 * b + 1];
+            double dz = xyz[3 * a + 2] - xyz[3 * b + 2];
+            double r = sqrt(dx * dx + dy * dy + dz * dz), ihc, ihh;
+            orc_lra_pair(eta, kappa, 1, &r, &ihc, &ihh);
+            ns_add(&shc, q[b] * ihc);
+            ns_add(&shh, q[b] * ihh);
+        }
+        Phc[t] = ns_get(&shc);
+        Phh[t] = ns_get(&shh);
+    }
+    return 0;
+}
+
+/* T_gamma of every site from the pair sums S_hh = sum_a Q_a P_hh[a], S_hc = sum_a Q_a P_hc[a]:
+ * h^lr_gamma = A_gamma sum_a Q_a phi_h, A_gamma = -beta k_e q_gamma / (2 eps_r); c^lr_gamma = B_gamma sum_a Q_a
+ * phi_c, B_gamma = -beta k_e q_gamma; Theta(x) = 1 for x > 0, else 0.  Returns S_hh, S_hc in S2[0..1]. */
+int orc_lra_integral(int64_t n, const double* xyz, const double* q, int32_t S, const double* qs, double beta,
+                     double k_e, double eps_r, double eta, double kappa, double* T, double* S2, int32_t nthreads)
+{
+    if (!(kappa > 0.0)) {
+        for (int32_t s = 0; s < S; ++s) T[s] = 0.0;
+        if (S2) { S2[0] = 0.0; S2[1] = 0.0; }
+        return 0;
+    }
+    int64_t* all = (int64_t*)malloc(sizeof(int64_t) * (size_t)(n > 0 ? n : 1));
+    double* phc = (double*)malloc(sizeof(double) * (size_t)(n > 0 ? n : 1));
+    double* phh = (double*)malloc(sizeof(double) * (size_t)(n > 0 ? n : 1));
+    if (!all || !phc || !phh) { free(all); free(phc); free(phh); return 1; }
+    for (int64_t i = 0; i < n; ++i) all[i] = i;
+    orc_lra_atom_sums(n, xyz, q, eta, kappa, n, all, phc, phh, nthreads);
+    nsum_t shh, shc, qt;
+    ns_init(&shh);
+    ns_init(&shc);
+    ns_init(&qt);
+    for (int64_t a = 0; a < n; ++a) {
+        ns_add(&shh, q[a] * phh[a]);
+        ns_add(&shc, q[a] * phc[a]);
+        ns_add(&qt, q[a]);
+    }
+    double Shh = ns_get(&shh), Shc = ns_get(&shc), Qu = ns_get(&qt);
+    for (int32_t s = 0; s < S; ++s) {
+        double A = -beta * k_e * qs[s] / (2.0 * eps_r), B = -beta * k_e * qs[s];
+        double theta = (Qu * qs[s] > 0.0) ? 1.0 : 0.0;
+        T[s] = 0.5 * theta * A * A * Shh - 0.5 * A * B * Shc;
+    }
+    if (S2) { S2[0] = Shh; S2[1] = Shc; }
+    free(all);
+    free(phc);
+    free(phh);
     return 0;
 }

@@ -91,7 +91,8 @@ def test_autotune_picks_a_shape_and_caches_it(R, tmp_path):
     path = str(tmp_path / "tune.txt")
     os.environ["RISM_AUTOTUNE_CACHE"] = path
     w = I.workload(1)
-    r = R.from_workload(w, method=R.METHOD_TREECODE, precision=R.PREC_FP32, autotune=1)
+    # a problem class no other test tunes (the in-memory cache would otherwise answer without timing)
+    r = R.from_workload(w, method=R.METHOD_TREECODE, precision=R.PREC_FP32, autotune=1, degree=7, theta=0.65)
     out = r.init()
     info = r.info()
     assert info["kernel_variant"] in (0, 1, 2)

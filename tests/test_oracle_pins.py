@@ -355,3 +355,114 @@ def test_gradient_against_finite_differences():
                 vals.append(_loss(pp, G))
             fd = (vals[0] - vals[1]) / (2 * step)
             assert want == pytest.approx(fd, rel=1e-5, abs=1e-9 * max(abs(v) for v in vals)), (i, field, comp)
+
+
+# ------------------------------------------------- all-space LRA integral
+def _lra_closed_forms(R, eta, kappa):
+    """I_hc(R), I_hh(R) in closed form at 30 digits.  With sigma^2 = eta^2/2, b = kappa sigma, s = R/(2 sigma),
+    P = e^{-kappa R} erfc(b - s), M = e^{kappa R} erfc(b + s) (the Gaussian-screened Yukawa transform evaluated
+    with sigma), partial fractions of 1/(k^2 (k^2 + kappa^2)) and d/d(kappa^2) of the Yukawa transform give
+    I_hc = (4 pi/kappa^2) [2 erf(s)/R - e^{b^2}(P - M)/R],
+    I_hh = (4 pi e^{b^2}/(kappa R)) [R (P + M) - 2 kappa sigma^2 (P - M)],
+    and at R = 0: I_hc = 8 pi erfcx(b)/kappa, I_hh = 32 [J + kappa J'/2], J(kappa) = (pi/(2 kappa)) erfcx(b)."""
+    mp.mp.dps = 30
+    k = mp.mpf(kappa)
+    s2 = mp.mpf(eta) ** 2 / 2
+    sig = mp.sqrt(s2)
+    R = mp.mpf(R)
+    E = mp.e ** ((k * sig) ** 2)
+    if R == 0:
+        J = lambda kk: mp.pi / (2 * kk) * mp.e ** ((kk * sig) ** 2) * mp.erfc(kk * sig)
+        return float(8 * mp.pi * E * mp.erfc(k * sig) / k), float(32 * (J(k) + k * mp.diff(J, k) / 2))
+    s = R / (2 * sig)
+    P = mp.e ** (-k * R) * mp.erfc(k * sig - s)
+    M = mp.e ** (k * R) * mp.erfc(k * sig + s)
+    ihc = 4 * mp.pi / k ** 2 * (2 * mp.erf(s) / R - E * (P - M) / R)
+    ihh = 4 * mp.pi * E / (k * R) * (R * (P + M) - 2 * k * s2 * (P - M))
+    return float(ihc), float(ihh)
+
+
+@pytest.mark.parametrize("eta,kappa", [(1.0, KAPPA), (0.7, 0.35)])
+def test_lra_pair_integrals_against_closed_forms(eta, kappa):
+    """The oracle's 1D quadratures of the overlap integrals against their closed forms."""
+    R = np.array([0.0, 0.3, 1.2, 3.0, 10.0, 40.0, 100.0])
+    ihc, ihh = O.lra_pair(eta, kappa, R)
+    for i, r in enumerate(R):
+        chc, chh = _lra_closed_forms(r, eta, kappa)
+        assert ihc[i] == pytest.approx(chc, rel=1e-11), r
+        assert ihh[i] == pytest.approx(chh, rel=1e-9, abs=1e-12 * abs(ihh[0])), r
+
+
+def test_lra_pair_integrals_in_real_space():
+    """The same overlaps from the real-space kernels of eqs. (tcf-r) and (dcf-r) (independent of the Fourier
+    constants 8 pi, 4 pi and 1/(2 pi^2)): at R = 0 the radial integrals 4 pi int r^2 phi_h phi_c dr and
+    4 pi int r^2 phi_h^2 dr; at R > 0 the radial convolution (2 pi/R) int r f(r) [G(R + r) - G(|R - r|)] dr
+    with G(s) = int_0^s t g(t) dt (closed form for g = phi_c, nested quadrature for g = phi_h)."""
+    from scipy.special import erf
+
+    ph = lambda r: float(O.kernels(ETA, KAPPA, [r])[1][0])
+    pc = lambda r: float(O.kernels(ETA, KAPPA, [r])[0][0])
+    rmax = 420.0
+    i0hc, _ = integrate.quad(lambda r: 4 * math.pi * r * r * ph(r) * pc(r), 0, rmax, limit=2000, epsrel=1e-12)
+    i0hh, _ = integrate.quad(lambda r: 4 * math.pi * r * r * ph(r) ** 2, 0, rmax, limit=2000, epsrel=1e-12)
+    ihc, ihh = O.lra_pair(ETA, KAPPA, [0.0, 4.0])
+    assert ihc[0] == pytest.approx(i0hc, rel=1e-8)
+    assert ihh[0] == pytest.approx(i0hh, rel=1e-8)
+    R = 4.0
+    Gc = lambda s: s * erf(s / ETA) + ETA / math.sqrt(math.pi) * (math.exp(-(s / ETA) ** 2) - 1.0)
+    val, _ = integrate.quad(lambda r: r * ph(r) * (Gc(R + r) - Gc(abs(R - r))), 0, rmax, limit=2000,
+                            epsrel=1e-11, points=[R])
+    assert ihc[1] == pytest.approx(2 * math.pi / R * val, rel=1e-8)
+    Gh = lambda s: integrate.quad(lambda t: t * ph(t), 0, s, epsrel=1e-12, limit=400)[0]
+    val, _ = integrate.quad(lambda r: r * ph(r) * (Gh(R + r) - Gh(abs(R - r))), 0, 300.0, limit=400,
+                            epsrel=1e-9, points=[R])
+    assert ihh[1] == pytest.approx(2 * math.pi / R * val, rel=1e-7)
+
+
+def _two_charge_problem(kappa, q=(0.7, -0.3), sep=(2.0, 1.0, -1.5), qs=(0.8, -0.5)):
+    return O.Problem(xyz=np.array([[0.0, 0.0, 0.0], list(sep)]), q=np.array(q), sigma=np.array([2.0, 2.0]),
+                     eps=np.array([0.1, 0.1]), qs=np.array(qs), sigs=np.array([3.0, 1.0]),
+                     epss=np.array([0.1, 0.01]), rho=np.array([0.03, 0.06]), is_ion=np.array([0, 0], dtype=np.int32),
+                     n=(4, 4, 4), h=0.5, origin=(0.0, 0.0, 0.0), kappa=kappa)
+
+
+def test_lra_integral_against_grid_integration():
+    """T_s, the all-space integral of [1/2 (h^lr)^2 Theta(Q q_s) - 1/2 h^lr c^lr], against a direct 3D grid
+    sum of that integrand built from the oracle's real-space fields (eqs. (tcf-r), (dcf-r)), for two charges
+    with a strong screening (kappa = 0.6 / A) so that a 64 A box holds the integrand; the integrand is smooth,
+    so the grid sum converges spectrally.  One site has Q q_s > 0 (the squared term counts), one has Q q_s < 0."""
+    kap = 0.6
+    p = _two_charge_problem(kap)
+    T, _ = O.lra_integral(p)
+    h, L = 0.4, 32.0
+    n = int(2 * L / h)
+    origin = (-L + 1.0, -L + 0.5, -L)
+    g = O.Problem(**{**p.__dict__, "n": (n, n, n), "h": h, "origin": origin})
+    f = O.fields(g, want=("c", "h"))
+    Q = float(np.sum(p.q))
+    for s in range(p.nsite):
+        theta = 1.0 if Q * p.qs[s] > 0 else 0.0
+        integrand = 0.5 * theta * f["h"][s] ** 2 - 0.5 * f["h"][s] * f["c"][s]
+        assert T[s] == pytest.approx(float(integrand.sum()) * h ** 3, rel=2e-6), s
+    assert (Q * p.qs[0] > 0) != (Q * p.qs[1] > 0)
+
+
+def test_lra_integral_invariants():
+    """T is quadratic in the solute charges, invariant under a rigid motion of the solute, zero without
+    ionic screening, and its squared term switches with the sign of Q q_s."""
+    p = _two_charge_problem(KAPPA)
+    T, (shh, shc) = O.lra_integral(p)
+    T2, _ = O.lra_integral(O.Problem(**{**p.__dict__, "q": 3.0 * p.q}))
+    np.testing.assert_allclose(T2, 9.0 * T, rtol=1e-13)
+    rot = np.array([[0.0, -1.0, 0.0], [1.0, 0.0, 0.0], [0.0, 0.0, 1.0]])
+    T3, _ = O.lra_integral(O.Problem(**{**p.__dict__, "xyz": p.xyz @ rot.T + np.array([5.0, -3.0, 7.0])}))
+    np.testing.assert_allclose(T3, T, rtol=1e-12)
+    T0, _ = O.lra_integral(O.Problem(**{**p.__dict__, "kappa": 0.0}))
+    assert np.all(T0 == 0.0)
+    Tneg, _ = O.lra_integral(O.Problem(**{**p.__dict__, "qs": -p.qs}))
+    beta = O.beta(p)
+    for s in range(p.nsite):
+        A = -beta * p.k_e * p.qs[s] / (2 * p.eps_r)
+        # flipping q_s flips Theta(Q q_s): the difference is the squared term
+        sq = 0.5 * A * A * shh
+        assert abs(T[s] - Tneg[s]) == pytest.approx(sq, rel=1e-12)
