@@ -203,6 +203,25 @@ RISM_API rism_status rism_potential_backward(rism_ctx* ctx, const double* g_u, c
 RISM_API rism_status rism_potential_batched(rism_ctx* const* ctxs, int32_t count, double* const* u, double* const* c_lr,
                                    double* const* h_lr);
 
+/* The all-space long-range term of the excess chemical potential: the last
+ * integral of eq. (excess-chemical-potential-LRA) (Sec. 2.2), per site s,
+ *   T_s = int over all space [ 1/2 (h_s^lr)^2 Theta(Q q_s) - 1/2 h_s^lr c_s^lr ] dr
+ * (A^3), with h^lr of eq. (tcf-r), c^lr of eq. (dcf-r), Q the total solute
+ * charge and Theta(x) = 1 for x > 0, else 0.  Its contribution to mu_ex is
+ * k_B T sum_s rho_s T_s (the caller's assembly, as for lj_tail).  It is a
+ * double sum over atom pairs, O(N_atom^2) as Sec. 4.7 notes, of the overlap
+ * integrals of the kernels of eqs. (tcf-r)/(dcf-r), evaluated in closed form
+ * on the GPU with FP32 pair terms and compensated sums.
+ * T: host [S], required.  atom_sums: nullable, device or host [n][2]:
+ * per atom a (order of rism_set_solute) P_hc = sum_b Q_b I_hc(|R_a - R_b|)
+ * and P_hh = sum_b Q_b I_hh(|R_a - R_b|) (e A, b = a included), so that
+ * S_hc = sum_a Q_a P_hc and S_hh = sum_a Q_a P_hh give
+ * T_s = 1/2 Theta A_s^2 S_hh - 1/2 A_s B_s S_hc, A_s = -beta k_e q_s/(2 eps_r),
+ * B_s = -beta k_e q_s.  Without ionic screening (kappa = 0) h^lr vanishes
+ * and T = 0.  Synchronises the context's stream.  RISM_E_STATE before
+ * set_solute/set_solvent. */
+RISM_API rism_status rism_lra_integral(rism_ctx* ctx, double* T, double* atom_sums);
+
 /* Largest solute accepted by rism_init_noalloc. */
 #define RISM_NOALLOC_MAX_ATOMS 8192
 

@@ -14,6 +14,7 @@
 #include "rism_tree.h"
 #include "rism_adjoint.h"
 #include "rism_validate.h"
+#include "rism_lra.h"
 
 using namespace rism;
 
@@ -57,6 +58,13 @@ struct rism_ctx {
     // host outputs: one copy stream per output grid, so the device-to-host copies run on several copy engines
     cudaStream_t cp_st[3] = {nullptr, nullptr, nullptr};
     cudaEvent_t cp_fork = nullptr, cp_join[3] = {nullptr, nullptr, nullptr};
+    // all-space long-range integral: chunk partials, per-atom sums, totals (device) and the totals' host copy
+    double* d_lra_part = nullptr;
+    size_t lra_part_cap = 0;
+    double2* d_lra_atom = nullptr;
+    int64_t lra_atom_cap = 0;
+    double* d_lra_tot = nullptr;
+    double* h_lra_tot = nullptr;  // pinned [3]
 };
 
 namespace {
@@ -557,6 +565,74 @@ rism_status rism_potential_batched(rism_ctx* const* ctxs, int32_t count, double*
     return fail(c0, RISM_E_NOMEM, "list buffers kept growing");
 }
 
+rism_status rism_lra_integral(rism_ctx* c, double* T, double* atom_sums) {
+    if (!c) return RISM_E_INVALID;
+    if (!T) return fail(c, RISM_E_INVALID, "T (host [S]) is required");
+    if (!c->have_solute || !c->have_solvent) return fail(c, RISM_E_STATE, "set_solute and set_solvent first");
+    cudaError_t e = cudaSetDevice(c->device);
+    if (e != cudaSuccess) return cuda_fail(c, e, "cudaSetDevice");
+    const int64_t n = c->n;
+    if (!(c->ph.kappa > 0.0) || n == 0) {
+        // no ionic screening: h^lr vanishes and so does the integral
+        for (int s = 0; s < c->S; ++s) T[s] = 0.0;
+        if (atom_sums && n > 0) {
+            if (is_device_ptr(atom_sums)) {
+                if ((e = cudaMemsetAsync(atom_sums, 0, sizeof(double) * 2 * n, c->st)) != cudaSuccess)
+                    return cuda_fail(c, e, "clearing atom sums");
+            } else {
+                std::memset(atom_sums, 0, sizeof(double) * 2 * n);
+            }
+        }
+        return RISM_OK;
+    }
+    rism_status s = ensure_tables(c);
+    if (s != RISM_OK) return s;
+    int sms = 0;
+    if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, c->device)) != cudaSuccess)
+        return cuda_fail(c, e, "device attribute");
+    const size_t need = lra_scratch_doubles(n, sms);
+    if (need > c->lra_part_cap) {
+        cudaFree(c->d_lra_part);
+        c->d_lra_part = nullptr;
+        c->lra_part_cap = 0;
+        if ((e = cudaMalloc(&c->d_lra_part, sizeof(double) * need)) != cudaSuccess)
+            return cuda_fail(c, e, "LRA scratch");
+        c->lra_part_cap = need;
+    }
+    if (n > c->lra_atom_cap) {
+        cudaFree(c->d_lra_atom);
+        c->d_lra_atom = nullptr;
+        c->lra_atom_cap = 0;
+        if ((e = cudaMalloc(&c->d_lra_atom, sizeof(double2) * n)) != cudaSuccess)
+            return cuda_fail(c, e, "LRA atom sums");
+        c->lra_atom_cap = n;
+    }
+    if (!c->d_lra_tot) {
+        if ((e = cudaMalloc(&c->d_lra_tot, sizeof(double) * 3)) != cudaSuccess ||
+            (e = cudaMallocHost(&c->h_lra_tot, sizeof(double) * 3)) != cudaSuccess)
+            return cuda_fail(c, e, "LRA totals");
+    }
+    if ((e = launch_lra(c->t, c->gd, c->ph, sms, c->d_lra_part, c->d_lra_atom, c->d_lra_tot, c->o.wait_limit,
+                        c->st)) != cudaSuccess)
+        return cuda_fail(c, e, "LRA kernels");
+    if ((e = cudaMemcpyAsync(c->h_lra_tot, c->d_lra_tot, sizeof(double) * 3, cudaMemcpyDeviceToHost, c->st)) !=
+        cudaSuccess)
+        return cuda_fail(c, e, "LRA totals copy");
+    if (atom_sums &&
+        (e = cudaMemcpyAsync(atom_sums, c->d_lra_atom, sizeof(double2) * n, cudaMemcpyDefault, c->st)) != cudaSuccess)
+        return cuda_fail(c, e, "LRA atom sums copy");
+    if ((s = check_device_error(c)) != RISM_OK) return s;  // synchronises the stream
+    const double Shh = c->h_lra_tot[0], Shc = c->h_lra_tot[1], Q = c->h_lra_tot[2];
+    for (int k = 0; k < c->S; ++k) {
+        const double A = -c->ph.beta * c->ph.k_e * c->qs[k] / (2.0 * c->ph.eps_r);
+        const double B = -c->ph.beta * c->ph.k_e * c->qs[k];
+        const double theta = (Q * c->qs[k] > 0.0) ? 1.0 : 0.0;
+        T[k] = 0.5 * theta * A * A * Shh - 0.5 * A * B * Shc;
+    }
+    c->info.launches = 3;
+    return RISM_OK;
+}
+
 rism_status rism_get_info(const rism_ctx* c, rism_info* info) {
     if (!c || !info) return RISM_E_INVALID;
     *info = c->info;
@@ -592,6 +668,10 @@ void rism_destroy(rism_ctx* c) {
         if (c->cp_join[k]) cudaEventDestroy(c->cp_join[k]);
     }
     if (c->cp_fork) cudaEventDestroy(c->cp_fork);
+    cudaFree(c->d_lra_part);
+    cudaFree(c->d_lra_atom);
+    cudaFree(c->d_lra_tot);
+    cudaFreeHost(c->h_lra_tot);
     delete c;
 }
 

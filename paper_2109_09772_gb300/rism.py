@@ -58,7 +58,7 @@ class Info(C.Structure):
 
 EXPORTS = ["rism_default_options", "rism_grid_create", "rism_set_solute", "rism_set_solvent", "rism_potential",
            "rism_asymptotics", "rism_init", "rism_potential_backward", "rism_potential_batched", "rism_get_info",
-           "rism_destroy", "rism_last_error", "rism_init_noalloc"]
+           "rism_destroy", "rism_last_error", "rism_init_noalloc", "rism_lra_integral"]
 NOALLOC_MAX_ATOMS = 8192
 
 _lib = None
@@ -99,6 +99,8 @@ def load(path: str = LIB_PATH):
         lib.rism_destroy.argtypes = [P]
         lib.rism_last_error.restype = C.c_char_p
         lib.rism_last_error.argtypes = [P]
+        lib.rism_lra_integral.restype = C.c_int
+        lib.rism_lra_integral.argtypes = [P, P, P]
         lib.rism_init_noalloc.restype = C.c_int
         lib.rism_init_noalloc.argtypes = [C.POINTER(GridDesc), C.POINTER(Options), I64, P, P, P, P, I32, P, P, P, P,
                                           P, P, P, P, P, C.c_char_p, C.c_size_t]
@@ -239,6 +241,14 @@ class Rism:
                                               _ptr(outs["q"]), _ptr(outs["sigma"]), _ptr(outs["eps"]))
         self._check(st, "rism_potential_backward")
         return {k: v for k, v in outs.items() if v is not None}
+
+    def lra_integral(self, atom_sums=False):
+        """The all-space long-range integral T_s (A^3) of every site (rism_lra_integral); with atom_sums also
+        the per-atom overlap sums (P_hc, P_hh) as an [n, 2] device tensor."""
+        T = np.zeros(max(self.S, 1))
+        a = self._torch.empty((self.natoms, 2), dtype=self._torch.float64, device=self.device) if atom_sums else None
+        self._check(self.lib.rism_lra_integral(self.ctx, T.ctypes.data, _ptr(a)), "rism_lra_integral")
+        return (T[: self.S].copy(), a) if atom_sums else T[: self.S].copy()
 
     def info(self):
         inf = Info()
