@@ -66,6 +66,12 @@ def _load():
             lib.orc_lra_atom_sums.argtypes = [I64, P, P, D, D, I64, P, P, P, I32]
             lib.orc_lra_integral.restype = C.c_int
             lib.orc_lra_integral.argtypes = [I64, P, P, I32, P, D, D, D, D, D, P, P, I32]
+            lib.orc_kspace.restype = C.c_int
+            lib.orc_kspace.argtypes = [I64, P, P, I32, P, D, D, D, D, D, I32, I32, I32, D, P, D, I64, P, P, P, I32]
+            lib.orc_kspace_bound.restype = D
+            lib.orc_kspace_bound.argtypes = [D, D, D, D, D, D]
+            lib.orc_kspace_kcut.restype = D
+            lib.orc_kspace_kcut.argtypes = [D, D, D, D, D, D]
             _lib = lib
     return _lib
 
@@ -249,3 +255,30 @@ def lra_integral(p: Problem, nthreads: int = 0):
     if rc != 0:
         raise MemoryError("oracle allocation failed")
     return T, (float(S2[0]), float(S2[1]))
+
+
+def kspace_kcut(p: Problem, tol):
+    """Cut-off wave number (1/A) where the bound of eq. (k-space-dcf-err) equals tol (0: no cut-off)."""
+    return _load().orc_kspace_kcut(p.eta, float(np.max(np.abs(p.qs))), float(np.sum(np.abs(p.q))), beta(p), p.k_e,
+                                   float(tol))
+
+
+def kspace_bound(p: Problem, k):
+    return _load().orc_kspace_bound(float(k), p.eta, float(np.max(np.abs(p.qs))), float(np.sum(np.abs(p.q))),
+                                    beta(p), p.k_e)
+
+
+def kspace(p: Problem, kcut=0.0, idx=None, want=("c", "h"), nthreads: int = 0):
+    """c_s(k), h_s(k) of eqs. (dcf-k)/(tcf-k) on the half spectrum [S, nz*ny*(nx//2+1)] (complex128), or at the
+    listed flat indices of it; entries with k > kcut are 0 (kcut <= 0: none)."""
+    lib = _load()
+    nx, ny, nz = (int(v) for v in p.n)
+    m = (nx // 2 + 1) * ny * nz if idx is None else int(len(idx))
+    if idx is not None:
+        idx = np.ascontiguousarray(idx, dtype=np.int64)
+    out = {k: (np.zeros((p.nsite, m), dtype=np.complex128) if k in want else None) for k in ("c", "h")}
+    org = _f64(p.origin)
+    lib.orc_kspace(p.natoms, _p(_f64(p.xyz)), _p(_f64(p.q)), p.nsite, _p(_f64(p.qs)), beta(p), p.k_e, p.eps_r,
+                   p.eta, kappa(p), nx, ny, nz, p.h, _p(org), float(kcut), m, _p(idx), _p(out["c"]), _p(out["h"]),
+                   int(nthreads))
+    return {k: v for k, v in out.items() if v is not None}

@@ -19,7 +19,10 @@
  *     [G_u u + G_c c + G_h h] (the paper has no gradient; these are the
  *     plain derivatives of the three definitions above);
  *   - T_s: the all-space integral of eq. (excess-chemical-potential-LRA)
- *     (Sec. 2.2), as a double sum over atom pairs of 1D integrals.
+ *     (Sec. 2.2), as a double sum over atom pairs of 1D integrals;
+ *   - c_s(k), h_s(k): the reciprocal-space asymptotics of eq. (dcf-k) and
+ *     eq. (tcf-k) on the grid's reciprocal lattice, with the frequency
+ *     cut-off of Sec. 2.5 (its bound eq. (k-space-dcf-err) and root).
  *
  * Readings of the paper taken here (the paper is silent or ambiguous):
  *   - Gaussian-unit formulas are multiplied by the Coulomb constant k_e
@@ -565,4 +568,86 @@ int orc_lra_integral(int64_t n, const double* xyz, const double* q, int32_t S, c
     free(phc);
     free(phh);
     return 0;
+}
+
+/* ------------------------------------------ reciprocal-space asymptotics */
+
+/*
+ * Eq. (dcf-k) and eq. (tcf-k) (Sec. 2.2) on the reciprocal lattice of the grid, with the Coulomb constant k_e
+ * of the unit reading:
+ *   c_s(k) = -(4 pi beta k_e q_s / k^2) e^{-k^2 eta^2/4} sum_a Q_a e^{i k.(R_a - o)}
+ *   h_s(k) = -(4 pi beta k_e q_s / (eps_r (k^2 + kappa^2))) e^{-k^2 eta^2/4} sum_a Q_a e^{i k.(R_a - o)}
+ * o = the grid origin, k = 2 pi (m_x/(n_x h), m_y/(n_y h), m_z/(n_z h)) with the frequency layout of a real-to-
+ * complex transform: index j_x in [0, n_x/2] is m_x = j_x; along y and z, m = j for j <= (n-1)/2 and j - n
+ * above.  The half spectrum is stored [S][n_z][n_y][n_x/2 + 1], re/im interleaved.  c(k = 0) is set to 0 (the
+ * 1/k^2 term is not defined there); with kappa = 0 h is 0.  Frequency cut-off (Sec. 2.5): entries with
+ * k^2 > kcut^2 are 0 (kcut <= 0: none).  idx lists flat indices into one site's half spectrum (NULL: all).
+ */
+int orc_kspace(int64_t n, const double* xyz, const double* q, int32_t S, const double* qs, double beta,
+               double k_e, double eps_r, double eta, double kappa, int32_t nx, int32_t ny, int32_t nz, double h,
+               const double* origin, double kcut, int64_t m, const int64_t* idx, double* c_out, double* h_out,
+               int32_t nthreads)
+{
+    int64_t nxh = nx / 2 + 1;
+    int64_t total = idx ? m : nxh * (int64_t)ny * nz;
+#ifdef _OPENMP
+    if (nthreads > 0) omp_set_num_threads(nthreads);
+#pragma omp parallel for schedule(dynamic, 16)
+#endif
+    for (int64_t p = 0; p < total; ++p) {
+        int64_t f = idx ? idx[p] : p;
+        int64_t jx = f % nxh, jy = (f / nxh) % ny, jz = f / (nxh * ny);
+        double mx = (double)jx;
+        double my = (double)(jy <= (ny - 1) / 2 ? jy : jy - ny);
+        double mz = (double)(jz <= (nz - 1) / 2 ? jz : jz - nz);
+        double kx = 2.0 * ORC_PI * mx / (nx * h), ky = 2.0 * ORC_PI * my / (ny * h), kz = 2.0 * ORC_PI * mz / (nz * h);
+        double k2 = kx * kx + ky * ky + kz * kz;
+        int keep = !(kcut > 0.0) || k2 <= kcut * kcut;
+        double sre = 0.0, sim = 0.0;
+        if (keep) {
+            nsum_t re, im;
+            ns_init(&re);
+            ns_init(&im);
+            for (int64_t a = 0; a < n; ++a) {
+                double ph = kx * (xyz[3 * a + 0] - origin[0]) + ky * (xyz[3 * a + 1] - origin[1]) +
+                            kz * (xyz[3 * a + 2] - origin[2]);
+                ns_add(&re, q[a] * cos(ph));
+                ns_add(&im, q[a] * sin(ph));
+            }
+            sre = ns_get(&re);
+            sim = ns_get(&im);
+        }
+        double gau = exp(-k2 * eta * eta / 4.0);
+        double fc = (keep && k2 > 0.0) ? -4.0 * ORC_PI * beta * k_e * gau / k2 : 0.0;
+        double fh = (keep && kappa > 0.0) ? -4.0 * ORC_PI * beta * k_e * gau / (eps_r * (k2 + kappa * kappa)) : 0.0;
+        for (int32_t s = 0; s < S; ++s) {
+            int64_t o = 2 * ((int64_t)s * total + p);
+            if (c_out) { c_out[o] = qs[s] * fc * sre; c_out[o + 1] = qs[s] * fc * sim; }
+            if (h_out) { h_out[o] = qs[s] * fh * sre; h_out[o + 1] = qs[s] * fh * sim; }
+        }
+    }
+    return 0;
+}
+
+/* The bound of eq. (k-space-dcf-err) (Sec. 2.5) at wave number k, as a true bound for every solute and site:
+ * 4 sqrt(2) pi beta k_e max_s |q_s| e^{-k^2 eta^2/4} sum_a |Q_a| / k^2 (the paper prints the signed sum
+ * sum_a Q_a, which vanishes for a neutral solute; |sum Q e^{ik.R}| <= sum |Q| is the bound it derives). */
+double orc_kspace_bound(double k, double eta, double qmax, double qabs, double beta, double k_e)
+{
+    return 4.0 * sqrt(2.0) * ORC_PI * beta * k_e * qmax * exp(-k * k * eta * eta / 4.0) * qabs / (k * k);
+}
+
+/* The cut-off wave number: the k where the bound equals tol (the bound decreases with k), by bisection. */
+double orc_kspace_kcut(double eta, double qmax, double qabs, double beta, double k_e, double tol)
+{
+    if (!(tol > 0.0) || !(qabs > 0.0) || !(qmax > 0.0)) return 0.0;
+    double lo = 1e-6, hi = 1.0;
+    while (orc_kspace_bound(hi, eta, qmax, qabs, beta, k_e) > tol) hi *= 2.0;
+    if (orc_kspace_bound(lo, eta, qmax, qabs, beta, k_e) <= tol) return lo;
+    for (int it = 0; it < 4000; ++it) {
+        double mid = 0.5 * (lo + hi);
+        if (mid <= lo || mid >= hi) break;
+        if (orc_kspace_bound(mid, eta, qmax, qabs, beta, k_e) > tol) lo = mid; else hi = mid;
+    }
+    return hi;
 }

@@ -466,3 +466,90 @@ def test_lra_integral_invariants():
         # flipping q_s flips Theta(Q q_s): the difference is the squared term
         sq = 0.5 * A * A * shh
         assert abs(T[s] - Tneg[s]) == pytest.approx(sq, rel=1e-12)
+
+
+# ---------------------------------------------- reciprocal-space asymptotics
+def _kspace_problem(kappa, n=(40, 37, 36), h=0.5, eta=2.0):
+    """Two opposite charges off-lattice, an ionic and a water-like site, an odd and an even grid axis."""
+    return O.Problem(xyz=np.array([[0.37, -0.81, 0.55], [2.13, 1.02, -1.44]]), q=np.array([0.9, -0.6]),
+                     sigma=np.array([2.0, 2.0]), eps=np.array([0.1, 0.1]), qs=np.array([1.0, -0.4]),
+                     sigs=np.array([2.0, 1.0]), epss=np.array([0.1, 0.01]), rho=np.array([0.03, 0.06]),
+                     is_ion=np.array([1, 0], dtype=np.int32), n=n, h=h,
+                     origin=tuple(-h * (v - 1) / 2.0 + 0.11 * (i + 1) for i, v in enumerate(n)), eta=eta, kappa=kappa)
+
+
+def test_kspace_tcf_is_the_transform_of_the_real_space_tcf():
+    """h_s(k) of eq. (tcf-k) on the grid's reciprocal lattice equals h^3 sum_j h_s^lr(o + h j) e^{+i k.(h j)}
+    over the real-space samples of eq. (tcf-r) (the complex conjugate of numpy's forward rfftn, whose frequency
+    layout the half spectrum follows): this fixes the sign of the phase, the origin, the lattice, the FFT order
+    (one odd axis) and the 4 pi / (eps_r (k^2 + kappa^2)) Gaussian factor.  Strong screening and eta = 2 A make
+    the truncated, sampled sum converge to the continuous transform."""
+    p = _kspace_problem(kappa=0.6, n=(128, 121, 120))
+    nx, ny, nz = p.n
+    real = O.fields(p, want=("h",))["h"]
+    ks = O.kspace(p, want=("c", "h"))
+    for s in range(p.nsite):
+        dft = np.conj(np.fft.rfftn(real[s].reshape(nz, ny, nx))) * p.h ** 3
+        got = ks["h"][s].reshape(nz, ny, nx // 2 + 1)
+        scale = np.abs(got).max()
+        assert np.abs(got - dft).max() <= 2e-7 * scale, (s, np.abs(got - dft).max() / scale)
+
+
+def test_kspace_dcf_against_tcf_and_at_k0():
+    """c_s(k)/h_s(k) = eps_r (k^2 + kappa^2)/k^2 at every k != 0 (eq. (dcf-k) vs eq. (tcf-k)); c_s(0) = 0,
+    h_s(0) = -(4 pi beta k_e q_s / (eps_r kappa^2)) sum_a Q_a."""
+    p = _kspace_problem(kappa=0.3)
+    nx, ny, nz = p.n
+    ks = O.kspace(p)
+    jx, jy, jz = np.meshgrid(np.arange(nx // 2 + 1), np.arange(ny), np.arange(nz), indexing="xy")
+    f = np.fft.fftfreq
+    kx = 2 * np.pi * np.arange(nx // 2 + 1) / (nx * p.h)
+    ky = 2 * np.pi * f(ny, d=p.h)
+    kz = 2 * np.pi * f(nz, d=p.h)
+    k2 = (kz[:, None, None] ** 2 + ky[None, :, None] ** 2 + kx[None, None, :] ** 2).ravel()
+    nz0 = k2 > 0
+    for s in range(p.nsite):
+        c, hh = ks["c"][s], ks["h"][s]
+        np.testing.assert_allclose(c[nz0], hh[nz0] * p.eps_r * (k2[nz0] + 0.09) / k2[nz0], rtol=1e-12, atol=0)
+        assert c[0] == 0.0
+        h0 = -4 * np.pi * O.beta(p) * p.k_e * p.qs[s] / (p.eps_r * 0.09) * p.q.sum()
+        assert hh[0] == pytest.approx(h0, rel=1e-13)
+
+
+def test_kspace_translation_phase():
+    """Moving the solute by a lattice vector t multiplies every entry by e^{i k.t}."""
+    p = _kspace_problem(kappa=0.3, eta=1.0)
+    t = np.array([3, -2, 5]) * p.h
+    a = O.kspace(p)["c"][0]
+    b = O.kspace(O.Problem(**{**p.__dict__, "xyz": p.xyz + t}))["c"][0]
+    nx, ny, nz = p.n
+    kx = 2 * np.pi * np.arange(nx // 2 + 1) / (nx * p.h)
+    ky = 2 * np.pi * np.fft.fftfreq(ny, d=p.h)
+    kz = 2 * np.pi * np.fft.fftfreq(nz, d=p.h)
+    kt = (kz[:, None, None] * t[2] + ky[None, :, None] * t[1] + kx[None, None, :] * t[0]).ravel()
+    np.testing.assert_allclose(b, a * np.exp(1j * kt), rtol=1e-12, atol=1e-12 * np.abs(a).max())
+
+
+def test_kspace_cutoff_bound_and_root():
+    """The cut-off wave number solves eq. (k-space-dcf-err) = tol (the bound decreases in k), every kept entry
+    lies within it, every dropped entry is zero, and no dropped entry of the full sum exceeds the bound."""
+    p = _kspace_problem(kappa=0.3, eta=1.0, n=(32, 30, 28))
+    ks_full = O.kspace(p)
+    tol = 1e-2 * float(np.abs(ks_full["c"]).max())
+    kc = O.kspace_kcut(p, tol)
+    assert O.kspace_bound(p, kc) == pytest.approx(tol, rel=1e-12)
+    ks = np.linspace(0.2, 8.0, 50)
+    b = np.array([O.kspace_bound(p, k) for k in ks])
+    assert np.all(np.diff(b) < 0)
+    cut = O.kspace(p, kcut=kc)
+    nx, ny, nz = p.n
+    kx = 2 * np.pi * np.arange(nx // 2 + 1) / (nx * p.h)
+    ky = 2 * np.pi * np.fft.fftfreq(ny, d=p.h)
+    kz = 2 * np.pi * np.fft.fftfreq(nz, d=p.h)
+    k2 = (kz[:, None, None] ** 2 + ky[None, :, None] ** 2 + kx[None, None, :] ** 2).ravel()
+    keep = k2 <= kc * kc
+    assert 0 < keep.sum() < keep.size
+    for key in ("c", "h"):
+        np.testing.assert_array_equal(cut[key][:, keep], ks_full[key][:, keep])
+        assert np.all(cut[key][:, ~keep] == 0)
+        assert np.abs(ks_full[key][:, ~keep]).max() <= tol
