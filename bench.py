@@ -610,6 +610,89 @@ def suite_adjoint(args):
     r.close()
 
 
+def suite_kspace(args):
+    """Reciprocal-space asymptotics (eqs. (dcf-k)/(tcf-k)) of the 13,600-atom ellipsoid on the half spectrum of
+    its 224x192x160 grid: the whole half spectrum, and with the frequency cut-off of Sec. 2.5 at tolerances
+    1e-4 and 1e-2 of the largest |c(k)|; CUDA events around the call's kernels; FMA-pipe roofline of the
+    structure-factor sum (4 FP32 FMAs per kept (k, atom) pair); sampled errors against the FP64 oracle."""
+    import numpy as np
+    import torch
+
+    from oracle import oracle as O
+    from paper_2109_09772_gb300 import build as B
+    from paper_2109_09772_gb300 import inputs as I
+    from paper_2109_09772_gb300 import rism as R
+
+    B.build()
+    torch.cuda.set_device(0)
+    w = I.workload(2)
+    nx, ny, nz = w.grid.n
+    nh = nx // 2 + 1
+    r = R.from_workload(w, method=R.METHOD_TREECODE, precision=R.PREC_FP32, debug_flags=2)
+    p = O.Problem.from_workload(w)
+    idx = I.sample_indices(nh * ny * nz, 1500, seed=4)
+    t = torch.as_tensor(idx, device="cuda")
+    peaks, src = _peaks()
+    clk = peaks.get("sm_max_mhz", 2070.0) * 1e6
+    fma_peak = SMS * FP32_LANES_PER_SM * clk  # FMA/s
+    c0, _, _ = r.asymptotics_k(0.0)
+    cmax = float(c0.abs().max())
+    kx = 2 * np.pi * np.arange(nh) / (nx * w.grid.h)
+    ky = 2 * np.pi * np.fft.fftfreq(ny, d=w.grid.h)
+    kz = 2 * np.pi * np.fft.fftfreq(nz, d=w.grid.h)
+    k2 = (kz[:, None, None] ** 2 + ky[None, :, None] ** 2 + kx[None, None, :] ** 2).ravel()
+    for rel in (0.0, 1e-4, 1e-2):
+        tol = rel * cmax
+        ms = []
+        for _ in range(max(3, args.reps)):
+            c, h, kc = r.asymptotics_k(tol)
+            torch.cuda.synchronize()
+            ms.append(r.info()["eval_ms"])
+        ms = min(ms)
+        kept = int(np.count_nonzero(k2 <= kc * kc)) if kc > 0 else k2.size
+        fma = 4.0 * kept * w.solute.n
+        ref = O.kspace(p, kcut=kc, idx=idx)
+        err = {k: float(np.linalg.norm(v.reshape(r.S, -1)[:, t].cpu().numpy() - ref[k]) / np.linalg.norm(ref[k]))
+               for k, v in (("c", c), ("h", h))}
+        print(json.dumps({"suite": "kspace", "workload": "ellipsoid13600_224x192x160", "k_tol_rel": rel,
+                          "k_cut": kc, "kept_k": kept, "half_spectrum": int(k2.size), "ms": ms,
+                          "roofline": {"bound": "alu", "unit": "FMA/s", "achieved": fma / (ms * 1e-3),
+                                       "peak": fma_peak, "frac": fma / (ms * 1e-3) / fma_peak,
+                                       "peak_source": f"FP32 FMA pipe, {SMS} SMs x 128 lanes at "
+                                                      f"{clk / 1e6:.0f} MHz ({src})"},
+                          "err_sampled_rel_l2": err}), flush=True)
+    r.close()
+
+
+def suite_lra(args):
+    """The all-space long-range integral (last integral of eq. (excess-chemical-potential-LRA)), O(N_atom^2)
+    atom pairs, for the 13,600-atom ellipsoid and the 55,000-atom stack; MUFU-bound pair roofline."""
+    import torch
+
+    from paper_2109_09772_gb300 import build as B
+    from paper_2109_09772_gb300 import inputs as I
+    from paper_2109_09772_gb300 import rism as R
+
+    B.build()
+    torch.cuda.set_device(0)
+    peaks, src = _peaks()
+    clk = peaks.get("sm_max_mhz", 2070.0) * 1e6
+    xu_peak = SMS * clk / MUFU_CLK_PER_PAIR
+    for idx in (2, 4):
+        w = I.workload(idx)
+        r = R.from_workload(w, method=R.METHOD_DIRECT, precision=R.PREC_FP32)
+        T = r.lra_integral()
+        ms = _events_ms(lambda: r.lra_integral(), reps=max(3, args.reps))
+        pairs = float(w.solute.n) ** 2
+        print(json.dumps({"suite": "lra", "workload": w.name, "atoms": w.solute.n, "T_A3": list(T), "ms": ms,
+                          "pairs_per_s": pairs / (ms * 1e-3),
+                          "roofline": {"bound": "alu", "unit": "pairs/s", "achieved": pairs / (ms * 1e-3),
+                                       "peak": xu_peak, "frac": pairs / (ms * 1e-3) / xu_peak,
+                                       "peak_source": "rsqrt + ex2 per pair on the special-function pipe"}}),
+              flush=True)
+        r.close()
+
+
 def suite_mufu(args):
     """Issue rates of rsqrt / ex2 / rcp / FFMA / DFMA (thread ops per clock per SM): compiles and runs the
     microbenchmark in microbench/ (the denominators of the pair kernels' rooflines)."""
@@ -639,14 +722,14 @@ def main():
     ap.add_argument("--no-fp64", action="store_true")
     ap.add_argument("--no-check", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
-    ap.add_argument("--suite", default=None, choices=["pareto", "batched", "adjoint", "mufu"])
+    ap.add_argument("--suite", default=None, choices=["pareto", "batched", "adjoint", "mufu", "kspace", "lra"])
     ap.add_argument("--reps", type=int, default=3)
     ap.add_argument("--adj-atoms", type=int, default=16)
     args = ap.parse_args()
     _WIDX[0] = _select(args.workload)
     if args.suite:
-        {"pareto": suite_pareto, "batched": suite_batched, "adjoint": suite_adjoint,
-         "mufu": suite_mufu}[args.suite](args)
+        {"pareto": suite_pareto, "batched": suite_batched, "adjoint": suite_adjoint, "mufu": suite_mufu,
+         "kspace": suite_kspace, "lra": suite_lra}[args.suite](args)
         return
     if args.warmup < 3:
         args.warmup = 3

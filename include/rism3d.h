@@ -203,6 +203,28 @@ RISM_API rism_status rism_potential_backward(rism_ctx* ctx, const double* g_u, c
 RISM_API rism_status rism_potential_batched(rism_ctx* const* ctxs, int32_t count, double* const* u, double* const* c_lr,
                                    double* const* h_lr);
 
+/* Reciprocal-space long-range asymptotics, eq. (dcf-k) and eq. (tcf-k)
+ * (Sec. 2.2), times k_e as in the real-space forms:
+ *   c_s(k) = -(4 pi beta k_e q_s / k^2) e^{-k^2 eta^2/4} sum_a Q_a e^{i k.(R_a - o)}
+ *   h_s(k) = -(4 pi beta k_e q_s / (eps_r (k^2 + kappa^2))) e^{-k^2 eta^2/4} sum_a Q_a e^{i k.(R_a - o)}
+ * (A^3), o = grid origin, on the reciprocal lattice of the grid in the half-
+ * spectrum layout of a real-to-complex transform: c_k, h_k are
+ * [S][nz][ny][nx/2+1] complex values stored as (re, im) FP64 pairs, k =
+ * 2 pi (m_x/(nx h), m_y/(ny h), m_z/(nz h)) with m_x = j_x and, along y and
+ * z, m = j for j <= (n-1)/2 and j - n above (numpy's rfftn frequency
+ * order).  c(0) = 0 (the 1/k^2 term has no value there).  Frequency cut-off
+ * of Sec. 2.5: with k_tol > 0 the cut-off k_cut solves the bound of
+ * eq. (k-space-dcf-err), 4 sqrt(2) pi beta k_e max_s|q_s| e^{-k^2 eta^2/4}
+ * sum_a |Q_a| / k^2 = k_tol (read with |Q_a|: the printed signed sum vanishes
+ * for a neutral solute), by Newton's method, and every entry with k^2 > k_cut^2
+ * is 0; k_tol <= 0 sums the whole half spectrum.  *k_cut (host, nullable)
+ * receives the cut-off (0 = none).  c_k, h_k: device or host memory, each
+ * nullable (h_k needs kappa > 0, RISM_E_INVALID otherwise).  The structure
+ * factor runs on the GPU with FP32 phase tables reduced exactly modulo one
+ * cycle and FP32 products with float-float sums.  Synchronises the
+ * context's stream.  RISM_E_STATE before set_solute/set_solvent. */
+RISM_API rism_status rism_asymptotics_k(rism_ctx* ctx, double k_tol, double* c_k, double* h_k, double* k_cut);
+
 /* The all-space long-range term of the excess chemical potential: the last
  * integral of eq. (excess-chemical-potential-LRA) (Sec. 2.2), per site s,
  *   T_s = int over all space [ 1/2 (h_s^lr)^2 Theta(Q q_s) - 1/2 h_s^lr c_s^lr ] dr

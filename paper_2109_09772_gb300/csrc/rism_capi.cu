@@ -4,6 +4,7 @@
 // the physical constants (beta, Debye kappa of eq. (tcf-r), the d -> 0 limits
 // of the two asymptotic kernels), dispatch to the kernels and status
 // reporting.  Every grid value is computed by the CUDA kernels.
+#include <algorithm>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -15,6 +16,7 @@
 #include "rism_adjoint.h"
 #include "rism_validate.h"
 #include "rism_lra.h"
+#include "rism_kspace.h"
 
 using namespace rism;
 
@@ -65,6 +67,11 @@ struct rism_ctx {
     int64_t lra_atom_cap = 0;
     double* d_lra_tot = nullptr;
     double* h_lra_tot = nullptr;  // pinned [3]
+    // reciprocal-space asymptotics: per-atom phase tables and device staging for host outputs
+    void* d_ktab = nullptr;
+    size_t ktab_bytes = 0;
+    double* d_kstage[2] = {nullptr, nullptr};
+    size_t kstage_bytes = 0;
 };
 
 namespace {
@@ -633,6 +640,84 @@ rism_status rism_lra_integral(rism_ctx* c, double* T, double* atom_sums) {
     return RISM_OK;
 }
 
+rism_status rism_asymptotics_k(rism_ctx* c, double k_tol, double* c_k, double* h_k, double* k_cut) {
+    if (!c) return RISM_E_INVALID;
+    if (!c->have_solute || !c->have_solvent) return fail(c, RISM_E_STATE, "set_solute and set_solvent first");
+    if (!std::isfinite(k_tol)) return fail(c, RISM_E_INVALID, "k_tol must be finite");
+    if (h_k && !(c->ph.kappa > 0.0)) return fail(c, RISM_E_INVALID, "h_k needs kappa > 0 (ionic solvent)");
+    cudaError_t e = cudaSetDevice(c->device);
+    if (e != cudaSuccess) return cuda_fail(c, e, "cudaSetDevice");
+    KspaceSetup ks;
+    ks.S = c->S;
+    ks.beta = c->ph.beta;
+    ks.k_e = c->ph.k_e;
+    ks.eps_r = c->ph.eps_r;
+    ks.eta = c->ph.eta;
+    ks.kappa = c->ph.kappa;
+    ks.qmax = 0.0;
+    for (int k = 0; k < kMaxSites; ++k) {
+        ks.qs[k] = k < c->S ? c->qs[k] : 0.0;
+        if (k < c->S) ks.qmax = std::max(ks.qmax, std::fabs(c->qs[k]));
+    }
+    ks.qabs = 0.0;
+    for (int64_t i = 0; i < c->n; ++i) ks.qabs += std::fabs(c->raw[6 * i + 3]);
+    ks.kcut = k_tol > 0.0 ? kspace_kcut(ks, k_tol) : 0.0;
+    if (k_cut) *k_cut = ks.kcut;
+    if (!c_k && !h_k) return RISM_OK;
+    rism_status s = ensure_tables(c);
+    if (s != RISM_OK) return s;
+    const size_t bytes = sizeof(double) * 2 * (size_t)c->S * (size_t)c->g.nz * c->g.ny * (c->g.nx / 2 + 1);
+    double* user[2] = {c_k, h_k};
+    double* dev[2] = {nullptr, nullptr};
+    bool host = false;
+    for (int k = 0; k < 2; ++k) {
+        if (!user[k]) continue;
+        if (is_device_ptr(user[k])) {
+            dev[k] = user[k];
+            continue;
+        }
+        host = true;
+        if (c->kstage_bytes < bytes) {
+            cudaFree(c->d_kstage[0]);
+            cudaFree(c->d_kstage[1]);
+            c->d_kstage[0] = c->d_kstage[1] = nullptr;
+            c->kstage_bytes = 0;
+            if ((e = cudaMalloc(&c->d_kstage[0], bytes)) != cudaSuccess ||
+                (e = cudaMalloc(&c->d_kstage[1], bytes)) != cudaSuccess)
+                return cuda_fail(c, e, "k-space staging buffer");
+            c->kstage_bytes = bytes;
+        }
+        dev[k] = c->d_kstage[k];
+    }
+    const size_t tb = kspace_table_bytes(c->n, c->g.nx, c->g.ny, c->g.nz);
+    if (tb > c->ktab_bytes) {
+        cudaFree(c->d_ktab);
+        c->d_ktab = nullptr;
+        c->ktab_bytes = 0;
+        if ((e = cudaMalloc(&c->d_ktab, tb)) != cudaSuccess) return cuda_fail(c, e, "k-space phase tables");
+        c->ktab_bytes = tb;
+    }
+    const bool timed = (c->o.debug_flags & 2) != 0;
+    if (timed) {
+        if (!c->ev[0]) {
+            cudaEventCreate(&c->ev[0]);
+            cudaEventCreate(&c->ev[1]);
+        }
+        cudaEventRecord(c->ev[0], c->st);
+    }
+    if ((e = launch_kspace(c->t, c->gd, ks, c->d_ktab, dev[0], dev[1], c->o.wait_limit, c->st)) != cudaSuccess)
+        return cuda_fail(c, e, "k-space kernels");
+    if (timed) cudaEventRecord(c->ev[1], c->st);
+    for (int k = 0; k < 2 && host; ++k)
+        if (user[k] && dev[k] != user[k] &&
+            (e = cudaMemcpyAsync(user[k], dev[k], bytes, cudaMemcpyDeviceToHost, c->st)) != cudaSuccess)
+            return cuda_fail(c, e, "k-space result copy");
+    c->info.launches = 2;
+    s = check_device_error(c);  // synchronises the stream
+    if (s == RISM_OK && timed) cudaEventElapsedTime(&c->info.eval_ms, c->ev[0], c->ev[1]);
+    return s;
+}
+
 rism_status rism_get_info(const rism_ctx* c, rism_info* info) {
     if (!c || !info) return RISM_E_INVALID;
     *info = c->info;
@@ -672,6 +757,9 @@ void rism_destroy(rism_ctx* c) {
     cudaFree(c->d_lra_atom);
     cudaFree(c->d_lra_tot);
     cudaFreeHost(c->h_lra_tot);
+    cudaFree(c->d_ktab);
+    cudaFree(c->d_kstage[0]);
+    cudaFree(c->d_kstage[1]);
     delete c;
 }
 

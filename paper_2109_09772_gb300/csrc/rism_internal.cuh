@@ -19,7 +19,7 @@ struct DevErr {
     int where;  // kernel id that reported it
 };
 enum : int { WHERE_DIRECT = 1, WHERE_TREE_EVAL = 2, WHERE_ADJOINT = 3, WHERE_BATCH = 4, WHERE_UPWARD = 5,
-             WHERE_INPUT_CHECK = 6, WHERE_LRA = 7 };
+             WHERE_INPUT_CHECK = 6, WHERE_LRA = 7, WHERE_KSPACE = 8 };
 
 // ---------------------------------------------------------------- records
 // Atom geometry: position (physical A for the FP64 path; grid units relative

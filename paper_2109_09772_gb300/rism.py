@@ -58,7 +58,8 @@ class Info(C.Structure):
 
 EXPORTS = ["rism_default_options", "rism_grid_create", "rism_set_solute", "rism_set_solvent", "rism_potential",
            "rism_asymptotics", "rism_init", "rism_potential_backward", "rism_potential_batched", "rism_get_info",
-           "rism_destroy", "rism_last_error", "rism_init_noalloc", "rism_lra_integral"]
+           "rism_destroy", "rism_last_error", "rism_init_noalloc", "rism_lra_integral",
+           "rism_asymptotics_k"]
 NOALLOC_MAX_ATOMS = 8192
 
 _lib = None
@@ -99,6 +100,8 @@ def load(path: str = LIB_PATH):
         lib.rism_destroy.argtypes = [P]
         lib.rism_last_error.restype = C.c_char_p
         lib.rism_last_error.argtypes = [P]
+        lib.rism_asymptotics_k.restype = C.c_int
+        lib.rism_asymptotics_k.argtypes = [P, C.c_double, P, P, P]
         lib.rism_lra_integral.restype = C.c_int
         lib.rism_lra_integral.argtypes = [P, P, P]
         lib.rism_init_noalloc.restype = C.c_int
@@ -241,6 +244,19 @@ class Rism:
                                               _ptr(outs["q"]), _ptr(outs["sigma"]), _ptr(outs["eps"]))
         self._check(st, "rism_potential_backward")
         return {k: v for k, v in outs.items() if v is not None}
+
+    def asymptotics_k(self, k_tol=0.0, c=True, h=True):
+        """c_s(k), h_s(k) of eqs. (dcf-k)/(tcf-k) on the half spectrum (rism_asymptotics_k) as complex128
+        device tensors [S, nz, ny, nx//2+1], and the cut-off wave number used (0 = none)."""
+        torch = self._torch
+        nx, ny, nz = self.n
+        shape = (self.S, nz, ny, nx // 2 + 1)
+        cc = torch.empty(shape, dtype=torch.complex128, device=self.device) if c else None
+        hh = torch.empty(shape, dtype=torch.complex128, device=self.device) if h else None
+        kc = C.c_double(0.0)
+        self._check(self.lib.rism_asymptotics_k(self.ctx, float(k_tol), _ptr(cc), _ptr(hh), C.byref(kc)),
+                    "rism_asymptotics_k")
+        return cc, hh, kc.value
 
     def lra_integral(self, atom_sums=False):
         """The all-space long-range integral T_s (A^3) of every site (rism_lra_integral); with atom_sums also
