@@ -38,7 +38,8 @@ if ROOT not in sys.path:
 METRIC = "grid-pt·site evals/s & init time per solute at stated error vs FP64 direct"
 UNIT = "Gpts·site/s"
 # name -> (index of the seeded workload definition, name of the workload with its sizes)
-WORKLOADS = {"ellipsoid13600": (2, "ellipsoid13600_224x192x160"), "globule2000": (1, "globule2000_128cubed")}
+WORKLOADS = {"ellipsoid13600": (2, "ellipsoid13600_224x192x160"), "globule2000": (1, "globule2000_128cubed"),
+             "sphere200": (0, "sphere200_64cubed")}
 DEFAULT_WORKLOAD = "ellipsoid13600"
 WORKLOAD = WORKLOADS[DEFAULT_WORKLOAD][1]
 
@@ -192,16 +193,17 @@ def run_gpu(args):
     method = R.METHOD_TREECODE if args.method == "treecode" else R.METHOD_DIRECT
     prec = R.PREC_FP32 if args.precision == "fp32" else R.PREC_FP64
     # the autotuner picks the target-batch shape and leaf size during the (untimed) warm-up
-    r = R.from_workload(w, method=method, precision=prec, debug_flags=2, autotune=1)
+    r = R.from_workload(w, method=method, precision=prec, debug_flags=2, autotune=0 if args.no_autotune else 1)
     S, M = w.solvent.nsite, w.grid.npts
     xyz, q, sg, ep = w.solute.xyz, w.solute.q, w.solute.sigma, w.solute.eps
-    out = {k: r.empty_grid() for k in ("u", "c", "h")}
+    fields = ("u", "c", "h") if r.info()["kappa"] > 0 else ("u", "c")  # h needs ionic screening
+    out = {k: r.empty_grid() for k in fields}
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
     st = torch.cuda.current_stream()
 
     def step():
         r.set_solute(xyz, q, sg, ep)
-        return r.init(u=True, c=True, h=True, lj_tail=True, out=out)
+        return r.init(u=True, c=True, h="h" in fields, lj_tail=True, out=out)
 
     for _ in range(args.warmup):
         step()
@@ -239,13 +241,13 @@ def run_gpu(args):
         # end to end: host (pinned) output buffers, device-to-host copies inside the timed region
         hu = torch.empty((S, M), dtype=torch.float64).pin_memory()
         hc = torch.empty((S, M), dtype=torch.float64).pin_memory()
-        hh = torch.empty((S, M), dtype=torch.float64).pin_memory()
+        hh = torch.empty((S, M), dtype=torch.float64).pin_memory() if "h" in fields else None
         tail = np.zeros(S)
         P = lambda t: t.numpy()
 
         def step_host():
             r.set_solute(xyz, q, sg, ep)
-            r.init_host(P(hu), P(hc), P(hh), tail)
+            r.init_host(P(hu), P(hc), None if hh is None else P(hh), tail)
 
         for _ in range(2):
             step_host()
@@ -259,7 +261,7 @@ def run_gpu(args):
         e2e_ms = reduce_max(dist, 1e3 * sum(et) / len(et), "cuda")
         e2e = {"value": job_value(world, S, M, e2e_ms), "unit": UNIT, "ms_per_step": e2e_ms,
                "h2d_bytes_per_step": int(xyz.nbytes + q.nbytes + sg.nbytes + ep.nbytes),
-               "d2h_bytes_per_step": int(3 * S * M * 8 + S * 8)}
+               "d2h_bytes_per_step": int(len(fields) * S * M * 8 + S * 8)}
 
     # accuracy of this step against the FP64 oracle at sampled points (rank 0 only; not timed)
     acc = None
@@ -274,7 +276,7 @@ def run_gpu(args):
         idx = np.union1d(I.sample_indices(M, args.check_points, seed=7), (ijk[:, 2] * ny + ijk[:, 1]) * nx + ijk[:, 0])
         ref = O.fields(O.Problem.from_workload(w), idx=idx)
         acc = {"points": int(idx.size)}
-        for k in ("u", "c", "h"):
+        for k in fields:
             g = out[k].reshape(S, -1)[:, torch.as_tensor(idx, device="cuda")].cpu().numpy()
             acc[k] = float(np.linalg.norm(g - ref[k]) / np.linalg.norm(ref[k]))
             acc[k + "_max_abs_over_max"] = float(np.abs(g - ref[k]).max() / np.abs(ref[k]).max())
@@ -610,6 +612,47 @@ def suite_adjoint(args):
     r.close()
 
 
+def suite_precision(args):
+    """Split of the treecode's error against the FP64 oracle (configs 1 and 2, sampled points and the point
+    nearest each atom): interpolation (treecode vs the FP32 direct sum of the same pairs) and FP32 rounding
+    (FP32 direct sum vs oracle), next to the FP64 direct sum vs oracle."""
+    import numpy as np
+    import torch
+
+    from oracle import oracle as O
+    from paper_2109_09772_gb300 import build as B
+    from paper_2109_09772_gb300 import inputs as I
+    from paper_2109_09772_gb300 import rism as R
+
+    B.build()
+    torch.cuda.set_device(0)
+    for wi in (1, 2):
+        w = I.workload(wi)
+        S, M = w.solvent.nsite, w.grid.npts
+        nx, ny, nz = w.grid.n
+        ijk = np.clip(np.rint((w.solute.xyz - np.asarray(w.grid.origin)) / w.grid.h).astype(np.int64), 0,
+                      np.array([nx - 1, ny - 1, nz - 1]))
+        idx = np.union1d(I.sample_indices(M, 20000, seed=31), (ijk[:, 2] * ny + ijk[:, 1]) * nx + ijk[:, 0])
+        t = torch.as_tensor(idx, device="cuda")
+        ref = O.fields(O.Problem.from_workload(w), idx=idx)
+        got = {}
+        for name, kw in (("direct_fp64", dict(method=R.METHOD_DIRECT, precision=R.PREC_FP64)),
+                         ("direct_fp32", dict(method=R.METHOD_DIRECT, precision=R.PREC_FP32)),
+                         ("treecode_fp32", dict(method=R.METHOD_TREECODE, precision=R.PREC_FP32))):
+            r = R.from_workload(w, **kw)
+            out = r.init()
+            got[name] = {k: out[k].reshape(S, -1)[:, t].cpu().numpy() for k in ("u", "c", "h")}
+            r.close()
+        rel = lambda a, b: float(np.linalg.norm(a - b) / np.linalg.norm(b))
+        res = {"suite": "precision", "workload": w.name, "points": int(idx.size)}
+        for k in ("u", "c", "h"):
+            res[k] = {"direct_fp64_vs_oracle": rel(got["direct_fp64"][k], ref[k]),
+                      "direct_fp32_vs_oracle": rel(got["direct_fp32"][k], ref[k]),
+                      "treecode_vs_direct_fp32": rel(got["treecode_fp32"][k], got["direct_fp32"][k]),
+                      "treecode_vs_oracle": rel(got["treecode_fp32"][k], ref[k])}
+        print(json.dumps(res), flush=True)
+
+
 def suite_kspace(args):
     """Reciprocal-space asymptotics (eqs. (dcf-k)/(tcf-k)) of the 13,600-atom ellipsoid on the half spectrum of
     its 224x192x160 grid: the whole half spectrum, and with the frequency cut-off of Sec. 2.5 at tolerances
@@ -722,14 +765,15 @@ def main():
     ap.add_argument("--no-fp64", action="store_true")
     ap.add_argument("--no-check", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
-    ap.add_argument("--suite", default=None, choices=["pareto", "batched", "adjoint", "mufu", "kspace", "lra"])
+    ap.add_argument("--no-autotune", action="store_true", help="default launch shape (profiling runs)")
+    ap.add_argument("--suite", default=None, choices=["pareto", "batched", "adjoint", "mufu", "kspace", "lra", "precision"])
     ap.add_argument("--reps", type=int, default=3)
     ap.add_argument("--adj-atoms", type=int, default=16)
     args = ap.parse_args()
     _WIDX[0] = _select(args.workload)
     if args.suite:
         {"pareto": suite_pareto, "batched": suite_batched, "adjoint": suite_adjoint, "mufu": suite_mufu,
-         "kspace": suite_kspace, "lra": suite_lra}[args.suite](args)
+         "kspace": suite_kspace, "lra": suite_lra, "precision": suite_precision}[args.suite](args)
         return
     if args.warmup < 3:
         args.warmup = 3
