@@ -502,13 +502,15 @@ def suite_pareto(args):
     cases = [(deg, th, 1) for deg in (4, 6, 8) for th in (0.5, 0.6, 0.7, 0.8)] + [(8, 0.7, 0)]
     for deg, th, tp in cases:
         ms, e, info = run(method=R.METHOD_TREECODE, precision=R.PREC_FP32, degree=deg, theta=th, autotune=1,
-                          target_proxies=tp)
+                          target_proxies=tp, debug_flags=2)
         print(json.dumps({"suite": "pareto", "method": "treecode", "precision": "fp32", "degree": deg,
                           "theta": th, "target_proxies": tp, "ms": ms, "speedup_vs_fp64_direct": ms64 / ms,
                           "gpts_site_s": S * M / (ms * 1e-3) / 1e9, "err": e,
                           "direct_pairs": info["direct_pairs"], "proxy_pairs": info["proxy_pairs"],
                           "cp_pairs": info["cp_pairs"], "near_pairs": info["near_pairs"],
-                          "variant": info["kernel_variant"]}), flush=True)
+                          "box_ms": info["box_ms"], "far_ms": info["far_ms"], "near_ms": info["near_ms"],
+                          "tree_boxes": info["tree_boxes"], "variant": info["kernel_variant"],
+                          "batch": info["batch"]}), flush=True)
 
 
 def suite_batched(args):

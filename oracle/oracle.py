@@ -72,6 +72,10 @@ def _load():
             lib.orc_kspace_bound.argtypes = [D, D, D, D, D, D]
             lib.orc_kspace_kcut.restype = D
             lib.orc_kspace_kcut.argtypes = [D, D, D, D, D, D]
+            lib.orc_taylor_coeffs.restype = C.c_int
+            lib.orc_taylor_coeffs.argtypes = [I32, I32, D, D, D, D, D, P]
+            lib.orc_taylor_eval.restype = C.c_int
+            lib.orc_taylor_eval.argtypes = [I32, I32, P, I64, P, P, D, D, I64, P, P]
             _lib = lib
     return _lib
 
@@ -282,3 +286,30 @@ def kspace(p: Problem, kcut=0.0, idx=None, want=("c", "h"), nthreads: int = 0):
                    p.eta, kappa(p), nx, ny, nz, p.h, _p(org), float(kcut), m, _p(idx), _p(out["c"]), _p(out["h"]),
                    int(nthreads))
     return {k: v for k, v in out.items() if v is not None}
+
+
+TAYLOR_KINDS = {"coulomb": 0, "erf": 1, "yukawa": 2}
+
+
+def taylor_index(k1, k2, k3):
+    """Graded position of multi-index k in the coefficient arrays of taylor_coeffs."""
+    n = k1 + k2 + k3
+    i = n - k1
+    return n * (n + 1) * (n + 2) // 6 + i * (i + 1) // 2 + (i - k2)
+
+
+def taylor_coeffs(kind, p, r, eta=1.0, kappa_=0.0):
+    """a_k = (1/k!) d^k/dy^k phi at x - y = r, |k| <= p, by the paper's recurrences (graded order)."""
+    a = np.empty((p + 1) * (p + 2) * (p + 3) // 6)
+    _load().orc_taylor_coeffs(TAYLOR_KINDS[kind], int(p), float(r[0]), float(r[1]), float(r[2]), float(eta),
+                              float(kappa_), _p(a))
+    return a
+
+
+def taylor_eval(kind, p, center, xyz, q, pts, eta=1.0, kappa_=0.0):
+    """The order-p Taylor approximation about `center` of sum_j q_j phi(x, y_j) at the points."""
+    xyz, q, pts, c = _f64(xyz), _f64(q), _f64(pts), _f64(center)
+    out = np.empty(len(pts))
+    _load().orc_taylor_eval(TAYLOR_KINDS[kind], int(p), _p(c), len(q), _p(xyz), _p(q), float(eta), float(kappa_),
+                            len(pts), _p(pts), _p(out))
+    return out

@@ -22,7 +22,10 @@
  *     (Sec. 2.2), as a double sum over atom pairs of 1D integrals;
  *   - c_s(k), h_s(k): the reciprocal-space asymptotics of eq. (dcf-k) and
  *     eq. (tcf-k) on the grid's reciprocal lattice, with the frequency
- *     cut-off of Sec. 2.5 (its bound eq. (k-space-dcf-err) and root).
+ *     cut-off of Sec. 2.5 (its bound eq. (k-space-dcf-err) and root);
+ *   - the Taylor coefficients of the cluster-particle treecode (Sec. 2.3,
+ *     Sec. 2.4) by the paper's recurrences, and the Taylor approximation of
+ *     one cluster's well-separated particles (eq. (taylor_approximation)).
  *
  * Readings of the paper taken here (the paper is silent or ambiguous):
  *   - Gaussian-unit formulas are multiplied by the Coulomb constant k_e
@@ -650,4 +653,116 @@ double orc_kspace_kcut(double eta, double qmax, double qabs, double beta, double
         if (orc_kspace_bound(mid, eta, qmax, qabs, beta, k_e) > tol) lo = mid; else hi = mid;
     }
     return hi;
+}
+
+/* ----------------------------------------- Taylor cluster-particle expansions */
+
+/*
+ * Taylor coefficients a_k(x, y) = (1/k!) d^k/dy^k phi(x, y), |k| <= p, of the cluster-particle treecode of
+ * Sec. 2.3 (eq. (taylor_coefficients)), by the recurrences of Sec. 2.3.2 and Sec. 2.4, with r = x - y,
+ * rho = |r|, n = |k| >= 1, and a_k = 0 when an index of k is negative:
+ *   1/rho (eq. (coulombrecurrence)):
+ *     a_k = [ (2 - 1/n) sum_i r_i a_{k-e_i} - (1 - 1/n) sum_i a_{k-2e_i} ] / rho^2
+ *   erf(rho/eta)/rho (eq. (dcfrecurrence)), b_k the coefficients of the auxiliary Gaussian
+ *   (eq. (dcfauxiliaryrecurrence)) with b_0 = -(eta/sqrt(pi)) e^{-rho^2/eta^2} (the paper does not print it):
+ *     b_k = 2/(eta^2 n) [ sum_i r_i b_{k-e_i} - sum_i b_{k-2e_i} ]
+ *     a_k = [ (2 - 1/n) sum_i r_i a_{k-e_i} - (1 - 1/n) sum_i a_{k-2e_i} + b_k ] / rho^2
+ *   e^{-kappa rho}/rho (eq. (screenedcoulombrecurrence)), b_k the coefficients of e^{-kappa rho}
+ *   (eq. (screenedcoulombauxiliaryrecurrence), b_0 = e^{-kappa rho}); the auxiliary term enters with
+ *   kappa/n (printed: kappa), which the exact derivatives require:
+ *     b_k = (kappa/n) [ sum_i r_i a_{k-e_i} - sum_i a_{k-2e_i} ]
+ *     a_k = [ (2 - 1/n) sum_i r_i a_{k-e_i} - (1 - 1/n) sum_i a_{k-2e_i}
+ *             + (kappa/n) ( sum_i r_i b_{k-e_i} - sum_i b_{k-2e_i} ) ] / rho^2
+ * Coefficients are stored in graded order: level n = |k| in turn, within a level k1 from n down to 0, then k2
+ * from n - k1 down to 0: index n(n+1)(n+2)/6 + i(i+1)/2 + (i - k2), i = n - k1.
+ */
+static int64_t tay_index(int k1, int k2, int k3)
+{
+    int n = k1 + k2 + k3, i = n - k1;
+    return (int64_t)n * (n + 1) * (n + 2) / 6 + (int64_t)i * (i + 1) / 2 + (i - k2);
+}
+
+static double tay_get(const double* a, int k1, int k2, int k3)
+{
+    if (k1 < 0 || k2 < 0 || k3 < 0) return 0.0;
+    return a[tay_index(k1, k2, k3)];
+}
+
+/* kind 0: 1/rho, 1: erf(rho/eta)/rho, 2: e^{-kappa rho}/rho.  a: C(p+3, 3) coefficients. */
+int orc_taylor_coeffs(int32_t kind, int32_t p, double rx, double ry, double rz, double eta, double kappa, double* a)
+{
+    const double r[3] = {rx, ry, rz};
+    double rho2 = rx * rx + ry * ry + rz * rz, rho = sqrt(rho2);
+    int64_t nc = (int64_t)(p + 1) * (p + 2) * (p + 3) / 6;
+    double* b = (double*)calloc((size_t)nc, sizeof(double));
+    if (!b) return 1;
+    if (kind == 0) a[0] = 1.0 / rho;
+    else if (kind == 1) { a[0] = erf(rho / eta) / rho; b[0] = -(eta / ORC_SQRT_PI) * exp(-rho2 / (eta * eta)); }
+    else { a[0] = exp(-kappa * rho) / rho; b[0] = exp(-kappa * rho); }
+    for (int n = 1; n <= p; ++n) {
+        for (int k1 = n; k1 >= 0; --k1)
+            for (int k2 = n - k1; k2 >= 0; --k2) {
+                int k3 = n - k1 - k2;
+                int k[3] = {k1, k2, k3};
+                double s1a = 0.0, s2a = 0.0, s1b = 0.0, s2b = 0.0;
+                for (int d = 0; d < 3; ++d) {
+                    int m1[3] = {k[0], k[1], k[2]}, m2[3] = {k[0], k[1], k[2]};
+                    m1[d] -= 1;
+                    m2[d] -= 2;
+                    s1a += r[d] * tay_get(a, m1[0], m1[1], m1[2]);
+                    s2a += tay_get(a, m2[0], m2[1], m2[2]);
+                    s1b += r[d] * tay_get(b, m1[0], m1[1], m1[2]);
+                    s2b += tay_get(b, m2[0], m2[1], m2[2]);
+                }
+                int64_t c = tay_index(k1, k2, k3);
+                double v = (2.0 - 1.0 / n) * s1a - (1.0 - 1.0 / n) * s2a;
+                if (kind == 1) {
+                    b[c] = 2.0 / (eta * eta * n) * (s1b - s2b);
+                    v += b[c];
+                } else if (kind == 2) {
+                    v += kappa / n * (s1b - s2b);
+                    b[c] = kappa / n * (s1a - s2a);
+                }
+                a[c] = v / rho2;
+            }
+    }
+    free(b);
+    return 0;
+}
+
+/* The Taylor approximation of eq. (taylor_approximation) for one cluster: the moments
+ * m_k = sum_j q_j (-1)^{|k|} a_k(x_c, y_j) of the listed particles about the centre x_c, evaluated at the m
+ * points x_i as sum_k m_k (x_i - x_c)^k. */
+int orc_taylor_eval(int32_t kind, int32_t p, const double* xc, int64_t n, const double* xyz, const double* q,
+                    double eta, double kappa, int64_t m, const double* pts, double* out)
+{
+    int64_t nc = (int64_t)(p + 1) * (p + 2) * (p + 3) / 6;
+    double* mom = (double*)calloc((size_t)nc, sizeof(double));
+    double* a = (double*)malloc(sizeof(double) * (size_t)nc);
+    if (!mom || !a) { free(mom); free(a); return 1; }
+    for (int64_t j = 0; j < n; ++j) {
+        if (orc_taylor_coeffs(kind, p, xc[0] - xyz[3 * j], xc[1] - xyz[3 * j + 1], xc[2] - xyz[3 * j + 2], eta,
+                              kappa, a)) { free(mom); free(a); return 1; }
+        for (int nn = 0; nn <= p; ++nn)
+            for (int k1 = nn; k1 >= 0; --k1)
+                for (int k2 = nn - k1; k2 >= 0; --k2) {
+                    int64_t c = tay_index(k1, k2, nn - k1 - k2);
+                    mom[c] += q[j] * ((nn & 1) ? -1.0 : 1.0) * a[c];
+                }
+    }
+    for (int64_t i = 0; i < m; ++i) {
+        double t[3] = {pts[3 * i] - xc[0], pts[3 * i + 1] - xc[1], pts[3 * i + 2] - xc[2]};
+        nsum_t acc;
+        ns_init(&acc);
+        for (int nn = 0; nn <= p; ++nn)
+            for (int k1 = nn; k1 >= 0; --k1)
+                for (int k2 = nn - k1; k2 >= 0; --k2) {
+                    int k3 = nn - k1 - k2;
+                    ns_add(&acc, mom[tay_index(k1, k2, k3)] * pow(t[0], k1) * pow(t[1], k2) * pow(t[2], k3));
+                }
+        out[i] = ns_get(&acc);
+    }
+    free(mom);
+    free(a);
+    return 0;
 }

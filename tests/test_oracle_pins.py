@@ -553,3 +553,47 @@ def test_kspace_cutoff_bound_and_root():
         np.testing.assert_array_equal(cut[key][:, keep], ks_full[key][:, keep])
         assert np.all(cut[key][:, ~keep] == 0)
         assert np.abs(ks_full[key][:, ~keep]).max() <= tol
+
+
+# --------------------------------------------------- Taylor recurrences
+@pytest.mark.parametrize("kind", ["coulomb", "erf", "yukawa"])
+def test_taylor_recurrences_against_exact_derivatives(kind):
+    """The recurrence coefficients against (1/k!) d^k/dy^k phi by 30-digit numerical differentiation, for every
+    |k| <= 5 at two separations (a wrong factor, sign, index shift or auxiliary normalization fails)."""
+    mp.mp.dps = 30
+    eta, kap = 1.3, 0.35
+    phi = {"coulomb": lambda r: 1 / r, "erf": lambda r: mp.erf(r / eta) / r,
+           "yukawa": lambda r: mp.e ** (-kap * r) / r}[kind]
+    P = 5
+    for x, y in (((3.1, -1.7, 2.3), (0.4, 0.9, -0.6)), ((0.5, 4.0, -1.0), (-1.2, 0.3, 0.8))):
+        a = O.taylor_coeffs(kind, P, [x[i] - y[i] for i in range(3)], eta, kap)
+        X = [mp.mpf(v) for v in x]
+        for n in range(P + 1):
+            for k1 in range(n + 1):
+                for k2 in range(n - k1 + 1):
+                    k3 = n - k1 - k2
+                    f = lambda y1, y2, y3: phi(mp.sqrt((X[0] - y1) ** 2 + (X[1] - y2) ** 2 + (X[2] - y3) ** 2))
+                    d = mp.diff(f, tuple(mp.mpf(v) for v in y), (k1, k2, k3))
+                    ex = float(d / (mp.factorial(k1) * mp.factorial(k2) * mp.factorial(k3)))
+                    got = a[O.taylor_index(k1, k2, k3)]
+                    assert got == pytest.approx(ex, rel=1e-10, abs=1e-13 * abs(a[0])), (kind, k1, k2, k3)
+
+
+@pytest.mark.parametrize("kind", ["coulomb", "erf", "yukawa"])
+def test_taylor_approximation_converges_to_direct_sum(kind):
+    """Eq. (taylor_approximation) for a cluster of targets and well-separated sources: the error against the
+    direct sum falls geometrically with the order, at the rate of the separation ratio."""
+    rng = np.random.default_rng(3)
+    eta, kap = 1.0, 0.3
+    center = np.array([0.0, 0.0, 0.0])
+    pts = rng.uniform(-1.0, 1.0, size=(40, 3))            # targets within r = sqrt(3) of the centre
+    src = rng.uniform(-1.5, 1.5, size=(25, 3)) + np.array([9.0, -4.0, 3.0])
+    q = rng.normal(0, 1, 25)
+    d = np.linalg.norm(pts[:, None, :] - src[None, :, :], axis=2)
+    from scipy.special import erf
+    phi = {"coulomb": 1 / d, "erf": erf(d / eta) / d, "yukawa": np.exp(-kap * d) / d}[kind]
+    direct = phi @ q
+    errs = [np.abs(O.taylor_eval(kind, p, center, src, q, pts, eta, kap) - direct).max() / np.abs(direct).max()
+            for p in (2, 4, 6, 8, 10)]
+    assert all(b < a for a, b in zip(errs, errs[1:])), errs
+    assert errs[-1] < 1e-8 and errs[0] / errs[-1] > 1e4, errs
