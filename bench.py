@@ -655,6 +655,50 @@ def suite_precision(args):
         print(json.dumps(res), flush=True)
 
 
+def suite_taylor(args):
+    """The two far-field approximation families on the same target boxes, acceptance test and near field:
+    barycentric-Lagrange Chebyshev proxies and the paper's Taylor moments (Sec. 2.3), degrees / orders 4..10 at
+    theta 0.5 and 0.7, on the 2,000-atom globule and the 13,600-atom ellipsoid: time per initialization (and
+    the box-level part) against the error at sampled points."""
+    import numpy as np
+    import torch
+
+    from oracle import oracle as O
+    from paper_2109_09772_gb300 import build as B
+    from paper_2109_09772_gb300 import inputs as I
+    from paper_2109_09772_gb300 import rism as R
+
+    B.build()
+    torch.cuda.set_device(0)
+    for wi in (1, 2):
+        w = I.workload(wi)
+        S = w.solvent.nsite
+        idx = I.sample_indices(w.grid.npts, 3000, seed=2)
+        ref = O.fields(O.Problem.from_workload(w), idx=idx)
+        t = torch.as_tensor(idx, device="cuda")
+        for approx in (R.APPROX_BARYCENTRIC, R.APPROX_TAYLOR):
+            for th in (0.5, 0.7):
+                for p in (4, 6, 8, 10):
+                    r = R.from_workload(w, method=R.METHOD_TREECODE, precision=R.PREC_FP32, degree=p, theta=th,
+                                        approx=approx, debug_flags=2)
+                    out = r.init()
+                    torch.cuda.synchronize()
+                    sol = (w.solute.xyz, w.solute.q, w.solute.sigma, w.solute.eps)
+
+                    def step():
+                        r.set_solute(*sol)
+                        r.init(out=out)
+
+                    ms = _events_ms(step, reps=args.reps)
+                    inf = r.info()
+                    err = {k: _rel(out[k].reshape(S, -1)[:, t].cpu().numpy(), ref[k]) for k in ("c", "h")}
+                    print(json.dumps({"suite": "taylor", "workload": w.name,
+                                      "approx": "taylor" if approx == R.APPROX_TAYLOR else "barycentric",
+                                      "theta": th, "order": p, "ms": ms, "box_ms": inf["box_ms"],
+                                      "err_rel_l2": err}), flush=True)
+                    r.close()
+
+
 def suite_kspace(args):
     """Reciprocal-space asymptotics (eqs. (dcf-k)/(tcf-k)) of the 13,600-atom ellipsoid on the half spectrum of
     its 224x192x160 grid: the whole half spectrum, and with the frequency cut-off of Sec. 2.5 at tolerances
@@ -768,14 +812,16 @@ def main():
     ap.add_argument("--no-check", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-autotune", action="store_true", help="default launch shape (profiling runs)")
-    ap.add_argument("--suite", default=None, choices=["pareto", "batched", "adjoint", "mufu", "kspace", "lra", "precision"])
+    ap.add_argument("--suite", default=None, choices=["pareto", "batched", "adjoint", "mufu", "kspace", "lra", "precision",
+                                                      "taylor"])
     ap.add_argument("--reps", type=int, default=3)
     ap.add_argument("--adj-atoms", type=int, default=16)
     args = ap.parse_args()
     _WIDX[0] = _select(args.workload)
     if args.suite:
         {"pareto": suite_pareto, "batched": suite_batched, "adjoint": suite_adjoint, "mufu": suite_mufu,
-         "kspace": suite_kspace, "lra": suite_lra, "precision": suite_precision}[args.suite](args)
+         "kspace": suite_kspace, "lra": suite_lra, "precision": suite_precision,
+         "taylor": suite_taylor}[args.suite](args)
         return
     if args.warmup < 3:
         args.warmup = 3

@@ -77,6 +77,11 @@ enum { RISM_PREC_FP64 = 0, RISM_PREC_FP32 = 1 };
 /* LJ truncation (Sec. 2.6): none; one cut-off for all pairs; per-pair
  * cut-off from a tolerance |u_LJ(rc)| = lj_tol. */
 enum { RISM_LJ_NONE = 0, RISM_LJ_RCUT = 1, RISM_LJ_TOL = 2 };
+/* Far-field approximation of the treecode's target boxes: barycentric-Lagrange
+ * Chebyshev proxies (interpolated onto the grid), or the paper's Taylor
+ * expansion about the box centre with coefficients from the recurrences of
+ * Sec. 2.3.2 and Sec. 2.4 (evaluated at every grid point of the box). */
+enum { RISM_APPROX_BARYCENTRIC = 0, RISM_APPROX_TAYLOR = 1 };
 
 #define RISM_MAX_SITES 8
 
@@ -118,6 +123,10 @@ typedef struct {
                                box is summed at the box's proxies and reaches its grid points by
                                interpolation (cluster-particle form, the paper's orientation of Sec. 2.3.1);
                                0 = only the atom clusters take proxies (particle-cluster form). */
+    int32_t approx;     /* RISM_APPROX_*; default BARYCENTRIC.  TAYLOR (treecode with target boxes only):
+                           the boxes take the order-`degree` Taylor moments of their accepted atoms (1/d and
+                           e^{-kappa d}/d recurrences, Sec. 2.3, eq. (taylor_approximation)) instead of
+                           Chebyshev proxies; the reverse mode then runs its far part directly. */
 } rism_options;
 
 typedef struct {

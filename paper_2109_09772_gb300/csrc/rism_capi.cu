@@ -220,6 +220,7 @@ void rism_default_options(rism_options* o) {
     o->autotune = 0;
     o->wait_limit = 1LL << 24;
     o->target_proxies = 1;
+    o->approx = RISM_APPROX_BARYCENTRIC;
 }
 
 rism_status rism_grid_create(const rism_grid_desc* grid, const rism_options* opts, void* stream, rism_ctx** out) {

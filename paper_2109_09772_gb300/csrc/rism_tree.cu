@@ -107,6 +107,8 @@ struct TBoxes {
     int nx, ny, nz;
     int deg, P3;
     int enabled;
+    int approx;                // RISM_APPROX_BARYCENTRIC: Chebyshev proxies; RISM_APPROX_TAYLOR: Taylor moments
+    float kapg;                // kappa in 1/grid units (Taylor moments of e^{-kappa d}/d)
     float ck[kMaxDegree + 1];  // cos(k pi / n), exact 1, 0, -1 where they occur
 };
 
@@ -3016,6 +3018,8 @@ rism_status tree_reserve(TreeState* s, const DevTables& t, const GridD& g, const
     tb.deg = deg;
     tb.P3 = P3;
     tb.enabled = o.target_proxies != 0 && n > 0;
+    tb.approx = o.approx;
+    tb.kapg = (float)(ph.kappa * g.h);
     for (int k = 0; k <= kMaxDegree; ++k)  // cos(k pi / n) as sin(pi (n - 2k) / (2n)): exact 0 at k = n/2
         tb.ck[k] = k <= deg ? (float)std::sin(3.14159265358979323846 * (deg - 2 * k) / (2.0 * deg)) : 0.f;
     const int nmax = std::max(g.nx, std::max(g.ny, g.nz));
@@ -3126,12 +3130,371 @@ CPArgs make_cp(TreeState* s) {
     return c;
 }
 
+// ---- Taylor moments of the target boxes (the paper's cluster-particle approximation, Sec. 2.3)
+// A box with accepted atoms y_j takes the moments M_k = sum_j q_j (-1)^{|k|} a_k(c, y_j), |k| <= p, of the
+// order-p Taylor expansion about its centre c (eq. (taylor_approximation)), with the coefficients a_k of
+// Sec. 2.3.2 / Sec. 2.4 from their recurrences: 1/d (eq. (coulombrecurrence)) for Phi1 and e^{-kappa d}/d (eq.
+// (screenedcoulombrecurrence) with its auxiliary e^{-kappa d}, eq. (screenedcoulombauxiliaryrecurrence), the
+// auxiliary term taken with kappa/|k|) for Phik.  Coordinates are scaled by the box radius s: with r = (c - y)/s
+// and t = (x - c)/s the field is (1/s) sum_k M_k t^k and kappa becomes kappa s, so every coefficient is O(1).
+// The recurrence runs one warp per atom, the lanes over the coefficients of one order |k| at a time (graded
+// order: |k|, then k1 descending, then k2 descending); the moments are stored in lexicographic order (k1, k2,
+// k3 ascending) for the nested Horner evaluation of k_tay_down.
+constexpr int kTayWarps = 8;
+
+__host__ __device__ constexpr int tay_nc(int p) { return (p + 1) * (p + 2) * (p + 3) / 6; }
+__device__ __forceinline__ int tay_graded(int k1, int k2, int k3) {
+    const int n = k1 + k2 + k3, i = n - k1;
+    return n * (n + 1) * (n + 2) / 6 + i * (i + 1) / 2 + (i - k2);
+}
+// position of (k1, k2, 0) in the lexicographic order of the multi-indices with |k| <= p
+__device__ __forceinline__ int tay_lexoff(int p, int k1, int k2) {
+    int o = 0;
+    for (int a = 0; a < k1; ++a) o += (p - a + 1) * (p - a + 2) / 2;
+    for (int b = 0; b < k2; ++b) o += p - k1 - b + 1;
+    return o;
+}
+
+template <int P, bool DH>
+__global__ void __launch_bounds__(kTayWarps * 32 + 32) k_tay_eval(EvalArgs a, CPArgs c) {
+    constexpr int NC = tay_nc(P), J = (NC + 31) / 32;
+    __shared__ Ring<1, false> r;
+    __shared__ int s_e, s_off, s_len, s_nch;
+    __shared__ char4 kk[NC];                        // multi-index of each graded position
+    __shared__ short2 lk[NC][3];                    // graded positions of k - e_d and k - 2 e_d (-1: none)
+    // dynamic: per warp the 1/d, e^{-kappa d}/d and e^{-kappa d} (auxiliary) coefficients of its current atom,
+    // then per warp its moments for the fixed-order CTA sum (tay_eval_smem bytes)
+    extern __shared__ __align__(16) unsigned char tay_raw[];
+    float2* red = reinterpret_cast<float2*>(tay_raw);                         // [kTayWarps][NC]
+    float* sa = reinterpret_cast<float*>(red + kTayWarps * NC);              // [kTayWarps][NC]
+    float* sA = sa + kTayWarps * NC;                                          // [kTayWarps][NC]
+    float* sB = sA + kTayWarps * NC;                                          // [kTayWarps][NC]
+    const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
+    if (tid == 0) r.inited = 0;
+    if (a.meta->overflow) return;
+    const int box = blockIdx.x, chunk = blockIdx.y;
+    const TBox T = tbox_flat(c.tb, box);
+    if (!T.proxied) return;
+    const int cnt = c.cp_cnt[box];
+    if (cnt == 0) {
+        if (chunk == 0) {
+            float2* out = c.tpot + (int64_t)box * c.tb.P3;
+            for (int k = tid; k < NC; k += blockDim.x) out[k] = make_float2(0.f, 0.f);
+            if (tid == 0) {
+                c.tflag[box] = 0;
+                c.tnch[box] = 1;
+            }
+        }
+        return;
+    }
+    const int2* ent = c.cp_ent + (int64_t)box * c.cp_cap;
+    if (tid == 0) {
+        int tot = 0;
+        for (int e = 0; e < cnt; ++e) tot += ent[e].y;
+        const int nch = min(kCPChunks, max(1, tot / kCPChunkMin));
+        s_nch = nch;
+        if (chunk < nch) {
+            const int a0 = (int)((long long)tot * chunk / nch), a1 = (int)((long long)tot * (chunk + 1) / nch);
+            int e = 0, acc = 0;
+            while (e < cnt && acc + ent[e].y <= a0) acc += ent[e++].y;
+            s_e = e;
+            s_off = a0 - acc;
+            s_len = a1 - a0;
+        }
+    }
+    for (int q = tid; q < NC; q += blockDim.x) {
+        int n = 0;
+        while (tay_nc(n) <= q) ++n;                  // graded level of position q
+        const int t = q - (n > 0 ? tay_nc(n - 1) : 0);
+        int i = 0;
+        while ((i + 1) * (i + 2) / 2 <= t) ++i;
+        const int k2 = i - (t - i * (i + 1) / 2);
+        const int ks[3] = {n - i, k2, i - k2};
+        kk[q] = make_char4((char)ks[0], (char)k2, (char)ks[2], (char)n);
+        for (int d = 0; d < 3; ++d) {
+            int m1[3] = {ks[0], ks[1], ks[2]}, m2[3] = {ks[0], ks[1], ks[2]};
+            m1[d] -= 1;
+            m2[d] -= 2;
+            lk[q][d] = make_short2(m1[d] >= 0 ? (short)tay_graded(m1[0], m1[1], m1[2]) : (short)-1,
+                                   m2[d] >= 0 ? (short)tay_graded(m2[0], m2[1], m2[2]) : (short)-1);
+        }
+    }
+    __syncthreads();
+    const int nch = s_nch;
+    if (chunk >= nch) return;
+    if (chunk == 0 && tid == 0) {
+        c.tflag[box] = 1;
+        c.tnch[box] = nch;
+    }
+    float2* out = chunk == 0 ? c.tpot + (int64_t)box * c.tb.P3
+                             : c.tpart + ((int64_t)box * (kCPChunks - 1) + chunk - 1) * c.tb.P3;
+    // box centre (exact half-integers) and radius; the scaled screening constant
+    const float cx = (float)T.lo[0] + 0.5f * (float)(T.ext[0] - 1), cy = (float)T.lo[1] + 0.5f * (float)(T.ext[1] - 1),
+                cz = (float)T.lo[2] + 0.5f * (float)(T.ext[2] - 1);
+    const float sc = T.r, isc = 1.f / sc, kh = c.tb.kapg * sc;
+    float m1h[J], m1l[J], mkh[J], mkl[J];
+#pragma unroll
+    for (int j = 0; j < J; ++j) m1h[j] = m1l[j] = mkh[j] = mkl[j] = 0.f;
+    Cursor cur;
+    __syncthreads();
+    if (tid == kTayWarps * 32) {
+        cur.e = box * c.cp_cap + s_e;
+        cur.e_end = box * c.cp_cap + cnt;
+        cur.off = s_off;
+        cur.left = s_len;
+        cur.produced = 0;
+        cur.done = false;
+        for (int st = 0; st < kStages; ++st) cur.last_phase[st] = -1;
+        ring_init(r, kTayWarps);
+    }
+    __syncthreads();
+    float* A1 = sa + w * NC;
+    float* Ak = sA + w * NC;
+    float* Bk = sB + w * NC;
+    const int rr = run_ring<1, false, kTayWarps>(
+        r, cur, c.cp_ent, a.srcf, nullptr, a, [&](int slot, int n) {
+            float p1[J], pk[J];
+#pragma unroll
+            for (int j = 0; j < J; ++j) p1[j] = pk[j] = 0.f;
+            for (int at = w; at < n; at += kTayWarps) {
+                const SrcF y = r.src[slot][at];
+                // r = (c - y) / s from the float-float source position (one rounding per component)
+                const float rx = ((cx - y.xh) - y.xl) * isc, ry = ((cy - y.yh) - y.yl) * isc,
+                            rz = ((cz - y.zh) - y.zl) * isc;
+                const float rho2 = fmaf(rx, rx, fmaf(ry, ry, rz * rz));
+                const float irho2 = 1.f / rho2, irho = rsqrtf(rho2), rho = rho2 * irho;
+                if (lane == 0) {
+                    A1[0] = irho;
+                    if (DH) {
+                        const float e = __expf(-kh * rho);
+                        Bk[0] = e;
+                        Ak[0] = e * irho;
+                    }
+                }
+                __syncwarp();
+                const float rv[3] = {rx, ry, rz};
+                for (int lv = 1; lv <= P; ++lv) {
+                    const int q0 = tay_nc(lv - 1), q1 = tay_nc(lv);
+                    const float inv = 1.f / (float)lv, f1 = 2.f - inv, f2 = 1.f - inv, kn = kh * inv;
+                    for (int q = q0 + lane; q < q1; q += 32) {
+                        float s1 = 0.f, s2 = 0.f, t1 = 0.f, t2 = 0.f, u1 = 0.f, u2 = 0.f;
+#pragma unroll
+                        for (int d = 0; d < 3; ++d) {
+                            const short2 l = lk[q][d];
+                            if (l.x >= 0) {
+                                s1 = fmaf(rv[d], A1[l.x], s1);
+                                if (DH) {
+                                    t1 = fmaf(rv[d], Ak[l.x], t1);
+                                    u1 = fmaf(rv[d], Bk[l.x], u1);
+                                }
+                            }
+                            if (l.y >= 0) {
+                                s2 += A1[l.y];
+                                if (DH) {
+                                    t2 += Ak[l.y];
+                                    u2 += Bk[l.y];
+                                }
+                            }
+                        }
+                        A1[q] = (f1 * s1 - f2 * s2) * irho2;
+                        if (DH) {
+                            Ak[q] = (f1 * t1 - f2 * t2 + kn * (u1 - u2)) * irho2;
+                            Bk[q] = kn * (t1 - t2);
+                        }
+                    }
+                    __syncwarp();
+                }
+                // moments: q (-1)^{|k|} a_k, each lane its positions lane + 32 j
+#pragma unroll
+                for (int j = 0; j < J; ++j) {
+                    const int q = lane + 32 * j;
+                    if (q < NC) {
+                        const float sq = (kk[q].w & 1) ? -y.q : y.q;
+                        p1[j] = fmaf(sq, A1[q], p1[j]);
+                        if (DH) pk[j] = fmaf(sq, Ak[q], pk[j]);
+                    }
+                }
+                __syncwarp();
+            }
+#pragma unroll
+            for (int j = 0; j < J; ++j) {
+                ff_add(m1h[j], m1l[j], p1[j]);
+                if (DH) ff_add(mkh[j], mkl[j], pk[j]);
+            }
+        },
+        [](int) {});
+    // every thread reaches this barrier (an aborted ring leaves uniformly, after it)
+    if (__syncthreads_or(rr == kRingAbort)) return;
+    if (w < kTayWarps) {
+#pragma unroll
+        for (int j = 0; j < J; ++j) {
+            const int q = lane + 32 * j;
+            if (q < NC) red[w * NC + q] = make_float2(m1h[j] + m1l[j], mkh[j] + mkl[j]);
+        }
+    }
+    __syncthreads();
+    for (int q = tid; q < NC; q += blockDim.x) {
+        float2 v = make_float2(0.f, 0.f);
+        for (int ww = 0; ww < kTayWarps; ++ww) {
+            v.x += red[ww * NC + q].x;
+            v.y += red[ww * NC + q].y;
+        }
+        const char4 k = kk[q];
+        out[tay_lexoff(P, k.x, k.y) + k.z] = v;
+    }
+}
+
+// Taylor field onto the grid: one CTA per level-0 box region; every box that contains it and holds moments
+// adds (1/s) sum_k M_k t^k at the region's points, evaluated by nested Horner (z innermost: a thread takes 8
+// points of one (x, y) column per pass).  Written to the far-field buffer as the far kernel's starting value.
+template <int P>
+__global__ void __launch_bounds__(256) k_tay_down(CPArgs c, float4* far, const TreeMeta* meta) {
+    constexpr int NC = tay_nc(P), M = kTB0, NZP = 8;
+    extern __shared__ __align__(16) unsigned char sm_raw[];
+    float2* mom = reinterpret_cast<float2*>(sm_raw);  // [L][NC]
+    __shared__ int lexoff[(P + 1) * (P + 1)];
+    __shared__ int lev[kMaxTL];
+    __shared__ float cen[kMaxTL][4];
+    __shared__ int nlev;
+    if (meta->overflow) return;
+    const TBoxes& tb = c.tb;
+    const int bi = blockIdx.x;
+    const int ib = bi % tb.nbx[0], jb = (bi / tb.nbx[0]) % tb.nby[0], kb = bi / (tb.nbx[0] * tb.nby[0]);
+    const TBox R = tbox_at(tb, 0, ib, jb, kb);
+    const int tid = threadIdx.x;
+    if (tid == 0) {
+        int k = 0;
+        for (int l = 0; l < tb.L; ++l) {
+            const TBox A = tbox_at(tb, l, ib >> l, jb >> l, kb >> l);
+            if (A.proxied && c.tflag[tbox_index(tb, l, A.ib, A.jb, A.kb)]) {
+                lev[k] = tbox_index(tb, l, A.ib, A.jb, A.kb);
+                cen[k][0] = A.c[0];
+                cen[k][1] = A.c[1];
+                cen[k][2] = A.c[2];
+                cen[k][3] = A.r;
+                ++k;
+            }
+        }
+        nlev = k;
+    }
+    for (int q = tid; q < (P + 1) * (P + 1); q += blockDim.x) {
+        const int k1 = q / (P + 1), k2 = q % (P + 1);
+        lexoff[q] = k1 + k2 <= P ? tay_lexoff(P, k1, k2) : 0;
+    }
+    __syncthreads();
+    const int nl = nlev;
+    for (int q = tid; q < nl * NC; q += blockDim.x) {
+        const int k = q / NC;
+        mom[q] = c.tpot[(int64_t)lev[k] * tb.P3 + (q - k * NC)];
+    }
+    __syncthreads();
+    const int m0 = R.ext[0], m1 = R.ext[1], m2 = R.ext[2];
+    const int ix = tid % M, iy = tid / M;  // the thread's (x, y) column
+    for (int z0 = 0; z0 < M; z0 += NZP) {
+        float2 v[NZP];
+#pragma unroll
+        for (int pz = 0; pz < NZP; ++pz) v[pz] = make_float2(0.f, 0.f);
+        for (int k = 0; k < nl; ++k) {
+            const float is = 1.f / cen[k][3];
+            const float tx = ((float)(R.lo[0] + ix) - cen[k][0]) * is, ty = ((float)(R.lo[1] + iy) - cen[k][1]) * is;
+            float tz[NZP];
+#pragma unroll
+            for (int pz = 0; pz < NZP; ++pz) tz[pz] = ((float)(R.lo[2] + z0 + pz) - cen[k][2]) * is;
+            const float2* Mk = mom + k * NC;
+            float2 V[NZP];
+#pragma unroll
+            for (int pz = 0; pz < NZP; ++pz) V[pz] = make_float2(0.f, 0.f);
+            for (int k1 = P; k1 >= 0; --k1) {
+                float2 W[NZP];
+#pragma unroll
+                for (int pz = 0; pz < NZP; ++pz) W[pz] = make_float2(0.f, 0.f);
+                for (int k2 = P - k1; k2 >= 0; --k2) {
+                    const float2* base = Mk + lexoff[k1 * (P + 1) + k2];
+                    float2 Q[NZP];
+#pragma unroll
+                    for (int pz = 0; pz < NZP; ++pz) Q[pz] = make_float2(0.f, 0.f);
+                    for (int k3 = P - k1 - k2; k3 >= 0; --k3) {
+                        const float2 m = base[k3];
+#pragma unroll
+                        for (int pz = 0; pz < NZP; ++pz) {
+                            Q[pz].x = fmaf(Q[pz].x, tz[pz], m.x);
+                            Q[pz].y = fmaf(Q[pz].y, tz[pz], m.y);
+                        }
+                    }
+#pragma unroll
+                    for (int pz = 0; pz < NZP; ++pz) {
+                        W[pz].x = fmaf(W[pz].x, ty, Q[pz].x);
+                        W[pz].y = fmaf(W[pz].y, ty, Q[pz].y);
+                    }
+                }
+#pragma unroll
+                for (int pz = 0; pz < NZP; ++pz) {
+                    V[pz].x = fmaf(V[pz].x, tx, W[pz].x);
+                    V[pz].y = fmaf(V[pz].y, tx, W[pz].y);
+                }
+            }
+#pragma unroll
+            for (int pz = 0; pz < NZP; ++pz) {
+                v[pz].x = fmaf(V[pz].x, is, v[pz].x);
+                v[pz].y = fmaf(V[pz].y, is, v[pz].y);
+            }
+        }
+#pragma unroll
+        for (int pz = 0; pz < NZP; ++pz) {
+            const int iz = z0 + pz;
+            if (ix < m0 && iy < m1 && iz < m2)
+                far[far_index(tb.nx, tb.ny, R.lo[0] + ix, R.lo[1] + iy, R.lo[2] + iz)] =
+                    make_float4(v[pz].x, 0.f, v[pz].y, 0.f);
+        }
+    }
+}
+
+template <int P>
+void launch_taylor(const TBoxes& tb, const EvalArgs& a, const CPArgs& c, float4* far, const TreeMeta* meta, bool dh,
+                   cudaStream_t st) {
+    const dim3 grid(tb.nbox, kCPChunks);
+    const size_t se = (size_t)kTayWarps * tay_nc(P) * (sizeof(float2) + 3 * sizeof(float));
+    if (dh) {
+        cudaFuncSetAttribute(k_tay_eval<P, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)se);
+        k_tay_eval<P, true><<<grid, kTayWarps * 32 + 32, se, st>>>(a, c);
+    } else {
+        cudaFuncSetAttribute(k_tay_eval<P, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)se);
+        k_tay_eval<P, false><<<grid, kTayWarps * 32 + 32, se, st>>>(a, c);
+    }
+    k_cp_reduce<<<tb.nbox, 256, 0, st>>>(c, meta);
+    const size_t sm = sizeof(float2) * (size_t)tb.L * tay_nc(P);
+    cudaFuncSetAttribute(k_tay_down<P>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    k_tay_down<P><<<tb.nbx[0] * tb.nby[0] * tb.nbz[0], 256, sm, st>>>(c, far, meta);
+}
+
+void launch_taylor_deg(const TBoxes& tb, const EvalArgs& a, const CPArgs& c, float4* far, const TreeMeta* meta,
+                       bool dh, cudaStream_t st) {
+    switch (tb.deg) {
+        case 1: return launch_taylor<1>(tb, a, c, far, meta, dh, st);
+        case 2: return launch_taylor<2>(tb, a, c, far, meta, dh, st);
+        case 3: return launch_taylor<3>(tb, a, c, far, meta, dh, st);
+        case 4: return launch_taylor<4>(tb, a, c, far, meta, dh, st);
+        case 5: return launch_taylor<5>(tb, a, c, far, meta, dh, st);
+        case 6: return launch_taylor<6>(tb, a, c, far, meta, dh, st);
+        case 7: return launch_taylor<7>(tb, a, c, far, meta, dh, st);
+        case 8: return launch_taylor<8>(tb, a, c, far, meta, dh, st);
+        case 9: return launch_taylor<9>(tb, a, c, far, meta, dh, st);
+        case 10: return launch_taylor<10>(tb, a, c, far, meta, dh, st);
+        case 11: return launch_taylor<11>(tb, a, c, far, meta, dh, st);
+        default: return launch_taylor<12>(tb, a, c, far, meta, dh, st);
+    }
+}
+
 // Box-level far field (no allocation, no host wait): proxies of every target box, the downward pass and the
 // interpolation onto the far-field buffer.  Returns the number of launches.
 int cp_enqueue(TreeState* s, const EvalArgs& a, bool dh, cudaStream_t st) {
     const TBoxes& tb = s->tb;
     if (!tb.enabled) return 0;
     const CPArgs c = make_cp(s);
+    if (tb.approx == RISM_APPROX_TAYLOR) {
+        launch_taylor_deg(tb, a, c, s->far, s->meta, dh, st);
+        return 3;
+    }
     const int n1 = tb.deg + 1;
     const int npass = (n1 * n1 * ((n1 + kCPP - 1) / kCPP) + kCPThreads - 1) / kCPThreads;
     const dim3 grid(tb.nbox, kCPChunks, npass);
@@ -3299,9 +3662,9 @@ std::string problem_class(const DevTables& t, const GridD& g, const Phys& ph, co
     cudaGetDeviceProperties(&p, dev);
     auto lg = [](double v) { return (int)std::lround(std::log2(v > 1 ? v : 1)); };
     char buf[400];
-    std::snprintf(buf, sizeof buf, "%s|sm%d|S%d|n2^%d|m2^%d|p%d|th%d|lj%d|k%d", p.name, p.multiProcessorCount,
+    std::snprintf(buf, sizeof buf, "%s|sm%d|S%d|n2^%d|m2^%d|p%d|th%d|lj%d|k%d|ap%d", p.name, p.multiProcessorCount,
                   t.smax, lg((double)t.n), lg((double)g.nx * g.ny * g.nz), o.degree, (int)std::lround(o.theta * 100),
-                  o.lj_mode, ph.kappa > 0.0);
+                  o.lj_mode, ph.kappa > 0.0, o.approx);
     for (char* c = buf; *c; ++c)
         if (*c == '"') *c = '\'';
     return buf;
@@ -4370,7 +4733,9 @@ rism_status tree_adjoint_far(TreeState* s, const DevTables& t, const GridD& g, c
     used = false;
     const TBoxes& tb = s->tb;
     const int n = (int)t.n;
-    if (!tb.enabled || !s->prepared || n == 0) return RISM_OK;
+    // the transposed far field uses the Chebyshev proxies; with Taylor moments the caller's direct reverse
+    // far part runs instead
+    if (!tb.enabled || tb.approx != RISM_APPROX_BARYCENTRIC || !s->prepared || n == 0) return RISM_OK;
     if (!s->adj) s->adj = new AdjTree();
     AdjTree& A = *s->adj;
     cudaError_t e;

@@ -60,6 +60,11 @@ inline const char* check_options(const rism_options& o, bool* unsupported) {
     if (!std::isfinite(o.kappa)) return "kappa must be finite";
     if (!(o.r_short >= 0.0 && std::isfinite(o.r_short))) return "r_short must be finite and >= 0";
     if (o.wait_limit < 1) return "wait_limit must be >= 1";
+    if (o.approx != RISM_APPROX_BARYCENTRIC && o.approx != RISM_APPROX_TAYLOR) return "approx";
+    if (o.approx == RISM_APPROX_TAYLOR && (o.method != RISM_METHOD_TREECODE || o.target_proxies == 0)) {
+        *unsupported = true;
+        return "Taylor moments are a far-field form of the treecode's target boxes (method TREECODE, target_proxies 1)";
+    }
     return nullptr;
 }
 

@@ -20,6 +20,7 @@ OK, E_INVALID, E_STATE, E_NOMEM, E_CUDA, E_TIMEOUT, E_UNSUPPORTED = range(7)
 METHOD_DIRECT, METHOD_TREECODE = 0, 1
 PREC_FP64, PREC_FP32 = 0, 1
 LJ_NONE, LJ_RCUT, LJ_TOL = 0, 1, 2
+APPROX_BARYCENTRIC, APPROX_TAYLOR = 0, 1
 MAX_SITES = 8
 
 _STATUS = {0: "RISM_OK", 1: "RISM_E_INVALID", 2: "RISM_E_STATE", 3: "RISM_E_NOMEM", 4: "RISM_E_CUDA",
@@ -43,7 +44,7 @@ class Options(C.Structure):
                 ("lj_tol", C.c_double), ("eta", C.c_double), ("T", C.c_double), ("eps_r", C.c_double),
                 ("kappa", C.c_double), ("k_e", C.c_double), ("k_B", C.c_double), ("r_short", C.c_double),
                 ("autotune", C.c_int32), ("wait_limit", C.c_int64),
-                ("debug_flags", C.c_int32), ("target_proxies", C.c_int32)]
+                ("debug_flags", C.c_int32), ("target_proxies", C.c_int32), ("approx", C.c_int32)]
 
 
 class Info(C.Structure):
