@@ -52,8 +52,22 @@ namespace rism {
 namespace {
 
 constexpr int kSortThreads = 1024;
+// The radix histograms hold one count per (digit, warp), stored digit-major with a pitch of 33 so that the 32
+// lanes of a warp, which update the entries of one warp column under different digits, fall in different banks
+// (a pitch of 32 would put a whole warp's updates in one bank).
+constexpr int kHistPitch = kSortThreads / 32 + 1;
+constexpr int kHistInts = 256 * kHistPitch;
+static_assert(kHistInts % 2 == 0, "the 64-bit sort keys after the histograms stay 8-byte aligned");
 constexpr int kSortSmem = 4096;  // atoms sorted in shared memory (64-bit keys, sorted codes, positions: 96 KB)
 constexpr int kNodeSmem = 1024;  // octree nodes kept in shared memory during the build (56 KB)
+// Above kSortSmem atoms the keys are radix-sorted: up to kCodeSmem atoms in shared memory, where the sorted codes
+// (64 KB) then stay for the octree's searches beside up to kNodeSmemL nodes (112 KB); beyond that through global
+// memory.
+constexpr int kCodeSmem = 16384;
+constexpr int kNodeSmemL = 2048;
+// Above kSortSmem atoms the leaf boxes gather the sorted positions into shared memory this many atoms at a time.
+constexpr int kPosChunk = 8192;
+static_assert(kPosChunk % kSortThreads == 0, "whole rounds of the block");
 constexpr int kMortonBits = 10;          // per axis
 constexpr int kMaxLevel = kMortonBits;   // octree depth limit
 constexpr int kChunk = 16;               // atoms per upward-pass work item
@@ -290,6 +304,9 @@ struct BuildArgs {
     LJf* ljs2;             // out: the same as {A, A, -B, -B} (two-wide operands of the near field)
 };
 
+// Shared-memory slot of the radix histogram entry at (digit, warp)-order position L.
+__device__ __forceinline__ int hist_at(int L) { return (L >> 5) * kHistPitch + (L & 31); }
+
 __device__ int block_exclusive_scan(int v, int* tmp /* >= 32 ints */, int& total) {
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
     int x = v;
@@ -319,8 +336,8 @@ __global__ void __launch_bounds__(kSortThreads) k_sort_build(BuildArgs a, uint32
                                                              int* items, int* prox_nodes, int* prox_items,
                                                              TreeMeta* meta) {
     extern __shared__ int sh[];
-    int* hist = sh;                     // [256][32]
-    int* tmp = sh + 256 * 32;           // [64]
+    int* hist = sh;                     // [256][kHistPitch]: radix histograms, (digit, warp) order
+    int* tmp = sh + kHistInts;          // [64]
     const int n = a.n;
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     constexpr int NW = kSortThreads / 32;
@@ -328,9 +345,9 @@ __global__ void __launch_bounds__(kSortThreads) k_sort_build(BuildArgs a, uint32
     const int s0 = min(n, w * seg), s1 = min(n, s0 + seg);
     // up to kSortSmem atoms: a bitonic sort in shared memory of the 64-bit keys (code << 32 | index), unique,
     // so the order is that of the stable radix sort; the sorted codes stay there for the octree's searches.
-    // Above that: the stable LSD radix sort through global memory.
+    // Above that: the stable LSD radix sort, in shared memory up to kCodeSmem atoms, else through global memory.
     const bool in_smem = n <= kSortSmem;
-    unsigned long long* sk = reinterpret_cast<unsigned long long*>(sh + 256 * 32 + 64);  // [kSortSmem]
+    unsigned long long* sk = reinterpret_cast<unsigned long long*>(sh + kHistInts + 64);  // [kSortSmem]
     uint32_t* sc = reinterpret_cast<uint32_t*>(sk + kSortSmem);                          // [kSortSmem]
     if (in_smem) {
         // Bucket sort on the top 10 bits of the code, one bucket per thread: count, scan, scatter, then each
@@ -411,28 +428,90 @@ __global__ void __launch_bounds__(kSortThreads) k_sort_build(BuildArgs a, uint32
             idx[i] = (uint32_t)v;
         }
         __syncthreads();
+    } else if (n <= kCodeSmem) {
+        // mid-sized solutes: the same stable LSD radix sort with the keys and values in shared memory.  Each
+        // warp holds its segment (<= 16 keys per lane) in registers through a pass, so the scatter of a pass
+        // writes in place (every key of the pass has been read before the first barrier); the scatter of
+        // single words to global memory would cost a memory transaction each.
+        constexpr int KPL = kCodeSmem / kSortThreads;  // 16
+        uint32_t* skm = reinterpret_cast<uint32_t*>(sh + kHistInts + 64);  // [kCodeSmem] keys
+        uint32_t* svm = skm + kCodeSmem;                                     // [kCodeSmem] values
+        for (int pass = 0; pass < 4; ++pass) {
+            const int shift = 8 * pass;
+            const uint32_t* kin = pass == 0 ? code : skm;
+            const uint32_t* vin = pass == 0 ? idx : svm;
+            uint32_t kr[KPL], vr[KPL];
+#pragma unroll
+            for (int j = 0; j < KPL; ++j) {
+                const int i = s0 + 32 * j + lane;
+                const bool act = i < s1;
+                kr[j] = act ? kin[i] : 0u;
+                vr[j] = act ? vin[i] : 0u;
+            }
+            for (int k = threadIdx.x; k < kHistInts; k += blockDim.x) hist[k] = 0;
+            __syncthreads();
+#pragma unroll
+            for (int j = 0; j < KPL; ++j)
+                if (s0 + 32 * j + lane < s1) atomicAdd(&hist[((kr[j] >> shift) & 255u) * kHistPitch + w], 1);
+            __syncthreads();
+            {
+                int loc[8], sum = 0;
+                for (int k = 0; k < 8; ++k) {
+                    loc[k] = hist[hist_at(threadIdx.x * 8 + k)];
+                    sum += loc[k];
+                }
+                int total;
+                int base = block_exclusive_scan(sum, tmp, total);
+                for (int k = 0; k < 8; ++k) {
+                    hist[hist_at(threadIdx.x * 8 + k)] = base;
+                    base += loc[k];
+                }
+            }
+            __syncthreads();
+#pragma unroll
+            for (int j = 0; j < KPL; ++j) {
+                const bool act = s0 + 32 * j + lane < s1;
+                const uint32_t d = act ? ((kr[j] >> shift) & 255u) : 256u + lane;  // inactive lanes never match
+                const unsigned peers = __match_any_sync(0xffffffffu, d);
+                const int rank = __popc(peers & ((1u << lane) - 1u));
+                const int base = act ? hist[d * kHistPitch + w] : 0;
+                if (act) {
+                    skm[base + rank] = kr[j];
+                    svm[base + rank] = vr[j];
+                }
+                __syncwarp();
+                if (act && rank == 0) hist[d * kHistPitch + w] = base + __popc(peers);
+                __syncwarp();
+            }
+            __syncthreads();
+        }
+        for (int i = threadIdx.x; i < n; i += blockDim.x) {
+            code[i] = skm[i];
+            idx[i] = svm[i];
+        }
+        __syncthreads();
     } else {
         uint32_t *kin = code, *vin = idx, *kout = code2, *vout = idx2;
         for (int pass = 0; pass < 4; ++pass) {
             const int shift = 8 * pass;
-            for (int k = threadIdx.x; k < 256 * NW; k += blockDim.x) hist[k] = 0;
+            for (int k = threadIdx.x; k < kHistInts; k += blockDim.x) hist[k] = 0;
             __syncthreads();
             for (int b = s0; b < s1; b += 32) {
                 int i = b + lane;
-                if (i < s1) atomicAdd(&hist[((kin[i] >> shift) & 255u) * NW + w], 1);
+                if (i < s1) atomicAdd(&hist[((kin[i] >> shift) & 255u) * kHistPitch + w], 1);
             }
             __syncthreads();
             // exclusive scan of hist in (digit, warp) order: 8192 entries, 8 per thread
             {
                 int loc[8], sum = 0;
                 for (int k = 0; k < 8; ++k) {
-                    loc[k] = hist[threadIdx.x * 8 + k];
+                    loc[k] = hist[hist_at(threadIdx.x * 8 + k)];
                     sum += loc[k];
                 }
                 int total;
                 int base = block_exclusive_scan(sum, tmp, total);
                 for (int k = 0; k < 8; ++k) {
-                    hist[threadIdx.x * 8 + k] = base;
+                    hist[hist_at(threadIdx.x * 8 + k)] = base;
                     base += loc[k];
                 }
             }
@@ -444,13 +523,13 @@ __global__ void __launch_bounds__(kSortThreads) k_sort_build(BuildArgs a, uint32
                 uint32_t d = act ? ((key >> shift) & 255u) : 256u + lane;  // inactive lanes never match
                 unsigned peers = __match_any_sync(0xffffffffu, d);
                 int rank = __popc(peers & ((1u << lane) - 1u));
-                int base = act ? hist[d * NW + w] : 0;
+                int base = act ? hist[d * kHistPitch + w] : 0;
                 if (act) {
                     kout[base + rank] = key;
                     vout[base + rank] = val;
                 }
                 __syncwarp();
-                if (act && rank == 0) hist[d * NW + w] = base + __popc(peers);
+                if (act && rank == 0) hist[d * kHistPitch + w] = base + __popc(peers);
                 __syncwarp();
             }
             __syncthreads();
@@ -459,7 +538,10 @@ __global__ void __launch_bounds__(kSortThreads) k_sort_build(BuildArgs a, uint32
         }
         // after 4 passes the sorted data is back in code/idx
     }
-    const uint32_t* scode = in_smem ? sc : code;  // sorted codes for the searches below
+    // a mid-sized solute keeps its sorted codes in shared memory for the searches of the octree build
+    const bool mid = !in_smem && n <= kCodeSmem;
+    uint32_t* scm = reinterpret_cast<uint32_t*>(sh + kHistInts + 64);  // [kCodeSmem] (mid-sized solutes)
+    const uint32_t* scode = in_smem ? sc : (mid ? scm : code);  // sorted codes for the searches below
     // small solutes keep the sorted high-part positions and (while they fit) the nodes in shared memory, so
     // the level-by-level phases below do not wait on global memory between levels
     float* spos = reinterpret_cast<float*>(sc + kSortSmem);  // [kSortSmem][3]
@@ -476,8 +558,9 @@ __global__ void __launch_bounds__(kSortThreads) k_sort_build(BuildArgs a, uint32
     // ---- octree, level by level: nodes [lvl_begin, lvl_end) at the current level, built in shared memory
     // while they fit in kNodeSmem, else (built again) in global memory
     __shared__ int s_nnodes, s_lvl_begin, s_lvl_end, s_overflow, s_lvl[kMaxLevel + 2], s_nlvl;
-    Node* store = in_smem ? snodes : nodes;
-    int cap = in_smem ? min(kNodeSmem, a.max_nodes) : a.max_nodes;
+    Node* snodes_mid = reinterpret_cast<Node*>(scm + kCodeSmem);  // [kNodeSmemL] (mid-sized solutes)
+    Node* store = in_smem ? snodes : (mid ? snodes_mid : nodes);
+    int cap = in_smem ? min(kNodeSmem, a.max_nodes) : (mid ? min(kNodeSmemL, a.max_nodes) : a.max_nodes);
     for (;;) {
         if (threadIdx.x == 0) {
             store[0] = Node{0, n, -1, 0, 0, -1, 0, 0, {0, 0, 0}, {0, 0, 0}};
@@ -627,33 +710,82 @@ __global__ void __launch_bounds__(kSortThreads) k_sort_build(BuildArgs a, uint32
     }
     __syncthreads();
     if (s_overflow) return;
-    // ---- tight bounding boxes (grid units), bottom-up: a leaf from its atoms, an
-    // internal node as the union of its children; one warp per node, level by level.
+    // ---- tight bounding boxes (grid units), reduced in FP32 over the high parts of the float-float positions
+    // (within 1e-5 grid units of the exact box; the box only steers the acceptance test and the proxy
+    // placement).  First every leaf from its atoms, one thread per leaf, over the sorted positions in shared
+    // memory: all of them for small solutes, else gathered chunk by chunk (kPosChunk atoms, every load of a
+    // chunk in flight together) into the space that the sort and the searches no longer need.  Then
+    // bottom-up, level by level, each internal node as the union of its children, one warp per node.
+    if (in_smem) {
+        for (int nid = threadIdx.x; nid < nn; nid += blockDim.x) {
+            const Node nd = store[nid];
+            if (nd.first_child >= 0) continue;
+            float lo[3] = {INFINITY, INFINITY, INFINITY}, hi[3] = {-INFINITY, -INFINITY, -INFINITY};
+            for (int i = nd.begin; i < nd.end; ++i)
+                for (int d = 0; d < 3; ++d) {
+                    lo[d] = fminf(lo[d], spos[3 * i + d]);
+                    hi[d] = fmaxf(hi[d], spos[3 * i + d]);
+                }
+            for (int d = 0; d < 3; ++d) {
+                store[nid].lo[d] = lo[d];
+                store[nid].hi[d] = hi[d];
+            }
+        }
+    } else {
+        float* cpos = reinterpret_cast<float*>(sh);  // [kPosChunk][3]: the histograms and the sorted codes
+        constexpr int U = kPosChunk / kSortThreads;
+        for (int c0 = 0; c0 < n; c0 += kPosChunk) {
+            const int c1 = min(n, c0 + kPosChunk);
+            __syncthreads();  // the previous chunk's readers are done
+            uint32_t j[U];
+#pragma unroll
+            for (int u = 0; u < U; ++u) {
+                const int i = c0 + threadIdx.x + u * kSortThreads;
+                j[u] = i < c1 ? idx[i] : 0u;
+            }
+            float4 f[U];
+#pragma unroll
+            for (int u = 0; u < U; ++u)
+                if (c0 + threadIdx.x + u * kSortThreads < c1) f[u] = *reinterpret_cast<const float4*>(&a.srcf[j[u]].xh);
+#pragma unroll
+            for (int u = 0; u < U; ++u) {
+                const int r = threadIdx.x + u * kSortThreads;
+                if (c0 + r < c1) {
+                    cpos[3 * r] = f[u].x;
+                    cpos[3 * r + 1] = f[u].y;
+                    cpos[3 * r + 2] = f[u].z;
+                }
+            }
+            __syncthreads();
+            for (int nid = threadIdx.x; nid < nn; nid += blockDim.x) {
+                const Node& nd = store[nid];
+                const int b0 = max(nd.begin, c0), b1 = min(nd.end, c1);
+                if (nd.first_child >= 0 || b0 >= b1) continue;
+                float lo[3] = {INFINITY, INFINITY, INFINITY}, hi[3] = {-INFINITY, -INFINITY, -INFINITY};
+                if (b0 > nd.begin)  // the leaf began in an earlier chunk
+                    for (int d = 0; d < 3; ++d) {
+                        lo[d] = nd.lo[d];
+                        hi[d] = nd.hi[d];
+                    }
+                for (int i = b0 - c0; i < b1 - c0; ++i)
+                    for (int d = 0; d < 3; ++d) {
+                        lo[d] = fminf(lo[d], cpos[3 * i + d]);
+                        hi[d] = fmaxf(hi[d], cpos[3 * i + d]);
+                    }
+                for (int d = 0; d < 3; ++d) {
+                    store[nid].lo[d] = lo[d];
+                    store[nid].hi[d] = hi[d];
+                }
+            }
+        }
+    }
+    __syncthreads();
     for (int lv = s_nlvl - 1; lv >= 0; --lv) {
         for (int nid = s_lvl[lv] + w; nid < s_lvl[lv + 1]; nid += NW) {
-            // reduced in FP32 over the high parts of the float-float positions (within 1e-5 grid units of
-            // the exact box; the box only steers the acceptance test and the proxy placement)
             const Node nd = store[nid];
+            if (nd.first_child < 0) continue;
             float lo[3] = {INFINITY, INFINITY, INFINITY}, hi[3] = {-INFINITY, -INFINITY, -INFINITY};
-            if (nd.first_child < 0) {
-                for (int i = nd.begin + lane; i < nd.end; i += 32) {
-                    float v[3];
-                    if (in_smem) {
-                        v[0] = spos[3 * i];
-                        v[1] = spos[3 * i + 1];
-                        v[2] = spos[3 * i + 2];
-                    } else {
-                        const SrcF g = a.srcf[idx[i]];
-                        v[0] = g.xh;
-                        v[1] = g.yh;
-                        v[2] = g.zh;
-                    }
-                    for (int d = 0; d < 3; ++d) {
-                        lo[d] = fminf(lo[d], v[d]);
-                        hi[d] = fmaxf(hi[d], v[d]);
-                    }
-                }
-            } else if (lane < nd.nchild) {
+            if (lane < nd.nchild) {
                 const Node ch = store[nd.first_child + lane];
                 for (int d = 0; d < 3; ++d) {
                     lo[d] = ch.lo[d];
@@ -3522,10 +3654,12 @@ rism_status tree_enqueue(TreeState* s, const DevTables& t, const GridD& g, const
         // the FP64 sorted positions feed only the source proxies' upward pass (off with target boxes)
         BuildArgs ba{n, s->leaf, P3, s->max_nodes, s->max_prox, s->max_items, t.geo, t.srcf, t.ljf, t.smax, g,
                      1.0 / g.h, s->tb.enabled ? nullptr : s->src, s->srcf, s->ljs, s->ljs2};
-        const size_t shb = (256 * 32 + 64) * sizeof(int) +
-                           (t.n <= kSortSmem ? kSortSmem * (sizeof(unsigned long long) + 4 * sizeof(uint32_t)) +
-                                                   kNodeSmem * sizeof(Node)
-                                             : 0);
+        const size_t shb = t.n <= kSortSmem ? (kHistInts + 64) * sizeof(int) +
+                                                  kSortSmem * (sizeof(unsigned long long) + 4 * sizeof(uint32_t)) +
+                                                  kNodeSmem * sizeof(Node)
+                           : t.n <= kCodeSmem ? (kHistInts + 64) * sizeof(int) + kCodeSmem * sizeof(uint32_t) +
+                                                    std::max(kCodeSmem * sizeof(uint32_t), kNodeSmemL * sizeof(Node))
+                                              : std::max((kHistInts + 64) * sizeof(int), 3 * kPosChunk * sizeof(float));
         cudaFuncSetAttribute(k_sort_build, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shb);
         k_sort_build<<<1, kSortThreads, shb, st>>>(ba, s->code, s->idx, s->code2, s->idx2, s->nodes, s->items,
                                                    s->prox_nodes, s->prox_items, s->meta);

@@ -304,3 +304,33 @@ def test_each_launch_shape(R, shape):
     g = run(R, w, debug_flags=(shape + 1) << 4)
     assert g["info"]["kernel_variant"] == shape
     check_fields({k: g[k][:, idx] for k in ("u", "c", "h")}, ref, ("u", "c", "h"), TREE_TOL, label=f"shape{shape}")
+
+
+def test_build_mid_sized_solute_paths(R):
+    """Between 4,096 and 16,384 atoms the build radix-sorts in shared memory and keeps the sorted codes and up to
+    2,048 nodes there: 6,000 atoms with leaf 32 build there, leaf 2 overflows the node store and builds again in
+    global memory; above 16,384 atoms (17,000) the sort and the nodes go through global memory, and the leaf boxes
+    gather the positions in three chunks of 8,192 atoms.  Each against the oracle, and the first two agree with
+    each other."""
+    base = I.small_workload(n_atoms=40, n=(112, 104, 96), h=0.5, seed=3, lj_rcut=6.0)
+    from dataclasses import replace
+
+    mid = I.sphere_solute(6000, I.globule_radius(6000), 2.0, seed=21)
+    w = replace(base, solute=mid)
+    idx = np.union1d(I.sample_indices(w.grid.npts, 2000, seed=9), nearest_points(w.grid, mid.xyz))
+    ref = O.fields(O.Problem.from_workload(w), idx=idx)
+    roomy = run(R, w, leaf=32)
+    many = run(R, w, leaf=2)
+    assert roomy["info"]["tree_nodes"] <= 2048 < many["info"]["tree_nodes"]
+    for g, label in ((roomy, "6000 leaf32"), (many, "6000 leaf2")):
+        check_fields({k: g[k][:, idx] for k in ("u", "c", "h")}, ref, ("u", "c", "h"), TREE_TOL, w.grid, mid.xyz,
+                     idx=idx, label=label)
+    for k in ("u", "c", "h"):
+        assert rel_l2(many[k], roomy[k]) < TREE_TOL
+    big = I.sphere_solute(17000, I.globule_radius(17000), -3.0, seed=22)
+    w = replace(I.small_workload(n_atoms=40, n=(144, 144, 144), h=0.5, seed=3, lj_rcut=6.0), solute=big)
+    idx = np.union1d(I.sample_indices(w.grid.npts, 1500, seed=10), nearest_points(w.grid, big.xyz)[:500])
+    ref = O.fields(O.Problem.from_workload(w), idx=idx)
+    g = run(R, w)
+    check_fields({k: g[k][:, idx] for k in ("u", "c", "h")}, ref, ("u", "c", "h"), TREE_TOL, w.grid, big.xyz,
+                 idx=idx, label="17000")
