@@ -65,9 +65,6 @@ constexpr int kNodeSmem = 1024;  // octree nodes kept in shared memory during th
 // memory.
 constexpr int kCodeSmem = 16384;
 constexpr int kNodeSmemL = 2048;
-// Above kSortSmem atoms the leaf boxes gather the sorted positions into shared memory this many atoms at a time.
-constexpr int kPosChunk = 8192;
-static_assert(kPosChunk % kSortThreads == 0, "whole rounds of the block");
 constexpr int kMortonBits = 10;          // per axis
 constexpr int kMaxLevel = kMortonBits;   // octree depth limit
 constexpr int kChunk = 16;               // atoms per upward-pass work item
@@ -304,6 +301,20 @@ struct BuildArgs {
     LJf* ljs2;             // out: the same as {A, A, -B, -B} (two-wide operands of the near field)
 };
 
+// Lanes of the warp whose 8-bit digit equals this lane's, among the lanes with act set: eight ballots, one per
+// bit (a match instruction costs far more when a warp holds many distinct digits).  Every lane of the warp calls
+// it; the result of a lane with act unset is unused.
+__device__ __forceinline__ unsigned warp_digit_peers(uint32_t d, bool act) {
+    unsigned m = __ballot_sync(0xffffffffu, act);
+#pragma unroll
+    for (int b = 0; b < 8; ++b) {
+        const bool bit = (d >> b) & 1u;
+        const unsigned bb = __ballot_sync(0xffffffffu, bit);
+        m &= bit ? bb : ~bb;
+    }
+    return m;
+}
+
 // Shared-memory slot of the radix histogram entry at (digit, warp)-order position L.
 __device__ __forceinline__ int hist_at(int L) { return (L >> 5) * kHistPitch + (L & 31); }
 
@@ -471,8 +482,8 @@ __global__ void __launch_bounds__(kSortThreads) k_sort_build(BuildArgs a, uint32
 #pragma unroll
             for (int j = 0; j < KPL; ++j) {
                 const bool act = s0 + 32 * j + lane < s1;
-                const uint32_t d = act ? ((kr[j] >> shift) & 255u) : 256u + lane;  // inactive lanes never match
-                const unsigned peers = __match_any_sync(0xffffffffu, d);
+                const uint32_t d = (kr[j] >> shift) & 255u;
+                const unsigned peers = warp_digit_peers(d, act);
                 const int rank = __popc(peers & ((1u << lane) - 1u));
                 const int base = act ? hist[d * kHistPitch + w] : 0;
                 if (act) {
@@ -520,8 +531,8 @@ __global__ void __launch_bounds__(kSortThreads) k_sort_build(BuildArgs a, uint32
                 int i = b + lane;
                 bool act = i < s1;
                 uint32_t key = act ? kin[i] : 0u, val = act ? vin[i] : 0u;
-                uint32_t d = act ? ((key >> shift) & 255u) : 256u + lane;  // inactive lanes never match
-                unsigned peers = __match_any_sync(0xffffffffu, d);
+                const uint32_t d = (key >> shift) & 255u;
+                const unsigned peers = warp_digit_peers(d, act);
                 int rank = __popc(peers & ((1u << lane) - 1u));
                 int base = act ? hist[d * kHistPitch + w] : 0;
                 if (act) {
@@ -710,12 +721,12 @@ __global__ void __launch_bounds__(kSortThreads) k_sort_build(BuildArgs a, uint32
     }
     __syncthreads();
     if (s_overflow) return;
-    // ---- tight bounding boxes (grid units), reduced in FP32 over the high parts of the float-float positions
-    // (within 1e-5 grid units of the exact box; the box only steers the acceptance test and the proxy
-    // placement).  First every leaf from its atoms, one thread per leaf, over the sorted positions in shared
-    // memory: all of them for small solutes, else gathered chunk by chunk (kPosChunk atoms, every load of a
-    // chunk in flight together) into the space that the sort and the searches no longer need.  Then
-    // bottom-up, level by level, each internal node as the union of its children, one warp per node.
+    // ---- tight bounding boxes (grid units) of a small solute, reduced in FP32 over the high parts of the
+    // float-float positions (within 1e-5 grid units of the exact box; the box only steers the acceptance test
+    // and the proxy placement): every leaf from its atoms' positions in shared memory, one thread per leaf, then
+    // bottom-up, level by level, each internal node as the union of its children, one warp per node.  Larger
+    // solutes take their boxes from k_node_boxes, over the sorted positions that k_gather_cells lays out (a
+    // gather of every atom's position through this one SM would wait on memory for longer than the whole build).
     if (in_smem) {
         for (int nid = threadIdx.x; nid < nn; nid += blockDim.x) {
             const Node nd = store[nid];
@@ -731,82 +742,89 @@ __global__ void __launch_bounds__(kSortThreads) k_sort_build(BuildArgs a, uint32
                 store[nid].hi[d] = hi[d];
             }
         }
-    } else {
-        float* cpos = reinterpret_cast<float*>(sh);  // [kPosChunk][3]: the histograms and the sorted codes
-        constexpr int U = kPosChunk / kSortThreads;
-        for (int c0 = 0; c0 < n; c0 += kPosChunk) {
-            const int c1 = min(n, c0 + kPosChunk);
-            __syncthreads();  // the previous chunk's readers are done
-            uint32_t j[U];
-#pragma unroll
-            for (int u = 0; u < U; ++u) {
-                const int i = c0 + threadIdx.x + u * kSortThreads;
-                j[u] = i < c1 ? idx[i] : 0u;
-            }
-            float4 f[U];
-#pragma unroll
-            for (int u = 0; u < U; ++u)
-                if (c0 + threadIdx.x + u * kSortThreads < c1) f[u] = *reinterpret_cast<const float4*>(&a.srcf[j[u]].xh);
-#pragma unroll
-            for (int u = 0; u < U; ++u) {
-                const int r = threadIdx.x + u * kSortThreads;
-                if (c0 + r < c1) {
-                    cpos[3 * r] = f[u].x;
-                    cpos[3 * r + 1] = f[u].y;
-                    cpos[3 * r + 2] = f[u].z;
+        __syncthreads();
+        for (int lv = s_nlvl - 1; lv >= 0; --lv) {
+            for (int nid = s_lvl[lv] + w; nid < s_lvl[lv + 1]; nid += NW) {
+                const Node nd = store[nid];
+                if (nd.first_child < 0) continue;
+                float lo[3] = {INFINITY, INFINITY, INFINITY}, hi[3] = {-INFINITY, -INFINITY, -INFINITY};
+                if (lane < nd.nchild) {
+                    const Node ch = store[nd.first_child + lane];
+                    for (int d = 0; d < 3; ++d) {
+                        lo[d] = ch.lo[d];
+                        hi[d] = ch.hi[d];
+                    }
                 }
+                for (int d = 0; d < 3; ++d)
+                    for (int o = 16; o > 0; o >>= 1) {
+                        lo[d] = fminf(lo[d], __shfl_xor_sync(0xffffffffu, lo[d], o));
+                        hi[d] = fmaxf(hi[d], __shfl_xor_sync(0xffffffffu, hi[d], o));
+                    }
+                if (lane == 0)
+                    for (int d = 0; d < 3; ++d) {
+                        store[nid].lo[d] = lo[d];
+                        store[nid].hi[d] = hi[d];
+                    }
             }
             __syncthreads();
-            for (int nid = threadIdx.x; nid < nn; nid += blockDim.x) {
-                const Node& nd = store[nid];
-                const int b0 = max(nd.begin, c0), b1 = min(nd.end, c1);
-                if (nd.first_child >= 0 || b0 >= b1) continue;
-                float lo[3] = {INFINITY, INFINITY, INFINITY}, hi[3] = {-INFINITY, -INFINITY, -INFINITY};
-                if (b0 > nd.begin)  // the leaf began in an earlier chunk
-                    for (int d = 0; d < 3; ++d) {
-                        lo[d] = nd.lo[d];
-                        hi[d] = nd.hi[d];
-                    }
-                for (int i = b0 - c0; i < b1 - c0; ++i)
-                    for (int d = 0; d < 3; ++d) {
-                        lo[d] = fminf(lo[d], cpos[3 * i + d]);
-                        hi[d] = fmaxf(hi[d], cpos[3 * i + d]);
-                    }
-                for (int d = 0; d < 3; ++d) {
-                    store[nid].lo[d] = lo[d];
-                    store[nid].hi[d] = hi[d];
-                }
-            }
         }
     }
-    __syncthreads();
-    for (int lv = s_nlvl - 1; lv >= 0; --lv) {
-        for (int nid = s_lvl[lv] + w; nid < s_lvl[lv + 1]; nid += NW) {
-            const Node nd = store[nid];
-            if (nd.first_child < 0) continue;
-            float lo[3] = {INFINITY, INFINITY, INFINITY}, hi[3] = {-INFINITY, -INFINITY, -INFINITY};
-            if (lane < nd.nchild) {
-                const Node ch = store[nd.first_child + lane];
-                for (int d = 0; d < 3; ++d) {
-                    lo[d] = ch.lo[d];
-                    hi[d] = ch.hi[d];
-                }
+    // the nodes kept in shared memory go out word by word (consecutive threads, consecutive words)
+    if (store != nodes) {
+        static_assert(sizeof(Node) % sizeof(int) == 0, "nodes copy as words");
+        constexpr int kW = sizeof(Node) / sizeof(int);
+        const int* sw = reinterpret_cast<const int*>(store);
+        int* gw = reinterpret_cast<int*>(nodes);
+        for (int k = threadIdx.x; k < nn * kW; k += blockDim.x) gw[k] = sw[k];
+    }
+}
+
+// Tight bounding boxes (grid units) of the nodes of a solute above kSortSmem atoms: one CTA per node over its
+// atoms' sorted float-float positions (high parts, within 1e-5 grid units of the exact box), reduced in FP32;
+// min and max are exact, so the boxes do not depend on the order of the reduction.  The root's CTA reads every
+// atom once; the other nodes run beside it on the other SMs.
+constexpr int kBoxThreads = 512;
+__global__ void __launch_bounds__(kBoxThreads) k_node_boxes(const TreeMeta* __restrict__ meta, Node* nodes,
+                                                            const SrcF* __restrict__ ssrcf) {
+    __shared__ float red[kBoxThreads / 32][6];
+    if (meta->build_overflow) return;
+    const int nn = meta->nnodes;
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    for (int nid = blockIdx.x; nid < nn; nid += gridDim.x) {
+        const int b = nodes[nid].begin, e = nodes[nid].end;
+        float lo[3] = {INFINITY, INFINITY, INFINITY}, hi[3] = {-INFINITY, -INFINITY, -INFINITY};
+#pragma unroll 4
+        for (int i = b + threadIdx.x; i < e; i += kBoxThreads) {
+            const float4 f = __ldg(reinterpret_cast<const float4*>(&ssrcf[i].xh));
+            lo[0] = fminf(lo[0], f.x);
+            lo[1] = fminf(lo[1], f.y);
+            lo[2] = fminf(lo[2], f.z);
+            hi[0] = fmaxf(hi[0], f.x);
+            hi[1] = fmaxf(hi[1], f.y);
+            hi[2] = fmaxf(hi[2], f.z);
+        }
+        for (int d = 0; d < 3; ++d)
+            for (int o = 16; o > 0; o >>= 1) {
+                lo[d] = fminf(lo[d], __shfl_xor_sync(0xffffffffu, lo[d], o));
+                hi[d] = fmaxf(hi[d], __shfl_xor_sync(0xffffffffu, hi[d], o));
             }
-            for (int d = 0; d < 3; ++d)
-                for (int o = 16; o > 0; o >>= 1) {
-                    lo[d] = fminf(lo[d], __shfl_xor_sync(0xffffffffu, lo[d], o));
-                    hi[d] = fmaxf(hi[d], __shfl_xor_sync(0xffffffffu, hi[d], o));
-                }
-            if (lane == 0)
-                for (int d = 0; d < 3; ++d) {
-                    store[nid].lo[d] = lo[d];
-                    store[nid].hi[d] = hi[d];
-                }
+        if (lane == 0)
+            for (int d = 0; d < 3; ++d) {
+                red[w][d] = lo[d];
+                red[w][3 + d] = hi[d];
+            }
+        __syncthreads();
+        if (threadIdx.x < 6) {
+            const int d = threadIdx.x;
+            float v = red[0][d];
+            for (int k = 1; k < kBoxThreads / 32; ++k) v = d < 3 ? fminf(v, red[k][d]) : fmaxf(v, red[k][d]);
+            if (d < 3)
+                nodes[nid].lo[d] = v;
+            else
+                nodes[nid].hi[d - 3] = v;
         }
         __syncthreads();
     }
-    if (store != nodes)
-        for (int k = threadIdx.x; k < nn; k += blockDim.x) nodes[k] = store[k];
 }
 
 // After the sort, in one launch: the sorted copies of the sources (FP64 grid units when the source proxies need
@@ -3659,12 +3677,16 @@ rism_status tree_enqueue(TreeState* s, const DevTables& t, const GridD& g, const
                                                   kNodeSmem * sizeof(Node)
                            : t.n <= kCodeSmem ? (kHistInts + 64) * sizeof(int) + kCodeSmem * sizeof(uint32_t) +
                                                     std::max(kCodeSmem * sizeof(uint32_t), kNodeSmemL * sizeof(Node))
-                                              : std::max((kHistInts + 64) * sizeof(int), 3 * kPosChunk * sizeof(float));
+                                              : (kHistInts + 64) * sizeof(int);
         cudaFuncSetAttribute(k_sort_build, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shb);
         k_sort_build<<<1, kSortThreads, shb, st>>>(ba, s->code, s->idx, s->code2, s->idx2, s->nodes, s->items,
                                                    s->prox_nodes, s->prox_items, s->meta);
         k_gather_cells<<<1024, 256, 0, st>>>(ba, s->idx, s->meta, s->code, s->cell_start);
         s->launches += 4;
+        if (t.n > kSortSmem) {
+            k_node_boxes<<<std::min(s->max_nodes, 4 * sm_count()), kBoxThreads, 0, st>>>(s->meta, s->nodes, s->srcf);
+            ++s->launches;
+        }
         if (!s->tb.enabled) {
             // source proxies: only the batch-level traversal uses them (with target boxes on, the box level
             // accepts every cluster a batch would)
