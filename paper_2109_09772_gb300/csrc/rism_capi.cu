@@ -298,8 +298,15 @@ rism_status rism_set_solvent(rism_ctx* c, int32_t nsite, const double* q, const 
 
 namespace {
 
+// z slabs of the treecode's near field when the outputs go to host memory: the copy of a slab's planes (at the
+// host link's rate) overlaps the evaluation of the slabs after it.
+constexpr int kOutSlabs = 4;
+static_assert(kOutSlabs <= kOutSlabsMax, "slab events of the tree state");
+
 // Device staging -> caller's host buffers for the outputs staged in device memory: each grid on its own stream
-// (forked from and joined back to the context's stream), so the copies overlap on several copy engines.
+// (forked from and joined back to the context's stream), so the copies overlap on several copy engines.  When
+// the treecode's near field ran in z slabs, each slab's planes of every site are copied as soon as the slab's
+// event has fired, while the later slabs are still being evaluated; otherwise the whole grids after the step.
 rism_status copy_outputs(rism_ctx* c, double* const (&user)[3], double* const (&dev)[3], const bool (&staged)[3],
                          size_t bytes) {
     cudaError_t e = cudaSuccess;
@@ -313,12 +320,31 @@ rism_status copy_outputs(rism_ctx* c, double* const (&user)[3], double* const (&
         if (e == cudaSuccess) e = cudaEventCreateWithFlags(&c->cp_fork, cudaEventDisableTiming);
         if (e != cudaSuccess) return cuda_fail(c, e, "copy streams");
     }
-    if ((e = cudaEventRecord(c->cp_fork, c->st)) != cudaSuccess) return cuda_fail(c, e, "copying result to host");
+    int z[kOutSlabsMax][2];
+    cudaEvent_t sev[kOutSlabsMax];
+    const int ns = (c->o.method == RISM_METHOD_TREECODE && c->tree) ? tree_slabs(c->tree, c->gd, z, sev) : 0;
+    const size_t plane = (size_t)c->g.nx * c->g.ny, M = plane * c->g.nz;
+    if (ns == 0 && (e = cudaEventRecord(c->cp_fork, c->st)) != cudaSuccess)
+        return cuda_fail(c, e, "copying result to host");
     for (int k = 0; k < 3; ++k) {
         if (!staged[k]) continue;
-        if ((e = cudaStreamWaitEvent(c->cp_st[k], c->cp_fork, 0)) != cudaSuccess ||
-            (e = cudaMemcpyAsync(user[k], dev[k], bytes, cudaMemcpyDeviceToHost, c->cp_st[k])) != cudaSuccess ||
-            (e = cudaEventRecord(c->cp_join[k], c->cp_st[k])) != cudaSuccess ||
+        cudaStream_t cs = c->cp_st[k];
+        if (ns == 0) {
+            if ((e = cudaStreamWaitEvent(cs, c->cp_fork, 0)) != cudaSuccess ||
+                (e = cudaMemcpyAsync(user[k], dev[k], bytes, cudaMemcpyDeviceToHost, cs)) != cudaSuccess)
+                return cuda_fail(c, e, "copying result to host");
+        } else {
+            for (int j = 0; j < ns; ++j) {
+                if ((e = cudaStreamWaitEvent(cs, sev[j], 0)) != cudaSuccess) return cuda_fail(c, e, "slab copy");
+                if (z[j][1] <= z[j][0]) continue;
+                const size_t off = (size_t)z[j][0] * plane, cnt = (size_t)(z[j][1] - z[j][0]) * plane;
+                for (int s = 0; s < c->S; ++s)
+                    if ((e = cudaMemcpyAsync(user[k] + s * M + off, dev[k] + s * M + off, cnt * sizeof(double),
+                                             cudaMemcpyDeviceToHost, cs)) != cudaSuccess)
+                        return cuda_fail(c, e, "slab copy");
+            }
+        }
+        if ((e = cudaEventRecord(c->cp_join[k], cs)) != cudaSuccess ||
             (e = cudaStreamWaitEvent(c->st, c->cp_join[k], 0)) != cudaSuccess)
             return cuda_fail(c, e, "copying result to host");
     }
@@ -360,6 +386,10 @@ rism_status rism_init(rism_ctx* c, double* u, double* c_lr, double* h_lr, double
         }
     }
     Outputs o{dev[0], dev[1], dev[2]};
+    // host outputs: the treecode's near field runs in z slabs whose copies overlap the rest of the evaluation
+    if (c->o.method == RISM_METHOD_TREECODE && c->tree &&
+        (s = tree_set_slabs(c->tree, host_out ? kOutSlabs : 1, c->err)) != RISM_OK)
+        return fail(c, s, c->err);
     // Graph-replayed step (treecode, new solute coordinates, from the context's second treecode call on; host
     // outputs use the staging buffers): solute upload from pinned memory, tables, tree, lists and evaluation in
     // one launch.
@@ -384,17 +414,16 @@ rism_status rism_init(rism_ctx* c, double* u, double* c_lr, double* h_lr, double
         s = tree_graph_step(c->tree, c->t, c->gd, c->ph, c->o, o, step, c->st, c->err, c->info, used);
         if (s != RISM_OK) return s;
         if (used) {
-            rism_status st = check_device_error(c);
+            // host outputs: the copies go out now, slab by slab as the replay completes them (a retry below
+            // evaluates and copies again)
+            rism_status st = host_out ? copy_outputs(c, user, dev, staged, bytes) : RISM_OK;
+            if (st == RISM_OK) st = check_device_error(c);  // synchronises the stream, the copies included
             bool retry = false;
             if (st == RISM_OK) st = tree_post(c->tree, c->info, retry, c->err);
             if (st != RISM_OK) return st;
             if (!retry) {
                 if (lj_tail)
                     for (int k = 0; k < c->S; ++k) lj_tail[k] = tail ? c->h_tail[k] : 0.0;
-                if (host_out) {
-                    if ((st = copy_outputs(c, user, dev, staged, bytes)) != RISM_OK) return st;
-                    if ((e = cudaStreamSynchronize(c->st)) != cudaSuccess) return cuda_fail(c, e, "copying result to host");
-                }
                 c->dirty = false;
                 c->setup_launches = 0;
                 if (c->o.debug_flags & 2) c->info.eval_ms = c->info.box_ms + c->info.far_ms + c->info.near_ms;

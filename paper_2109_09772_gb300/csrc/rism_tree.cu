@@ -1378,28 +1378,40 @@ __global__ void __launch_bounds__(32 * kListWarps) k_near_lists(ListArgs a, cons
 // Launch order of the batches, heaviest first: a counting sort of the batches by the binary order of magnitude
 // of their work (one CTA per list: CTA 0 orders work0 into order0, CTA 1 work1 into order1).  The order changes
 // nothing but which CTAs start first (each batch is computed independently), so long batches do not trail at
-// the end of the launch.
+// the end of the launch.  With nslab > 1, order0 is sorted by z slab first: slab k holds the batch layers
+// kb with floor(kb nslab / nbz) = k, and its batches (heaviest first) fill positions [kb_k nbxy, kb_(k+1) nbxy),
+// kb_k = ceil(k nbz / nslab), so each slab can run as a launch of its own.
 constexpr int kOrderBuckets = 33;
+constexpr int kMaxSlabs = 16;
 __global__ void __launch_bounds__(1024) k_order(int nb, const int* __restrict__ work0, int* order0,
-                                                const int* __restrict__ work1, int* order1) {
-    __shared__ int hist[kOrderBuckets], start[kOrderBuckets];
+                                                const int* __restrict__ work1, int* order1, int nslab, int nbxy,
+                                                int nbz) {
+    __shared__ int hist[kOrderBuckets * kMaxSlabs], start[kOrderBuckets * kMaxSlabs];
     const int* __restrict__ work = blockIdx.x == 0 ? work0 : work1;
     int* order = blockIdx.x == 0 ? order0 : order1;
+    const int ns = blockIdx.x == 0 ? nslab : 1;
+    const int nkey = kOrderBuckets * ns;
     const int tid = threadIdx.x;
-    if (tid < kOrderBuckets) hist[tid] = 0;
+    for (int k = tid; k < nkey; k += blockDim.x) hist[k] = 0;
     __syncthreads();
-    auto bucket = [](int w) { return w <= 0 ? 0 : 32 - __clz(w); };  // 0 .. 32
-    for (int b = tid; b < nb; b += blockDim.x) atomicAdd(&hist[bucket(work[b])], 1);
+    // key: slab-major, then the work's order of magnitude from the largest (32) down to none (0)
+    auto key = [&](int b) {
+        const int w = work[b];
+        const int mag = w <= 0 ? 0 : 32 - __clz(w);
+        const int sl = ns > 1 ? (int)((long long)(b / nbxy) * ns / nbz) : 0;
+        return sl * kOrderBuckets + (kOrderBuckets - 1 - mag);
+    };
+    for (int b = tid; b < nb; b += blockDim.x) atomicAdd(&hist[key(b)], 1);
     __syncthreads();
     if (tid == 0) {
         int acc = 0;
-        for (int k = kOrderBuckets - 1; k >= 0; --k) {
+        for (int k = 0; k < nkey; ++k) {
             start[k] = acc;
             acc += hist[k];
         }
     }
     __syncthreads();
-    for (int b = tid; b < nb; b += blockDim.x) order[atomicAdd(&start[bucket(work[b])], 1)] = b;
+    for (int b = tid; b < nb; b += blockDim.x) order[atomicAdd(&start[key(b)], 1)] = b;
 }
 
 __global__ void k_reset_meta(TreeMeta* meta) {
@@ -1449,6 +1461,7 @@ struct EvalArgs {
     int uni_rc;            // every (atom, site) pair has the same LJ cut-off (global cut-off or none)
     const int* near_order; // work item -> batch of the per-solute near kernel (heaviest first)
     int* wq;               // [2] work queue of the persistent near kernel: items taken, CTAs done (0 between launches)
+    int q0, q1;            // positions [q0, q1) of the near order (in sub-batches) that this near launch takes
     const int* far_order;  // the same for the far kernel
     const int* near_work;  // per batch: candidate atoms of the near list
     const int* far_work;   // per batch: atoms and proxies of the far list
@@ -1748,6 +1761,7 @@ __device__ __forceinline__ bool stage_pairs(const SrcF* __restrict__ Sx, int cnt
 template <int P, bool DH, bool ON>
 __device__ __forceinline__ void far_pairs(const PairRec* wp, int np, const f32x2 (&GX)[P], f32x2 FY, f32x2 FZ,
                                           f32x2 K2, f32x2 (&P1)[P], f32x2 (&PK)[P]) {
+#pragma unroll 2
     for (int l = 0; l < np; ++l) {
         const ulonglong2 X = *reinterpret_cast<const ulonglong2*>(&wp[l].x);
         const ulonglong2 Y = *reinterpret_cast<const ulonglong2*>(&wp[l].y);
@@ -2812,7 +2826,6 @@ __global__ void __launch_bounds__(NearShape<NXB, NYB, NZB>::NTP, (NearOcc<NXB, N
         r.stat_warps = 0;
     }
     __syncthreads();
-    const int total = a.nbx * a.nby * a.nbz * NS;
     const NearConst c = near_const(a);
     const LJf* ljt = c.uni ? a.ljs2 : a.ljs;  // the two-wide tile reads {A, A, -B, -B}
     NearPts<SM> q;
@@ -2821,8 +2834,8 @@ __global__ void __launch_bounds__(NearShape<NXB, NYB, NZB>::NTP, (NearOcc<NXB, N
     const int rr = run_stream<SM, true, Sh::NW>(
         r, a.wlim, a.err,
         [&](int, int& item, ItemSrc& is) {
-            const int qi = atomicAdd(&a.wq[0], 1);  // next position of the heaviest-first order
-            if (qi >= total) return false;
+            const int qi = a.q0 + atomicAdd(&a.wq[0], 1);  // next position of the heaviest-first order
+            if (qi >= a.q1) return false;
             const int b = a.near_order[qi / NS];
             item = b * NS + qi % NS;
             is = ItemSrc{a.near_ent, b * a.near_cap, b * a.near_cap + a.near_cnt[b], a.srcf, ljt};
@@ -3052,6 +3065,11 @@ struct TreeState {
     BatchCache* bc = nullptr;
     cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};  // box / far / near timing (debug_flags bit 1)
     bool timed = false;
+    // z slabs of the near launch: with nslab > 1 the near kernel runs as one launch per slab, each followed by a
+    // record of slab_ev[k], so copies of a finished slab's outputs can overlap the next slabs' evaluation
+    int nslab = 1;
+    cudaEvent_t slab_ev[kMaxSlabs] = {};
+    bool slabs_live = false;  // the last enqueued evaluation recorded the slab events
     // target boxes (cluster-particle far field)
     TBoxes tb{};
     int cap_cp = 0, cap_dn = 0, cap_tbox = 0;
@@ -3717,7 +3735,8 @@ rism_status tree_enqueue(TreeState* s, const DevTables& t, const GridD& g, const
     k_far_lists<<<lgrid, 32 * kListWarps, 0, st>>>(fa, s->nodes, s->far_ent, s->far_cnt, s->far_work, s->meta);
     k_near_lists<<<lgrid, 32 * kListWarps, 0, st>>>(na, s->cell_start, s->near_ent, s->near_cnt, s->near_work,
                                                      s->meta);
-    k_order<<<2, 1024, 0, st>>>(s->nb, s->near_work, s->near_order, s->far_work, s->far_order);
+    k_order<<<2, 1024, 0, st>>>(s->nb, s->near_work, s->near_order, s->far_work, s->far_order, s->nslab,
+                                s->nbx * s->nby, s->nbz);
     s->launches += 3;
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_err(err, e, "tree build");
@@ -3750,6 +3769,8 @@ EvalArgs make_args(TreeState* s, const DevTables& t, const GridD& g, const Phys&
     a.uni_rc = o.lj_mode != RISM_LJ_TOL ? 1 : 0;
     a.near_order = s->near_order;
     a.wq = s->wq;
+    a.q0 = 0;
+    a.q1 = s->nb * (shape_of(s->variant).nx / 8);  // sub-batches of 8 points along x
     a.far_order = s->far_order;
     a.near_work = s->near_work;
     a.far_work = s->far_work;
@@ -3893,6 +3914,8 @@ void tree_destroy(TreeState* s) {
     delete s->bc;
     for (int k = 0; k < 4; ++k)
         if (s->ev[k]) cudaEventDestroy(s->ev[k]);
+    for (int k = 0; k < kMaxSlabs; ++k)
+        if (s->slab_ev[k]) cudaEventDestroy(s->slab_ev[k]);
     cudaFree(s->cp_cnt);
     cudaFree(s->dn_cnt);
     cudaFree(s->dn_ent);
@@ -4028,10 +4051,65 @@ static rism_status tree_autotune(TreeState* s, const DevTables& t, const GridD& 
     return r != RISM_OK ? r : tree_enqueue(s, t, g, ph, o, st, err);
 }
 
+// The near kernel (+ epilogue) as one launch, or as one launch per z slab of batch layers (s->nslab > 1), each
+// followed by a record of its slab event; external records when the launches are being captured into a graph,
+// so that streams outside the graph can wait on a slab.
+namespace {
+cudaError_t near_enqueue(TreeState* s, int smax, const EvalArgs& a, bool du, bool dh, cudaStream_t st,
+                         bool captured) {
+    if (s->nslab <= 1) {
+        s->slabs_live = false;
+        return dispatch(smax, s->variant, 3, du, dh, &a, s->nb, nullptr, 0, st);
+    }
+    const int NS = shape_of(s->variant).nx / 8, nbxy = s->nbx * s->nby;
+    cudaError_t e = cudaSuccess;
+    for (int k = 0; k < s->nslab && e == cudaSuccess; ++k) {
+        const int kb0 = (int)(((int64_t)k * s->nbz + s->nslab - 1) / s->nslab);
+        const int kb1 = (int)(((int64_t)(k + 1) * s->nbz + s->nslab - 1) / s->nslab);
+        if (kb1 > kb0) {
+            EvalArgs b = a;
+            b.q0 = kb0 * nbxy * NS;
+            b.q1 = kb1 * nbxy * NS;
+            e = dispatch(smax, s->variant, 3, du, dh, &b, (kb1 - kb0) * nbxy, nullptr, 0, st);
+        }
+        if (e == cudaSuccess)
+            e = captured ? cudaEventRecordWithFlags(s->slab_ev[k], st, cudaEventRecordExternal)
+                         : cudaEventRecord(s->slab_ev[k], st);
+    }
+    s->slabs_live = e == cudaSuccess;
+    return e;
+}
+}  // namespace
+
+rism_status tree_set_slabs(TreeState* s, int nslab, std::string& err) {
+    nslab = std::max(1, std::min(nslab, kMaxSlabs));
+    for (int k = 0; k < nslab; ++k)
+        if (!s->slab_ev[k]) {
+            const cudaError_t e = cudaEventCreateWithFlags(&s->slab_ev[k], cudaEventDisableTiming);
+            if (e != cudaSuccess) return cuda_err(err, e, "slab events");
+        }
+    s->nslab = nslab;
+    return RISM_OK;
+}
+
+int tree_slabs(const TreeState* s, const GridD& g, int (*z)[2], cudaEvent_t* ev) {
+    if (!s->slabs_live || s->nslab <= 1) return 0;
+    const int nzb = shape_of(s->variant).nz;
+    for (int k = 0; k < s->nslab; ++k) {
+        const int kb0 = (int)(((int64_t)k * s->nbz + s->nslab - 1) / s->nslab);
+        const int kb1 = (int)(((int64_t)(k + 1) * s->nbz + s->nslab - 1) / s->nslab);
+        z[k][0] = std::min(kb0 * nzb, g.nz);
+        z[k][1] = std::min(kb1 * nzb, g.nz);
+        ev[k] = s->slab_ev[k];
+    }
+    return s->nslab;
+}
+
 // Enqueue a10 + a11: far kernel, near kernel + epilogue, then a copy of the
 // meta block (counts, overflow flag) to pinned memory for tree_post.
 rism_status tree_eval(TreeState* s, const DevTables& t, const GridD& g, const Phys& ph, const rism_options& o,
                       Outputs out, cudaStream_t st, std::string& err, rism_info& info) {
+    s->slabs_live = false;
     if (!s->prepared) {
         err = "tree not prepared";
         return RISM_E_STATE;
@@ -4053,16 +4131,17 @@ rism_status tree_eval(TreeState* s, const DevTables& t, const GridD& g, const Ph
         cudaEventRecord(s->ev[1], st);
         e = dispatch(t.smax, s->variant, 2, du, dh, &a, s->nb, nullptr, 0, st);
         cudaEventRecord(s->ev[2], st);
-        if (e == cudaSuccess) e = dispatch(t.smax, s->variant, 3, du, dh, &a, s->nb, nullptr, 0, st);
+        if (e == cudaSuccess) e = near_enqueue(s, t.smax, a, du, dh, st, false);
         cudaEventRecord(s->ev[3], st);
     } else {
         cpl = cp_enqueue(s, a, dh, st);
-        e = dispatch(t.smax, s->variant, 0, du, dh, &a, s->nb, nullptr, 0, st);
+        e = dispatch(t.smax, s->variant, 2, du, dh, &a, s->nb, nullptr, 0, st);
+        if (e == cudaSuccess) e = near_enqueue(s, t.smax, a, du, dh, st, false);
     }
     if (e != cudaSuccess) return cuda_err(err, e, "tree eval");
     if ((e = cudaMemcpyAsync(s->h_meta, s->meta, sizeof(TreeMeta), cudaMemcpyDeviceToHost, st)) != cudaSuccess)
         return cuda_err(err, e, "tree meta copy");
-    info.launches += s->launches + 2 + cpl;
+    info.launches += s->launches + 1 + std::max(1, s->nslab) + cpl;
     const ShapeDesc sd = shape_of(s->variant);
     info.batch[0] = sd.nx;
     info.batch[1] = sd.ny;
@@ -4126,6 +4205,7 @@ rism_status tree_graph_step(TreeState* s, const DevTables& t, const GridD& g, co
                             Outputs out, const SoluteStep& step, cudaStream_t st, std::string& err, rism_info& info,
                             bool& used) {
     used = false;
+    s->slabs_live = false;
     if (o.autotune && s->tuned_key != problem_class(t, g, ph, o)) return RISM_OK;  // time the candidates first
     if (!o.autotune) fixed_shape(s, o);
     rism_status r = tree_reserve(s, t, g, ph, o, err);
@@ -4150,7 +4230,7 @@ rism_status tree_graph_step(TreeState* s, const DevTables& t, const GridD& g, co
                           s->meta, s->h_meta, s->dn_cnt, s->dn_ent, s->tflag, s->tnch, s->ntab};
     put(ptrs, sizeof ptrs);
     const int ints[] = {s->variant, s->leaf, s->max_nodes, s->max_prox, s->max_items, s->cap_far, s->cap_near,
-                        s->cap_cp, s->cap_dn, s->nb};
+                        s->cap_cp, s->cap_dn, s->nb, s->nslab};
     put(ints, sizeof ints);
     cudaError_t e = cudaSuccess;
     if (!s->sg || s->sg->sig != sig) {
@@ -4205,9 +4285,9 @@ rism_status tree_graph_step(TreeState* s, const DevTables& t, const GridD& g, co
             rec(1);
             if (e == cudaSuccess) e = dispatch(t.smax, s->variant, 2, du, dh, &a, s->nb, nullptr, 0, cs);
             rec(2);
-            if (e == cudaSuccess) e = dispatch(t.smax, s->variant, 3, du, dh, &a, s->nb, nullptr, 0, cs);
+            if (e == cudaSuccess) e = near_enqueue(s, t.smax, a, du, dh, cs, true);
             rec(3);
-            launches += 2;
+            launches += 1 + std::max(1, s->nslab);
         }
         if (tail) cudaStreamWaitEvent(cs, G->join, 0);
         if (e == cudaSuccess && r == RISM_OK)
@@ -4233,6 +4313,7 @@ rism_status tree_graph_step(TreeState* s, const DevTables& t, const GridD& g, co
         return cuda_err(err, e, "graph launch");
     }
     used = true;
+    s->slabs_live = s->nslab > 1;  // the graph records the slab events (the slab count is in its signature)
     s->prepared = true;
     s->timed = (o.debug_flags & 2) != 0;
     info.launches = s->sg->launches;
@@ -4342,7 +4423,7 @@ rism_status batch_eval(std::vector<BatchItem>& items, const rism_options& o, cud
             for (int nr = 0; nr < 2; ++nr) {  // global heaviest-first orders over all (solute, batch) items
                 k_gather_work<<<count, 256, 0, cs>>>(bc->d_args, bc->d_off, count, nr, bc->d_work);
                 k_order<<<1, 1024, 0, cs>>>(off[count], bc->d_work, bc->d_order + (size_t)nr * off[count], nullptr,
-                                            nullptr);
+                                            nullptr, 1, 1, 1);
             }
             BatchEval be{bc->d_args, bc->d_off, count, off[count], bc->d_queue, bc->d_order};
             const bool du = items[0].o.u != nullptr, dh = items[0].o.h != nullptr;

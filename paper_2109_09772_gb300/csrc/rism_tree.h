@@ -59,6 +59,15 @@ rism_status tree_graph_step(TreeState* ts, const DevTables& t, const GridD& g, c
 // Drop the captured solute graph (buffers moved or the retry path ran).
 void tree_graph_reset(TreeState* ts);
 
+// Split the near kernel of the following evaluations into nslab launches over z slabs of batch layers (1: one
+// launch), each followed by a record of a slab event, so that copies of a finished slab's outputs can overlap
+// the rest of the evaluation.  The slab count is part of the solute graph's signature.
+rism_status tree_set_slabs(TreeState* ts, int nslab, std::string& err);
+// After tree_eval or tree_graph_step enqueued an evaluation with slabs: their number, the grid planes
+// [z[k][0], z[k][1]) whose outputs slab k completes, and the event recorded after it; 0 without slabs.
+int tree_slabs(const TreeState* ts, const GridD& g, int (*z)[2], cudaEvent_t* ev);
+constexpr int kOutSlabsMax = 16;
+
 // Reverse mode, far part, with the grid boxes as source clusters: w holds the per-point weights (A1 of 1/d,
 // Ak of e^{-kappa d}/d in .x, .y); part receives per atom (original order) dq, Gx, Gy, Gz in grid units, as
 // one chunk of the direct far kernel would.  used = false (nothing done) when target boxes are off or the tree

@@ -19,7 +19,7 @@ def _rank(rank, world, port, q):
         ms = 2.0 + rank  # rank 1 is the slow one
         ms_max = bench.reduce_max(dist, ms, "cpu")
         value = bench.job_value(world, w.solvent.nsite, w.grid.npts, ms_max)
-        q.put((rank, ms_max, value, w.solute.n, tuple(w.grid.n), float(w.solute.xyz[0, 0])))
+        q.put((rank, ms_max, value, w.solute.n, tuple(w.grid.n), float(w.solute.xyz[0, 0]), w.solvent.nsite))
     finally:
         dist.destroy_process_group()
 
@@ -37,10 +37,11 @@ def test_two_gloo_ranks_weak_scaling():
     for p in procs:
         p.join(timeout=60)
         assert p.exitcode == 0
-    (r0, ms0, v0, n0, g0, x0), (r1, ms1, v1, n1, g1, x1) = res
+    (r0, ms0, v0, n0, g0, x0, s0), (r1, ms1, v1, n1, g1, x1, s1) = res
     assert ms0 == ms1 == 3.0  # both ranks report the slowest rank's time
-    assert v0 == v1 == pytest.approx(2 * 4 * 128 ** 3 / 3.0e-3 / 1e9)
-    assert n0 == n1 == 2000 and g0 == g1 == (128, 128, 128)
+    # the default workload: the 13,600-atom ellipsoid on 224 x 192 x 160 with 4 sites, one per rank
+    assert n0 == n1 == 13600 and g0 == g1 == (224, 192, 160) and s0 == s1 == 4
+    assert v0 == v1 == pytest.approx(2 * 4 * 224 * 192 * 160 / 3.0e-3 / 1e9)
     assert x0 != x1  # each rank has its own seeded solute
 
 

@@ -334,3 +334,29 @@ def test_build_mid_sized_solute_paths(R):
     g = run(R, w)
     check_fields({k: g[k][:, idx] for k in ("u", "c", "h")}, ref, ("u", "c", "h"), TREE_TOL, w.grid, big.xyz,
                  idx=idx, label="17000")
+
+
+def test_host_outputs_in_z_slabs_ragged_and_empty(R):
+    """With host outputs the near field runs in four z slabs whose copies start as each slab finishes: on a grid
+    of three batch layers (nz = 20: 8 + 8 + 4 planes) the last slab is empty and the last layer ragged.  The host
+    grids equal the device grids bit for bit, on the regular path (first call) and the replayed one."""
+    import torch
+
+    w = I.small_workload(n_atoms=300, n=(40, 24, 20), h=0.5, seed=31, ions=True, lj_rcut=6.0, net=1.0)
+    S, M = w.solvent.nsite, w.grid.npts
+    sol = w.solute
+    rd = R.from_workload(w, method=R.METHOD_TREECODE, precision=R.PREC_FP32)
+    rh = R.from_workload(w, method=R.METHOD_TREECODE, precision=R.PREC_FP32)
+    host = [torch.empty((S, M), dtype=torch.float64).pin_memory().numpy() for _ in range(3)]
+    for step in range(3):
+        xyz = sol.xyz + (0.21 if step == 2 else 0.0)
+        rd.set_solute(xyz, sol.q, sol.sigma, sol.eps)
+        out = rd.init()
+        rh.set_solute(xyz, sol.q, sol.sigma, sol.eps)
+        for hb in host:
+            hb.fill(np.nan)
+        rh.init_host(*host)
+        for i, k in enumerate(("u", "c", "h")):
+            assert np.array_equal(out[k].cpu().numpy().reshape(S, M), host[i]), (step, k)
+    for r in (rd, rh):
+        r.close()
