@@ -478,12 +478,12 @@ cudaError_t run_direct(const GridD& g, const Phys& ph, const DevTables& t, int p
     if (prec == RISM_PREC_FP64) {
         size_t sm = 2 * kT * sizeof(Geo) + 2 * kT * SM * sizeof(LJd) + 2 * sizeof(uint64_t);
         auto kern = k_direct64<SM, kP, kBX, kBY, kBZ, kT, DU, DH>;
-        cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+        raise_dyn_smem(kern, sm);
         kern<<<grid, block, sm, st>>>(g, ph, t.geo, t.ljd, t.n, o, t.err, wl, dbg);
     } else {
         size_t sm = 2 * kT * sizeof(SrcF) + 2 * kT * SM * sizeof(LJf) + 2 * sizeof(uint64_t);
         auto kern = k_direct32<SM, kP, kBX, kBY, kBZ, kT, DU, DH>;
-        cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+        raise_dyn_smem(kern, sm);
         kern<<<grid, block, sm, st>>>(g, ph, t.srcf, t.ljf, t.n, o, t.err, wl, dbg);
     }
     return cudaGetLastError();

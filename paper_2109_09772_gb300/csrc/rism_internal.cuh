@@ -6,6 +6,10 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <map>
+#include <mutex>
+#include <utility>
+
 #include "rism3d.h"
 
 namespace rism {
@@ -59,6 +63,25 @@ struct GridD {
     int nx, ny, nz;
     double h, ox, oy, oz;
 };
+
+// Raise, never lower, the dynamic shared-memory limit of a kernel on the current device.  The limit is a
+// property of the function, not of a launch: lowering it for a small launch would leave a launch of the same
+// kernel captured earlier in a graph (with more shared memory) over the limit whenever that node is launched
+// on its own, as a profiler's replay does.
+template <typename F>
+cudaError_t raise_dyn_smem(F* kernel, size_t bytes) {
+    static std::mutex mu;
+    static std::map<std::pair<int, const void*>, size_t> cur;
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    std::lock_guard<std::mutex> lock(mu);
+    size_t& c = cur[{dev, reinterpret_cast<const void*>(kernel)}];
+    if (bytes <= c) return cudaSuccess;
+    e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+    if (e == cudaSuccess) c = bytes;
+    return e;
+}
 
 // ------------------------------------------------------------ PTX helpers
 __device__ __forceinline__ float rsqrt_approx(float x) {

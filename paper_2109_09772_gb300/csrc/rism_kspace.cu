@@ -356,7 +356,7 @@ cudaError_t launch_kspace(const DevTables& t, const GridD& g, const KspaceSetup&
     a.err = t.err;
     a.wlim = wait_limit;
     const size_t sm = sizeof(float2) * (2 * kKT * kKBX + 2 * kKT * kKBY + 2 * kKT + kKT * kKBY) + 2 * sizeof(uint64_t);
-    cudaFuncSetAttribute(k_ksum, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    raise_dyn_smem(k_ksum, sm);
     dim3 grid((unsigned)(tb.mxp / kKBX), (unsigned)(tb.nyp / kKBY), (unsigned)g.nz);
     k_ksum<<<grid, kKThreads, sm, st>>>(a);
     return cudaGetLastError();

@@ -2285,8 +2285,8 @@ __global__ void __launch_bounds__(256) k_tdown(CPArgs c, float4* far, const Tree
 template <int N1>
 void launch_down(const TBoxes& tb, const CPArgs& c, float4* far, const TreeMeta* meta, cudaStream_t st) {
     const size_t sl = interp_smem(N1, N1), sd = interp_smem(N1, kTB0);
-    cudaFuncSetAttribute(k_l2l<N1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sl);
-    cudaFuncSetAttribute(k_tdown<N1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sd);
+    raise_dyn_smem(k_l2l<N1>, sl);
+    raise_dyn_smem(k_tdown<N1>, sd);
     for (int l = tb.L - 2; l >= 0; --l) k_l2l<N1><<<tb.nbx[l] * tb.nby[l] * tb.nbz[l], 256, sl, st>>>(c, l, meta);
     k_tdown<N1><<<tb.nbx[0] * tb.nby[0] * tb.nbz[0], 256, sd, st>>>(c, far, meta);
 }
@@ -2955,8 +2955,7 @@ struct Kern {
         // persistent: at most the CTAs that are resident at once
         constexpr size_t dyn = sizeof(float4) * 512 * kFarBuf;  // far-field record buffers
         static const int resident = [] {
-            cudaFuncSetAttribute(k_near32<S::NX, S::NY, S::NZ, SM, DU, DH>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 (int)dyn);
+            raise_dyn_smem(k_near32<S::NX, S::NY, S::NZ, SM, DU, DH>, dyn);
             int b = 0;
             cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_near32<S::NX, S::NY, S::NZ, SM, DU, DH>, S::NTN, dyn);
             return std::max(1, b) * sm_count();
@@ -3623,15 +3622,15 @@ void launch_taylor(const TBoxes& tb, const EvalArgs& a, const CPArgs& c, float4*
     const dim3 grid(tb.nbox, kCPChunks);
     const size_t se = (size_t)kTayWarps * tay_nc(P) * (sizeof(float2) + 3 * sizeof(float));
     if (dh) {
-        cudaFuncSetAttribute(k_tay_eval<P, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)se);
+        raise_dyn_smem(k_tay_eval<P, true>, se);
         k_tay_eval<P, true><<<grid, kTayWarps * 32 + 32, se, st>>>(a, c);
     } else {
-        cudaFuncSetAttribute(k_tay_eval<P, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)se);
+        raise_dyn_smem(k_tay_eval<P, false>, se);
         k_tay_eval<P, false><<<grid, kTayWarps * 32 + 32, se, st>>>(a, c);
     }
     k_cp_reduce<<<tb.nbox, 256, 0, st>>>(c, meta);
     const size_t sm = sizeof(float2) * (size_t)tb.L * tay_nc(P);
-    cudaFuncSetAttribute(k_tay_down<P>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    raise_dyn_smem(k_tay_down<P>, sm);
     k_tay_down<P><<<tb.nbx[0] * tb.nby[0] * tb.nbz[0], 256, sm, st>>>(c, far, meta);
 }
 
@@ -3696,7 +3695,7 @@ rism_status tree_enqueue(TreeState* s, const DevTables& t, const GridD& g, const
                            : t.n <= kCodeSmem ? (kHistInts + 64) * sizeof(int) + kCodeSmem * sizeof(uint32_t) +
                                                     std::max(kCodeSmem * sizeof(uint32_t), kNodeSmemL * sizeof(Node))
                                               : (kHistInts + 64) * sizeof(int);
-        cudaFuncSetAttribute(k_sort_build, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shb);
+        raise_dyn_smem(k_sort_build, shb);
         k_sort_build<<<1, kSortThreads, shb, st>>>(ba, s->code, s->idx, s->code2, s->idx2, s->nodes, s->items,
                                                    s->prox_nodes, s->prox_items, s->meta);
         k_gather_cells<<<1024, 256, 0, st>>>(ba, s->idx, s->meta, s->code, s->cell_start);
@@ -3709,7 +3708,7 @@ rism_status tree_enqueue(TreeState* s, const DevTables& t, const GridD& g, const
             // source proxies: only the batch-level traversal uses them (with target boxes on, the box level
             // accepts every cluster a batch would)
             const size_t shu = (kChunk * 3 * np + kChunk + 3 * np) * sizeof(double);
-            cudaFuncSetAttribute(k_upward, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shu);
+            raise_dyn_smem(k_upward, shu);
             k_upward<<<4 * sm_count(), 256, shu, st>>>(deg, s->meta, s->nodes, s->prox_nodes, s->items, s->src,
                                                        s->part);
             k_proxy_reduce<<<2 * sm_count(), 256, 0, st>>>(deg, n, s->meta, s->nodes, s->prox_nodes,
@@ -4911,8 +4910,8 @@ void launch_adj_q(const TBoxes& tb, const float4* w, float2* qpart, int* rlow, f
     constexpr int M = kTB0, P3 = N1 * N1 * N1;
     const size_t sr = sizeof(float2) * (M * M * M + M * M * N1 + M * N1 * N1) + sizeof(float) * 3 * M * N1;
     const size_t sa = sizeof(float2) * 4 * P3 + sizeof(float) * 3 * N1 * N1;
-    cudaFuncSetAttribute(k_adj_qregion<N1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sr);
-    cudaFuncSetAttribute(k_adj_qagg<N1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sa);
+    raise_dyn_smem(k_adj_qregion<N1>, sr);
+    raise_dyn_smem(k_adj_qagg<N1>, sa);
     k_adj_qregion<N1><<<tb.nbx[0] * tb.nby[0] * tb.nbz[0], 256, sr, st>>>(tb, w, qpart, rlow);
     for (int l = 0; l < tb.L; ++l)
         k_adj_qagg<N1><<<tb.nbx[l] * tb.nby[l] * tb.nbz[l], 256, sa, st>>>(tb, l, qpart, rlow, qtot);
