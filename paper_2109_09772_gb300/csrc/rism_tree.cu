@@ -2730,41 +2730,6 @@ __device__ __forceinline__ void near_publish(R& r, TreeMeta* meta, const unsigne
     }
 }
 
-// One work item (sub-batch `sub` of batch b) with its own ring setup: the body of the persistent batched
-// kernel, whose consecutive items may belong to different solutes.
-template <int NXB, int NYB, int NZB, int SM, bool DU, bool DH>
-__device__ void near_body(const EvalArgs& a, int b, int sub, Ring<SM, true>& r, float4* tab) {
-    using Sh = NearShape<NXB, NYB, NZB>;
-    const int tid = threadIdx.x;
-    const NearConst c = near_const(a);
-    NearPts<SM> q;
-    unsigned cnt3[3] = {0u, 0u, 0u};  // pairs tested / inside the LJ cut-off / inside r_short
-    Cursor cur;
-    __syncthreads();
-    for (int k = tid; k < 2 * kNTab; k += blockDim.x) tab[k] = a.ntab[k];
-    if (tid == Sh::NT) {
-        cur.e = b * a.near_cap;
-        cur.e_end = cur.e + a.near_cnt[b];
-        cur.off = 0;
-        cur.left = INT_MAX;
-        cur.produced = 0;
-        cur.done = false;
-        for (int s = 0; s < kStages; ++s) cur.last_phase[s] = -1;
-        ring_init(r, Sh::NW);
-        r.stat[0] = r.stat[1] = r.stat[2] = 0ull;
-        r.stat_warps = 0;
-    }
-    __syncthreads();
-    if (tid < Sh::NT) near_begin<NXB, NYB, NZB, SM>(q, a, b, sub);
-    const LJf* ljt = c.uni ? a.ljs2 : a.ljs;  // the two-wide tile reads {A, A, -B, -B}
-    const int rr = run_ring<SM, true, Sh::NW>(r, cur, a.near_ent, a.srcf, ljt, a, [&](int slot, int cnt) {
-        near_stage<SM, DU, DH>(q, c, r.src[slot], r.lj[slot], cnt, tab, cnt3);
-    }, [](int) {});
-    if (rr != kRingDone) return;
-    near_publish<Sh::NW>(r, a.meta, cnt3);
-    near_finish<SM, DU, DH>(q, c, a, a.far + far_index(a.g.nx, a.g.ny, q.i0, q.j, q.k));  // both in one block row
-}
-
 // ---- per-solute kernels
 // Work queue of a persistent kernel: wq[0] counts the items taken, wq[1] the CTAs whose producer takes no more.
 // The last CTA to leave resets both, so every launch (and every replay of a captured one) starts from zero.
@@ -2908,31 +2873,86 @@ __global__ void __launch_bounds__(FarShape<NXB, NYB, NZB, PF>::NTP) k_far32_batc
     }
 }
 
+// Pair counters of one finished item, added to its solute's totals (one lane per warp).
+__device__ __forceinline__ void near_count(TreeMeta* meta, const unsigned (&cnt3)[3]) {
+    unsigned long long c0 = cnt3[0], c1 = cnt3[1], c2 = cnt3[2];
+    for (int o = 16; o > 0; o >>= 1) {
+        c0 += __shfl_xor_sync(0xffffffffu, c0, o);
+        c1 += __shfl_xor_sync(0xffffffffu, c1, o);
+        c2 += __shfl_xor_sync(0xffffffffu, c2, o);
+    }
+    if ((threadIdx.x & 31) == 0 && c0) {
+        atomicAdd(&meta->near_tested, c0);
+        atomicAdd(&meta->lj_pairs, c1);
+        atomicAdd(&meta->sr_pairs, c2);
+    }
+}
+
+// Persistent near-field kernel over the (solute, batch) items of many solutes, in the global heaviest-first
+// order: the same item stream as k_near32 (the producer streams item after item through one ring, with each
+// sub-batch's far-field records), every item resolved to its solute's arguments.  The short-range tables are
+// read through the L1 cache from the item's own solute (solutes may differ in them); items of a solute whose
+// lists overflowed are skipped (the host grows the lists and runs again).
 template <int NXB, int NYB, int NZB, int SM, bool DU, bool DH>
 __global__ void __launch_bounds__(NearShape<NXB, NYB, NZB>::NTP, (NearOcc<NXB, NYB, NZB, SM, DU, DH>::v))
     k_near32_batched(BatchEval be) {
-    constexpr int NS = NearShape<NXB, NYB, NZB>::NSUB;
+    using Sh = NearShape<NXB, NYB, NZB>;
+    constexpr int NS = Sh::NSUB;
     __shared__ Ring<SM, true> r;
-    __shared__ float4 tab[2 * kNTab];
-    __shared__ int s_item, s_sub;
-    __shared__ EvalArgs sa;
-    if (threadIdx.x == 0) r.inited = 0;
-    for (;;) {
-        __syncthreads();
-        if (threadIdx.x == 0) {
-            // queue position q: sub-batch q % NS of the item at order position q / NS
-            const int q = atomicAdd(be.queue, 1);
-            s_item = q < be.total * NS ? be.order[q / NS] : be.total;
-            s_sub = q % NS;
-            if (s_item < be.total) sa = be.args[find_solute(be, s_item)];
-        }
-        __syncthreads();
-        const int it = s_item;
-        if (it >= be.total) break;
-        if (sa.meta->overflow) continue;
-        const int sid = find_solute(be, it);
-        near_body<NXB, NYB, NZB, SM, DU, DH>(sa, it - be.item_off[sid], s_sub, r, tab);
+    static_assert(Sh::SX == 8 && NYB == 8 && NZB == 8, "a sub-batch is one 8x8x8 block of the far buffer");
+    static_assert(kStages <= kFarBuf - 1, "the far-field buffers cover the sub-batches the producer runs ahead");
+    extern __shared__ __align__(16) float4 farbuf[];  // [kFarBuf][512], dynamic
+    const int tid = threadIdx.x;
+    if (tid == Sh::NT) {
+        r.inited = 0;
+        ring_init(r, Sh::NW);
     }
+    __syncthreads();
+    const int total = be.total * NS;
+    NearPts<SM> q;
+    NearConst c{};
+    const EvalArgs* ap = be.args;
+    unsigned cnt3[3] = {0u, 0u, 0u};
+    int seq = 0;
+    run_stream<SM, true, Sh::NW>(
+        r, be.args[0].wlim, be.args[0].err,
+        [&](int, int& item, ItemSrc& is) {
+            for (;;) {
+                const int qi = atomicAdd(be.queue, 1);
+                if (qi >= total) return false;
+                const int gi = be.order[qi / NS], sid = find_solute(be, gi);
+                const EvalArgs& A = be.args[sid];
+                if (A.meta->overflow) continue;
+                const int b = gi - be.item_off[sid];
+                item = gi * NS + qi % NS;
+                is = ItemSrc{A.near_ent, b * A.near_cap, b * A.near_cap + A.near_cnt[b], A.srcf,
+                             A.uni_rc ? A.ljs2 : A.ljs};
+                return true;
+            }
+        },
+        [&](int n, int item, uint64_t* bar) {
+            const int gi = item / NS, sid = find_solute(be, gi);
+            const EvalArgs& A = be.args[sid];
+            const int b = gi - be.item_off[sid], ib = b % A.nbx, jb = (b / A.nbx) % A.nby, kb = b / (A.nbx * A.nby);
+            const int64_t blk = far_index(A.g.nx, A.g.ny, ib * NXB + (item % NS) * 8, jb * NYB, kb * NZB);
+            mbar_expect_tx_only(bar, 512 * sizeof(float4));
+            bulk_g2s(farbuf + (n % kFarBuf) * 512, A.far + blk, 512 * sizeof(float4), bar);
+        },
+        [&](int item) {
+            const int gi = item / NS, sid = find_solute(be, gi);
+            ap = be.args + sid;
+            c = near_const(*ap);
+            cnt3[0] = cnt3[1] = cnt3[2] = 0u;
+            near_begin<NXB, NYB, NZB, SM>(q, *ap, gi - be.item_off[sid], item % NS);
+        },
+        [&](int slot, int cnt) { near_stage<SM, DU, DH>(q, c, r.src[slot], r.lj[slot], cnt, ap->ntab, cnt3); },
+        [](int) {},
+        [&](int) {
+            near_finish<SM, DU, DH>(q, c, *ap,
+                                    farbuf + (seq % kFarBuf) * 512 + ((q.k & 7) << 6 | (q.j & 7) << 3 | (q.i0 & 7)));
+            near_count(ap->meta, cnt3);
+            ++seq;
+        });
 }
 
 // ---- dispatch over (shape, sites, outputs)
@@ -2966,8 +2986,10 @@ struct Kern {
     static void far_b(const BatchEval& be, int grid, cudaStream_t st) {
         k_far32_batched<S::NX, S::NY, S::NZ, S::PF, DH><<<grid, S::FT, 0, st>>>(be);
     }
+    static constexpr size_t kNearDyn = sizeof(float4) * 512 * kFarBuf;  // far-field record buffers
     static void near_b(const BatchEval& be, int grid, cudaStream_t st) {
-        k_near32_batched<S::NX, S::NY, S::NZ, SM, DU, DH><<<grid, S::NTN, 0, st>>>(be);
+        raise_dyn_smem(k_near32_batched<S::NX, S::NY, S::NZ, SM, DU, DH>, kNearDyn);
+        k_near32_batched<S::NX, S::NY, S::NZ, SM, DU, DH><<<grid, S::NTN, kNearDyn, st>>>(be);
     }
     static int occ_far() {
         int b = 0;
@@ -2976,8 +2998,9 @@ struct Kern {
     }
     static int occ_near() {
         int b = 0;
+        raise_dyn_smem(k_near32_batched<S::NX, S::NY, S::NZ, SM, DU, DH>, kNearDyn);
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_near32_batched<S::NX, S::NY, S::NZ, SM, DU, DH>, S::NTN,
-                                                      0);
+                                                      kNearDyn);
         return b;
     }
 };
