@@ -3092,6 +3092,11 @@ struct TreeState {
     int nslab = 1;
     cudaEvent_t slab_ev[kMaxSlabs] = {};
     bool slabs_live = false;  // the last enqueued evaluation recorded the slab events
+    // side branch of the preparation: the near lists beside the box-level lists, the far lists and the launch
+    // orders beside the box-level evaluation; joined back before anything reads them (side_pending until then)
+    cudaStream_t side = nullptr;
+    cudaEvent_t side_fork[2] = {nullptr, nullptr}, side_join = nullptr;
+    bool side_pending = false;
     // target boxes (cluster-particle far field)
     TBoxes tb{};
     int cap_cp = 0, cap_dn = 0, cap_tbox = 0;
@@ -3181,6 +3186,13 @@ rism_status tree_reserve(TreeState* s, const DevTables& t, const GridD& g, const
     if (!s->wq) {
         if ((e = cudaMalloc(&s->wq, 2 * sizeof(int))) || (e = cudaMemset(s->wq, 0, 2 * sizeof(int))))
             return cuda_err(err, e, "work queue");
+    }
+    if (!s->side) {
+        if ((e = cudaStreamCreateWithFlags(&s->side, cudaStreamNonBlocking)) ||
+            (e = cudaEventCreateWithFlags(&s->side_fork[0], cudaEventDisableTiming)) ||
+            (e = cudaEventCreateWithFlags(&s->side_fork[1], cudaEventDisableTiming)) ||
+            (e = cudaEventCreateWithFlags(&s->side_join, cudaEventDisableTiming)))
+            return cuda_err(err, e, "side stream");
     }
     if (s->nb + 1 > s->cap_nb) {
         if ((e = regrow(s->far_cnt, (size_t)s->nb + 1)) || (e = regrow(s->near_cnt, (size_t)s->nb + 1)) ||
@@ -3677,12 +3689,24 @@ void launch_taylor_deg(const TBoxes& tb, const EvalArgs& a, const CPArgs& c, flo
 
 // Box-level far field (no allocation, no host wait): proxies of every target box, the downward pass and the
 // interpolation onto the far-field buffer.  Returns the number of launches.
+// The preparation's side branch joined back into st (its lists and orders are read after this point).
+void side_join(TreeState* s, cudaStream_t st) {
+    if (!s->side_pending) return;
+    cudaStreamWaitEvent(st, s->side_join, 0);
+    s->side_pending = false;
+}
+
+// Box-level far field (a10, cluster-particle form), then the join of the preparation's side branch.
 int cp_enqueue(TreeState* s, const EvalArgs& a, bool dh, cudaStream_t st) {
     const TBoxes& tb = s->tb;
-    if (!tb.enabled) return 0;
+    if (!tb.enabled) {
+        side_join(s, st);
+        return 0;
+    }
     const CPArgs c = make_cp(s);
     if (tb.approx == RISM_APPROX_TAYLOR) {
         launch_taylor_deg(tb, a, c, s->far, s->meta, dh, st);
+        side_join(s, st);
         return 3;
     }
     const int n1 = tb.deg + 1;
@@ -3692,6 +3716,7 @@ int cp_enqueue(TreeState* s, const EvalArgs& a, bool dh, cudaStream_t st) {
     else k_cp_eval<false><<<grid, kCPThreads + 32, 0, st>>>(a, c);
     k_cp_reduce<<<tb.nbox, 256, 0, st>>>(c, s->meta);
     launch_down_deg(tb, c, s->far, s->meta, st);
+    side_join(s, st);
     return 2 + (tb.L - 1) + 1;
 }
 
@@ -3739,7 +3764,19 @@ rism_status tree_enqueue(TreeState* s, const DevTables& t, const GridD& g, const
             s->launches += 2;
         }
     }
+    // side branch: the near lists need only the cell table, so they run beside the box-level lists; the far
+    // lists (which start from the box level's pass-down lists) and the launch orders run beside the box-level
+    // evaluation that the caller enqueues next (cp_enqueue joins the branch back)
     const TBoxes& tb = s->tb;
+    ListArgs fa{s->nbx, s->nby, s->nbz, sd.nx, sd.ny, sd.nz, o.theta, n, P3, s->cap_far,
+                tb.enabled ? s->dn_cnt : nullptr, s->dn_ent, s->cap_dn, tb, tb.enabled ? 0 : 1};
+    ListArgs na = fa;
+    na.cap = s->cap_near;
+    const int lgrid = (s->nb + kListWarps - 1) / kListWarps;
+    cudaEventRecord(s->side_fork[0], st);
+    cudaStreamWaitEvent(s->side, s->side_fork[0], 0);
+    k_near_lists<<<lgrid, 32 * kListWarps, 0, s->side>>>(na, s->cell_start, s->near_ent, s->near_cnt, s->near_work,
+                                                          s->meta);
     if (tb.enabled) {
         TListArgs ta{tb, 0, n, P3, o.theta, s->cap_cp, s->cap_dn, s->cp_cnt, s->cp_ent, s->dn_cnt, s->dn_ent};
         for (int l = tb.L - 1; l >= 0; --l) {
@@ -3749,16 +3786,13 @@ rism_status tree_enqueue(TreeState* s, const DevTables& t, const GridD& g, const
             ++s->launches;
         }
     }
-    ListArgs fa{s->nbx, s->nby, s->nbz, sd.nx, sd.ny, sd.nz, o.theta, n, P3, s->cap_far,
-                tb.enabled ? s->dn_cnt : nullptr, s->dn_ent, s->cap_dn, tb, tb.enabled ? 0 : 1};
-    ListArgs na = fa;
-    na.cap = s->cap_near;
-    const int lgrid = (s->nb + kListWarps - 1) / kListWarps;
-    k_far_lists<<<lgrid, 32 * kListWarps, 0, st>>>(fa, s->nodes, s->far_ent, s->far_cnt, s->far_work, s->meta);
-    k_near_lists<<<lgrid, 32 * kListWarps, 0, st>>>(na, s->cell_start, s->near_ent, s->near_cnt, s->near_work,
-                                                     s->meta);
-    k_order<<<2, 1024, 0, st>>>(s->nb, s->near_work, s->near_order, s->far_work, s->far_order, s->nslab,
-                                s->nbx * s->nby, s->nbz);
+    cudaEventRecord(s->side_fork[1], st);
+    cudaStreamWaitEvent(s->side, s->side_fork[1], 0);
+    k_far_lists<<<lgrid, 32 * kListWarps, 0, s->side>>>(fa, s->nodes, s->far_ent, s->far_cnt, s->far_work, s->meta);
+    k_order<<<2, 1024, 0, s->side>>>(s->nb, s->near_work, s->near_order, s->far_work, s->far_order, s->nslab,
+                                     s->nbx * s->nby, s->nbz);
+    cudaEventRecord(s->side_join, s->side);
+    s->side_pending = true;
     s->launches += 3;
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_err(err, e, "tree build");
@@ -3989,7 +4023,9 @@ rism_status tree_prepare(TreeState* s, const DevTables& t, const GridD& g, const
     if (!o.autotune) fixed_shape(s, o);
     rism_status r = tree_reserve(s, t, g, ph, o, err);
     if (r != RISM_OK) return r;
-    return tree_enqueue(s, t, g, ph, o, st, err);
+    r = tree_enqueue(s, t, g, ph, o, st, err);
+    side_join(s, st);  // callers of the prepared tree may read every list next
+    return r;
 }
 
 // Time each (shape, leaf) candidate once (prepare + evaluation, CUDA events)
