@@ -298,15 +298,16 @@ rism_status rism_set_solvent(rism_ctx* c, int32_t nsite, const double* q, const 
 
 namespace {
 
-// z slabs of the treecode's near field when the outputs go to host memory: the copy of a slab's planes (at the
-// host link's rate) overlaps the evaluation of the slabs after it.
+// z slabs of the treecode's far and near fields when the outputs go to host memory: the copy of a slab's planes
+// (at the host link's rate) overlaps the evaluation of the slabs after it.
 constexpr int kOutSlabs = 4;
 static_assert(kOutSlabs <= kOutSlabsMax, "slab events of the tree state");
 
 // Device staging -> caller's host buffers for the outputs staged in device memory: each grid on its own stream
 // (forked from and joined back to the context's stream), so the copies overlap on several copy engines.  When
-// the treecode's near field ran in z slabs, each slab's planes of every site are copied as soon as the slab's
-// event has fired, while the later slabs are still being evaluated; otherwise the whole grids after the step.
+// the treecode's far and near fields ran in z slabs, each slab's planes of every site are copied as soon as the
+// slab's event has fired, while the later slabs are still being evaluated; otherwise the whole grids after the
+// step.
 rism_status copy_outputs(rism_ctx* c, double* const (&user)[3], double* const (&dev)[3], const bool (&staged)[3],
                          size_t bytes) {
     cudaError_t e = cudaSuccess;
@@ -386,7 +387,8 @@ rism_status rism_init(rism_ctx* c, double* u, double* c_lr, double* h_lr, double
         }
     }
     Outputs o{dev[0], dev[1], dev[2]};
-    // host outputs: the treecode's near field runs in z slabs whose copies overlap the rest of the evaluation
+    // host outputs: the treecode's far and near fields run in z slabs whose copies overlap the rest of the
+    // evaluation
     if (c->o.method == RISM_METHOD_TREECODE && c->tree &&
         (s = tree_set_slabs(c->tree, host_out ? kOutSlabs : 1, c->err)) != RISM_OK)
         return fail(c, s, c->err);

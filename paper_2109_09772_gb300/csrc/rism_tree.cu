@@ -1378,9 +1378,9 @@ __global__ void __launch_bounds__(32 * kListWarps) k_near_lists(ListArgs a, cons
 // Launch order of the batches, heaviest first: a counting sort of the batches by the binary order of magnitude
 // of their work (one CTA per list: CTA 0 orders work0 into order0, CTA 1 work1 into order1).  The order changes
 // nothing but which CTAs start first (each batch is computed independently), so long batches do not trail at
-// the end of the launch.  With nslab > 1, order0 is sorted by z slab first: slab k holds the batch layers
+// the end of the launch.  With nslab > 1, both orders are sorted by z slab first: slab k holds the batch layers
 // kb with floor(kb nslab / nbz) = k, and its batches (heaviest first) fill positions [kb_k nbxy, kb_(k+1) nbxy),
-// kb_k = ceil(k nbz / nslab), so each slab can run as a launch of its own.
+// kb_k = ceil(k nbz / nslab), so each slab can run as launches of its own.
 constexpr int kOrderBuckets = 33;
 constexpr int kMaxSlabs = 16;
 __global__ void __launch_bounds__(1024) k_order(int nb, const int* __restrict__ work0, int* order0,
@@ -1389,7 +1389,7 @@ __global__ void __launch_bounds__(1024) k_order(int nb, const int* __restrict__ 
     __shared__ int hist[kOrderBuckets * kMaxSlabs], start[kOrderBuckets * kMaxSlabs];
     const int* __restrict__ work = blockIdx.x == 0 ? work0 : work1;
     int* order = blockIdx.x == 0 ? order0 : order1;
-    const int ns = blockIdx.x == 0 ? nslab : 1;
+    const int ns = nslab;
     const int nkey = kOrderBuckets * ns;
     const int tid = threadIdx.x;
     for (int k = tid; k < nkey; k += blockDim.x) hist[k] = 0;
@@ -1462,6 +1462,7 @@ struct EvalArgs {
     const int* near_order; // work item -> batch of the per-solute near kernel (heaviest first)
     int* wq;               // [2] work queue of the persistent near kernel: items taken, CTAs done (0 between launches)
     int q0, q1;            // positions [q0, q1) of the near order (in sub-batches) that this near launch takes
+    int f0;                // first position of the far order that this far launch takes (one CTA per batch)
     const int* far_order;  // the same for the far kernel
     const int* near_work;  // per batch: candidate atoms of the near list
     const int* far_work;   // per batch: atoms and proxies of the far list
@@ -2749,7 +2750,7 @@ __global__ void __launch_bounds__(FarShape<NXB, NYB, NZB, PF>::NTP) k_far32(Eval
     __shared__ PairRec pairs[FarShape<NXB, NYB, NZB, PF>::NW][kPairs];
     if (threadIdx.x == 0) r.inited = 0;
     if (a.meta->overflow) return;  // incomplete lists: the host grows them and runs again
-    far_body<NXB, NYB, NZB, PF, DH>(a, a.far_order[blockIdx.x], r, pairs);
+    far_body<NXB, NYB, NZB, PF, DH>(a, a.far_order[a.f0 + blockIdx.x], r, pairs);
 }
 
 // Register cap (resident CTAs of consumer warps + producer warp) for up to 4 sites: 3 when only u or only the
@@ -3827,6 +3828,7 @@ EvalArgs make_args(TreeState* s, const DevTables& t, const GridD& g, const Phys&
     a.wq = s->wq;
     a.q0 = 0;
     a.q1 = s->nb * (shape_of(s->variant).nx / 8);  // sub-batches of 8 points along x
+    a.f0 = 0;
     a.far_order = s->far_order;
     a.near_work = s->near_work;
     a.far_work = s->far_work;
@@ -4109,15 +4111,19 @@ static rism_status tree_autotune(TreeState* s, const DevTables& t, const GridD& 
     return r != RISM_OK ? r : tree_enqueue(s, t, g, ph, o, st, err);
 }
 
-// The near kernel (+ epilogue) as one launch, or as one launch per z slab of batch layers (s->nslab > 1), each
-// followed by a record of its slab event; external records when the launches are being captured into a graph,
-// so that streams outside the graph can wait on a slab.
+// The far and near kernels (+ epilogue) as one launch each, or per z slab of batch layers (s->nslab > 1): the
+// far and then the near launch of each slab, followed by a record of the slab's event (external records when the
+// launches are being captured into a graph, so that streams outside the graph can wait on a slab).  The first
+// slab's outputs are then complete after a slab's share of both kernels, not after the whole far field.
 namespace {
-cudaError_t near_enqueue(TreeState* s, int smax, const EvalArgs& a, bool du, bool dh, cudaStream_t st,
-                         bool captured) {
+cudaError_t farnear_enqueue(TreeState* s, int smax, const EvalArgs& a, bool du, bool dh, cudaStream_t st,
+                            bool captured, cudaEvent_t mid = nullptr) {
     if (s->nslab <= 1) {
         s->slabs_live = false;
-        return dispatch(smax, s->variant, 3, du, dh, &a, s->nb, nullptr, 0, st);
+        cudaError_t e = dispatch(smax, s->variant, 2, du, dh, &a, s->nb, nullptr, 0, st);
+        if (e == cudaSuccess && mid)
+            e = captured ? cudaEventRecordWithFlags(mid, st, cudaEventRecordExternal) : cudaEventRecord(mid, st);
+        return e == cudaSuccess ? dispatch(smax, s->variant, 3, du, dh, &a, s->nb, nullptr, 0, st) : e;
     }
     const int NS = shape_of(s->variant).nx / 8, nbxy = s->nbx * s->nby;
     cudaError_t e = cudaSuccess;
@@ -4126,14 +4132,18 @@ cudaError_t near_enqueue(TreeState* s, int smax, const EvalArgs& a, bool du, boo
         const int kb1 = (int)(((int64_t)(k + 1) * s->nbz + s->nslab - 1) / s->nslab);
         if (kb1 > kb0) {
             EvalArgs b = a;
+            b.f0 = kb0 * nbxy;
             b.q0 = kb0 * nbxy * NS;
             b.q1 = kb1 * nbxy * NS;
-            e = dispatch(smax, s->variant, 3, du, dh, &b, (kb1 - kb0) * nbxy, nullptr, 0, st);
+            e = dispatch(smax, s->variant, 2, du, dh, &b, (kb1 - kb0) * nbxy, nullptr, 0, st);
+            if (e == cudaSuccess) e = dispatch(smax, s->variant, 3, du, dh, &b, (kb1 - kb0) * nbxy, nullptr, 0, st);
         }
         if (e == cudaSuccess)
             e = captured ? cudaEventRecordWithFlags(s->slab_ev[k], st, cudaEventRecordExternal)
                          : cudaEventRecord(s->slab_ev[k], st);
     }
+    if (e == cudaSuccess && mid)  // no separate far time: the interleaved launches count as far + near
+        e = captured ? cudaEventRecordWithFlags(mid, st, cudaEventRecordExternal) : cudaEventRecord(mid, st);
     s->slabs_live = e == cudaSuccess;
     return e;
 }
@@ -4187,19 +4197,16 @@ rism_status tree_eval(TreeState* s, const DevTables& t, const GridD& g, const Ph
         cudaEventRecord(s->ev[0], st);
         cpl = cp_enqueue(s, a, dh, st);
         cudaEventRecord(s->ev[1], st);
-        e = dispatch(t.smax, s->variant, 2, du, dh, &a, s->nb, nullptr, 0, st);
-        cudaEventRecord(s->ev[2], st);
-        if (e == cudaSuccess) e = near_enqueue(s, t.smax, a, du, dh, st, false);
+        e = farnear_enqueue(s, t.smax, a, du, dh, st, false, s->ev[2]);
         cudaEventRecord(s->ev[3], st);
     } else {
         cpl = cp_enqueue(s, a, dh, st);
-        e = dispatch(t.smax, s->variant, 2, du, dh, &a, s->nb, nullptr, 0, st);
-        if (e == cudaSuccess) e = near_enqueue(s, t.smax, a, du, dh, st, false);
+        e = farnear_enqueue(s, t.smax, a, du, dh, st, false);
     }
     if (e != cudaSuccess) return cuda_err(err, e, "tree eval");
     if ((e = cudaMemcpyAsync(s->h_meta, s->meta, sizeof(TreeMeta), cudaMemcpyDeviceToHost, st)) != cudaSuccess)
         return cuda_err(err, e, "tree meta copy");
-    info.launches += s->launches + 1 + std::max(1, s->nslab) + cpl;
+    info.launches += s->launches + 2 * std::max(1, s->nslab) + cpl;
     const ShapeDesc sd = shape_of(s->variant);
     info.batch[0] = sd.nx;
     info.batch[1] = sd.ny;
@@ -4341,11 +4348,9 @@ rism_status tree_graph_step(TreeState* s, const DevTables& t, const GridD& g, co
             rec(0);
             launches += cp_enqueue(s, a, dh, cs);
             rec(1);
-            if (e == cudaSuccess) e = dispatch(t.smax, s->variant, 2, du, dh, &a, s->nb, nullptr, 0, cs);
-            rec(2);
-            if (e == cudaSuccess) e = near_enqueue(s, t.smax, a, du, dh, cs, true);
+            if (e == cudaSuccess) e = farnear_enqueue(s, t.smax, a, du, dh, cs, true, timed ? s->ev[2] : nullptr);
             rec(3);
-            launches += 1 + std::max(1, s->nslab);
+            launches += 2 * std::max(1, s->nslab);
         }
         if (tail) cudaStreamWaitEvent(cs, G->join, 0);
         if (e == cudaSuccess && r == RISM_OK)

@@ -59,9 +59,10 @@ rism_status tree_graph_step(TreeState* ts, const DevTables& t, const GridD& g, c
 // Drop the captured solute graph (buffers moved or the retry path ran).
 void tree_graph_reset(TreeState* ts);
 
-// Split the near kernel of the following evaluations into nslab launches over z slabs of batch layers (1: one
-// launch), each followed by a record of a slab event, so that copies of a finished slab's outputs can overlap
-// the rest of the evaluation.  The slab count is part of the solute graph's signature.
+// Split the far and near kernels of the following evaluations into nslab pairs of launches over z slabs of
+// batch layers (1: one launch each), each pair followed by a record of a slab event, so that copies of a
+// finished slab's outputs can overlap the rest of the evaluation.  The slab count is part of the solute graph's
+// signature.  With slabs, rism_info's far time covers the far and near launches together (near time 0).
 rism_status tree_set_slabs(TreeState* ts, int nslab, std::string& err);
 // After tree_eval or tree_graph_step enqueued an evaluation with slabs: their number, the grid planes
 // [z[k][0], z[k][1]) whose outputs slab k completes, and the event recorded after it; 0 without slabs.
