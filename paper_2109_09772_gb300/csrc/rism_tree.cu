@@ -1305,8 +1305,15 @@ __global__ void __launch_bounds__(32 * kListWarps) k_tbox_lists(TListArgs a, con
 // Near lists: one warp per target batch; lanes test the cells of the box
 // grown by rnear (x fastest), keep those whose box lies within rnear of the
 // batch box, and emit their atom ranges in cell order.
+// Up to kNearSort entries of a near list are sorted by their first atom in shared memory and contiguous ranges
+// merged: the cells of a batch's neighbourhood hold an atom or two each, and a tile built from one range per cell
+// takes a bulk copy per atom, which starves the near kernel's consumers; neighbouring cells are mostly
+// neighbours in the Morton order of the sorted atoms too, so merged ranges hold many cells.
+constexpr int kNearSort = 512;
+
 __global__ void __launch_bounds__(32 * kListWarps) k_near_lists(ListArgs a, const int* __restrict__ cell_start,
                                                                int2* ent, int* cnt, int* work, TreeMeta* meta) {
+    __shared__ int2 sbuf[kListWarps][kNearSort];
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     const int nb = a.nbx * a.nby * a.nbz;
     const int lc = meta->lc, ncell = 1 << lc;
@@ -1363,9 +1370,49 @@ __global__ void __launch_bounds__(32 * kListWarps) k_near_lists(ListArgs a, cons
             m += __popc(em);
         }
         for (int o = 16; o > 0; o >>= 1) cand += __shfl_xor_sync(0xffffffffu, cand, o);
+        int mout = m;  // entries written
+        if (m > 1 && m <= a.cap && m <= kNearSort) {
+            // bitonic sort of the entries by first atom (padded to a power of two with empty ranges at the end)
+            int P = 1;
+            while (P < m) P <<= 1;
+            int2* sb = sbuf[w];
+            __syncwarp();
+            for (int i = lane; i < P; i += 32) sb[i] = i < m ? out[i] : make_int2(INT_MAX, 0);
+            __syncwarp();
+            for (int k = 2; k <= P; k <<= 1)
+                for (int j = k >> 1; j > 0; j >>= 1) {
+                    for (int t = lane; t < P / 2; t += 32) {
+                        const int i = ((t & ~(j - 1)) << 1) | (t & (j - 1)), l = i + j;
+                        const int2 x = sb[i], y = sb[l];
+                        if ((x.x > y.x) == ((i & k) == 0)) {
+                            sb[i] = y;
+                            sb[l] = x;
+                        }
+                    }
+                    __syncwarp();
+                }
+            // merge: an entry that starts where the previous one ends continues its range; each run's first entry
+            // writes the start, its last entry the length
+            int runs = 0;
+            for (int i0 = 0; i0 < m; i0 += 32) {
+                const int i = i0 + lane;
+                const bool in = i < m;
+                const int2 e = in ? sb[i] : make_int2(0, 0);
+                const bool head = in && (i == 0 || sb[i - 1].x + sb[i - 1].y != e.x);
+                const unsigned hm = __ballot_sync(0xffffffffu, head);
+                const int r = runs + __popc(hm & ((2u << lane) - 1u)) - 1;  // run of entry i
+                if (head) out[r].x = e.x;
+                runs += __popc(hm);
+                __syncwarp();
+                const bool tail = in && (i == m - 1 || sb[i + 1].x != e.x + e.y);
+                if (tail) out[r].y = e.x + e.y - out[r].x;
+                __syncwarp();
+            }
+            mout = runs;
+        }
         if (lane == 0) {
             work[b] = (int)min(cand, (long long)INT_MAX);
-            cnt[b] = min(m, a.cap);
+            cnt[b] = min(mout, a.cap);
             if (m > a.cap) {
                 meta->overflow = 1;
                 atomicMax(&meta->near_need, m);
@@ -2357,7 +2404,8 @@ __device__ __forceinline__ void near_tile(const SrcF* __restrict__ Sx, const LJf
                                           const float (&gx)[P], float fy, float fz, float rn2, float rs2, float rcu2,
                                           float tinv, const float4* tab, bool DC, float c0h, float h0h,
                                           const float (&wlo)[3], const float (&whi)[3], float rcull2,
-                                          float (&psc)[P], float (&psh)[P], float (&plj)[P][SM], unsigned& hit,
+                                          float (&sch)[P], float (&scl)[P], float (&shh)[P], float (&shl)[P],
+                                          float (&plj)[P][SM], unsigned& hit,
                                           unsigned (&cnt3)[3]) {
     // Warp-parallel culling of the tile: lane l tests sources l and l + 32 against the warp's point box; the
     // ballots list the survivors, which every lane then visits in tile order.  A culled source has no point
@@ -2399,16 +2447,16 @@ __device__ __forceinline__ void near_tile(const SrcF* __restrict__ Sx, const LJf
                     const float tt = seg_split(uu, it);
                     if (DC) {
                         const float4 cc = tab[2 * it];
-                        psc[p] = fmaf(qr, fmaf(fmaf(fmaf(cc.w, tt, cc.z), tt, cc.y), tt, cc.x), psc[p]);
+                        ff_add(sch[p], scl[p], qr * fmaf(fmaf(fmaf(cc.w, tt, cc.z), tt, cc.y), tt, cc.x));
                     }
                     if (DH) {
                         const float4 ch = tab[2 * it + 1];
-                        psh[p] = fmaf(qr, fmaf(fmaf(fmaf(ch.w, tt, ch.z), tt, ch.y), tt, ch.x), psh[p]);
+                        ff_add(shh[p], shl[p], qr * fmaf(fmaf(fmaf(ch.w, tt, ch.z), tt, ch.y), tt, ch.x));
                     }
                 } else {
                     hit |= 1u << p;
-                    if (DC) psc[p] -= g0.w * c0h;
-                    if (DH) psh[p] -= g0.w * h0h;
+                    if (DC) ff_add(sch[p], scl[p], -(g0.w * c0h));
+                    if (DH) ff_add(shh[p], shl[p], -(g0.w * h0h));
                 }
             }
             if (DU) {
@@ -2447,7 +2495,8 @@ __device__ __forceinline__ void near_tile_uni2(const SrcF* __restrict__ Sx, cons
                                                const float (&gx)[2], float fy, float fz, float rn2, float rs2,
                                                float rcu2, float tinv, const float4* tab, bool DC, float c0h,
                                                float h0h, const float (&wlo)[3], const float (&whi)[3], float rcull2,
-                                               float (&psc)[2], float (&psh)[2], float (&plj)[2][SM], unsigned& hit,
+                                               float (&sch)[2], float (&scl)[2], float (&shh)[2], float (&shl)[2],
+                                               float (&plj)[2][SM], unsigned& hit,
                                                unsigned (&cnt3)[3]) {
     // the tile's sources that survive the culling, listed per warp in tile order (kernels of up to 16 warps)
     __shared__ int wl_all[16][kT];
@@ -2512,16 +2561,16 @@ __device__ __forceinline__ void near_tile_uni2(const SrcF* __restrict__ Sx, cons
                     const float tt = seg_split(uu, it);
                     if (DC) {
                         const float4 cc = tab[2 * it];
-                        psc[p] = fmaf(qr, fmaf(fmaf(fmaf(cc.w, tt, cc.z), tt, cc.y), tt, cc.x), psc[p]);
+                        ff_add(sch[p], scl[p], qr * fmaf(fmaf(fmaf(cc.w, tt, cc.z), tt, cc.y), tt, cc.x));
                     }
                     if (DH) {
                         const float4 ch = tab[2 * it + 1];
-                        psh[p] = fmaf(qr, fmaf(fmaf(fmaf(ch.w, tt, ch.z), tt, ch.y), tt, ch.x), psh[p]);
+                        ff_add(shh[p], shl[p], qr * fmaf(fmaf(fmaf(ch.w, tt, ch.z), tt, ch.y), tt, ch.x));
                     }
                 } else {
                     hit |= 1u << p;
-                    if (DC) psc[p] -= q * c0h;
-                    if (DH) psh[p] -= q * h0h;
+                    if (DC) ff_add(sch[p], scl[p], -(q * c0h));
+                    if (DH) ff_add(shh[p], shl[p], -(q * h0h));
                 }
             }
         }
@@ -2628,23 +2677,23 @@ __device__ __forceinline__ void near_begin(NearPts<SM>& q, const EvalArgs& a, in
 template <int SM, bool DU, bool DH>
 __device__ __forceinline__ void near_stage(NearPts<SM>& q, const NearConst& c, const SrcF* Sx, const LJf* L, int cnt,
                                            const float4* tab, unsigned (&cnt3)[3]) {
-    float psc[2], psh[2], plj[2][SM];
+    float plj[2][SM];
 #pragma unroll
     for (int p = 0; p < 2; ++p) {
-        psc[p] = psh[p] = 0.f;
 #pragma unroll
         for (int s = 0; s < SM; ++s) plj[p][s] = 0.f;
     }
+    // the short-range remainders go straight into the float-pair sums (they nearly cancel the far field next
+    // to an atom, so an FP32 partial sum of a tile's terms would lose the digits that survive the cancellation)
     if (c.uni)
         near_tile_uni2<SM, DU, DH>(Sx, L, cnt, q.gx, q.fy, q.fz, c.rn2, c.rs2, c.rcu2, c.tinv, tab, c.DC, c.c0h,
-                                   c.h0h, q.wlo, q.whi, c.rcull2, psc, psh, plj, q.hit, cnt3);
+                                   c.h0h, q.wlo, q.whi, c.rcull2, q.sch, q.scl, q.shh, q.shl, plj, q.hit, cnt3);
     else
         near_tile<2, SM, DU, DH, false>(Sx, L, cnt, q.gx, q.fy, q.fz, c.rn2, c.rs2, c.rcu2, c.tinv, tab, c.DC, c.c0h,
-                                        c.h0h, q.wlo, q.whi, c.rcull2, psc, psh, plj, q.hit, cnt3);
+                                        c.h0h, q.wlo, q.whi, c.rcull2, q.sch, q.scl, q.shh, q.shl, plj, q.hit,
+                                        cnt3);
 #pragma unroll
     for (int p = 0; p < 2; ++p) {
-        if (c.DC) ff_add(q.sch[p], q.scl[p], psc[p]);
-        if (DH) ff_add(q.shh[p], q.shl[p], psh[p]);
         if (DU) {
 #pragma unroll
             for (int s = 0; s < SM; ++s) ff_add(q.ljh[p][s], q.ljl[p][s], plj[p][s]);
