@@ -29,7 +29,6 @@ struct rism_ctx {
 
     // host copies of the inputs
     int64_t n = 0;
-    std::vector<double> raw;  // [n][6] x, y, z, q, sigma, eps
     int S = 0;
     double qs[kMaxSites] = {}, sigs[kMaxSites] = {}, epss[kMaxSites] = {}, rho[kMaxSites] = {};
     int is_ion[kMaxSites] = {};
@@ -44,7 +43,10 @@ struct rism_ctx {
     DevErr* d_err = nullptr;
     DevErr* h_err = nullptr;  // pinned
     double* d_tail = nullptr;
-    double* h_raw = nullptr;  // pinned copy of raw for the graph-replayed step
+    // the solute, [n][6] x, y, z, q, sigma, eps, in page-locked host memory: uploaded as it stands (by the
+    // replayed graph's copy node or an asynchronous copy); every entry point that uploads it synchronises its
+    // stream before it returns, so rism_set_solute never overwrites it under a copy of a completed call
+    double* h_raw = nullptr;
     int64_t cap_h_raw = 0;
     double* h_tail = nullptr;  // pinned [RISM_MAX_SITES]
     double* d_stage[3] = {nullptr, nullptr, nullptr};
@@ -163,7 +165,7 @@ rism_status ensure_tables(rism_ctx* c) {
     if (rs != RISM_OK) return rs;
     const int smax = c->t.smax;
     if (c->n > 0) {
-        if ((e = cudaMemcpyAsync(c->d_raw, c->raw.data(), sizeof(double) * 6 * c->n, cudaMemcpyHostToDevice,
+        if ((e = cudaMemcpyAsync(c->d_raw, c->h_raw, sizeof(double) * 6 * c->n, cudaMemcpyHostToDevice,
                                  c->st)) != cudaSuccess)
             return cuda_fail(c, e, "uploading solute");
         if ((e = launch_setup(c->d_raw, c->n, c->S, smax, c->sigs, c->epss, c->o.lj_mode, c->o.lj_rcut,
@@ -261,14 +263,24 @@ rism_status rism_set_solute(rism_ctx* c, int64_t n, const double* xyz, const dou
                             const double* eps) {
     if (!c) return RISM_E_INVALID;
     if (const char* m = check_host_solute(n, xyz, q, sigma, eps)) return fail(c, RISM_E_INVALID, m);
-    c->raw.assign((size_t)(6 * n), 0.0);
+    if (n > c->cap_h_raw) {
+        cudaFreeHost(c->h_raw);
+        c->h_raw = nullptr;
+        c->cap_h_raw = 0;
+        c->n = 0;
+        c->have_solute = false;
+        const cudaError_t e = cudaMallocHost(&c->h_raw, sizeof(double) * 6 * n);
+        if (e != cudaSuccess) return cuda_fail(c, e, "page-locked solute buffer");
+        c->cap_h_raw = n;
+    }
+    double* raw = c->h_raw;
     for (int64_t i = 0; i < n; ++i) {
-        c->raw[6 * i + 0] = xyz[3 * i + 0];
-        c->raw[6 * i + 1] = xyz[3 * i + 1];
-        c->raw[6 * i + 2] = xyz[3 * i + 2];
-        c->raw[6 * i + 3] = q[i];
-        c->raw[6 * i + 4] = sigma[i];
-        c->raw[6 * i + 5] = eps[i];
+        raw[6 * i + 0] = xyz[3 * i + 0];
+        raw[6 * i + 1] = xyz[3 * i + 1];
+        raw[6 * i + 2] = xyz[3 * i + 2];
+        raw[6 * i + 3] = q[i];
+        raw[6 * i + 4] = sigma[i];
+        raw[6 * i + 5] = eps[i];
     }
     c->n = n;
     c->have_solute = true;
@@ -399,15 +411,6 @@ rism_status rism_init(rism_ctx* c, double* u, double* c_lr, double* h_lr, double
     if (c->o.method == RISM_METHOD_TREECODE && any_out) ++c->tree_calls;
     if (c->o.method == RISM_METHOD_TREECODE && c->dirty && c->n > 0 && any_out && c->tree_calls > 1) {
         if ((s = reserve_tables(c)) != RISM_OK) return s;
-        if (c->cap_h_raw < c->n) {
-            cudaFreeHost(c->h_raw);
-            c->h_raw = nullptr;
-            c->cap_h_raw = 0;
-            if ((e = cudaMallocHost(&c->h_raw, sizeof(double) * 6 * c->n)) != cudaSuccess)
-                return cuda_fail(c, e, "pinned solute buffer");
-            c->cap_h_raw = c->n;
-        }
-        std::memcpy(c->h_raw, c->raw.data(), sizeof(double) * 6 * c->n);
         const bool tail = lj_tail && c->o.lj_mode != RISM_LJ_NONE;
         SoluteStep step{c->h_raw, c->d_raw, c->n, c->sigs, c->epss, c->o.lj_mode, c->o.lj_rcut, c->o.lj_tol,
                         tail ? c->d_tail : nullptr, c->h_tail};
@@ -562,7 +565,7 @@ rism_status rism_potential_batched(rism_ctx* const* ctxs, int32_t count, double*
         // allocations and the solute upload happen here, outside the captured graph
         rism_status s = reserve_tables(c);
         if (s != RISM_OK) return fail(c0, s, c->err);
-        if (c->n > 0 && (e = cudaMemcpyAsync(c->d_raw, c->raw.data(), sizeof(double) * 6 * c->n,
+        if (c->n > 0 && (e = cudaMemcpyAsync(c->d_raw, c->h_raw, sizeof(double) * 6 * c->n,
                                              cudaMemcpyHostToDevice, c0->st)) != cudaSuccess)
             return cuda_fail(c0, e, "uploading solute");
         BatchItem it;
@@ -692,7 +695,7 @@ rism_status rism_asymptotics_k(rism_ctx* c, double k_tol, double* c_k, double* h
         if (k < c->S) ks.qmax = std::max(ks.qmax, std::fabs(c->qs[k]));
     }
     ks.qabs = 0.0;
-    for (int64_t i = 0; i < c->n; ++i) ks.qabs += std::fabs(c->raw[6 * i + 3]);
+    for (int64_t i = 0; i < c->n; ++i) ks.qabs += std::fabs(c->h_raw[6 * i + 3]);
     ks.kcut = k_tol > 0.0 ? kspace_kcut(ks, k_tol) : 0.0;
     if (k_cut) *k_cut = ks.kcut;
     if (!c_k && !h_k) return RISM_OK;

@@ -75,10 +75,15 @@ inline const char* check_host_solute(int64_t n, const double* xyz, const double*
     if (n > 0 && (!xyz || !q || !sigma || !eps)) return "NULL solute array";
     if (n > (1LL << 31)) return "too many atoms";
     if (n == 0) return nullptr;
-    if (!finite_all(xyz, 3 * n) || !finite_all(q, n) || !finite_all(sigma, n) || !finite_all(eps, n))
-        return "NaN or Inf in solute";
-    for (int64_t i = 0; i < n; ++i)
-        if (sigma[i] < 0.0 || eps[i] < 0.0) return "negative sigma or eps";
+    // one pass over the atoms (this runs on every solute update, before the GPU gets the step)
+    bool finite = true, nonneg = true;
+    for (int64_t i = 0; i < n; ++i) {
+        finite &= std::isfinite(xyz[3 * i]) & std::isfinite(xyz[3 * i + 1]) & std::isfinite(xyz[3 * i + 2]) &
+                  std::isfinite(q[i]) & std::isfinite(sigma[i]) & std::isfinite(eps[i]);
+        nonneg &= (sigma[i] >= 0.0) & (eps[i] >= 0.0);
+    }
+    if (!finite) return "NaN or Inf in solute";
+    if (!nonneg) return "negative sigma or eps";
     return nullptr;
 }
 
