@@ -1485,7 +1485,7 @@ __global__ void k_reset_meta(TreeMeta* meta) {
 // Sources reach shared memory through bulk TMA copies issued by one producer
 // lane into a kStages-deep ring of tiles guarded by full (copy landed) and empty
 // (all warps done) mbarriers; every wait is bounded.
-constexpr int kStages = 3;
+constexpr int kStages = 4;
 constexpr int kNTab = 128;  // segments of the short-range kernel tables over [0, r_short]
 
 struct EvalArgs {
@@ -2826,7 +2826,7 @@ struct NearOcc {
     static constexpr int v = SM <= 4 ? ((DU && DH) ? 2 : 3) : 1;
 };
 
-constexpr int kFarBuf = 4;  // far-field record buffers of the persistent near kernel (sub-batches in flight)
+constexpr int kFarBuf = 5;  // far-field record buffers of the persistent near kernel (sub-batches in flight)
 
 // Persistent near-field kernel of one solute: the producer of each CTA takes the next item (sub-batch) of the
 // heaviest-first order from the work queue and streams the near lists of its items through one ring
@@ -2839,9 +2839,9 @@ __global__ void __launch_bounds__(NearShape<NXB, NYB, NZB>::NTP, (NearOcc<NXB, N
     __shared__ Ring<SM, true> r;
     __shared__ float4 tab[2 * kNTab];
     // far-field records of the last kFarBuf sub-batches (one 8x8x8 block of the far buffer each), copied by the
-    // producer with each sub-batch's first tile.  It runs at most kStages = 3 tiles, so 3 sub-batches, ahead of
-    // the slowest warp, whose epilogue reads sub-batch n - 4's buffer before it releases the tile that lets the
-    // producer start sub-batch n.
+    // producer with each sub-batch's first tile.  It runs at most kStages tiles, so kStages sub-batches, ahead
+    // of the slowest warp, whose epilogue reads sub-batch n - kFarBuf's buffer before it releases the tile that
+    // lets the producer start sub-batch n.
     static_assert(Sh::SX == 8 && NYB == 8 && NZB == 8, "a sub-batch is one 8x8x8 block of the far buffer");
     static_assert(kStages <= kFarBuf - 1, "the far-field buffers cover the sub-batches the producer runs ahead");
     extern __shared__ __align__(16) float4 farbuf[];  // [kFarBuf][512], dynamic
