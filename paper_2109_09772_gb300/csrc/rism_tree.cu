@@ -1991,9 +1991,9 @@ __device__ __forceinline__ void stage_rel(const SrcF* __restrict__ Sx, int cnt, 
 }
 
 template <int P, bool DH>
-__device__ __forceinline__ void cp_pairs(const RelRec* wp, int np, const f32x2 (&GX)[P], f32x2 FY, f32x2 FZ,
-                                         f32x2 K2, f32x2 (&P1)[P], f32x2 (&PK)[P]) {
-    for (int l = 0; l < np; ++l) {
+__device__ __forceinline__ void cp_pairs(const RelRec* wp, int l0, int np, int stride, const f32x2 (&GX)[P], f32x2 FY,
+                                         f32x2 FZ, f32x2 K2, f32x2 (&P1)[P], f32x2 (&PK)[P]) {
+    for (int l = l0; l < np; l += stride) {
         const ulonglong2 A = *reinterpret_cast<const ulonglong2*>(&wp[l].xy);
         const ulonglong2 B = *reinterpret_cast<const ulonglong2*>(&wp[l].zq);
         const f32x2 DY = sub2(FY, A.y);
@@ -2024,11 +2024,14 @@ constexpr int kCPOrderBoxes = 1024;  // boxes from which the box-level launch ru
 // One CTA per (target box, list chunk, pass): the box's accepted atoms split into up to kCPChunks chunks of
 // at least kCPChunkMin atoms; the (n+1)^2 proxy lines of the box split into chunks of kCPP nodes along x,
 // kCPThreads chunks per pass.  Sources stream through the TMA ring.  Chunk 0 writes the box's proxy values,
-// later chunks their partial sums (added in chunk order by k_cp_reduce).
+// later chunks their partial sums (added in chunk order by k_cp_reduce).  At low degree a box has few proxy
+// chunks (50 at degree 4): then G = kCPThreads / chunks groups of threads share them, group g taking the source
+// pairs g, g + G, ..., and the groups' float-pair sums are added in group order at the end.
 template <bool DH>
 __global__ void __launch_bounds__(kCPThreads + 32) k_cp_eval(EvalArgs a, CPArgs c) {
     __shared__ Ring<1, false> r;
     __shared__ RelRec pairs[kCPThreads / 32][kPairs];
+    __shared__ float4 gsum[kCPThreads][kCPP];  // the groups' sums (G > 1): f1h, f1l, fkh, fkl
     __shared__ int s_e, s_off, s_len, s_nch;
     constexpr int NW = kCPThreads / 32;
     const int tid = threadIdx.x, lane = tid & 31;
@@ -2076,8 +2079,10 @@ __global__ void __launch_bounds__(kCPThreads + 32) k_cp_eval(EvalArgs a, CPArgs 
     }
     float2* out = chunk == 0 ? c.tpot + (int64_t)box * P3
                              : c.tpart + ((int64_t)box * (kCPChunks - 1) + chunk - 1) * P3;
-    const int task = pass * kCPThreads + tid;
-    const bool act = tid < kCPThreads && task < ntask;
+    const int G = 2 * ntask <= kCPThreads ? kCPThreads / ntask : 1;  // thread groups sharing the proxy chunks
+    const int grp = G > 1 && tid < G * ntask ? tid / ntask : 0;
+    const int task = G > 1 ? tid % ntask : pass * kCPThreads + tid;
+    const bool act = tid < kCPThreads && (G > 1 ? tid < G * ntask : task < ntask);
     const int tk = act ? task : 0;
     const int line = tk / nxc, xc = tk % nxc, ky = line % n1, kz = line / n1;
     const float hx = 0.5f * (T.ext[0] - 1), hy = 0.5f * (T.ext[1] - 1), hz = 0.5f * (T.ext[2] - 1);
@@ -2122,7 +2127,7 @@ __global__ void __launch_bounds__(kCPThreads + 32) k_cp_eval(EvalArgs a, CPArgs 
             f32x2 P1[kCPP], PK[kCPP];
 #pragma unroll
             for (int p = 0; p < kCPP; ++p) P1[p] = PK[p] = 0ull;
-            cp_pairs<kCPP, DH>(wp, (n + 1) >> 1, GX, FY, FZ, K2, P1, PK);
+            cp_pairs<kCPP, DH>(wp, grp, (n + 1) >> 1, G, GX, FY, FZ, K2, P1, PK);
 #pragma unroll
             for (int p = 0; p < kCPP; ++p) {
                 const float2 s1 = up2(P1[p]);
@@ -2133,7 +2138,26 @@ __global__ void __launch_bounds__(kCPThreads + 32) k_cp_eval(EvalArgs a, CPArgs 
                 }
             }
         });
-    if (rr != kRingDone || !act) return;
+    if (G > 1) {
+        // every consumer warp leaves the ring (done or aborted, its waits are bounded) and meets the others here
+        if (rr == kRingProducer) return;
+        if (act && grp > 0)
+#pragma unroll
+            for (int p = 0; p < kCPP; ++p) gsum[tid][p] = make_float4(f1h[p], f1l[p], fkh[p], fkl[p]);
+        asm volatile("bar.sync 1, %0;" ::"r"(kCPThreads) : "memory");
+        if (rr != kRingDone || !act || grp > 0) return;
+        for (int g = 1; g < G; ++g)
+#pragma unroll
+            for (int p = 0; p < kCPP; ++p) {
+                const float4 o = gsum[g * ntask + tid][p];
+                ff_add(f1h[p], f1l[p], o.x);
+                f1l[p] += o.y;
+                ff_add(fkh[p], fkl[p], o.z);
+                fkl[p] += o.w;
+            }
+    } else if (rr != kRingDone || !act) {
+        return;
+    }
 #pragma unroll
     for (int p = 0; p < kCPP; ++p) {
         const int kx = xc * kCPP + p;
