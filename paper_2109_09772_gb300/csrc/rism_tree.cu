@@ -2127,7 +2127,9 @@ __global__ void __launch_bounds__(kCPThreads + 32) k_cp_eval(EvalArgs a, CPArgs 
             f32x2 P1[kCPP], PK[kCPP];
 #pragma unroll
             for (int p = 0; p < kCPP; ++p) P1[p] = PK[p] = 0ull;
-            cp_pairs<kCPP, DH>(wp, grp, (n + 1) >> 1, G, GX, FY, FZ, K2, P1, PK);
+            // the unit-stride call is its own loop (a runtime stride costs the degree-8 loop 9%)
+            if (G == 1) cp_pairs<kCPP, DH>(wp, 0, (n + 1) >> 1, 1, GX, FY, FZ, K2, P1, PK);
+            else cp_pairs<kCPP, DH>(wp, grp, (n + 1) >> 1, G, GX, FY, FZ, K2, P1, PK);
 #pragma unroll
             for (int p = 0; p < kCPP; ++p) {
                 const float2 s1 = up2(P1[p]);
