@@ -162,11 +162,11 @@ FP32_LANES_PER_SM = 128
 SMS = 152
 # DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum of one ncu capture of the kernel as it
 # stands), per workload; None when the kernel has changed since the capture or no capture was taken.
-# "box" sums the box-level launches of one step (k_cp_eval, k_cp_reduce, k_l2l per level, k_tdown); summarised
-# with the commands in profiles/launches_<workload>.md.
+# "box" sums the box-level launches of one step (k_cp_work and its k_order where the boxes are ordered,
+# k_cp_eval, k_cp_reduce, k_l2l per level, k_tdown).
 TRAFFIC_BYTES = {
-    "ellipsoid13600_224x192x160": {"k_far32": 162919168, "k_near32": 726142720, "box": 100232960},
-    "globule2000_128cubed": {"k_far32": 33917952, "k_near32": 178510336, "box": 15797504},
+    "ellipsoid13600_224x192x160": {"k_far32": 163688192, "k_near32": 719262464, "box": 125491968},
+    "globule2000_128cubed": {"k_far32": 34168064, "k_near32": 185520128, "box": 17669632},
 }
 
 
