@@ -69,6 +69,13 @@ struct rism_ctx {
     int64_t lra_atom_cap = 0;
     double* d_lra_tot = nullptr;
     double* h_lra_tot = nullptr;  // pinned [3]
+    // the atoms in a spatial order for the pair sum (position -> original index), recomputed for a new solute
+    int* h_lra_perm = nullptr;    // pinned [lra_perm_cap]
+    int* d_lra_perm = nullptr;
+    void* d_lra_src = nullptr;    // the sorted source table
+    int64_t lra_perm_cap = 0;
+    int64_t lra_perm_version = -1;
+    int64_t solute_version = 0;   // incremented by every rism_set_solute
     // reciprocal-space asymptotics: per-atom phase tables and device staging for host outputs
     void* d_ktab = nullptr;
     size_t ktab_bytes = 0;
@@ -285,6 +292,7 @@ rism_status rism_set_solute(rism_ctx* c, int64_t n, const double* xyz, const dou
     c->n = n;
     c->have_solute = true;
     c->dirty = true;
+    ++c->solute_version;
     c->err.clear();
     return RISM_OK;
 }
@@ -607,6 +615,62 @@ rism_status rism_potential_batched(rism_ctx* const* ctxs, int32_t count, double*
     return fail(c0, RISM_E_NOMEM, "list buffers kept growing");
 }
 
+namespace {
+
+uint32_t spread10(uint32_t v) {  // the 10 low bits of v to every third bit
+    v &= 0x3ffu;
+    v = (v | (v << 16)) & 0x030000ffu;
+    v = (v | (v << 8)) & 0x0300f00fu;
+    v = (v | (v << 4)) & 0x030c30c3u;
+    v = (v | (v << 2)) & 0x09249249u;
+    return v;
+}
+
+// Spatial order of the atoms for the all-space pair sum: cells of about 32 atoms over the atoms' bounding box,
+// the cells in Morton order, the atoms of a cell in index order (a stable counting sort, O(n)).  A warp then
+// takes nearby targets and a tile nearby sources, so the costly short-range branch of the pair term is taken by
+// whole warps or by none.  perm[k] = original index of the atom at position k.
+void lra_order(const double* raw, int64_t n, int* perm) {
+    double lo[3] = {raw[0], raw[1], raw[2]}, hi[3] = {raw[0], raw[1], raw[2]};
+    for (int64_t i = 1; i < n; ++i)
+        for (int d = 0; d < 3; ++d) {
+            lo[d] = std::min(lo[d], raw[6 * i + d]);
+            hi[d] = std::max(hi[d], raw[6 * i + d]);
+        }
+    double ext[3], vol = 1.0;
+    for (int d = 0; d < 3; ++d) {
+        ext[d] = std::max(hi[d] - lo[d], 1e-6);
+        vol *= ext[d];
+    }
+    const double side = std::cbrt(vol / (double)std::max<int64_t>(1, n / 32));
+    int nc[3];
+    for (int d = 0; d < 3; ++d) nc[d] = std::max(1, std::min(1024, (int)std::ceil(ext[d] / side)));
+    const int64_t ncell = (int64_t)nc[0] * nc[1] * nc[2];
+    std::vector<uint64_t> key((size_t)ncell);
+    for (int z = 0; z < nc[2]; ++z)
+        for (int y = 0; y < nc[1]; ++y)
+            for (int x = 0; x < nc[0]; ++x) {
+                const uint64_t m = spread10((uint32_t)x) | (spread10((uint32_t)y) << 1) | (spread10((uint32_t)z) << 2);
+                const int64_t lin = ((int64_t)z * nc[1] + y) * nc[0] + x;
+                key[(size_t)lin] = (m << 32) | (uint64_t)lin;
+            }
+    std::sort(key.begin(), key.end());
+    std::vector<int> rank((size_t)ncell), start((size_t)ncell + 1, 0);
+    for (int64_t r = 0; r < ncell; ++r) rank[(size_t)(key[(size_t)r] & 0xffffffffu)] = (int)r;
+    std::vector<int> cell((size_t)n);
+    for (int64_t i = 0; i < n; ++i) {
+        int cc[3];
+        for (int d = 0; d < 3; ++d)
+            cc[d] = std::min(nc[d] - 1, std::max(0, (int)((raw[6 * i + d] - lo[d]) / side)));
+        cell[(size_t)i] = rank[(size_t)(((int64_t)cc[2] * nc[1] + cc[1]) * nc[0] + cc[0])];
+        ++start[(size_t)cell[(size_t)i] + 1];
+    }
+    for (int64_t r = 0; r < ncell; ++r) start[(size_t)r + 1] += start[(size_t)r];
+    for (int64_t i = 0; i < n; ++i) perm[start[(size_t)cell[(size_t)i]]++] = (int)i;
+}
+
+}  // namespace
+
 rism_status rism_lra_integral(rism_ctx* c, double* T, double* atom_sums) {
     if (!c) return RISM_E_INVALID;
     if (!T) return fail(c, RISM_E_INVALID, "T (host [S]) is required");
@@ -654,8 +718,30 @@ rism_status rism_lra_integral(rism_ctx* c, double* T, double* atom_sums) {
             (e = cudaMallocHost(&c->h_lra_tot, sizeof(double) * 3)) != cudaSuccess)
             return cuda_fail(c, e, "LRA totals");
     }
-    if ((e = launch_lra(c->t, c->gd, c->ph, sms, c->d_lra_part, c->d_lra_atom, c->d_lra_tot, c->o.wait_limit,
-                        c->st)) != cudaSuccess)
+    if (n > c->lra_perm_cap) {
+        cudaFree(c->d_lra_perm);
+        cudaFree(c->d_lra_src);
+        cudaFreeHost(c->h_lra_perm);
+        c->d_lra_perm = nullptr;
+        c->d_lra_src = nullptr;
+        c->h_lra_perm = nullptr;
+        c->lra_perm_cap = 0;
+        c->lra_perm_version = -1;
+        if ((e = cudaMalloc(&c->d_lra_perm, sizeof(int) * n)) != cudaSuccess ||
+            (e = cudaMalloc(&c->d_lra_src, sizeof(SrcF) * n)) != cudaSuccess ||
+            (e = cudaMallocHost(&c->h_lra_perm, sizeof(int) * n)) != cudaSuccess)
+            return cuda_fail(c, e, "LRA atom order");
+        c->lra_perm_cap = n;
+    }
+    if (c->lra_perm_version != c->solute_version) {  // a new solute: its spatial order
+        lra_order(c->h_raw, n, c->h_lra_perm);
+        if ((e = cudaMemcpyAsync(c->d_lra_perm, c->h_lra_perm, sizeof(int) * n, cudaMemcpyHostToDevice, c->st)) !=
+            cudaSuccess)
+            return cuda_fail(c, e, "LRA atom order upload");
+        c->lra_perm_version = c->solute_version;
+    }
+    if ((e = launch_lra(c->t, c->gd, c->ph, sms, c->d_lra_perm, static_cast<SrcF*>(c->d_lra_src), c->d_lra_part,
+                        c->d_lra_atom, c->d_lra_tot, c->o.wait_limit, c->st)) != cudaSuccess)
         return cuda_fail(c, e, "LRA kernels");
     if ((e = cudaMemcpyAsync(c->h_lra_tot, c->d_lra_tot, sizeof(double) * 3, cudaMemcpyDeviceToHost, c->st)) !=
         cudaSuccess)
@@ -671,7 +757,7 @@ rism_status rism_lra_integral(rism_ctx* c, double* T, double* atom_sums) {
         const double theta = (Q * c->qs[k] > 0.0) ? 1.0 : 0.0;
         T[k] = 0.5 * theta * A * A * Shh - 0.5 * A * B * Shc;
     }
-    c->info.launches = 3;
+    c->info.launches = 4;
     return RISM_OK;
 }
 
@@ -790,6 +876,9 @@ void rism_destroy(rism_ctx* c) {
     if (c->cp_fork) cudaEventDestroy(c->cp_fork);
     cudaFree(c->d_lra_part);
     cudaFree(c->d_lra_atom);
+    cudaFree(c->d_lra_perm);
+    cudaFree(c->d_lra_src);
+    cudaFreeHost(c->h_lra_perm);
     cudaFree(c->d_lra_tot);
     cudaFreeHost(c->h_lra_tot);
     cudaFree(c->d_ktab);

@@ -19,10 +19,13 @@
 // limits I_hc(0) = 8 pi erfcx(b)/kappa and I_hh(0) = (8 pi/kappa) erfcx(b) + 16 pi sigma b erfcx(b)
 // - 16 sigma sqrt(pi) apply.
 //
+//   k_lra_gather: the source table in the spatial order chosen on the host (cells of about 32 atoms in Morton
+//                 order), so that a warp's targets and a tile's sources are each close together and the
+//                 short-range branch of the pair term is taken by whole warps or by none
 //   k_lra_pairs:  atoms as targets (two per thread) against one chunk of all atoms as sources, streamed through
 //                 shared memory by bulk TMA copies; FP32 pair terms in grid units from the float-float source
 //                 records, per-tile FP32 partials folded into float-float sums; partials per chunk in FP64
-//   k_lra_atoms:  fixed-order sum of the chunks, per-atom sums P_hc, P_hh (FP64)
+//   k_lra_atoms:  fixed-order sum of the chunks, per-atom sums P_hc, P_hh (FP64), back in the original order
 //   k_lra_total:  one CTA: S_hh = sum_a Q_a P_hh, S_hc = sum_a Q_a P_hc, Q, fixed-order tree reduction
 #include <algorithm>
 #include <cmath>
@@ -36,9 +39,10 @@ constexpr int kLT = 128;    // threads per pair CTA
 constexpr int kLPT = 2;     // target atoms per thread
 constexpr int kLTile = 64;  // source atoms per shared-memory tile
 constexpr int kLParts = 10; // partial values per (chunk, atom)
+constexpr int kLCtasPerSM = 5;  // pair CTAs resident per SM (registers: about 95 per thread)
 
 struct LraPairArgs {
-    const SrcF* srcf;   // [n] grid-unit float-float positions + charge (original order)
+    const SrcF* srcf;   // [n] grid-unit float-float positions + charge (the pair sum's spatial order)
     int n;
     int chunk;          // source atoms per chunk
     float kap2;         // -kappa h log2(e): e^{-kappa R} = 2^(kap2 R_grid)
@@ -180,8 +184,14 @@ struct LraConst {
     double h, kappa, E, sig2, I0hc, I0hh;
 };
 
+// The source table in the pair sum's order: ssrc[k] = srcf[perm[k]].
+__global__ void k_lra_gather(const SrcF* __restrict__ srcf, const int* __restrict__ perm, int n, SrcF* ssrc) {
+    for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < n; k += gridDim.x * blockDim.x) ssrc[k] = srcf[perm[k]];
+}
+
 // Per atom: fixed-order sum of the chunk partials and the assembly of the two overlap sums (FP64).
-__global__ void k_lra_atoms(const double* __restrict__ part, int n, int chunks, LraConst k, double2* atom) {
+__global__ void k_lra_atoms(const double* __restrict__ part, int n, int chunks, LraConst k,
+                            const int* __restrict__ perm, double2* atom) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
     double v[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
@@ -197,7 +207,7 @@ __global__ void k_lra_atoms(const double* __restrict__ part, int n, int chunks, 
     const double phc = pi4 / (k.kappa * k.kappa) * (2.0 * P1 - 2.0 * k.E * Pkf + 2.0 * Pd - SRhc) + z * k.I0hc;
     const double phh = 2.0 * pi4 * k.E / k.kappa * Pe - 4.0 * pi4 * k.sig2 * k.E * (Pkf + Pkn) +
                        pi4 / k.kappa * (SRh1 + 2.0 * k.kappa * k.sig2 * SRh2) + z * k.I0hh;
-    atom[i] = make_double2(phc, phh);
+    atom[perm[i]] = make_double2(phc, phh);
 }
 
 // S_hh, S_hc and Q in one CTA (fixed order: strided per-thread sums, then a tree).
@@ -235,18 +245,19 @@ size_t lra_scratch_doubles(int64_t n, int sms) {
 int lra_chunks(int64_t n, int sms) {
     if (n <= 0) return 1;
     const int64_t tblocks = (n + kLT * kLPT - 1) / (kLT * kLPT);
-    int64_t c = (2 * (int64_t)sms + tblocks - 1) / tblocks;     // about two CTAs per SM
+    int64_t c = (kLCtasPerSM * (int64_t)sms + tblocks - 1) / tblocks;  // every SM's CTA slots filled
     c = std::min<int64_t>(c, (n + kLTile - 1) / kLTile);        // at least one tile of sources per chunk
     return (int)std::max<int64_t>(c, 1);
 }
 
-cudaError_t launch_lra(const DevTables& t, const GridD& g, const Phys& ph, int sms, double* part, double2* atom,
-                       double* tot, long long wait_limit, cudaStream_t st) {
+cudaError_t launch_lra(const DevTables& t, const GridD& g, const Phys& ph, int sms, const int* perm, SrcF* ssrc,
+                       double* part, double2* atom, double* tot, long long wait_limit, cudaStream_t st) {
     const int n = (int)t.n;
     if (n <= 0) return cudaSuccess;
     const int chunks = lra_chunks(n, sms);
+    k_lra_gather<<<std::min((n + 255) / 256, 4 * sms), 256, 0, st>>>(t.srcf, perm, n, ssrc);
     LraPairArgs a;
-    a.srcf = t.srcf;
+    a.srcf = ssrc;
     a.n = n;
     a.chunk = (int)((n + chunks - 1) / chunks);
     // 16-byte aligned bulk copies: every chunk starts at a multiple of 2 records (SrcF is 32 bytes)
@@ -274,7 +285,7 @@ cudaError_t launch_lra(const DevTables& t, const GridD& g, const Phys& ph, int s
     const double ex = std::exp(b * b) * std::erfc(b);  // erfcx(b), b small and positive
     k.I0hc = 8.0 * M_PI * ex / ph.kappa;
     k.I0hh = 8.0 * M_PI * ex / ph.kappa + 16.0 * M_PI * sigma * b * ex - 16.0 * sigma * std::sqrt(M_PI);
-    k_lra_atoms<<<(n + 255) / 256, 256, 0, st>>>(part, n, chunks, k, atom);
+    k_lra_atoms<<<(n + 255) / 256, 256, 0, st>>>(part, n, chunks, k, perm, atom);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     k_lra_total<<<1, kTotT, 0, st>>>(atom, t.geo, n, tot);
     return cudaGetLastError();
