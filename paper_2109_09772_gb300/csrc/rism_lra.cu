@@ -24,7 +24,9 @@
 //                 short-range branch of the pair term is taken by whole warps or by none
 //   k_lra_pairs:  atoms as targets (two per thread) against one chunk of all atoms as sources, streamed through
 //                 shared memory by bulk TMA copies; FP32 pair terms in grid units from the float-float source
-//                 records, per-tile FP32 partials folded into float-float sums; partials per chunk in FP64
+//                 records, per-tile FP32 partials folded into float-float sums; partials per chunk in FP64.  A
+//                 tile whose box lies beyond r_s from every target of a warp (most tiles, in the spatial
+//                 order) takes a two-wide form of the far terms: two sources per instruction
 //   k_lra_atoms:  fixed-order sum of the chunks, per-atom sums P_hc, P_hh (FP64), back in the original order
 //   k_lra_total:  one CTA: S_hh = sum_a Q_a P_hh, S_hc = sum_a Q_a P_hc, Q, fixed-order tree reduction
 #include <algorithm>
@@ -39,7 +41,7 @@ constexpr int kLT = 128;    // threads per pair CTA
 constexpr int kLPT = 2;     // target atoms per thread
 constexpr int kLTile = 64;  // source atoms per shared-memory tile
 constexpr int kLParts = 10; // partial values per (chunk, atom)
-constexpr int kLCtasPerSM = 5;  // pair CTAs resident per SM (registers: about 95 per thread)
+constexpr int kLCtasPerSM = 4;  // pair CTAs resident per SM (registers: about 124 per thread)
 
 struct LraPairArgs {
     const SrcF* srcf;   // [n] grid-unit float-float positions + charge (the pair sum's spatial order)
@@ -49,6 +51,7 @@ struct LraPairArgs {
     float kapg;         // kappa h
     float bb;           // b^2 = (kappa sigma)^2
     float rs2;          // (short-range radius / h)^2
+    float rsm2;         // (short-range radius / h + 0.01)^2: the far test of a whole tile
     float sgrid;        // h / (2 sigma): s = R_grid * sgrid
     float b;            // kappa sigma
     double* part;       // [chunks][n][kLParts]
@@ -65,6 +68,10 @@ __device__ __forceinline__ void fold(Acc& a, float v) { ff_add(a.h, a.l, v); }
 __global__ void __launch_bounds__(kLT) k_lra_pairs(LraPairArgs a) {
     __shared__ __align__(16) SrcF tile[2][kLTile];
     __shared__ __align__(8) uint64_t bar[2];
+    // the current tile as pair records (x_hi, x_hi', x_lo, x_lo' | y.. | z.. | q, q', 0, 0: sources 2l, 2l + 1)
+    // and the box of its sources' high parts, for the two-wide far form
+    __shared__ __align__(16) float4 prec[kLTile / 2][4];
+    __shared__ float tbox[6];
     const int tid = threadIdx.x;
     const int c = blockIdx.y;
     const int64_t s0 = (int64_t)c * a.chunk;
@@ -118,37 +125,125 @@ __global__ void __launch_bounds__(kLT) k_lra_pairs(LraPairArgs a) {
         const SrcF* S = tile[t & 1];
         float q1[kLPT] = {}, qk[kLPT] = {}, qkn[kLPT] = {}, qd[kLPT] = {}, qe[kLPT] = {}, qhc[kLPT] = {},
               qh1[kLPT] = {}, qh2[kLPT] = {}, qz[kLPT] = {};
-        for (int j = 0; j < cnt; ++j) {
-            const float4 g0 = *reinterpret_cast<const float4*>(&S[j].xh);
-            const float4 g1 = *reinterpret_cast<const float4*>(&S[j].xl);
+        // restage the tile as pair records (the first warp; an odd count is padded with a zero charge 10^6 grid
+        // units away, whose terms are exactly zero) and reduce the box of its sources
+        if (tid < 32) {
+            const int l = tid;
+            float bl[3] = {INFINITY, INFINITY, INFINITY}, bh[3] = {-INFINITY, -INFINITY, -INFINITY};
+            if (2 * l < cnt) {
+                const float4 a0 = *reinterpret_cast<const float4*>(&S[2 * l].xh);
+                const float4 a1 = *reinterpret_cast<const float4*>(&S[2 * l].xl);
+                float4 b0 = make_float4(1.0e6f, 1.0e6f, 1.0e6f, 0.f), b1 = make_float4(0.f, 0.f, 0.f, 0.f);
+                if (2 * l + 1 < cnt) {
+                    b0 = *reinterpret_cast<const float4*>(&S[2 * l + 1].xh);
+                    b1 = *reinterpret_cast<const float4*>(&S[2 * l + 1].xl);
+                }
+                prec[l][0] = make_float4(a0.x, b0.x, a1.x, b1.x);
+                prec[l][1] = make_float4(a0.y, b0.y, a1.y, b1.y);
+                prec[l][2] = make_float4(a0.z, b0.z, a1.z, b1.z);
+                prec[l][3] = make_float4(a0.w, b0.w, 0.f, 0.f);
+                const float ax[3] = {a0.x, a0.y, a0.z}, bx[3] = {b0.x, b0.y, b0.z};
+                for (int d = 0; d < 3; ++d) {
+                    bl[d] = ax[d];
+                    bh[d] = ax[d];
+                    if (2 * l + 1 < cnt) {
+                        bl[d] = fminf(bl[d], bx[d]);
+                        bh[d] = fmaxf(bh[d], bx[d]);
+                    }
+                }
+            }
+            for (int d = 0; d < 3; ++d)
+                for (int o = 16; o > 0; o >>= 1) {
+                    bl[d] = fminf(bl[d], __shfl_xor_sync(0xffffffffu, bl[d], o));
+                    bh[d] = fmaxf(bh[d], __shfl_xor_sync(0xffffffffu, bh[d], o));
+                }
+            if (l == 0)
+                for (int d = 0; d < 3; ++d) {
+                    tbox[d] = bl[d];
+                    tbox[3 + d] = bh[d];
+                }
+        }
+        __syncthreads();
+        // far form when every target of the warp lies beyond r_s (plus 0.01 grid units for the sources' low
+        // parts) from the tile's box: no pair of the tile takes the short-range branch
+        bool far = true;
+#pragma unroll
+        for (int k = 0; k < kLPT; ++k) {
+            if (!live[k]) continue;
+            const float gx = fmaxf(0.f, fmaxf(tbox[0] - tx[k], tx[k] - tbox[3]));
+            const float gy = fmaxf(0.f, fmaxf(tbox[1] - ty[k], ty[k] - tbox[4]));
+            const float gz = fmaxf(0.f, fmaxf(tbox[2] - tz[k], tz[k] - tbox[5]));
+            far = far && fmaf(gx, gx, fmaf(gy, gy, gz * gz)) > a.rsm2;
+        }
+        if (__all_sync(0xffffffffu, far)) {
+            // two sources per two-wide instruction: 1/R by rsqrt, e^{-kappa R} by ex2, the far sums only
+            const f32x2 K2 = pk2(a.kap2, a.kap2);
+            f32x2 P1[kLPT], PK[kLPT], PE[kLPT];
+#pragma unroll
+            for (int k = 0; k < kLPT; ++k) P1[k] = PK[k] = PE[k] = 0ull;
+            const int np = (cnt + 1) >> 1;
+            for (int l = 0; l < np; ++l) {
+                const ulonglong2 X = *reinterpret_cast<const ulonglong2*>(&prec[l][0]);
+                const ulonglong2 Y = *reinterpret_cast<const ulonglong2*>(&prec[l][1]);
+                const ulonglong2 Z = *reinterpret_cast<const ulonglong2*>(&prec[l][2]);
+                const f32x2 Q = *reinterpret_cast<const f32x2*>(&prec[l][3]);
+#pragma unroll
+                for (int k = 0; k < kLPT; ++k) {
+                    const f32x2 DX = add2(sub2(pk2(tx[k], tx[k]), X.x), sub2(pk2(txl[k], txl[k]), X.y));
+                    const f32x2 DY = add2(sub2(pk2(ty[k], ty[k]), Y.x), sub2(pk2(tyl[k], tyl[k]), Y.y));
+                    const f32x2 DZ = add2(sub2(pk2(tz[k], tz[k]), Z.x), sub2(pk2(tzl[k], tzl[k]), Z.y));
+                    const f32x2 D2 = fma2(DX, DX, fma2(DY, DY, mul2(DZ, DZ)));
+                    const float2 d2 = up2(D2);
+                    const f32x2 RI = pk2(rsqrt_approx(d2.x), rsqrt_approx(d2.y));
+                    const float2 e = up2(mul2(K2, mul2(D2, RI)));
+                    const f32x2 E = pk2(ex2_approx(e.x), ex2_approx(e.y));
+                    const f32x2 QR = mul2(Q, RI);
+                    P1[k] = add2(P1[k], QR);
+                    PK[k] = fma2(QR, E, PK[k]);
+                    PE[k] = fma2(Q, E, PE[k]);
+                }
+            }
 #pragma unroll
             for (int k = 0; k < kLPT; ++k) {
-                // relative position to one rounding of each component: (hi - hi) + (lo - lo)
-                const float dx = (tx[k] - g0.x) + (txl[k] - g1.x);
-                const float dy = (ty[k] - g0.y) + (tyl[k] - g1.y);
-                const float dz = (tz[k] - g0.z) + (tzl[k] - g1.z);
-                const float d2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
-                const float rr = rsqrt_approx(d2);
-                const float ri = d2 > 0.f ? rr : 0.f;
-                const float R = d2 * ri;
-                const float e = d2 > 0.f ? ex2_approx(a.kap2 * R) : 0.f;  // R = 0 takes the limits below
-                const float qr = g0.w * ri;
-                qe[k] = fmaf(g0.w, e, qe[k]);
-                if (d2 >= a.rs2) {
-                    q1[k] += qr;
-                    qk[k] = fmaf(qr, e, qk[k]);
-                } else {
-                    if (d2 > 0.f) {
-                        qkn[k] = fmaf(qr, e, qkn[k]);
-                        qd[k] = fmaf(qr, -expm1f(a.bb - a.kapg * R), qd[k]);
-                        const float s = R * a.sgrid;
-                        const float gg = __expf(-s * s);
-                        const float X1 = erfcxf(s - a.b), X2 = erfcxf(s + a.b);
-                        qhc[k] = fmaf(qr, 2.f * erfcf(s) - gg * (X1 + X2), qhc[k]);
-                        qh1[k] = fmaf(g0.w, gg * (X2 - X1), qh1[k]);
-                        qh2[k] = fmaf(qr, gg * (X1 + X2), qh2[k]);
+                const float2 v1 = up2(P1[k]), vk = up2(PK[k]), ve = up2(PE[k]);
+                q1[k] = v1.x + v1.y;
+                qk[k] = vk.x + vk.y;
+                qe[k] = ve.x + ve.y;
+            }
+        } else {
+            for (int j = 0; j < cnt; ++j) {
+                const float4 g0 = *reinterpret_cast<const float4*>(&S[j].xh);
+                const float4 g1 = *reinterpret_cast<const float4*>(&S[j].xl);
+#pragma unroll
+                for (int k = 0; k < kLPT; ++k) {
+                    // relative position to one rounding of each component: (hi - hi) + (lo - lo)
+                    const float dx = (tx[k] - g0.x) + (txl[k] - g1.x);
+                    const float dy = (ty[k] - g0.y) + (tyl[k] - g1.y);
+                    const float dz = (tz[k] - g0.z) + (tzl[k] - g1.z);
+                    const float d2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+                    const float rr = rsqrt_approx(d2);
+                    const float ri = d2 > 0.f ? rr : 0.f;
+                    const float R = d2 * ri;
+                    const float e = d2 > 0.f ? ex2_approx(a.kap2 * R) : 0.f;  // R = 0 takes the limits below
+                    const float qr = g0.w * ri;
+                    qe[k] = fmaf(g0.w, e, qe[k]);
+                    if (d2 >= a.rs2) {
+                        q1[k] += qr;
+                        qk[k] = fmaf(qr, e, qk[k]);
                     } else {
-                        qz[k] += g0.w;  // an atom with itself (or two atoms at one position): the R = 0 limits
+                        if (d2 > 0.f) {
+                            qkn[k] = fmaf(qr, e, qkn[k]);
+                            qd[k] = fmaf(qr, -expm1f(a.bb - a.kapg * R), qd[k]);
+                            const float s = R * a.sgrid;
+                            const float gg = __expf(-s * s);
+                            const float X1 = erfcxf(s - a.b), X2 = erfcxf(s + a.b);
+                            qhc[k] = fmaf(qr, 2.f * erfcf(s) - gg * (X1 + X2), qhc[k]);
+                            qh1[k] = fmaf(g0.w, gg * (X2 - X1), qh1[k]);
+                            qh2[k] = fmaf(qr, gg * (X1 + X2), qh2[k]);
+                        } else {
+                            // an atom with itself (or two atoms at one position): the R = 0 limits
+                            qz[k] += g0.w;
+                        }
                     }
                 }
             }
@@ -267,6 +362,7 @@ cudaError_t launch_lra(const DevTables& t, const GridD& g, const Phys& ph, int s
     a.bb = (float)((ph.kappa * sigma) * (ph.kappa * sigma));
     const double rs = 6.0 * std::sqrt(2.0) * ph.eta;
     a.rs2 = (float)((rs / g.h) * (rs / g.h));
+    a.rsm2 = (float)((rs / g.h + 0.01) * (rs / g.h + 0.01));
     a.sgrid = (float)(g.h / (2.0 * sigma));
     a.b = (float)(ph.kappa * sigma);
     a.part = part;
