@@ -13,11 +13,11 @@
 //             record; the phase m x / n is reduced modulo one cycle exactly -- integer part of x modulo n in
 //             integer arithmetic, the rest as an error-free product and float-float sum -- before sincospif),
 //             the charge folded into the z table;
-//   k_ksum:   CTAs of (one m_z, 32 m_y, 128 m_x); per tile of 16 atoms the x, y and z tables arrive as three
+//   k_ksum:   CTAs of (one m_z, 32 m_y, 128 m_x); per tile of 32 atoms the x, y and z tables arrive as three
 //             bulk TMA copies (the tables are blocked so that a tile is contiguous), the CTA forms T = E_y E_z Q
 //             in shared memory, and each thread accumulates 4 m_x x 4 m_y complex sums S += E_x T (4 FP32 FMAs
-//             per (k, atom) pair), partials of 32 atoms folded into float-float sums; rows beyond the cut-off sphere are skipped warp by warp, CTAs wholly beyond it
-//             only write zeros.  The epilogue applies the k-dependent factors and writes c and h of every site
+//             per (k, atom) pair), partials of 32 atoms folded into float-float sums; rows beyond the cut-off
+//             sphere are skipped warp by warp, CTAs wholly beyond it only write zeros.  The epilogue applies the k-dependent factors and writes c and h of every site
 //             as FP64 complex values (each rounded once to FP32, widened on the integer pipe).
 #include <algorithm>
 #include <cmath>
@@ -28,7 +28,7 @@
 namespace rism {
 namespace {
 
-constexpr int kKT = 16;        // atoms per tile (partials are folded every second tile)
+constexpr int kKT = 32;        // atoms per tile (the FP32 partials are folded after every tile)
 constexpr int kKW = 8;         // warps per CTA
 constexpr int kKMY = 4;        // m_y rows per warp
 constexpr int kKMX = 4;        // m_x per lane (stride 32)
@@ -36,7 +36,7 @@ constexpr int kKBX = 32 * kKMX;    // m_x per CTA (128)
 constexpr int kKBY = kKW * kKMY;   // m_y per CTA (32)
 constexpr int kKThreads = 32 * kKW;
 
-// Blocked so that one tile of a CTA (its m_x or m_y block, 16 atoms) is one contiguous bulk copy.
+// Blocked so that one tile of a CTA (its m_x or m_y block, 32 atoms) is one contiguous bulk copy.
 struct KTables {
     float2* ex;  // [mxp / 128][npad][128]
     float2* ey;  // [nyp / 32][npad][32]
@@ -195,19 +195,17 @@ __global__ void __launch_bounds__(kKThreads, 2) k_ksum(KSumArgs a) {
                 }
                 return;
             }
-            // T[a][my] = E_y(a, my) * (Q_a E_z(a, mz)): 16 atoms x 32 rows, two per thread
+            // T[a][my] = E_y(a, my) * (Q_a E_z(a, mz)): 32 atoms x 32 rows, four per thread
             for (int e = tid; e < kKT * kKBY; e += kKThreads) {
                 const int aa = e / kKBY, yy = e - aa * kKBY;
                 const float2 y = sy[(b * kKT + aa) * kKBY + yy], z = sz[b * kKT + aa];
                 st[e] = make_float2(y.x * z.x - y.y * z.y, y.x * z.y + y.y * z.x);
             }
             __syncthreads();
-            if ((t & 1) == 0) {
 #pragma unroll
-                for (int i = 0; i < kKMX; ++i)
+            for (int i = 0; i < kKMX; ++i)
 #pragma unroll
-                    for (int j = 0; j < kKMY; ++j) acc[i][j] = make_float2(0.f, 0.f);
-            }
+                for (int j = 0; j < kKMY; ++j) acc[i][j] = make_float2(0.f, 0.f);
             const float2* X = sx + b * kKT * kKBX;
             auto body = [&](auto NG) {
                 constexpr int G = decltype(NG)::value;
@@ -234,15 +232,13 @@ __global__ void __launch_bounds__(kKThreads, 2) k_ksum(KSumArgs a) {
                 case 4: body(std::integral_constant<int, 4>{}); break;
                 default: break;
             }
-            if ((t & 1) == 1 || t == ntiles - 1) {
 #pragma unroll
-                for (int i = 0; i < kKMX; ++i)
+            for (int i = 0; i < kKMX; ++i)
 #pragma unroll
-                    for (int j = 0; j < kKMY; ++j) {
-                        ff_add(hi[i][j].x, lo[i][j].x, acc[i][j].x);
-                        ff_add(hi[i][j].y, lo[i][j].y, acc[i][j].y);
-                    }
-            }
+                for (int j = 0; j < kKMY; ++j) {
+                    ff_add(hi[i][j].x, lo[i][j].x, acc[i][j].x);
+                    ff_add(hi[i][j].y, lo[i][j].y, acc[i][j].y);
+                }
             __syncthreads();
             if (tid == 0 && t + 2 < ntiles) issue(t + 2);
         }
