@@ -111,6 +111,12 @@ class Clocks:
         for line in self.proc.stdout:
             self.lines.append(line.strip())
 
+    def wait_first(self, timeout_s=3.0):
+        """Block until nvidia-smi has printed its first sample, so the samples cover the timed region."""
+        t0 = time.perf_counter()
+        while self.proc is not None and not self.lines and time.perf_counter() - t0 < timeout_s:
+            time.sleep(0.01)
+
     def stop(self):
         if self.proc is None:
             return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
@@ -214,6 +220,7 @@ def run_gpu(args):
         dist.barrier()
     clocks = Clocks(torch.cuda.current_device())
     clocks.start()
+    clocks.wait_first()
     times, evals, launches, far_ms, near_ms, box_ms = [], [], 0, [], [], []
     torch.cuda.synchronize()
     t_wall0 = time.perf_counter()
@@ -800,7 +807,7 @@ def suite_mufu(args):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--steps", type=int, default=50)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--method", default="treecode", choices=["treecode", "direct"])
