@@ -4075,6 +4075,10 @@ void tree_destroy(TreeState* s) {
         if (s->ev[k]) cudaEventDestroy(s->ev[k]);
     for (int k = 0; k < kMaxSlabs; ++k)
         if (s->slab_ev[k]) cudaEventDestroy(s->slab_ev[k]);
+    for (int k = 0; k < 2; ++k)
+        if (s->side_fork[k]) cudaEventDestroy(s->side_fork[k]);
+    if (s->side_join) cudaEventDestroy(s->side_join);
+    if (s->side) cudaStreamDestroy(s->side);
     cudaFree(s->cp_cnt);
     cudaFree(s->dn_cnt);
     cudaFree(s->dn_ent);
