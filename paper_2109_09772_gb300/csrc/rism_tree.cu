@@ -1971,7 +1971,7 @@ struct RelRec {
 };
 
 __device__ __forceinline__ void stage_rel(const SrcF* __restrict__ Sx, int cnt, RelRec* wp, int lane, float cx,
-                                          float cy, float cz) {
+                                          float cy, float cz, float sc) {
     if (2 * lane < cnt) {
         const float4 a0 = *reinterpret_cast<const float4*>(&Sx[2 * lane].xh);
         const float4 a1 = *reinterpret_cast<const float4*>(&Sx[2 * lane].xl);
@@ -1980,19 +1980,19 @@ __device__ __forceinline__ void stage_rel(const SrcF* __restrict__ Sx, int cnt, 
         if (2 * lane + 1 < cnt) {
             b0 = *reinterpret_cast<const float4*>(&Sx[2 * lane + 1].xh);
             b1 = *reinterpret_cast<const float4*>(&Sx[2 * lane + 1].xl);
-            bx = (b0.x - cx) + b1.x;
-            by = (b0.y - cy) + b1.y;
-            bz = (b0.z - cz) + b1.z;
+            bx = ((b0.x - cx) + b1.x) * sc;
+            by = ((b0.y - cy) + b1.y) * sc;
+            bz = ((b0.z - cz) + b1.z) * sc;
         }
         RelRec& o = wp[lane];
-        o.xy = make_float4((a0.x - cx) + a1.x, bx, (a0.y - cy) + a1.y, by);
-        o.zq = make_float4((a0.z - cz) + a1.z, bz, a0.w, b0.w);
+        o.xy = make_float4(((a0.x - cx) + a1.x) * sc, bx, ((a0.y - cy) + a1.y) * sc, by);
+        o.zq = make_float4(((a0.z - cz) + a1.z) * sc, bz, a0.w, b0.w);
     }
 }
 
 template <int P, bool DH>
 __device__ __forceinline__ void cp_pairs(const RelRec* wp, int l0, int np, int stride, const f32x2 (&GX)[P], f32x2 FY,
-                                         f32x2 FZ, f32x2 K2, f32x2 (&P1)[P], f32x2 (&PK)[P]) {
+                                         f32x2 FZ, f32x2 (&P1)[P], f32x2 (&PK)[P]) {
     for (int l = l0; l < np; l += stride) {
         const ulonglong2 A = *reinterpret_cast<const ulonglong2*>(&wp[l].xy);
         const ulonglong2 B = *reinterpret_cast<const ulonglong2*>(&wp[l].zq);
@@ -2007,9 +2007,9 @@ __device__ __forceinline__ void cp_pairs(const RelRec* wp, int l0, int np, int s
             const f32x2 RI = pk2(rsqrt_approx(d2.x), rsqrt_approx(d2.y));
             const f32x2 QR = mul2(B.y, RI);
             P1[p] = add2(P1[p], QR);
-            if (DH) {
-                const float2 e = up2(mul2(K2, mul2(D2, RI)));
-                PK[p] = fma2(QR, pk2(ex2_approx(e.x), ex2_approx(e.y)), PK[p]);
+            if (DH) {  // coordinates scaled by -kappa h log2(e): the exponent is -d' = -(d'^2 / d')
+                const float2 e = up2(mul2(D2, RI));
+                PK[p] = fma2(QR, pk2(ex2_approx(-e.x), ex2_approx(-e.y)), PK[p]);
             }
         }
     }
@@ -2086,16 +2086,19 @@ __global__ void __launch_bounds__(kCPThreads + 32) k_cp_eval(EvalArgs a, CPArgs 
     const int tk = act ? task : 0;
     const int line = tk / nxc, xc = tk % nxc, ky = line % n1, kz = line / n1;
     const float hx = 0.5f * (T.ext[0] - 1), hy = 0.5f * (T.ext[1] - 1), hz = 0.5f * (T.ext[2] - 1);
+    // With screening every coordinate is scaled by s = kappa h log2(e), so the screening exponent is the scaled
+    // distance itself and both sums are multiplied by s at the end.  Below 1e-18 the exponent rounds to 0 either
+    // way, so the floor changes no value; it keeps the scaled squared distances normal numbers.
+    const float csc = DH ? fmaxf(-a.kap2, 1e-18f) : 1.f;
     f32x2 GX[kCPP];
 #pragma unroll
     for (int p = 0; p < kCPP; ++p) {
         const int kx = min(xc * kCPP + p, deg);
-        const float u = hx * c.tb.ck[kx];
+        const float u = hx * c.tb.ck[kx] * csc;
         GX[p] = pk2(u, u);
     }
-    const float uy = hy * c.tb.ck[ky], uz = hz * c.tb.ck[kz];
+    const float uy = hy * c.tb.ck[ky] * csc, uz = hz * c.tb.ck[kz] * csc;
     const f32x2 FY = pk2(uy, uy), FZ = pk2(uz, uz);
-    const f32x2 K2 = pk2(a.kap2, a.kap2);
     // box centre lo + (ext - 1) / 2: exact in FP32 (the same value as the FP64 centre)
     const float cx = (float)T.lo[0] + 0.5f * (float)(T.ext[0] - 1), cy = (float)T.lo[1] + 0.5f * (float)(T.ext[1] - 1),
                 cz = (float)T.lo[2] + 0.5f * (float)(T.ext[2] - 1);
@@ -2120,7 +2123,7 @@ __global__ void __launch_bounds__(kCPThreads + 32) k_cp_eval(EvalArgs a, CPArgs 
         r, cur, c.cp_ent, a.srcf, nullptr, a,
         [&](int slot, int n) {
             __syncwarp();
-            stage_rel(r.src[slot], n, wp, lane, cx, cy, cz);
+            stage_rel(r.src[slot], n, wp, lane, cx, cy, cz, csc);
             __syncwarp();
         },
         [&](int n) {
@@ -2128,8 +2131,8 @@ __global__ void __launch_bounds__(kCPThreads + 32) k_cp_eval(EvalArgs a, CPArgs 
 #pragma unroll
             for (int p = 0; p < kCPP; ++p) P1[p] = PK[p] = 0ull;
             // the unit-stride call is its own loop (a runtime stride costs the degree-8 loop 9%)
-            if (G == 1) cp_pairs<kCPP, DH>(wp, 0, (n + 1) >> 1, 1, GX, FY, FZ, K2, P1, PK);
-            else cp_pairs<kCPP, DH>(wp, grp, (n + 1) >> 1, G, GX, FY, FZ, K2, P1, PK);
+            if (G == 1) cp_pairs<kCPP, DH>(wp, 0, (n + 1) >> 1, 1, GX, FY, FZ, P1, PK);
+            else cp_pairs<kCPP, DH>(wp, grp, (n + 1) >> 1, G, GX, FY, FZ, P1, PK);
 #pragma unroll
             for (int p = 0; p < kCPP; ++p) {
                 const float2 s1 = up2(P1[p]);
@@ -2163,7 +2166,7 @@ __global__ void __launch_bounds__(kCPThreads + 32) k_cp_eval(EvalArgs a, CPArgs 
 #pragma unroll
     for (int p = 0; p < kCPP; ++p) {
         const int kx = xc * kCPP + p;
-        if (kx < n1) out[(kz * n1 + ky) * n1 + kx] = make_float2(f1h[p] + f1l[p], fkh[p] + fkl[p]);
+        if (kx < n1) out[(kz * n1 + ky) * n1 + kx] = make_float2((f1h[p] + f1l[p]) * csc, (fkh[p] + fkl[p]) * csc);
     }
 }
 
