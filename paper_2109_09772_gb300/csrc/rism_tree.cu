@@ -1422,30 +1422,49 @@ __global__ void __launch_bounds__(32 * kListWarps) k_near_lists(ListArgs a, cons
     }
 }
 
-// Launch order of the batches, heaviest first: a counting sort of the batches by the binary order of magnitude
-// of their work (one CTA per list: CTA 0 orders work0 into order0, CTA 1 work1 into order1).  The order changes
-// nothing but which CTAs start first (each batch is computed independently), so long batches do not trail at
-// the end of the launch.  With nslab > 1, both orders are sorted by z slab first: slab k holds the batch layers
-// kb with floor(kb nslab / nbz) = k, and its batches (heaviest first) fill positions [kb_k nbxy, kb_(k+1) nbxy),
-// kb_k = ceil(k nbz / nslab), so each slab can run as launches of its own.
+// Launch order of the batches (or target boxes), heaviest first: a counting sort of the items by the binary
+// order of magnitude of their work (one CTA per list: CTA 0 orders work0 into order0, CTA 1 work1 into order1).
+// The order changes nothing but which CTAs start first (each item is computed independently), so long items do
+// not trail at the end of the launch.  The items may first be grouped by z slab for launches of their own
+// (OrderGroups): the items of level l are [off[l], off[l+1]), item b of level l lies in layer (b - off[l]) /
+// nbxy[l], and slab k holds the layers [bnd[l][k], bnd[l][k+1]) of every level; slab 0's items come first, and
+// each slab's items fill one contiguous range of positions (the sizes of the groups are known on the host).
 constexpr int kOrderBuckets = 33;
 constexpr int kMaxSlabs = 16;
+struct OrderGroups {
+    int ns, nlev;
+    int off[kMaxTL + 1], nbxy[kMaxTL];
+    int bnd[kMaxTL][kMaxSlabs];  // first layer of each slab, per level, ascending
+};
+__host__ inline OrderGroups order_plain(int nb) {
+    OrderGroups g{};
+    g.ns = 1;
+    g.nlev = 1;
+    g.off[1] = nb;
+    g.nbxy[0] = 1;
+    return g;
+}
+// Batch layers in nslab slabs: slab k starts at layer ceil(k nbz / nslab).
+__host__ inline int slab_start(int k, int nslab, int nbz) { return (int)(((int64_t)k * nbz + nslab - 1) / nslab); }
 __global__ void __launch_bounds__(1024) k_order(int nb, const int* __restrict__ work0, int* order0,
-                                                const int* __restrict__ work1, int* order1, int nslab, int nbxy,
-                                                int nbz) {
+                                                const int* __restrict__ work1, int* order1, OrderGroups og) {
     __shared__ int hist[kOrderBuckets * kMaxSlabs], start[kOrderBuckets * kMaxSlabs];
     const int* __restrict__ work = blockIdx.x == 0 ? work0 : work1;
     int* order = blockIdx.x == 0 ? order0 : order1;
-    const int ns = nslab;
-    const int nkey = kOrderBuckets * ns;
+    const int nkey = kOrderBuckets * og.ns;
     const int tid = threadIdx.x;
     for (int k = tid; k < nkey; k += blockDim.x) hist[k] = 0;
     __syncthreads();
-    // key: slab-major, then the work's order of magnitude from the largest (32) down to none (0)
+    // key: group-major, then the work's order of magnitude from the largest (32) down to none (0)
     auto key = [&](int b) {
         const int w = work[b];
         const int mag = w <= 0 ? 0 : 32 - __clz(w);
-        const int sl = ns > 1 ? (int)((long long)(b / nbxy) * ns / nbz) : 0;
+        int l = 0;
+        while (l + 1 < og.nlev && og.off[l + 1] <= b) ++l;
+        const int layer = (b - og.off[l]) / og.nbxy[l];
+        int sl = 0;
+        for (int k = 1; k < og.ns; ++k)
+            if (og.bnd[l][k] <= layer) sl = k;
         return sl * kOrderBuckets + (kOrderBuckets - 1 - mag);
     };
     for (int b = tid; b < nb; b += blockDim.x) atomicAdd(&hist[key(b)], 1);
@@ -1960,7 +1979,8 @@ struct CPArgs {
     float2* tpart;       // [nbox][kCPChunks - 1][P3] sums of the list chunks after the first
     int* tnch;           // [nbox] chunks the box's list was split into
     int* tflag;          // [nbox] nonzero: the box's proxies hold a field (own or inherited)
-    const int* order;    // [nbox] launch order of the boxes, most accepted atoms first (null: index order)
+    const int* order;    // launch order of the boxes, most accepted atoms first (null: index order from box0)
+    int box0;            // first box of an index-order launch
 };
 
 // Source pairs relative to the box centre: x_s - c = (x_hi - c) + x_lo, one rounding; the proxies are
@@ -2037,7 +2057,7 @@ __global__ void __launch_bounds__(kCPThreads + 32) k_cp_eval(EvalArgs a, CPArgs 
     const int tid = threadIdx.x, lane = tid & 31;
     if (tid == 0) r.inited = 0;
     if (a.meta->overflow) return;
-    const int box = c.order ? c.order[blockIdx.x] : (int)blockIdx.x, chunk = blockIdx.y, pass = blockIdx.z;
+    const int box = c.order ? c.order[blockIdx.x] : c.box0 + (int)blockIdx.x, chunk = blockIdx.y, pass = blockIdx.z;
     const TBox T = tbox_flat(c.tb, box);
     if (!T.proxied) return;
     const int deg = c.tb.deg, n1 = deg + 1, P3 = c.tb.P3;
@@ -2188,7 +2208,7 @@ __global__ void __launch_bounds__(256) k_cp_work(CPArgs c, const TreeMeta* meta,
 // Chunk partials added to the box's proxy values in chunk order (deterministic).
 __global__ void __launch_bounds__(256) k_cp_reduce(CPArgs c, const TreeMeta* meta) {
     if (meta->overflow) return;
-    const int box = blockIdx.x;
+    const int box = c.order ? c.order[blockIdx.x] : c.box0 + (int)blockIdx.x;
     const TBox T = tbox_flat(c.tb, box);
     if (!T.proxied || c.cp_cnt[box] == 0) return;
     const int nch = c.tnch[box], P3 = c.tb.P3;
@@ -2293,12 +2313,12 @@ __host__ __device__ constexpr size_t interp_smem(int n1, int m) {
 
 // Downward pass, level l + 1 -> l: a box with proxies adds its parent's field interpolated at its own proxies.
 template <int N1>
-__global__ void __launch_bounds__(256) k_l2l(CPArgs c, int l, const TreeMeta* meta) {
+__global__ void __launch_bounds__(256) k_l2l(CPArgs c, int l, int bi0, const TreeMeta* meta) {
     extern __shared__ __align__(16) unsigned char sm_raw[];
     constexpr int P3 = N1 * N1 * N1;
     if (meta->overflow) return;
     const TBoxes& tb = c.tb;
-    const int bi = blockIdx.x;
+    const int bi = bi0 + (int)blockIdx.x;
     const int ib = bi % tb.nbx[l], jb = (bi / tb.nbx[l]) % tb.nby[l], kb = bi / (tb.nbx[l] * tb.nby[l]);
     const TBox T = tbox_at(tb, l, ib, jb, kb);
     if (!T.proxied) return;
@@ -2330,12 +2350,12 @@ __global__ void __launch_bounds__(256) k_l2l(CPArgs c, int l, const TreeMeta* me
 // (its field includes every ancestor's) is interpolated at the region's points and written to the far-field
 // buffer as the starting value of the far kernel (zero where no box holds a field).
 template <int N1>
-__global__ void __launch_bounds__(256) k_tdown(CPArgs c, float4* far, const TreeMeta* meta) {
+__global__ void __launch_bounds__(256) k_tdown(CPArgs c, float4* far, int bi0, const TreeMeta* meta) {
     extern __shared__ __align__(16) unsigned char sm_raw[];
     constexpr int P3 = N1 * N1 * N1, M = kTB0;
     if (meta->overflow) return;
     const TBoxes& tb = c.tb;
-    const int bi = blockIdx.x;
+    const int bi = bi0 + (int)blockIdx.x;
     const int ib = bi % tb.nbx[0], jb = (bi / tb.nbx[0]) % tb.nby[0], kb = bi / (tb.nbx[0] * tb.nby[0]);
     const TBox R = tbox_at(tb, 0, ib, jb, kb);
     int la = -1;
@@ -2376,29 +2396,46 @@ __global__ void __launch_bounds__(256) k_tdown(CPArgs c, float4* far, const Tree
     });
 }
 
+// The downward pass and the interpolation onto the grid, over the box layers [zr[l][0], zr[l][1]) of each level
+// l (null: every layer): the levels from the second highest down, then the level-0 boxes' grid points.  Returns
+// the number of launches.
 template <int N1>
-void launch_down(const TBoxes& tb, const CPArgs& c, float4* far, const TreeMeta* meta, cudaStream_t st) {
+int launch_down(const TBoxes& tb, const CPArgs& c, float4* far, const TreeMeta* meta, cudaStream_t st,
+                const int (*zr)[2]) {
     const size_t sl = interp_smem(N1, N1), sd = interp_smem(N1, kTB0);
     raise_dyn_smem(k_l2l<N1>, sl);
     raise_dyn_smem(k_tdown<N1>, sd);
-    for (int l = tb.L - 2; l >= 0; --l) k_l2l<N1><<<tb.nbx[l] * tb.nby[l] * tb.nbz[l], 256, sl, st>>>(c, l, meta);
-    k_tdown<N1><<<tb.nbx[0] * tb.nby[0] * tb.nbz[0], 256, sd, st>>>(c, far, meta);
+    int n = 0;
+    for (int l = tb.L - 1; l >= 0; --l) {
+        const int nbxy = tb.nbx[l] * tb.nby[l], z0 = zr ? zr[l][0] : 0, z1 = zr ? zr[l][1] : tb.nbz[l];
+        if (z1 <= z0) continue;
+        if (l < tb.L - 1) {
+            k_l2l<N1><<<(z1 - z0) * nbxy, 256, sl, st>>>(c, l, z0 * nbxy, meta);
+            ++n;
+        }
+        if (l == 0) {
+            k_tdown<N1><<<(z1 - z0) * nbxy, 256, sd, st>>>(c, far, z0 * nbxy, meta);
+            ++n;
+        }
+    }
+    return n;
 }
 
-void launch_down_deg(const TBoxes& tb, const CPArgs& c, float4* far, const TreeMeta* meta, cudaStream_t st) {
+int launch_down_deg(const TBoxes& tb, const CPArgs& c, float4* far, const TreeMeta* meta, cudaStream_t st,
+                    const int (*zr)[2] = nullptr) {
     switch (tb.deg) {
-        case 1: return launch_down<2>(tb, c, far, meta, st);
-        case 2: return launch_down<3>(tb, c, far, meta, st);
-        case 3: return launch_down<4>(tb, c, far, meta, st);
-        case 4: return launch_down<5>(tb, c, far, meta, st);
-        case 5: return launch_down<6>(tb, c, far, meta, st);
-        case 6: return launch_down<7>(tb, c, far, meta, st);
-        case 7: return launch_down<8>(tb, c, far, meta, st);
-        case 8: return launch_down<9>(tb, c, far, meta, st);
-        case 9: return launch_down<10>(tb, c, far, meta, st);
-        case 10: return launch_down<11>(tb, c, far, meta, st);
-        case 11: return launch_down<12>(tb, c, far, meta, st);
-        default: return launch_down<13>(tb, c, far, meta, st);
+        case 1: return launch_down<2>(tb, c, far, meta, st, zr);
+        case 2: return launch_down<3>(tb, c, far, meta, st, zr);
+        case 3: return launch_down<4>(tb, c, far, meta, st, zr);
+        case 4: return launch_down<5>(tb, c, far, meta, st, zr);
+        case 5: return launch_down<6>(tb, c, far, meta, st, zr);
+        case 6: return launch_down<7>(tb, c, far, meta, st, zr);
+        case 7: return launch_down<8>(tb, c, far, meta, st, zr);
+        case 8: return launch_down<9>(tb, c, far, meta, st, zr);
+        case 9: return launch_down<10>(tb, c, far, meta, st, zr);
+        case 10: return launch_down<11>(tb, c, far, meta, st, zr);
+        case 11: return launch_down<12>(tb, c, far, meta, st, zr);
+        default: return launch_down<13>(tb, c, far, meta, st, zr);
     }
 }
 
@@ -3188,6 +3225,11 @@ struct TreeState {
     int nslab = 1;
     cudaEvent_t slab_ev[kMaxSlabs] = {};
     bool slabs_live = false;  // the last enqueued evaluation recorded the slab events
+    // the box level of the last cp_enqueue stopped after the coarser levels: each slab's launches start with
+    // its level-0 boxes (box_slab_launches: the launches those added)
+    bool box_split = false;
+    int box_slab_launches = 0;
+    int box_pos = 0;  // box order positions taken by the slabs so far
     // side branch of the preparation: the near lists beside the box-level lists, the far lists and the launch
     // orders beside the box-level evaluation; joined back before anything reads them (side_pending until then)
     cudaStream_t side = nullptr;
@@ -3430,6 +3472,7 @@ CPArgs make_cp(TreeState* s) {
     // heaviest-first box order from kCPOrderBoxes boxes on: below that the two launches that make it cost more
     // than the shorter tail saves (measured: +11 us of 0.22 ms at 585 boxes, -23 us of 1.47 ms at 1,935)
     c.order = s->tb.nbox >= kCPOrderBoxes ? s->cp_order : nullptr;
+    c.box0 = 0;
     return c;
 }
 
@@ -3797,32 +3840,95 @@ void side_join(TreeState* s, cudaStream_t st) {
     s->side_pending = false;
 }
 
+// Box layers [z0, z1) of level l that z slab k of the far and near launches needs first: every layer of the
+// level that meets the slab's grid planes and no earlier slab's (a level-l box is 16 2^l points high, a batch
+// layer 8 or 16).  The layers a slab needs at level l hold the parents of those it needs at level l - 1.
+void box_layers(const TreeState* s, int l, int k, int& z0, int& z1) {
+    const int nzb = shape_of(s->variant).nz, nbzl = s->tb.nbz[l], E = kTB0 << l;
+    auto end = [&](int kk) {
+        const int kb1 = slab_start(kk + 1, s->nslab, s->nbz);
+        return std::min(nbzl, (int)(((int64_t)kb1 * nzb + E - 1) / E));
+    };
+    z0 = k == 0 ? 0 : end(k - 1);
+    z1 = end(k);
+}
+
+void cp_launch(const EvalArgs& a, const CPArgs& c, int nbox, bool dh, cudaStream_t st, const TreeMeta* meta) {
+    const int n1 = c.tb.deg + 1;
+    const int npass = (n1 * n1 * ((n1 + kCPP - 1) / kCPP) + kCPThreads - 1) / kCPThreads;
+    const dim3 grid(nbox, kCPChunks, npass);
+    if (dh) k_cp_eval<true><<<grid, kCPThreads + 32, 0, st>>>(a, c);
+    else k_cp_eval<false><<<grid, kCPThreads + 32, 0, st>>>(a, c);
+    k_cp_reduce<<<nbox, 256, 0, st>>>(c, meta);
+}
+
 // Box-level far field (a10, cluster-particle form), then the join of the preparation's side branch.
-int cp_enqueue(TreeState* s, const EvalArgs& a, bool dh, cudaStream_t st) {
+// split (with z slabs): only the box order here, grouped by slab; each slab's launches start with the boxes of
+// every level that the slab needs first (cp_slab), so the first slab's outputs are final after its share of the
+// box level, and the side branch joins after the first slab's boxes.
+int cp_enqueue(TreeState* s, const EvalArgs& a, bool dh, cudaStream_t st, bool split = false) {
     const TBoxes& tb = s->tb;
+    s->box_split = false;
     if (!tb.enabled) {
         side_join(s, st);
         return 0;
     }
-    const CPArgs c = make_cp(s);
+    CPArgs c = make_cp(s);
     if (tb.approx == RISM_APPROX_TAYLOR) {
+        c.order = nullptr;  // the moment kernels run in index order (no box order is made for them)
         launch_taylor_deg(tb, a, c, s->far, s->meta, dh, st);
         side_join(s, st);
         return 3;
     }
-    const int n1 = tb.deg + 1;
-    const int npass = (n1 * n1 * ((n1 + kCPP - 1) / kCPP) + kCPThreads - 1) / kCPThreads;
-    const dim3 grid(tb.nbox, kCPChunks, npass);
+    split = split && s->nslab > 1;
+    if (split) c.order = s->cp_order;  // a slab's boxes of several levels are one launch: always by the order
     if (c.order) {
+        OrderGroups og = order_plain(tb.nbox);
+        if (split) {
+            og.ns = s->nslab;
+            og.nlev = tb.L;
+            for (int l = 0; l < tb.L; ++l) {
+                og.off[l] = tb.off[l];
+                og.nbxy[l] = tb.nbx[l] * tb.nby[l];
+                for (int k = 0; k < s->nslab; ++k) {
+                    int z1;
+                    box_layers(s, l, k, og.bnd[l][k], z1);
+                }
+            }
+            og.off[tb.L] = tb.nbox;
+        }
         k_cp_work<<<(tb.nbox + 7) / 8, 256, 0, st>>>(c, s->meta, s->cp_work);
-        k_order<<<1, 1024, 0, st>>>(tb.nbox, s->cp_work, s->cp_order, nullptr, nullptr, 1, 1, 1);
+        k_order<<<1, 1024, 0, st>>>(tb.nbox, s->cp_work, s->cp_order, nullptr, nullptr, og);
     }
-    if (dh) k_cp_eval<true><<<grid, kCPThreads + 32, 0, st>>>(a, c);
-    else k_cp_eval<false><<<grid, kCPThreads + 32, 0, st>>>(a, c);
-    k_cp_reduce<<<tb.nbox, 256, 0, st>>>(c, s->meta);
-    launch_down_deg(tb, c, s->far, s->meta, st);
+    const int nord = c.order ? 2 : 0;
+    if (split) {
+        s->box_split = true;
+        s->box_pos = 0;
+        return nord;
+    }
+    cp_launch(a, c, tb.nbox, dh, st, s->meta);
+    const int nd = launch_down_deg(tb, c, s->far, s->meta, st);
     side_join(s, st);
-    return (c.order ? 4 : 2) + (tb.L - 1) + 1;
+    return nord + 2 + nd;
+}
+
+// The boxes z slab k needs first after a split cp_enqueue (the next range of the box order): their proxies and
+// chunk sums, the downward pass into their layers level by level, and the level-0 boxes' grid points.  Returns
+// the number of launches.
+int cp_slab(TreeState* s, const EvalArgs& a, bool dh, int k, cudaStream_t st) {
+    const TBoxes& tb = s->tb;
+    int zr[kMaxTL][2];
+    int count = 0;
+    for (int l = 0; l < tb.L; ++l) {
+        box_layers(s, l, k, zr[l][0], zr[l][1]);
+        count += (zr[l][1] - zr[l][0]) * tb.nbx[l] * tb.nby[l];
+    }
+    if (count == 0) return 0;
+    CPArgs c = make_cp(s);
+    c.order = s->cp_order + s->box_pos;
+    s->box_pos += count;
+    cp_launch(a, c, count, dh, st, s->meta);
+    return 2 + launch_down_deg(tb, c, s->far, s->meta, st, zr);
 }
 
 // Kernel launches of a7..a9 for one solute (no allocation, no host wait:
@@ -3894,8 +4000,11 @@ rism_status tree_enqueue(TreeState* s, const DevTables& t, const GridD& g, const
     cudaEventRecord(s->side_fork[1], st);
     cudaStreamWaitEvent(s->side, s->side_fork[1], 0);
     k_far_lists<<<lgrid, 32 * kListWarps, 0, s->side>>>(fa, s->nodes, s->far_ent, s->far_cnt, s->far_work, s->meta);
-    k_order<<<2, 1024, 0, s->side>>>(s->nb, s->near_work, s->near_order, s->far_work, s->far_order, s->nslab,
-                                     s->nbx * s->nby, s->nbz);
+    OrderGroups og = order_plain(s->nb);
+    og.ns = std::max(1, s->nslab);
+    og.nbxy[0] = s->nbx * s->nby;
+    for (int k = 0; k < og.ns; ++k) og.bnd[0][k] = slab_start(k, og.ns, s->nbz);
+    k_order<<<2, 1024, 0, s->side>>>(s->nb, s->near_work, s->near_order, s->far_work, s->far_order, og);
     cudaEventRecord(s->side_join, s->side);
     s->side_pending = true;
     s->launches += 3;
@@ -4223,11 +4332,13 @@ static rism_status tree_autotune(TreeState* s, const DevTables& t, const GridD& 
 
 // The far and near kernels (+ epilogue) as one launch each, or per z slab of batch layers (s->nslab > 1): the
 // far and then the near launch of each slab, followed by a record of the slab's event (external records when the
-// launches are being captured into a graph, so that streams outside the graph can wait on a slab).  The first
-// slab's outputs are then complete after a slab's share of both kernels, not after the whole far field.
+// launches are being captured into a graph, so that streams outside the graph can wait on a slab).  After a split
+// cp_enqueue each slab's launches start with its level-0 boxes.  The first slab's outputs are then complete after
+// the coarser box levels and a slab's share of the rest, not after the whole box level and far field.
 namespace {
 cudaError_t farnear_enqueue(TreeState* s, int smax, const EvalArgs& a, bool du, bool dh, cudaStream_t st,
                             bool captured, cudaEvent_t mid = nullptr) {
+    s->box_slab_launches = 0;
     if (s->nslab <= 1) {
         s->slabs_live = false;
         cudaError_t e = dispatch(smax, s->variant, 2, du, dh, &a, s->nb, nullptr, 0, st);
@@ -4238,8 +4349,11 @@ cudaError_t farnear_enqueue(TreeState* s, int smax, const EvalArgs& a, bool du, 
     const int NS = shape_of(s->variant).nx / 8, nbxy = s->nbx * s->nby;
     cudaError_t e = cudaSuccess;
     for (int k = 0; k < s->nslab && e == cudaSuccess; ++k) {
-        const int kb0 = (int)(((int64_t)k * s->nbz + s->nslab - 1) / s->nslab);
-        const int kb1 = (int)(((int64_t)(k + 1) * s->nbz + s->nslab - 1) / s->nslab);
+        const int kb0 = slab_start(k, s->nslab, s->nbz), kb1 = slab_start(k + 1, s->nslab, s->nbz);
+        if (s->box_split) {
+            s->box_slab_launches += cp_slab(s, a, dh, k, st);
+            if (k == 0) side_join(s, st);
+        }
         if (kb1 > kb0) {
             EvalArgs b = a;
             b.f0 = kb0 * nbxy;
@@ -4254,6 +4368,7 @@ cudaError_t farnear_enqueue(TreeState* s, int smax, const EvalArgs& a, bool du, 
     }
     if (e == cudaSuccess && mid)  // no separate far time: the interleaved launches count as far + near
         e = captured ? cudaEventRecordWithFlags(mid, st, cudaEventRecordExternal) : cudaEventRecord(mid, st);
+    s->box_split = false;
     s->slabs_live = e == cudaSuccess;
     return e;
 }
@@ -4274,8 +4389,7 @@ int tree_slabs(const TreeState* s, const GridD& g, int (*z)[2], cudaEvent_t* ev)
     if (!s->slabs_live || s->nslab <= 1) return 0;
     const int nzb = shape_of(s->variant).nz;
     for (int k = 0; k < s->nslab; ++k) {
-        const int kb0 = (int)(((int64_t)k * s->nbz + s->nslab - 1) / s->nslab);
-        const int kb1 = (int)(((int64_t)(k + 1) * s->nbz + s->nslab - 1) / s->nslab);
+        const int kb0 = slab_start(k, s->nslab, s->nbz), kb1 = slab_start(k + 1, s->nslab, s->nbz);
         z[k][0] = std::min(kb0 * nzb, g.nz);
         z[k][1] = std::min(kb1 * nzb, g.nz);
         ev[k] = s->slab_ev[k];
@@ -4305,18 +4419,18 @@ rism_status tree_eval(TreeState* s, const DevTables& t, const GridD& g, const Ph
         for (int k = 0; k < 4; ++k)
             if (!s->ev[k]) cudaEventCreate(&s->ev[k]);
         cudaEventRecord(s->ev[0], st);
-        cpl = cp_enqueue(s, a, dh, st);
+        cpl = cp_enqueue(s, a, dh, st, true);
         cudaEventRecord(s->ev[1], st);
         e = farnear_enqueue(s, t.smax, a, du, dh, st, false, s->ev[2]);
         cudaEventRecord(s->ev[3], st);
     } else {
-        cpl = cp_enqueue(s, a, dh, st);
+        cpl = cp_enqueue(s, a, dh, st, true);
         e = farnear_enqueue(s, t.smax, a, du, dh, st, false);
     }
     if (e != cudaSuccess) return cuda_err(err, e, "tree eval");
     if ((e = cudaMemcpyAsync(s->h_meta, s->meta, sizeof(TreeMeta), cudaMemcpyDeviceToHost, st)) != cudaSuccess)
         return cuda_err(err, e, "tree meta copy");
-    info.launches += s->launches + 2 * std::max(1, s->nslab) + cpl;
+    info.launches += s->launches + 2 * std::max(1, s->nslab) + cpl + s->box_slab_launches;
     const ShapeDesc sd = shape_of(s->variant);
     info.batch[0] = sd.nx;
     info.batch[1] = sd.ny;
@@ -4457,11 +4571,11 @@ rism_status tree_graph_step(TreeState* s, const DevTables& t, const GridD& g, co
         };
         if (e == cudaSuccess && r == RISM_OK) {
             rec(0);
-            launches += cp_enqueue(s, a, dh, cs);
+            launches += cp_enqueue(s, a, dh, cs, true);
             rec(1);
             if (e == cudaSuccess) e = farnear_enqueue(s, t.smax, a, du, dh, cs, true, timed ? s->ev[2] : nullptr);
             rec(3);
-            launches += 2 * std::max(1, s->nslab);
+            launches += 2 * std::max(1, s->nslab) + s->box_slab_launches;
         }
         if (tail) cudaStreamWaitEvent(cs, G->join, 0);
         if (e == cudaSuccess && r == RISM_OK)
@@ -4597,7 +4711,7 @@ rism_status batch_eval(std::vector<BatchItem>& items, const rism_options& o, cud
             for (int nr = 0; nr < 2; ++nr) {  // global heaviest-first orders over all (solute, batch) items
                 k_gather_work<<<count, 256, 0, cs>>>(bc->d_args, bc->d_off, count, nr, bc->d_work);
                 k_order<<<1, 1024, 0, cs>>>(off[count], bc->d_work, bc->d_order + (size_t)nr * off[count], nullptr,
-                                            nullptr, 1, 1, 1);
+                                            nullptr, order_plain(off[count]));
             }
             BatchEval be{bc->d_args, bc->d_off, count, off[count], bc->d_queue, bc->d_order};
             const bool du = items[0].o.u != nullptr, dh = items[0].o.h != nullptr;

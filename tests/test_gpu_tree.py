@@ -360,3 +360,29 @@ def test_host_outputs_in_z_slabs_ragged_and_empty(R):
             assert np.array_equal(out[k].cpu().numpy().reshape(S, M), host[i]), (step, k)
     for r in (rd, rh):
         r.close()
+
+
+def test_host_outputs_box_level_in_slabs_ordered(R):
+    """With host outputs the target boxes run slab by slab: each z slab first takes the boxes of every level that
+    it needs first, in the heaviest-first box order (1,935 boxes in five levels on the 13,600-atom ellipsoid's
+    224x192x160 grid; z slabs of five batch layers, which split level-0 box layers).  The host grids equal the
+    device grids bit for bit, on the regular path and the replayed one."""
+    import torch
+
+    w = I.workload(2)
+    S, M = w.solvent.nsite, w.grid.npts
+    sol = w.solute
+    rd = R.from_workload(w, method=R.METHOD_TREECODE, precision=R.PREC_FP32)
+    rh = R.from_workload(w, method=R.METHOD_TREECODE, precision=R.PREC_FP32)
+    host = [torch.empty((S, M), dtype=torch.float64).pin_memory().numpy() for _ in range(3)]
+    for step in range(2):
+        rd.set_solute(sol.xyz, sol.q, sol.sigma, sol.eps)
+        out = rd.init()
+        rh.set_solute(sol.xyz, sol.q, sol.sigma, sol.eps)
+        for hb in host:
+            hb.fill(np.nan)
+        rh.init_host(*host)
+        for i, k in enumerate(("u", "c", "h")):
+            assert np.array_equal(out[k].cpu().numpy().reshape(S, M), host[i]), (step, k)
+    for r in (rd, rh):
+        r.close()
