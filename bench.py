@@ -171,8 +171,8 @@ SMS = 152
 # "box" sums the box-level launches of one step (k_cp_work and its k_order where the boxes are ordered,
 # k_cp_eval, k_cp_reduce, k_l2l per level, k_tdown).
 TRAFFIC_BYTES = {
-    "ellipsoid13600_224x192x160": {"k_far32": 163688192, "k_near32": 719262464, "box": 125491968},
-    "globule2000_128cubed": {"k_far32": 34168064, "k_near32": 185520128, "box": 17669632},
+    "ellipsoid13600_224x192x160": {"k_far32": 163232256, "k_near32": 719858944, "box": 125013504},
+    "globule2000_128cubed": {"k_far32": 33913088, "k_near32": 181672960, "box": 17674496},
 }
 
 
