@@ -50,6 +50,32 @@ def test_small_full_half_spectrum(R, grid):
     assert np.all(got["c"][:, 0] == 0)
 
 
+def test_two_mx_blocks_ragged_quads(R):
+    """A grid whose half spectrum spans two 128-wide m_x blocks (nx = 262: 132 m_x) and whose rows end in a
+    ragged quad (ny = 9): every entry against the oracle, for the whole half spectrum (4 groups of 32 m_x per
+    item in the first block, 1 in the second) and two cut-offs (m_x up to about 80 and 49: items of 3, 2, 1 and
+    0 groups, the second block empty)."""
+    w = I.small_workload(n_atoms=60, n=(262, 9, 7), h=0.4, seed=12, ions=True, lj_rcut=4.0, net=1.0)
+    p = O.Problem.from_workload(w)
+    r = R.from_workload(w, method=R.METHOD_DIRECT, precision=R.PREC_FP32)
+    S = r.S
+    full = O.kspace(p)
+    for rel in (0.0, 1e-5, 1e-3):
+        tol = rel * float(np.abs(full["c"]).max())
+        c, h, kc = r.asymptotics_k(tol)
+        assert r.info()["launches"] == 2
+        got = {"c": c.cpu().numpy().reshape(S, -1), "h": h.cpu().numpy().reshape(S, -1)}
+        ref = O.kspace(p, kcut=kc) if kc > 0 else full
+        if kc > 0:
+            keep = np.abs(ref["h"][0]) > 0
+            assert 0 < keep.sum() < keep.size
+            for k in ("c", "h"):
+                assert np.all(got[k][:, ~keep & (np.arange(keep.size) > 0)] == 0)
+        for k in ("c", "h"):
+            _check(got[k], ref[k], f"nx 262, tol {rel} {k}")
+    r.close()
+
+
 def test_cutoff_matches_oracle_root_and_zeroes(R):
     w = I.small_workload(n_atoms=150, n=(40, 36, 33), h=0.5, seed=8, ions=True, lj_rcut=4.0, net=-1.0)
     p = O.Problem.from_workload(w)
