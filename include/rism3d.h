@@ -253,6 +253,36 @@ RISM_API rism_status rism_asymptotics_k(rism_ctx* ctx, double k_tol, double* c_k
  * set_solute/set_solvent. */
 RISM_API rism_status rism_lra_integral(rism_ctx* ctx, double* T, double* atom_sums);
 
+/* The paper's guide to the accuracy parameters for a residual tolerance of
+ * the 3D-RISM solution (Sec. 4.2.1 with Table 3, Sec. 4.3.1, Sec. 4.4.1). */
+typedef struct {
+    /* Table 3: Taylor order of each kernel,
+     *   p_TCF     = max(2, (log10(tolerance) + 5.7) / -0.7)   (h_lr),
+     *   p_DCF     = max(2, (log10(tolerance) + 1.9) / -0.8)   (c_lr),
+     *   p_Coulomb = max(2, (log10(tolerance) + 1.4) / -0.8)   (u),
+     * each rounded up to an integer (the rounding that reproduces the orders
+     * Table 2 lists for the guide's solutes at tolerance 1e-6: 2, 6 and 6).
+     * With RISM_APPROX_TAYLOR one order serves every moment of a box: set
+     * degree to the largest order of the outputs wanted. */
+    int32_t p_tcf, p_dcf, p_coulomb;
+    double mac;      /* Table 3: acceptance parameter 0.3 (set theta to it) */
+    int32_t n0;      /* Table 3: 500 target points per leaf; no counterpart here (the target boxes are fixed
+                        16^3-point grid boxes) */
+    double k_tol;    /* Sec. 4.3.1: error tolerance of the reciprocal-space cut-off (eq. (k-space-dcf-err),
+                        the k_tol of rism_asymptotics_k), 0.04 tolerance^0.9 (the fit to the smaller solutes;
+                        the paper found tubulin to need 0.006 tolerance^1.1) */
+    double lj_tol;   /* Sec. 4.4.1: LJ cut-off tolerance |u_LJ(r_cut)| (the lj_tol of RISM_LJ_TOL), tolerance / 10,
+                        the paper's safe default */
+} rism_guide;
+
+/* rism_parameter_guide -- fill *g with the guide's parameters for the
+ * residual tolerance `tolerance`.  The paper recommends checking a Taylor
+ * order against a run at p + 2, and all of these are starting points.
+ * tolerance: finite, 0 < tolerance < 1; g: host memory, non-NULL; else
+ * RISM_E_INVALID with *g untouched.  Host arithmetic only; needs no context
+ * and no GPU. */
+RISM_API rism_status rism_parameter_guide(double tolerance, rism_guide* g);
+
 /* Largest solute accepted by rism_init_noalloc. */
 #define RISM_NOALLOC_MAX_ATOMS 8192
 

@@ -313,3 +313,27 @@ def taylor_eval(kind, p, center, xyz, q, pts, eta=1.0, kappa_=0.0):
     _load().orc_taylor_eval(TAYLOR_KINDS[kind], int(p), _p(c), len(q), _p(xyz), _p(q), float(eta), float(kappa_),
                             len(pts), _p(pts), _p(out))
     return out
+
+
+def parameter_guide(tolerance):
+    """The paper's accuracy parameters for a residual tolerance of the 3D-RISM solution.  Table 3 (Sec. 4.2.1):
+    MAC 0.3, leaf size N0 = 500 and the Taylor order of each kernel, the least integer p >= 2 that is at least
+    (log10 tolerance + 5.7) / -0.7 for the TCF, (log10 tolerance + 1.9) / -0.8 for the DCF and
+    (log10 tolerance + 1.4) / -0.8 for the Coulomb potential (counted up from 2; a value the expression hits
+    exactly, up to the rounding of log10, is kept).  Sec. 4.3.1: the reciprocal-space cut-off tolerance
+    0.04 tolerance^0.9.  Sec. 4.4.1: the LJ cut-off tolerance, one tenth of the residual tolerance."""
+    import math
+
+    if not (0.0 < tolerance < 1.0) or not math.isfinite(tolerance):
+        raise ValueError("tolerance must lie in (0, 1)")
+    lt = math.log10(tolerance)
+
+    def least_order(intercept, slope):
+        bound = (lt + intercept) / slope
+        p = 2
+        while p < bound - 1e-9:
+            p += 1
+        return p
+
+    return {"p_tcf": least_order(5.7, -0.7), "p_dcf": least_order(1.9, -0.8), "p_coulomb": least_order(1.4, -0.8),
+            "mac": 0.3, "n0": 500, "k_tol": 0.04 * tolerance ** 0.9, "lj_tol": 0.1 * tolerance}

@@ -892,4 +892,21 @@ const char* rism_last_error(const rism_ctx* c) {
     return c->err.c_str();
 }
 
+// Table 3: p = max(2, (log10 tol + a) / -s) per kernel, rounded up; MAC 0.3, N0 500 (the 1e-9 keeps an order
+// that the expression hits exactly, up to the rounding of log10, from rising by one).  Sec. 4.3.1: the
+// reciprocal-space cut-off tolerance 0.04 tol^0.9; Sec. 4.4.1: the LJ cut-off tolerance tol / 10.
+rism_status rism_parameter_guide(double tolerance, rism_guide* g) {
+    if (!g || !std::isfinite(tolerance) || !(tolerance > 0.0) || !(tolerance < 1.0)) return RISM_E_INVALID;
+    const double lt = std::log10(tolerance);
+    auto order = [&](double a, double s) { return (int32_t)std::max(2.0, std::ceil((lt + a) / -s - 1e-9)); };
+    g->p_tcf = order(5.7, 0.7);
+    g->p_dcf = order(1.9, 0.8);
+    g->p_coulomb = order(1.4, 0.8);
+    g->mac = 0.3;
+    g->n0 = 500;
+    g->k_tol = 0.04 * std::pow(tolerance, 0.9);
+    g->lj_tol = tolerance / 10.0;
+    return RISM_OK;
+}
+
 }  // extern "C"

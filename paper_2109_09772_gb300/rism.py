@@ -57,10 +57,15 @@ class Info(C.Structure):
                 ("near_tested", C.c_int64), ("lj_pairs", C.c_int64), ("sr_pairs", C.c_int64)]
 
 
+class Guide(C.Structure):
+    _fields_ = [("p_tcf", C.c_int32), ("p_dcf", C.c_int32), ("p_coulomb", C.c_int32), ("mac", C.c_double),
+                ("n0", C.c_int32), ("k_tol", C.c_double), ("lj_tol", C.c_double)]
+
+
 EXPORTS = ["rism_default_options", "rism_grid_create", "rism_set_solute", "rism_set_solvent", "rism_potential",
            "rism_asymptotics", "rism_init", "rism_potential_backward", "rism_potential_batched", "rism_get_info",
            "rism_destroy", "rism_last_error", "rism_init_noalloc", "rism_lra_integral",
-           "rism_asymptotics_k"]
+           "rism_asymptotics_k", "rism_parameter_guide"]
 NOALLOC_MAX_ATOMS = 8192
 
 _lib = None
@@ -108,6 +113,8 @@ def load(path: str = LIB_PATH):
         lib.rism_init_noalloc.restype = C.c_int
         lib.rism_init_noalloc.argtypes = [C.POINTER(GridDesc), C.POINTER(Options), I64, P, P, P, P, I32, P, P, P, P,
                                           P, P, P, P, P, C.c_char_p, C.c_size_t]
+        lib.rism_parameter_guide.restype = C.c_int
+        lib.rism_parameter_guide.argtypes = [C.c_double, C.POINTER(Guide)]
         _lib = lib
         return lib
 
@@ -295,6 +302,20 @@ def init_noalloc(grid_n, h, origin, xyz, q, sigma, eps, solvent, u=None, c=None,
                                _ptr(u), _ptr(c), _ptr(hh), C.c_void_p(st.cuda_stream), buf, 256)
     if rc != OK:
         raise RismError(rc, "rism_init_noalloc: " + buf.value.decode(errors="replace"))
+
+
+def parameter_guide(tolerance):
+    """rism_parameter_guide: the paper's accuracy parameters for a residual tolerance of the 3D-RISM solution,
+    as a dict: the Taylor orders p_tcf (h_lr), p_dcf (c_lr), p_coulomb (u), the acceptance parameter mac and
+    the leaf size n0 (Table 3), the reciprocal-space cut-off tolerance k_tol (Sec. 4.3.1) and the LJ cut-off
+    tolerance lj_tol (Sec. 4.4.1).  Raises RismError(E_INVALID) unless 0 < tolerance < 1.  Host arithmetic only
+    (no GPU)."""
+    lib = load()
+    g = Guide()
+    st = lib.rism_parameter_guide(float(tolerance), C.byref(g))
+    if st != OK:
+        raise RismError(st, f"rism_parameter_guide: tolerance {tolerance!r} is not in (0, 1)")
+    return {k: getattr(g, k) for k, _ in Guide._fields_}
 
 
 def potential_batched(rs, u=True, c=True, h=True, out=None):

@@ -97,3 +97,20 @@ def test_reverse_mode_in_taylor_context(R):
     ref = O.grad(O.Problem.from_workload(w), atoms, G["u"], G["c"], G["h"])
     for k, v in (("xyz", ref[:, 0:3]), ("q", ref[:, 3]), ("sigma", ref[:, 4]), ("eps", ref[:, 5])):
         assert rel_l2(g[k].cpu().numpy()[atoms], v) <= 2e-5, k
+
+
+def test_parameter_guide_applied(R):
+    """The paper's guide at a residual tolerance of 1e-6 (Table 3: Taylor orders 2 / 6 / 6 for h / c / u, so
+    one order 6 for every moment, MAC 0.3; Sec. 4.4.1: per-pair LJ cut-offs at |u_LJ(r_cut)| = 1e-7): every
+    output within ten times the tolerance (TREE_TOL, 1e-5) of the FP64 oracle with the same LJ cut-offs (the
+    relation between error and residual tolerance of eq. (error-tolerance))."""
+    w0 = I.workload(1)
+    gd = R.parameter_guide(1e-6)
+    assert (gd["p_tcf"], gd["p_dcf"], gd["p_coulomb"], gd["mac"]) == (2, 6, 6, 0.3)
+    w = I.Workload(w0.name, w0.solute, w0.solvent, w0.grid, dict(w0.opts, lj_rcut=0.0, lj_tol=gd["lj_tol"]))
+    idx = np.union1d(I.sample_indices(w.grid.npts, 3000, seed=6), nearest_points(w.grid, w.solute.xyz))
+    ref = O.fields(O.Problem.from_workload(w), idx=idx)
+    g = run(R, w, degree=max(gd["p_tcf"], gd["p_dcf"], gd["p_coulomb"]), theta=gd["mac"])
+    assert g["info"]["cp_pairs"] > 0
+    check_fields({k: g[k][:, idx] for k in ("u", "c", "h")}, ref, ("u", "c", "h"), TREE_TOL, w.grid, w.solute.xyz,
+                 idx=idx, label="guide 1e-6")
